@@ -1,0 +1,311 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms,
+continuous spectra on the circle (Graf's addition theorem), the exact Mie current,
+an independent high-precision integrator (mpmath), the divergence theorem, the
+Woodbury identity, printed values of Table I, and brute-force dense solves.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import bem_oracle as O
+from paper_2210_08580_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def circle_mats():
+    out = {}
+    for N in (64, 128):
+        v = I.regular_polygon(N)
+        out[N] = (v, O.assemble(v, 1.0, "SWD"))
+    return out
+
+
+@pytest.fixture(scope="module")
+def star_case():
+    v, _, _ = I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), 96)
+    k = 1.3
+    mats = O.assemble(v, k, "SWD")
+    return v, k, mats
+
+
+# ------------------------------------------------------------------ special functions
+
+
+def test_bessel_against_mpmath():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    from scipy import special
+    zs = [1e-6, 1e-3, 0.05, 0.7, 2.0, 4.9, 7.99, 8.01, 12.5, 17.0, 26.0]
+    for z in zs:
+        for fn, ref in ((special.j0, lambda x: mp.besselj(0, x)), (special.y0, lambda x: mp.bessely(0, x)),
+                        (special.j1, lambda x: mp.besselj(1, x)), (special.y1, lambda x: mp.bessely(1, x))):
+            a = fn(z)
+            b = float(ref(mp.mpf(z)))
+            assert abs(a - b) <= 2e-15 * max(1.0, abs(b)), (fn, z, a, b)
+
+
+def test_green_log_limit():
+    # DLMF 10.8.2: g2(r) + ln(r)/(2 pi) -> i/4 - (ln(k/2) + gamma)/(2 pi) as r -> 0
+    for k in (1e-3, 1.0, 5.0):
+        r = 1e-9
+        lim = 0.25j - (math.log(k / 2) + np.euler_gamma) / (2 * math.pi)
+        val = O.green(k, r) + math.log(r) / (2 * math.pi)
+        assert abs(val - lim) < 1e-12
+
+
+# ------------------------------------------------------------------ quadrature
+
+
+def _mp_pair(mp, k, x0, tx, hx, y0, ty, hy, a, b, split_inner_at_s=False, kernel="S", nu=None,
+             method="tanh-sinh"):
+    lam = lambda c, u, hh: (1 - u / hh) if c == 0 else (u / hh)
+
+    def g(r):
+        return 0.25j * mp.besselj(0, k * r) - 0.25 * mp.bessely(0, k * r)
+
+    def dg(r, dn):
+        return (-0.25j * k) * (mp.besselj(1, k * r) + 1j * mp.bessely(1, k * r)) / r * dn
+
+    def inner(s):
+        xs = (x0[0] + s * tx[0], x0[1] + s * tx[1])
+
+        def f(t):
+            yt = (y0[0] + t * ty[0], y0[1] + t * ty[1])
+            dx, dy = yt[0] - xs[0], yt[1] - xs[1]
+            r = mp.sqrt(dx * dx + dy * dy)
+            ker = g(r) if kernel == "S" else dg(r, dx * nu[0] + dy * nu[1])
+            return lam(a, s, hx) * lam(b, t, hy) * ker
+        pts = [0, s, hy] if split_inner_at_s else [0, hy]
+        return mp.quad(f, pts, method=method)
+    return complex(mp.quad(inner, [0, hx], method=method))
+
+
+@pytest.mark.parametrize("which", ["self", "adjacent", "near"])
+def test_pair_integrals_against_mpmath(which):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 17
+    v, _, _ = I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), 24)
+    mesh = O.Mesh(v)
+    k = 2.0
+    e = 3
+    f = {"self": 3, "adjacent": 4, "near": 6}[which]
+    Iq, Jq, _ = O.pair_integrals(mesh, k, [e], [f], need_d=True)
+    method = "gauss-legendre" if which == "near" else "tanh-sinh"
+    for (a, b) in ((0, 1), (1, 1)):
+        ref = _mp_pair(mp, k, mesh.P0[e], mesh.t[e], mesh.h[e], mesh.P0[f], mesh.t[f], mesh.h[f],
+                       a, b, split_inner_at_s=(which == "self"), method=method)
+        assert abs(Iq[0, a, b] - ref) <= 1e-13 * abs(ref), (which, a, b, Iq[0, a, b], ref)
+        if which != "self" and (a, b) == (0, 1):
+            refd = _mp_pair(mp, k, mesh.P0[e], mesh.t[e], mesh.h[e], mesh.P0[f], mesh.t[f], mesh.h[f],
+                            a, b, kernel="D", nu=mesh.nu[f], method=method)
+            assert abs(Jq[0, a, b] - refd) <= 1e-12 * abs(refd) + 1e-16, (which, a, b, Jq[0, a, b], refd)
+    if which == "self":
+        assert np.all(Jq == 0)
+
+
+# ------------------------------------------------------------------ discrete operators
+
+
+def test_circulant_and_symmetric(circle_mats):
+    for N, (v, m) in circle_mats.items():
+        for op in "SWD":
+            A = m[op]
+            shifted = np.roll(np.roll(A, 1, 0), 1, 1)
+            assert np.max(np.abs(A - shifted)) <= 1e-13 * np.max(np.abs(A)), op
+        for op in "SW":
+            A = m[op]
+            assert np.max(np.abs(A - A.T)) <= 1e-14 * np.max(np.abs(A)), op
+
+
+def test_circle_spectra_second_order(circle_mats):
+    """Eigenvalues of G^-1 X on the regular polygon converge at O(h^2) to the continuous
+    circle spectra of S, N and D (sign and scale of all three operators)."""
+    k = 1.0
+    ms = np.arange(0, 3)
+    errs = {}
+    for N, (v, m) in circle_mats.items():
+        G = O.gram(v).astype(complex)
+        g = np.fft.fft(G[0])[ms]
+        s_c, w_c, d_c = O.circle_spectra(k, 1.0, ms)
+        errs[N] = [np.abs(np.fft.fft(m[op][0])[ms] / g - ref) / np.abs(ref)
+                   for op, ref in (("S", s_c), ("W", w_c), ("D", d_c))]
+    for i in range(3):
+        ratio = errs[64][i] / errs[128][i]
+        assert np.all(ratio > 3.5) and np.all(ratio < 5.0), (i, ratio)
+        assert np.all(errs[128][i] < 2e-3)
+
+
+def test_calderon_identity_circle():
+    """S N = I/4 + compact: the continuous product of the circle spectra tends to 1/4,
+    and the discrete Z_x = G^-1 S G^-1 N clusters at 1/4 for 1 << |m| << N."""
+    k = 1.0
+    s_c, w_c, _ = O.circle_spectra(k, 1.0, np.array([20, 40, 80]))
+    assert np.all(np.abs(s_c * w_c - 0.25) < np.array([2e-3, 5e-4, 1.5e-4]))
+    N = 256
+    v = I.regular_polygon(N)
+    m = O.assemble(v, k, "SW")
+    G = O.gram(v)
+    Zx = np.linalg.solve(G, m["S"]) @ np.linalg.solve(G, m["W"])
+    z = np.fft.fft(Zx[0])
+    assert np.all(np.abs(z[10:30] - 0.25) < 5e-3)
+    # away from the cluster: the low-frequency m = 0 mode is not near 1/4
+    assert abs(z[0] - 0.25) > 0.1
+
+
+def test_laplace_limit_constant():
+    """As k -> 0, S(k) = S_Laplace + c(k) m m^T + O(k^2) with c(k) = i/4 - (ln(k/2)+gamma)/(2 pi)
+    and m_i = int phi_i (DLMF 10.8.2); the difference of two small k isolates c."""
+    v, _, _ = I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), 40)
+    mesh = O.Mesh(v)
+    k1, k2 = 1e-6, 1e-5
+    S1 = O.assemble(v, k1, "S")["S"]
+    S2 = O.assemble(v, k2, "S")["S"]
+    mvec = 0.5 * (mesh.h + np.roll(mesh.h, 1))
+    c = lambda k: 0.25j - (math.log(k / 2) + np.euler_gamma) / (2 * math.pi)
+    pred = (c(k1) - c(k2)) * np.outer(mvec, mvec)
+    assert np.max(np.abs((S1 - S2) - pred)) <= 1e-8 * np.max(np.abs(pred))
+
+
+def test_rhs_divergence_theorem():
+    """sum_i f_i = -int_Gamma du/dnu = -int_Omega Lap u = k^2 int_Omega u (sum_i phi_i = 1),
+    with the area integral over the polygon done by a triangle fan and collapsed Gauss."""
+    for verts in (I.regular_polygon(48), I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), 64)[0]):
+        k = 1.7
+        ang = np.array([0.0, 0.9, 2.5])
+        f = O.rhs_planewave(verts, k, ang)
+        xs, ws = O.gauss01(24)
+        U, V = np.meshgrid(xs, xs, indexing="ij")
+        W2 = np.outer(ws, ws) * U                                # collapsed-square Jacobian
+        P1 = np.roll(verts, -1, axis=0)
+        area = []
+        for phi in ang:
+            d = np.array([math.cos(phi), math.sin(phi)])
+            tot = 0j
+            for a_, b_ in zip(verts, P1):
+                # triangle (0, a, b): x = U (a + V (b - a))
+                pts = U[..., None] * (a_[None, None, :] + V[..., None] * (b_ - a_)[None, None, :])
+                jac = abs(a_[0] * b_[1] - a_[1] * b_[0])
+                tot += jac * np.sum(W2 * np.exp(1j * k * (pts @ d)))
+            area.append(tot)
+        area = np.array(area)
+        assert np.allclose(f.sum(axis=0), k * k * area, rtol=1e-13, atol=0)
+
+
+# ------------------------------------------------------------------ filter, compression, solve
+
+
+def test_filter_projector_properties(star_case):
+    v, _, _ = star_case
+    N = v.shape[0]
+    n = 21
+    P, lam = O.filter_literal(v, n)
+    assert np.allclose(P @ P, P, atol=1e-12)
+    assert np.allclose(P, P.T, atol=1e-13)
+    assert abs(np.trace(P) - n) < 1e-10
+    G = O.gram(v)
+    Gm = np.linalg.inv(np.linalg.cholesky(G))
+    # P commutes with L~; equal chords make P the projector on the Fourier modes |m| <= 10
+    Q = O.fourier_basis(N, 10)
+    assert np.allclose(P, Q @ Q.T, atol=1e-9)
+    Pk, _ = O.filter_literal(v, n, include_kernel=False)
+    assert abs(np.trace(Pk) - (n - 1)) < 1e-10
+    # the Fourier eigenvalues of the equal-chord Gram matrix
+    g = O.gram_eigs(N, float(np.mean(O.Mesh(v).h)), 10)
+    assert np.allclose(np.einsum("ij,jk,ki->i", Q.T, G, Q), g, rtol=1e-11)
+
+
+def test_woodbury_identity():
+    rng = np.random.default_rng(5)
+    N, r = 50, 7
+    U = rng.standard_normal((N, r)) + 1j * rng.standard_normal((N, r))
+    Vh = rng.standard_normal((r, N)) + 1j * rng.standard_normal((r, N))
+    v = rng.standard_normal((N, 3)) + 1j * rng.standard_normal((N, 3))
+    for beta in (0.25, 0.75):
+        x = O.woodbury_solve(beta, U * 0.1, Vh * 0.1, v)
+        A = beta * np.eye(N) + 0.01 * U @ Vh
+        assert np.max(np.abs(A @ x - v)) <= 1e-13 * np.max(np.abs(v))
+
+
+def test_literal_and_projected_routes_agree(star_case):
+    v, k, mats = star_case
+    f = O.rhs_planewave(v, k, I.planewave_angles(4))
+    lit = O.filtered_solve_literal(mats, v, f, 21, 1e-10)
+    pro = O.filtered_solve_projected(mats, v, f, 10, 1e-10)
+    assert lit["rank"] == pro["rank"]
+    assert np.max(np.abs(lit["x"] - pro["x"])) <= 1e-12 * np.max(np.abs(lit["x"]))
+    # rank(P C) <= n
+    assert lit["rank"] <= 21
+    # the filtered compact part has rank <= n in every representation
+    s = np.linalg.svd(lit["PC"], compute_uv=False)
+    assert np.all(s[21:] < 1e-13 * s[0])
+
+
+def test_woodbury_matches_dense_lu(star_case):
+    """Uncompressed Woodbury = dense LU of (I/4 + P C2); compressed within tol * kappa."""
+    v, k, mats = star_case
+    f = O.rhs_planewave(v, k, I.planewave_angles(3))
+    lit = O.filtered_solve_literal(mats, v, f, 21, 0.0)
+    A = 0.25 * np.eye(v.shape[0]) + lit["PC"]
+    kappa = np.linalg.cond(A)
+    assert np.max(np.abs(lit["x"] - lit["x_full"])) <= 1e-13 * kappa * np.max(np.abs(lit["x_full"]))
+    for tol in (1e-4, 1e-7):
+        c = O.filtered_solve_literal(mats, v, f, 21, tol)
+        err = np.max(np.abs(c["x"] - c["x_full"])) / np.max(np.abs(c["x_full"]))
+        assert err <= 10 * tol * kappa, (tol, err, kappa)
+        assert c["rank"] <= lit["rank"]
+
+
+def test_mie_second_order():
+    """The filtered, compressed solution approaches the exact Mie current at O(h^2)."""
+    k = 1.0
+    errs = []
+    for N in (64, 128):
+        v = I.regular_polygon(N)
+        m = O.assemble(v, k, "SW")
+        ang = np.array([0.3, 2.0])
+        f = O.rhs_planewave(v, k, ang)
+        res = O.filtered_solve_projected(m, v, f, 15, 1e-10)
+        G = O.gram(v)
+        th = 2 * math.pi * np.arange(N) / N
+        e = max(O.g_norm(G, res["x"][:, w] - O.mie_current(k, 1.0, th, ang[w]))[0]
+                / O.g_norm(G, O.mie_current(k, 1.0, th, ang[w]))[0] for w in range(2))
+        errs.append(e)
+    assert errs[1] < 3e-4
+    assert 3.5 < errs[0] / errs[1] < 4.6
+
+
+def test_cfie_filtered_solution_matches_efie():
+    """EFIE, MFIE and the Yukawa-Calderon CFIE (Sec. IV-A) describe the same current:
+    uncompressed filtered solutions for alpha = 0 and alpha = 1 agree to discretisation
+    accuracy, and both approach the Mie current."""
+    N, k = 128, 1.0
+    v = I.regular_polygon(N)
+    m = O.assemble(v, k, "SWD")
+    ang = np.array([0.4])
+    f = O.rhs_planewave(v, k, ang)
+    h2 = O.rhs_planewave_h(v, k, ang)
+    e0 = O.filtered_solve_projected(m, v, f, 15, 0.0)
+    e1 = O.filtered_solve_projected(m, v, f, 15, 0.0, alpha=1.0, h2=h2)
+    th = 2 * math.pi * np.arange(N) / N
+    jm = O.mie_current(k, 1.0, th, ang[0])
+    G = O.gram(v)
+    for res in (e0, e1):
+        assert O.g_norm(G, res["x"][:, 0] - jm)[0] / O.g_norm(G, jm)[0] < 1e-3
+    assert abs(e1["beta"] - 0.75) < 1e-15
+
+
+def test_table1_dense_memory_is_complex128():
+    """Table I's dense-memory column equals N^2 x 16 bytes: the matrices are complex128,
+    the storage the oracle uses."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table1.txt")) if l.strip() and not l.startswith("#")]
+    for N, _err, dense_mb, _skel in rows:
+        N = int(N)
+        assert round(N * N * 16 / 1e6) == int(dense_mb) or abs(N * N * 16 / 1e6 - float(dense_mb)) / float(dense_mb) < 0.01
+    m = O.assemble(I.regular_polygon(8), 1.0, "S")
+    assert m["S"].dtype == np.complex128
