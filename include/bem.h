@@ -1,0 +1,189 @@
+/*
+ * bem.h -- C ABI of the GB300 filtered-Calderon fast direct solver for the 2D TE-EFIE
+ * (and its Yukawa-Calderon CFIE variant), after
+ *   C. Henry et al., "Fast Direct Solvers for Integral Equations at Low-Frequency Based
+ *   on Operator Filtering", EuCAP 2023 (arXiv 2210.08580).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; the library
+ *    never frees them.  Complex data are interleaved (re, im) IEEE doubles
+ *    (the layout of torch.complex128 / cuDoubleComplex).
+ *  - Matrices are column-major: element (i, j) of a block with leading dimension ld is at
+ *    index i + j*ld.  An N x nrhs block of right-hand sides with ld = N is exactly a
+ *    contiguous torch tensor of shape (nrhs, N).
+ *  - A handle owns all internal matrices (S, N, D, the filtered block B, the skeleton
+ *    U, V^H and the LU of the Woodbury core) and its workspace; bem_destroy frees them.
+ *  - All work is enqueued on the handle's CUDA stream.  Calls return after enqueueing,
+ *    except where a host-side result is requested (noted per call), in which case the
+ *    call synchronises that stream.
+ *  - The solver state advances assemble -> filter_apply -> compress_compact -> factor ->
+ *    solve_many / solve_backward.  A call made out of order returns BEM_E_INVALID and
+ *    changes nothing.  Re-running an earlier stage invalidates the later ones.
+ *  - No call aborts, prints or exits.  On failure the status says what kind of error
+ *    happened and bem_last_error(h) returns a message (valid until the next call on h).
+ *  - Meshes must be equal-chord (all segment lengths equal to within 1e-10 relative):
+ *    that makes the P1 Gram and Laplacian matrices circulant, so the Laplacian filter is
+ *    exactly a set of Fourier modes (Sec. III-A).  Other meshes return
+ *    BEM_E_UNSUPPORTED.
+ */
+#ifndef BEM_GB300_H
+#define BEM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BEM_OK = 0,
+    BEM_E_INVALID = 1,        /* bad argument or call out of order */
+    BEM_E_NOMEM = 2,          /* device allocation failed */
+    BEM_E_CUDA = 3,           /* a CUDA runtime call or kernel launch failed */
+    BEM_E_UNSUPPORTED = 4,    /* mesh not equal-chord, k h too large, size limits */
+    BEM_E_SINGULAR = 5,       /* zero pivot in the Woodbury core */
+    BEM_E_NOT_CONVERGED = 6,  /* mixed-precision refinement missed refine_rtol */
+    BEM_E_TIMEOUT = 7         /* a bounded device-side wait gave up */
+} bem_status;
+
+typedef enum {
+    BEM_FP64 = 0,             /* every dense product in FP64 on the CUDA cores */
+    BEM_MIXED_BF16 = 1        /* dense products as split-bf16 tcgen05 GEMMs (FP32 in-MMA
+                                 accumulation, FP64 across K chunks) + FP64 refinement */
+} bem_precision;
+
+enum { BEM_OP_S = 1, BEM_OP_W = 2, BEM_OP_D = 4 };
+
+/* which internal matrix bem_get_matrix copies out */
+enum {
+    BEM_MAT_S = 0,            /* N x N  single layer  [S]_ij = <phi_i, S phi_j>            */
+    BEM_MAT_W = 1,            /* N x N  hypersingular [N]_ij = <phi_i, N phi_j> (Maue)    */
+    BEM_MAT_D = 2,            /* N x N  double layer  [D]_ij = <phi_i, D phi_j>            */
+    BEM_MAT_B = 3,            /* n x N  B = Q^T (C_x - alpha G^-1 D): P C_x = Q B          */
+    BEM_MAT_U = 4,            /* N x r  skeleton left factor                                */
+    BEM_MAT_VH = 5,           /* r x N  skeleton right factor V^H                           */
+    BEM_MAT_SIGMA = 6         /* n real doubles: singular values of the filtered compact
+                                 part in the orthonormal basis, descending                 */
+};
+
+typedef struct {
+    int prec;                 /* bem_precision; default BEM_FP64 */
+    int include_kernel_mode;  /* 1 (default): the filter keeps the constant Laplacian mode;
+                                 0: the literal L_n^+ L_n of eq. (LapFilter), which drops it */
+    double refine_rtol;       /* mixed path: target max relative residual (default 1e-10)  */
+    int max_refine;           /* mixed path: maximum refinement sweeps (default 6)         */
+    int split_slices;         /* mixed path: bf16 slices per operand, 0 = default (6)      */
+} bem_options;
+
+typedef struct {
+    int64_t N;                /* unknowns (vertices = segments)                             */
+    int64_t n;                /* filter modes kept (n = 2M+1 with the constant mode)        */
+    int64_t r;                /* compressed rank                                            */
+    double k;                 /* wavenumber                                                 */
+    double h;                 /* mean chord length                                          */
+    double alpha;             /* CFIE weight (0 = EFIE)                                     */
+    double beta;              /* (1 + 2 alpha) / 4                                          */
+    double sigma_max;         /* largest singular value of the filtered compact part        */
+    int stage;                /* 0 empty, 1 assembled, 2 filtered, 3 compressed, 4 factored */
+    int prec;                 /* bem_precision in use                                       */
+} bem_info;
+
+typedef struct bem_ctx* bem_handle;
+
+/* Fills *opt with the defaults listed in bem_options. */
+void bem_default_options(bem_options* opt);
+
+/* Creates a solver handle on CUDA device `device`, enqueueing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  `opt` may be NULL (defaults). */
+bem_status bem_create(bem_handle* h, int device, void* cuda_stream, const bem_options* opt);
+
+/* Frees everything the handle owns (synchronises its stream first).  NULL is accepted. */
+bem_status bem_destroy(bem_handle h);
+
+/* Message of the last failed call on h (empty string if none). */
+const char* bem_last_error(bem_handle h);
+
+/* Redirects subsequent work to another stream. */
+bem_status bem_set_stream(bem_handle h, void* cuda_stream);
+
+/* bem_assemble -- dense Galerkin matrices of the single-layer S, hypersingular N and
+ * double-layer D operators of Sec. II,
+ *     [X]_ij = <phi_i, X phi_j>,  g2(r) = (i/4) H0^(1)(k r),
+ * on the closed polygon with N vertices verts_xy_dev[2*i], verts_xy_dev[2*i+1]
+ * (counter-clockwise, segment i joins vertex i to vertex i+1 mod N, P1 hats phi_i).
+ * N uses Maue's integration by parts:
+ *     <phi_i, N phi_j> = int int g2 [phi_i' phi_j' - k^2 (nu_x . nu_y) phi_i phi_j].
+ * `ops` is a mask of BEM_OP_S | BEM_OP_W | BEM_OP_D; S and W are needed by the EFIE
+ * path, D by the CFIE (alpha != 0).  Requires N >= 16, k > 0, k*h <= 2.  Synchronises
+ * the stream once (to validate the mesh).  Errors: BEM_E_INVALID (bad arguments),
+ * BEM_E_UNSUPPORTED (chords not equal to 1e-10, k h > 2), BEM_E_NOMEM, BEM_E_CUDA. */
+bem_status bem_assemble(bem_handle h, const double* verts_xy_dev, int64_t N, double k,
+                        unsigned ops);
+
+/* filter_apply -- the Laplacian filter of eq. (LapFilter) applied to the compact part of
+ * the Calderon-preconditioned equation (Sec. IV-A).  With the equal-chord mesh the filter
+ * is P = Q Q^T, Q the N x n real Fourier modes |m| <= M (n = 2M+1; columns ordered
+ * constant, cos 1, sin 1, cos 2, sin 2, ...).  Computes the n x N block
+ *     B = Q^T (G^-1 S G^-1 N - I/4 - alpha G^-1 D)
+ *       = diag(1/g_m) (Q^T S G^-1 N - alpha Q^T D) - Q^T/4,
+ * so that the filtered operator in nodal coordinates is beta I + Q B with
+ * beta = (1 + 2 alpha)/4 (alpha = 0: filtered TE-EFIE; alpha > 0: filtered Yukawa-Calderon
+ * TE-CFIE).  n_modes must be odd, 3 <= n_modes <= min(N - 1, 1023).  Needs S, W (and D if alpha != 0). */
+bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha);
+
+/* compress_compact -- skeleton of the filtered compact part (Sec. IV-C): computes the SVD
+ * of diag(sqrt g) B G^-1/2 (the block in the orthonormal, G^1/2-weighted basis of the
+ * paper) by Householder QR plus one-sided Jacobi, keeps the singular values
+ * sigma_i >= rel_tol * sigma_1 and forms U (N x r), V^H (r x N) with Q B ~= U V^H.
+ * Writes the rank to *rank_out (host pointer, may be NULL); synchronises the stream. */
+bem_status compress_compact(bem_handle h, double rel_tol, int64_t* rank_out);
+
+/* factor -- Woodbury core of (beta I + U V^H)^-1 (Sec. IV-C): K = I_r + beta^-1 V^H U and
+ * its LU factorisation with partial pivoting.  Errors: BEM_E_SINGULAR if a pivot is zero
+ * (reported when solve_many is next called, or here if the stream is synchronised). */
+bem_status factor(bem_handle h);
+
+/* bem_rhs_planewave -- right-hand sides for incident plane waves u_inc = exp(i k d.x),
+ * d = (cos a_w, sin a_w), a_w = angles_dev[w] (device doubles):
+ *     f_i = -<phi_i, d u_inc / d nu>               (the TE-EFIE data times i k, Sec. II)
+ *     v   = G^-1 S G^-1 f - alpha G^-1 h2,  [h2]_i = <phi_i, u_inc>
+ * (v is the right-hand side of beta x + Q B x = v in nodal coordinates).  f_out and v_out
+ * are N x nrhs complex blocks with leading dimension ld >= N; either may be NULL;
+ * 1 <= nrhs <= 65535.
+ * Needs bem_assemble (S); alpha is the value given to filter_apply (0 before). */
+bem_status bem_rhs_planewave(bem_handle h, const double* angles_dev, int64_t nrhs,
+                             void* f_out_dev, void* v_out_dev, int64_t ld);
+
+/* solve_many -- x = (beta I + U V^H)^-1 v by the Woodbury identity (Sec. IV-C):
+ *     x = v/beta - beta^-2 U (I_r + beta^-1 V^H U)^-1 V^H v,
+ * for nrhs columns v (ldv >= N) into x (ldx >= N).  x may not alias v.
+ * In BEM_MIXED_BF16 mode the products run as split-bf16 tensor-core GEMMs and the
+ * result is refined against the FP64 residual v - (beta x + U V^H x) until its max
+ * relative column norm is <= refine_rtol.  iters_out (host, may be NULL) receives the
+ * refinement sweeps used; max_rel_resid_out (host, may be NULL) the max relative residual.
+ * If either pointer is non-NULL the call synchronises the stream.
+ * Errors: BEM_E_NOT_CONVERGED (x holds the best iterate), BEM_E_SINGULAR. */
+bem_status solve_many(bem_handle h, const void* v_dev, int64_t ldv, void* x_dev, int64_t ldx,
+                      int64_t nrhs, int32_t* iters_out, double* max_rel_resid_out);
+
+/* solve_backward -- adjoint solve (beta I + U V^H)^H lambda = g, i.e.
+ *     lambda = g/conj(beta) - conj(beta)^-2 V (I_r + conj(beta)^-1 U^H V)^-1 U^H g,
+ * which gives dJ/dv = lambda for a real loss J of x (the Woodbury identity applied to the
+ * adjoint operator).  Same layouts as solve_many; lambda may not alias g. */
+bem_status solve_backward(bem_handle h, const void* g_dev, int64_t ldg, void* lambda_dev,
+                          int64_t ldl, int64_t nrhs);
+
+/* Copies an internal matrix (BEM_MAT_*) into dst_dev with leading dimension ld (>= rows).
+ * For BEM_MAT_SIGMA, dst_dev receives n doubles and ld is ignored. */
+bem_status bem_get_matrix(bem_handle h, int which, void* dst_dev, int64_t ld);
+
+/* Sizes and scalars of the current state (synchronises the stream). */
+bem_status bem_get_info(bem_handle h, bem_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_GB300_H */

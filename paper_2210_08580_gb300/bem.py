@@ -1,0 +1,209 @@
+"""Thin ctypes binding of the C ABI in include/bem.h.
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``libbem_gb300.so`` (built by ``paper_2210_08580_gb300.build``).  PyTorch provides the
+device memory and the stream.  If the library is missing the import of this module
+succeeds but the first call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbem_gb300.so")
+
+BEM_FP64 = 0
+BEM_MIXED_BF16 = 1
+BEM_OP_S, BEM_OP_W, BEM_OP_D = 1, 2, 4
+MATS = {"S": 0, "W": 1, "N": 1, "D": 2, "B": 3, "U": 4, "Vh": 5, "sigma": 6}
+STATUS = {0: "BEM_OK", 1: "BEM_E_INVALID", 2: "BEM_E_NOMEM", 3: "BEM_E_CUDA", 4: "BEM_E_UNSUPPORTED",
+          5: "BEM_E_SINGULAR", 6: "BEM_E_NOT_CONVERGED", 7: "BEM_E_TIMEOUT"}
+
+# every symbol include/bem.h declares
+EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error", "bem_set_stream",
+           "bem_assemble", "filter_apply", "compress_compact", "factor", "bem_rhs_planewave",
+           "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info")
+
+
+class BemOptions(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("include_kernel_mode", ctypes.c_int),
+                ("refine_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
+                ("split_slices", ctypes.c_int)]
+
+
+class BemInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("n", ctypes.c_int64), ("r", ctypes.c_int64),
+                ("k", ctypes.c_double), ("h", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double), ("sigma_max", ctypes.c_double), ("stage", ctypes.c_int),
+                ("prec", ctypes.c_int)]
+
+
+class BemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build() "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    vp, i64, dbl, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    L.bem_default_options.argtypes = [ctypes.POINTER(BemOptions)]
+    L.bem_default_options.restype = None
+    L.bem_create.argtypes = [ctypes.POINTER(vp), i32, vp, ctypes.POINTER(BemOptions)]
+    L.bem_destroy.argtypes = [vp]
+    L.bem_last_error.argtypes = [vp]
+    L.bem_last_error.restype = ctypes.c_char_p
+    L.bem_set_stream.argtypes = [vp, vp]
+    L.bem_assemble.argtypes = [vp, vp, i64, dbl, ctypes.c_uint]
+    L.filter_apply.argtypes = [vp, i64, dbl]
+    L.compress_compact.argtypes = [vp, dbl, ctypes.POINTER(i64)]
+    L.factor.argtypes = [vp]
+    L.bem_rhs_planewave.argtypes = [vp, vp, i64, vp, vp, i64]
+    L.solve_many.argtypes = [vp, vp, i64, vp, i64, i64, ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(ctypes.c_double)]
+    L.solve_backward.argtypes = [vp, vp, i64, vp, i64, i64]
+    L.bem_get_matrix.argtypes = [vp, i32, vp, i64]
+    L.bem_get_info.argtypes = [vp, ctypes.POINTER(BemInfo)]
+    for name in ("bem_create", "bem_destroy", "bem_set_stream", "bem_assemble", "filter_apply",
+                 "compress_compact", "factor", "bem_rhs_planewave", "solve_many", "solve_backward",
+                 "bem_get_matrix", "bem_get_info"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+class Solver:
+    """One geometry, one handle: assemble -> filter_apply -> compress -> factor -> solve.
+
+    Complex blocks of right-hand sides are torch.complex128 tensors of shape (nrhs, N)
+    (column-major N x nrhs with leading dimension N on the C side).
+    """
+
+    def __init__(self, device: int = 0, prec: str = "fp64", include_kernel_mode: bool = True,
+                 refine_rtol: float = 1e-10, max_refine: int = 6, stream: torch.cuda.Stream | None = None):
+        self.L = load_library()
+        self.device = torch.device("cuda", device)
+        opt = BemOptions()
+        self.L.bem_default_options(ctypes.byref(opt))
+        opt.prec = BEM_MIXED_BF16 if prec == "mixed" else BEM_FP64
+        opt.include_kernel_mode = 1 if include_kernel_mode else 0
+        opt.refine_rtol = refine_rtol
+        opt.max_refine = max_refine
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        self._check(self.L.bem_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream),
+                                      ctypes.byref(opt)), None)
+        self.h = h
+        self.N = None
+        self._ik = bool(include_kernel_mode)
+
+    def _check(self, st, h=-1):
+        if st != 0:
+            hh = self.h if h == -1 else h
+            msg = self.L.bem_last_error(hh).decode() if hh is not None else ""
+            raise BemError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.bem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- stages
+    def assemble(self, verts: torch.Tensor, k: float, ops: str = "SW"):
+        v = verts.to(device=self.device, dtype=torch.float64).contiguous()
+        assert v.ndim == 2 and v.shape[1] == 2
+        mask = (BEM_OP_S if "S" in ops else 0) | (BEM_OP_W if ("W" in ops or "N" in ops) else 0) | \
+               (BEM_OP_D if "D" in ops else 0)
+        self._verts = v
+        self._check(self.L.bem_assemble(self.h, _ptr(v), v.shape[0], float(k), mask))
+        self.N = v.shape[0]
+        self.k = float(k)
+
+    def filter_apply(self, n_modes: int, alpha: float = 0.0):
+        self._check(self.L.filter_apply(self.h, int(n_modes), float(alpha)))
+
+    def compress(self, rel_tol: float) -> int:
+        r = ctypes.c_int64()
+        self._check(self.L.compress_compact(self.h, float(rel_tol), ctypes.byref(r)))
+        return r.value
+
+    def factor(self):
+        self._check(self.L.factor(self.h))
+
+    def rhs_planewave(self, angles, want_f: bool = False, want_v: bool = True):
+        ang = torch.as_tensor(angles, dtype=torch.float64).to(self.device).contiguous()
+        nrhs = ang.numel()
+        f = torch.empty((nrhs, self.N), dtype=torch.complex128, device=self.device) if want_f else None
+        v = torch.empty((nrhs, self.N), dtype=torch.complex128, device=self.device) if want_v else None
+        self._check(self.L.bem_rhs_planewave(self.h, _ptr(ang), nrhs, _ptr(f) if f is not None else None,
+                                             _ptr(v) if v is not None else None, self.N))
+        return (f, v) if want_f else v
+
+    def solve(self, v: torch.Tensor, report: bool = False, out: torch.Tensor | None = None):
+        v = v.contiguous()
+        nrhs = v.shape[0]
+        x = out if out is not None else torch.empty_like(v)
+        it = ctypes.c_int32(0)
+        res = ctypes.c_double(0.0)
+        self._check(self.L.solve_many(self.h, _ptr(v), self.N, _ptr(x), self.N, nrhs,
+                                      ctypes.byref(it) if report else None,
+                                      ctypes.byref(res) if report else None))
+        if report:
+            return x, it.value, res.value
+        return x
+
+    def solve_backward(self, g: torch.Tensor, out: torch.Tensor | None = None):
+        g = g.contiguous()
+        lam = out if out is not None else torch.empty_like(g)
+        self._check(self.L.solve_backward(self.h, _ptr(g), self.N, _ptr(lam), self.N, g.shape[0]))
+        return lam
+
+    # ---------------------------------------------------------------- introspection
+    def info(self) -> dict:
+        inf = BemInfo()
+        self._check(self.L.bem_get_info(self.h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in BemInfo._fields_}
+
+    def matrix(self, name: str) -> torch.Tensor:
+        """Copy of an internal matrix as a (rows, cols) complex128 tensor."""
+        inf = self.info()
+        N, r = inf["N"], inf["r"]
+        nc = inf["n"] if self._include_kernel() else inf["n"] - 1
+        which = MATS[name]
+        if name == "sigma":
+            out = torch.empty(nc, dtype=torch.float64, device=self.device)
+            self._check(self.L.bem_get_matrix(self.h, which, _ptr(out), 0))
+            torch.cuda.synchronize(self.device)
+            return out
+        rows, cols = {"S": (N, N), "W": (N, N), "N": (N, N), "D": (N, N), "B": (nc, N),
+                      "U": (N, r), "Vh": (r, N)}[name]
+        buf = torch.empty((cols, rows), dtype=torch.complex128, device=self.device)
+        self._check(self.L.bem_get_matrix(self.h, which, _ptr(buf), rows))
+        torch.cuda.synchronize(self.device)
+        return buf.T
+
+    def _include_kernel(self) -> bool:
+        return self._ik

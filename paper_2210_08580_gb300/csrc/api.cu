@@ -1,0 +1,518 @@
+// C ABI entry points (include/bem.h): the stage machine of the filtered Calderon fast
+// direct solver, Sec. IV of Henry et al. (EuCAP 2023), on top of the kernels in
+// assemble.cu, linalg.cu and tc_gemm.cu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "kernels.h"
+#include "tc_gemm.h"
+
+bem_status bem_fail(bem_ctx* h, bem_status st, const std::string& msg) {
+    if (h) h->err = msg;
+    return st;
+}
+
+bem_status bem_cuda_check(bem_ctx* h, cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return bem_fail(h, BEM_E_NOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    return bem_fail(h, BEM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bem_status bem_workspace(bem_ctx* h, size_t bytes, void** out) {
+    if (bytes > h->work_bytes) {
+        if (h->work) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->work);
+            h->work = nullptr;
+            h->work_bytes = 0;
+        }
+        size_t want = std::max(bytes, (size_t)1 << 20);
+        BEM_CUDA(h, cudaMalloc(&h->work, want));
+        h->work_bytes = want;
+    }
+    *out = h->work;
+    return BEM_OK;
+}
+
+// carve sub-buffers (256-byte aligned) out of one workspace request
+struct Carve {
+    size_t off = 0;
+    std::vector<std::pair<void**, size_t>> parts;
+    void add(void** p, size_t bytes) { parts.push_back({p, bytes}); off += (bytes + 255) & ~size_t(255); }
+    bem_status commit(bem_ctx* h) {
+        void* base = nullptr;
+        bem_status st = bem_workspace(h, off, &base);
+        if (st != BEM_OK) return st;
+        size_t o = 0;
+        for (auto& pr : parts) { *pr.first = (char*)base + o; o += (pr.second + 255) & ~size_t(255); }
+        return BEM_OK;
+    }
+};
+
+static void free_ptr(void** p) {
+    if (*p) { cudaFree(*p); *p = nullptr; }
+}
+
+static bem_status ensure_alloc(bem_ctx* h, void** p, size_t bytes) {
+    if (*p) return BEM_OK;
+    BEM_CUDA(h, cudaMalloc(p, bytes));
+    return BEM_OK;
+}
+
+static bem_status check_dev_err(bem_ctx* h) {
+    int e = 0;
+    BEM_CUDA(h, cudaMemcpyAsync(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    BEM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (e) {
+        BEM_CUDA(h, cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
+        if (e & DEVERR_TIMEOUT) return bem_fail(h, BEM_E_TIMEOUT, "a device-side wait timed out");
+        if (e & DEVERR_SINGULAR) return bem_fail(h, BEM_E_SINGULAR, "zero pivot in the Woodbury core");
+        return bem_fail(h, BEM_E_CUDA, "device error flag set");
+    }
+    return BEM_OK;
+}
+
+static std::mutex g_tab_mutex;
+static bool g_tab_done[64] = {false};
+
+extern "C" {
+
+void bem_default_options(bem_options* opt) {
+    if (!opt) return;
+    opt->prec = BEM_FP64;
+    opt->include_kernel_mode = 1;
+    opt->refine_rtol = 1e-10;
+    opt->max_refine = 6;
+    opt->split_slices = 0;
+}
+
+bem_status bem_create(bem_handle* out, int device, void* cuda_stream, const bem_options* opt) {
+    if (!out) return BEM_E_INVALID;
+    *out = nullptr;
+    bem_ctx* h = new (std::nothrow) bem_ctx();
+    if (!h) return BEM_E_NOMEM;
+    if (opt) h->opt = *opt; else bem_default_options(&h->opt);
+    if (h->opt.prec != BEM_FP64 && h->opt.prec != BEM_MIXED_BF16) { delete h; return BEM_E_INVALID; }
+    if (h->opt.refine_rtol <= 0.0) h->opt.refine_rtol = 1e-10;
+    if (h->opt.max_refine < 0) h->opt.max_refine = 0;
+    h->device = device;
+    h->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) { delete h; return BEM_E_CUDA; }
+    {
+        std::lock_guard<std::mutex> lk(g_tab_mutex);
+        if (device < 0 || device >= 64) { delete h; return BEM_E_INVALID; }
+        if (!g_tab_done[device]) {
+            if (init_gauss_tables() != cudaSuccess) { delete h; return BEM_E_CUDA; }
+            g_tab_done[device] = true;
+        }
+    }
+    if (cudaMalloc((void**)&h->dev_err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&h->bar, 4 * sizeof(unsigned)) != cudaSuccess) {
+        cudaFree(h->dev_err);
+        delete h;
+        return BEM_E_NOMEM;
+    }
+    cudaMemset(h->dev_err, 0, sizeof(int));
+    cudaMemset(h->bar, 0, 4 * sizeof(unsigned));
+    *out = h;
+    return BEM_OK;
+}
+
+static void free_stage_buffers(bem_ctx* h, int from_stage) {
+    if (from_stage <= 1) {
+        free_ptr((void**)&h->S); free_ptr((void**)&h->W); free_ptr((void**)&h->D);
+        free_ptr((void**)&h->seg);
+        tc_release_operands(h);
+    }
+    if (from_stage <= 2) {
+        free_ptr((void**)&h->B); free_ptr((void**)&h->gm); free_ptr((void**)&h->Q);
+        free_ptr((void**)&h->Bs);
+    }
+    if (from_stage <= 3) {
+        free_ptr((void**)&h->sigma); free_ptr((void**)&h->E);
+        free_ptr((void**)&h->U); free_ptr((void**)&h->Vh);
+    }
+    if (from_stage <= 4) {
+        free_ptr((void**)&h->K); free_ptr((void**)&h->piv);
+        tc_release_solve(h);
+    }
+}
+
+bem_status bem_destroy(bem_handle h) {
+    if (!h) return BEM_OK;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    free_stage_buffers(h, 0);
+    tc_destroy(h);
+    free_ptr(&h->work);
+    free_ptr((void**)&h->dev_err);
+    free_ptr((void**)&h->bar);
+    delete h;
+    return BEM_OK;
+}
+
+const char* bem_last_error(bem_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+bem_status bem_set_stream(bem_handle h, void* s) {
+    if (!h) return BEM_E_INVALID;
+    h->stream = (cudaStream_t)s;
+    return BEM_OK;
+}
+
+bem_status bem_assemble(bem_handle h, const double* verts, int64_t N, double k, unsigned ops) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (!verts || N < 16 || N > (1 << 20) || !(k > 0.0) || !std::isfinite(k) || (ops & ~7u) || !(ops & 3u))
+        return bem_fail(h, BEM_E_INVALID, "bem_assemble: need verts, 16 <= N <= 2^20, k > 0, ops with S or W");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    if (N != h->N) free_stage_buffers(h, 0);
+    else free_stage_buffers(h, 2);
+    h->stage = 0;
+    const size_t NN = (size_t)N * (size_t)N;
+    bem_status st;
+    if ((st = ensure_alloc(h, (void**)&h->seg, sizeof(double) * 5 * N)) != BEM_OK) return st;
+    // S and W are always assembled together (the EFIE needs both); D on request
+    if ((st = ensure_alloc(h, (void**)&h->S, sizeof(cplx) * NN)) != BEM_OK) return st;
+    if ((st = ensure_alloc(h, (void**)&h->W, sizeof(cplx) * NN)) != BEM_OK) return st;
+    if (ops & BEM_OP_D) {
+        if ((st = ensure_alloc(h, (void**)&h->D, sizeof(cplx) * NN)) != BEM_OK) return st;
+    } else {
+        free_ptr((void**)&h->D);
+    }
+    h->N = N;
+    h->k = k;
+    double* stats = nullptr;
+    Carve cv; cv.add((void**)&stats, 3 * sizeof(double));
+    if ((st = cv.commit(h)) != BEM_OK) return st;
+    if ((st = launch_geometry(h, verts, N, stats)) != BEM_OK) return st;
+    double hs[3];
+    BEM_CUDA(h, cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, h->stream));
+    BEM_CUDA(h, cudaStreamSynchronize(h->stream));
+    const double hmean = hs[2] / (double)N;
+    if (!(hs[0] > 0.0) || !std::isfinite(hs[2]))
+        return bem_fail(h, BEM_E_INVALID, "bem_assemble: degenerate or non-finite vertices");
+    if ((hs[1] - hs[0]) > 1e-10 * hmean)
+        return bem_fail(h, BEM_E_UNSUPPORTED, "bem_assemble: mesh is not equal-chord (spread " +
+                                                  std::to_string((hs[1] - hs[0]) / hmean) + ")");
+    if (k * hs[1] > 2.0)
+        return bem_fail(h, BEM_E_UNSUPPORTED, "bem_assemble: k h > 2 (mesh too coarse for this frequency)");
+    h->hbar = hmean;
+    h->ops = BEM_OP_S | BEM_OP_W | (ops & BEM_OP_D);
+    if ((st = launch_assemble(h, h->ops)) != BEM_OK) return st;
+    if (h->opt.prec == BEM_MIXED_BF16) {
+        if ((st = tc_prepare_operators(h)) != BEM_OK) return st;
+    }
+    h->stage = 1;
+    return BEM_OK;
+}
+
+bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 1) return bem_fail(h, BEM_E_INVALID, "filter_apply: call bem_assemble first");
+    const int64_t N = h->N;
+    if (n_modes < 3 || (n_modes % 2) == 0 || n_modes > N - 1 || n_modes > 1023)
+        return bem_fail(h, BEM_E_INVALID, "filter_apply: n_modes must be odd, 3 <= n <= min(N-1, 1023)");
+    if (!std::isfinite(alpha) || alpha < 0.0)
+        return bem_fail(h, BEM_E_INVALID, "filter_apply: alpha must be finite and >= 0");
+    if (alpha != 0.0 && !h->D)
+        return bem_fail(h, BEM_E_INVALID, "filter_apply: alpha != 0 needs D (assemble with BEM_OP_D)");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    free_stage_buffers(h, 2);
+    h->stage = 1;
+    const int inc = h->opt.include_kernel_mode ? 1 : 0;
+    const int64_t nc = inc ? n_modes : n_modes - 1;
+    bem_status st;
+    if ((st = ensure_alloc(h, (void**)&h->B, sizeof(cplx) * nc * N)) != BEM_OK) return st;
+    if ((st = ensure_alloc(h, (void**)&h->gm, sizeof(double) * nc)) != BEM_OK) return st;
+    if ((st = ensure_alloc(h, (void**)&h->Q, sizeof(double) * nc * N)) != BEM_OK) return st;
+    h->n = n_modes;
+    h->ncols = nc;
+    h->M = (n_modes - 1) / 2;
+    h->alpha = alpha;
+    h->beta = (1.0 + 2.0 * alpha) / 4.0;
+    if ((st = launch_fourier_basis(h, h->Q, N, nc, inc, h->gm, h->hbar)) != BEM_OK) return st;
+    cplx *Y1 = nullptr, *tmp = nullptr;
+    Carve cv;
+    cv.add((void**)&Y1, sizeof(cplx) * nc * N);
+    cv.add((void**)&tmp, sizeof(cplx) * nc * N);
+    if ((st = cv.commit(h)) != BEM_OK) return st;
+    if (h->opt.prec == BEM_MIXED_BF16) {
+        // Y1 = Q^T S and B = Y2 N as split-bf16 tensor-core products
+        if ((st = tc_product_left(h, TC_OP_S, h->Q, nullptr, nc, Y1)) != BEM_OK) return st;
+    } else {
+        // Y1 = Q^T S  (ncols x N)
+        if ((st = dzgemm_realA(h, OP_T, nc, N, N, 1.0, h->Q, N, h->S, N, 0.0, Y1, nc)) != BEM_OK) return st;
+    }
+    // Y2 = Y1 G^-1 (along the N index of each row)
+    if ((st = apply_gram_inverse(h, 0, Y1, Y1, tmp, N, nc, nc, 1, h->hbar, false)) != BEM_OK) return st;
+    if (h->opt.prec == BEM_MIXED_BF16) {
+        if ((st = tc_product_left(h, TC_OP_W, nullptr, Y1, nc, h->B)) != BEM_OK) return st;
+        if (alpha != 0.0) {
+            if ((st = tc_product_left(h, TC_OP_D, h->Q, nullptr, nc, tmp)) != BEM_OK) return st;
+            if ((st = launch_axpby(h, h->B, nc, tmp, nc, cmk(-alpha, 0), cmk(1, 0), nc, N)) != BEM_OK) return st;
+        }
+    } else {
+        // B = Y2 N  (- alpha Q^T D)
+        if ((st = zgemm(h, OP_N, OP_N, nc, N, N, cmk(1, 0), Y1, nc, h->W, N, cmk(0, 0), h->B, nc)) != BEM_OK) return st;
+        if (alpha != 0.0)
+            if ((st = dzgemm_realA(h, OP_T, nc, N, N, -alpha, h->Q, N, h->D, N, 1.0, h->B, nc)) != BEM_OK) return st;
+    }
+    // B = diag(1/g) B - Q^T/4
+    if ((st = launch_finish_B(h, h->B, h->gm, h->Q, nc, N)) != BEM_OK) return st;
+    h->stage = 2;
+    return BEM_OK;
+}
+
+bem_status compress_compact(bem_handle h, double rel_tol, int64_t* rank_out) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 2) return bem_fail(h, BEM_E_INVALID, "compress_compact: call filter_apply first");
+    if (!std::isfinite(rel_tol) || rel_tol >= 1.0)
+        return bem_fail(h, BEM_E_INVALID, "compress_compact: rel_tol must be < 1");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    free_stage_buffers(h, 3);
+    h->stage = 2;
+    const int64_t N = h->N, nc = h->ncols;
+    bem_status st;
+    if ((st = ensure_alloc(h, (void**)&h->sigma, sizeof(double) * nc)) != BEM_OK) return st;
+    if ((st = ensure_alloc(h, (void**)&h->E, sizeof(cplx) * nc * nc)) != BEM_OK) return st;
+    if ((st = ensure_alloc(h, (void**)&h->Bs, sizeof(cplx) * nc * N)) != BEM_OK) return st;
+    cplx *X = nullptr, *R = nullptr;
+    double* Qs = nullptr;
+    Carve cv;
+    cv.add((void**)&X, sizeof(cplx) * nc * N);
+    cv.add((void**)&R, sizeof(cplx) * nc * nc);
+    cv.add((void**)&Qs, sizeof(double) * nc * N);
+    if ((st = cv.commit(h)) != BEM_OK) return st;
+    // Bs = diag(sqrt g) B ;  X = (Bs F^-1)^H  (N x nc, stored with row stride nc)
+    if ((st = launch_row_scale(h, h->B, h->Bs, h->gm, 1, nc, N, nc)) != BEM_OK) return st;
+    if ((st = apply_gram_inverse(h, 1, h->Bs, X, nullptr, N, nc, nc, 1, h->hbar, true)) != BEM_OK) return st;
+    if ((st = launch_house_qr(h, X, N, (int)nc, R)) != BEM_OK) return st;
+    if ((st = launch_jacobi_svd(h, R, (int)nc, h->sigma, h->E)) != BEM_OK) return st;
+    std::vector<double> sig(nc);
+    BEM_CUDA(h, cudaMemcpyAsync(sig.data(), h->sigma, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->stream));
+    if ((st = check_dev_err(h)) != BEM_OK) return st;
+    h->sigma_max = sig[0];
+    int64_t r = 0;
+    for (int64_t i = 0; i < nc; ++i) {
+        if (rel_tol > 0.0 ? (sig[i] >= rel_tol * sig[0]) : (sig[i] > 0.0)) ++r;
+    }
+    if (r < 1) r = 1;
+    h->r = r;
+    if ((st = ensure_alloc(h, (void**)&h->U, sizeof(cplx) * N * r)) != BEM_OK) return st;
+    if ((st = ensure_alloc(h, (void**)&h->Vh, sizeof(cplx) * r * N)) != BEM_OK) return st;
+    // U = Q diag(g^-1/2) E_r ;  V^H = E_r^H diag(g^1/2) B
+    if ((st = launch_scale_real_cols(h, h->Q, Qs, h->gm, -1, N, nc)) != BEM_OK) return st;
+    if ((st = dzgemm_realA(h, OP_N, N, r, nc, 1.0, Qs, N, h->E, nc, 0.0, h->U, N)) != BEM_OK) return st;
+    if ((st = zgemm(h, OP_C, OP_N, r, N, nc, cmk(1, 0), h->E, nc, h->Bs, nc, cmk(0, 0), h->Vh, r)) != BEM_OK) return st;
+    if (rank_out) *rank_out = r;
+    h->stage = 3;
+    return BEM_OK;
+}
+
+bem_status factor(bem_handle h) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 3) return bem_fail(h, BEM_E_INVALID, "factor: call compress_compact first");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    free_stage_buffers(h, 4);
+    h->stage = 3;
+    const int64_t N = h->N, r = h->r;
+    bem_status st;
+    if ((st = ensure_alloc(h, (void**)&h->K, sizeof(cplx) * r * r)) != BEM_OK) return st;
+    cplx* Kt = nullptr;
+    Carve cv;
+    cv.add((void**)&Kt, sizeof(cplx) * r * r);
+    if ((st = cv.commit(h)) != BEM_OK) return st;
+    // K = I_r + beta^-1 V^H U, stored as its inverse
+    if ((st = zgemm(h, OP_N, OP_N, r, r, N, cmk(1.0 / h->beta, 0), h->Vh, r, h->U, N, cmk(0, 0), Kt, r)) != BEM_OK) return st;
+    if ((st = launch_add_identity(h, Kt, r, (int)r, cmk(1, 0))) != BEM_OK) return st;
+    if ((st = launch_gauss_jordan(h, Kt, h->K, (int)r)) != BEM_OK) return st;
+    if (h->opt.prec == BEM_MIXED_BF16) {
+        if ((st = tc_prepare_solve(h)) != BEM_OK) return st;
+    }
+    if ((st = check_dev_err(h)) != BEM_OK) return st;
+    h->stage = 4;
+    return BEM_OK;
+}
+
+bem_status bem_rhs_planewave(bem_handle h, const double* angles, int64_t nrhs, void* f_out, void* v_out, int64_t ld) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 1) return bem_fail(h, BEM_E_INVALID, "bem_rhs_planewave: call bem_assemble first");
+    const int64_t N = h->N;
+    if (!angles || nrhs < 1 || nrhs > 65535 || ld < N)
+        return bem_fail(h, BEM_E_INVALID, "bem_rhs_planewave: need angles, 1 <= nrhs <= 65535, ld >= N");
+    if (!f_out && !v_out) return BEM_OK;
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    bem_status st;
+    // every internal block uses the caller's leading dimension ld
+    cplx *f = (cplx*)f_out, *hz = nullptr, *y = nullptr, *tmp = nullptr;
+    Carve cv;
+    if (!f) cv.add((void**)&f, sizeof(cplx) * ld * nrhs);
+    if (v_out) {
+        if (h->alpha != 0.0) cv.add((void**)&hz, sizeof(cplx) * ld * nrhs);
+        cv.add((void**)&y, sizeof(cplx) * ld * nrhs);
+        cv.add((void**)&tmp, sizeof(cplx) * ld * nrhs);
+    }
+    if ((st = cv.commit(h)) != BEM_OK) return st;
+    if ((st = launch_rhs(h, angles, nrhs, f, hz, ld)) != BEM_OK) return st;
+    if (!v_out) return BEM_OK;
+    cplx* v = (cplx*)v_out;
+    // y = G^-1 f
+    if ((st = apply_gram_inverse(h, 0, f, y, tmp, N, nrhs, 1, ld, h->hbar, false)) != BEM_OK) return st;
+    // v <- S y (- alpha h2), then v <- G^-1 v
+    if (h->opt.prec == BEM_MIXED_BF16) {
+        if ((st = tc_product_right(h, TC_OP_S, y, ld, nrhs, v, ld)) != BEM_OK) return st;
+    } else {
+        if ((st = zgemm(h, OP_N, OP_N, N, nrhs, N, cmk(1, 0), h->S, N, y, ld, cmk(0, 0), v, ld)) != BEM_OK) return st;
+    }
+    if (hz) {
+        if ((st = launch_axpby(h, v, ld, hz, ld, cmk(-h->alpha, 0), cmk(1, 0), N, nrhs)) != BEM_OK) return st;
+    }
+    if ((st = apply_gram_inverse(h, 0, v, v, tmp, N, nrhs, 1, ld, h->hbar, false)) != BEM_OK) return st;
+    return BEM_OK;
+}
+
+// x = v/beta - beta^-2 U Kinv V^H v, all FP64 products
+static bem_status woodbury_fp64(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x, int64_t ldx, int64_t nrhs,
+                                cplx* T, cplx* T2) {
+    const int64_t N = h->N, r = h->r;
+    bem_status st;
+    if ((st = zgemm(h, OP_N, OP_N, r, nrhs, N, cmk(1, 0), h->Vh, r, v, ldv, cmk(0, 0), T, r)) != BEM_OK) return st;
+    if ((st = zgemm(h, OP_N, OP_N, r, nrhs, r, cmk(1, 0), h->K, r, T, r, cmk(0, 0), T2, r)) != BEM_OK) return st;
+    if ((st = launch_axpby(h, x, ldx, v, ldv, cmk(1.0 / h->beta, 0), cmk(0, 0), N, nrhs)) != BEM_OK) return st;
+    return zgemm(h, OP_N, OP_N, N, nrhs, r, cmk(-1.0 / (h->beta * h->beta), 0), h->U, N, T2, r, cmk(1, 0), x, ldx);
+}
+
+// rho = v - (beta x + U V^H x), FP64
+static bem_status residual_fp64(bem_ctx* h, const cplx* v, int64_t ldv, const cplx* x, int64_t ldx, int64_t nrhs,
+                                cplx* rho, cplx* T) {
+    const int64_t N = h->N, r = h->r;
+    bem_status st;
+    if ((st = zgemm(h, OP_N, OP_N, r, nrhs, N, cmk(1, 0), h->Vh, r, x, ldx, cmk(0, 0), T, r)) != BEM_OK) return st;
+    if ((st = launch_copy2d(h, rho, N, v, ldv, N, nrhs, sizeof(cplx))) != BEM_OK) return st;
+    if ((st = launch_axpby(h, rho, N, x, ldx, cmk(-h->beta, 0), cmk(1, 0), N, nrhs)) != BEM_OK) return st;
+    return zgemm(h, OP_N, OP_N, N, nrhs, r, cmk(-1, 0), h->U, N, T, r, cmk(1, 0), rho, N);
+}
+
+bem_status solve_many(bem_handle h, const void* v_dev, int64_t ldv, void* x_dev, int64_t ldx, int64_t nrhs,
+                      int32_t* iters_out, double* max_rel_resid_out) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 4) return bem_fail(h, BEM_E_INVALID, "solve_many: call factor first");
+    const int64_t N = h->N, r = h->r;
+    if (!v_dev || !x_dev || nrhs < 1 || nrhs > (1 << 24) || ldv < N || ldx < N || v_dev == x_dev)
+        return bem_fail(h, BEM_E_INVALID, "solve_many: need v, x (not aliased), nrhs >= 1, ld >= N");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    const cplx* v = (const cplx*)v_dev;
+    cplx* x = (cplx*)x_dev;
+    bem_status st;
+    if (h->opt.prec == BEM_MIXED_BF16) {
+        int32_t it = 0;
+        double res = 0.0;
+        st = tc_solve_refined(h, v, ldv, x, ldx, nrhs, &it, &res);
+        if (iters_out) *iters_out = it;
+        if (max_rel_resid_out) *max_rel_resid_out = res;
+        return st;
+    }
+    cplx *T = nullptr, *T2 = nullptr, *rho = nullptr;
+    Carve cv;
+    cv.add((void**)&T, sizeof(cplx) * r * nrhs);
+    cv.add((void**)&T2, sizeof(cplx) * r * nrhs);
+    if (max_rel_resid_out) cv.add((void**)&rho, sizeof(cplx) * N * nrhs);
+    if ((st = cv.commit(h)) != BEM_OK) return st;
+    if ((st = woodbury_fp64(h, v, ldv, x, ldx, nrhs, T, T2)) != BEM_OK) return st;
+    if (iters_out) *iters_out = 0;
+    if (max_rel_resid_out) {
+        double* dres = (double*)T2;     // reuse
+        if ((st = residual_fp64(h, v, ldv, x, ldx, nrhs, rho, T)) != BEM_OK) return st;
+        if ((st = launch_col_norm_ratio(h, rho, N, v, ldv, N, nrhs, dres)) != BEM_OK) return st;
+        BEM_CUDA(h, cudaMemcpyAsync(max_rel_resid_out, dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (iters_out || max_rel_resid_out) return check_dev_err(h);
+    return BEM_OK;
+}
+
+bem_status solve_backward(bem_handle h, const void* g_dev, int64_t ldg, void* lam_dev, int64_t ldl, int64_t nrhs) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 4) return bem_fail(h, BEM_E_INVALID, "solve_backward: call factor first");
+    const int64_t N = h->N, r = h->r;
+    if (!g_dev || !lam_dev || nrhs < 1 || ldg < N || ldl < N || g_dev == lam_dev)
+        return bem_fail(h, BEM_E_INVALID, "solve_backward: need g, lambda (not aliased), nrhs >= 1, ld >= N");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    const cplx* g = (const cplx*)g_dev;
+    cplx* lam = (cplx*)lam_dev;
+    bem_status st;
+    cplx *T = nullptr, *T2 = nullptr;
+    Carve cv;
+    cv.add((void**)&T, sizeof(cplx) * r * nrhs);
+    cv.add((void**)&T2, sizeof(cplx) * r * nrhs);
+    if ((st = cv.commit(h)) != BEM_OK) return st;
+    // lambda = g/beta - beta^-2 V Kinv^H U^H g  (beta real)
+    if ((st = zgemm(h, OP_C, OP_N, r, nrhs, N, cmk(1, 0), h->U, N, g, ldg, cmk(0, 0), T, r)) != BEM_OK) return st;
+    if ((st = zgemm(h, OP_C, OP_N, r, nrhs, r, cmk(1, 0), h->K, r, T, r, cmk(0, 0), T2, r)) != BEM_OK) return st;
+    if ((st = launch_axpby(h, lam, ldl, g, ldg, cmk(1.0 / h->beta, 0), cmk(0, 0), N, nrhs)) != BEM_OK) return st;
+    return zgemm(h, OP_C, OP_N, N, nrhs, r, cmk(-1.0 / (h->beta * h->beta), 0), h->Vh, r, T2, r, cmk(1, 0), lam, ldl);
+}
+
+bem_status bem_get_matrix(bem_handle h, int which, void* dst, int64_t ld) {
+    if (!h || !dst) return BEM_E_INVALID;
+    h->err.clear();
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    const int64_t N = h->N;
+    switch (which) {
+        case BEM_MAT_S: case BEM_MAT_W: case BEM_MAT_D: {
+            const cplx* src = which == BEM_MAT_S ? h->S : (which == BEM_MAT_W ? h->W : h->D);
+            if (h->stage < 1 || !src) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: not assembled");
+            if (ld < N) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: ld < rows");
+            return launch_copy2d(h, dst, ld, src, N, N, N, sizeof(cplx));
+        }
+        case BEM_MAT_B:
+            if (h->stage < 2) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: not filtered");
+            if (ld < h->ncols) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: ld < rows");
+            return launch_copy2d(h, dst, ld, h->B, h->ncols, h->ncols, N, sizeof(cplx));
+        case BEM_MAT_U:
+            if (h->stage < 3) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: not compressed");
+            if (ld < N) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: ld < rows");
+            return launch_copy2d(h, dst, ld, h->U, N, N, h->r, sizeof(cplx));
+        case BEM_MAT_VH:
+            if (h->stage < 3) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: not compressed");
+            if (ld < h->r) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: ld < rows");
+            return launch_copy2d(h, dst, ld, h->Vh, h->r, h->r, N, sizeof(cplx));
+        case BEM_MAT_SIGMA:
+            if (h->stage < 3) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: not compressed");
+            BEM_CUDA(h, cudaMemcpyAsync(dst, h->sigma, sizeof(double) * h->ncols, cudaMemcpyDeviceToDevice, h->stream));
+            return BEM_OK;
+        default:
+            return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: unknown matrix");
+    }
+}
+
+bem_status bem_get_info(bem_handle h, bem_info* info) {
+    if (!h || !info) return BEM_E_INVALID;
+    cudaSetDevice(h->device);
+    BEM_CUDA(h, cudaStreamSynchronize(h->stream));
+    info->N = h->N;
+    info->n = h->n;
+    info->r = h->r;
+    info->k = h->k;
+    info->h = h->hbar;
+    info->alpha = h->alpha;
+    info->beta = h->beta;
+    info->sigma_max = h->sigma_max;
+    info->stage = h->stage;
+    info->prec = h->opt.prec;
+    return BEM_OK;
+}
+
+}  // extern "C"

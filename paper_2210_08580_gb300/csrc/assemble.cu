@@ -1,0 +1,487 @@
+// Dense Galerkin assembly of S, N (Maue form) and D on a closed polygon (Sec. II), and the
+// plane-wave right-hand sides.  FP64 throughout: the Hankel kernels are evaluated by the
+// project's own Bessel routines (bessel.cuh); singular pairs use closed forms.
+//
+// Work decomposition: a CTA owns a T x T tile of vertex pairs (i, j) in the upper
+// triangle of tiles.  It first computes the 2x2 local integrals of the (T+1)^2 segment
+// pairs that touch the tile into shared memory, then combines them into vertex entries
+// (vertex i = segment i as its first node, segment i-1 as its second) and writes the tile
+// and, for off-diagonal tiles, its mirror (S and N are complex symmetric; D's mirror
+// uses the integrals with the normal on the other segment).  Stores are column-major and
+// coalesced along i.
+#include <math.h>
+#include <stdio.h>
+
+#include "bessel.cuh"
+#include "kernels.h"
+
+#define GL_MAXQ 16
+__constant__ double c_glx[GL_MAXQ * (GL_MAXQ + 1) / 2];
+__constant__ double c_glw[GL_MAXQ * (GL_MAXQ + 1) / 2];
+__device__ __forceinline__ int gl_off(int q) { return q * (q - 1) / 2; }
+
+// Gauss-Legendre nodes/weights on [0,1] for q = 1..16 by Newton's method on P_q.
+cudaError_t init_gauss_tables() {
+    double hx[GL_MAXQ * (GL_MAXQ + 1) / 2], hw[GL_MAXQ * (GL_MAXQ + 1) / 2];
+    for (int q = 1; q <= GL_MAXQ; ++q) {
+        for (int i = 0; i < q; ++i) {
+            double x = cos(M_PI * (i + 0.75) / (q + 0.5));
+            double dp = 1.0;
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1.0, p1 = x;
+                for (int n = 2; n <= q; ++n) {
+                    double p2 = ((2.0 * n - 1.0) * x * p1 - (n - 1.0) * p0) / n;
+                    p0 = p1; p1 = p2;
+                }
+                double pq = (q == 1) ? x : p1;
+                double pqm1 = (q == 1) ? 1.0 : p0;
+                dp = q * (x * pq - pqm1) / (x * x - 1.0);
+                double dx = pq / dp;
+                x -= dx;
+                if (fabs(dx) < 1e-17) break;
+            }
+            // recompute derivative at the converged node
+            double p0 = 1.0, p1 = x;
+            for (int n = 2; n <= q; ++n) {
+                double p2 = ((2.0 * n - 1.0) * x * p1 - (n - 1.0) * p0) / n;
+                p0 = p1; p1 = p2;
+            }
+            double pq = (q == 1) ? x : p1, pqm1 = (q == 1) ? 1.0 : p0;
+            dp = q * (x * pq - pqm1) / (x * x - 1.0);
+            double w = 2.0 / ((1.0 - x * x) * dp * dp);
+            int o = q * (q - 1) / 2 + (q - 1 - i);      // ascending order on [0,1]
+            hx[o] = 0.5 * (x + 1.0);
+            hw[o] = 0.5 * w;
+        }
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_glx, hx, sizeof(hx));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_glw, hw, sizeof(hw));
+}
+
+// Coefficients of the small-r expansions (DLMF 10.8.1, 10.8.2), H_m harmonic numbers:
+//   alpha_m = (-1)^m (k/2)^{2m} / (m!)^2
+//   A_m = alpha_m [ i/4 - (ln(k/2) + gamma)/(2 pi) + H_m/(2 pi) ],  B_m = -alpha_m / (2 pi)
+//   delta_m = (-1)^m (k/2)^{2m} / (m! (m+1)!)
+//   E_m = delta_m k^2 [ -i/8 + (ln(k/2) + gamma)/(4 pi) - (H_m + H_{m+1})/(8 pi) ],
+//   F_m = delta_m k^2 / (4 pi)
+void series_coefficients(double k, double rmax, SeriesCoef* sc) {
+    const double lk = log(0.5 * k) + BEM_EULER_GAMMA;
+    double Hm = 0.0, am = 1.0, dm = 1.0;
+    int nm = 0;
+    for (int m = 0; m < BEM_SERIES_MAX; ++m) {
+        if (m > 0) {
+            Hm += 1.0 / m;
+            am *= -(0.25 * k * k) / ((double)m * m);
+            dm *= -(0.25 * k * k) / ((double)m * (m + 1));
+        }
+        const double Hm1 = Hm + 1.0 / (m + 1);
+        sc->A[m] = make_double2(am * (-lk / (2 * BEM_PI) + Hm / (2 * BEM_PI)), 0.25 * am);
+        sc->B[m] = -am / (2 * BEM_PI);
+        sc->E[m] = make_double2(dm * k * k * (lk / (4 * BEM_PI) - (Hm + Hm1) / (8 * BEM_PI)),
+                                -0.125 * dm * k * k);
+        sc->F[m] = dm * k * k / (4 * BEM_PI);
+        nm = m + 1;
+        // stop once the m-th term at r = rmax is negligible against the leading one
+        const double r2m = pow(rmax, 2.0 * m);
+        if (m > 1 && fabs(am) * r2m * (1.0 + fabs(log(rmax))) < 1e-19 &&
+            fabs(dm) * k * k * r2m * (1.0 + fabs(log(rmax))) < 1e-19 * k * k)
+            break;
+    }
+    sc->nm = nm;
+}
+
+struct AsmParams {
+    int N;
+    double k;
+    const double* seg;   // SoA x0[N], y0[N], tx[N], ty[N], h[N]
+    cplx *S, *W, *D;
+    int64_t ld;
+    int nT;
+    SeriesCoef sc;
+};
+
+struct SegV { double x0, y0, tx, ty, h; };
+
+__device__ __forceinline__ SegV load_seg(const double* seg, int N, int e) {
+    SegV s;
+    s.x0 = seg[e]; s.y0 = seg[N + e]; s.tx = seg[2 * N + e]; s.ty = seg[3 * N + e]; s.h = seg[4 * N + e];
+    return s;
+}
+
+// ---------------------------------------------------------------------------------------
+// pair integrals: I[ab] = int_e int_f lambda_a(s) lambda_b(t) g2, J: normal on f, Jt: on e
+// ---------------------------------------------------------------------------------------
+
+// self pair, closed form: with u = |s - t| the integral reduces to
+//   h^2 sum_m h^{2m} [A_m T_ab(2m) + B_m (ln h T_ab(2m) + L_ab(2m))]
+// where T_ab(p) = int_0^1 u^p w_ab(u) du, L_ab(p) = int_0^1 u^p ln u w_ab(u) du and
+// w_11 = w_00 = 2/3 - u + u^3/3, w_01 = w_10 = 1/3 - u^3/3.
+__device__ void pair_self(double h, const SeriesCoef& sc, cplx I[4]) {
+    const double lnh = log(h);
+    cplx i11 = cmk(0, 0), i01 = cmk(0, 0);
+    double h2m = h * h;
+    for (int m = 0; m < sc.nm; ++m) {
+        const double p = 2.0 * m;
+        const double T11 = (2.0 / 3.0) / (p + 1) - 1.0 / (p + 2) + (1.0 / 3.0) / (p + 4);
+        const double L11 = -(2.0 / 3.0) / ((p + 1) * (p + 1)) + 1.0 / ((p + 2) * (p + 2)) -
+                           (1.0 / 3.0) / ((p + 4) * (p + 4));
+        const double T01 = (1.0 / 3.0) / (p + 1) - (1.0 / 3.0) / (p + 4);
+        const double L01 = -(1.0 / 3.0) / ((p + 1) * (p + 1)) + (1.0 / 3.0) / ((p + 4) * (p + 4));
+        const cplx A = sc.A[m];
+        const double B = sc.B[m];
+        i11.x += h2m * (A.x * T11 + B * (lnh * T11 + L11));
+        i11.y += h2m * (A.y * T11);
+        i01.x += h2m * (A.x * T01 + B * (lnh * T01 + L01));
+        i01.y += h2m * (A.y * T01);
+        h2m *= h * h;
+    }
+    I[0] = i11; I[3] = i11; I[1] = i01; I[2] = i01;
+}
+
+// adjacent pair, f follows e (shared vertex P = end of e = start of f).  u = sigma/h_e
+// (x = P - sigma t_e), v = tau/h_f (y = P + tau t_f); triangles v <= u and u < v in Duffy
+// coordinates (rho, w), r = rho R(w).  The rho integrals are closed form, w by Gauss.
+template <bool WD>
+__device__ void pair_adjacent_fwd(const SegV& e, const SegV& f, const SeriesCoef& sc, cplx I[4],
+                                  cplx J[4], cplx Jt[4]) {
+    const int qw = 16;
+    const double* wx = c_glx + gl_off(qw);
+    const double* ww = c_glw + gl_off(qw);
+    const double nfx = f.ty, nfy = -f.tx, nex = e.ty, ney = -e.tx;
+    const double cef = e.tx * nfx + e.ty * nfy;        // t_e . nu_f
+    const double cfe = -(f.tx * nex + f.ty * ney);     // -t_f . nu_e
+    for (int q = 0; q < 4; ++q) { I[q] = cmk(0, 0); if (WD) { J[q] = cmk(0, 0); Jt[q] = cmk(0, 0); } }
+    const double hh = e.h * f.h;
+    for (int tri = 0; tri < 2; ++tri) {
+        for (int iw = 0; iw < qw; ++iw) {
+            const double w = wx[iw], wt = ww[iw] * hh;
+            double Rx, Ry;
+            // polynomial coefficients (c0, c1, c2) in rho of lambda_a^e lambda_b^f
+            double c[4][3];
+            double sfac, tfac;
+            if (tri == 0) {
+                Rx = e.h * e.tx + w * f.h * f.tx; Ry = e.h * e.ty + w * f.h * f.ty;
+                c[0][0] = 0; c[0][1] = 1; c[0][2] = -w;            // (0,0)
+                c[1][0] = 0; c[1][1] = 0; c[1][2] = w;             // (0,1)
+                c[2][0] = 1; c[2][1] = -(1 + w); c[2][2] = w;      // (1,0)
+                c[3][0] = 0; c[3][1] = w; c[3][2] = -w;            // (1,1)
+                sfac = 1.0; tfac = w;
+            } else {
+                Rx = w * e.h * e.tx + f.h * f.tx; Ry = w * e.h * e.ty + f.h * f.ty;
+                c[0][0] = 0; c[0][1] = w; c[0][2] = -w;
+                c[1][0] = 0; c[1][1] = 0; c[1][2] = w;
+                c[2][0] = 1; c[2][1] = -(1 + w); c[2][2] = w;
+                c[3][0] = 0; c[3][1] = 1; c[3][2] = -w;
+                sfac = w; tfac = 1.0;
+            }
+            const double R2 = Rx * Rx + Ry * Ry;
+            const double lnR = 0.5 * log(R2);
+            cplx Gj[3] = {cmk(0, 0), cmk(0, 0), cmk(0, 0)};
+            cplx Hj[3] = {cmk(0, 0), cmk(0, 0), cmk(0, 0)};
+            double R2m = 1.0;
+            for (int m = 0; m < sc.nm; ++m) {
+                for (int j = 0; j < 3; ++j) {
+                    const double a = 2.0 + j + 2.0 * m;
+                    Gj[j].x += R2m * ((sc.A[m].x + sc.B[m] * lnR) / a - sc.B[m] / (a * a));
+                    Gj[j].y += R2m * (sc.A[m].y / a);
+                    if (WD) {
+                        const double b = 3.0 + j + 2.0 * m;
+                        Hj[j].x += R2m * ((sc.E[m].x + sc.F[m] * lnR) / b - sc.F[m] / (b * b));
+                        Hj[j].y += R2m * (sc.E[m].y / b);
+                    }
+                }
+                R2m *= R2;
+            }
+            const double Hs = -1.0 / (2.0 * BEM_PI * R2);
+            for (int ab = 0; ab < 4; ++ab) {
+                cplx si = cmk(0, 0);
+                for (int j = 0; j < 3; ++j) { si.x += c[ab][j] * Gj[j].x; si.y += c[ab][j] * Gj[j].y; }
+                I[ab].x += wt * si.x; I[ab].y += wt * si.y;
+                if (WD) {
+                    cplx sd = cmk(0, 0);
+                    for (int j = 0; j < 3; ++j) {
+                        sd.x += c[ab][j] * (Hs / (j + 1.0) + Hj[j].x);
+                        sd.y += c[ab][j] * Hj[j].y;
+                    }
+                    const double fJ = wt * e.h * sfac * cef, fJt = wt * f.h * tfac * cfe;
+                    J[ab].x += fJ * sd.x; J[ab].y += fJ * sd.y;
+                    Jt[ab].x += fJt * sd.x; Jt[ab].y += fJt * sd.y;
+                }
+            }
+        }
+    }
+}
+
+// separated pair: q x q tensor Gauss-Legendre
+template <bool WD>
+__device__ void pair_gauss(int q, const SegV& e, const SegV& f, double k, cplx I[4], cplx J[4], cplx Jt[4]) {
+    const double* xs = c_glx + gl_off(q);
+    const double* ws = c_glw + gl_off(q);
+    const double nfx = f.ty, nfy = -f.tx, nex = e.ty, ney = -e.tx;
+    cplx a00 = cmk(0, 0), a01 = cmk(0, 0), a10 = cmk(0, 0), a11 = cmk(0, 0);
+    cplx d00 = cmk(0, 0), d01 = cmk(0, 0), d10 = cmk(0, 0), d11 = cmk(0, 0);
+    cplx t00 = cmk(0, 0), t01 = cmk(0, 0), t10 = cmk(0, 0), t11 = cmk(0, 0);
+    const double kq = 0.25 * k;
+    for (int i = 0; i < q; ++i) {
+        const double s = xs[i], wi = ws[i];
+        const double px = e.x0 + s * e.h * e.tx, py = e.y0 + s * e.h * e.ty;
+        for (int j = 0; j < q; ++j) {
+            const double t = xs[j], w = wi * ws[j];
+            const double dx = f.x0 + t * f.h * f.tx - px, dy = f.y0 + t * f.h * f.ty - py;
+            const double r = sqrt(dx * dx + dy * dy);
+            const Bessel01 b = bessel01<WD>(k * r);
+            const double gr = -0.25 * b.Y0, gi = 0.25 * b.J0;
+            const double w00 = w * (1 - s) * (1 - t), w01 = w * (1 - s) * t, w10 = w * s * (1 - t), w11 = w * s * t;
+            a00.x += w00 * gr; a00.y += w00 * gi;
+            a01.x += w01 * gr; a01.y += w01 * gi;
+            a10.x += w10 * gr; a10.y += w10 * gi;
+            a11.x += w11 * gr; a11.y += w11 * gi;
+            if (WD) {
+                // -(i k/4) H1 / r = (k/4)(Y1 - i J1) / r
+                const double ir = 1.0 / r;
+                const double fr = kq * b.Y1 * ir, fi = -kq * b.J1 * ir;
+                const double dnf = dx * nfx + dy * nfy, dne = -(dx * nex + dy * ney);
+                d00.x += w00 * dnf * fr; d00.y += w00 * dnf * fi;
+                d01.x += w01 * dnf * fr; d01.y += w01 * dnf * fi;
+                d10.x += w10 * dnf * fr; d10.y += w10 * dnf * fi;
+                d11.x += w11 * dnf * fr; d11.y += w11 * dnf * fi;
+                t00.x += w00 * dne * fr; t00.y += w00 * dne * fi;
+                t01.x += w01 * dne * fr; t01.y += w01 * dne * fi;
+                t10.x += w10 * dne * fr; t10.y += w10 * dne * fi;
+                t11.x += w11 * dne * fr; t11.y += w11 * dne * fi;
+            }
+        }
+    }
+    const double hh = e.h * f.h;
+    I[0] = cscale(a00, hh); I[1] = cscale(a01, hh); I[2] = cscale(a10, hh); I[3] = cscale(a11, hh);
+    if (WD) {
+        J[0] = cscale(d00, hh); J[1] = cscale(d01, hh); J[2] = cscale(d10, hh); J[3] = cscale(d11, hh);
+        Jt[0] = cscale(t00, hh); Jt[1] = cscale(t01, hh); Jt[2] = cscale(t10, hh); Jt[3] = cscale(t11, hh);
+    }
+}
+
+// Gauss order for a separated pair from the gap-to-length ratio (Bernstein-ellipse
+// estimate rho^{-2q} <= ~1e-15 for the log-singular kernel, rho = a + sqrt(a^2-1),
+// a = 1 + 2 gap/h).
+__device__ __forceinline__ int q_for_gap(double ratio) {
+    if (ratio < 1.5) return 10;
+    if (ratio < 2.5) return 8;
+    if (ratio < 4.0) return 7;
+    if (ratio < 7.0) return 6;
+    if (ratio < 15.0) return 5;
+    if (ratio < 50.0) return 4;
+    if (ratio < 400.0) return 3;
+    return 2;
+}
+
+template <bool WD>
+__device__ void pair_moments(int e, int f, const SegV& se, const SegV& sf, const AsmParams& p,
+                             cplx I[4], cplx J[4], cplx Jt[4]) {
+    const int N = p.N;
+    int d = e - f; if (d < 0) d = -d;
+    const int cyc = min(d, N - d);
+    if (cyc == 0) {
+        pair_self(se.h, p.sc, I);
+        if (WD) for (int q = 0; q < 4; ++q) { J[q] = cmk(0, 0); Jt[q] = cmk(0, 0); }
+    } else if (cyc == 1) {
+        if (f == (e + 1) % N) {
+            pair_adjacent_fwd<WD>(se, sf, p.sc, I, J, Jt);
+        } else {
+            cplx I2[4], J2[4], Jt2[4];
+            pair_adjacent_fwd<WD>(sf, se, p.sc, I2, J2, Jt2);
+            // swap the roles of the segments: (a,b) -> (b,a), J <-> Jt
+            I[0] = I2[0]; I[1] = I2[2]; I[2] = I2[1]; I[3] = I2[3];
+            if (WD) {
+                J[0] = Jt2[0]; J[1] = Jt2[2]; J[2] = Jt2[1]; J[3] = Jt2[3];
+                Jt[0] = J2[0]; Jt[1] = J2[2]; Jt[2] = J2[1]; Jt[3] = J2[3];
+            }
+        }
+    } else {
+        const double mx = se.x0 + 0.5 * se.h * se.tx - sf.x0 - 0.5 * sf.h * sf.tx;
+        const double my = se.y0 + 0.5 * se.h * se.ty - sf.y0 - 0.5 * sf.h * sf.ty;
+        const double hmax = fmax(se.h, sf.h);
+        const double gap = sqrt(mx * mx + my * my) - 0.5 * (se.h + sf.h);
+        const int q = q_for_gap(gap / hmax);
+        pair_gauss<WD>(q, se, sf, p.k, I, J, Jt);
+    }
+}
+
+template <int T, bool WD>
+__global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    if (tj < ti) return;
+    constexpr int TP = T + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx* sI = reinterpret_cast<cplx*>(smem_raw);                 // TP*TP*4
+    cplx* sJ = sI + TP * TP * 4;                                    // (WD)
+    cplx* sJt = sJ + (WD ? TP * TP * 4 : 0);
+    double* sgE = reinterpret_cast<double*>(sJt + (WD ? TP * TP * 4 : 0));   // 5*TP
+    double* sgF = sgE + 5 * TP;
+    const int N = p.N;
+    const int i0 = ti * T, j0 = tj * T;
+    for (int t = threadIdx.x; t < TP; t += blockDim.x) {
+        const int e = (i0 - 1 + t + N) % N, f = (j0 - 1 + t + N) % N;
+        const SegV a = load_seg(p.seg, N, e), b = load_seg(p.seg, N, f);
+        sgE[t] = a.x0; sgE[TP + t] = a.y0; sgE[2 * TP + t] = a.tx; sgE[3 * TP + t] = a.ty; sgE[4 * TP + t] = a.h;
+        sgF[t] = b.x0; sgF[TP + t] = b.y0; sgF[2 * TP + t] = b.tx; sgF[3 * TP + t] = b.ty; sgF[4 * TP + t] = b.h;
+    }
+    __syncthreads();
+    for (int pi = threadIdx.x; pi < TP * TP; pi += blockDim.x) {
+        const int el = pi / TP, fl = pi % TP;
+        // skip segment pairs touching only rows/cols beyond N
+        if (i0 - 1 + el >= N || j0 - 1 + fl >= N) continue;
+        const int e = (i0 - 1 + el + N) % N, f = (j0 - 1 + fl + N) % N;
+        SegV se = {sgE[el], sgE[TP + el], sgE[2 * TP + el], sgE[3 * TP + el], sgE[4 * TP + el]};
+        SegV sf = {sgF[fl], sgF[TP + fl], sgF[2 * TP + fl], sgF[3 * TP + fl], sgF[4 * TP + fl]};
+        cplx I[4], J[4], Jt[4];
+        pair_moments<WD>(e, f, se, sf, p, I, J, Jt);
+        for (int q = 0; q < 4; ++q) {
+            sI[pi * 4 + q] = I[q];
+            if (WD) { sJ[pi * 4 + q] = J[q]; sJt[pi * 4 + q] = Jt[q]; }
+        }
+    }
+    __syncthreads();
+    const double k2 = p.k * p.k;
+    const bool mirror = (ti != tj);
+    for (int pass = 0; pass < (mirror ? 2 : 1); ++pass) {
+        for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+            int il, jl;
+            if (pass == 0) { il = idx % T; jl = idx / T; } else { jl = idx % T; il = idx / T; }
+            const int i = i0 + il, j = j0 + jl;
+            if (i >= N || j >= N) continue;
+            cplx s = cmk(0, 0), w = cmk(0, 0), dd = cmk(0, 0);
+            for (int a = 0; a < 2; ++a) {
+                const int el = il + 1 - a;
+                const double hex = sgE[4 * TP + el];
+                const double nex = sgE[3 * TP + el], ney = -sgE[2 * TP + el];
+                for (int b = 0; b < 2; ++b) {
+                    const int fl = jl + 1 - b;
+                    const int pi = el * TP + fl;
+                    const cplx* Ip = sI + pi * 4;
+                    const cplx Iab = Ip[a * 2 + b];
+                    s = cadd(s, Iab);
+                    if (p.W) {
+                        const double hf = sgF[4 * TP + fl];
+                        const double nfx = sgF[3 * TP + fl], nfy = -sgF[2 * TP + fl];
+                        const double sig = (a == b) ? 1.0 : -1.0;
+                        const double inv = sig / (hex * hf);
+                        const cplx M0 = cadd(cadd(Ip[0], Ip[1]), cadd(Ip[2], Ip[3]));
+                        const double nd = k2 * (nex * nfx + ney * nfy);
+                        w.x += inv * M0.x - nd * Iab.x;
+                        w.y += inv * M0.y - nd * Iab.y;
+                    }
+                    if (WD) dd = cadd(dd, (pass == 0 ? sJ : sJt)[pi * 4 + a * 2 + b]);
+                }
+            }
+            const int64_t off = (pass == 0) ? ((int64_t)i + (int64_t)j * p.ld) : ((int64_t)j + (int64_t)i * p.ld);
+            if (p.S) p.S[off] = s;
+            if (p.W) p.W[off] = w;
+            if (WD && p.D) p.D[off] = dd;
+        }
+    }
+}
+
+// per-segment geometry (SoA) and chord statistics: stats[0] = min h, stats[1] = max h,
+// stats[2] = sum h (by atomics on ordered bit patterns of positive doubles)
+__global__ void k_geometry(const double* verts, int N, double* seg, double* stats) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const int f = (e + 1) % N;
+    const double x0 = verts[2 * e], y0 = verts[2 * e + 1];
+    const double dx = verts[2 * f] - x0, dy = verts[2 * f + 1] - y0;
+    const double h = sqrt(dx * dx + dy * dy);
+    seg[e] = x0; seg[N + e] = y0; seg[2 * N + e] = dx / h; seg[3 * N + e] = dy / h; seg[4 * N + e] = h;
+    unsigned long long hb = __double_as_longlong(h);
+    atomicMin(reinterpret_cast<unsigned long long*>(stats), hb);
+    atomicMax(reinterpret_cast<unsigned long long*>(stats + 1), hb);
+    atomicAdd(stats + 2, h);
+}
+
+bem_status launch_geometry(bem_ctx* h, const double* verts, int64_t N, double* stats_dev) {
+    double init[3] = {1e300, 0.0, 0.0};
+    BEM_CUDA(h, cudaMemcpyAsync(stats_dev, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+    k_geometry<<<(unsigned)((N + 255) / 256), 256, 0, h->stream>>>(verts, (int)N, h->seg, stats_dev);
+    BEM_LAUNCH(h, "k_geometry");
+    return BEM_OK;
+}
+
+template <int T, bool WD>
+static bem_status run_assemble(bem_ctx* h, AsmParams& p) {
+    constexpr int TP = T + 1;
+    const size_t smem = (size_t)TP * TP * 4 * sizeof(cplx) * (WD ? 3 : 1) + 10 * TP * sizeof(double);
+    BEM_CUDA(h, cudaFuncSetAttribute(k_assemble<T, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    p.nT = (p.N + T - 1) / T;
+    dim3 grid(p.nT, p.nT);
+    k_assemble<T, WD><<<grid, 256, smem, h->stream>>>(p);
+    BEM_LAUNCH(h, "k_assemble");
+    return BEM_OK;
+}
+
+bem_status launch_assemble(bem_ctx* h, unsigned ops) {
+    AsmParams p;
+    p.N = (int)h->N;
+    p.k = h->k;
+    p.seg = h->seg;
+    p.S = (ops & BEM_OP_S) ? h->S : nullptr;
+    p.W = (ops & BEM_OP_W) ? h->W : nullptr;
+    p.D = (ops & BEM_OP_D) ? h->D : nullptr;
+    p.ld = h->N;
+    series_coefficients(h->k, 2.0 * h->hbar, &p.sc);
+    if (ops & BEM_OP_D) return run_assemble<15, true>(h, p);
+    return run_assemble<31, false>(h, p);
+}
+
+// ---------------------------------------------------------------------------------------
+// plane-wave right-hand sides
+//   per segment e and direction d: beta = k h_e (d.t_e), base = exp(i k d.P0_e),
+//   phi_0 = int_0^1 (1-s) e^{i beta s} ds = sum_n (i beta)^n / (n! (n+1)(n+2)),
+//   phi_1 = int_0^1 s e^{i beta s} ds     = sum_n (i beta)^n / (n! (n+2))
+//   f-part  -i k (d.nu_e) h_e base phi_a   (f_i = -<phi_i, du/dnu>)
+//   h2-part h_e base phi_a                  ([h2]_i = <phi_i, u_inc>)
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_rhs(const double* seg, int N, const double* angles, double k,
+                                             cplx* f, cplx* hz, int64_t ld) {
+    __shared__ cplx sf0[257], sf1[257], sh0[257], sh1[257];
+    const int i0 = blockIdx.x * 256, w = blockIdx.y;
+    double dy_, dx_;
+    sincos(angles[w], &dy_, &dx_);
+    for (int t = threadIdx.x; t < 257; t += 256) {
+        const int e = ((i0 - 1 + t) % N + N) % N;
+        const double x0 = seg[e], y0 = seg[N + e], tx = seg[2 * N + e], ty = seg[3 * N + e], he = seg[4 * N + e];
+        const double beta = k * he * (dx_ * tx + dy_ * ty);
+        const double dn = dx_ * ty - dy_ * tx;          // d . nu_e, nu = (ty, -tx)
+        double sb, cb;
+        sincos(k * (dx_ * x0 + dy_ * y0), &sb, &cb);
+        cplx c = cmk(1, 0), p0 = cmk(0, 0), p1 = cmk(0, 0);
+        for (int n = 0; n < 60; ++n) {
+            const double dn1 = (double)n + 1.0, dn2 = (double)n + 2.0;
+            p0.x += c.x / (dn1 * dn2); p0.y += c.y / (dn1 * dn2);
+            p1.x += c.x / dn2; p1.y += c.y / dn2;
+            // c <- c * i beta / (n+1)
+            const double nr = -c.y * beta / dn1, ni = c.x * beta / dn1;
+            c.x = nr; c.y = ni;
+            if (fabs(c.x) + fabs(c.y) < 1e-19) break;
+        }
+        const cplx base = cmk(cb * he, sb * he);
+        const cplx b0 = cmul(base, p0), b1 = cmul(base, p1);
+        // -i k dn * b = (k dn b.y, -k dn b.x)
+        sf0[t] = cmk(k * dn * b0.y, -k * dn * b0.x);
+        sf1[t] = cmk(k * dn * b1.y, -k * dn * b1.x);
+        sh0[t] = b0; sh1[t] = b1;
+    }
+    __syncthreads();
+    const int i = i0 + threadIdx.x;
+    if (i >= N) return;
+    const int t = threadIdx.x;
+    // vertex i: segment i (local t+1) as node 0, segment i-1 (local t) as node 1
+    if (f) f[(int64_t)i + (int64_t)w * ld] = cadd(sf0[t + 1], sf1[t]);
+    if (hz) hz[(int64_t)i + (int64_t)w * ld] = cadd(sh0[t + 1], sh1[t]);
+}
+
+bem_status launch_rhs(bem_ctx* h, const double* angles, int64_t nrhs, cplx* f, cplx* hz, int64_t ld) {
+    dim3 grid((unsigned)((h->N + 255) / 256), (unsigned)nrhs);
+    k_rhs<<<grid, 256, 0, h->stream>>>(h->seg, (int)h->N, angles, h->k, f, hz, ld);
+    BEM_LAUNCH(h, "k_rhs");
+    return BEM_OK;
+}

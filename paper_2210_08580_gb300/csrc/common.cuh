@@ -1,0 +1,134 @@
+// Shared device/host helpers of the GB300 BEM library: complex arithmetic on double2,
+// launch checking, a bounded grid-wide barrier for cooperative kernels, and the handle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/bem.h"
+
+typedef double2 cplx;
+
+__host__ __device__ __forceinline__ cplx cmk(double re, double im) { return make_double2(re, im); }
+__host__ __device__ __forceinline__ cplx cadd(cplx a, cplx b) { return cmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ cplx csub(cplx a, cplx b) { return cmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+    return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ cplx cconj(cplx a) { return cmk(a.x, -a.y); }
+__host__ __device__ __forceinline__ cplx cscale(cplx a, double s) { return cmk(a.x * s, a.y * s); }
+// acc += a * b
+__host__ __device__ __forceinline__ void cfma(cplx& acc, cplx a, cplx b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__host__ __device__ __forceinline__ void cfma_conj(cplx& acc, cplx a, cplx b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+    double d = 1.0 / cabs2(b);
+    return cmk((a.x * b.x + a.y * b.y) * d, (a.y * b.x - a.x * b.y) * d);
+}
+
+// Device-side status word: kernels OR error bits into it instead of trapping.
+enum { DEVERR_TIMEOUT = 1, DEVERR_SINGULAR = 2, DEVERR_BOUNDS = 4, DEVERR_NAN = 8 };
+
+// Bounded grid barrier for kernels launched with cudaLaunchCooperativeKernel (all CTAs
+// co-resident).  `bar[0]` counts arrivals, `bar[1]` is the generation.  A CTA that waits
+// longer than the spin limit sets DEVERR_TIMEOUT in *err and returns false; callers then
+// return, so every CTA ends (the others time out as well).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* vgen = bar + 1;
+        unsigned gen = *vgen;
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > (1ll << 26)) { atomicOr(err, DEVERR_TIMEOUT); ok = 0; break; }
+                if ((spins & 1023) == 0 && *(volatile int*)err) { ok = 0; break; }
+                if (spins > 64) __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile int*)err) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+struct bem_ctx {
+    int device = 0;
+    cudaStream_t stream = 0;
+    bem_options opt{};
+    std::string err;
+
+    // geometry and assembly
+    int64_t N = 0;
+    double k = 0.0, hbar = 0.0;
+    unsigned ops = 0;
+    double* seg = nullptr;            // 5*N: x0, y0, tx, ty, h (SoA)
+    cplx *S = nullptr, *W = nullptr, *D = nullptr;
+
+    // filter
+    int64_t n = 0, M = 0, ncols = 0;  // n modes requested, ncols Fourier columns kept
+    double alpha = 0.0, beta = 0.25;
+    cplx* B = nullptr;                // ncols x N, ld = ncols
+    cplx* Bs = nullptr;               // diag(sqrt g) B
+    double* gm = nullptr;             // ncols Gram eigenvalues of the Fourier columns
+    double* Q = nullptr;              // N x ncols Fourier basis
+
+    // compression / factor
+    int64_t r = 0;
+    double sigma_max = 0.0;
+    double* sigma = nullptr;          // n
+    cplx* E = nullptr;                // n x n right singular vectors (ld = n), sorted
+    cplx *U = nullptr, *Vh = nullptr; // N x r (ld N), r x N (ld r)
+    cplx* K = nullptr;                // r x r inverse of the Woodbury core (ld r)
+    int* piv = nullptr;               // r
+
+    // workspace
+    void* work = nullptr;
+    size_t work_bytes = 0;
+    int* dev_err = nullptr;           // device status word
+    unsigned* bar = nullptr;          // grid barrier words (2)
+    int stage = 0;
+
+    // mixed-precision state (owned by the tensor-core module)
+    void* tc = nullptr;
+};
+
+// error helpers ---------------------------------------------------------------------------
+bem_status bem_fail(bem_ctx* h, bem_status st, const std::string& msg);
+bem_status bem_cuda_check(bem_ctx* h, cudaError_t e, const char* what);
+#define BEM_CUDA(h, call)                                                       \
+    do {                                                                        \
+        cudaError_t _e = (call);                                                \
+        if (_e != cudaSuccess) return bem_cuda_check((h), _e, #call);           \
+    } while (0)
+#define BEM_LAUNCH(h, what)                                                     \
+    do {                                                                        \
+        cudaError_t _e = cudaGetLastError();                                    \
+        if (_e != cudaSuccess) return bem_cuda_check((h), _e, what);            \
+    } while (0)
+
+// workspace: returns a device pointer of at least `bytes`, growing the handle's buffer
+bem_status bem_workspace(bem_ctx* h, size_t bytes, void** out);

@@ -1,0 +1,55 @@
+// Host-side launchers shared between the CUDA translation units (internal).
+#pragma once
+
+#include "common.cuh"
+
+#define BEM_SERIES_MAX 24
+
+// Small-argument expansions in r of the kernels (coefficients depend on k only):
+//   g2(r)                    = sum_m r^{2m} (A_m + B_m ln r)
+//   -(i k/4) H1^(1)(k r) / r = -1/(2 pi r^2) + sum_m r^{2m} (E_m + F_m ln r)
+struct SeriesCoef {
+    int nm;
+    double2 A[BEM_SERIES_MAX];
+    double B[BEM_SERIES_MAX];
+    double2 E[BEM_SERIES_MAX];
+    double F[BEM_SERIES_MAX];
+};
+
+void series_coefficients(double k, double hmax, SeriesCoef* sc);
+cudaError_t init_gauss_tables();
+
+// assemble.cu
+bem_status launch_geometry(bem_ctx* h, const double* verts, int64_t N, double* stats_dev);
+bem_status launch_assemble(bem_ctx* h, unsigned ops);
+bem_status launch_rhs(bem_ctx* h, const double* angles, int64_t nrhs, cplx* f, cplx* hz, int64_t ld);
+
+// linalg.cu
+enum { OP_N = 0, OP_T = 1, OP_C = 2 };
+bem_status zgemm(bem_ctx* h, int opa, int opb, int64_t M, int64_t Nc, int64_t K, cplx alpha,
+                 const cplx* A, int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc);
+bem_status dzgemm_realA(bem_ctx* h, int opa, int64_t M, int64_t Nc, int64_t K, double alpha,
+                        const double* A, int64_t lda, const cplx* B, int64_t ldb, double beta,
+                        cplx* C, int64_t ldc);
+// G^-1 (mode 0) or F^-T = (I + r Z)^-1 * sqrt(6 r/h) (mode 1) along index i of a strided array
+bem_status apply_gram_inverse(bem_ctx* h, int mode, const cplx* in, cplx* out, cplx* tmp,
+                              int64_t N, int64_t ncols, int64_t si, int64_t sc, double hbar,
+                              bool conj_out);
+bem_status launch_fourier_basis(bem_ctx* h, double* Q, int64_t N, int64_t ncols, int include_kernel,
+                                double* gm, double hbar);
+bem_status launch_finish_B(bem_ctx* h, cplx* B, const double* gm, const double* Q, int64_t ncols,
+                           int64_t N);
+bem_status launch_row_scale(bem_ctx* h, const cplx* in, cplx* out, const double* s, int pw,
+                            int64_t rows, int64_t cols, int64_t ld);
+bem_status launch_scale_real_cols(bem_ctx* h, const double* in, double* out, const double* s, int pw,
+                                  int64_t rows, int64_t cols);
+bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R);
+bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, double* sigma, cplx* E);
+bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r);
+bem_status launch_axpby(bem_ctx* h, cplx* y, int64_t ldy, const cplx* x, int64_t ldx, cplx a, cplx b,
+                        int64_t rows, int64_t cols);   // y = a*x + b*y
+bem_status launch_add_identity(bem_ctx* h, cplx* A, int64_t ld, int r, cplx d);
+bem_status launch_col_norm_ratio(bem_ctx* h, const cplx* num, int64_t ldn, const cplx* den,
+                                 int64_t ldd, int64_t rows, int64_t cols, double* out_max);
+bem_status launch_copy2d(bem_ctx* h, void* dst, int64_t ldd, const void* src, int64_t lds,
+                         int64_t rows, int64_t cols, size_t elem);

@@ -1,0 +1,730 @@
+// Dense FP64 building blocks of the filter, compression and Woodbury stages (Sec. III-IV):
+//   - complex (and real x complex) GEMM on the FP64 CUDA cores,
+//   - G^-1 and the Gram square-root factor applied as two first-order recursions
+//     (the equal-chord Gram matrix is circulant: G = (h/6)(Z + 4 + Z^-1) =
+//      (h/(6 r))(I + r Z)(I + r Z^-1), r = 2 - sqrt 3),
+//   - the Fourier filter basis,
+//   - Householder QR of a tall-skinny matrix and one-sided Jacobi SVD (cooperative
+//     kernels with bounded grid barriers), Gauss-Jordan inversion of the Woodbury core.
+#include <math.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "kernels.h"
+
+// =========================================================================================
+// GEMM: C = alpha op(A) op(B) + beta C, column-major, 64x64 tiles, 16-deep K slices
+// =========================================================================================
+template <int OPA, int OPB, bool AREAL>
+__global__ void __launch_bounds__(256) k_zgemm(int M, int Nc, int K, cplx alpha, const void* Av,
+                                               int64_t lda, const cplx* B, int64_t ldb, cplx beta,
+                                               cplx* C, int64_t ldc) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ cplx Bs[BK][BN];
+    __shared__ typename std::conditional<AREAL, double, cplx>::type As[BK][BM];
+    const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    cplx acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cmk(0, 0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        // A tile
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            int mm, kk;
+            if (OPA == OP_N) { mm = t % 64; kk = t / 64 + 4 * s; } else { kk = t % 16; mm = t / 16 + 16 * s; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            if (AREAL) {
+                const double* A = reinterpret_cast<const double*>(Av);
+                double v = 0.0;
+                if (gm < M && gk < K) v = (OPA == OP_N) ? A[gm + (int64_t)gk * lda] : A[gk + (int64_t)gm * lda];
+                reinterpret_cast<double*>(&As[0][0])[kk * BM + mm] = v;
+            } else {
+                const cplx* A = reinterpret_cast<const cplx*>(Av);
+                cplx v = cmk(0, 0);
+                if (gm < M && gk < K) {
+                    v = (OPA == OP_N) ? A[gm + (int64_t)gk * lda] : A[gk + (int64_t)gm * lda];
+                    if (OPA == OP_C) v.y = -v.y;
+                }
+                reinterpret_cast<cplx*>(&As[0][0])[kk * BM + mm] = v;
+            }
+        }
+        // B tile
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            int kk, nn;
+            if (OPB == OP_N) { kk = t % 16; nn = t / 16 + 16 * s; } else { nn = t % 64; kk = t / 64 + 4 * s; }
+            const int gk = k0 + kk, gn = n0 + nn;
+            cplx v = cmk(0, 0);
+            if (gk < K && gn < Nc) {
+                v = (OPB == OP_N) ? B[gk + (int64_t)gn * ldb] : B[gn + (int64_t)gk * ldb];
+                if (OPB == OP_C) v.y = -v.y;
+            }
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < BK; ++kk) {
+            cplx b[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+            if (AREAL) {
+                double a[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = reinterpret_cast<const double*>(&As[0][0])[kk * BM + tx + 16 * i];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        acc[i][j].x = fma(a[i], b[j].x, acc[i][j].x);
+                        acc[i][j].y = fma(a[i], b[j].y, acc[i][j].y);
+                    }
+            } else {
+                cplx a[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = reinterpret_cast<const cplx*>(&As[0][0])[kk * BM + tx + 16 * i];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+            }
+        }
+        __syncthreads();
+    }
+    const bool zb = (beta.x == 0.0 && beta.y == 0.0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + tx + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + ty + 16 * j;
+            if (gn >= Nc) continue;
+            cplx* cp = C + gm + (int64_t)gn * ldc;
+            cplx v = cmul(alpha, acc[i][j]);
+            if (!zb) v = cadd(v, cmul(beta, *cp));
+            *cp = v;
+        }
+    }
+}
+
+template <int OPA, int OPB, bool AREAL>
+static void zgemm_launch(cudaStream_t st, int64_t M, int64_t Nc, int64_t K, cplx alpha, const void* A,
+                         int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc) {
+    dim3 grid((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
+    k_zgemm<OPA, OPB, AREAL><<<grid, 256, 0, st>>>((int)M, (int)Nc, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+bem_status zgemm(bem_ctx* h, int opa, int opb, int64_t M, int64_t Nc, int64_t K, cplx alpha,
+                 const cplx* A, int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc) {
+    if (M <= 0 || Nc <= 0) return BEM_OK;
+    if (K <= 0) { K = 0; }
+    cudaStream_t st = h->stream;
+#define ZG(a, b) if (opa == a && opb == b) zgemm_launch<a, b, false>(st, M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc)
+    ZG(OP_N, OP_N); else ZG(OP_N, OP_T); else ZG(OP_N, OP_C);
+    else ZG(OP_T, OP_N); else ZG(OP_T, OP_T); else ZG(OP_T, OP_C);
+    else ZG(OP_C, OP_N); else ZG(OP_C, OP_T); else ZG(OP_C, OP_C);
+#undef ZG
+    BEM_LAUNCH(h, "k_zgemm");
+    return BEM_OK;
+}
+
+bem_status dzgemm_realA(bem_ctx* h, int opa, int64_t M, int64_t Nc, int64_t K, double alpha,
+                        const double* A, int64_t lda, const cplx* B, int64_t ldb, double beta,
+                        cplx* C, int64_t ldc) {
+    if (M <= 0 || Nc <= 0) return BEM_OK;
+    if (opa == OP_N)
+        zgemm_launch<OP_N, OP_N, true>(h->stream, M, Nc, K, cmk(alpha, 0), A, lda, B, ldb, cmk(beta, 0), C, ldc);
+    else
+        zgemm_launch<OP_T, OP_N, true>(h->stream, M, Nc, K, cmk(alpha, 0), A, lda, B, ldb, cmk(beta, 0), C, ldc);
+    BEM_LAUNCH(h, "k_dzgemm");
+    return BEM_OK;
+}
+
+// =========================================================================================
+// Gram recursions.  r = 2 - sqrt(3), |r|^33 < 1e-18: a chunk's first output is seeded with
+// the truncated lookback sum y_i0 = sum_{j<33} (-r)^j x_{i0 -/+ j} (periodic indices).
+// =========================================================================================
+#define IIR_CHUNK 32
+#define IIR_LOOK 33
+
+__global__ void k_iir(const cplx* __restrict__ in, cplx* __restrict__ out, int64_t N, int64_t ncols,
+                      int64_t si, int64_t sc, double r, int dir, double scale, int conj_out) {
+    const int64_t nchunk = (N + IIR_CHUNK - 1) / IIR_CHUNK;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t col, ch;
+    if (sc == 1) { col = tid % ncols; ch = tid / ncols; } else { ch = tid % nchunk; col = tid / nchunk; }
+    if (col >= ncols || ch >= nchunk) return;
+    const cplx* x = in + col * sc;
+    cplx* y = out + col * sc;
+    const int64_t a = ch * IIR_CHUNK, b = min(N, a + IIR_CHUNK);
+    if (dir > 0) {
+        cplx acc = cmk(0, 0);
+        double c = 1.0;
+        for (int j = 0; j < IIR_LOOK; ++j) {
+            int64_t ii = a - j; ii %= N; if (ii < 0) ii += N;
+            const cplx v = x[ii * si];
+            acc.x += c * v.x; acc.y += c * v.y;
+            c *= -r;
+        }
+        cplx prev = acc;
+        y[a * si] = cmk(scale * prev.x, conj_out ? -scale * prev.y : scale * prev.y);
+        for (int64_t i = a + 1; i < b; ++i) {
+            const cplx v = x[i * si];
+            prev = cmk(v.x - r * prev.x, v.y - r * prev.y);
+            y[i * si] = cmk(scale * prev.x, conj_out ? -scale * prev.y : scale * prev.y);
+        }
+    } else {
+        const int64_t last = b - 1;
+        cplx acc = cmk(0, 0);
+        double c = 1.0;
+        for (int j = 0; j < IIR_LOOK; ++j) {
+            int64_t ii = (last + j) % N;
+            const cplx v = x[ii * si];
+            acc.x += c * v.x; acc.y += c * v.y;
+            c *= -r;
+        }
+        cplx prev = acc;
+        y[last * si] = cmk(scale * prev.x, conj_out ? -scale * prev.y : scale * prev.y);
+        for (int64_t i = last - 1; i >= a; --i) {
+            const cplx v = x[i * si];
+            prev = cmk(v.x - r * prev.x, v.y - r * prev.y);
+            y[i * si] = cmk(scale * prev.x, conj_out ? -scale * prev.y : scale * prev.y);
+        }
+    }
+}
+
+bem_status apply_gram_inverse(bem_ctx* h, int mode, const cplx* in, cplx* out, cplx* tmp, int64_t N,
+                              int64_t ncols, int64_t si, int64_t sc, double hbar, bool conj_out) {
+    const double r = 2.0 - sqrt(3.0);
+    const int64_t nchunk = (N + IIR_CHUNK - 1) / IIR_CHUNK;
+    const int64_t threads = nchunk * ncols;
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    if (mode == 0) {
+        // G^-1 = (6 r / h) (I + r Z)^-1 (I + r Z^-1)^-1
+        k_iir<<<blocks, 256, 0, h->stream>>>(in, tmp, N, ncols, si, sc, r, +1, 1.0, 0);
+        k_iir<<<blocks, 256, 0, h->stream>>>(tmp, out, N, ncols, si, sc, r, -1, 6.0 * r / hbar, conj_out ? 1 : 0);
+    } else {
+        // F^-T with G = F^T F, F = sqrt(h/(6r)) (I + r Z^-1): one causal pass
+        k_iir<<<blocks, 256, 0, h->stream>>>(in, out, N, ncols, si, sc, r, +1, sqrt(6.0 * r / hbar), conj_out ? 1 : 0);
+    }
+    BEM_LAUNCH(h, "k_iir");
+    return BEM_OK;
+}
+
+// =========================================================================================
+// Fourier filter basis: column c of Q (N x ncols, column-major) with m = mode index:
+//   constant 1/sqrt(N);  cos: sqrt(2/N) cos(2 pi m i/N);  sin: sqrt(2/N) sin(2 pi m i/N)
+// (argument reduced exactly as (m i mod N)).  gm[c] = h (2 + cos(2 pi m/N))/3.
+// =========================================================================================
+__device__ __forceinline__ void fourier_col(int c, int include_kernel, int& m, int& is_sin) {
+    if (include_kernel) {
+        if (c == 0) { m = 0; is_sin = 0; return; }
+        m = (c + 1) / 2; is_sin = (c % 2 == 0);
+    } else {
+        m = c / 2 + 1; is_sin = (c % 2 == 1);
+    }
+}
+
+__global__ void k_fourier(double* Q, int64_t N, int64_t ncols, int include_kernel, double* gm, double hbar) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * ncols) return;
+    const int64_t i = idx % N;
+    const int c = (int)(idx / N);
+    int m, is_sin;
+    fourier_col(c, include_kernel, m, is_sin);
+    double v;
+    if (m == 0) {
+        v = 1.0 / sqrt((double)N);
+    } else {
+        const int64_t red = ((int64_t)m * i) % N;
+        double s, co;
+        sincospi(2.0 * (double)red / (double)N, &s, &co);
+        v = sqrt(2.0 / (double)N) * (is_sin ? s : co);
+    }
+    Q[i + c * N] = v;
+    if (i == 0) {
+        double s, co;
+        sincospi(2.0 * (double)m / (double)N, &s, &co);
+        gm[c] = hbar * (2.0 + co) / 3.0;
+    }
+}
+
+bem_status launch_fourier_basis(bem_ctx* h, double* Q, int64_t N, int64_t ncols, int include_kernel,
+                                double* gm, double hbar) {
+    const int64_t tot = N * ncols;
+    k_fourier<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(Q, N, ncols, include_kernel, gm, hbar);
+    BEM_LAUNCH(h, "k_fourier");
+    return BEM_OK;
+}
+
+// B[c, i] <- B[c, i] / g_c - Q[i, c] / 4     (B: ncols x N, ld = ncols)
+__global__ void k_finish_B(cplx* B, const double* gm, const double* Q, int64_t ncols, int64_t N) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ncols * N) return;
+    const int64_t c = idx % ncols, i = idx / ncols;
+    const double ig = 1.0 / gm[c];
+    cplx v = B[idx];
+    B[idx] = cmk(v.x * ig - 0.25 * Q[i + c * N], v.y * ig);
+}
+
+bem_status launch_finish_B(bem_ctx* h, cplx* B, const double* gm, const double* Q, int64_t ncols, int64_t N) {
+    const int64_t tot = ncols * N;
+    k_finish_B<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(B, gm, Q, ncols, N);
+    BEM_LAUNCH(h, "k_finish_B");
+    return BEM_OK;
+}
+
+// out[row, col] = in[row, col] * s[row]^(pw/2)   (pw = +1: sqrt, -1: 1/sqrt, 2: s, -2: 1/s)
+__device__ __forceinline__ double powsel(double s, int pw) {
+    switch (pw) {
+        case 1: return sqrt(s);
+        case -1: return 1.0 / sqrt(s);
+        case 2: return s;
+        default: return 1.0 / s;
+    }
+}
+__global__ void k_row_scale(const cplx* in, cplx* out, const double* s, int pw, int64_t rows, int64_t cols, int64_t ld) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t rr = idx % rows, cc = idx / rows;
+    const double f = powsel(s[rr], pw);
+    const cplx v = in[rr + cc * ld];
+    out[rr + cc * ld] = cmk(v.x * f, v.y * f);
+}
+bem_status launch_row_scale(bem_ctx* h, const cplx* in, cplx* out, const double* s, int pw, int64_t rows,
+                            int64_t cols, int64_t ld) {
+    const int64_t tot = rows * cols;
+    k_row_scale<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(in, out, s, pw, rows, cols, ld);
+    BEM_LAUNCH(h, "k_row_scale");
+    return BEM_OK;
+}
+// real matrix (rows x cols, ld = rows): out[:, c] = in[:, c] * s[c]^(pw/2)
+__global__ void k_scale_real_cols(const double* in, double* out, const double* s, int pw, int64_t rows, int64_t cols) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    out[idx] = in[idx] * powsel(s[idx / rows], pw);
+}
+bem_status launch_scale_real_cols(bem_ctx* h, const double* in, double* out, const double* s, int pw,
+                                  int64_t rows, int64_t cols) {
+    const int64_t tot = rows * cols;
+    k_scale_real_cols<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(in, out, s, pw, rows, cols);
+    BEM_LAUNCH(h, "k_scale_real_cols");
+    return BEM_OK;
+}
+
+// =========================================================================================
+// Householder QR of X (N x n, stored row-major: X[i*n + c]), R (n x n, column-major).
+// Cooperative: CTA b owns rows [b*rb, (b+1)*rb).  Per column j: (1) partial |x|^2, barrier,
+// (2) reflector from the global norm, (3) partial w_c = v^H X[:, c], barrier, (4) update.
+// =========================================================================================
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int q = 0; q < nw; ++q) s += red[q];
+    return s;
+}
+
+__global__ void __launch_bounds__(256) k_house_qr(cplx* X, int64_t N, int n, cplx* R, double* partN, cplx* partW,
+                                                  unsigned* bar, int* err) {
+    __shared__ double red[32];
+    __shared__ cplx wred[8][33];
+    __shared__ cplx wsm[1024];
+    const unsigned G = gridDim.x;
+    const int64_t rb = (N + G - 1) / G;
+    const int64_t r0 = (int64_t)blockIdx.x * rb, r1 = min(N, r0 + rb);
+    const int tid = threadIdx.x, cg = tid & 31, rg = tid >> 5;
+    for (int j = 0; j < n; ++j) {
+        // (1) partial norm of column j over rows >= j
+        double s = 0.0;
+        for (int64_t i = max(r0, (int64_t)j) + tid; i < r1; i += blockDim.x) s += cabs2(X[i * n + j]);
+        s = block_sum(s, red);
+        if (tid == 0) partN[blockIdx.x] = s;
+        if (!grid_barrier(bar, G, err)) return;
+        // (2) reflector
+        double nrm2 = 0.0;
+        for (unsigned q = tid; q < G; q += blockDim.x) nrm2 += partN[q];
+        nrm2 = block_sum(nrm2, red);
+        const cplx xjj = X[(int64_t)j * n + j];
+        double tau = 0.0;
+        cplx alpha = cmk(0, 0), vj = cmk(0, 0);
+        if (nrm2 > 0.0) {
+            const double a = sqrt(nrm2), ax = sqrt(cabs2(xjj));
+            const cplx ph = (ax > 0.0) ? cmk(xjj.x / ax, xjj.y / ax) : cmk(1, 0);
+            alpha = cmk(-ph.x * a, -ph.y * a);
+            vj = csub(xjj, alpha);
+            const double vn2 = nrm2 - ax * ax + cabs2(vj);
+            tau = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
+        }
+        // (3) partial dots w_c = sum_i conj(v_i) X[i, c], c > j
+        for (int cb = j + 1; cb < n; cb += 32) {
+            const int c = cb + cg;
+            cplx acc = cmk(0, 0);
+            if (c < n && tau != 0.0) {
+                for (int64_t i = max(r0, (int64_t)j) + rg; i < r1; i += 8) {
+                    const cplx vi = (i == j) ? vj : X[i * n + j];
+                    cfma_conj(acc, vi, X[i * n + c]);
+                }
+            }
+            wred[rg][cg] = acc;
+            __syncthreads();
+            if (rg == 0) {
+                cplx t = wred[0][cg];
+                for (int q = 1; q < 8; ++q) t = cadd(t, wred[q][cg]);
+                if (c < n) partW[(int64_t)blockIdx.x * n + c] = t;
+            }
+            __syncthreads();
+        }
+        if (!grid_barrier(bar, G, err)) return;
+        // (4) reduce w over CTAs, update my rows, write row j of R
+        for (int c = j + 1 + tid; c < n; c += blockDim.x) {
+            cplx t = cmk(0, 0);
+            for (unsigned q = 0; q < G; ++q) t = cadd(t, partW[(int64_t)q * n + c]);
+            wsm[c] = cscale(t, tau);
+        }
+        __syncthreads();
+        if (tau != 0.0) {
+            for (int cb = j + 1; cb < n; cb += 32) {
+                const int c = cb + cg;
+                if (c >= n) continue;
+                const cplx wc = wsm[c];
+                for (int64_t i = max(r0, (int64_t)j) + rg; i < r1; i += 8) {
+                    const cplx vi = (i == j) ? vj : X[i * n + j];
+                    cplx x = X[i * n + c];
+                    x = csub(x, cmul(vi, wc));
+                    X[i * n + c] = x;
+                }
+            }
+        }
+        __syncthreads();
+        if (j >= r0 && j < r1) {
+            for (int c = tid; c < n; c += blockDim.x) {
+                cplx v;
+                if (c < j) v = cmk(0, 0);
+                else if (c == j) v = (nrm2 > 0.0) ? alpha : cmk(0, 0);
+                else v = X[(int64_t)j * n + c];
+                R[j + (int64_t)c * n] = v;
+            }
+        }
+    }
+}
+
+static bem_status coop_launch(bem_ctx* h, const void* fn, int blocks_wanted, int threads, void** args, const char* what) {
+    int dev = h->device, nsm = 0, per = 0;
+    BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    BEM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0));
+    if (per < 1) return bem_fail(h, BEM_E_CUDA, std::string(what) + ": kernel cannot be resident");
+    int G = blocks_wanted;
+    if (G > nsm * per) G = nsm * per;
+    if (G < 1) G = 1;
+    BEM_CUDA(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), h->stream));
+    BEM_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(G), dim3(threads), args, 0, h->stream));
+    BEM_LAUNCH(h, what);
+    return BEM_OK;
+}
+
+bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R) {
+    if (n > 1024) return bem_fail(h, BEM_E_UNSUPPORTED, "QR: more than 1024 columns");
+    int nsm = 0;
+    BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    int G = (int)std::min<int64_t>(nsm, (N + 15) / 16);
+    bem_status st;
+    double* partN = nullptr;
+    cplx* partW = nullptr;
+    BEM_CUDA(h, cudaMallocAsync((void**)&partN, sizeof(double) * G, h->stream));
+    BEM_CUDA(h, cudaMallocAsync((void**)&partW, sizeof(cplx) * (size_t)G * n, h->stream));
+    void* args[] = {&X, &N, &n, &R, &partN, &partW, &h->bar, &h->dev_err};
+    st = coop_launch(h, (const void*)k_house_qr, G, 256, args, "k_house_qr");
+    cudaFreeAsync(partN, h->stream);
+    cudaFreeAsync(partW, h->stream);
+    return st;
+}
+
+// =========================================================================================
+// One-sided Jacobi SVD of R (n x n, column-major): R V = U S.  Column pairs (p, q) of a
+// round-robin tournament are rotated in parallel, one pair per CTA; rotation
+//   R_p' = c R_p - s e^{-i phi} R_q,   R_q' = s e^{i phi} R_p + c R_q,
+// where R_p^H R_q = |g| e^{i phi}, zeta = (b - a)/(2|g|), t = sign(zeta)/(|zeta| + sqrt(1+zeta^2)),
+// c = 1/sqrt(1+t^2), s = c t (a = |R_p|^2, b = |R_q|^2).
+// =========================================================================================
+__device__ __forceinline__ void tourney(int round, int idx, int np, int& p, int& q) {
+    auto pos = [&](int k) { return (k == 0) ? 0 : ((round + k - 1) % (np - 1)) + 1; };
+    p = pos(idx);
+    q = pos(np - 1 - idx);
+}
+
+__global__ void __launch_bounds__(256) k_jacobi(cplx* R, cplx* V, int n, int* flags, int max_sweeps,
+                                                unsigned* bar, int* err) {
+    __shared__ double red[32];
+    const unsigned G = gridDim.x;
+    const int np = n + (n & 1);
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        for (int round = 0; round < np - 1; ++round) {
+            for (int idx = blockIdx.x; idx < np / 2; idx += G) {
+                int p, q;
+                tourney(round, idx, np, p, q);
+                if (p >= n || q >= n) continue;
+                if (p > q) { int t = p; p = q; q = t; }
+                cplx* Rp = R + (int64_t)p * n;
+                cplx* Rq = R + (int64_t)q * n;
+                double a = 0.0, b = 0.0, gr = 0.0, gi = 0.0;
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const cplx x = Rp[i], y = Rq[i];
+                    a += cabs2(x); b += cabs2(y);
+                    gr += x.x * y.x + x.y * y.y;     // conj(x) y
+                    gi += x.x * y.y - x.y * y.x;
+                }
+                a = block_sum(a, red); b = block_sum(b, red);
+                gr = block_sum(gr, red); gi = block_sum(gi, red);
+                const double ag = sqrt(gr * gr + gi * gi);
+                if (ag <= 1e-15 * sqrt(a * b) || ag == 0.0) continue;
+                if (threadIdx.x == 0) flags[sweep] = 1;
+                const double zeta = (b - a) / (2.0 * ag);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                const cplx e = cmk(gr / ag, gi / ag);            // e^{i phi}
+                const cplx sem = cmk(s * e.x, -s * e.y);           // s e^{-i phi}
+                const cplx sep = cmk(s * e.x, s * e.y);            // s e^{i phi}
+                cplx* Vp = V + (int64_t)p * n;
+                cplx* Vq = V + (int64_t)q * n;
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const cplx x = Rp[i], y = Rq[i];
+                    Rp[i] = csub(cscale(x, c), cmul(sem, y));
+                    Rq[i] = cadd(cmul(sep, x), cscale(y, c));
+                    const cplx u = Vp[i], w = Vq[i];
+                    Vp[i] = csub(cscale(u, c), cmul(sem, w));
+                    Vq[i] = cadd(cmul(sep, u), cscale(w, c));
+                }
+            }
+            if (!grid_barrier(bar, G, err)) return;
+        }
+        if (*(volatile int*)(flags + sweep) == 0) return;
+    }
+}
+
+// sigma_c = |R_c|, sorted descending; E[:, rank] = V[:, c]
+__global__ void k_sort_sv(const cplx* R, const cplx* V, int n, double* sigma, cplx* E, double* tmp) {
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += cabs2(R[(int64_t)c * n + i]);
+        tmp[c] = sqrt(s);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const double sc = tmp[c];
+        int rank = 0;
+        for (int d = 0; d < n; ++d) {
+            const double sd = tmp[d];
+            if (sd > sc || (sd == sc && d < c)) ++rank;
+        }
+        sigma[rank] = sc;
+        for (int i = 0; i < n; ++i) E[(int64_t)rank * n + i] = V[(int64_t)c * n + i];
+    }
+}
+
+__global__ void k_identity(cplx* V, int n) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * n) return;
+    V[idx] = cmk((idx % n) == (idx / n) ? 1.0 : 0.0, 0.0);
+}
+
+bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, double* sigma, cplx* E) {
+    cplx* V = nullptr;
+    int* flags = nullptr;
+    double* tmp = nullptr;
+    const int max_sweeps = 40;
+    BEM_CUDA(h, cudaMallocAsync((void**)&V, sizeof(cplx) * (size_t)n * n, h->stream));
+    BEM_CUDA(h, cudaMallocAsync((void**)&flags, sizeof(int) * max_sweeps, h->stream));
+    BEM_CUDA(h, cudaMallocAsync((void**)&tmp, sizeof(double) * n, h->stream));
+    BEM_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(int) * max_sweeps, h->stream));
+    k_identity<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, h->stream>>>(V, n);
+    BEM_LAUNCH(h, "k_identity");
+    int ms = max_sweeps;
+    void* args[] = {&R, &V, &n, &flags, &ms, &h->bar, &h->dev_err};
+    bem_status st = coop_launch(h, (const void*)k_jacobi, (n + 1) / 2, 128, args, "k_jacobi");
+    if (st == BEM_OK) {
+        k_sort_sv<<<1, 256, 0, h->stream>>>(R, V, n, sigma, E, tmp);
+        BEM_LAUNCH(h, "k_sort_sv");
+    }
+    cudaFreeAsync(V, h->stream);
+    cudaFreeAsync(flags, h->stream);
+    cudaFreeAsync(tmp, h->stream);
+    return st;
+}
+
+// =========================================================================================
+// Gauss-Jordan inversion with partial pivoting of A (r x r) on the augmented [A | I]
+// (r x 2r, column-major, ld = r).  CTA b owns a block of augmented columns.  Per step j
+// every CTA copies the pivot column and finds the pivot, barrier, then updates its columns.
+// =========================================================================================
+__global__ void __launch_bounds__(256) k_gauss_jordan(cplx* M, int r, unsigned* bar, int* err) {
+    extern __shared__ cplx colj[];
+    __shared__ double rv[256];
+    __shared__ int ri[256];
+    __shared__ int piv_s;
+    const unsigned G = gridDim.x;
+    const int ncol = 2 * r;
+    const int cb = (ncol + G - 1) / G;
+    const int c0 = blockIdx.x * cb, c1 = min(ncol, c0 + cb);
+    for (int j = 0; j < r; ++j) {
+        for (int i = threadIdx.x; i < r; i += blockDim.x) colj[i] = M[i + (int64_t)j * r];
+        __syncthreads();
+        // argmax |colj[i]|, i >= j
+        double best = -1.0; int bi = j;
+        for (int i = j + threadIdx.x; i < r; i += blockDim.x) {
+            const double v = cabs2(colj[i]);
+            if (v > best) { best = v; bi = i; }
+        }
+        rv[threadIdx.x] = best; ri[threadIdx.x] = bi;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bb = -1.0; int bbi = j;
+            for (int q = 0; q < (int)blockDim.x; ++q)
+                if (rv[q] > bb || (rv[q] == bb && ri[q] < bbi)) { bb = rv[q]; bbi = ri[q]; }
+            piv_s = bbi;
+            if (!(bb > 0.0)) atomicOr(err, DEVERR_SINGULAR);
+        }
+        __syncthreads();
+        const int p = piv_s;
+        if (threadIdx.x == 0 && p != j) { cplx t = colj[j]; colj[j] = colj[p]; colj[p] = t; }
+        __syncthreads();
+        if (!grid_barrier(bar, G, err)) return;     // everyone has read column j
+        const cplx pv = colj[j];
+        const bool sing = !(cabs2(pv) > 0.0);
+        const cplx ipv = sing ? cmk(0, 0) : cdiv(cmk(1, 0), pv);
+        for (int c = c0 + threadIdx.x / 32; c < c1; c += blockDim.x / 32) {
+            cplx* col = M + (int64_t)c * r;
+            // swap rows j, p of this column and normalise row j
+            cplx xj = col[p], xp = col[j];
+            xj = cmul(xj, ipv);
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) { col[p] = xp; }
+            __syncwarp();
+            for (int i = threadIdx.x & 31; i < r; i += 32) {
+                if (i == j) continue;
+                cplx v = (i == p) ? xp : col[i];
+                v = csub(v, cmul(colj[i], xj));
+                col[i] = v;
+            }
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) col[j] = xj;
+            __syncwarp();
+        }
+        if (!grid_barrier(bar, G, err)) return;
+    }
+}
+
+__global__ void k_augment(const cplx* K, cplx* M, int r) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)r * 2 * r) return;
+    const int64_t i = idx % r, c = idx / r;
+    M[idx] = (c < r) ? K[i + c * r] : cmk((c - r) == i ? 1.0 : 0.0, 0.0);
+}
+
+bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
+    cplx* M = nullptr;
+    BEM_CUDA(h, cudaMallocAsync((void**)&M, sizeof(cplx) * (size_t)r * 2 * r, h->stream));
+    k_augment<<<(unsigned)(((int64_t)r * 2 * r + 255) / 256), 256, 0, h->stream>>>(K, M, r);
+    BEM_LAUNCH(h, "k_augment");
+    const size_t smem = sizeof(cplx) * (size_t)r;
+    if (smem > 48 * 1024)
+        BEM_CUDA(h, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int nsm = 0, per = 0;
+    BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    BEM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gauss_jordan, 256, smem));
+    if (per < 1) return bem_fail(h, BEM_E_CUDA, "k_gauss_jordan cannot be resident");
+    int G = std::min(nsm * per, std::max(1, (2 * r + 7) / 8));
+    BEM_CUDA(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), h->stream));
+    void* args[] = {&M, &r, &h->bar, &h->dev_err};
+    BEM_CUDA(h, cudaLaunchCooperativeKernel((const void*)k_gauss_jordan, dim3(G), dim3(256), args, smem, h->stream));
+    BEM_LAUNCH(h, "k_gauss_jordan");
+    BEM_CUDA(h, cudaMemcpy2DAsync(Kinv, sizeof(cplx) * r, M + (size_t)r * r, sizeof(cplx) * r,
+                                  sizeof(cplx) * r, r, cudaMemcpyDeviceToDevice, h->stream));
+    cudaFreeAsync(M, h->stream);
+    return BEM_OK;
+}
+
+// =========================================================================================
+// small elementwise helpers
+// =========================================================================================
+__global__ void k_axpby(cplx* y, int64_t ldy, const cplx* x, int64_t ldx, cplx a, cplx b, int64_t rows, int64_t cols) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t rr = idx % rows, cc = idx / rows;
+    const cplx xv = x[rr + cc * ldx];
+    cplx v = cmul(a, xv);
+    if (b.x != 0.0 || b.y != 0.0) v = cadd(v, cmul(b, y[rr + cc * ldy]));
+    y[rr + cc * ldy] = v;
+}
+bem_status launch_axpby(bem_ctx* h, cplx* y, int64_t ldy, const cplx* x, int64_t ldx, cplx a, cplx b,
+                        int64_t rows, int64_t cols) {
+    const int64_t tot = rows * cols;
+    if (tot == 0) return BEM_OK;
+    k_axpby<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(y, ldy, x, ldx, a, b, rows, cols);
+    BEM_LAUNCH(h, "k_axpby");
+    return BEM_OK;
+}
+
+__global__ void k_add_identity(cplx* A, int64_t ld, int r, cplx d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r) return;
+    A[i + i * ld] = cadd(A[i + i * ld], d);
+}
+bem_status launch_add_identity(bem_ctx* h, cplx* A, int64_t ld, int r, cplx d) {
+    k_add_identity<<<(r + 255) / 256, 256, 0, h->stream>>>(A, ld, r, d);
+    BEM_LAUNCH(h, "k_add_identity");
+    return BEM_OK;
+}
+
+// out_max = max over columns of |num_c| / |den_c| (2-norms); one CTA per column, then max
+__global__ void k_col_ratio(const cplx* num, int64_t ldn, const cplx* den, int64_t ldd, int64_t rows, double* ratios) {
+    __shared__ double red[32];
+    const int64_t c = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) {
+        a += cabs2(num[i + c * ldn]);
+        b += cabs2(den[i + c * ldd]);
+    }
+    a = block_sum(a, red);
+    b = block_sum(b, red);
+    if (threadIdx.x == 0) ratios[c] = (b > 0.0) ? sqrt(a / b) : sqrt(a);
+}
+__global__ void k_max(const double* v, int64_t n, double* out) {
+    __shared__ double red[32];
+    double m = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, v[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r = fmax(r, red[q]);
+        *out = r;
+    }
+}
+bem_status launch_col_norm_ratio(bem_ctx* h, const cplx* num, int64_t ldn, const cplx* den, int64_t ldd,
+                                 int64_t rows, int64_t cols, double* out_max) {
+    double* ratios = nullptr;
+    BEM_CUDA(h, cudaMallocAsync((void**)&ratios, sizeof(double) * cols, h->stream));
+    k_col_ratio<<<(unsigned)cols, 256, 0, h->stream>>>(num, ldn, den, ldd, rows, ratios);
+    BEM_LAUNCH(h, "k_col_ratio");
+    k_max<<<1, 256, 0, h->stream>>>(ratios, cols, out_max);
+    BEM_LAUNCH(h, "k_max");
+    cudaFreeAsync(ratios, h->stream);
+    return BEM_OK;
+}
+
+bem_status launch_copy2d(bem_ctx* h, void* dst, int64_t ldd, const void* src, int64_t lds, int64_t rows,
+                         int64_t cols, size_t elem) {
+    BEM_CUDA(h, cudaMemcpy2DAsync(dst, elem * ldd, src, elem * lds, elem * rows, cols,
+                                  cudaMemcpyDeviceToDevice, h->stream));
+    return BEM_OK;
+}

@@ -1,0 +1,318 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Small cases (N = 256..301, several assembly tiles plus a ragged tail) are compared
+element by element; the large configurations (N = 4096, 16384) on entries the oracle
+computes one by one and on residual properties that hold at any size.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import bem_oracle as O
+from paper_2210_08580_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+ENTRY_TOL = 1e-13      # |X_gpu - X_orc| <= ENTRY_TOL * max|X_orc|  (matrix entries)
+SOLVE_TOL = 1e-10      # FP64 path: relative current error against the oracle
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2210_08580_gb300 import bem
+    bem.load_library()
+    return bem
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.fixture(scope="module")
+def star301():
+    v, _, _ = I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), 301)
+    k = 2.0
+    return v, k, O.assemble(v, k, "SWD")
+
+
+@pytest.fixture(scope="module")
+def star301_solution(star301):
+    v, k, mats = star301
+    ang = I.planewave_angles(6)
+    f = O.rhs_planewave(v, k, ang)
+    h2 = O.rhs_planewave_h(v, k, ang)
+    return dict(ang=ang, f=f, h2=h2,
+                efie=O.filtered_solve_projected(mats, v, f, 20, 1e-10),
+                efie_t=O.filtered_solve_projected(mats, v, f, 20, 1e-4),
+                cfie=O.filtered_solve_projected(mats, v, f, 20, 1e-10, alpha=0.5, h2=h2),
+                nokernel=O.filtered_solve_projected(mats, v, f, 20, 1e-10, include_kernel=False))
+
+
+def _solver(B, v, k, ops="SW", **kw):
+    s = B.Solver(device=0, **kw)
+    s.assemble(_cuda(v), k, ops=ops)
+    return s
+
+
+# ------------------------------------------------------------------ assembly
+
+
+@pytest.mark.parametrize("ops", ["SWD", "SW"])
+def test_assembly_matches_oracle(B, star301, ops):
+    v, k, mats = star301
+    s = _solver(B, v, k, ops)
+    for op in ops:
+        g = _np(s.matrix(op))
+        assert _rel(g, mats[op]) <= ENTRY_TOL, (op, _rel(g, mats[op]))
+    s.close()
+
+
+@pytest.mark.parametrize("k", [12.0, 24.0])
+def test_assembly_bessel_regimes(B, k):
+    """k r up to ~24 (Miller recurrence) and ~48 (Hankel asymptotics) on a circle."""
+    N = 512
+    v = I.regular_polygon(N)
+    s = _solver(B, v, k, "SWD")
+    rng = np.random.default_rng(3)
+    rows = rng.integers(0, N, 120)
+    cols = rng.integers(0, N, 120)
+    rows[:8] = np.arange(8); cols[:8] = (np.arange(8) + np.array([0, 1, 2, 3, 256, 255, 511, 100])) % N
+    ref = O.assemble_entries(v, k, rows, cols, "SWD")
+    for op in "SWD":
+        g = _np(s.matrix(op))
+        scale = np.max(np.abs(g))
+        err = np.max(np.abs(g[rows, cols] - ref[op])) / scale
+        assert err <= ENTRY_TOL, (op, k, err)
+    s.close()
+
+
+# ------------------------------------------------------------------ rhs, filter, compression, solve
+
+
+def test_rhs_matches_oracle(B, star301, star301_solution):
+    v, k, mats = star301
+    sol = star301_solution
+    s = _solver(B, v, k, "SW")
+    f, vv = s.rhs_planewave(_cuda(sol["ang"]), want_f=True)
+    assert _rel(_np(f).T, sol["f"]) <= 1e-13
+    assert _rel(_np(vv).T, sol["efie"]["vx"]) <= 1e-12
+    s.close()
+
+
+def test_filter_block_matches_oracle(B, star301, star301_solution):
+    v, k, _ = star301
+    ref = star301_solution["efie"]
+    s = _solver(B, v, k, "SW")
+    s.filter_apply(41)
+    Bg = _np(s.matrix("B"))
+    assert Bg.shape == ref["B"].shape
+    assert _rel(Bg, ref["B"]) <= 1e-12, _rel(Bg, ref["B"])
+    s.close()
+
+
+def test_compression_and_solve_match_oracle(B, star301, star301_solution):
+    v, k, _ = star301
+    sol = star301_solution
+    for key, tol in (("efie", 1e-10), ("efie_t", 1e-4)):
+        ref = sol[key]
+        s = _solver(B, v, k, "SW")
+        s.filter_apply(41)
+        r = s.compress(tol)
+        sig = _np(s.matrix("sigma"))
+        assert np.max(np.abs(sig - ref["sigma"])) <= 1e-12 * ref["sigma"][0]
+        assert abs(r - ref["rank"]) <= 1
+        s.factor()
+        vv = s.rhs_planewave(_cuda(sol["ang"]))
+        x, it, res = s.solve(vv, report=True)
+        assert res <= 1e-13
+        xg = _np(x).T
+        if r == ref["rank"]:
+            assert _rel(xg, ref["x"]) <= SOLVE_TOL, (key, _rel(xg, ref["x"]))
+        else:
+            assert _rel(xg, ref["x"]) <= 10 * tol
+        s.close()
+
+
+def test_cfie_matches_oracle(B, star301, star301_solution):
+    v, k, _ = star301
+    ref = star301_solution["cfie"]
+    s = _solver(B, v, k, "SWD")
+    s.filter_apply(41, alpha=0.5)
+    assert _rel(_np(s.matrix("B")), ref["B"]) <= 1e-12
+    assert s.compress(1e-10) == ref["rank"]
+    s.factor()
+    x = s.solve(s.rhs_planewave(_cuda(star301_solution["ang"])))
+    assert _rel(_np(x).T, ref["x"]) <= SOLVE_TOL
+    assert abs(s.info()["beta"] - 0.5) < 1e-15
+    s.close()
+
+
+def test_literal_filter_without_kernel_mode(B, star301, star301_solution):
+    v, k, _ = star301
+    ref = star301_solution["nokernel"]
+    s = _solver(B, v, k, "SW", include_kernel_mode=False)
+    s.filter_apply(41)
+    assert s.compress(1e-10) == ref["rank"]
+    s.factor()
+    x = s.solve(s.rhs_planewave(_cuda(star301_solution["ang"])))
+    assert _rel(_np(x).T, ref["x"]) <= SOLVE_TOL
+    s.close()
+
+
+def test_backward_is_the_adjoint_solve(B, star301):
+    v, k, _ = star301
+    s = _solver(B, v, k, "SW")
+    s.filter_apply(41)
+    s.compress(1e-10)
+    s.factor()
+    rng = np.random.default_rng(1)
+    g = _cuda(rng.standard_normal((5, v.shape[0])) + 1j * rng.standard_normal((5, v.shape[0])))
+    lam = s.solve_backward(g)
+    U, Vh = s.matrix("U"), s.matrix("Vh")
+    beta = s.info()["beta"]
+    # (beta I + U V^H)^H lam = g
+    A_H_lam = beta * lam.T + Vh.conj().T @ (U.conj().T @ lam.T)
+    assert float((A_H_lam - g.T).abs().max() / g.abs().max()) <= 1e-13
+    s.close()
+
+
+def test_mie_circle_c1(B):
+    """C1: unit circle, N = 256, k = 1, n = 65, tol 1e-10, 16 plane waves."""
+    N, k, M, nrhs = 256, 1.0, 32, 16
+    v = I.regular_polygon(N)
+    ang = I.planewave_angles(nrhs)
+    s = _solver(B, v, k, "SW")
+    s.filter_apply(2 * M + 1)
+    s.compress(1e-10)
+    s.factor()
+    x = _np(s.solve(s.rhs_planewave(_cuda(ang)))).T
+    mats = O.assemble(v, k, "SW")
+    ref = O.filtered_solve_projected(mats, v, O.rhs_planewave(v, k, ang), M, 1e-10)
+    assert _rel(x, ref["x"]) <= SOLVE_TOL
+    G = O.gram(v)
+    th = 2 * math.pi * np.arange(N) / N
+    for w in range(nrhs):
+        jm = O.mie_current(k, 1.0, th, ang[w])
+        assert O.g_norm(G, x[:, w] - jm)[0] / O.g_norm(G, jm)[0] < 1e-4
+    s.close()
+
+
+# ------------------------------------------------------------------ large configurations
+
+
+def _filtered_residual(s, Q, x, vv):
+    """max_w |(beta I + Q B) x_w - v_w| / |v_w|  with the uncompressed filtered operator."""
+    Bm = s.matrix("B")
+    beta = s.info()["beta"]
+    Ax = beta * x.T + Q @ (Bm @ x.T)
+    return float(((Ax - vv.T).norm(dim=0) / vv.T.norm(dim=0)).max())
+
+
+@pytest.mark.parametrize("k", [1e-3, 1e-2, 1e-1, 1.0, 5.0])
+def test_c2_star_4096(B, k):
+    """C2: r = 1 + 0.3 cos 5t, N = 4096, n = 201, tol 1e-10, 256 plane waves."""
+    N, M, nrhs = 4096, 100, 256
+    v, _, _ = I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), N)
+    s = _solver(B, v, k, "SW")
+    rng = np.random.default_rng(int(k * 1000) + 7)
+    rows = np.concatenate([rng.integers(0, N, 48), np.arange(8)])
+    cols = np.concatenate([rng.integers(0, N, 48), (np.arange(8) + np.array([0, 1, 2, 5, 2048, 4095, 3, 1])) % N])
+    ref = O.assemble_entries(v, k, rows, cols, "SW")
+    for op in "SW":
+        g = s.matrix(op)
+        scale = float(g.abs().max())
+        got = _np(g[torch.as_tensor(rows).cuda(), torch.as_tensor(cols).cuda()])
+        assert np.max(np.abs(got - ref[op])) / scale <= ENTRY_TOL, (op, k)
+        del g
+    s.filter_apply(2 * M + 1)
+    s.compress(1e-10)
+    s.factor()
+    vv = s.rhs_planewave(_cuda(I.planewave_angles(nrhs)))
+    x, _, res = s.solve(vv, report=True)
+    assert res <= 1e-12
+    Q = _cuda(O.fourier_basis(N, M)).to(torch.complex128)
+    assert _filtered_residual(s, Q, x, vv) <= 1e-9
+    s.close()
+
+
+def test_c3_random_star_16384_fp64(B):
+    """C3 geometry at full size (N = 16384, k = 2, n = 201, tol 1e-10) on the FP64 path:
+    sampled entries against the oracle and residuals of the solve."""
+    N, k, M, nrhs = 16384, 2.0, 100, 64
+    v, _, _ = I.equal_chord_mesh(I.random_star(0), N)
+    s = _solver(B, v, k, "SW")
+    rng = np.random.default_rng(11)
+    rows = np.concatenate([rng.integers(0, N, 40), np.arange(6)])
+    cols = np.concatenate([rng.integers(0, N, 40), (np.arange(6) + np.array([0, 1, 2, 8192, 16383, 4])) % N])
+    ref = O.assemble_entries(v, k, rows, cols, "SW")
+    for op in "SW":
+        g = s.matrix(op)
+        scale = float(g.abs().max())
+        got = _np(g[torch.as_tensor(rows).cuda(), torch.as_tensor(cols).cuda()])
+        assert np.max(np.abs(got - ref[op])) / scale <= ENTRY_TOL, op
+        del g
+    s.filter_apply(2 * M + 1)
+    s.compress(1e-10)
+    s.factor()
+    vv = s.rhs_planewave(_cuda(I.planewave_angles(nrhs)))
+    x, _, res = s.solve(vv, report=True)
+    assert res <= 1e-12
+    Q = _cuda(O.fourier_basis(N, M)).to(torch.complex128)
+    assert _filtered_residual(s, Q, x, vv) <= 1e-9
+    s.close()
+
+
+# ------------------------------------------------------------------ errors and edge cases
+
+
+def test_errors_are_reported_not_raised_on_device(B):
+    v = I.regular_polygon(64)
+    s = B.Solver(device=0)
+    with pytest.raises(B.BemError) as e:
+        s.filter_apply(15)
+    assert e.value.status == 1
+    # unequal chords
+    vb = v.copy()
+    vb[3] *= 1.01
+    with pytest.raises(B.BemError) as e:
+        s.assemble(_cuda(vb), 1.0)
+    assert e.value.status == 4
+    s.assemble(_cuda(v), 1.0)
+    for bad in (14, 2, 64):
+        with pytest.raises(B.BemError):
+            s.filter_apply(bad)
+    with pytest.raises(B.BemError):
+        s.filter_apply(15, alpha=1.0)        # needs D
+    s.filter_apply(15)
+    with pytest.raises(B.BemError):
+        s.factor()                           # compress first
+    s.compress(1e-10)
+    s.factor()
+    x = s.solve(s.rhs_planewave(_cuda(I.planewave_angles(3))))
+    assert torch.isfinite(torch.view_as_real(x)).all()
+    s.close()
+
+
+def test_smallest_mesh_and_single_rhs(B):
+    N, k = 16, 0.5
+    v = I.regular_polygon(N)
+    s = _solver(B, v, k, "SW")
+    s.filter_apply(7)
+    s.compress(0.0)
+    s.factor()
+    ang = np.array([0.7])
+    x = _np(s.solve(s.rhs_planewave(_cuda(ang)))).T
+    mats = O.assemble(v, k, "SW")
+    ref = O.filtered_solve_projected(mats, v, O.rhs_planewave(v, k, ang), 3, 0.0)
+    assert _rel(x, ref["x"]) <= SOLVE_TOL
+    s.close()
