@@ -125,14 +125,15 @@ def graded_gauss01(ratio: float = 0.3, q: int = 16, levels: int = 34):
     return np.concatenate(nodes), np.concatenate(weights)
 
 
-def _q_for_gap(gap_over_h):
-    """Gauss order that makes the Bernstein-ellipse estimate rho^{-2q} of a
-    log-singular integrand fall below 1e-20 (rho for a singularity at distance
-    ``gap`` beyond the end of a unit-normalised segment), plus one point of margin."""
+def _q_for_gap(gap_over_h, k_gap):
+    """Gauss order from the Bernstein-ellipse bound rho^{-2q} exp(k Im r) <= 1e-20 for the
+    kernel on a segment pair: rho for a singularity at distance ``gap`` beyond the end of a
+    unit-normalised segment, and the Hankel kernel grows like exp(k Im r) off the real
+    axis, where Im r reaches about the gap (``k_gap`` = k (gap + h)); one point of margin."""
     a = 1.0 + 2.0 * np.maximum(gap_over_h, 1e-3)
     rho = a + np.sqrt(a * a - 1.0)
-    q = np.ceil(20.0 * math.log(10.0) / (2.0 * np.log(rho))) + 1
-    return np.clip(q, 4, 40).astype(int)
+    q = np.ceil((20.0 * math.log(10.0) + k_gap) / (2.0 * np.log(rho))) + 1
+    return np.clip(q, 4, 60).astype(int)
 
 
 def _seg_seg_gap(mesh: Mesh, e, f):
@@ -280,8 +281,9 @@ def pair_integrals(mesh: Mesh, k: float, e, f, need_d: bool = True):
             Jt[bwd] = np.swapaxes(j_, 1, 2)
     if far.any():
         idx = np.nonzero(far)[0]
-        gap = _seg_seg_gap(mesh, e[idx], f[idx]) / np.maximum(mesh.h[e[idx]], mesh.h[f[idx]])
-        qs = _q_for_gap(gap)
+        hmx = np.maximum(mesh.h[e[idx]], mesh.h[f[idx]])
+        gap = _seg_seg_gap(mesh, e[idx], f[idx])
+        qs = _q_for_gap(gap / hmx, k * (gap + hmx))
         for q in np.unique(qs):
             sel = idx[qs == q]
             for c0 in range(0, len(sel), 20000):
