@@ -261,18 +261,15 @@ __device__ void pair_gauss(int q, const SegV& e, const SegV& f, double k, cplx I
     }
 }
 
-// Gauss order for a separated pair from the gap-to-length ratio (Bernstein-ellipse
-// estimate rho^{-2q} <= ~1e-15 for the log-singular kernel, rho = a + sqrt(a^2-1),
-// a = 1 + 2 gap/h).
-__device__ __forceinline__ int q_for_gap(double ratio) {
-    if (ratio < 1.5) return 10;
-    if (ratio < 2.5) return 8;
-    if (ratio < 4.0) return 7;
-    if (ratio < 7.0) return 6;
-    if (ratio < 15.0) return 5;
-    if (ratio < 50.0) return 4;
-    if (ratio < 400.0) return 3;
-    return 2;
+// Gauss order for a separated pair: Bernstein-ellipse bound rho^{-2q} exp(k Im r) <= 1e-15
+// with rho = a + sqrt(a^2 - 1), a = 1 + 2 gap/h (log singularity at the gap beyond the end
+// of the segment) and Im r up to about gap + h on that ellipse (the Hankel kernel grows
+// like exp(k Im r) off the real axis).
+__device__ __forceinline__ int q_for_gap(double ratio, double kgap) {
+    const double a = 1.0 + 2.0 * fmax(ratio, 1e-3);
+    const double rho = a + sqrt(a * a - 1.0);
+    const int q = (int)ceil((34.54 + kgap) / (2.0 * log(rho)));
+    return min(16, max(2, q));
 }
 
 template <bool WD>
@@ -301,8 +298,8 @@ __device__ void pair_moments(int e, int f, const SegV& se, const SegV& sf, const
         const double mx = se.x0 + 0.5 * se.h * se.tx - sf.x0 - 0.5 * sf.h * sf.tx;
         const double my = se.y0 + 0.5 * se.h * se.ty - sf.y0 - 0.5 * sf.h * sf.ty;
         const double hmax = fmax(se.h, sf.h);
-        const double gap = sqrt(mx * mx + my * my) - 0.5 * (se.h + sf.h);
-        const int q = q_for_gap(gap / hmax);
+        const double gap = fmax(sqrt(mx * mx + my * my) - 0.5 * (se.h + sf.h), 0.0);
+        const int q = q_for_gap(gap / hmax, p.k * (gap + hmax));
         pair_gauss<WD>(q, se, sf, p.k, I, J, Jt);
     }
 }
