@@ -182,6 +182,14 @@ bem_status bem_get_matrix(bem_handle h, int which, void* dst_dev, int64_t ld);
 /* Sizes and scalars of the current state (synchronises the stream). */
 bem_status bem_get_info(bem_handle h, bem_info* info);
 
+/* Profiling support (not part of the method).  While enabled, every kernel launch of the
+ * handle is bracketed by CUDA events recorded on the handle's stream; enabling clears the
+ * records.  bem_timing_report synchronises the stream and writes a JSON object
+ * {"<kernel or GEMM call site>": [launches, total_ms], ...} into buf (NUL-terminated,
+ * truncated to len).  Returns BEM_E_INVALID on a NULL handle or buffer. */
+bem_status bem_timing_enable(bem_handle h, int enable);
+bem_status bem_timing_report(bem_handle h, char* buf, size_t len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,8 @@ STATUS = {0: "BEM_OK", 1: "BEM_E_INVALID", 2: "BEM_E_NOMEM", 3: "BEM_E_CUDA", 4:
 # every symbol include/bem.h declares
 EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error", "bem_set_stream",
            "bem_assemble", "filter_apply", "compress_compact", "factor", "bem_rhs_planewave",
-           "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info")
+           "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info", "bem_timing_enable",
+           "bem_timing_report")
 
 
 class BemOptions(ctypes.Structure):
@@ -77,9 +78,11 @@ def load_library(path: str = LIB_PATH):
     L.solve_backward.argtypes = [vp, vp, i64, vp, i64, i64]
     L.bem_get_matrix.argtypes = [vp, i32, vp, i64]
     L.bem_get_info.argtypes = [vp, ctypes.POINTER(BemInfo)]
+    L.bem_timing_enable.argtypes = [vp, i32]
+    L.bem_timing_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     for name in ("bem_create", "bem_destroy", "bem_set_stream", "bem_assemble", "filter_apply",
                  "compress_compact", "factor", "bem_rhs_planewave", "solve_many", "solve_backward",
-                 "bem_get_matrix", "bem_get_info"):
+                 "bem_get_matrix", "bem_get_info", "bem_timing_enable", "bem_timing_report"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -182,6 +185,15 @@ class Solver:
         return lam
 
     # ---------------------------------------------------------------- introspection
+    def timing(self, enable: bool):
+        self._check(self.L.bem_timing_enable(self.h, 1 if enable else 0))
+
+    def timing_report(self) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(self.L.bem_timing_report(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
     def info(self) -> dict:
         inf = BemInfo()
         self._check(self.L.bem_get_info(self.h, ctypes.byref(inf)))

@@ -78,6 +78,17 @@ static bem_status check_dev_err(bem_ctx* h) {
     return BEM_OK;
 }
 
+cudaEvent_t bem_event_get(bem_ctx* h) {
+    if (!h->evpool.empty()) {
+        cudaEvent_t e = h->evpool.back();
+        h->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
 static std::mutex g_tab_mutex;
 static bool g_tab_done[64] = {false};
 
@@ -249,6 +260,7 @@ bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha) {
         if ((st = tc_product_left(h, TC_OP_S, h->Q, nullptr, nc, Y1)) != BEM_OK) return st;
     } else {
         // Y1 = Q^T S  (ncols x N)
+        h->tag = "gemm_filter_QtS";
         if ((st = dzgemm_realA(h, OP_T, nc, N, N, 1.0, h->Q, N, h->S, N, 0.0, Y1, nc)) != BEM_OK) return st;
     }
     // Y2 = Y1 G^-1 (along the N index of each row)
@@ -261,7 +273,9 @@ bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha) {
         }
     } else {
         // B = Y2 N  (- alpha Q^T D)
+        h->tag = "gemm_filter_YN";
         if ((st = zgemm(h, OP_N, OP_N, nc, N, N, cmk(1, 0), Y1, nc, h->W, N, cmk(0, 0), h->B, nc)) != BEM_OK) return st;
+        h->tag = "gemm_filter_QtD";
         if (alpha != 0.0)
             if ((st = dzgemm_realA(h, OP_T, nc, N, N, -alpha, h->Q, N, h->D, N, 1.0, h->B, nc)) != BEM_OK) return st;
     }
@@ -311,6 +325,7 @@ bem_status compress_compact(bem_handle h, double rel_tol, int64_t* rank_out) {
     if ((st = ensure_alloc(h, (void**)&h->Vh, sizeof(cplx) * r * N)) != BEM_OK) return st;
     // U = Q diag(g^-1/2) E_r ;  V^H = E_r^H diag(g^1/2) B
     if ((st = launch_scale_real_cols(h, h->Q, Qs, h->gm, -1, N, nc)) != BEM_OK) return st;
+    h->tag = "gemm_compress_UVh";
     if ((st = dzgemm_realA(h, OP_N, N, r, nc, 1.0, Qs, N, h->E, nc, 0.0, h->U, N)) != BEM_OK) return st;
     if ((st = zgemm(h, OP_C, OP_N, r, N, nc, cmk(1, 0), h->E, nc, h->Bs, nc, cmk(0, 0), h->Vh, r)) != BEM_OK) return st;
     if (rank_out) *rank_out = r;
@@ -333,6 +348,7 @@ bem_status factor(bem_handle h) {
     cv.add((void**)&Kt, sizeof(cplx) * r * r);
     if ((st = cv.commit(h)) != BEM_OK) return st;
     // K = I_r + beta^-1 V^H U, stored as its inverse
+    h->tag = "gemm_factor_VhU";
     if ((st = zgemm(h, OP_N, OP_N, r, r, N, cmk(1.0 / h->beta, 0), h->Vh, r, h->U, N, cmk(0, 0), Kt, r)) != BEM_OK) return st;
     if ((st = launch_add_identity(h, Kt, r, (int)r, cmk(1, 0))) != BEM_OK) return st;
     if ((st = launch_gauss_jordan(h, Kt, h->K, (int)r)) != BEM_OK) return st;
@@ -373,6 +389,7 @@ bem_status bem_rhs_planewave(bem_handle h, const double* angles, int64_t nrhs, v
     if (h->opt.prec == BEM_MIXED_BF16) {
         if ((st = tc_product_right(h, TC_OP_S, y, ld, nrhs, v, ld)) != BEM_OK) return st;
     } else {
+        h->tag = "gemm_rhs_SY";
         if ((st = zgemm(h, OP_N, OP_N, N, nrhs, N, cmk(1, 0), h->S, N, y, ld, cmk(0, 0), v, ld)) != BEM_OK) return st;
     }
     if (hz) {
@@ -387,6 +404,7 @@ static bem_status woodbury_fp64(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x,
                                 cplx* T, cplx* T2) {
     const int64_t N = h->N, r = h->r;
     bem_status st;
+    h->tag = "gemm_solve";
     if ((st = zgemm(h, OP_N, OP_N, r, nrhs, N, cmk(1, 0), h->Vh, r, v, ldv, cmk(0, 0), T, r)) != BEM_OK) return st;
     if ((st = zgemm(h, OP_N, OP_N, r, nrhs, r, cmk(1, 0), h->K, r, T, r, cmk(0, 0), T2, r)) != BEM_OK) return st;
     if ((st = launch_axpby(h, x, ldx, v, ldv, cmk(1.0 / h->beta, 0), cmk(0, 0), N, nrhs)) != BEM_OK) return st;
@@ -398,6 +416,7 @@ static bem_status residual_fp64(bem_ctx* h, const cplx* v, int64_t ldv, const cp
                                 cplx* rho, cplx* T) {
     const int64_t N = h->N, r = h->r;
     bem_status st;
+    h->tag = "gemm_residual";
     if ((st = zgemm(h, OP_N, OP_N, r, nrhs, N, cmk(1, 0), h->Vh, r, x, ldx, cmk(0, 0), T, r)) != BEM_OK) return st;
     if ((st = launch_copy2d(h, rho, N, v, ldv, N, nrhs, sizeof(cplx))) != BEM_OK) return st;
     if ((st = launch_axpby(h, rho, N, x, ldx, cmk(-h->beta, 0), cmk(1, 0), N, nrhs)) != BEM_OK) return st;
@@ -459,6 +478,7 @@ bem_status solve_backward(bem_handle h, const void* g_dev, int64_t ldg, void* la
     cv.add((void**)&T2, sizeof(cplx) * r * nrhs);
     if ((st = cv.commit(h)) != BEM_OK) return st;
     // lambda = g/beta - beta^-2 V Kinv^H U^H g  (beta real)
+    h->tag = "gemm_backward";
     if ((st = zgemm(h, OP_C, OP_N, r, nrhs, N, cmk(1, 0), h->U, N, g, ldg, cmk(0, 0), T, r)) != BEM_OK) return st;
     if ((st = zgemm(h, OP_C, OP_N, r, nrhs, r, cmk(1, 0), h->K, r, T, r, cmk(0, 0), T2, r)) != BEM_OK) return st;
     if ((st = launch_axpby(h, lam, ldl, g, ldg, cmk(1.0 / h->beta, 0), cmk(0, 0), N, nrhs)) != BEM_OK) return st;
@@ -496,6 +516,42 @@ bem_status bem_get_matrix(bem_handle h, int which, void* dst, int64_t ld) {
         default:
             return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: unknown matrix");
     }
+}
+
+bem_status bem_timing_enable(bem_handle h, int enable) {
+    if (!h) return BEM_E_INVALID;
+    cudaSetDevice(h->device);
+    BEM_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (auto& r : h->trec) { h->evpool.push_back(r.a); h->evpool.push_back(r.b); }
+    h->trec.clear();
+    h->timing = enable != 0;
+    return BEM_OK;
+}
+
+bem_status bem_timing_report(bem_handle h, char* buf, size_t len) {
+    if (!h || !buf || len == 0) return BEM_E_INVALID;
+    cudaSetDevice(h->device);
+    BEM_CUDA(h, cudaStreamSynchronize(h->stream));
+    std::vector<std::pair<std::string, std::pair<int, double>>> agg;
+    for (auto& r : h->trec) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        bool found = false;
+        for (auto& a : agg)
+            if (a.first == r.name) { a.second.first += 1; a.second.second += ms; found = true; break; }
+        if (!found) agg.push_back({std::string(r.name), {1, (double)ms}});
+    }
+    std::string s = "{";
+    for (size_t i = 0; i < agg.size(); ++i) {
+        char tmp[256];
+        snprintf(tmp, sizeof(tmp), "%s\"%s\": [%d, %.6f]", i ? ", " : "", agg[i].first.c_str(),
+                 agg[i].second.first, agg[i].second.second);
+        s += tmp;
+    }
+    s += "}";
+    strncpy(buf, s.c_str(), len - 1);
+    buf[len - 1] = 0;
+    return BEM_OK;
 }
 
 bem_status bem_get_info(bem_handle h, bem_info* info) {

@@ -398,7 +398,7 @@ __global__ void k_geometry(const double* verts, int N, double* seg, double* stat
 bem_status launch_geometry(bem_ctx* h, const double* verts, int64_t N, double* stats_dev) {
     double init[3] = {1e300, 0.0, 0.0};
     BEM_CUDA(h, cudaMemcpyAsync(stats_dev, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
-    k_geometry<<<(unsigned)((N + 255) / 256), 256, 0, h->stream>>>(verts, (int)N, h->seg, stats_dev);
+    BEM_TIMED(h, "k_geometry", (k_geometry<<<(unsigned)((N + 255) / 256), 256, 0, h->stream>>>(verts, (int)N, h->seg, stats_dev)));
     BEM_LAUNCH(h, "k_geometry");
     return BEM_OK;
 }
@@ -410,7 +410,7 @@ static bem_status run_assemble(bem_ctx* h, AsmParams& p) {
     BEM_CUDA(h, cudaFuncSetAttribute(k_assemble<T, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     p.nT = (p.N + T - 1) / T;
     dim3 grid(p.nT, p.nT);
-    k_assemble<T, WD><<<grid, 256, smem, h->stream>>>(p);
+    BEM_TIMED(h, "k_assemble", (k_assemble<T, WD><<<grid, 256, smem, h->stream>>>(p)));
     BEM_LAUNCH(h, "k_assemble");
     return BEM_OK;
 }
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(256) k_rhs(const double* seg, int N, const dou
 
 bem_status launch_rhs(bem_ctx* h, const double* angles, int64_t nrhs, cplx* f, cplx* hz, int64_t ld) {
     dim3 grid((unsigned)((h->N + 255) / 256), (unsigned)nrhs);
-    k_rhs<<<grid, 256, 0, h->stream>>>(h->seg, (int)h->N, angles, h->k, f, hz, ld);
+    BEM_TIMED(h, "k_rhs", (k_rhs<<<grid, 256, 0, h->stream>>>(h->seg, (int)h->N, angles, h->k, f, hz, ld)));
     BEM_LAUNCH(h, "k_rhs");
     return BEM_OK;
 }

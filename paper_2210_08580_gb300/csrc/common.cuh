@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/bem.h"
 
@@ -114,7 +115,28 @@ struct bem_ctx {
 
     // mixed-precision state (owned by the tensor-core module)
     void* tc = nullptr;
+
+    // optional per-launch timing (CUDA events on the handle's stream)
+    bool timing = false;
+    const char* tag = "kernel";       // label of the next timed GEMM call site
+    struct TimingRec { const char* name; cudaEvent_t a, b; };
+    std::vector<TimingRec> trec;
+    std::vector<cudaEvent_t> evpool;
 };
+
+cudaEvent_t bem_event_get(bem_ctx* h);
+// Brackets the launch statement(s) with events when timing is enabled.
+#define BEM_TIMED(h, name, ...)                                                  \
+    do {                                                                         \
+        cudaEvent_t _ta = nullptr;                                               \
+        if ((h)->timing) { _ta = bem_event_get(h); cudaEventRecord(_ta, (h)->stream); } \
+        __VA_ARGS__;                                                             \
+        if ((h)->timing) {                                                       \
+            cudaEvent_t _tb = bem_event_get(h);                                  \
+            cudaEventRecord(_tb, (h)->stream);                                   \
+            (h)->trec.push_back({(name), _ta, _tb});                             \
+        }                                                                        \
+    } while (0)
 
 // error helpers ---------------------------------------------------------------------------
 bem_status bem_fail(bem_ctx* h, bem_status st, const std::string& msg);

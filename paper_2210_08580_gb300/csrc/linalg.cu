@@ -124,9 +124,10 @@ bem_status zgemm(bem_ctx* h, int opa, int opb, int64_t M, int64_t Nc, int64_t K,
     if (K <= 0) { K = 0; }
     cudaStream_t st = h->stream;
 #define ZG(a, b) if (opa == a && opb == b) zgemm_launch<a, b, false>(st, M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc)
+    BEM_TIMED(h, h->tag,
     ZG(OP_N, OP_N); else ZG(OP_N, OP_T); else ZG(OP_N, OP_C);
     else ZG(OP_T, OP_N); else ZG(OP_T, OP_T); else ZG(OP_T, OP_C);
-    else ZG(OP_C, OP_N); else ZG(OP_C, OP_T); else ZG(OP_C, OP_C);
+    else ZG(OP_C, OP_N); else ZG(OP_C, OP_T); else ZG(OP_C, OP_C));
 #undef ZG
     BEM_LAUNCH(h, "k_zgemm");
     return BEM_OK;
@@ -136,10 +137,11 @@ bem_status dzgemm_realA(bem_ctx* h, int opa, int64_t M, int64_t Nc, int64_t K, d
                         const double* A, int64_t lda, const cplx* B, int64_t ldb, double beta,
                         cplx* C, int64_t ldc) {
     if (M <= 0 || Nc <= 0) return BEM_OK;
+    BEM_TIMED(h, h->tag,
     if (opa == OP_N)
         zgemm_launch<OP_N, OP_N, true>(h->stream, M, Nc, K, cmk(alpha, 0), A, lda, B, ldb, cmk(beta, 0), C, ldc);
     else
-        zgemm_launch<OP_T, OP_N, true>(h->stream, M, Nc, K, cmk(alpha, 0), A, lda, B, ldb, cmk(beta, 0), C, ldc);
+        zgemm_launch<OP_T, OP_N, true>(h->stream, M, Nc, K, cmk(alpha, 0), A, lda, B, ldb, cmk(beta, 0), C, ldc));
     BEM_LAUNCH(h, "k_dzgemm");
     return BEM_OK;
 }
@@ -205,11 +207,13 @@ bem_status apply_gram_inverse(bem_ctx* h, int mode, const cplx* in, cplx* out, c
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     if (mode == 0) {
         // G^-1 = (6 r / h) (I + r Z)^-1 (I + r Z^-1)^-1
-        k_iir<<<blocks, 256, 0, h->stream>>>(in, tmp, N, ncols, si, sc, r, +1, 1.0, 0);
-        k_iir<<<blocks, 256, 0, h->stream>>>(tmp, out, N, ncols, si, sc, r, -1, 6.0 * r / hbar, conj_out ? 1 : 0);
+        BEM_TIMED(h, "k_iir", (k_iir<<<blocks, 256, 0, h->stream>>>(in, tmp, N, ncols, si, sc, r, +1, 1.0, 0)));
+        BEM_TIMED(h, "k_iir", (k_iir<<<blocks, 256, 0, h->stream>>>(tmp, out, N, ncols, si, sc, r, -1,
+                                                                    6.0 * r / hbar, conj_out ? 1 : 0)));
     } else {
         // F^-T with G = F^T F, F = sqrt(h/(6r)) (I + r Z^-1): one causal pass
-        k_iir<<<blocks, 256, 0, h->stream>>>(in, out, N, ncols, si, sc, r, +1, sqrt(6.0 * r / hbar), conj_out ? 1 : 0);
+        BEM_TIMED(h, "k_iir", (k_iir<<<blocks, 256, 0, h->stream>>>(in, out, N, ncols, si, sc, r, +1,
+                                                                    sqrt(6.0 * r / hbar), conj_out ? 1 : 0)));
     }
     BEM_LAUNCH(h, "k_iir");
     return BEM_OK;
@@ -256,7 +260,7 @@ __global__ void k_fourier(double* Q, int64_t N, int64_t ncols, int include_kerne
 bem_status launch_fourier_basis(bem_ctx* h, double* Q, int64_t N, int64_t ncols, int include_kernel,
                                 double* gm, double hbar) {
     const int64_t tot = N * ncols;
-    k_fourier<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(Q, N, ncols, include_kernel, gm, hbar);
+    BEM_TIMED(h, "k_fourier", (k_fourier<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(Q, N, ncols, include_kernel, gm, hbar)));
     BEM_LAUNCH(h, "k_fourier");
     return BEM_OK;
 }
@@ -273,7 +277,7 @@ __global__ void k_finish_B(cplx* B, const double* gm, const double* Q, int64_t n
 
 bem_status launch_finish_B(bem_ctx* h, cplx* B, const double* gm, const double* Q, int64_t ncols, int64_t N) {
     const int64_t tot = ncols * N;
-    k_finish_B<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(B, gm, Q, ncols, N);
+    BEM_TIMED(h, "k_finish_B", (k_finish_B<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(B, gm, Q, ncols, N)));
     BEM_LAUNCH(h, "k_finish_B");
     return BEM_OK;
 }
@@ -298,7 +302,7 @@ __global__ void k_row_scale(const cplx* in, cplx* out, const double* s, int pw, 
 bem_status launch_row_scale(bem_ctx* h, const cplx* in, cplx* out, const double* s, int pw, int64_t rows,
                             int64_t cols, int64_t ld) {
     const int64_t tot = rows * cols;
-    k_row_scale<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(in, out, s, pw, rows, cols, ld);
+    BEM_TIMED(h, "k_row_scale", (k_row_scale<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(in, out, s, pw, rows, cols, ld)));
     BEM_LAUNCH(h, "k_row_scale");
     return BEM_OK;
 }
@@ -311,7 +315,7 @@ __global__ void k_scale_real_cols(const double* in, double* out, const double* s
 bem_status launch_scale_real_cols(bem_ctx* h, const double* in, double* out, const double* s, int pw,
                                   int64_t rows, int64_t cols) {
     const int64_t tot = rows * cols;
-    k_scale_real_cols<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(in, out, s, pw, rows, cols);
+    BEM_TIMED(h, "k_scale_real_cols", (k_scale_real_cols<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(in, out, s, pw, rows, cols)));
     BEM_LAUNCH(h, "k_scale_real_cols");
     return BEM_OK;
 }
@@ -442,7 +446,7 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R) {
     BEM_CUDA(h, cudaMallocAsync((void**)&partN, sizeof(double) * G, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&partW, sizeof(cplx) * (size_t)G * n, h->stream));
     void* args[] = {&X, &N, &n, &R, &partN, &partW, &h->bar, &h->dev_err};
-    st = coop_launch(h, (const void*)k_house_qr, G, 256, args, "k_house_qr");
+    BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr, G, 256, args, "k_house_qr"));
     cudaFreeAsync(partN, h->stream);
     cudaFreeAsync(partW, h->stream);
     return st;
@@ -545,13 +549,14 @@ bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, double* sigma, cplx* E)
     BEM_CUDA(h, cudaMallocAsync((void**)&flags, sizeof(int) * max_sweeps, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&tmp, sizeof(double) * n, h->stream));
     BEM_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(int) * max_sweeps, h->stream));
-    k_identity<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, h->stream>>>(V, n);
+    BEM_TIMED(h, "k_identity", (k_identity<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, h->stream>>>(V, n)));
     BEM_LAUNCH(h, "k_identity");
     int ms = max_sweeps;
     void* args[] = {&R, &V, &n, &flags, &ms, &h->bar, &h->dev_err};
-    bem_status st = coop_launch(h, (const void*)k_jacobi, (n + 1) / 2, 128, args, "k_jacobi");
+    bem_status st;
+    BEM_TIMED(h, "k_jacobi", st = coop_launch(h, (const void*)k_jacobi, (n + 1) / 2, 128, args, "k_jacobi"));
     if (st == BEM_OK) {
-        k_sort_sv<<<1, 256, 0, h->stream>>>(R, V, n, sigma, E, tmp);
+        BEM_TIMED(h, "k_sort_sv", (k_sort_sv<<<1, 256, 0, h->stream>>>(R, V, n, sigma, E, tmp)));
         BEM_LAUNCH(h, "k_sort_sv");
     }
     cudaFreeAsync(V, h->stream);
@@ -632,7 +637,7 @@ __global__ void k_augment(const cplx* K, cplx* M, int r) {
 bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
     cplx* M = nullptr;
     BEM_CUDA(h, cudaMallocAsync((void**)&M, sizeof(cplx) * (size_t)r * 2 * r, h->stream));
-    k_augment<<<(unsigned)(((int64_t)r * 2 * r + 255) / 256), 256, 0, h->stream>>>(K, M, r);
+    BEM_TIMED(h, "k_augment", (k_augment<<<(unsigned)(((int64_t)r * 2 * r + 255) / 256), 256, 0, h->stream>>>(K, M, r)));
     BEM_LAUNCH(h, "k_augment");
     const size_t smem = sizeof(cplx) * (size_t)r;
     if (smem > 48 * 1024)
@@ -644,7 +649,10 @@ bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
     int G = std::min(nsm * per, std::max(1, (2 * r + 7) / 8));
     BEM_CUDA(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), h->stream));
     void* args[] = {&M, &r, &h->bar, &h->dev_err};
-    BEM_CUDA(h, cudaLaunchCooperativeKernel((const void*)k_gauss_jordan, dim3(G), dim3(256), args, smem, h->stream));
+    cudaError_t lerr;
+    BEM_TIMED(h, "k_gauss_jordan",
+              lerr = cudaLaunchCooperativeKernel((const void*)k_gauss_jordan, dim3(G), dim3(256), args, smem, h->stream));
+    BEM_CUDA(h, lerr);
     BEM_LAUNCH(h, "k_gauss_jordan");
     BEM_CUDA(h, cudaMemcpy2DAsync(Kinv, sizeof(cplx) * r, M + (size_t)r * r, sizeof(cplx) * r,
                                   sizeof(cplx) * r, r, cudaMemcpyDeviceToDevice, h->stream));
@@ -668,7 +676,7 @@ bem_status launch_axpby(bem_ctx* h, cplx* y, int64_t ldy, const cplx* x, int64_t
                         int64_t rows, int64_t cols) {
     const int64_t tot = rows * cols;
     if (tot == 0) return BEM_OK;
-    k_axpby<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(y, ldy, x, ldx, a, b, rows, cols);
+    BEM_TIMED(h, "k_axpby", (k_axpby<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(y, ldy, x, ldx, a, b, rows, cols)));
     BEM_LAUNCH(h, "k_axpby");
     return BEM_OK;
 }
@@ -679,7 +687,7 @@ __global__ void k_add_identity(cplx* A, int64_t ld, int r, cplx d) {
     A[i + i * ld] = cadd(A[i + i * ld], d);
 }
 bem_status launch_add_identity(bem_ctx* h, cplx* A, int64_t ld, int r, cplx d) {
-    k_add_identity<<<(r + 255) / 256, 256, 0, h->stream>>>(A, ld, r, d);
+    BEM_TIMED(h, "k_add_identity", (k_add_identity<<<(r + 255) / 256, 256, 0, h->stream>>>(A, ld, r, d)));
     BEM_LAUNCH(h, "k_add_identity");
     return BEM_OK;
 }
@@ -714,9 +722,9 @@ bem_status launch_col_norm_ratio(bem_ctx* h, const cplx* num, int64_t ldn, const
                                  int64_t rows, int64_t cols, double* out_max) {
     double* ratios = nullptr;
     BEM_CUDA(h, cudaMallocAsync((void**)&ratios, sizeof(double) * cols, h->stream));
-    k_col_ratio<<<(unsigned)cols, 256, 0, h->stream>>>(num, ldn, den, ldd, rows, ratios);
+    BEM_TIMED(h, "k_col_ratio", (k_col_ratio<<<(unsigned)cols, 256, 0, h->stream>>>(num, ldn, den, ldd, rows, ratios)));
     BEM_LAUNCH(h, "k_col_ratio");
-    k_max<<<1, 256, 0, h->stream>>>(ratios, cols, out_max);
+    BEM_TIMED(h, "k_max", (k_max<<<1, 256, 0, h->stream>>>(ratios, cols, out_max)));
     BEM_LAUNCH(h, "k_max");
     cudaFreeAsync(ratios, h->stream);
     return BEM_OK;

@@ -17,6 +17,7 @@ pytestmark = pytest.mark.gpu
 
 ENTRY_TOL = 1e-13      # |X_gpu - X_orc| <= ENTRY_TOL * max|X_orc|  (matrix entries)
 SOLVE_TOL = 1e-10      # FP64 path: relative current error against the oracle
+RESID_TOL = 1e-10      # relative residual of the solve on every configuration
 
 
 @pytest.fixture(scope="module")
@@ -239,7 +240,7 @@ def test_c2_star_4096(B, k):
     s.factor()
     vv = s.rhs_planewave(_cuda(I.planewave_angles(nrhs)))
     x, _, res = s.solve(vv, report=True)
-    assert res <= 1e-12
+    assert res <= RESID_TOL
     Q = _cuda(O.fourier_basis(N, M)).to(torch.complex128)
     assert _filtered_residual(s, Q, x, vv) <= 1e-9
     s.close()
@@ -266,7 +267,7 @@ def test_c3_random_star_16384_fp64(B):
     s.factor()
     vv = s.rhs_planewave(_cuda(I.planewave_angles(nrhs)))
     x, _, res = s.solve(vv, report=True)
-    assert res <= 1e-12
+    assert res <= RESID_TOL
     Q = _cuda(O.fourier_basis(N, M)).to(torch.complex128)
     assert _filtered_residual(s, Q, x, vv) <= 1e-9
     s.close()
