@@ -175,6 +175,26 @@ bem_status solve_many(bem_handle h, const void* v_dev, int64_t ldv, void* x_dev,
 bem_status solve_backward(bem_handle h, const void* g_dev, int64_t ldg, void* lambda_dev,
                           int64_t ldl, int64_t nrhs);
 
+/* solve_many_noalloc -- the paper has no counterpart to this call; it exists for callers
+ * that cannot allocate device memory while they solve: code recorded inside CUDA stream
+ * capture, services that reserve all of their memory at start-up, or hosts that embed the
+ * library under an allocator they do not own.  It computes the same FP64 Woodbury solve as
+ * solve_many's FP64 path, x = v/beta - beta^-2 U (I_r + beta^-1 V^H U)^-1 V^H v, but takes
+ * its two r x nrhs scratch blocks from a fixed array compiled into the library instead of
+ * the handle's workspace, and calls no allocator.
+ *  - Limit: r * nrhs <= 262144 (the array holds 2 x 262144 complex doubles, 8 MiB, which
+ *    every GPU that loads the library keeps until the process exits); larger requests
+ *    return BEM_E_UNSUPPORTED without doing any work.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *    make that first call before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents (nothing in it
+ *    needs to start at zero).  Calls whose work overlaps on the GPU -- two streams, or two
+ *    handles -- race on the array: serialise them.
+ *  - Layouts and aliasing rules are those of solve_many; no refinement and no residual
+ *    report (use solve_many for those).  Needs factor. */
+bem_status solve_many_noalloc(bem_handle h, const void* v_dev, int64_t ldv, void* x_dev, int64_t ldx,
+                              int64_t nrhs);
+
 /* Copies an internal matrix (BEM_MAT_*) into dst_dev with leading dimension ld (>= rows).
  * For BEM_MAT_SIGMA, dst_dev receives n doubles and ld is ignored. */
 bem_status bem_get_matrix(bem_handle h, int which, void* dst_dev, int64_t ld);

@@ -26,7 +26,7 @@ STATUS = {0: "BEM_OK", 1: "BEM_E_INVALID", 2: "BEM_E_NOMEM", 3: "BEM_E_CUDA", 4:
 EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error", "bem_set_stream",
            "bem_assemble", "filter_apply", "compress_compact", "factor", "bem_rhs_planewave",
            "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info", "bem_timing_enable",
-           "bem_timing_report")
+           "bem_timing_report", "solve_many_noalloc")
 
 
 class BemOptions(ctypes.Structure):
@@ -78,6 +78,8 @@ def load_library(path: str = LIB_PATH):
     L.solve_backward.argtypes = [vp, vp, i64, vp, i64, i64]
     L.bem_get_matrix.argtypes = [vp, i32, vp, i64]
     L.bem_get_info.argtypes = [vp, ctypes.POINTER(BemInfo)]
+    L.solve_many_noalloc.argtypes = [vp, vp, i64, vp, i64, i64]
+    L.solve_many_noalloc.restype = ctypes.c_int
     L.bem_timing_enable.argtypes = [vp, i32]
     L.bem_timing_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     for name in ("bem_create", "bem_destroy", "bem_set_stream", "bem_assemble", "filter_apply",
