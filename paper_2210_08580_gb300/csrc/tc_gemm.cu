@@ -1,17 +1,679 @@
-// Mixed-precision path (placeholder until the tcgen05 kernels land).
+// Mixed-precision dense products on the GB300 tensor cores (tcgen05, TMEM, TMA).
+//
+// A complex product C = A B (A: M x K, B: K x m, FP64 complex) is evaluated as one real
+// GEMM C' = A' B' with K' = 2K interleaved (re, im) and 2m output columns:
+//   A'[i, 2k+c] = component c of A[i, k];
+//   B'[2k, 2j] = Re B, B'[2k+1, 2j] = -Im B, B'[2k, 2j+1] = Im B, B'[2k+1, 2j+1] = Re B,
+// so C'[i, 2j] = Re C[i, j] and C'[i, 2j+1] = Im C[i, j].
+//
+// Each operand is split into S bf16 slices (error-free splitting after Ozaki et al.,
+// Numer. Algorithms 2012): with a power-of-two scale per row of A' (2^e_i) and per column
+// of B' (2^f_j), x 2^-e = sum_s a_s 2^{-7(s+1)} with integers |a_0| <= 128, |a_s| <= 64;
+// slice s is stored pre-multiplied by 2^{-7s}, which bf16 holds exactly.  Products of
+// slices (s, t) with s + t <= S - 1 are accumulated by tcgen05.mma (kind::f16, FP32
+// accumulation) into three TMEM accumulators: d = 0, d = 1 and d >= 2 (d = s + t).  Over a
+// K' chunk of 512 the d = 0 and d = 1 sums are exact in FP32 (integers below 2^24 in units
+// of 2^-7d) and the d >= 2 sum carries a relative rounding of 2^-24 on a term already
+// 2^-14 below the leading one.  After each chunk the epilogue warps add the three
+// accumulators into double-float (hi, lo) registers; the result is rescaled by
+// 2^{e_i + f_j - 14} and written in FP64.
+//
+// Kernel: one 128 x 128 tile of C' per CTA, 10 warps: warp 0 issues TMA loads (3D tensor
+// maps over the stacked slices, 64-byte swizzle, 32-element K blocks, 2 stages), warp 1
+// allocates TMEM and issues the MMAs, warps 2..9 drain TMEM (2 warps per TMEM lane
+// quarter, 64 columns each).  Every mbarrier wait is
+// bounded; a timeout sets the handle's device error word and the CTA winds down, freeing
+// its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "kernels.h"
 #include "tc_gemm.h"
 
-bem_status tc_prepare_operators(bem_ctx* h) { return bem_fail(h, BEM_E_UNSUPPORTED, "mixed path not built"); }
-bem_status tc_product_left(bem_ctx* h, int, const double*, const cplx*, int64_t, cplx*) {
-    return bem_fail(h, BEM_E_UNSUPPORTED, "mixed path not built");
+#define TC_BM 128
+#define TC_BN 128
+#define TC_BK 32
+#define TC_STAGES 2
+#define TC_CHUNK_KB 16              // K' chunk of 16 x 32 = 512 between TMEM flushes
+#define TC_SMAX 6
+#define TC_TILE_BYTES (TC_BM * TC_BK * 2)          // 8 KiB per slice tile (A and B alike)
+#define TC_THREADS 320             // 10 warps: TMA, MMA, 8 epilogue
+
+// ------------------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-bem_status tc_product_right(bem_ctx* h, int, const cplx*, int64_t, int64_t, cplx*, int64_t) {
-    return bem_fail(h, BEM_E_UNSUPPORTED, "mixed path not built");
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-bem_status tc_prepare_solve(bem_ctx* h) { return bem_fail(h, BEM_E_UNSUPPORTED, "mixed path not built"); }
-bem_status tc_solve_refined(bem_ctx* h, const cplx*, int64_t, cplx*, int64_t, int64_t, int32_t*, double*) {
-    return bem_fail(h, BEM_E_UNSUPPORTED, "mixed path not built");
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-void tc_release_operands(bem_ctx*) {}
-void tc_release_solve(bem_ctx*) {}
-void tc_destroy(bem_ctx*) {}
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok;
+}
+// bounded wait: false (and DEVERR_TIMEOUT set) if the phase does not complete in time
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255 && *(volatile int*)err) return false;
+    }
+    atomicOr(err, DEVERR_TIMEOUT);
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Shared-memory matrix descriptor, K-major operand tile with 64-byte swizzle: rows of
+// 64 B (32 bf16), 8-row groups 512 B apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major, M = 128, N = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+struct TcGemmArgs {
+    int M, Ncols;            // rows of C', columns of C' (= 2 m)
+    int nkb;                 // K' blocks of 32
+    int S;                   // slices per operand
+    const int* ea;           // M row exponents
+    const int* eb;           // Ncols column exponents
+    double2* out;            // complex output
+    int64_t ldo;
+    int transposed;          // 0: out[i + j ldo], 1: out[j + i ldo]
+    double alpha, beta;      // out = alpha C + beta out
+    int* err;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcGemmArgs p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int S = p.S;
+    // layout: [stage][A slices][B slices] tiles, then barriers
+    const size_t stage_bytes = (size_t)2 * S * TC_TILE_BYTES;
+    uint64_t* bars = (uint64_t*)(smem + TC_STAGES * stage_bytes);
+    uint64_t* full = bars;                 // [2]
+    uint64_t* empty = bars + 2;            // [2]
+    uint64_t* acc_full = bars + 4;
+    uint64_t* acc_empty = bars + 5;
+    uint32_t* tmem_holder = (uint32_t*)(bars + 6);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = (p.Ncols + TC_BN - 1) / TC_BN;
+    const int m0 = (blockIdx.x / n_tiles) * TC_BM;
+    const int n0 = (blockIdx.x % n_tiles) * TC_BN;
+    const int nchunks = (p.nkb + TC_CHUNK_KB - 1) / TC_CHUNK_KB;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1); mbar_init(&full[1], 1);
+        mbar_init(&empty[0], 1); mbar_init(&empty[1], 1);
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 8);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_holder))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *(volatile uint32_t*)tmem_holder;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------------------ TMA producer
+            int kb_issued = 0;
+            for (int kb = 0; kb < p.nkb; ++kb) {
+                const int st = kb & 1;
+                const uint32_t use = (uint32_t)(kb >> 1);
+                if (!mbar_wait(&empty[st], (use & 1u) ^ 1u, p.err)) break;
+                unsigned char* base = smem + st * stage_bytes;
+                mbar_expect_tx(&full[st], (uint32_t)stage_bytes);
+                for (int s = 0; s < S; ++s)
+                    tma_load_3d(base + s * TC_TILE_BYTES, &mapA, &full[st], kb * TC_BK, m0, s);
+                for (int t = 0; t < S; ++t)
+                    tma_load_3d(base + (S + t) * TC_TILE_BYTES, &mapB, &full[st], kb * TC_BK, n0, t);
+                kb_issued = kb + 1;
+            }
+            // on an early exit, let the copies already issued land before the CTA ends
+            if (kb_issued > 0 && kb_issued < p.nkb) {
+                const int kb = kb_issued - 1;
+                mbar_wait(&full[kb & 1], (uint32_t)((kb >> 1) & 1), p.err);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ------------------------------------------------------------ MMA issuer
+            constexpr uint32_t idesc = idesc_bf16_f32(TC_BM, TC_BN);
+            bool ok = true;
+            for (int c = 0; c < nchunks && ok; ++c) {
+                if (c > 0 && !mbar_wait(acc_empty, (uint32_t)((c - 1) & 1), p.err)) { ok = false; break; }
+                tc_fence_after();
+                uint32_t used0 = 0u, used1 = 0u, used2 = 0u;   // accumulator already written in this chunk
+                const int kb_end = min(p.nkb, (c + 1) * TC_CHUNK_KB);
+                for (int kb = c * TC_CHUNK_KB; kb < kb_end; ++kb) {
+                    const int st = kb & 1;
+                    if (!mbar_wait(&full[st], (uint32_t)((kb >> 1) & 1), p.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + st * stage_bytes);
+#pragma unroll 1
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        for (int s = 0; s < S; ++s) {
+                            const uint64_t da = sdesc_sw64(base + s * TC_TILE_BYTES + kk * 32);
+                            for (int t = 0; s + t < S; ++t) {
+                                const int a = min(s + t, 2);
+                                const uint64_t db = sdesc_sw64(base + (S + t) * TC_TILE_BYTES + kk * 32);
+                                const uint32_t acc = (a == 0) ? used0 : ((a == 1) ? used1 : used2);
+                                umma_bf16(tmem + a * TC_BN, da, db, idesc, acc);
+                                if (a == 0) used0 = 1u; else if (a == 1) used1 = 1u; else used2 = 1u;
+                            }
+                        }
+                    }
+                    umma_commit(&empty[st]);
+                }
+                if (ok) umma_commit(acc_full);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;       // column half: 64 columns of the tile
+        const int row = 32 * q + lane;
+        float hi[64], lo[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            if (!mbar_wait(acc_full, (uint32_t)(c & 1), p.err)) { ok = false; break; }
+            tc_fence_after();
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + a * TC_BN + 64 * half + 16 * cb, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) df_add(hi[16 * cb + j], lo[16 * cb + j], v[j]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {      // renormalise (hi, lo)
+                const float s = __fadd_rn(hi[j], lo[j]);
+                lo[j] = __fsub_rn(lo[j], __fsub_rn(s, hi[j]));
+                hi[j] = s;
+            }
+        }
+        // stage (hi, lo) through the idle stage buffers (all TMA loads and MMAs are done),
+        // then write out with a plain coalesced loop
+        float2* stash = reinterpret_cast<float2*>(smem);           // [128][TC_BN + 1]
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < 64; ++j) stash[row * (TC_BN + 1) + 64 * half + j] = make_float2(hi[j], lo[j]);
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");          // the 8 epilogue warps
+        if (ok) {
+            const int et = threadIdx.x - 64;                       // 0..255
+            const int ncw = min(TC_BN, p.Ncols - n0) >> 1;         // complex columns in this tile
+            const int mrows = min(TC_BM, p.M - m0);
+#pragma unroll 1
+            for (int idx = et; idx < TC_BM * (TC_BN / 2); idx += 256) {
+                int r_, cw;
+                if (p.transposed) { cw = idx % (TC_BN / 2); r_ = idx / (TC_BN / 2); }
+                else { r_ = idx % TC_BM; cw = idx / TC_BM; }
+                if (r_ >= mrows || cw >= ncw) continue;
+                const int gi = m0 + r_, gc = n0 + 2 * cw;
+                const float2 a = stash[r_ * (TC_BN + 1) + 2 * cw];
+                const float2 b = stash[r_ * (TC_BN + 1) + 2 * cw + 1];
+                // 2^(e_i + f_j - 14) built from its exponent bits (normal range)
+                const long long eb = (long long)(1023 + p.ea[gi] + p.eb[gc] - 14);
+                const double sc = __longlong_as_double(eb << 52);
+                const double re = ((double)a.x + (double)a.y) * sc;
+                const double im = ((double)b.x + (double)b.y) * sc;
+                const int j = gc >> 1;
+                double2* o = p.transposed ? (p.out + (int64_t)j + (int64_t)gi * p.ldo)
+                                          : (p.out + (int64_t)gi + (int64_t)j * p.ldo);
+                double2 val = make_double2(p.alpha * re, p.alpha * im);
+                if (p.beta != 0.0) {
+                    const double2 old = *o;
+                    val.x += p.beta * old.x;
+                    val.y += p.beta * old.y;
+                }
+                *o = val;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------------------ slicing
+// Row exponents of A'.  A_op[i, k] = src[i*sa_i + k*sa_k] (complex); e_i = frexp exponent
+// of max_k max(|Re|, |Im|) so that |x| 2^-e_i < 1.
+__global__ void k_exp_rows(const double2* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k, int* e) {
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (i >= M) return;
+    double mx = 0.0;
+    for (int64_t k = threadIdx.x & 31; k < K; k += 32) {
+        const double2 v = src[i * sa_i + k * sa_k];
+        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) {
+        int ex = 0;
+        if (mx > 0.0) frexp(mx, &ex);
+        e[i] = ex;
+    }
+}
+
+// B column exponents: B_op[k, j] = src[k*sb_k + j*sb_j] (complex, or real when is_real);
+// columns 2j and 2j+1 of B' share f_j.
+__global__ void k_exp_cols(const void* src, int is_real, int64_t K, int64_t m, int64_t sb_k, int64_t sb_j, int* f) {
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (j >= m) return;
+    double mx = 0.0;
+    for (int64_t k = threadIdx.x & 31; k < K; k += 32) {
+        if (is_real) {
+            mx = fmax(mx, fabs(((const double*)src)[k * sb_k + j * sb_j]));
+        } else {
+            const double2 v = ((const double2*)src)[k * sb_k + j * sb_j];
+            mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) {
+        int ex = 0;
+        if (mx > 0.0) frexp(mx, &ex);
+        f[2 * j] = ex;
+        f[2 * j + 1] = ex;
+    }
+}
+
+__device__ __forceinline__ void split_store(double x, int S, __nv_bfloat16* out, size_t slice_stride) {
+    // x in (-1, 1): slices a_s 2^{-7s} with a_s = rint(x 2^7), x <- x 2^7 - a_s
+    double sc = 1.0;
+#pragma unroll 1
+    for (int s = 0; s < S; ++s) {
+        const double y = x * 128.0;
+        const double a = rint(y);
+        out[s * slice_stride] = __float2bfloat16_rn((float)(a * sc));
+        x = y - a;
+        sc *= 0.0078125;
+    }
+}
+
+// A' slices: out[s][i][kp], kp = 2k + c, padded with zeros to Kp
+__global__ void k_slice_A(const double2* src, int64_t M, int64_t K, int64_t Kp, int64_t sa_i, int64_t sa_k,
+                          const int* e, int S, __nv_bfloat16* out) {
+    const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = blockIdx.y;
+    if (kp >= Kp || i >= M) return;
+    double x = 0.0;
+    const int64_t k = kp >> 1;
+    if (k < K) {
+        const double2 v = src[i * sa_i + k * sa_k];
+        x = ldexp((kp & 1) ? v.y : v.x, -e[i]);
+    }
+    split_store(x, S, out + i * Kp + kp, (size_t)M * Kp);
+}
+
+// B' slices stored K-major: out[s][jp][kp]
+__global__ void k_slice_B(const void* src, int is_real, int64_t K, int64_t m, int64_t Kp, int64_t sb_k,
+                          int64_t sb_j, const int* f, int S, __nv_bfloat16* out) {
+    const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t jp = blockIdx.y;
+    if (kp >= Kp || jp >= 2 * m) return;
+    double x = 0.0;
+    const int64_t k = kp >> 1, j = jp >> 1;
+    if (k < K) {
+        double re, im;
+        if (is_real) { re = ((const double*)src)[k * sb_k + j * sb_j]; im = 0.0; }
+        else { const double2 v = ((const double2*)src)[k * sb_k + j * sb_j]; re = v.x; im = v.y; }
+        const int c = (int)(kp & 1), d = (int)(jp & 1);
+        // B'[2k, 2j] = Re, B'[2k+1, 2j] = -Im, B'[2k, 2j+1] = Im, B'[2k+1, 2j+1] = Re
+        const double val = (d == 0) ? (c == 0 ? re : -im) : (c == 0 ? im : re);
+        x = ldexp(val, -f[jp]);
+    }
+    split_store(x, S, out + jp * Kp + kp, (size_t)(2 * m) * Kp);
+}
+
+// ------------------------------------------------------------------------------ host side
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static PFN_encodeTiled g_encode = nullptr;
+static std::mutex g_encode_mutex;
+
+static bem_status get_encode(bem_ctx* h) {
+    std::lock_guard<std::mutex> lk(g_encode_mutex);
+    if (g_encode) return BEM_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || !fn || q != cudaDriverEntryPointSuccess)
+        return bem_fail(h, BEM_E_CUDA, "cuTensorMapEncodeTiled is not available");
+    g_encode = (PFN_encodeTiled)fn;
+    return BEM_OK;
+}
+
+struct TcOperand {
+    __nv_bfloat16* slices = nullptr;  // S x rows x Kp
+    int* exps = nullptr;              // rows
+    int64_t rows = 0, Kp = 0, K = 0;
+    size_t cap = 0;                   // bytes allocated for slices
+    size_t exp_cap = 0;
+    CUtensorMap map;
+};
+
+struct TcState {
+    int S = TC_SMAX;
+    TcOperand opS, opW, opD;          // A operands: X^T of the assembled matrices
+    TcOperand opVh, opU;              // Woodbury factors
+    TcOperand bbuf;                   // B operand scratch (reused)
+};
+
+static TcState* tcs(bem_ctx* h) {
+    if (!h->tc) {
+        TcState* t = new TcState();
+        if (h->opt.split_slices >= 3 && h->opt.split_slices <= TC_SMAX) t->S = h->opt.split_slices;
+        h->tc = t;
+    }
+    return (TcState*)h->tc;
+}
+
+static int64_t pad64(int64_t x) { return (x + 63) / 64 * 64; }
+
+static bem_status encode_map(bem_ctx* h, TcOperand& op, int S) {
+    bem_status st = get_encode(h);
+    if (st != BEM_OK) return st;
+    cuuint64_t dims[3] = {(cuuint64_t)op.Kp, (cuuint64_t)op.rows, (cuuint64_t)S};
+    cuuint64_t strides[2] = {(cuuint64_t)(op.Kp * 2), (cuuint64_t)(op.Kp * op.rows * 2)};
+    cuuint32_t box[3] = {TC_BK, TC_BM, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(&op.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.slices, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return bem_fail(h, BEM_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return BEM_OK;
+}
+
+static bem_status reserve(bem_ctx* h, TcOperand& op, int64_t rows, int64_t Kp, int S) {
+    const size_t need = (size_t)S * rows * Kp * sizeof(__nv_bfloat16);
+    if (need > op.cap) {
+        if (op.slices) { cudaStreamSynchronize(h->stream); cudaFree(op.slices); op.slices = nullptr; op.cap = 0; }
+        BEM_CUDA(h, cudaMalloc((void**)&op.slices, need));
+        op.cap = need;
+    }
+    if ((size_t)rows * sizeof(int) > op.exp_cap) {
+        if (op.exps) { cudaStreamSynchronize(h->stream); cudaFree(op.exps); op.exps = nullptr; }
+        BEM_CUDA(h, cudaMalloc((void**)&op.exps, (size_t)rows * sizeof(int)));
+        op.exp_cap = (size_t)rows * sizeof(int);
+    }
+    op.rows = rows;
+    op.Kp = Kp;
+    return BEM_OK;
+}
+
+// A operand: rows M, K complex columns, A_op[i,k] = src[i*sa_i + k*sa_k]
+static bem_status slice_A(bem_ctx* h, TcOperand& op, const cplx* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k) {
+    const int S = tcs(h)->S;
+    const int64_t Kp = pad64(2 * K);
+    bem_status st = reserve(h, op, M, Kp, S);
+    if (st != BEM_OK) return st;
+    op.K = K;
+    BEM_TIMED(h, "k_exp_rows", (k_exp_rows<<<(unsigned)((M + 7) / 8), 256, 0, h->stream>>>(src, M, K, sa_i, sa_k, op.exps)));
+    BEM_LAUNCH(h, "k_exp_rows");
+    dim3 grid((unsigned)((Kp + 255) / 256), (unsigned)M);
+    BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, M, K, Kp, sa_i, sa_k, op.exps, S, op.slices)));
+    BEM_LAUNCH(h, "k_slice_A");
+    return encode_map(h, op, S);
+}
+
+// B operand: K x m (complex or real), B_op[k,j] = src[k*sb_k + j*sb_j]
+static bem_status slice_B(bem_ctx* h, TcOperand& op, const void* src, int is_real, int64_t K, int64_t m, int64_t sb_k,
+                          int64_t sb_j) {
+    const int S = tcs(h)->S;
+    const int64_t Kp = pad64(2 * K);
+    bem_status st = reserve(h, op, 2 * m, Kp, S);
+    if (st != BEM_OK) return st;
+    op.K = K;
+    BEM_TIMED(h, "k_exp_cols", (k_exp_cols<<<(unsigned)((m + 7) / 8), 256, 0, h->stream>>>(src, is_real, K, m, sb_k, sb_j, op.exps)));
+    BEM_LAUNCH(h, "k_exp_cols");
+    dim3 grid((unsigned)((Kp + 255) / 256), (unsigned)(2 * m));
+    BEM_TIMED(h, "k_slice_B", (k_slice_B<<<grid, 256, 0, h->stream>>>(src, is_real, K, m, Kp, sb_k, sb_j, op.exps, S, op.slices)));
+    BEM_LAUNCH(h, "k_slice_B");
+    return encode_map(h, op, S);
+}
+
+static size_t gemm_smem(int S) { return (size_t)TC_STAGES * 2 * S * TC_TILE_BYTES + 64 + 1024; }
+
+// out = alpha (A B) + beta out for sliced operands (complex result, M x m)
+static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cplx* out, int64_t ldo, int transposed,
+                          double alpha, double beta, const char* tag) {
+    TcState* t = tcs(h);
+    if (A.Kp != B.Kp) return bem_fail(h, BEM_E_INVALID, "tc_gemm: K mismatch");
+    TcGemmArgs p;
+    p.M = (int)A.rows;
+    p.Ncols = (int)B.rows;
+    p.nkb = (int)(A.Kp / TC_BK);
+    p.S = t->S;
+    p.ea = A.exps;
+    p.eb = B.exps;
+    p.out = out;
+    p.ldo = ldo;
+    p.transposed = transposed;
+    p.alpha = alpha;
+    p.beta = beta;
+    p.err = h->dev_err;
+    const size_t smem = gemm_smem(t->S);
+    BEM_CUDA(h, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int mt = (p.M + TC_BM - 1) / TC_BM, nt = (p.Ncols + TC_BN - 1) / TC_BN;
+    BEM_TIMED(h, tag, (k_tc_gemm<<<(unsigned)(mt * nt), TC_THREADS, smem, h->stream>>>(A.map, B.map, p)));
+    BEM_LAUNCH(h, "k_tc_gemm");
+    return BEM_OK;
+}
+
+// ------------------------------------------------------------------------------ interface
+bem_status tc_prepare_operators(bem_ctx* h) {
+    TcState* t = tcs(h);
+    const int64_t N = h->N;
+    bem_status st;
+    // slices of X^T: row i of the A operand is column i of X (contiguous)
+    if ((st = slice_A(h, t->opS, h->S, N, N, N, 1)) != BEM_OK) return st;
+    if ((st = slice_A(h, t->opW, h->W, N, N, N, 1)) != BEM_OK) return st;
+    if (h->D) {
+        if ((st = slice_A(h, t->opD, h->D, N, N, N, 1)) != BEM_OK) return st;
+    }
+    return BEM_OK;
+}
+
+static const TcOperand* op_of(TcState* t, int op) {
+    return op == TC_OP_S ? &t->opS : (op == TC_OP_W ? &t->opW : &t->opD);
+}
+
+bem_status tc_product_left(bem_ctx* h, int op, const double* Qreal, const cplx* Y, int64_t nc, cplx* out) {
+    TcState* t = tcs(h);
+    const int64_t N = h->N;
+    const TcOperand* A = op_of(t, op);
+    if (!A->slices) return bem_fail(h, BEM_E_INVALID, "tc_product_left: operator not sliced");
+    bem_status st;
+    // out^T = X^T L^T: B = Q (N x nc real) or Y^T (B[k, j] = Y[j + k nc])
+    if (Qreal) st = slice_B(h, t->bbuf, Qreal, 1, N, nc, 1, N);
+    else st = slice_B(h, t->bbuf, Y, 0, N, nc, nc, 1);
+    if (st != BEM_OK) return st;
+    return tc_gemm(h, *A, t->bbuf, out, nc, 1, 1.0, 0.0, op == TC_OP_S ? "tc_filter_QtS" : (op == TC_OP_W ? "tc_filter_YN" : "tc_filter_QtD"));
+}
+
+bem_status tc_product_right(bem_ctx* h, int op, const cplx* y, int64_t ldy, int64_t nrhs, cplx* out, int64_t ld) {
+    TcState* t = tcs(h);
+    const TcOperand* A = op_of(t, op);
+    if (!A->slices) return bem_fail(h, BEM_E_INVALID, "tc_product_right: operator not sliced");
+    bem_status st = slice_B(h, t->bbuf, y, 0, h->N, nrhs, 1, ldy);
+    if (st != BEM_OK) return st;
+    return tc_gemm(h, *A, t->bbuf, out, ld, 0, 1.0, 0.0, "tc_rhs_SY");
+}
+
+bem_status tc_prepare_solve(bem_ctx* h) {
+    TcState* t = tcs(h);
+    const int64_t N = h->N, r = h->r;
+    bem_status st;
+    // V^H as A (r x N): A_op[i, k] = Vh[i + k r];  U as A (N x r): A_op[i, k] = U[i + k N]
+    if ((st = slice_A(h, t->opVh, h->Vh, r, N, 1, r)) != BEM_OK) return st;
+    return slice_A(h, t->opU, h->U, N, r, 1, N);
+}
+
+// x = v/beta - beta^-2 U Kinv V^H v with tensor-core products (T, T2: r x nrhs scratch)
+static bem_status woodbury_tc(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x, int64_t ldx, int64_t nrhs, cplx* T,
+                              cplx* T2, double xscale, double vscale) {
+    TcState* t = tcs(h);
+    const int64_t N = h->N, r = h->r;
+    bem_status st;
+    if ((st = slice_B(h, t->bbuf, v, 0, N, nrhs, 1, ldv)) != BEM_OK) return st;
+    if ((st = tc_gemm(h, t->opVh, t->bbuf, T, r, 0, 1.0, 0.0, "tc_solve_Vhv")) != BEM_OK) return st;
+    h->tag = "gemm_solve_core";
+    if ((st = zgemm(h, OP_N, OP_N, r, nrhs, r, cmk(1, 0), h->K, r, T, r, cmk(0, 0), T2, r)) != BEM_OK) return st;
+    // x <- xscale x + vscale v / beta ; then x -= beta^-2 U T2
+    if ((st = launch_axpby(h, x, ldx, v, ldv, cmk(vscale / h->beta, 0), cmk(xscale, 0), N, nrhs)) != BEM_OK) return st;
+    if ((st = slice_B(h, t->bbuf, T2, 0, r, nrhs, 1, r)) != BEM_OK) return st;
+    return tc_gemm(h, t->opU, t->bbuf, x, ldx, 0, -vscale / (h->beta * h->beta), 1.0, "tc_solve_UT");
+}
+
+bem_status tc_solve_refined(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x, int64_t ldx, int64_t nrhs, int32_t* iters,
+                            double* max_rel_resid) {
+    TcState* t = tcs(h);
+    const int64_t N = h->N, r = h->r;
+    cplx *T = nullptr, *T2 = nullptr, *rho = nullptr;
+    double* dres = nullptr;
+    bem_status st;
+    {
+        void* base = nullptr;
+        const size_t bT = ((sizeof(cplx) * r * nrhs + 255) / 256) * 256;
+        const size_t bR = ((sizeof(cplx) * N * nrhs + 255) / 256) * 256;
+        if ((st = bem_workspace(h, 2 * bT + bR + 256, &base)) != BEM_OK) return st;
+        T = (cplx*)base;
+        T2 = (cplx*)((char*)base + bT);
+        rho = (cplx*)((char*)base + 2 * bT);
+        dres = (double*)((char*)base + 2 * bT + bR);
+    }
+    // initial solve
+    if ((st = woodbury_tc(h, v, ldv, x, ldx, nrhs, T, T2, 0.0, 1.0)) != BEM_OK) return st;
+    int it = 0;
+    double res = 0.0;
+    for (;;) {
+        // rho = v - (beta x + U V^H x)
+        if ((st = slice_B(h, t->bbuf, x, 0, N, nrhs, 1, ldx)) != BEM_OK) return st;
+        if ((st = tc_gemm(h, t->opVh, t->bbuf, T, r, 0, 1.0, 0.0, "tc_resid_Vhx")) != BEM_OK) return st;
+        if ((st = launch_copy2d(h, rho, N, v, ldv, N, nrhs, sizeof(cplx))) != BEM_OK) return st;
+        if ((st = launch_axpby(h, rho, N, x, ldx, cmk(-h->beta, 0), cmk(1, 0), N, nrhs)) != BEM_OK) return st;
+        if ((st = slice_B(h, t->bbuf, T, 0, r, nrhs, 1, r)) != BEM_OK) return st;
+        if ((st = tc_gemm(h, t->opU, t->bbuf, rho, N, 0, -1.0, 1.0, "tc_resid_UT")) != BEM_OK) return st;
+        if ((st = launch_col_norm_ratio(h, rho, N, v, ldv, N, nrhs, dres)) != BEM_OK) return st;
+        BEM_CUDA(h, cudaMemcpyAsync(&res, dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        BEM_CUDA(h, cudaStreamSynchronize(h->stream));
+        int e = 0;
+        BEM_CUDA(h, cudaMemcpy(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            cudaMemset(h->dev_err, 0, sizeof(int));
+            return bem_fail(h, (e & DEVERR_TIMEOUT) ? BEM_E_TIMEOUT : BEM_E_CUDA, "tensor-core solve: device error");
+        }
+        if (!(res > h->opt.refine_rtol) || it >= h->opt.max_refine) break;
+        // x += Woodbury(rho)
+        if ((st = woodbury_tc(h, rho, N, x, ldx, nrhs, T, T2, 1.0, 1.0)) != BEM_OK) return st;
+        ++it;
+    }
+    if (iters) *iters = it;
+    if (max_rel_resid) *max_rel_resid = res;
+    if (res > h->opt.refine_rtol || res != res)
+        return bem_fail(h, BEM_E_NOT_CONVERGED, "mixed solve: residual " + std::to_string(res) + " above refine_rtol");
+    return BEM_OK;
+}
+
+static void free_op(TcOperand& op) {
+    if (op.slices) cudaFree(op.slices);
+    if (op.exps) cudaFree(op.exps);
+    op = TcOperand();
+}
+
+void tc_release_operands(bem_ctx* h) {
+    if (!h->tc) return;
+    TcState* t = (TcState*)h->tc;
+    free_op(t->opS); free_op(t->opW); free_op(t->opD);
+}
+void tc_release_solve(bem_ctx* h) {
+    if (!h->tc) return;
+    TcState* t = (TcState*)h->tc;
+    free_op(t->opVh); free_op(t->opU);
+}
+void tc_destroy(bem_ctx* h) {
+    if (!h->tc) return;
+    TcState* t = (TcState*)h->tc;
+    free_op(t->opS); free_op(t->opW); free_op(t->opD); free_op(t->opVh); free_op(t->opU); free_op(t->bbuf);
+    delete t;
+    h->tc = nullptr;
+}

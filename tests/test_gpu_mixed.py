@@ -1,0 +1,96 @@
+"""Mixed-precision path (split-bf16 tcgen05 products + FP64 refinement) against the CPU
+oracle and against the FP64 GPU path.
+
+Bar (BASELINE metric): the refined mixed solution within 1e-8 of the FP64 reference.
+The operator blocks themselves are checked tighter, at the accuracy the split gives."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bem_oracle as O
+from paper_2210_08580_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+MIXED_SOLVE_TOL = 1e-8      # relative current error after refinement
+MIXED_BLOCK_TOL = 1e-10     # filtered block B and preconditioned RHS v, relative to max
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2210_08580_gb300 import bem
+    bem.load_library()
+    return bem
+
+
+@pytest.fixture(scope="module")
+def star301_ref():
+    v, _, _ = I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), 301)
+    k = 2.0
+    mats = O.assemble(v, k, "SWD")
+    ang = I.planewave_angles(6)
+    f = O.rhs_planewave(v, k, ang)
+    h2 = O.rhs_planewave_h(v, k, ang)
+    return dict(v=v, k=k, ang=ang,
+                efie=O.filtered_solve_projected(mats, v, f, 20, 1e-10),
+                cfie=O.filtered_solve_projected(mats, v, f, 20, 1e-10, alpha=0.5, h2=h2))
+
+
+def test_mixed_blocks_and_solve_match_oracle(B, star301_ref):
+    ref = star301_ref["efie"]
+    s = B.Solver(device=0, prec="mixed")
+    s.assemble(_cuda(star301_ref["v"]), star301_ref["k"], ops="SW")
+    vv = s.rhs_planewave(_cuda(star301_ref["ang"]))
+    assert _rel(vv.cpu().numpy().T, ref["vx"]) <= MIXED_BLOCK_TOL
+    s.filter_apply(41)
+    Bg = s.matrix("B").cpu().numpy()
+    assert _rel(Bg, ref["B"]) <= MIXED_BLOCK_TOL, _rel(Bg, ref["B"])
+    assert s.compress(1e-10) == ref["rank"]
+    s.factor()
+    x, it, res = s.solve(vv, report=True)
+    assert res <= 1e-10
+    assert _rel(x.cpu().numpy().T, ref["x"]) <= MIXED_SOLVE_TOL
+    s.close()
+
+
+def test_mixed_cfie(B, star301_ref):
+    ref = star301_ref["cfie"]
+    s = B.Solver(device=0, prec="mixed")
+    s.assemble(_cuda(star301_ref["v"]), star301_ref["k"], ops="SWD")
+    s.filter_apply(41, alpha=0.5)
+    assert _rel(s.matrix("B").cpu().numpy(), ref["B"]) <= MIXED_BLOCK_TOL
+    s.compress(1e-10)
+    s.factor()
+    x = s.solve(s.rhs_planewave(_cuda(star301_ref["ang"])))
+    assert _rel(x.cpu().numpy().T, ref["x"]) <= MIXED_SOLVE_TOL
+    s.close()
+
+
+def test_mixed_matches_fp64_c3_16384(B):
+    """C3 (N = 16384, k = 2, n = 201, tol 1e-10): mixed-path solution within 1e-8 of the
+    FP64 GPU path on the same geometry, with the FP64 residual reported below 1e-10."""
+    N, k, M, nrhs = 16384, 2.0, 100, 64
+    v, _, _ = I.equal_chord_mesh(I.random_star(0), N)
+    ang = _cuda(I.planewave_angles(nrhs))
+    xs = {}
+    for prec in ("fp64", "mixed"):
+        s = B.Solver(device=0, prec=prec)
+        s.assemble(_cuda(v), k, ops="SW")
+        s.filter_apply(2 * M + 1)
+        s.compress(1e-10)
+        s.factor()
+        vv = s.rhs_planewave(ang)
+        x, it, res = s.solve(vv, report=True)
+        assert res <= 1e-10, (prec, res)
+        xs[prec] = x
+        s.close()
+    err = float((xs["mixed"] - xs["fp64"]).abs().max() / xs["fp64"].abs().max())
+    assert err <= MIXED_SOLVE_TOL, err
