@@ -102,7 +102,8 @@ class Solver:
     """
 
     def __init__(self, device: int = 0, prec: str = "fp64", include_kernel_mode: bool = True,
-                 refine_rtol: float = 1e-10, max_refine: int = 6, stream: torch.cuda.Stream | None = None):
+                 refine_rtol: float = 1e-10, max_refine: int = 6, stream: torch.cuda.Stream | None = None,
+                 split_slices: int = 0):
         self.L = load_library()
         self.device = torch.device("cuda", device)
         opt = BemOptions()
@@ -111,6 +112,7 @@ class Solver:
         opt.include_kernel_mode = 1 if include_kernel_mode else 0
         opt.refine_rtol = refine_rtol
         opt.max_refine = max_refine
+        opt.split_slices = split_slices
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = ctypes.c_void_p()
         self._check(self.L.bem_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream),

@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "kernels.h"
@@ -40,6 +41,7 @@
 #define TC_CHUNK_KB 16              // K' chunk of 16 x 32 = 512 between TMEM flushes
 #define TC_SMAX 6
 #define TC_TILE_BYTES (TC_BM * TC_BK * 2)          // 8 KiB per slice tile (A and B alike)
+#define TC_STASH_BYTES (TC_BM * (TC_BN + 1) * 8)   // epilogue staging of (hi, lo) pairs
 #define TC_THREADS 320             // 10 warps: TMA, MMA, 8 epilogue
 
 // ------------------------------------------------------------------------------ PTX helpers
@@ -147,9 +149,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int S = p.S;
-    // layout: [stage][A slices][B slices] tiles, then barriers
+    // layout: [stage][A slices][B slices] tiles (reused as the epilogue stash once the
+    // MMAs are done), then the barriers after max(stages, stash)
     const size_t stage_bytes = (size_t)2 * S * TC_TILE_BYTES;
-    uint64_t* bars = (uint64_t*)(smem + TC_STAGES * stage_bytes);
+    const size_t data_bytes = max((size_t)TC_STAGES * stage_bytes, (size_t)TC_STASH_BYTES);
+    uint64_t* bars = (uint64_t*)(smem + data_bytes);
     uint64_t* full = bars;                 // [2]
     uint64_t* empty = bars + 2;            // [2]
     uint64_t* acc_full = bars + 4;
@@ -511,7 +515,10 @@ static bem_status slice_B(bem_ctx* h, TcOperand& op, const void* src, int is_rea
     return encode_map(h, op, S);
 }
 
-static size_t gemm_smem(int S) { return (size_t)TC_STAGES * 2 * S * TC_TILE_BYTES + 64 + 1024; }
+static size_t gemm_smem(int S) {
+    const size_t data = std::max((size_t)TC_STAGES * 2 * S * TC_TILE_BYTES, (size_t)TC_STASH_BYTES);
+    return data + 64 + 1024;    // barriers + TMEM address, and slack for 1024-byte alignment
+}
 
 // out = alpha (A B) + beta out for sliced operands (complex result, M x m)
 static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cplx* out, int64_t ldo, int transposed,
