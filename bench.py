@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--N", type=int, default=16384)
     ap.add_argument("--k", type=float, default=2.0)
     ap.add_argument("--M", type=int, default=100)
@@ -48,8 +48,8 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--compare-fp64", action="store_true",
-                    help="also time the FP64 path once and report it beside the mixed path")
+    ap.add_argument("--no-compare-fp64", action="store_true",
+                    help="skip timing the FP64 path beside the mixed path")
     return ap.parse_args()
 
 
@@ -290,7 +290,7 @@ def main():
                "d2h_bytes_per_step": int(xh.numel() * 16)}
 
     fp64_cmp = None
-    if args.compare_fp64 and args.prec == "mixed":
+    if not args.no_compare_fp64 and args.prec == "mixed":
         s64 = bem.Solver(device=local, prec="fp64", stream=stream)
         t64 = timed(lambda: (s64.assemble(verts, args.k, ops="SW"), s64.filter_apply(n_modes),
                              s64.compress(args.tol), s64.factor(),

@@ -11,12 +11,13 @@
 // of B' (2^f_j), x 2^-e = sum_s a_s 2^{-7(s+1)} with integers |a_0| <= 128, |a_s| <= 64;
 // slice s is stored pre-multiplied by 2^{-7s}, which bf16 holds exactly.  Products of
 // slices (s, t) with s + t <= S - 1 are accumulated by tcgen05.mma (kind::f16, FP32
-// accumulation) into three TMEM accumulators: d = 0, d = 1 and d >= 2 (d = s + t).  Over a
-// K' chunk of 512 the d = 0 and d = 1 sums are exact in FP32 (integers below 2^24 in units
-// of 2^-7d) and the d >= 2 sum carries a relative rounding of 2^-24 on a term already
-// 2^-14 below the leading one.  After each chunk the epilogue warps add the three
-// accumulators into double-float (hi, lo) registers; the result is rescaled by
-// 2^{e_i + f_j - 14} and written in FP64.
+// accumulation) into four TMEM accumulators: d = 0, 1, 2 and d >= 3 (d = s + t).  Over a
+// K' chunk of 256 the d = 0, 1, 2 sums are multiples of 2^-7d spanning at most 23 bits, so
+// FP32 accumulation is exact for them (measured on GB300: a group of one magnitude is
+// exact, while mixing groups 7 or more bits apart in one accumulator rounds at 2^-24 of
+// it); the d >= 3 sum carries that 2^-24 rounding on a term 2^-21 below the leading one.
+// After each chunk the epilogue warps add the accumulators into double-float (hi, lo)
+// registers; the result is rescaled by 2^{e_i + f_j - 14} and written in FP64.
 //
 // Kernel: one 128 x 128 tile of C' per CTA, 10 warps: warp 0 issues TMA loads (3D tensor
 // maps over the stacked slices, 64-byte swizzle, 32-element K blocks, 2 stages), warp 1
@@ -38,8 +39,10 @@
 #define TC_BN 128
 #define TC_BK 32
 #define TC_STAGES 2
-#define TC_CHUNK_KB 16              // K' chunk of 16 x 32 = 512 between TMEM flushes
-#define TC_SMAX 6
+#define TC_CHUNK_KB 8               // K' chunk of 8 x 32 = 256 between TMEM flushes
+#define TC_NACC 4                   // TMEM accumulators (4 x 128 columns = all 512)
+#define TC_SMAX 7
+#define TC_W_BAND 64                // |i - j| (cyclic) <= band of N applied in FP64
 #define TC_TILE_BYTES (TC_BM * TC_BK * 2)          // 8 KiB per slice tile (A and B alike)
 #define TC_STASH_BYTES (TC_BM * (TC_BN + 1) * 8)   // epilogue staging of (hi, lo) pairs
 #define TC_THREADS 320             // 10 warps: TMA, MMA, 8 epilogue
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int c = 0; c < nchunks && ok; ++c) {
                 if (c > 0 && !mbar_wait(acc_empty, (uint32_t)((c - 1) & 1), p.err)) { ok = false; break; }
                 tc_fence_after();
-                uint32_t used0 = 0u, used1 = 0u, used2 = 0u;   // accumulator already written in this chunk
+                uint32_t used0 = 0u, used1 = 0u, used2 = 0u, used3 = 0u;   // written in this chunk
                 const int kb_end = min(p.nkb, (c + 1) * TC_CHUNK_KB);
                 for (int kb = c * TC_CHUNK_KB; kb < kb_end; ++kb) {
                     const int st = kb & 1;
@@ -225,11 +228,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         for (int s = 0; s < S; ++s) {
                             const uint64_t da = sdesc_sw64(base + s * TC_TILE_BYTES + kk * 32);
                             for (int t = 0; s + t < S; ++t) {
-                                const int a = min(s + t, 2);
+                                const int a = min(s + t, TC_NACC - 1);
                                 const uint64_t db = sdesc_sw64(base + (S + t) * TC_TILE_BYTES + kk * 32);
-                                const uint32_t acc = (a == 0) ? used0 : ((a == 1) ? used1 : used2);
+                                const uint32_t acc = (a == 0) ? used0 : ((a == 1) ? used1 : ((a == 2) ? used2 : used3));
                                 umma_bf16(tmem + a * TC_BN, da, db, idesc, acc);
-                                if (a == 0) used0 = 1u; else if (a == 1) used1 = 1u; else used2 = 1u;
+                                if (a == 0) used0 = 1u; else if (a == 1) used1 = 1u; else if (a == 2) used2 = 1u; else used3 = 1u;
                             }
                         }
                     }
@@ -250,14 +253,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int c = 0; c < nchunks; ++c) {
             if (!mbar_wait(acc_full, (uint32_t)(c & 1), p.err)) { ok = false; break; }
             tc_fence_after();
+            const int nacc = min(S, TC_NACC);   // accumulators the MMAs wrote (TMEM is not zeroed)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
+            for (int a = 0; a < TC_NACC; ++a) {
 #pragma unroll
                 for (int cb = 0; cb < 4; ++cb) {
                     float v[16];
                     tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + a * TC_BN + 64 * half + 16 * cb, v);
+                    if (a < nacc) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) df_add(hi[16 * cb + j], lo[16 * cb + j], v[j]);
+                        for (int j = 0; j < 16; ++j) df_add(hi[16 * cb + j], lo[16 * cb + j], v[j]);
+                    }
                 }
             }
             tc_fence_before();
@@ -320,11 +326,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // ------------------------------------------------------------------------------ slicing
 // Row exponents of A'.  A_op[i, k] = src[i*sa_i + k*sa_k] (complex); e_i = frexp exponent
 // of max_k max(|Re|, |Im|) so that |x| 2^-e_i < 1.
-__global__ void k_exp_rows(const double2* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k, int* e) {
+// band >= 0 (square operators): entries with cyclic |i - k| <= band are excluded (they are
+// applied separately in FP64).
+__device__ __forceinline__ bool in_band(int64_t i, int64_t k, int64_t K, int band) {
+    if (band < 0) return false;
+    int64_t d = i - k;
+    if (d < 0) d = -d;
+    if (K - d < d) d = K - d;
+    return d <= band;
+}
+
+__global__ void k_exp_rows(const double2* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k, int band, int* e) {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (i >= M) return;
     double mx = 0.0;
     for (int64_t k = threadIdx.x & 31; k < K; k += 32) {
+        if (in_band(i, k, K, band)) continue;
         const double2 v = src[i * sa_i + k * sa_k];
         mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
     }
@@ -374,13 +391,13 @@ __device__ __forceinline__ void split_store(double x, int S, __nv_bfloat16* out,
 
 // A' slices: out[s][i][kp], kp = 2k + c, padded with zeros to Kp
 __global__ void k_slice_A(const double2* src, int64_t M, int64_t K, int64_t Kp, int64_t sa_i, int64_t sa_k,
-                          const int* e, int S, __nv_bfloat16* out) {
+                          int band, const int* e, int S, __nv_bfloat16* out) {
     const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = blockIdx.y;
     if (kp >= Kp || i >= M) return;
     double x = 0.0;
     const int64_t k = kp >> 1;
-    if (k < K) {
+    if (k < K && !in_band(i, k, K, band)) {
         const double2 v = src[i * sa_i + k * sa_k];
         x = ldexp((kp & 1) ? v.y : v.x, -e[i]);
     }
@@ -436,7 +453,7 @@ struct TcOperand {
 };
 
 struct TcState {
-    int S = TC_SMAX;
+    int S = 6;                        // slices per operand (3..TC_SMAX), 6 = 42 bits
     TcOperand opS, opW, opD;          // A operands: X^T of the assembled matrices
     TcOperand opVh, opU;              // Woodbury factors
     TcOperand bbuf;                   // B operand scratch (reused)
@@ -484,17 +501,19 @@ static bem_status reserve(bem_ctx* h, TcOperand& op, int64_t rows, int64_t Kp, i
     return BEM_OK;
 }
 
-// A operand: rows M, K complex columns, A_op[i,k] = src[i*sa_i + k*sa_k]
-static bem_status slice_A(bem_ctx* h, TcOperand& op, const cplx* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k) {
+// A operand: rows M, K complex columns, A_op[i,k] = src[i*sa_i + k*sa_k]; band >= 0 drops
+// the cyclic band |i - k| <= band (square operators)
+static bem_status slice_A(bem_ctx* h, TcOperand& op, const cplx* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k,
+                          int band = -1) {
     const int S = tcs(h)->S;
     const int64_t Kp = pad64(2 * K);
     bem_status st = reserve(h, op, M, Kp, S);
     if (st != BEM_OK) return st;
     op.K = K;
-    BEM_TIMED(h, "k_exp_rows", (k_exp_rows<<<(unsigned)((M + 7) / 8), 256, 0, h->stream>>>(src, M, K, sa_i, sa_k, op.exps)));
+    BEM_TIMED(h, "k_exp_rows", (k_exp_rows<<<(unsigned)((M + 7) / 8), 256, 0, h->stream>>>(src, M, K, sa_i, sa_k, band, op.exps)));
     BEM_LAUNCH(h, "k_exp_rows");
     dim3 grid((unsigned)((Kp + 255) / 256), (unsigned)M);
-    BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, M, K, Kp, sa_i, sa_k, op.exps, S, op.slices)));
+    BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, M, K, Kp, sa_i, sa_k, band, op.exps, S, op.slices)));
     BEM_LAUNCH(h, "k_slice_A");
     return encode_map(h, op, S);
 }
@@ -553,11 +572,30 @@ bem_status tc_prepare_operators(bem_ctx* h) {
     bem_status st;
     // slices of X^T: row i of the A operand is column i of X (contiguous)
     if ((st = slice_A(h, t->opS, h->S, N, N, N, 1)) != BEM_OK) return st;
-    if ((st = slice_A(h, t->opW, h->W, N, N, N, 1)) != BEM_OK) return st;
+    // N's near band (entries up to ~1e4 x its far field) is applied exactly in FP64, so the
+    // split only carries the far part with its own, much smaller row scale
+    if ((st = slice_A(h, t->opW, h->W, N, N, N, 1, (int)std::min<int64_t>(TC_W_BAND, (N - 1) / 2))) != BEM_OK) return st;
     if (h->D) {
         if ((st = slice_A(h, t->opD, h->D, N, N, N, 1)) != BEM_OK) return st;
     }
     return BEM_OK;
+}
+
+// out (nc x N, ld nc) += Y (nc x N, ld nc) * W_band, W_band = entries of W with cyclic
+// |k - j| <= band; FP64.  Thread (m, j): sum over the 2 band + 1 rows k of column j.
+__global__ void k_band_left(const double2* __restrict__ Y, const double2* __restrict__ W, int64_t N, int64_t nc,
+                            int band, double2* out) {
+    const int64_t m = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.y * 8 + threadIdx.y;
+    if (m >= nc || j >= N) return;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int t = -band; t <= band; ++t) {
+        int64_t k = j + t;
+        if (k < 0) k += N; else if (k >= N) k -= N;
+        cfma(acc, Y[m + k * nc], W[k + j * N]);
+    }
+    double2* o = out + m + j * nc;
+    *o = cadd(*o, acc);
 }
 
 static const TcOperand* op_of(TcState* t, int op) {
@@ -574,7 +612,14 @@ bem_status tc_product_left(bem_ctx* h, int op, const double* Qreal, const cplx* 
     if (Qreal) st = slice_B(h, t->bbuf, Qreal, 1, N, nc, 1, N);
     else st = slice_B(h, t->bbuf, Y, 0, N, nc, nc, 1);
     if (st != BEM_OK) return st;
-    return tc_gemm(h, *A, t->bbuf, out, nc, 1, 1.0, 0.0, op == TC_OP_S ? "tc_filter_QtS" : (op == TC_OP_W ? "tc_filter_YN" : "tc_filter_QtD"));
+    st = tc_gemm(h, *A, t->bbuf, out, nc, 1, 1.0, 0.0, op == TC_OP_S ? "tc_filter_QtS" : (op == TC_OP_W ? "tc_filter_YN" : "tc_filter_QtD"));
+    if (st != BEM_OK || op != TC_OP_W) return st;
+    if (!Y) return bem_fail(h, BEM_E_INVALID, "tc_product_left: N needs a complex left factor");
+    const int band = (int)std::min<int64_t>(TC_W_BAND, (N - 1) / 2);
+    dim3 grid((unsigned)((nc + 31) / 32), (unsigned)((N + 7) / 8));
+    BEM_TIMED(h, "k_band_left", (k_band_left<<<grid, dim3(32, 8), 0, h->stream>>>(Y, h->W, N, nc, band, out)));
+    BEM_LAUNCH(h, "k_band_left");
+    return BEM_OK;
 }
 
 bem_status tc_product_right(bem_ctx* h, int op, const cplx* y, int64_t ldy, int64_t nrhs, cplx* out, int64_t ld) {

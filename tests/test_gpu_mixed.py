@@ -13,7 +13,8 @@ from paper_2210_08580_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 MIXED_SOLVE_TOL = 1e-8      # relative current error after refinement
-MIXED_BLOCK_TOL = 1e-10     # filtered block B and preconditioned RHS v, relative to max
+MIXED_RHS_TOL = 1e-10       # preconditioned RHS v, relative to max
+MIXED_BLOCK_TOL = 1e-9      # filtered block B, relative to max: B = Y/g - Q^T/4 cancels ~3 digits
 
 
 def _cuda(a):
@@ -49,7 +50,7 @@ def test_mixed_blocks_and_solve_match_oracle(B, star301_ref):
     s = B.Solver(device=0, prec="mixed")
     s.assemble(_cuda(star301_ref["v"]), star301_ref["k"], ops="SW")
     vv = s.rhs_planewave(_cuda(star301_ref["ang"]))
-    assert _rel(vv.cpu().numpy().T, ref["vx"]) <= MIXED_BLOCK_TOL
+    assert _rel(vv.cpu().numpy().T, ref["vx"]) <= MIXED_RHS_TOL
     s.filter_apply(41)
     Bg = s.matrix("B").cpu().numpy()
     assert _rel(Bg, ref["B"]) <= MIXED_BLOCK_TOL, _rel(Bg, ref["B"])
