@@ -348,13 +348,17 @@ bem_status factor(bem_handle h) {
     cv.add((void**)&Kt, sizeof(cplx) * r * r);
     if ((st = cv.commit(h)) != BEM_OK) return st;
     // K = I_r + beta^-1 V^H U, stored as its inverse
-    h->tag = "gemm_factor_VhU";
-    if ((st = zgemm(h, OP_N, OP_N, r, r, N, cmk(1.0 / h->beta, 0), h->Vh, r, h->U, N, cmk(0, 0), Kt, r)) != BEM_OK) return st;
+    if (h->opt.prec == BEM_MIXED_BF16) {
+        // slices of U and V^H serve the core product here and every later solve
+        if ((st = tc_prepare_solve(h)) != BEM_OK) return st;
+        if ((st = tc_core_product(h, Kt)) != BEM_OK) return st;
+    } else {
+        h->tag = "gemm_factor_VhU";
+        if ((st = zgemm(h, OP_N, OP_N, r, r, N, cmk(1.0 / h->beta, 0), h->Vh, r, h->U, N, cmk(0, 0), Kt, r)) != BEM_OK)
+            return st;
+    }
     if ((st = launch_add_identity(h, Kt, r, (int)r, cmk(1, 0))) != BEM_OK) return st;
     if ((st = launch_gauss_jordan(h, Kt, h->K, (int)r)) != BEM_OK) return st;
-    if (h->opt.prec == BEM_MIXED_BF16) {
-        if ((st = tc_prepare_solve(h)) != BEM_OK) return st;
-    }
     if ((st = check_dev_err(h)) != BEM_OK) return st;
     h->stage = 4;
     return BEM_OK;

@@ -12,6 +12,9 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <mutex>
+#include <vector>
+
 #include "bessel.cuh"
 #include "kernels.h"
 
@@ -91,6 +94,129 @@ void series_coefficients(double k, double rmax, SeriesCoef* sc) {
     sc->nm = nm;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Host construction of the far-field Bessel table (bessel.cuh), in long double.
+// ---------------------------------------------------------------------------------------
+typedef long double ld;
+static const ld LD_PI = 3.141592653589793238462643383279502884L;
+static const ld LD_GAMMA = 0.577215664901532860606512090082402431L;
+
+// J0, J1 and the log-free parts Yh0, Yh1 by the ascending series (z <= 4)
+static void host_series(ld z, ld* J0, ld* Yh0, ld* J1, ld* Yh1) {
+    const ld q = 0.25L * z * z;
+    ld t = 1, u = 1, Hm = 0, sJ0 = 1, sY0 = 0, sJ1 = 1, sY1 = 1;
+    for (int m = 1; m < 80; ++m) {
+        t *= -q / ((ld)m * m);
+        Hm += 1.0L / m;
+        sJ0 += t; sY0 += Hm * t;
+        u *= -q / ((ld)m * (m + 1));
+        sJ1 += u; sY1 += (2 * Hm + 1.0L / (m + 1)) * u;
+        if (fabsl(t) < 1e-30L && fabsl(u) < 1e-30L) break;
+    }
+    *J0 = sJ0;
+    *Yh0 = (2 / LD_PI) * (LD_GAMMA * sJ0 - sY0);
+    *J1 = 0.5L * z * sJ1;
+    *Yh1 = (2 / LD_PI) * LD_GAMMA * (*J1) - (z / (2 * LD_PI)) * sY1;
+}
+
+// J0, Y0, J1, Y1 by Miller's recurrence and Neumann's expansion (z > 4)
+static void host_miller(ld z, ld* J0, ld* Y0, ld* J1, ld* Y1) {
+    int nstart = 2 * (int)((z + 40 + 8 * cbrtl(z)) * 0.5L);
+    ld jp1 = 0, jn = 1e-40L, norm = 0, neu0 = 0, neu1 = 0, jodd = 0;
+    for (int n = nstart; n >= 1; --n) {
+        if ((n & 1) == 0) {
+            const int k = n >> 1;
+            norm += 2 * jn;
+            neu0 += ((k & 1) ? -1 : 1) * jn / k;
+            jodd = jp1;
+        } else {
+            const int k = (n + 1) >> 1;
+            neu1 += ((k & 1) ? -1 : 1) * (jn - jodd) / k;
+        }
+        const ld jm1 = (ld)n * (2 / z) * jn - jp1;
+        jp1 = jn; jn = jm1;
+        if (fabsl(jn) > 1e300L) { jn *= 1e-300L; jp1 *= 1e-300L; norm *= 1e-300L; neu0 *= 1e-300L; neu1 *= 1e-300L; jodd *= 1e-300L; }
+    }
+    norm += jn;
+    const ld s = 1 / norm, lg = logl(0.5L * z) + LD_GAMMA;
+    *J0 = jn * s; *J1 = jp1 * s;
+    *Y0 = (2 / LD_PI) * lg * (*J0) - (4 / LD_PI) * neu0 * s;
+    *Y1 = -(2 / LD_PI) * (*J0) / z + (2 / LD_PI) * lg * (*J1) + (2 / LD_PI) * neu1 * s;
+}
+
+// the four tabulated functions of interval i at z
+static void host_funcs(int i, ld z, ld f[4]) {
+    ld J0, Y0, J1, Y1;
+    if (z <= 4) {
+        ld Yh0, Yh1;
+        host_series(z, &J0, &Yh0, &J1, &Yh1);
+        if (i < BTAB_LOGSPLIT) { Y0 = Yh0; Y1 = Yh1; }
+        else {
+            const ld lg = (2 / LD_PI) * logl(0.5L * z);
+            Y0 = Yh0 + lg * J0;
+            Y1 = Yh1 + lg * J1 - 2 / (LD_PI * z);
+        }
+    } else {
+        host_miller(z, &J0, &Y0, &J1, &Y1);
+    }
+    f[0] = J0; f[1] = Y0; f[2] = J1; f[3] = Y1;
+}
+
+static void build_bessel_table(std::vector<double>& tab) {
+    const int n = BTAB_NC;
+    tab.assign((size_t)BTAB_NINT * 4 * n, 0.0);
+    std::vector<ld> tk((size_t)n * n);        // monomial coefficients of T_k
+    for (int k = 0; k < n; ++k) {
+        for (int j = 0; j < n; ++j) {
+            ld v = 0;
+            if (k == 0) v = (j == 0);
+            else if (k == 1) v = (j == 1);
+            else v = 2 * (j > 0 ? tk[(size_t)(k - 1) * n + j - 1] : 0) - tk[(size_t)(k - 2) * n + j];
+            tk[(size_t)k * n + j] = v;
+        }
+    }
+    for (int i = 0; i < BTAB_NINT; ++i) {
+        const ld zm = (i + 0.5L) * (ld)BTAB_W, hw = 0.5L * (ld)BTAB_W;
+        std::vector<ld> fv((size_t)4 * n);
+        for (int j = 0; j < n; ++j) {
+            const ld tj = cosl(LD_PI * (j + 0.5L) / n);
+            ld f[4];
+            host_funcs(i, zm + hw * tj, f);
+            for (int q = 0; q < 4; ++q) fv[(size_t)q * n + j] = f[q];
+        }
+        for (int q = 0; q < 4; ++q) {
+            std::vector<ld> a(n, 0), mono(n, 0);
+            for (int k = 0; k < n; ++k) {
+                ld sum = 0;
+                for (int j = 0; j < n; ++j) sum += fv[(size_t)q * n + j] * cosl(LD_PI * k * (j + 0.5L) / n);
+                a[k] = (k == 0 ? 1.0L : 2.0L) * sum / n;
+            }
+            for (int k = 0; k < n; ++k)
+                for (int j = 0; j < n; ++j) mono[j] += a[k] * tk[(size_t)k * n + j];
+            for (int j = 0; j < n; ++j) tab[((size_t)i * 4 + q) * n + j] = (double)mono[j];
+        }
+    }
+}
+
+static std::mutex g_btab_mutex;
+static double* g_btab[64] = {nullptr};
+
+static bem_status bessel_table(bem_ctx* h, const double** out) {
+    std::lock_guard<std::mutex> lk(g_btab_mutex);
+    if (h->device < 0 || h->device >= 64) return bem_fail(h, BEM_E_INVALID, "bad device");
+    if (!g_btab[h->device]) {
+        std::vector<double> tab;
+        build_bessel_table(tab);
+        double* d = nullptr;
+        BEM_CUDA(h, cudaMalloc((void**)&d, tab.size() * sizeof(double)));
+        BEM_CUDA(h, cudaMemcpy(d, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+        g_btab[h->device] = d;
+    }
+    *out = g_btab[h->device];
+    return BEM_OK;
+}
+
 struct AsmParams {
     int N;
     double k;
@@ -98,6 +224,7 @@ struct AsmParams {
     cplx *S, *W, *D;
     int64_t ld;
     int nT;
+    const double* btab;   // far-field Bessel table
     SeriesCoef sc;
 };
 
@@ -215,7 +342,8 @@ __device__ void pair_adjacent_fwd(const SegV& e, const SegV& f, const SeriesCoef
 
 // separated pair: q x q tensor Gauss-Legendre
 template <bool WD>
-__device__ void pair_gauss(int q, const SegV& e, const SegV& f, double k, cplx I[4], cplx J[4], cplx Jt[4]) {
+__device__ void pair_gauss(int q, const SegV& e, const SegV& f, double k, const double* __restrict__ btab,
+                           cplx I[4], cplx J[4], cplx Jt[4]) {
     const double* xs = c_glx + gl_off(q);
     const double* ws = c_glw + gl_off(q);
     const double nfx = f.ty, nfy = -f.tx, nex = e.ty, ney = -e.tx;
@@ -230,7 +358,7 @@ __device__ void pair_gauss(int q, const SegV& e, const SegV& f, double k, cplx I
             const double t = xs[j], w = wi * ws[j];
             const double dx = f.x0 + t * f.h * f.tx - px, dy = f.y0 + t * f.h * f.ty - py;
             const double r = sqrt(dx * dx + dy * dy);
-            const Bessel01 b = bessel01<WD>(k * r);
+            const Bessel01 b = bessel01_tab<WD>(btab, k * r);
             const double gr = -0.25 * b.Y0, gi = 0.25 * b.J0;
             const double w00 = w * (1 - s) * (1 - t), w01 = w * (1 - s) * t, w10 = w * s * (1 - t), w11 = w * s * t;
             a00.x += w00 * gr; a00.y += w00 * gi;
@@ -300,7 +428,7 @@ __device__ void pair_moments(int e, int f, const SegV& se, const SegV& sf, const
         const double hmax = fmax(se.h, sf.h);
         const double gap = fmax(sqrt(mx * mx + my * my) - 0.5 * (se.h + sf.h), 0.0);
         const int q = q_for_gap(gap / hmax, p.k * (gap + hmax));
-        pair_gauss<WD>(q, se, sf, p.k, I, J, Jt);
+        pair_gauss<WD>(q, se, sf, p.k, p.btab, I, J, Jt);
     }
 }
 
@@ -425,6 +553,8 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     p.D = (ops & BEM_OP_D) ? h->D : nullptr;
     p.ld = h->N;
     series_coefficients(h->k, 2.0 * h->hbar, &p.sc);
+    bem_status st = bessel_table(h, &p.btab);
+    if (st != BEM_OK) return st;
     if (ops & BEM_OP_D) return run_assemble<15, true>(h, p);
     return run_assemble<31, false>(h, p);
 }

@@ -142,3 +142,45 @@ __device__ __forceinline__ Bessel01 bessel01(double z) {
     }
     return b;
 }
+
+// ---------------------------------------------------------------------------------------
+// Table-driven evaluation for the far field.  On intervals of width BTAB_W in z the four
+// functions are degree-(BTAB_NC-1) polynomials in the local variable t = (z - z_mid)/(W/2),
+// fitted on the host (Chebyshev interpolation in long double, converted to monomials).
+// For z < 2 the logarithmic parts are removed so that the tabulated functions are entire:
+//   Yh0 = Y0 - (2/pi) ln(z/2) J0,   Yh1 = Y1 + 2/(pi z) - (2/pi) ln(z/2) J1;
+// for z >= 2 Y0 and Y1 are tabulated directly.  Beyond BTAB_ZMAX: bessel01().
+// Layout: tab[((i * 4) + f) * BTAB_NC + j], f = 0: J0, 1: Y0 or Yh0, 2: J1, 3: Y1 or Yh1.
+#define BTAB_W 0.25
+#define BTAB_NC 13
+#define BTAB_ZMAX 64.0
+#define BTAB_NINT 256
+#define BTAB_LOGSPLIT 8          // intervals below z = 2 carry the log-free functions
+
+__device__ __forceinline__ double btab_horner(const double* c, double t) {
+    double r = c[BTAB_NC - 1];
+#pragma unroll
+    for (int j = BTAB_NC - 2; j >= 0; --j) r = fma(r, t, c[j]);
+    return r;
+}
+
+template <bool WITH1>
+__device__ __forceinline__ Bessel01 bessel01_tab(const double* __restrict__ tab, double z) {
+    if (z >= BTAB_ZMAX) return bessel01<WITH1>(z);
+    Bessel01 b;
+    int i = (int)(z * (1.0 / BTAB_W));
+    const double t = (z - (i + 0.5) * BTAB_W) * (2.0 / BTAB_W);
+    const double* c = tab + (size_t)i * 4 * BTAB_NC;
+    b.J0 = btab_horner(c, t);
+    b.Y0 = btab_horner(c + BTAB_NC, t);
+    if (WITH1) {
+        b.J1 = btab_horner(c + 2 * BTAB_NC, t);
+        b.Y1 = btab_horner(c + 3 * BTAB_NC, t);
+    }
+    if (i < BTAB_LOGSPLIT) {
+        const double lg = (2.0 / BEM_PI) * log(0.5 * z);
+        b.Y0 = fma(lg, b.J0, b.Y0);
+        if (WITH1) b.Y1 = fma(lg, b.J1, b.Y1) - 2.0 / (BEM_PI * z);
+    }
+    return b;
+}

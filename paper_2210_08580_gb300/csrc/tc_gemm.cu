@@ -376,17 +376,21 @@ __global__ void k_exp_cols(const void* src, int is_real, int64_t K, int64_t m, i
     }
 }
 
-__device__ __forceinline__ void split_store(double x, int S, __nv_bfloat16* out, size_t slice_stride) {
-    // x in (-1, 1): slices a_s 2^{-7s} with a_s = rint(x 2^7), x <- x 2^7 - a_s
-    double sc = 1.0;
-#pragma unroll 1
-    for (int s = 0; s < S; ++s) {
-        const double y = x * 128.0;
-        const double a = rint(y);
-        out[s * slice_stride] = __float2bfloat16_rn((float)(a * sc));
-        x = y - a;
-        sc *= 0.0078125;
+// 2^p as a double from its exponent bits (p in the normal range)
+__device__ __forceinline__ double pow2i(int p) { return __longlong_as_double((long long)(1023 + p) << 52); }
+
+// val 2^-e in (-1, 1) -> S slices: X = round(val 2^{7S - e}) (exact scaling and one
+// rounding), then balanced base-128 digits from the least significant up: d in [-64, 63]
+// for s >= 1 and the leading |d_0| <= 128; slice s stores d_s 2^{-7s} (exact in bf16).
+__device__ __forceinline__ void split_store(double val, int e, int S, __nv_bfloat16* out, size_t slice_stride) {
+    long long X = __double2ll_rn(val * pow2i(7 * S - e));
+    for (int s = S - 1; s >= 1; --s) {
+        long long d = X & 127;
+        if (d >= 64) d -= 128;
+        X = (X - d) >> 7;
+        out[s * slice_stride] = __float2bfloat16_rn((float)d * __int_as_float((127 - 7 * s) << 23));
     }
+    out[0] = __float2bfloat16_rn((float)X);
 }
 
 // A' slices: out[s][i][kp], kp = 2k + c, padded with zeros to Kp
@@ -399,9 +403,9 @@ __global__ void k_slice_A(const double2* src, int64_t M, int64_t K, int64_t Kp, 
     const int64_t k = kp >> 1;
     if (k < K && !in_band(i, k, K, band)) {
         const double2 v = src[i * sa_i + k * sa_k];
-        x = ldexp((kp & 1) ? v.y : v.x, -e[i]);
+        x = (kp & 1) ? v.y : v.x;
     }
-    split_store(x, S, out + i * Kp + kp, (size_t)M * Kp);
+    split_store(x, e[i], S, out + i * Kp + kp, (size_t)M * Kp);
 }
 
 // B' slices stored K-major: out[s][jp][kp]
@@ -418,10 +422,9 @@ __global__ void k_slice_B(const void* src, int is_real, int64_t K, int64_t m, in
         else { const double2 v = ((const double2*)src)[k * sb_k + j * sb_j]; re = v.x; im = v.y; }
         const int c = (int)(kp & 1), d = (int)(jp & 1);
         // B'[2k, 2j] = Re, B'[2k+1, 2j] = -Im, B'[2k, 2j+1] = Im, B'[2k+1, 2j+1] = Re
-        const double val = (d == 0) ? (c == 0 ? re : -im) : (c == 0 ? im : re);
-        x = ldexp(val, -f[jp]);
+        x = (d == 0) ? (c == 0 ? re : -im) : (c == 0 ? im : re);
     }
-    split_store(x, S, out + jp * Kp + kp, (size_t)(2 * m) * Kp);
+    split_store(x, f[jp], S, out + jp * Kp + kp, (size_t)(2 * m) * Kp);
 }
 
 // ------------------------------------------------------------------------------ host side
@@ -638,6 +641,16 @@ bem_status tc_prepare_solve(bem_ctx* h) {
     // V^H as A (r x N): A_op[i, k] = Vh[i + k r];  U as A (N x r): A_op[i, k] = U[i + k N]
     if ((st = slice_A(h, t->opVh, h->Vh, r, N, 1, r)) != BEM_OK) return st;
     return slice_A(h, t->opU, h->U, N, r, 1, N);
+}
+
+bem_status tc_core_product(bem_ctx* h, cplx* Kt) {
+    TcState* t = tcs(h);
+    const int64_t N = h->N, r = h->r;
+    if (!t->opVh.slices) return bem_fail(h, BEM_E_INVALID, "tc_core_product: call tc_prepare_solve first");
+    // Kt = beta^-1 V^H U: A = V^H (sliced), B = U (N x r, column-major)
+    bem_status st = slice_B(h, t->bbuf, h->U, 0, N, r, 1, N);
+    if (st != BEM_OK) return st;
+    return tc_gemm(h, t->opVh, t->bbuf, Kt, r, 0, 1.0 / h->beta, 0.0, "tc_factor_VhU");
 }
 
 // x = v/beta - beta^-2 U Kinv V^H v with tensor-core products (T, T2: r x nrhs scratch)

@@ -13,6 +13,8 @@ bem_status tc_product_left(bem_ctx* h, int op, const double* Qreal, const cplx* 
 bem_status tc_product_right(bem_ctx* h, int op, const cplx* y, int64_t ldy, int64_t nrhs, cplx* out, int64_t ld);
 // Slices U and V^H for the Woodbury products (after factor).
 bem_status tc_prepare_solve(bem_ctx* h);
+// Kt = beta^-1 V^H U (r x r, ld r) as a split-bf16 product (after tc_prepare_solve).
+bem_status tc_core_product(bem_ctx* h, cplx* Kt);
 // Woodbury solve with split-bf16 products and FP64 residual refinement.
 bem_status tc_solve_refined(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x, int64_t ldx, int64_t nrhs,
                             int32_t* iters, double* max_rel_resid);
