@@ -102,24 +102,6 @@ typedef long double ld;
 static const ld LD_PI = 3.141592653589793238462643383279502884L;
 static const ld LD_GAMMA = 0.577215664901532860606512090082402431L;
 
-// J0, J1 and the log-free parts Yh0, Yh1 by the ascending series (z <= 4)
-static void host_series(ld z, ld* J0, ld* Yh0, ld* J1, ld* Yh1) {
-    const ld q = 0.25L * z * z;
-    ld t = 1, u = 1, Hm = 0, sJ0 = 1, sY0 = 0, sJ1 = 1, sY1 = 1;
-    for (int m = 1; m < 80; ++m) {
-        t *= -q / ((ld)m * m);
-        Hm += 1.0L / m;
-        sJ0 += t; sY0 += Hm * t;
-        u *= -q / ((ld)m * (m + 1));
-        sJ1 += u; sY1 += (2 * Hm + 1.0L / (m + 1)) * u;
-        if (fabsl(t) < 1e-30L && fabsl(u) < 1e-30L) break;
-    }
-    *J0 = sJ0;
-    *Yh0 = (2 / LD_PI) * (LD_GAMMA * sJ0 - sY0);
-    *J1 = 0.5L * z * sJ1;
-    *Yh1 = (2 / LD_PI) * LD_GAMMA * (*J1) - (z / (2 * LD_PI)) * sY1;
-}
-
 // J0, Y0, J1, Y1 by Miller's recurrence and Neumann's expansion (z > 4)
 static void host_miller(ld z, ld* J0, ld* Y0, ld* J1, ld* Y1) {
     int nstart = 2 * (int)((z + 40 + 8 * cbrtl(z)) * 0.5L);
@@ -145,27 +127,38 @@ static void host_miller(ld z, ld* J0, ld* Y0, ld* J1, ld* Y1) {
     *Y1 = -(2 / LD_PI) * (*J0) / z + (2 / LD_PI) * lg * (*J1) + (2 / LD_PI) * neu1 * s;
 }
 
-// the four tabulated functions of interval i at z
+// the four tabulated functions of interval i at z (see bessel.cuh)
 static void host_funcs(int i, ld z, ld f[4]) {
-    ld J0, Y0, J1, Y1;
     if (z <= 4) {
-        ld Yh0, Yh1;
-        host_series(z, &J0, &Yh0, &J1, &Yh1);
-        if (i < BTAB_LOGSPLIT) { Y0 = Yh0; Y1 = Yh1; }
-        else {
+        // series: J1/z and Yh1/z without dividing by z
+        const ld q = 0.25L * z * z;
+        ld t = 1, uu = 1, Hm = 0, sJ0 = 1, sY0 = 0, sJ1 = 1, sY1 = 1;
+        for (int m = 1; m < 80; ++m) {
+            t *= -q / ((ld)m * m);
+            Hm += 1.0L / m;
+            sJ0 += t; sY0 += Hm * t;
+            uu *= -q / ((ld)m * (m + 1));
+            sJ1 += uu; sY1 += (2 * Hm + 1.0L / (m + 1)) * uu;
+            if (fabsl(t) < 1e-30L && fabsl(uu) < 1e-30L) break;
+        }
+        const ld J0 = sJ0, Yh0 = (2 / LD_PI) * (LD_GAMMA * sJ0 - sY0);
+        const ld J1z = 0.5L * sJ1, Yh1z = (2 / LD_PI) * LD_GAMMA * J1z - sY1 / (2 * LD_PI);
+        if (i < BTAB_LOGSPLIT) {
+            f[0] = J0; f[1] = Yh0; f[2] = J1z; f[3] = Yh1z;
+        } else {
             const ld lg = (2 / LD_PI) * logl(0.5L * z);
-            Y0 = Yh0 + lg * J0;
-            Y1 = Yh1 + lg * J1 - 2 / (LD_PI * z);
+            f[0] = J0; f[1] = Yh0 + lg * J0; f[2] = J1z; f[3] = Yh1z + lg * J1z - 2 / (LD_PI * z * z);
         }
     } else {
+        ld J0, Y0, J1, Y1;
         host_miller(z, &J0, &Y0, &J1, &Y1);
+        f[0] = J0; f[1] = Y0; f[2] = J1 / z; f[3] = Y1 / z;
     }
-    f[0] = J0; f[1] = Y0; f[2] = J1; f[3] = Y1;
 }
 
 static void build_bessel_table(std::vector<double>& tab) {
     const int n = BTAB_NC;
-    tab.assign((size_t)BTAB_NINT * 4 * n, 0.0);
+    tab.assign((size_t)BTAB_NINT * BTAB_STRIDE, 0.0);
     std::vector<ld> tk((size_t)n * n);        // monomial coefficients of T_k
     for (int k = 0; k < n; ++k) {
         for (int j = 0; j < n; ++j) {
@@ -177,12 +170,17 @@ static void build_bessel_table(std::vector<double>& tab) {
         }
     }
     for (int i = 0; i < BTAB_NINT; ++i) {
-        const ld zm = (i + 0.5L) * (ld)BTAB_W, hw = 0.5L * (ld)BTAB_W;
+        // u-interval of z in [i W, (i+1) W], widened by 1e-6 in z on both sides
+        const ld za = (ld)i * (ld)BTAB_W - 1e-6L, zb = (ld)(i + 1) * (ld)BTAB_W + 1e-6L;
+        const ld ua = (za > 0 ? za * za : 0.0L), ub = zb * zb;
+        const ld um = 0.5L * (ua + ub), uh = 0.5L * (ub - ua);
+        tab[(size_t)i * BTAB_STRIDE] = (double)um;
+        tab[(size_t)i * BTAB_STRIDE + 1] = (double)(1.0L / uh);
         std::vector<ld> fv((size_t)4 * n);
         for (int j = 0; j < n; ++j) {
             const ld tj = cosl(LD_PI * (j + 0.5L) / n);
             ld f[4];
-            host_funcs(i, zm + hw * tj, f);
+            host_funcs(i, sqrtl(um + uh * tj), f);
             for (int q = 0; q < 4; ++q) fv[(size_t)q * n + j] = f[q];
         }
         for (int q = 0; q < 4; ++q) {
@@ -194,7 +192,7 @@ static void build_bessel_table(std::vector<double>& tab) {
             }
             for (int k = 0; k < n; ++k)
                 for (int j = 0; j < n; ++j) mono[j] += a[k] * tk[(size_t)k * n + j];
-            for (int j = 0; j < n; ++j) tab[((size_t)i * 4 + q) * n + j] = (double)mono[j];
+            for (int j = 0; j < n; ++j) tab[(size_t)i * BTAB_STRIDE + 2 + (size_t)q * n + j] = (double)mono[j];
         }
     }
 }
@@ -350,25 +348,29 @@ __device__ void pair_gauss(int q, const SegV& e, const SegV& f, double k, const 
     cplx a00 = cmk(0, 0), a01 = cmk(0, 0), a10 = cmk(0, 0), a11 = cmk(0, 0);
     cplx d00 = cmk(0, 0), d01 = cmk(0, 0), d10 = cmk(0, 0), d11 = cmk(0, 0);
     cplx t00 = cmk(0, 0), t01 = cmk(0, 0), t10 = cmk(0, 0), t11 = cmk(0, 0);
-    const double kq = 0.25 * k;
+    const double k2 = k * k, k2q = 0.25 * k2;
+    // y - x = (f.x0 - e.x0) + t h_f t_f - s h_e t_e
+    const double bx = f.x0 - e.x0, by = f.y0 - e.y0;
+    const double ux = e.h * e.tx, uy = e.h * e.ty, vx = f.h * f.tx, vy = f.h * f.ty;
     for (int i = 0; i < q; ++i) {
-        const double s = xs[i], wi = ws[i];
-        const double px = e.x0 + s * e.h * e.tx, py = e.y0 + s * e.h * e.ty;
+        const double s = xs[i];
+        const double ws0 = ws[i] * (1.0 - s), ws1 = ws[i] * s;
+        const double cx = bx - s * ux, cy = by - s * uy;
         for (int j = 0; j < q; ++j) {
-            const double t = xs[j], w = wi * ws[j];
-            const double dx = f.x0 + t * f.h * f.tx - px, dy = f.y0 + t * f.h * f.ty - py;
-            const double r = sqrt(dx * dx + dy * dy);
-            const Bessel01 b = bessel01_tab<WD>(btab, k * r);
+            const double t = xs[j];
+            const double wt0 = ws[j] * (1.0 - t), wt1 = ws[j] * t;
+            const double dx = fma(t, vx, cx), dy = fma(t, vy, cy);
+            const double r2 = fma(dx, dx, dy * dy);
+            const BesselU b = bessel_u<WD>(btab, k2 * r2);
             const double gr = -0.25 * b.Y0, gi = 0.25 * b.J0;
-            const double w00 = w * (1 - s) * (1 - t), w01 = w * (1 - s) * t, w10 = w * s * (1 - t), w11 = w * s * t;
-            a00.x += w00 * gr; a00.y += w00 * gi;
-            a01.x += w01 * gr; a01.y += w01 * gi;
-            a10.x += w10 * gr; a10.y += w10 * gi;
-            a11.x += w11 * gr; a11.y += w11 * gi;
+            const double w00 = ws0 * wt0, w01 = ws0 * wt1, w10 = ws1 * wt0, w11 = ws1 * wt1;
+            a00.x = fma(w00, gr, a00.x); a00.y = fma(w00, gi, a00.y);
+            a01.x = fma(w01, gr, a01.x); a01.y = fma(w01, gi, a01.y);
+            a10.x = fma(w10, gr, a10.x); a10.y = fma(w10, gi, a10.y);
+            a11.x = fma(w11, gr, a11.x); a11.y = fma(w11, gi, a11.y);
             if (WD) {
-                // -(i k/4) H1 / r = (k/4)(Y1 - i J1) / r
-                const double ir = 1.0 / r;
-                const double fr = kq * b.Y1 * ir, fi = -kq * b.J1 * ir;
+                // -(i k/4) H1(k r) / r = (k^2/4) (Y1/z - i J1/z)
+                const double fr = k2q * b.Y1z, fi = -k2q * b.J1z;
                 const double dnf = dx * nfx + dy * nfy, dne = -(dx * nex + dy * ney);
                 d00.x += w00 * dnf * fr; d00.y += w00 * dnf * fi;
                 d01.x += w01 * dnf * fr; d01.y += w01 * dnf * fi;
@@ -392,11 +394,11 @@ __device__ void pair_gauss(int q, const SegV& e, const SegV& f, double k, const 
 // Gauss order for a separated pair: Bernstein-ellipse bound rho^{-2q} exp(k Im r) <= 1e-15
 // with rho = a + sqrt(a^2 - 1), a = 1 + 2 gap/h (log singularity at the gap beyond the end
 // of the segment) and Im r up to about gap + h on that ellipse (the Hankel kernel grows
-// like exp(k Im r) off the real axis).
-__device__ __forceinline__ int q_for_gap(double ratio, double kgap) {
-    const double a = 1.0 + 2.0 * fmax(ratio, 1e-3);
-    const double rho = a + sqrt(a * a - 1.0);
-    const int q = (int)ceil((34.54 + kgap) / (2.0 * log(rho)));
+// like exp(k Im r) off the real axis).  Only a threshold, so single precision suffices.
+__device__ __forceinline__ int q_for_gap(float ratio, float kgap) {
+    const float a = 1.0f + 2.0f * fmaxf(ratio, 1e-3f);
+    const float rho = a + sqrtf(a * a - 1.0f);
+    const int q = (int)ceilf((34.54f + kgap) / (2.0f * __logf(rho)) + 1e-3f);
     return min(16, max(2, q));
 }
 
@@ -423,25 +425,42 @@ __device__ void pair_moments(int e, int f, const SegV& se, const SegV& sf, const
             }
         }
     } else {
-        const double mx = se.x0 + 0.5 * se.h * se.tx - sf.x0 - 0.5 * sf.h * sf.tx;
-        const double my = se.y0 + 0.5 * se.h * se.ty - sf.y0 - 0.5 * sf.h * sf.ty;
-        const double hmax = fmax(se.h, sf.h);
-        const double gap = fmax(sqrt(mx * mx + my * my) - 0.5 * (se.h + sf.h), 0.0);
-        const int q = q_for_gap(gap / hmax, p.k * (gap + hmax));
+        const float mx = (float)(se.x0 - sf.x0) + 0.5f * (float)(se.h * se.tx - sf.h * sf.tx);
+        const float my = (float)(se.y0 - sf.y0) + 0.5f * (float)(se.h * se.ty - sf.h * sf.ty);
+        const float hmax = (float)fmax(se.h, sf.h);
+        const float gap = fmaxf(sqrtf(mx * mx + my * my) - 0.5f * (float)(se.h + sf.h), 0.0f);
+        const int q = q_for_gap(gap / hmax, (float)p.k * (gap + hmax));
         pair_gauss<WD>(q, se, sf, p.k, p.btab, I, J, Jt);
     }
 }
 
+// Tiles of the upper triangle, ordered by distance from the diagonal (the expensive tiles,
+// which hold the singular and near pairs, start first): linear index L -> (ti, tj).
+__device__ __forceinline__ void tile_of(int L, int nT, int& ti, int& tj) {
+    // start(d) = d nT - d (d - 1)/2 tiles precede diagonal d
+    int lo = 0, hi = nT - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const long long st = (long long)mid * nT - (long long)mid * (mid - 1) / 2;
+        if (st <= L) lo = mid; else hi = mid - 1;
+    }
+    const int d = lo;
+    ti = L - (int)((long long)d * nT - (long long)d * (d - 1) / 2);
+    tj = ti + d;
+}
+
 template <int T, bool WD>
 __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
-    const int ti = blockIdx.y, tj = blockIdx.x;
-    if (tj < ti) return;
+    int ti, tj;
+    tile_of((int)blockIdx.x, p.nT, ti, tj);
     constexpr int TP = T + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx* sI = reinterpret_cast<cplx*>(smem_raw);                 // TP*TP*4
-    cplx* sJ = sI + TP * TP * 4;                                    // (WD)
+    cplx* sM = sI + TP * TP * 4;                                    // TP*TP: sum_ab I / (h_e h_f)
+    cplx* sJ = sM + TP * TP;                                        // (WD)
     cplx* sJt = sJ + (WD ? TP * TP * 4 : 0);
-    double* sgE = reinterpret_cast<double*>(sJt + (WD ? TP * TP * 4 : 0));   // 5*TP
+    double* sND = reinterpret_cast<double*>(sJt + (WD ? TP * TP * 4 : 0));   // TP*TP: k^2 nu_e.nu_f
+    double* sgE = sND + TP * TP;                                    // 5*TP
     double* sgF = sgE + 5 * TP;
     const int N = p.N;
     const int i0 = ti * T, j0 = tj * T;
@@ -452,6 +471,7 @@ __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
         sgF[t] = b.x0; sgF[TP + t] = b.y0; sgF[2 * TP + t] = b.tx; sgF[3 * TP + t] = b.ty; sgF[4 * TP + t] = b.h;
     }
     __syncthreads();
+    const double k2 = p.k * p.k;
     for (int pi = threadIdx.x; pi < TP * TP; pi += blockDim.x) {
         const int el = pi / TP, fl = pi % TP;
         // skip segment pairs touching only rows/cols beyond N
@@ -465,9 +485,13 @@ __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
             sI[pi * 4 + q] = I[q];
             if (WD) { sJ[pi * 4 + q] = J[q]; sJt[pi * 4 + q] = Jt[q]; }
         }
+        // per-pair terms of N's Maue form: sum_ab I / (h_e h_f) and k^2 nu_e . nu_f
+        const double ihh = 1.0 / (se.h * sf.h);
+        const cplx M0 = cadd(cadd(I[0], I[1]), cadd(I[2], I[3]));
+        sM[pi] = cscale(M0, ihh);
+        sND[pi] = k2 * (se.ty * sf.ty + se.tx * sf.tx);   // nu = (t_y, -t_x): nu_e . nu_f = t_e . t_f
     }
     __syncthreads();
-    const double k2 = p.k * p.k;
     const bool mirror = (ti != tj);
     for (int pass = 0; pass < (mirror ? 2 : 1); ++pass) {
         for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
@@ -476,25 +500,21 @@ __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
             const int i = i0 + il, j = j0 + jl;
             if (i >= N || j >= N) continue;
             cplx s = cmk(0, 0), w = cmk(0, 0), dd = cmk(0, 0);
+#pragma unroll
             for (int a = 0; a < 2; ++a) {
                 const int el = il + 1 - a;
-                const double hex = sgE[4 * TP + el];
-                const double nex = sgE[3 * TP + el], ney = -sgE[2 * TP + el];
+#pragma unroll
                 for (int b = 0; b < 2; ++b) {
                     const int fl = jl + 1 - b;
                     const int pi = el * TP + fl;
-                    const cplx* Ip = sI + pi * 4;
-                    const cplx Iab = Ip[a * 2 + b];
+                    const cplx Iab = sI[pi * 4 + a * 2 + b];
                     s = cadd(s, Iab);
                     if (p.W) {
-                        const double hf = sgF[4 * TP + fl];
-                        const double nfx = sgF[3 * TP + fl], nfy = -sgF[2 * TP + fl];
-                        const double sig = (a == b) ? 1.0 : -1.0;
-                        const double inv = sig / (hex * hf);
-                        const cplx M0 = cadd(cadd(Ip[0], Ip[1]), cadd(Ip[2], Ip[3]));
-                        const double nd = k2 * (nex * nfx + ney * nfy);
-                        w.x += inv * M0.x - nd * Iab.x;
-                        w.y += inv * M0.y - nd * Iab.y;
+                        // sigma_a sigma_b sum I/(h_e h_f) - k^2 (nu_e . nu_f) I_ab
+                        const cplx M0 = sM[pi];
+                        const double nd = sND[pi];
+                        if (a == b) { w.x += M0.x - nd * Iab.x; w.y += M0.y - nd * Iab.y; }
+                        else { w.x += -M0.x - nd * Iab.x; w.y += -M0.y - nd * Iab.y; }
                     }
                     if (WD) dd = cadd(dd, (pass == 0 ? sJ : sJt)[pi * 4 + a * 2 + b]);
                 }
@@ -534,10 +554,11 @@ bem_status launch_geometry(bem_ctx* h, const double* verts, int64_t N, double* s
 template <int T, bool WD>
 static bem_status run_assemble(bem_ctx* h, AsmParams& p) {
     constexpr int TP = T + 1;
-    const size_t smem = (size_t)TP * TP * 4 * sizeof(cplx) * (WD ? 3 : 1) + 10 * TP * sizeof(double);
+    const size_t smem = (size_t)TP * TP * 4 * sizeof(cplx) * (WD ? 3 : 1) + (size_t)TP * TP * (sizeof(cplx) + sizeof(double)) +
+                        10 * TP * sizeof(double);
     BEM_CUDA(h, cudaFuncSetAttribute(k_assemble<T, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     p.nT = (p.N + T - 1) / T;
-    dim3 grid(p.nT, p.nT);
+    const unsigned grid = (unsigned)((int64_t)p.nT * (p.nT + 1) / 2);
     BEM_TIMED(h, "k_assemble", (k_assemble<T, WD><<<grid, 256, smem, h->stream>>>(p)));
     BEM_LAUNCH(h, "k_assemble");
     return BEM_OK;

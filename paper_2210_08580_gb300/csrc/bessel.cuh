@@ -144,18 +144,24 @@ __device__ __forceinline__ Bessel01 bessel01(double z) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Table-driven evaluation for the far field.  On intervals of width BTAB_W in z the four
-// functions are degree-(BTAB_NC-1) polynomials in the local variable t = (z - z_mid)/(W/2),
-// fitted on the host (Chebyshev interpolation in long double, converted to monomials).
-// For z < 2 the logarithmic parts are removed so that the tabulated functions are entire:
-//   Yh0 = Y0 - (2/pi) ln(z/2) J0,   Yh1 = Y1 + 2/(pi z) - (2/pi) ln(z/2) J1;
-// for z >= 2 Y0 and Y1 are tabulated directly.  Beyond BTAB_ZMAX: bessel01().
-// Layout: tab[((i * 4) + f) * BTAB_NC + j], f = 0: J0, 1: Y0 or Yh0, 2: J1, 3: Y1 or Yh1.
+// Table-driven evaluation for the far field, as polynomials in u = z^2 (no square root).
+// Intervals are uniform in z (width BTAB_W); on interval i the tabulated functions are
+// degree-(BTAB_NC-1) polynomials in t = (u - u_mid) / u_half over [z_i^2, z_{i+1}^2]
+// (slightly widened), fitted on the host (Chebyshev interpolation in long double,
+// converted to monomials):
+//   f0 = J0,  f1 = Y0,  f2 = J1/z,  f3 = Y1/z         for z >= 4,
+//   f0 = J0,  f1 = Yh0, f2 = J1/z,  f3 = Yh1/z        for z < 4, with the entire parts
+//   Yh0 = Y0 - (2/pi) ln(z/2) J0,  Yh1 = Y1 + 2/(pi z) - (2/pi) ln(z/2) J1.
+// Per interval: [u_mid, 1/u_half, f0[NC], f1[NC], f2[NC], f3[NC]].  Beyond BTAB_ZMAX the
+// series/recurrence/asymptotic routines above are used.
 #define BTAB_W 0.25
-#define BTAB_NC 13
+#define BTAB_NC 11
 #define BTAB_ZMAX 64.0
 #define BTAB_NINT 256
-#define BTAB_LOGSPLIT 8          // intervals below z = 2 carry the log-free functions
+#define BTAB_LOGSPLIT 16          // intervals below z = 4 carry the log-free functions
+#define BTAB_STRIDE (2 + 4 * BTAB_NC)
+
+struct BesselU { double J0, Y0, J1z, Y1z; };   // J1z = J1(z)/z, Y1z = Y1(z)/z
 
 __device__ __forceinline__ double btab_horner(const double* c, double t) {
     double r = c[BTAB_NC - 1];
@@ -165,22 +171,29 @@ __device__ __forceinline__ double btab_horner(const double* c, double t) {
 }
 
 template <bool WITH1>
-__device__ __forceinline__ Bessel01 bessel01_tab(const double* __restrict__ tab, double z) {
-    if (z >= BTAB_ZMAX) return bessel01<WITH1>(z);
-    Bessel01 b;
-    int i = (int)(z * (1.0 / BTAB_W));
-    const double t = (z - (i + 0.5) * BTAB_W) * (2.0 / BTAB_W);
-    const double* c = tab + (size_t)i * 4 * BTAB_NC;
-    b.J0 = btab_horner(c, t);
-    b.Y0 = btab_horner(c + BTAB_NC, t);
+__device__ __forceinline__ BesselU bessel_u(const double* __restrict__ tab, double u) {
+    BesselU b;
+    const float zf = sqrtf((float)u);
+    if (zf >= (float)BTAB_ZMAX) {
+        const double z = sqrt(u);
+        const Bessel01 c = bessel01<WITH1>(z);
+        b.J0 = c.J0; b.Y0 = c.Y0;
+        if (WITH1) { b.J1z = c.J1 / z; b.Y1z = c.Y1 / z; }
+        return b;
+    }
+    const int i = min((int)(zf * (float)(1.0 / BTAB_W)), BTAB_NINT - 1);
+    const double* c = tab + (size_t)i * BTAB_STRIDE;
+    const double t = (u - c[0]) * c[1];
+    b.J0 = btab_horner(c + 2, t);
+    b.Y0 = btab_horner(c + 2 + BTAB_NC, t);
     if (WITH1) {
-        b.J1 = btab_horner(c + 2 * BTAB_NC, t);
-        b.Y1 = btab_horner(c + 3 * BTAB_NC, t);
+        b.J1z = btab_horner(c + 2 + 2 * BTAB_NC, t);
+        b.Y1z = btab_horner(c + 2 + 3 * BTAB_NC, t);
     }
     if (i < BTAB_LOGSPLIT) {
-        const double lg = (2.0 / BEM_PI) * log(0.5 * z);
+        const double lg = (1.0 / BEM_PI) * log(0.25 * u);       // (2/pi) ln(z/2)
         b.Y0 = fma(lg, b.J0, b.Y0);
-        if (WITH1) b.Y1 = fma(lg, b.J1, b.Y1) - 2.0 / (BEM_PI * z);
+        if (WITH1) b.Y1z = fma(lg, b.J1z, b.Y1z) - (2.0 / BEM_PI) / u;
     }
     return b;
 }
