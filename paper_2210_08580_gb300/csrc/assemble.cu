@@ -127,10 +127,10 @@ static void host_miller(ld z, ld* J0, ld* Y0, ld* J1, ld* Y1) {
     *Y1 = -(2 / LD_PI) * (*J0) / z + (2 / LD_PI) * lg * (*J1) + (2 / LD_PI) * neu1 * s;
 }
 
-// the four tabulated functions of interval i at z (see bessel.cuh)
-static void host_funcs(int i, ld z, ld f[4]) {
+// the four tabulated functions at z (see bessel.cuh): J0, Y0, J1/z, Y1/z + 2/(pi z^2)
+static void host_funcs(ld z, ld f[4]) {
     if (z <= 4) {
-        // series: J1/z and Yh1/z without dividing by z
+        // ascending series: J1/z and the log-free parts without dividing by z
         const ld q = 0.25L * z * z;
         ld t = 1, uu = 1, Hm = 0, sJ0 = 1, sY0 = 0, sJ1 = 1, sY1 = 1;
         for (int m = 1; m < 80; ++m) {
@@ -141,18 +141,14 @@ static void host_funcs(int i, ld z, ld f[4]) {
             sJ1 += uu; sY1 += (2 * Hm + 1.0L / (m + 1)) * uu;
             if (fabsl(t) < 1e-30L && fabsl(uu) < 1e-30L) break;
         }
+        const ld lg = (2 / LD_PI) * logl(0.5L * z);
         const ld J0 = sJ0, Yh0 = (2 / LD_PI) * (LD_GAMMA * sJ0 - sY0);
         const ld J1z = 0.5L * sJ1, Yh1z = (2 / LD_PI) * LD_GAMMA * J1z - sY1 / (2 * LD_PI);
-        if (i < BTAB_LOGSPLIT) {
-            f[0] = J0; f[1] = Yh0; f[2] = J1z; f[3] = Yh1z;
-        } else {
-            const ld lg = (2 / LD_PI) * logl(0.5L * z);
-            f[0] = J0; f[1] = Yh0 + lg * J0; f[2] = J1z; f[3] = Yh1z + lg * J1z - 2 / (LD_PI * z * z);
-        }
+        f[0] = J0; f[1] = Yh0 + lg * J0; f[2] = J1z; f[3] = Yh1z + lg * J1z;
     } else {
         ld J0, Y0, J1, Y1;
         host_miller(z, &J0, &Y0, &J1, &Y1);
-        f[0] = J0; f[1] = Y0; f[2] = J1 / z; f[3] = Y1 / z;
+        f[0] = J0; f[1] = Y0; f[2] = J1 / z; f[3] = Y1 / z + 2 / (LD_PI * z * z);
     }
 }
 
@@ -170,9 +166,18 @@ static void build_bessel_table(std::vector<double>& tab) {
         }
     }
     for (int i = 0; i < BTAB_NINT; ++i) {
-        // u-interval of z in [i W, (i+1) W], widened by 1e-6 in z on both sides
-        const ld za = (ld)i * (ld)BTAB_W - 1e-6L, zb = (ld)(i + 1) * (ld)BTAB_W + 1e-6L;
-        const ld ua = (za > 0 ? za * za : 0.0L), ub = zb * zb;
+        ld za, zb;
+        if (i < BTAB_NLOG) {
+            const int m = BTAB_LOG_EMIN + i / 8, j = i % 8;
+            za = ldexpl(1.0L + j / 8.0L, m);
+            zb = ldexpl(1.0L + (j + 1) / 8.0L, m);
+        } else {
+            za = (ld)BTAB_ZLIN + (i - BTAB_NLOG) * (ld)BTAB_W;
+            zb = za + (ld)BTAB_W;
+        }
+        za *= 1 - 1e-6L;
+        zb *= 1 + 1e-6L;
+        const ld ua = za * za, ub = zb * zb;
         const ld um = 0.5L * (ua + ub), uh = 0.5L * (ub - ua);
         tab[(size_t)i * BTAB_STRIDE] = (double)um;
         tab[(size_t)i * BTAB_STRIDE + 1] = (double)(1.0L / uh);
@@ -180,7 +185,7 @@ static void build_bessel_table(std::vector<double>& tab) {
         for (int j = 0; j < n; ++j) {
             const ld tj = cosl(LD_PI * (j + 0.5L) / n);
             ld f[4];
-            host_funcs(i, sqrtl(um + uh * tj), f);
+            host_funcs(sqrtl(um + uh * tj), f);
             for (int q = 0; q < 4; ++q) fv[(size_t)q * n + j] = f[q];
         }
         for (int q = 0; q < 4; ++q) {

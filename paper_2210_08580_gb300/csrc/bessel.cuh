@@ -144,21 +144,26 @@ __device__ __forceinline__ Bessel01 bessel01(double z) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Table-driven evaluation for the far field, as polynomials in u = z^2 (no square root).
-// Intervals are uniform in z (width BTAB_W); on interval i the tabulated functions are
-// degree-(BTAB_NC-1) polynomials in t = (u - u_mid) / u_half over [z_i^2, z_{i+1}^2]
-// (slightly widened), fitted on the host (Chebyshev interpolation in long double,
-// converted to monomials):
-//   f0 = J0,  f1 = Y0,  f2 = J1/z,  f3 = Y1/z         for z >= 4,
-//   f0 = J0,  f1 = Yh0, f2 = J1/z,  f3 = Yh1/z        for z < 4, with the entire parts
-//   Yh0 = Y0 - (2/pi) ln(z/2) J0,  Yh1 = Y1 + 2/(pi z) - (2/pi) ln(z/2) J1.
-// Per interval: [u_mid, 1/u_half, f0[NC], f1[NC], f2[NC], f3[NC]].  Beyond BTAB_ZMAX the
-// series/recurrence/asymptotic routines above are used.
-#define BTAB_W 0.25
+// Table-driven evaluation for the far field, as polynomials in u = z^2: no square root, no
+// logarithm and (for S, N) no division on the hot path.  Intervals in z:
+//   [2^-10, 4): 8 per octave, [2^m (1 + j/8), 2^m (1 + (j+1)/8)] -- every interval lies at
+//               least 17 half-widths from the z = 0 singularity, so Y0 is tabulated
+//               directly;
+//   [4, 64):    uniform width 1/4 (the oscillation scale is 2 pi).
+// On each interval four functions are degree-(BTAB_NC-1) polynomials in
+// t = (u - u_mid)/u_half over [z_a^2, z_b^2] (widened by 1e-6 relative), fitted on the
+// host (Chebyshev interpolation in long double, converted to monomials):
+//   f0 = J0,  f1 = Y0,  f2 = J1/z,  f3 = Y1/z + 2/(pi z^2)   (pole removed).
+// Per interval: [u_mid, 1/u_half, f0[NC], f1[NC], f2[NC], f3[NC]].  Outside [2^-10, 64)
+// the series/recurrence/asymptotic routines above are used.
 #define BTAB_NC 11
+#define BTAB_LOG_OCT 12            // octaves 2^-10 .. 2^2
+#define BTAB_LOG_EMIN (-10)
+#define BTAB_NLOG (8 * BTAB_LOG_OCT)
+#define BTAB_W 0.25
+#define BTAB_ZLIN 4.0
 #define BTAB_ZMAX 64.0
-#define BTAB_NINT 256
-#define BTAB_LOGSPLIT 16          // intervals below z = 4 carry the log-free functions
+#define BTAB_NINT (BTAB_NLOG + 240)
 #define BTAB_STRIDE (2 + 4 * BTAB_NC)
 
 struct BesselU { double J0, Y0, J1z, Y1z; };   // J1z = J1(z)/z, Y1z = Y1(z)/z
@@ -174,26 +179,31 @@ template <bool WITH1>
 __device__ __forceinline__ BesselU bessel_u(const double* __restrict__ tab, double u) {
     BesselU b;
     const float zf = sqrtf((float)u);
-    if (zf >= (float)BTAB_ZMAX) {
+    int i;
+    if (zf < (float)BTAB_ZLIN) {
+        const int bits = __float_as_int(zf);
+        i = (((bits >> 23) & 255) - 127 - BTAB_LOG_EMIN) * 8 + ((bits >> 20) & 7);
+    } else {
+        i = BTAB_NLOG + (int)((zf - (float)BTAB_ZLIN) * (float)(1.0 / BTAB_W));
+    }
+    if (i < 0 || i >= BTAB_NINT) {
         const double z = sqrt(u);
         const Bessel01 c = bessel01<WITH1>(z);
         b.J0 = c.J0; b.Y0 = c.Y0;
         if (WITH1) { b.J1z = c.J1 / z; b.Y1z = c.Y1 / z; }
         return b;
     }
-    const int i = min((int)(zf * (float)(1.0 / BTAB_W)), BTAB_NINT - 1);
     const double* c = tab + (size_t)i * BTAB_STRIDE;
     const double t = (u - c[0]) * c[1];
     b.J0 = btab_horner(c + 2, t);
     b.Y0 = btab_horner(c + 2 + BTAB_NC, t);
     if (WITH1) {
         b.J1z = btab_horner(c + 2 + 2 * BTAB_NC, t);
-        b.Y1z = btab_horner(c + 2 + 3 * BTAB_NC, t);
-    }
-    if (i < BTAB_LOGSPLIT) {
-        const double lg = (1.0 / BEM_PI) * log(0.25 * u);       // (2/pi) ln(z/2)
-        b.Y0 = fma(lg, b.J0, b.Y0);
-        if (WITH1) b.Y1z = fma(lg, b.J1z, b.Y1z) - (2.0 / BEM_PI) / u;
+        // 1/u from a single-precision seed and two Newton steps
+        double ru = (double)__frcp_rn((float)u);
+        ru = ru * fma(-u, ru, 2.0);
+        ru = ru * fma(-u, ru, 2.0);
+        b.Y1z = btab_horner(c + 2 + 3 * BTAB_NC, t) - (2.0 / BEM_PI) * ru;
     }
     return b;
 }
