@@ -325,9 +325,14 @@ bem_status compress_compact(bem_handle h, double rel_tol, int64_t* rank_out) {
     if ((st = ensure_alloc(h, (void**)&h->Vh, sizeof(cplx) * r * N)) != BEM_OK) return st;
     // U = Q diag(g^-1/2) E_r ;  V^H = E_r^H diag(g^1/2) B
     if ((st = launch_scale_real_cols(h, h->Q, Qs, h->gm, -1, N, nc)) != BEM_OK) return st;
-    h->tag = "gemm_compress_UVh";
-    if ((st = dzgemm_realA(h, OP_N, N, r, nc, 1.0, Qs, N, h->E, nc, 0.0, h->U, N)) != BEM_OK) return st;
-    if ((st = zgemm(h, OP_C, OP_N, r, N, nc, cmk(1, 0), h->E, nc, h->Bs, nc, cmk(0, 0), h->Vh, r)) != BEM_OK) return st;
+    if (h->opt.prec == BEM_MIXED_BF16) {
+        if ((st = tc_compress_factors(h, Qs, h->U, h->Vh)) != BEM_OK) return st;
+    } else {
+        h->tag = "gemm_compress_UVh";
+        if ((st = dzgemm_realA(h, OP_N, N, r, nc, 1.0, Qs, N, h->E, nc, 0.0, h->U, N)) != BEM_OK) return st;
+        if ((st = zgemm(h, OP_C, OP_N, r, N, nc, cmk(1, 0), h->E, nc, h->Bs, nc, cmk(0, 0), h->Vh, r)) != BEM_OK)
+            return st;
+    }
     if (rank_out) *rank_out = r;
     h->stage = 3;
     return BEM_OK;

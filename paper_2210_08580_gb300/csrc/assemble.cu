@@ -22,6 +22,8 @@
 __constant__ double c_glx[GL_MAXQ * (GL_MAXQ + 1) / 2];
 __constant__ double c_glw[GL_MAXQ * (GL_MAXQ + 1) / 2];
 __device__ __forceinline__ int gl_off(int q) { return q * (q - 1) / 2; }
+#define RCP_MAX 72
+__constant__ double c_rcp[RCP_MAX];     // c_rcp[k] = 1/k (c_rcp[0] = 0)
 
 // Gauss-Legendre nodes/weights on [0,1] for q = 1..16 by Newton's method on P_q.
 cudaError_t init_gauss_tables() {
@@ -58,6 +60,11 @@ cudaError_t init_gauss_tables() {
         }
     }
     cudaError_t e = cudaMemcpyToSymbol(c_glx, hx, sizeof(hx));
+    if (e != cudaSuccess) return e;
+    double rc[RCP_MAX];
+    rc[0] = 0.0;
+    for (int k = 1; k < RCP_MAX; ++k) rc[k] = 1.0 / k;
+    e = cudaMemcpyToSymbol(c_rcp, rc, sizeof(rc));
     if (e != cudaSuccess) return e;
     return cudaMemcpyToSymbol(c_glw, hw, sizeof(hw));
 }
@@ -607,12 +614,13 @@ __global__ void __launch_bounds__(256) k_rhs(const double* seg, int N, const dou
         double sb, cb;
         sincos(k * (dx_ * x0 + dy_ * y0), &sb, &cb);
         cplx c = cmk(1, 0), p0 = cmk(0, 0), p1 = cmk(0, 0);
-        for (int n = 0; n < 60; ++n) {
-            const double dn1 = (double)n + 1.0, dn2 = (double)n + 2.0;
-            p0.x += c.x / (dn1 * dn2); p0.y += c.y / (dn1 * dn2);
-            p1.x += c.x / dn2; p1.y += c.y / dn2;
+        for (int n = 0; n < RCP_MAX - 2; ++n) {
+            const double r1 = c_rcp[n + 1], r2 = c_rcp[n + 2], r12 = r1 * r2;
+            p0.x = fma(c.x, r12, p0.x); p0.y = fma(c.y, r12, p0.y);
+            p1.x = fma(c.x, r2, p1.x); p1.y = fma(c.y, r2, p1.y);
             // c <- c * i beta / (n+1)
-            const double nr = -c.y * beta / dn1, ni = c.x * beta / dn1;
+            const double br = beta * r1;
+            const double nr = -c.y * br, ni = c.x * br;
             c.x = nr; c.y = ni;
             if (fabs(c.x) + fabs(c.y) < 1e-19) break;
         }

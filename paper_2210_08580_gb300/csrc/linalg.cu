@@ -467,9 +467,11 @@ __device__ __forceinline__ void tourney(int round, int idx, int np, int& p, int&
 
 __global__ void __launch_bounds__(256) k_jacobi(cplx* R, cplx* V, int n, int* flags, int max_sweeps,
                                                 unsigned* bar, int* err) {
-    __shared__ double red[32];
+    __shared__ double red[8][4];
     const unsigned G = gridDim.x;
     const int np = n + (n & 1);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int EPT = 4;                        // elements per thread (n <= 1024)
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int round = 0; round < np - 1; ++round) {
             for (int idx = blockIdx.x; idx < np / 2; idx += G) {
@@ -479,30 +481,46 @@ __global__ void __launch_bounds__(256) k_jacobi(cplx* R, cplx* V, int n, int* fl
                 if (p > q) { int t = p; p = q; q = t; }
                 cplx* Rp = R + (int64_t)p * n;
                 cplx* Rq = R + (int64_t)q * n;
+                cplx x[EPT], y[EPT];
                 double a = 0.0, b = 0.0, gr = 0.0, gi = 0.0;
-                for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                    const cplx x = Rp[i], y = Rq[i];
-                    a += cabs2(x); b += cabs2(y);
-                    gr += x.x * y.x + x.y * y.y;     // conj(x) y
-                    gi += x.x * y.y - x.y * y.x;
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) {
+                    const int i = tid + 256 * e;
+                    x[e] = (i < n) ? Rp[i] : cmk(0, 0);
+                    y[e] = (i < n) ? Rq[i] : cmk(0, 0);
+                    a += cabs2(x[e]); b += cabs2(y[e]);
+                    gr += x[e].x * y[e].x + x[e].y * y[e].y;     // conj(x) y
+                    gi += x[e].x * y[e].y - x[e].y * y[e].x;
                 }
-                a = block_sum(a, red); b = block_sum(b, red);
-                gr = block_sum(gr, red); gi = block_sum(gi, red);
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    b += __shfl_xor_sync(0xffffffffu, b, o);
+                    gr += __shfl_xor_sync(0xffffffffu, gr, o);
+                    gi += __shfl_xor_sync(0xffffffffu, gi, o);
+                }
+                __syncthreads();
+                if (lane == 0) { red[wid][0] = a; red[wid][1] = b; red[wid][2] = gr; red[wid][3] = gi; }
+                __syncthreads();
+                a = b = gr = gi = 0.0;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) { a += red[w][0]; b += red[w][1]; gr += red[w][2]; gi += red[w][3]; }
                 const double ag = sqrt(gr * gr + gi * gi);
-                if (ag <= 1e-15 * sqrt(a * b) || ag == 0.0) continue;
-                if (threadIdx.x == 0) flags[sweep] = 1;
+                // converged pair: |x^H y| <= 1e-14 |x| |y| (about n eps for n ~ 100)
+                if (ag <= 1e-14 * sqrt(a * b) || ag == 0.0) continue;
+                if (tid == 0) flags[sweep] = 1;
                 const double zeta = (b - a) / (2.0 * ag);
                 const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                 const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                const cplx e = cmk(gr / ag, gi / ag);            // e^{i phi}
-                const cplx sem = cmk(s * e.x, -s * e.y);           // s e^{-i phi}
-                const cplx sep = cmk(s * e.x, s * e.y);            // s e^{i phi}
+                const cplx sem = cmk(s * gr / ag, -s * gi / ag);       // s e^{-i phi}
+                const cplx sep = cmk(s * gr / ag, s * gi / ag);        // s e^{i phi}
                 cplx* Vp = V + (int64_t)p * n;
                 cplx* Vq = V + (int64_t)q * n;
-                for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                    const cplx x = Rp[i], y = Rq[i];
-                    Rp[i] = csub(cscale(x, c), cmul(sem, y));
-                    Rq[i] = cadd(cmul(sep, x), cscale(y, c));
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) {
+                    const int i = tid + 256 * e;
+                    if (i >= n) continue;
+                    Rp[i] = csub(cscale(x[e], c), cmul(sem, y[e]));
+                    Rq[i] = cadd(cmul(sep, x[e]), cscale(y[e], c));
                     const cplx u = Vp[i], w = Vq[i];
                     Vp[i] = csub(cscale(u, c), cmul(sem, w));
                     Vq[i] = cadd(cmul(sep, u), cscale(w, c));
@@ -541,6 +559,7 @@ __global__ void k_identity(cplx* V, int n) {
 }
 
 bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, double* sigma, cplx* E) {
+    if (n > 1024) return bem_fail(h, BEM_E_UNSUPPORTED, "Jacobi SVD: more than 1024 columns");
     cplx* V = nullptr;
     int* flags = nullptr;
     double* tmp = nullptr;
@@ -554,7 +573,7 @@ bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, double* sigma, cplx* E)
     int ms = max_sweeps;
     void* args[] = {&R, &V, &n, &flags, &ms, &h->bar, &h->dev_err};
     bem_status st;
-    BEM_TIMED(h, "k_jacobi", st = coop_launch(h, (const void*)k_jacobi, (n + 1) / 2, 128, args, "k_jacobi"));
+    BEM_TIMED(h, "k_jacobi", st = coop_launch(h, (const void*)k_jacobi, (n + 1) / 2, 256, args, "k_jacobi"));
     if (st == BEM_OK) {
         BEM_TIMED(h, "k_sort_sv", (k_sort_sv<<<1, 256, 0, h->stream>>>(R, V, n, sigma, E, tmp)));
         BEM_LAUNCH(h, "k_sort_sv");

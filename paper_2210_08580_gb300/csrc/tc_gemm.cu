@@ -336,14 +336,19 @@ __device__ __forceinline__ bool in_band(int64_t i, int64_t k, int64_t K, int ban
     return d <= band;
 }
 
-__global__ void k_exp_rows(const double2* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k, int band, int* e) {
+__global__ void k_exp_rows(const void* src, int is_real, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k, int band,
+                           int* e) {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (i >= M) return;
     double mx = 0.0;
     for (int64_t k = threadIdx.x & 31; k < K; k += 32) {
         if (in_band(i, k, K, band)) continue;
-        const double2 v = src[i * sa_i + k * sa_k];
-        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+        if (is_real) {
+            mx = fmax(mx, fabs(((const double*)src)[i * sa_i + k * sa_k]));
+        } else {
+            const double2 v = ((const double2*)src)[i * sa_i + k * sa_k];
+            mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+        }
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) {
@@ -382,49 +387,72 @@ __device__ __forceinline__ double pow2i(int p) { return __longlong_as_double((lo
 // val 2^-e in (-1, 1) -> S slices: X = round(val 2^{7S - e}) (exact scaling and one
 // rounding), then balanced base-128 digits from the least significant up: d in [-64, 63]
 // for s >= 1 and the leading |d_0| <= 128; slice s stores d_s 2^{-7s} (exact in bf16).
-__device__ __forceinline__ void split_store(double val, int e, int S, __nv_bfloat16* out, size_t slice_stride) {
+// digits of one value, returned as the floats d_s 2^{-7s}
+__device__ __forceinline__ void split_digits(double val, int e, int S, float* d) {
     long long X = __double2ll_rn(val * pow2i(7 * S - e));
-    for (int s = S - 1; s >= 1; --s) {
-        long long d = X & 127;
-        if (d >= 64) d -= 128;
-        X = (X - d) >> 7;
-        out[s * slice_stride] = __float2bfloat16_rn((float)d * __int_as_float((127 - 7 * s) << 23));
+#pragma unroll
+    for (int s = TC_SMAX - 1; s >= 1; --s) {
+        if (s >= S) { d[s] = 0.f; continue; }
+        long long q = X & 127;
+        if (q >= 64) q -= 128;
+        X = (X - q) >> 7;
+        d[s] = (float)q * __int_as_float((127 - 7 * s) << 23);
     }
-    out[0] = __float2bfloat16_rn((float)X);
+    d[0] = (float)X;
 }
 
-// A' slices: out[s][i][kp], kp = 2k + c, padded with zeros to Kp
-__global__ void k_slice_A(const double2* src, int64_t M, int64_t K, int64_t Kp, int64_t sa_i, int64_t sa_k,
-                          int band, const int* e, int S, __nv_bfloat16* out) {
-    const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// A' slices: out[s][i][kp], kp = 2k + c, padded with zeros to Kp.  One thread per complex
+// entry (k) writes the (re, im) pair of every slice as one bf16x2.  conj negates Im.
+__global__ void k_slice_A(const void* src, int is_real, int conj, int64_t M, int64_t K, int64_t Kp, int64_t sa_i,
+                          int64_t sa_k, int band, const int* e, int S, __nv_bfloat16* out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = blockIdx.y;
-    if (kp >= Kp || i >= M) return;
-    double x = 0.0;
-    const int64_t k = kp >> 1;
+    if (2 * k >= Kp || i >= M) return;
+    double re = 0.0, im = 0.0;
     if (k < K && !in_band(i, k, K, band)) {
-        const double2 v = src[i * sa_i + k * sa_k];
-        x = (kp & 1) ? v.y : v.x;
+        if (is_real) {
+            re = ((const double*)src)[i * sa_i + k * sa_k];
+        } else {
+            const double2 v = ((const double2*)src)[i * sa_i + k * sa_k];
+            re = v.x; im = conj ? -v.y : v.y;
+        }
     }
-    split_store(x, e[i], S, out + i * Kp + kp, (size_t)M * Kp);
+    float dr[TC_SMAX], di[TC_SMAX];
+    split_digits(re, e[i], S, dr);
+    split_digits(im, e[i], S, di);
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + i * Kp + 2 * k);
+    const size_t stride2 = (size_t)M * Kp / 2;
+#pragma unroll
+    for (int s = 0; s < TC_SMAX; ++s)
+        if (s < S) o[s * stride2] = __floats2bfloat162_rn(dr[s], di[s]);
 }
 
-// B' slices stored K-major: out[s][jp][kp]
+// B' slices stored K-major: out[s][jp][kp].  One thread per complex entry (k, j) writes rows
+// jp = 2j: (Re, -Im) and jp = 2j + 1: (Im, Re) at kp = 2k, 2k + 1.
 __global__ void k_slice_B(const void* src, int is_real, int64_t K, int64_t m, int64_t Kp, int64_t sb_k,
                           int64_t sb_j, const int* f, int S, __nv_bfloat16* out) {
-    const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t jp = blockIdx.y;
-    if (kp >= Kp || jp >= 2 * m) return;
-    double x = 0.0;
-    const int64_t k = kp >> 1, j = jp >> 1;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = blockIdx.y;
+    if (2 * k >= Kp || j >= m) return;
+    double re = 0.0, im = 0.0;
     if (k < K) {
-        double re, im;
-        if (is_real) { re = ((const double*)src)[k * sb_k + j * sb_j]; im = 0.0; }
+        if (is_real) { re = ((const double*)src)[k * sb_k + j * sb_j]; }
         else { const double2 v = ((const double2*)src)[k * sb_k + j * sb_j]; re = v.x; im = v.y; }
-        const int c = (int)(kp & 1), d = (int)(jp & 1);
-        // B'[2k, 2j] = Re, B'[2k+1, 2j] = -Im, B'[2k, 2j+1] = Im, B'[2k+1, 2j+1] = Re
-        x = (d == 0) ? (c == 0 ? re : -im) : (c == 0 ? im : re);
     }
-    split_store(x, f[jp], S, out + jp * Kp + kp, (size_t)(2 * m) * Kp);
+    const int fe = f[2 * j];
+    float dr[TC_SMAX], di[TC_SMAX];
+    split_digits(re, fe, S, dr);
+    split_digits(im, fe, S, di);
+    __nv_bfloat162* o0 = reinterpret_cast<__nv_bfloat162*>(out + (2 * j) * Kp + 2 * k);
+    __nv_bfloat162* o1 = reinterpret_cast<__nv_bfloat162*>(out + (2 * j + 1) * Kp + 2 * k);
+    const size_t stride2 = (size_t)(2 * m) * Kp / 2;
+#pragma unroll
+    for (int s = 0; s < TC_SMAX; ++s) {
+        if (s < S) {
+            o0[s * stride2] = __floats2bfloat162_rn(dr[s], -di[s]);
+            o1[s * stride2] = __floats2bfloat162_rn(di[s], dr[s]);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------ host side
@@ -460,6 +488,7 @@ struct TcState {
     TcOperand opS, opW, opD;          // A operands: X^T of the assembled matrices
     TcOperand opVh, opU;              // Woodbury factors
     TcOperand bbuf;                   // B operand scratch (reused)
+    TcOperand tmpA;                   // A operand scratch (reused)
 };
 
 static TcState* tcs(bem_ctx* h) {
@@ -506,17 +535,17 @@ static bem_status reserve(bem_ctx* h, TcOperand& op, int64_t rows, int64_t Kp, i
 
 // A operand: rows M, K complex columns, A_op[i,k] = src[i*sa_i + k*sa_k]; band >= 0 drops
 // the cyclic band |i - k| <= band (square operators)
-static bem_status slice_A(bem_ctx* h, TcOperand& op, const cplx* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k,
-                          int band = -1) {
+static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k,
+                          int band = -1, int is_real = 0, int conj = 0) {
     const int S = tcs(h)->S;
     const int64_t Kp = pad64(2 * K);
     bem_status st = reserve(h, op, M, Kp, S);
     if (st != BEM_OK) return st;
     op.K = K;
-    BEM_TIMED(h, "k_exp_rows", (k_exp_rows<<<(unsigned)((M + 7) / 8), 256, 0, h->stream>>>(src, M, K, sa_i, sa_k, band, op.exps)));
+    BEM_TIMED(h, "k_exp_rows", (k_exp_rows<<<(unsigned)((M + 7) / 8), 256, 0, h->stream>>>(src, is_real, M, K, sa_i, sa_k, band, op.exps)));
     BEM_LAUNCH(h, "k_exp_rows");
-    dim3 grid((unsigned)((Kp + 255) / 256), (unsigned)M);
-    BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, M, K, Kp, sa_i, sa_k, band, op.exps, S, op.slices)));
+    dim3 grid((unsigned)((Kp / 2 + 255) / 256), (unsigned)M);
+    BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, is_real, conj, M, K, Kp, sa_i, sa_k, band, op.exps, S, op.slices)));
     BEM_LAUNCH(h, "k_slice_A");
     return encode_map(h, op, S);
 }
@@ -531,7 +560,7 @@ static bem_status slice_B(bem_ctx* h, TcOperand& op, const void* src, int is_rea
     op.K = K;
     BEM_TIMED(h, "k_exp_cols", (k_exp_cols<<<(unsigned)((m + 7) / 8), 256, 0, h->stream>>>(src, is_real, K, m, sb_k, sb_j, op.exps)));
     BEM_LAUNCH(h, "k_exp_cols");
-    dim3 grid((unsigned)((Kp + 255) / 256), (unsigned)(2 * m));
+    dim3 grid((unsigned)((Kp / 2 + 255) / 256), (unsigned)m);
     BEM_TIMED(h, "k_slice_B", (k_slice_B<<<grid, 256, 0, h->stream>>>(src, is_real, K, m, Kp, sb_k, sb_j, op.exps, S, op.slices)));
     BEM_LAUNCH(h, "k_slice_B");
     return encode_map(h, op, S);
@@ -643,6 +672,20 @@ bem_status tc_prepare_solve(bem_ctx* h) {
     return slice_A(h, t->opU, h->U, N, r, 1, N);
 }
 
+bem_status tc_compress_factors(bem_ctx* h, const double* Qs, cplx* U, cplx* Vh) {
+    TcState* t = tcs(h);
+    const int64_t N = h->N, nc = h->ncols, r = h->r;
+    bem_status st;
+    // U (N x r) = Qs (N x nc, real) E_r (nc x r)
+    if ((st = slice_A(h, t->tmpA, Qs, N, nc, 1, N, -1, 1, 0)) != BEM_OK) return st;
+    if ((st = slice_B(h, t->bbuf, h->E, 0, nc, r, 1, nc)) != BEM_OK) return st;
+    if ((st = tc_gemm(h, t->tmpA, t->bbuf, U, N, 0, 1.0, 0.0, "tc_compress_U")) != BEM_OK) return st;
+    // V^H (r x N) = E_r^H (r x nc) Bs (nc x N):  A_op[i, k] = conj(E[k + i nc])
+    if ((st = slice_A(h, t->tmpA, h->E, r, nc, nc, 1, -1, 0, 1)) != BEM_OK) return st;
+    if ((st = slice_B(h, t->bbuf, h->Bs, 0, nc, N, 1, nc)) != BEM_OK) return st;
+    return tc_gemm(h, t->tmpA, t->bbuf, Vh, r, 0, 1.0, 0.0, "tc_compress_Vh");
+}
+
 bem_status tc_core_product(bem_ctx* h, cplx* Kt) {
     TcState* t = tcs(h);
     const int64_t N = h->N, r = h->r;
@@ -739,6 +782,7 @@ void tc_destroy(bem_ctx* h) {
     if (!h->tc) return;
     TcState* t = (TcState*)h->tc;
     free_op(t->opS); free_op(t->opW); free_op(t->opD); free_op(t->opVh); free_op(t->opU); free_op(t->bbuf);
+    free_op(t->tmpA);
     delete t;
     h->tc = nullptr;
 }

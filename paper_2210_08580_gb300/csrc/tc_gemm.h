@@ -13,6 +13,8 @@ bem_status tc_product_left(bem_ctx* h, int op, const double* Qreal, const cplx* 
 bem_status tc_product_right(bem_ctx* h, int op, const cplx* y, int64_t ldy, int64_t nrhs, cplx* out, int64_t ld);
 // Slices U and V^H for the Woodbury products (after factor).
 bem_status tc_prepare_solve(bem_ctx* h);
+// U = Qs E_r and V^H = E_r^H Bs (compression factors) as split-bf16 products.
+bem_status tc_compress_factors(bem_ctx* h, const double* Qs, cplx* U, cplx* Vh);
 // Kt = beta^-1 V^H U (r x r, ld r) as a split-bf16 product (after tc_prepare_solve).
 bem_status tc_core_product(bem_ctx* h, cplx* Kt);
 // Woodbury solve with split-bf16 products and FP64 residual refinement.
