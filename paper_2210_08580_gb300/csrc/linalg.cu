@@ -465,13 +465,18 @@ __device__ __forceinline__ void tourney(int round, int idx, int np, int& p, int&
     q = pos(np - 1 - idx);
 }
 
-__global__ void __launch_bounds__(256) k_jacobi(cplx* R, cplx* V, int n, int* flags, int max_sweeps,
-                                                unsigned* bar, int* err) {
-    __shared__ double red[8][4];
+// One-sided Jacobi on the columns of X (n x n, column-major).  Applied to X = R^H it
+// leaves X_final = U Sigma with U the left singular vectors of R^H (= those of the block
+// the QR came from); R^H from a QR is close to diagonally dominant, which makes the
+// sweeps few.  128 threads per pair; one pair per CTA per round.
+#define JAC_NT 128
+__global__ void __launch_bounds__(JAC_NT) k_jacobi(cplx* X, int n, int* flags, int max_sweeps, unsigned* bar,
+                                                   int* err) {
+    __shared__ double red[JAC_NT / 32][4];
     const unsigned G = gridDim.x;
     const int np = n + (n & 1);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    constexpr int EPT = 4;                        // elements per thread (n <= 1024)
+    constexpr int EPT = 1024 / JAC_NT;            // elements per thread (n <= 1024)
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int round = 0; round < np - 1; ++round) {
             for (int idx = blockIdx.x; idx < np / 2; idx += G) {
@@ -479,15 +484,15 @@ __global__ void __launch_bounds__(256) k_jacobi(cplx* R, cplx* V, int n, int* fl
                 tourney(round, idx, np, p, q);
                 if (p >= n || q >= n) continue;
                 if (p > q) { int t = p; p = q; q = t; }
-                cplx* Rp = R + (int64_t)p * n;
-                cplx* Rq = R + (int64_t)q * n;
+                cplx* Xp = X + (int64_t)p * n;
+                cplx* Xq = X + (int64_t)q * n;
                 cplx x[EPT], y[EPT];
                 double a = 0.0, b = 0.0, gr = 0.0, gi = 0.0;
 #pragma unroll
                 for (int e = 0; e < EPT; ++e) {
-                    const int i = tid + 256 * e;
-                    x[e] = (i < n) ? Rp[i] : cmk(0, 0);
-                    y[e] = (i < n) ? Rq[i] : cmk(0, 0);
+                    const int i = tid + JAC_NT * e;
+                    x[e] = (i < n) ? Xp[i] : cmk(0, 0);
+                    y[e] = (i < n) ? Xq[i] : cmk(0, 0);
                     a += cabs2(x[e]); b += cabs2(y[e]);
                     gr += x[e].x * y[e].x + x[e].y * y[e].y;     // conj(x) y
                     gi += x[e].x * y[e].y - x[e].y * y[e].x;
@@ -503,9 +508,9 @@ __global__ void __launch_bounds__(256) k_jacobi(cplx* R, cplx* V, int n, int* fl
                 __syncthreads();
                 a = b = gr = gi = 0.0;
 #pragma unroll
-                for (int w = 0; w < 8; ++w) { a += red[w][0]; b += red[w][1]; gr += red[w][2]; gi += red[w][3]; }
+                for (int w = 0; w < JAC_NT / 32; ++w) { a += red[w][0]; b += red[w][1]; gr += red[w][2]; gi += red[w][3]; }
                 const double ag = sqrt(gr * gr + gi * gi);
-                // converged pair: |x^H y| <= 1e-14 |x| |y| (about n eps for n ~ 100)
+                // converged pair: |x^H y| <= 1e-14 |x| |y|
                 if (ag <= 1e-14 * sqrt(a * b) || ag == 0.0) continue;
                 if (tid == 0) flags[sweep] = 1;
                 const double zeta = (b - a) / (2.0 * ag);
@@ -513,17 +518,12 @@ __global__ void __launch_bounds__(256) k_jacobi(cplx* R, cplx* V, int n, int* fl
                 const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
                 const cplx sem = cmk(s * gr / ag, -s * gi / ag);       // s e^{-i phi}
                 const cplx sep = cmk(s * gr / ag, s * gi / ag);        // s e^{i phi}
-                cplx* Vp = V + (int64_t)p * n;
-                cplx* Vq = V + (int64_t)q * n;
 #pragma unroll
                 for (int e = 0; e < EPT; ++e) {
-                    const int i = tid + 256 * e;
+                    const int i = tid + JAC_NT * e;
                     if (i >= n) continue;
-                    Rp[i] = csub(cscale(x[e], c), cmul(sem, y[e]));
-                    Rq[i] = cadd(cmul(sep, x[e]), cscale(y[e], c));
-                    const cplx u = Vp[i], w = Vq[i];
-                    Vp[i] = csub(cscale(u, c), cmul(sem, w));
-                    Vq[i] = cadd(cmul(sep, u), cscale(w, c));
+                    Xp[i] = csub(cscale(x[e], c), cmul(sem, y[e]));
+                    Xq[i] = cadd(cmul(sep, x[e]), cscale(y[e], c));
                 }
             }
             if (!grid_barrier(bar, G, err)) return;
@@ -532,11 +532,12 @@ __global__ void __launch_bounds__(256) k_jacobi(cplx* R, cplx* V, int n, int* fl
     }
 }
 
-// sigma_c = |R_c|, sorted descending; E[:, rank] = V[:, c]
-__global__ void k_sort_sv(const cplx* R, const cplx* V, int n, double* sigma, cplx* E, double* tmp) {
+// sigma_c = |X_c|, sorted descending; E[:, rank] = X_c / sigma_c (a unit vector e_c when
+// sigma_c = 0, which is then below any truncation threshold)
+__global__ void k_sort_sv(const cplx* X, int n, double* sigma, cplx* E, double* tmp) {
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         double s = 0.0;
-        for (int i = 0; i < n; ++i) s += cabs2(R[(int64_t)c * n + i]);
+        for (int i = 0; i < n; ++i) s += cabs2(X[(int64_t)c * n + i]);
         tmp[c] = sqrt(s);
     }
     __syncthreads();
@@ -548,37 +549,42 @@ __global__ void k_sort_sv(const cplx* R, const cplx* V, int n, double* sigma, cp
             if (sd > sc || (sd == sc && d < c)) ++rank;
         }
         sigma[rank] = sc;
-        for (int i = 0; i < n; ++i) E[(int64_t)rank * n + i] = V[(int64_t)c * n + i];
+        const double inv = (sc > 0.0) ? 1.0 / sc : 0.0;
+        for (int i = 0; i < n; ++i)
+            E[(int64_t)rank * n + i] = (sc > 0.0) ? cscale(X[(int64_t)c * n + i], inv) : cmk(i == c ? 1.0 : 0.0, 0.0);
     }
 }
 
-__global__ void k_identity(cplx* V, int n) {
+// X = R^H (n x n)
+__global__ void k_conj_transpose(const cplx* R, cplx* X, int n) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n * n) return;
-    V[idx] = cmk((idx % n) == (idx / n) ? 1.0 : 0.0, 0.0);
+    const int64_t i = idx % n, j = idx / n;
+    X[idx] = cconj(R[j + i * n]);
 }
 
 bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, double* sigma, cplx* E) {
     if (n > 1024) return bem_fail(h, BEM_E_UNSUPPORTED, "Jacobi SVD: more than 1024 columns");
-    cplx* V = nullptr;
+    cplx* X = nullptr;
     int* flags = nullptr;
     double* tmp = nullptr;
     const int max_sweeps = 40;
-    BEM_CUDA(h, cudaMallocAsync((void**)&V, sizeof(cplx) * (size_t)n * n, h->stream));
+    BEM_CUDA(h, cudaMallocAsync((void**)&X, sizeof(cplx) * (size_t)n * n, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&flags, sizeof(int) * max_sweeps, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&tmp, sizeof(double) * n, h->stream));
     BEM_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(int) * max_sweeps, h->stream));
-    BEM_TIMED(h, "k_identity", (k_identity<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, h->stream>>>(V, n)));
-    BEM_LAUNCH(h, "k_identity");
+    BEM_TIMED(h, "k_conj_transpose",
+              (k_conj_transpose<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, h->stream>>>(R, X, n)));
+    BEM_LAUNCH(h, "k_conj_transpose");
     int ms = max_sweeps;
-    void* args[] = {&R, &V, &n, &flags, &ms, &h->bar, &h->dev_err};
+    void* args[] = {&X, &n, &flags, &ms, &h->bar, &h->dev_err};
     bem_status st;
-    BEM_TIMED(h, "k_jacobi", st = coop_launch(h, (const void*)k_jacobi, (n + 1) / 2, 256, args, "k_jacobi"));
+    BEM_TIMED(h, "k_jacobi", st = coop_launch(h, (const void*)k_jacobi, (n + 1) / 2, JAC_NT, args, "k_jacobi"));
     if (st == BEM_OK) {
-        BEM_TIMED(h, "k_sort_sv", (k_sort_sv<<<1, 256, 0, h->stream>>>(R, V, n, sigma, E, tmp)));
+        BEM_TIMED(h, "k_sort_sv", (k_sort_sv<<<1, 256, 0, h->stream>>>(X, n, sigma, E, tmp)));
         BEM_LAUNCH(h, "k_sort_sv");
     }
-    cudaFreeAsync(V, h->stream);
+    cudaFreeAsync(X, h->stream);
     cudaFreeAsync(flags, h->stream);
     cudaFreeAsync(tmp, h->stream);
     return st;
