@@ -31,7 +31,57 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "factor s + RHS solves/s at N=16384: mixed/batched vs FP64 GPU, rel err ≤1e-8"
-FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 (CUDA-core and tensor) nominal rate
+# GB300 FP64 pipe: 2 DFMA per SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma
+# peak_sustained = 2), 152 SMs, 2070 MHz maximum SM clock -> 1.259 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP64 flops per far-field Gauss point of the assembly (S and N): argument u = k^2 r^2
+# from the two node coordinates (8), J0 and Y0 as degree-10 polynomials in u (2 x 10 FMA =
+# 40), the four lambda-weighted complex moments (8 FMA = 16)
+ASM_FLOPS_PER_POINT = 64
+# DRAM bytes per launch from ncu captures of the kernels as they stand (None = not captured
+# since the kernel last changed); the summaries are under profiles/
+TRAFFIC_BYTES = {}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def tc_gemm_flops(name, N, nrhs, n_modes, r, S):
+    """bf16 tensor flops of one split-slice launch: S(S+1)/2 slice pairs, each a real GEMM
+    of the complex product in 2x2 real block form (M x 2Nc x 2K real -> 8 M Nc K flops)."""
+    dims = {"tc_rhs_SY": (N, nrhs, N), "tc_filter_QtS": (n_modes, N, N),
+            "tc_filter_YN": (n_modes, N, N)}
+    if name not in dims:
+        return None
+    M, Nc, K = dims[name]
+    return S * (S + 1) / 2 * 8.0 * M * Nc * K
+
+
+def roofline(rep, args, n_modes, r, quad_points):
+    dom_name, (dom_cnt, dom_ms) = max(rep.items(), key=lambda kv: kv[1][1])
+    avg_s = dom_ms / dom_cnt / 1000.0
+    pk = _peaks()
+    if dom_name == "k_assemble":
+        ach = quad_points * ASM_FLOPS_PER_POINT / avg_s / 1e12
+        return {"kernel": dom_name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES.get(dom_name),
+                "units_per_launch": quad_points, "flops_per_unit": ASM_FLOPS_PER_POINT,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
+    fl = tc_gemm_flops(dom_name, args.N, args.nrhs, n_modes, r, 6)
+    if fl is not None:
+        peak = pk.get("bf16_tflops_sustained", 1700.0)
+        ach = fl / avg_s / 1e12
+        return {"kernel": dom_name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": TRAFFIC_BYTES.get(dom_name),
+                "peak_source": "of measured (bf16_tflops_sustained)" if "bf16_tflops_sustained" in pk
+                else "of fallback (1.7 PFLOP/s sustained)"}
+    return {"kernel": dom_name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None}
 
 
 def parse():
@@ -250,21 +300,8 @@ def main():
 
     # ---- roofline of the dominant kernel
     launches = sum(c for c, _ in rep.values())
-    dom = max(rep.items(), key=lambda kv: kv[1][1])
-    dom_name, (dom_cnt, dom_ms) = dom
-    N, nr, nc, r = args.N, args.nrhs, n_modes, info["r"]
-    flops_per_launch = {
-        "gemm_rhs_SY": 8.0 * N * N * nr,
-        "gemm_filter_YN": 8.0 * nc * N * N,
-        "gemm_filter_QtS": 4.0 * nc * N * N,
-    }
-    roof = None
-    if dom_name in flops_per_launch:
-        avg_s = dom_ms / dom_cnt / 1000.0
-        ach = flops_per_launch[dom_name] / avg_s / 1e12
-        roof = {"kernel": dom_name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (152 SMs x 2.07 GHz x 4 flop/clk/SM)"}
+    quad_points = s.info()["quad_points"]
+    roof = roofline(rep, args, n_modes, info["r"], quad_points)
 
     # ---- end to end through the Python API with host buffers
     e2e = None

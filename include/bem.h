@@ -88,6 +88,8 @@ typedef struct {
     double sigma_max;         /* largest singular value of the filtered compact part        */
     int stage;                /* 0 empty, 1 assembled, 2 filtered, 3 compressed, 4 factored */
     int prec;                 /* bem_precision in use                                       */
+    int64_t quad_points;      /* Gauss points (kernel evaluations) the last bem_assemble
+                                 spent on separated segment pairs, counted on the device   */
 } bem_info;
 
 typedef struct bem_ctx* bem_handle;

@@ -125,13 +125,16 @@ bem_status bem_create(bem_handle* out, int device, void* cuda_stream, const bem_
         }
     }
     if (cudaMalloc((void**)&h->dev_err, sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&h->bar, 4 * sizeof(unsigned)) != cudaSuccess) {
+        cudaMalloc((void**)&h->bar, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc((void**)&h->qpts, sizeof(unsigned long long)) != cudaSuccess) {
         cudaFree(h->dev_err);
+        cudaFree(h->bar);
         delete h;
         return BEM_E_NOMEM;
     }
     cudaMemset(h->dev_err, 0, sizeof(int));
     cudaMemset(h->bar, 0, 4 * sizeof(unsigned));
+    cudaMemset(h->qpts, 0, sizeof(unsigned long long));
     *out = h;
     return BEM_OK;
 }
@@ -165,6 +168,7 @@ bem_status bem_destroy(bem_handle h) {
     free_ptr(&h->work);
     free_ptr((void**)&h->dev_err);
     free_ptr((void**)&h->bar);
+    free_ptr((void**)&h->qpts);
     delete h;
     return BEM_OK;
 }
@@ -577,6 +581,9 @@ bem_status bem_get_info(bem_handle h, bem_info* info) {
     info->sigma_max = h->sigma_max;
     info->stage = h->stage;
     info->prec = h->opt.prec;
+    unsigned long long q = 0;
+    BEM_CUDA(h, cudaMemcpy(&q, h->qpts, sizeof(q), cudaMemcpyDeviceToHost));
+    info->quad_points = (int64_t)q;
     return BEM_OK;
 }
 

@@ -235,6 +235,7 @@ struct AsmParams {
     int64_t ld;
     int nT;
     const double* btab;   // far-field Bessel table
+    unsigned long long* qpts;   // Gauss points of separated pairs (accumulated)
     SeriesCoef sc;
 };
 
@@ -416,7 +417,7 @@ __device__ __forceinline__ int q_for_gap(float ratio, float kgap) {
 
 template <bool WD>
 __device__ void pair_moments(int e, int f, const SegV& se, const SegV& sf, const AsmParams& p,
-                             cplx I[4], cplx J[4], cplx Jt[4]) {
+                             cplx I[4], cplx J[4], cplx Jt[4], unsigned& npts) {
     const int N = p.N;
     int d = e - f; if (d < 0) d = -d;
     const int cyc = min(d, N - d);
@@ -442,6 +443,7 @@ __device__ void pair_moments(int e, int f, const SegV& se, const SegV& sf, const
         const float hmax = (float)fmax(se.h, sf.h);
         const float gap = fmaxf(sqrtf(mx * mx + my * my) - 0.5f * (float)(se.h + sf.h), 0.0f);
         const int q = q_for_gap(gap / hmax, (float)p.k * (gap + hmax));
+        npts += (unsigned)(q * q);
         pair_gauss<WD>(q, se, sf, p.k, p.btab, I, J, Jt);
     }
 }
@@ -484,6 +486,7 @@ __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
     }
     __syncthreads();
     const double k2 = p.k * p.k;
+    unsigned npts = 0;
     for (int pi = threadIdx.x; pi < TP * TP; pi += blockDim.x) {
         const int el = pi / TP, fl = pi % TP;
         // skip segment pairs touching only rows/cols beyond N
@@ -492,7 +495,7 @@ __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
         SegV se = {sgE[el], sgE[TP + el], sgE[2 * TP + el], sgE[3 * TP + el], sgE[4 * TP + el]};
         SegV sf = {sgF[fl], sgF[TP + fl], sgF[2 * TP + fl], sgF[3 * TP + fl], sgF[4 * TP + fl]};
         cplx I[4], J[4], Jt[4];
-        pair_moments<WD>(e, f, se, sf, p, I, J, Jt);
+        pair_moments<WD>(e, f, se, sf, p, I, J, Jt, npts);
         for (int q = 0; q < 4; ++q) {
             sI[pi * 4 + q] = I[q];
             if (WD) { sJ[pi * 4 + q] = J[q]; sJt[pi * 4 + q] = Jt[q]; }
@@ -503,6 +506,8 @@ __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
         sM[pi] = cscale(M0, ihh);
         sND[pi] = k2 * (se.ty * sf.ty + se.tx * sf.tx);   // nu = (t_y, -t_x): nu_e . nu_f = t_e . t_f
     }
+    for (int o = 16; o > 0; o >>= 1) npts += __shfl_xor_sync(0xffffffffu, npts, o);
+    if ((threadIdx.x & 31) == 0 && npts) atomicAdd(p.qpts, (unsigned long long)npts);
     __syncthreads();
     const bool mirror = (ti != tj);
     for (int pass = 0; pass < (mirror ? 2 : 1); ++pass) {
@@ -585,6 +590,8 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     p.W = (ops & BEM_OP_W) ? h->W : nullptr;
     p.D = (ops & BEM_OP_D) ? h->D : nullptr;
     p.ld = h->N;
+    p.qpts = h->qpts;
+    BEM_CUDA(h, cudaMemsetAsync(h->qpts, 0, sizeof(unsigned long long), h->stream));
     series_coefficients(h->k, 2.0 * h->hbar, &p.sc);
     bem_status st = bessel_table(h, &p.btab);
     if (st != BEM_OK) return st;

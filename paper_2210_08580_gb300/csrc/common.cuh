@@ -111,6 +111,7 @@ struct bem_ctx {
     size_t work_bytes = 0;
     int* dev_err = nullptr;           // device status word
     unsigned* bar = nullptr;          // grid barrier words (2)
+    unsigned long long* qpts = nullptr;   // Gauss points of separated pairs, last assembly
     int stage = 0;
 
     // mixed-precision state (owned by the tensor-core module)
