@@ -24,6 +24,15 @@ __constant__ double c_glw[GL_MAXQ * (GL_MAXQ + 1) / 2];
 __device__ __forceinline__ int gl_off(int q) { return q * (q - 1) / 2; }
 #define RCP_MAX 72
 __constant__ double c_rcp[RCP_MAX];     // c_rcp[k] = 1/k (c_rcp[0] = 0)
+// the same rules as double-float pairs: node x, weights w (1 - x) and w x
+__constant__ float2 c_gx_df[GL_MAXQ * (GL_MAXQ + 1) / 2];
+__constant__ float2 c_gw0_df[GL_MAXQ * (GL_MAXQ + 1) / 2];
+__constant__ float2 c_gw1_df[GL_MAXQ * (GL_MAXQ + 1) / 2];
+
+static float2 host_df(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
 
 // Gauss-Legendre nodes/weights on [0,1] for q = 1..16 by Newton's method on P_q.
 cudaError_t init_gauss_tables() {
@@ -61,6 +70,15 @@ cudaError_t init_gauss_tables() {
     }
     cudaError_t e = cudaMemcpyToSymbol(c_glx, hx, sizeof(hx));
     if (e != cudaSuccess) return e;
+    float2 fx[GL_MAXQ * (GL_MAXQ + 1) / 2], fw0[GL_MAXQ * (GL_MAXQ + 1) / 2], fw1[GL_MAXQ * (GL_MAXQ + 1) / 2];
+    for (int o = 0; o < GL_MAXQ * (GL_MAXQ + 1) / 2; ++o) {
+        fx[o] = host_df(hx[o]);
+        fw0[o] = host_df(hw[o] * (1.0 - hx[o]));
+        fw1[o] = host_df(hw[o] * hx[o]);
+    }
+    if ((e = cudaMemcpyToSymbol(c_gx_df, fx, sizeof(fx))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_gw0_df, fw0, sizeof(fw0))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_gw1_df, fw1, sizeof(fw1))) != cudaSuccess) return e;
     double rc[RCP_MAX];
     rc[0] = 0.0;
     for (int k = 1; k < RCP_MAX; ++k) rc[k] = 1.0 / k;
@@ -159,9 +177,15 @@ static void host_funcs(ld z, ld f[4]) {
     }
 }
 
-static void build_bessel_table(std::vector<double>& tab) {
+static void build_bessel_table(std::vector<double>& tab, std::vector<float>& tabf) {
     const int n = BTAB_NC;
     tab.assign((size_t)BTAB_NINT * BTAB_STRIDE, 0.0);
+    tabf.assign((size_t)BTAB_NINT * BTAB_DF_STRIDE, 0.0f);
+    auto put_df = [&](size_t at, ld v) {
+        const float hi = (float)v;
+        tabf[at] = hi;
+        tabf[at + 1] = (float)(v - (ld)hi);
+    };
     std::vector<ld> tk((size_t)n * n);        // monomial coefficients of T_k
     for (int k = 0; k < n; ++k) {
         for (int j = 0; j < n; ++j) {
@@ -188,6 +212,8 @@ static void build_bessel_table(std::vector<double>& tab) {
         const ld um = 0.5L * (ua + ub), uh = 0.5L * (ub - ua);
         tab[(size_t)i * BTAB_STRIDE] = (double)um;
         tab[(size_t)i * BTAB_STRIDE + 1] = (double)(1.0L / uh);
+        put_df((size_t)i * BTAB_DF_STRIDE, um);
+        put_df((size_t)i * BTAB_DF_STRIDE + 2, 1.0L / uh);
         std::vector<ld> fv((size_t)4 * n);
         for (int j = 0; j < n; ++j) {
             const ld tj = cosl(LD_PI * (j + 0.5L) / n);
@@ -205,25 +231,34 @@ static void build_bessel_table(std::vector<double>& tab) {
             for (int k = 0; k < n; ++k)
                 for (int j = 0; j < n; ++j) mono[j] += a[k] * tk[(size_t)k * n + j];
             for (int j = 0; j < n; ++j) tab[(size_t)i * BTAB_STRIDE + 2 + (size_t)q * n + j] = (double)mono[j];
+            if (q < 2)
+                for (int j = 0; j < n; ++j) put_df((size_t)i * BTAB_DF_STRIDE + 4 * (j + 1) + 2 * q, mono[j]);
         }
     }
 }
 
 static std::mutex g_btab_mutex;
 static double* g_btab[64] = {nullptr};
+static float4* g_btabf[64] = {nullptr};
 
-static bem_status bessel_table(bem_ctx* h, const double** out) {
+static bem_status bessel_table(bem_ctx* h, const double** out, const float4** outf) {
     std::lock_guard<std::mutex> lk(g_btab_mutex);
     if (h->device < 0 || h->device >= 64) return bem_fail(h, BEM_E_INVALID, "bad device");
     if (!g_btab[h->device]) {
         std::vector<double> tab;
-        build_bessel_table(tab);
+        std::vector<float> tabf;
+        build_bessel_table(tab, tabf);
         double* d = nullptr;
+        float* df = nullptr;
         BEM_CUDA(h, cudaMalloc((void**)&d, tab.size() * sizeof(double)));
         BEM_CUDA(h, cudaMemcpy(d, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+        BEM_CUDA(h, cudaMalloc((void**)&df, tabf.size() * sizeof(float)));
+        BEM_CUDA(h, cudaMemcpy(df, tabf.data(), tabf.size() * sizeof(float), cudaMemcpyHostToDevice));
         g_btab[h->device] = d;
+        g_btabf[h->device] = reinterpret_cast<float4*>(df);
     }
     *out = g_btab[h->device];
+    *outf = g_btabf[h->device];
     return BEM_OK;
 }
 
@@ -235,6 +270,7 @@ struct AsmParams {
     int64_t ld;
     int nT;
     const double* btab;   // far-field Bessel table
+    const float4* btabf;  // its J0, Y0 part as double-float pairs
     unsigned long long* qpts;   // Gauss points of separated pairs (accumulated)
     SeriesCoef sc;
 };
@@ -463,6 +499,251 @@ __device__ __forceinline__ void tile_of(int L, int nT, int& ti, int& tj) {
     tj = ti + d;
 }
 
+// ---------------------------------------------------------------------------------------
+// Double-float arithmetic for the S/N far field.  GB300 issues FP32 at 64x its FP64 rate,
+// so the separated pairs -- nearly all of the N^2/2 pair integrals -- are computed with
+// unevaluated sums hi + lo of two floats (about 48 significant bits): Dekker's product via
+// fmaf and Knuth's two-sum.  The _rn intrinsics keep the compiler from contracting or
+// reassociating the error terms.  Accuracy is relative to the operands' magnitudes, which
+// is what the entry tolerance (relative to max |S|, max |N|) asks for.
+// ---------------------------------------------------------------------------------------
+struct dfl { float hi, lo; };
+struct cdfl { dfl re, im; };
+
+__device__ __forceinline__ dfl dfl_mk(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ dfl dfl_from(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double dfl_to(dfl a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfl dfl_qts(float s, float e) {    // |s| >= |e|
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return dfl_qts(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl dfl_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl dfl_sub(dfl a, dfl b) { return dfl_add(a, dfl_neg(b)); }
+__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return dfl_qts(p, e);
+}
+// a * b + c
+__device__ __forceinline__ dfl dfl_fma(dfl a, dfl b, dfl c) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = fmaf(a.hi, b.hi, -p);
+    pe = fmaf(a.hi, b.lo, pe);
+    pe = fmaf(a.lo, b.hi, pe);
+    const float s = __fadd_rn(p, c.hi);
+    const float bb = __fsub_rn(s, p);
+    const float e = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.hi, bb));
+    return dfl_qts(s, __fadd_rn(e, __fadd_rn(pe, c.lo)));
+}
+__device__ __forceinline__ dfl dfl_scale(dfl a, float p2) { return {a.hi * p2, a.lo * p2}; }   // p2 a power of 2
+__device__ __forceinline__ cdfl cdfl_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+__device__ __forceinline__ cdfl cdfl_add(cdfl a, cdfl b) { return {dfl_add(a.re, b.re), dfl_add(a.im, b.im)}; }
+__device__ __forceinline__ cdfl cdfl_fma_real(dfl w, cdfl g, cdfl acc) {   // w g + acc
+    return {dfl_fma(w, g.re, acc.re), dfl_fma(w, g.im, acc.im)};
+}
+__device__ __forceinline__ cdfl cdfl_from(cplx z) { return {dfl_from(z.x), dfl_from(z.y)}; }
+__device__ __forceinline__ cplx cdfl_to(cdfl z) { return cmk(dfl_to(z.re), dfl_to(z.im)); }
+__device__ __forceinline__ float4 cdfl_pack(cdfl z) { return make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo); }
+__device__ __forceinline__ cdfl cdfl_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+
+// J0(z), Y0(z) at u = z^2 from the double-float table (FP64 routines outside it)
+__device__ __forceinline__ void bessel_u_df(const float4* __restrict__ tab, dfl u, dfl& J0, dfl& Y0) {
+    const float zf = sqrtf(u.hi);
+    int i;
+    if (zf < (float)BTAB_ZLIN) {
+        const int bits = __float_as_int(zf);
+        i = (((bits >> 23) & 255) - 127 - BTAB_LOG_EMIN) * 8 + ((bits >> 20) & 7);
+    } else {
+        i = BTAB_NLOG + (int)((zf - (float)BTAB_ZLIN) * (float)(1.0 / BTAB_W));
+    }
+    if (i < 0 || i >= BTAB_NINT) {
+        const Bessel01 b = bessel01<false>(sqrt(dfl_to(u)));
+        J0 = dfl_from(b.J0);
+        Y0 = dfl_from(b.Y0);
+        return;
+    }
+    const float4* c = tab + (size_t)i * (BTAB_DF_STRIDE / 4);
+    const float4 h = __ldg(c);
+    const dfl t = dfl_mul(dfl_sub(u, dfl{h.x, h.y}), dfl{h.z, h.w});
+    float4 cc = __ldg(c + BTAB_NC);
+    dfl rJ = {cc.x, cc.y}, rY = {cc.z, cc.w};
+#pragma unroll
+    for (int j = BTAB_NC - 2; j >= 0; --j) {
+        cc = __ldg(c + 1 + j);
+        rJ = dfl_fma(rJ, t, dfl{cc.x, cc.y});
+        rY = dfl_fma(rY, t, dfl{cc.z, cc.w});
+    }
+    J0 = rJ;
+    Y0 = rY;
+}
+
+// Separated pair (S/N only), q x q tensor Gauss-Legendre in double-float.  b = y_f(0) -
+// x_e(0), ue = h_e t_e, vf = h_f t_f; returns A_ab with I_ab = h_e h_f A_ab.  The sum over
+// the f-nodes runs first (two row sums R_b), then the e-node weights multiply them.
+__device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, dfl vfy, dfl k2,
+                              const float4* __restrict__ tab, cdfl A[4]) {
+    const int o = gl_off(q);
+    A[0] = A[1] = A[2] = A[3] = cdfl_zero();
+    for (int i = 0; i < q; ++i) {
+        const dfl s = dfl_mk(c_gx_df[o + i]);
+        const dfl cx = dfl_sub(bx, dfl_mul(s, uex)), cy = dfl_sub(by, dfl_mul(s, uey));
+        cdfl R0 = cdfl_zero(), R1 = cdfl_zero();
+        for (int j = 0; j < q; ++j) {
+            const dfl t = dfl_mk(c_gx_df[o + j]);
+            const dfl dx = dfl_fma(t, vfx, cx), dy = dfl_fma(t, vfy, cy);
+            const dfl r2 = dfl_fma(dx, dx, dfl_mul(dy, dy));
+            dfl J0, Y0;
+            bessel_u_df(tab, dfl_mul(k2, r2), J0, Y0);
+            const cdfl g = {dfl_scale(Y0, -0.25f), dfl_scale(J0, 0.25f)};   // (i/4) (J0 + i Y0)
+            R0 = cdfl_fma_real(dfl_mk(c_gw0_df[o + j]), g, R0);
+            R1 = cdfl_fma_real(dfl_mk(c_gw1_df[o + j]), g, R1);
+        }
+        const dfl w0 = dfl_mk(c_gw0_df[o + i]), w1 = dfl_mk(c_gw1_df[o + i]);
+        A[0] = cdfl_fma_real(w0, R0, A[0]);
+        A[1] = cdfl_fma_real(w0, R1, A[1]);
+        A[2] = cdfl_fma_real(w1, R0, A[2]);
+        A[3] = cdfl_fma_real(w1, R1, A[3]);
+    }
+}
+
+// self and adjacent pairs in FP64 (closed forms), returned as double-float
+__device__ __noinline__ void near_pair_df(int e, int f, const AsmParams& p, cdfl I[4], cdfl& M0) {
+    const SegV se = load_seg(p.seg, p.N, e), sf = load_seg(p.seg, p.N, f);
+    cplx Id[4], Jd[4], Jtd[4];
+    unsigned unused = 0;
+    pair_moments<false>(e, f, se, sf, p, Id, Jd, Jtd, unused);
+    const double ihh = 1.0 / (se.h * sf.h);
+    const cplx m = cscale(cadd(cadd(Id[0], Id[1]), cadd(Id[2], Id[3])), ihh);
+    for (int c = 0; c < 4; ++c) I[c] = cdfl_from(Id[c]);
+    M0 = cdfl_from(m);
+}
+
+// S and N tiles with double-float far pairs.  Same decomposition as k_assemble below: one
+// CTA per T x T vertex tile of the upper triangle, (T+1)^2 segment pairs staged in shared
+// memory, entries combined and written with their mirror.  Segment positions are kept as
+// offsets from the tile's first segment on each side, plus one tile offset, so nearby
+// pairs keep their relative geometry to double-float precision.  Self and adjacent pairs
+// use the FP64 closed forms.
+template <int T>
+__global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
+    int ti, tj;
+    tile_of((int)blockIdx.x, p.nT, ti, tj);
+    constexpr int TP = T + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* sI = reinterpret_cast<float4*>(smem_raw);               // TP*TP*4 complex df
+    float4* sM = sI + TP * TP * 4;                                   // TP*TP: sum_ab I / (h_e h_f)
+    float2* sND = reinterpret_cast<float2*>(sM + TP * TP);          // TP*TP: k^2 nu_e . nu_f
+    float2* gE = sND + TP * TP;                                      // 7*TP: ox, oy, ux, uy, tx, ty, h
+    float2* gF = gE + 7 * TP;
+    __shared__ float2 sOff[2];
+    const int N = p.N;
+    const int i0 = ti * T, j0 = tj * T;
+    const int e0 = (i0 - 1 + N) % N, f0 = (j0 - 1 + N) % N;
+    const double ex0 = p.seg[e0], ey0 = p.seg[N + e0], fx0 = p.seg[f0], fy0 = p.seg[N + f0];
+    if (threadIdx.x == 0) {
+        const dfl ox = dfl_from(fx0 - ex0), oy = dfl_from(fy0 - ey0);
+        sOff[0] = make_float2(ox.hi, ox.lo);
+        sOff[1] = make_float2(oy.hi, oy.lo);
+    }
+    for (int t = threadIdx.x; t < 2 * TP; t += blockDim.x) {
+        const bool isE = t < TP;
+        const int l = isE ? t : t - TP;
+        const int s = ((isE ? i0 : j0) - 1 + l + N) % N;
+        const SegV a = load_seg(p.seg, N, s);
+        float2* g = isE ? gE : gF;
+        const double vals[7] = {a.x0 - (isE ? ex0 : fx0), a.y0 - (isE ? ey0 : fy0), a.h * a.tx, a.h * a.ty,
+                                a.tx, a.ty, a.h};
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            const dfl v = dfl_from(vals[c]);
+            g[c * TP + l] = make_float2(v.hi, v.lo);
+        }
+    }
+    __syncthreads();
+    const dfl k2 = dfl_from(p.k * p.k);
+    const dfl offx = dfl_mk(sOff[0]), offy = dfl_mk(sOff[1]);
+    unsigned npts = 0;
+    for (int pi = threadIdx.x; pi < TP * TP; pi += blockDim.x) {
+        const int el = pi / TP, fl = pi % TP;
+        if (i0 - 1 + el >= N || j0 - 1 + fl >= N) continue;
+        const int e = (i0 - 1 + el + N) % N, f = (j0 - 1 + fl + N) % N;
+        int d = e - f; if (d < 0) d = -d;
+        const int cyc = min(d, N - d);
+        const dfl etx = dfl_mk(gE[4 * TP + el]), ety = dfl_mk(gE[5 * TP + el]);
+        const dfl ftx = dfl_mk(gF[4 * TP + fl]), fty = dfl_mk(gF[5 * TP + fl]);
+        const dfl nd = dfl_mul(k2, dfl_fma(etx, ftx, dfl_mul(ety, fty)));   // nu_e . nu_f = t_e . t_f
+        cdfl I[4], M0;
+        if (cyc <= 1) {
+            near_pair_df(e, f, p, I, M0);
+        } else {
+            // y_f(0) - x_e(0) = (f offset) - (e offset) + tile offset
+            const dfl bx = dfl_add(dfl_sub(dfl_mk(gF[fl]), dfl_mk(gE[el])), offx);
+            const dfl by = dfl_add(dfl_sub(dfl_mk(gF[TP + fl]), dfl_mk(gE[TP + el])), offy);
+            const dfl uex = dfl_mk(gE[2 * TP + el]), uey = dfl_mk(gE[3 * TP + el]);
+            const dfl vfx = dfl_mk(gF[2 * TP + fl]), vfy = dfl_mk(gF[3 * TP + fl]);
+            const float he = gE[6 * TP + el].x, hf = gF[6 * TP + fl].x;
+            const float mx = bx.hi + 0.5f * (vfx.hi - uex.hi), my = by.hi + 0.5f * (vfy.hi - uey.hi);
+            const float hmax = fmaxf(he, hf);
+            const float gap = fmaxf(sqrtf(mx * mx + my * my) - 0.5f * (he + hf), 0.0f);
+            const int q = q_for_gap(gap / hmax, (float)p.k * (gap + hmax));
+            npts += (unsigned)(q * q);
+            cdfl A[4];
+            pair_gauss_df(q, bx, by, uex, uey, vfx, vfy, k2, p.btabf, A);
+            const dfl hh = dfl_mul(dfl_mk(gE[6 * TP + el]), dfl_mk(gF[6 * TP + fl]));
+            for (int c = 0; c < 4; ++c) I[c] = {dfl_mul(hh, A[c].re), dfl_mul(hh, A[c].im)};
+            M0 = cdfl_add(cdfl_add(A[0], A[1]), cdfl_add(A[2], A[3]));
+        }
+        for (int c = 0; c < 4; ++c) sI[pi * 4 + c] = cdfl_pack(I[c]);
+        sM[pi] = cdfl_pack(M0);
+        sND[pi] = make_float2(nd.hi, nd.lo);
+    }
+    for (int o = 16; o > 0; o >>= 1) npts += __shfl_xor_sync(0xffffffffu, npts, o);
+    if ((threadIdx.x & 31) == 0 && npts) atomicAdd(p.qpts, (unsigned long long)npts);
+    __syncthreads();
+    const bool mirror = (ti != tj);
+    for (int pass = 0; pass < (mirror ? 2 : 1); ++pass) {
+        for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+            int il, jl;
+            if (pass == 0) { il = idx % T; jl = idx / T; } else { jl = idx % T; il = idx / T; }
+            const int i = i0 + il, j = j0 + jl;
+            if (i >= N || j >= N) continue;
+            cdfl sv = cdfl_zero(), wv = cdfl_zero();
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int el = il + 1 - a;
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const int fl = jl + 1 - b;
+                    const int pi = el * TP + fl;
+                    const cdfl Iab = cdfl_unpack(sI[pi * 4 + a * 2 + b]);
+                    sv = cdfl_add(sv, Iab);
+                    if (p.W) {
+                        // sigma_a sigma_b sum I/(h_e h_f) - k^2 (nu_e . nu_f) I_ab
+                        cdfl M0 = cdfl_unpack(sM[pi]);
+                        if (a != b) M0 = {dfl_neg(M0.re), dfl_neg(M0.im)};
+                        const dfl nnd = dfl_neg(dfl_mk(sND[pi]));
+                        wv = cdfl_add(wv, cdfl_fma_real(nnd, Iab, M0));
+                    }
+                }
+            }
+            const int64_t off = (pass == 0) ? ((int64_t)i + (int64_t)j * p.ld) : ((int64_t)j + (int64_t)i * p.ld);
+            if (p.S) p.S[off] = cdfl_to(sv);
+            if (p.W) p.W[off] = cdfl_to(wv);
+        }
+    }
+}
+
 template <int T, bool WD>
 __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
     int ti, tj;
@@ -581,6 +862,19 @@ static bem_status run_assemble(bem_ctx* h, AsmParams& p) {
     return BEM_OK;
 }
 
+template <int T>
+static bem_status run_assemble_sn(bem_ctx* h, AsmParams& p) {
+    constexpr int TP = T + 1;
+    const size_t smem = (size_t)TP * TP * (4 * sizeof(float4) + sizeof(float4) + sizeof(float2)) +
+                        (size_t)14 * TP * sizeof(float2);
+    BEM_CUDA(h, cudaFuncSetAttribute(k_assemble_sn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    p.nT = (p.N + T - 1) / T;
+    const unsigned grid = (unsigned)((int64_t)p.nT * (p.nT + 1) / 2);
+    BEM_TIMED(h, "k_assemble", (k_assemble_sn<T><<<grid, 256, smem, h->stream>>>(p)));
+    BEM_LAUNCH(h, "k_assemble");
+    return BEM_OK;
+}
+
 bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     AsmParams p;
     p.N = (int)h->N;
@@ -593,10 +887,10 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     p.qpts = h->qpts;
     BEM_CUDA(h, cudaMemsetAsync(h->qpts, 0, sizeof(unsigned long long), h->stream));
     series_coefficients(h->k, 2.0 * h->hbar, &p.sc);
-    bem_status st = bessel_table(h, &p.btab);
+    bem_status st = bessel_table(h, &p.btab, &p.btabf);
     if (st != BEM_OK) return st;
     if (ops & BEM_OP_D) return run_assemble<15, true>(h, p);
-    return run_assemble<31, false>(h, p);
+    return run_assemble_sn<31>(h, p);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -165,6 +165,9 @@ __device__ __forceinline__ Bessel01 bessel01(double z) {
 #define BTAB_ZMAX 64.0
 #define BTAB_NINT (BTAB_NLOG + 240)
 #define BTAB_STRIDE (2 + 4 * BTAB_NC)
+// double-float copy for the S/N far field: per interval 4 + 4 * BTAB_NC floats,
+// [u_mid (hi, lo), 1/u_half (hi, lo)], then per power j: [J0_j (hi, lo), Y0_j (hi, lo)]
+#define BTAB_DF_STRIDE (4 + 4 * BTAB_NC)
 
 struct BesselU { double J0, Y0, J1z, Y1z; };   // J1z = J1(z)/z, Y1z = Y1(z)/z
 
