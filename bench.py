@@ -184,6 +184,27 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
+# ----------------------------------------------------------------------------- replicas
+def replica_seed(rank: int) -> int:
+    """Each rank solves its own star (independent problems, no data-path collective)."""
+    return rank
+
+
+def reduce_max(x: float, dist=None, device=None) -> float:
+    """Maximum of a per-rank time over all ranks (identity on one rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 # ----------------------------------------------------------------------------- main
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, timed on the host cores."""
@@ -237,7 +258,7 @@ def main():
     torch.cuda.set_device(dev)
     from paper_2210_08580_gb300 import bem, inputs as I
 
-    verts_np, _, _ = I.equal_chord_mesh(I.random_star(rank), args.N)
+    verts_np, _, _ = I.equal_chord_mesh(I.random_star(replica_seed(rank)), args.N)
     ang_np = I.planewave_angles(args.nrhs)
     verts = torch.from_numpy(verts_np).to(dev)
     ang = torch.from_numpy(ang_np).to(dev)
@@ -280,12 +301,9 @@ def main():
     rep = s.timing_report()
     s.timing(False)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dist, dev)
     ms_step = ms / args.steps
-    value = args.nrhs * world / (ms_step / 1000.0)
+    value = job_value(args.nrhs, world, ms_step / 1000.0)
 
     # ---- phase split of one extra instrumented step (factor vs RHS vs solve)
     def timed(fn):
@@ -317,12 +335,8 @@ def main():
             step(vd, ad)
             xh.copy_(x, non_blocking=True)
         barrier()
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        if dist is not None:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": args.nrhs * world / e2e_s, "unit": "RHS/s",
+        e2e_s = reduce_max((time.perf_counter() - t0) / args.steps, dist, dev)
+        e2e = {"value": job_value(args.nrhs, world, e2e_s), "unit": "RHS/s",
                "h2d_bytes_per_step": int(vh.numel() * 8 + ah.numel() * 8),
                "d2h_bytes_per_step": int(xh.numel() * 16)}
 

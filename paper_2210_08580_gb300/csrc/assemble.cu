@@ -515,7 +515,16 @@ __device__ __forceinline__ dfl dfl_from(double x) {
     const float h = __double2float_rn(x);
     return {h, __double2float_rn(x - (double)h)};
 }
-__device__ __forceinline__ double dfl_to(dfl a) { return (double)a.hi + (double)a.lo; }
+// exact float -> double by moving the bit fields (the FP64 pipe's conversion is as slow as
+// its arithmetic); subnormal floats become zero
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 255u;
+    if (e == 0u) return 0.0;
+    const unsigned hiw = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hiw, (int)(u << 29));
+}
+__device__ __forceinline__ double dfl_to(dfl a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
 __device__ __forceinline__ dfl dfl_qts(float s, float e) {    // |s| >= |e|
     const float h = __fadd_rn(s, e);
     return {h, __fsub_rn(e, __fsub_rn(h, s))};

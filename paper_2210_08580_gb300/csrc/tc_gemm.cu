@@ -40,6 +40,7 @@
 #define TC_BK 32
 #define TC_STAGES 2
 #define TC_CHUNK_KB 8               // K' chunk of 8 x 32 = 256 between TMEM flushes
+#define TC_SPLIT_TARGET 152         // CTAs to aim for when splitting K' (one per SM)
 #define TC_NACC 4                   // TMEM accumulators (4 x 128 columns = all 512)
 #define TC_SMAX 7
 #define TC_W_BAND 64                // |i - j| (cyclic) <= band of N applied in FP64
@@ -145,6 +146,8 @@ struct TcGemmArgs {
     int transposed;          // 0: out[i + j ldo], 1: out[j + i ldo]
     double alpha, beta;      // out = alpha C + beta out
     int* err;
+    int kps;                 // K' blocks per split (blockIdx.y); == nkb without split
+    double2* part;           // split partials [split][j][i] (M x m each), or null
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -167,7 +170,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int n_tiles = (p.Ncols + TC_BN - 1) / TC_BN;
     const int m0 = (blockIdx.x / n_tiles) * TC_BM;
     const int n0 = (blockIdx.x % n_tiles) * TC_BN;
-    const int nchunks = (p.nkb + TC_CHUNK_KB - 1) / TC_CHUNK_KB;
+    // this CTA's K' range (split-K over blockIdx.y)
+    const int kb0 = blockIdx.y * p.kps;
+    const int nkb = min(p.nkb - kb0, p.kps);
+    const int nchunks = (nkb + TC_CHUNK_KB - 1) / TC_CHUNK_KB;
 
     if (threadIdx.x == 0) {
         mbar_init(&full[0], 1); mbar_init(&full[1], 1);
@@ -190,20 +196,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             // ------------------------------------------------------------ TMA producer
             int kb_issued = 0;
-            for (int kb = 0; kb < p.nkb; ++kb) {
+            for (int kb = 0; kb < nkb; ++kb) {
                 const int st = kb & 1;
                 const uint32_t use = (uint32_t)(kb >> 1);
                 if (!mbar_wait(&empty[st], (use & 1u) ^ 1u, p.err)) break;
                 unsigned char* base = smem + st * stage_bytes;
                 mbar_expect_tx(&full[st], (uint32_t)stage_bytes);
                 for (int s = 0; s < S; ++s)
-                    tma_load_3d(base + s * TC_TILE_BYTES, &mapA, &full[st], kb * TC_BK, m0, s);
+                    tma_load_3d(base + s * TC_TILE_BYTES, &mapA, &full[st], (kb0 + kb) * TC_BK, m0, s);
                 for (int t = 0; t < S; ++t)
-                    tma_load_3d(base + (S + t) * TC_TILE_BYTES, &mapB, &full[st], kb * TC_BK, n0, t);
+                    tma_load_3d(base + (S + t) * TC_TILE_BYTES, &mapB, &full[st], (kb0 + kb) * TC_BK, n0, t);
                 kb_issued = kb + 1;
             }
             // on an early exit, let the copies already issued land before the CTA ends
-            if (kb_issued > 0 && kb_issued < p.nkb) {
+            if (kb_issued > 0 && kb_issued < nkb) {
                 const int kb = kb_issued - 1;
                 mbar_wait(&full[kb & 1], (uint32_t)((kb >> 1) & 1), p.err);
             }
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (c > 0 && !mbar_wait(acc_empty, (uint32_t)((c - 1) & 1), p.err)) { ok = false; break; }
                 tc_fence_after();
                 uint32_t used0 = 0u, used1 = 0u, used2 = 0u, used3 = 0u;   // written in this chunk
-                const int kb_end = min(p.nkb, (c + 1) * TC_CHUNK_KB);
+                const int kb_end = min(nkb, (c + 1) * TC_CHUNK_KB);
                 for (int kb = c * TC_CHUNK_KB; kb < kb_end; ++kb) {
                     const int st = kb & 1;
                     if (!mbar_wait(&full[st], (uint32_t)((kb >> 1) & 1), p.err)) { ok = false; break; }
@@ -303,6 +309,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const double re = ((double)a.x + (double)a.y) * sc;
                 const double im = ((double)b.x + (double)b.y) * sc;
                 const int j = gc >> 1;
+                if (p.part) {
+                    p.part[((int64_t)blockIdx.y * (p.Ncols >> 1) + j) * p.M + gi] = make_double2(re, im);
+                    continue;
+                }
                 double2* o = p.transposed ? (p.out + (int64_t)j + (int64_t)gi * p.ldo)
                                           : (p.out + (int64_t)gi + (int64_t)j * p.ldo);
                 double2 val = make_double2(p.alpha * re, p.alpha * im);
@@ -336,26 +346,27 @@ __device__ __forceinline__ bool in_band(int64_t i, int64_t k, int64_t K, int ban
     return d <= band;
 }
 
+// Exponents are taken from the IEEE exponent fields with integer operations (GB300's FP64
+// pipe is 1/64 of its FP32 rate): for a normal double with biased exponent E, frexp gives
+// E - 1022, and the largest magnitude of a row carries its largest exponent field.
+__device__ __forceinline__ int exp_field(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
+
 __global__ void k_exp_rows(const void* src, int is_real, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k, int band,
                            int* e) {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (i >= M) return;
-    double mx = 0.0;
+    int mx = 0;
     for (int64_t k = threadIdx.x & 31; k < K; k += 32) {
         if (in_band(i, k, K, band)) continue;
         if (is_real) {
-            mx = fmax(mx, fabs(((const double*)src)[i * sa_i + k * sa_k]));
+            mx = max(mx, exp_field(((const double*)src)[i * sa_i + k * sa_k]));
         } else {
             const double2 v = ((const double2*)src)[i * sa_i + k * sa_k];
-            mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+            mx = max(mx, max(exp_field(v.x), exp_field(v.y)));
         }
     }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) {
-        int ex = 0;
-        if (mx > 0.0) frexp(mx, &ex);
-        e[i] = ex;
-    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) e[i] = mx ? mx - 1022 : 0;
 }
 
 // B column exponents: B_op[k, j] = src[k*sb_k + j*sb_j] (complex, or real when is_real);
@@ -363,33 +374,38 @@ __global__ void k_exp_rows(const void* src, int is_real, int64_t M, int64_t K, i
 __global__ void k_exp_cols(const void* src, int is_real, int64_t K, int64_t m, int64_t sb_k, int64_t sb_j, int* f) {
     const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (j >= m) return;
-    double mx = 0.0;
+    int mx = 0;
     for (int64_t k = threadIdx.x & 31; k < K; k += 32) {
         if (is_real) {
-            mx = fmax(mx, fabs(((const double*)src)[k * sb_k + j * sb_j]));
+            mx = max(mx, exp_field(((const double*)src)[k * sb_k + j * sb_j]));
         } else {
             const double2 v = ((const double2*)src)[k * sb_k + j * sb_j];
-            mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+            mx = max(mx, max(exp_field(v.x), exp_field(v.y)));
         }
     }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mx = __reduce_max_sync(0xffffffffu, mx);
     if ((threadIdx.x & 31) == 0) {
-        int ex = 0;
-        if (mx > 0.0) frexp(mx, &ex);
+        const int ex = mx ? mx - 1022 : 0;
         f[2 * j] = ex;
         f[2 * j + 1] = ex;
     }
 }
 
-// 2^p as a double from its exponent bits (p in the normal range)
-__device__ __forceinline__ double pow2i(int p) { return __longlong_as_double((long long)(1023 + p) << 52); }
-
-// val 2^-e in (-1, 1) -> S slices: X = round(val 2^{7S - e}) (exact scaling and one
-// rounding), then balanced base-128 digits from the least significant up: d in [-64, 63]
-// for s >= 1 and the leading |d_0| <= 128; slice s stores d_s 2^{-7s} (exact in bf16).
-// digits of one value, returned as the floats d_s 2^{-7s}
+// val 2^-e in (-1, 1) -> S slices: X = round(val 2^{7S - e}) (one rounding, half away from
+// zero), then balanced base-128 digits from the least significant up: d in [-64, 63] for
+// s >= 1 and the leading |d_0| <= 128; slice s stores d_s 2^{-7s} (exact in bf16).  X is
+// formed from the significand and exponent fields with integer shifts: |val| < 2^e makes
+// the right shift 1075 + e - 7S - E at least 53 - 7S > 0.  Zeros and subnormals give 0.
 __device__ __forceinline__ void split_digits(double val, int e, int S, float* d) {
-    long long X = __double2ll_rn(val * pow2i(7 * S - e));
+    const long long b = __double_as_longlong(val);
+    const int E = (int)((b >> 52) & 0x7FF);
+    const int sh = 1075 + e - 7 * S - E;
+    long long X = 0;
+    if (E != 0 && sh < 63) {
+        const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+        X = (m + (1LL << (sh - 1))) >> sh;
+        if (b < 0) X = -X;
+    }
 #pragma unroll
     for (int s = TC_SMAX - 1; s >= 1; --s) {
         if (s >= S) { d[s] = 0.f; continue; }
@@ -489,6 +505,8 @@ struct TcState {
     TcOperand opVh, opU;              // Woodbury factors
     TcOperand bbuf;                   // B operand scratch (reused)
     TcOperand tmpA;                   // A operand scratch (reused)
+    double2* part = nullptr;          // split-K partials
+    size_t part_cap = 0;
 };
 
 static TcState* tcs(bem_ctx* h) {
@@ -572,6 +590,28 @@ static size_t gemm_smem(int S) {
 }
 
 // out = alpha (A B) + beta out for sliced operands (complex result, M x m)
+// out = alpha sum_s part[s] + beta out over the M x m split partials
+__global__ void k_splitk_reduce(const double2* __restrict__ part, int splits, int M, int m, double2* out, int64_t ldo,
+                                int transposed, double alpha, double beta) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)M * m) return;
+    const int i = (int)(idx % M), j = (int)(idx / M);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < splits; ++s) {
+        const double2 v = part[(int64_t)s * M * m + idx];
+        re += v.x;
+        im += v.y;
+    }
+    double2* o = transposed ? (out + (int64_t)j + (int64_t)i * ldo) : (out + (int64_t)i + (int64_t)j * ldo);
+    double2 val = make_double2(alpha * re, alpha * im);
+    if (beta != 0.0) {
+        const double2 old = *o;
+        val.x += beta * old.x;
+        val.y += beta * old.y;
+    }
+    *o = val;
+}
+
 static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cplx* out, int64_t ldo, int transposed,
                           double alpha, double beta, const char* tag) {
     TcState* t = tcs(h);
@@ -589,11 +629,40 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     p.alpha = alpha;
     p.beta = beta;
     p.err = h->dev_err;
+    p.kps = p.nkb;
+    p.part = nullptr;
     const size_t smem = gemm_smem(t->S);
     BEM_CUDA(h, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int mt = (p.M + TC_BM - 1) / TC_BM, nt = (p.Ncols + TC_BN - 1) / TC_BN;
-    BEM_TIMED(h, tag, (k_tc_gemm<<<(unsigned)(mt * nt), TC_THREADS, smem, h->stream>>>(A.map, B.map, p)));
+    // skinny outputs (r x nrhs, r x r) fill few SMs: split K' so that about one wave of
+    // CTAs runs, each split at least a few accumulation chunks long
+    int splits = 1;
+    if (mt * nt < TC_SPLIT_TARGET && p.nkb >= 4 * TC_CHUNK_KB) {
+        splits = std::min((TC_SPLIT_TARGET + mt * nt - 1) / (mt * nt), p.nkb / (4 * TC_CHUNK_KB));
+        if (splits > 1) {
+            p.kps = ((p.nkb + splits - 1) / splits + TC_CHUNK_KB - 1) / TC_CHUNK_KB * TC_CHUNK_KB;
+            splits = (p.nkb + p.kps - 1) / p.kps;
+        }
+    }
+    const int m = p.Ncols / 2;
+    if (splits > 1) {
+        const size_t need = (size_t)splits * p.M * m * sizeof(double2);
+        if (need > t->part_cap) {
+            if (t->part) { cudaStreamSynchronize(h->stream); cudaFree(t->part); t->part = nullptr; t->part_cap = 0; }
+            BEM_CUDA(h, cudaMalloc((void**)&t->part, need));
+            t->part_cap = need;
+        }
+        p.part = t->part;
+    }
+    dim3 grid((unsigned)(mt * nt), (unsigned)splits);
+    BEM_TIMED(h, tag, (k_tc_gemm<<<grid, TC_THREADS, smem, h->stream>>>(A.map, B.map, p)));
     BEM_LAUNCH(h, "k_tc_gemm");
+    if (splits > 1) {
+        const int64_t n = (int64_t)p.M * m;
+        BEM_TIMED(h, "k_splitk_reduce", (k_splitk_reduce<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+                                            p.part, splits, p.M, m, out, ldo, transposed, alpha, beta)));
+        BEM_LAUNCH(h, "k_splitk_reduce");
+    }
     return BEM_OK;
 }
 
@@ -783,6 +852,7 @@ void tc_destroy(bem_ctx* h) {
     TcState* t = (TcState*)h->tc;
     free_op(t->opS); free_op(t->opW); free_op(t->opD); free_op(t->opVh); free_op(t->opU); free_op(t->bbuf);
     free_op(t->tmpA);
+    if (t->part) cudaFree(t->part);
     delete t;
     h->tc = nullptr;
 }
