@@ -272,6 +272,7 @@ struct AsmParams {
     const double* btab;   // far-field Bessel table
     const float4* btabf;  // its J0, Y0 part as double-float pairs
     unsigned long long* qpts;   // Gauss points of separated pairs (accumulated)
+    const cplx* near;     // self / adjacent pair table (k_near_pairs)
     SeriesCoef sc;
 };
 
@@ -315,75 +316,135 @@ __device__ void pair_self(double h, const SeriesCoef& sc, cplx I[4]) {
 
 // adjacent pair, f follows e (shared vertex P = end of e = start of f).  u = sigma/h_e
 // (x = P - sigma t_e), v = tau/h_f (y = P + tau t_f); triangles v <= u and u < v in Duffy
-// coordinates (rho, w), r = rho R(w).  The rho integrals are closed form, w by Gauss.
+// coordinates (rho, w), r = rho R(w).  The rho integrals are closed form, w by 16-point
+// Gauss.  One call gives the contribution of one node (triangle tri, Gauss node iw): the
+// 32 nodes map onto the lanes of a warp (k_near_pairs).
 template <bool WD>
-__device__ void pair_adjacent_fwd(const SegV& e, const SegV& f, const SeriesCoef& sc, cplx I[4],
-                                  cplx J[4], cplx Jt[4]) {
+__device__ void adjacent_node(const SegV& e, const SegV& f, const SeriesCoef& sc, int tri, int iw, cplx I[4],
+                              cplx J[4], cplx Jt[4]) {
     const int qw = 16;
-    const double* wx = c_glx + gl_off(qw);
-    const double* ww = c_glw + gl_off(qw);
     const double nfx = f.ty, nfy = -f.tx, nex = e.ty, ney = -e.tx;
     const double cef = e.tx * nfx + e.ty * nfy;        // t_e . nu_f
     const double cfe = -(f.tx * nex + f.ty * ney);     // -t_f . nu_e
-    for (int q = 0; q < 4; ++q) { I[q] = cmk(0, 0); if (WD) { J[q] = cmk(0, 0); Jt[q] = cmk(0, 0); } }
     const double hh = e.h * f.h;
-    for (int tri = 0; tri < 2; ++tri) {
-        for (int iw = 0; iw < qw; ++iw) {
-            const double w = wx[iw], wt = ww[iw] * hh;
-            double Rx, Ry;
-            // polynomial coefficients (c0, c1, c2) in rho of lambda_a^e lambda_b^f
-            double c[4][3];
-            double sfac, tfac;
-            if (tri == 0) {
-                Rx = e.h * e.tx + w * f.h * f.tx; Ry = e.h * e.ty + w * f.h * f.ty;
-                c[0][0] = 0; c[0][1] = 1; c[0][2] = -w;            // (0,0)
-                c[1][0] = 0; c[1][1] = 0; c[1][2] = w;             // (0,1)
-                c[2][0] = 1; c[2][1] = -(1 + w); c[2][2] = w;      // (1,0)
-                c[3][0] = 0; c[3][1] = w; c[3][2] = -w;            // (1,1)
-                sfac = 1.0; tfac = w;
-            } else {
-                Rx = w * e.h * e.tx + f.h * f.tx; Ry = w * e.h * e.ty + f.h * f.ty;
-                c[0][0] = 0; c[0][1] = w; c[0][2] = -w;
-                c[1][0] = 0; c[1][1] = 0; c[1][2] = w;
-                c[2][0] = 1; c[2][1] = -(1 + w); c[2][2] = w;
-                c[3][0] = 0; c[3][1] = 1; c[3][2] = -w;
-                sfac = w; tfac = 1.0;
-            }
-            const double R2 = Rx * Rx + Ry * Ry;
-            const double lnR = 0.5 * log(R2);
-            cplx Gj[3] = {cmk(0, 0), cmk(0, 0), cmk(0, 0)};
-            cplx Hj[3] = {cmk(0, 0), cmk(0, 0), cmk(0, 0)};
-            double R2m = 1.0;
-            for (int m = 0; m < sc.nm; ++m) {
-                for (int j = 0; j < 3; ++j) {
-                    const double a = 2.0 + j + 2.0 * m;
-                    Gj[j].x += R2m * ((sc.A[m].x + sc.B[m] * lnR) / a - sc.B[m] / (a * a));
-                    Gj[j].y += R2m * (sc.A[m].y / a);
-                    if (WD) {
-                        const double b = 3.0 + j + 2.0 * m;
-                        Hj[j].x += R2m * ((sc.E[m].x + sc.F[m] * lnR) / b - sc.F[m] / (b * b));
-                        Hj[j].y += R2m * (sc.E[m].y / b);
-                    }
-                }
-                R2m *= R2;
-            }
-            const double Hs = -1.0 / (2.0 * BEM_PI * R2);
-            for (int ab = 0; ab < 4; ++ab) {
-                cplx si = cmk(0, 0);
-                for (int j = 0; j < 3; ++j) { si.x += c[ab][j] * Gj[j].x; si.y += c[ab][j] * Gj[j].y; }
-                I[ab].x += wt * si.x; I[ab].y += wt * si.y;
-                if (WD) {
-                    cplx sd = cmk(0, 0);
-                    for (int j = 0; j < 3; ++j) {
-                        sd.x += c[ab][j] * (Hs / (j + 1.0) + Hj[j].x);
-                        sd.y += c[ab][j] * Hj[j].y;
-                    }
-                    const double fJ = wt * e.h * sfac * cef, fJt = wt * f.h * tfac * cfe;
-                    J[ab].x += fJ * sd.x; J[ab].y += fJ * sd.y;
-                    Jt[ab].x += fJt * sd.x; Jt[ab].y += fJt * sd.y;
-                }
+    const double w = c_glx[gl_off(qw) + iw], wt = c_glw[gl_off(qw) + iw] * hh;
+    double Rx, Ry;
+    // polynomial coefficients (c0, c1, c2) in rho of lambda_a^e lambda_b^f
+    double c[4][3];
+    double sfac, tfac;
+    if (tri == 0) {
+        Rx = e.h * e.tx + w * f.h * f.tx; Ry = e.h * e.ty + w * f.h * f.ty;
+        c[0][0] = 0; c[0][1] = 1; c[0][2] = -w;            // (0,0)
+        c[1][0] = 0; c[1][1] = 0; c[1][2] = w;             // (0,1)
+        c[2][0] = 1; c[2][1] = -(1 + w); c[2][2] = w;      // (1,0)
+        c[3][0] = 0; c[3][1] = w; c[3][2] = -w;            // (1,1)
+        sfac = 1.0; tfac = w;
+    } else {
+        Rx = w * e.h * e.tx + f.h * f.tx; Ry = w * e.h * e.ty + f.h * f.ty;
+        c[0][0] = 0; c[0][1] = w; c[0][2] = -w;
+        c[1][0] = 0; c[1][1] = 0; c[1][2] = w;
+        c[2][0] = 1; c[2][1] = -(1 + w); c[2][2] = w;
+        c[3][0] = 0; c[3][1] = 1; c[3][2] = -w;
+        sfac = w; tfac = 1.0;
+    }
+    const double R2 = Rx * Rx + Ry * Ry;
+    const double lnR = 0.5 * log(R2);
+    cplx Gj[3] = {cmk(0, 0), cmk(0, 0), cmk(0, 0)};
+    cplx Hj[3] = {cmk(0, 0), cmk(0, 0), cmk(0, 0)};
+    double R2m = 1.0;
+    for (int m = 0; m < sc.nm; ++m) {
+        for (int j = 0; j < 3; ++j) {
+            const double a = 2.0 + j + 2.0 * m;
+            Gj[j].x += R2m * ((sc.A[m].x + sc.B[m] * lnR) / a - sc.B[m] / (a * a));
+            Gj[j].y += R2m * (sc.A[m].y / a);
+            if (WD) {
+                const double b = 3.0 + j + 2.0 * m;
+                Hj[j].x += R2m * ((sc.E[m].x + sc.F[m] * lnR) / b - sc.F[m] / (b * b));
+                Hj[j].y += R2m * (sc.E[m].y / b);
             }
         }
+        R2m *= R2;
+    }
+    const double Hs = -1.0 / (2.0 * BEM_PI * R2);
+    for (int ab = 0; ab < 4; ++ab) {
+        cplx si = cmk(0, 0);
+        for (int j = 0; j < 3; ++j) { si.x += c[ab][j] * Gj[j].x; si.y += c[ab][j] * Gj[j].y; }
+        I[ab] = cmk(wt * si.x, wt * si.y);
+        if (WD) {
+            cplx sd = cmk(0, 0);
+            for (int j = 0; j < 3; ++j) {
+                sd.x += c[ab][j] * (Hs / (j + 1.0) + Hj[j].x);
+                sd.y += c[ab][j] * Hj[j].y;
+            }
+            const double fJ = wt * e.h * sfac * cef, fJt = wt * f.h * tfac * cfe;
+            J[ab] = cmk(fJ * sd.x, fJ * sd.y);
+            Jt[ab] = cmk(fJt * sd.x, fJt * sd.y);
+        }
+    }
+}
+
+// Self and adjacent pair integrals of every segment, one warp per segment e: lanes
+// (tri, iw) evaluate the 32 Duffy nodes of the pair (e, e+1) and are summed by shuffles;
+// lane 0 adds the closed-form self pair.  near[e * NEAR_STRIDE + ...]:
+//   [0..3] I(e,e), [4] M0(e,e), [5..8] I(e,e+1), [9] M0(e,e+1), [10..13] J(e,e+1),
+//   [14..17] Jt(e,e+1);  M0 = sum_ab I_ab / (h_e h_f) (the pair's term of N's Maue form).
+#define NEAR_STRIDE 18
+template <bool WD>
+__global__ void __launch_bounds__(256) k_near_pairs(const double* __restrict__ seg, int N, SeriesCoef sc,
+                                                    cplx* __restrict__ near) {
+    const int e = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= N) return;                  // whole warps leave together
+    const int f = (e + 1) % N;
+    const SegV se = load_seg(seg, N, e), sf = load_seg(seg, N, f);
+    cplx I[4], J[4], Jt[4];
+    adjacent_node<WD>(se, sf, sc, lane >> 4, lane & 15, I, J, Jt);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        for (int o = 16; o > 0; o >>= 1) {
+            I[q].x += __shfl_xor_sync(0xffffffffu, I[q].x, o);
+            I[q].y += __shfl_xor_sync(0xffffffffu, I[q].y, o);
+            if (WD) {
+                J[q].x += __shfl_xor_sync(0xffffffffu, J[q].x, o);
+                J[q].y += __shfl_xor_sync(0xffffffffu, J[q].y, o);
+                Jt[q].x += __shfl_xor_sync(0xffffffffu, Jt[q].x, o);
+                Jt[q].y += __shfl_xor_sync(0xffffffffu, Jt[q].y, o);
+            }
+        }
+    }
+    if (lane != 0) return;
+    cplx* out = near + (size_t)e * NEAR_STRIDE;
+    cplx Is[4];
+    pair_self(se.h, sc, Is);
+    const cplx ms = cadd(cadd(Is[0], Is[1]), cadd(Is[2], Is[3]));
+    const cplx ma = cadd(cadd(I[0], I[1]), cadd(I[2], I[3]));
+    for (int q = 0; q < 4; ++q) {
+        out[q] = Is[q];
+        out[5 + q] = I[q];
+        out[10 + q] = WD ? J[q] : cmk(0, 0);
+        out[14 + q] = WD ? Jt[q] : cmk(0, 0);
+    }
+    out[4] = cscale(ms, 1.0 / (se.h * se.h));
+    out[9] = cscale(ma, 1.0 / (se.h * sf.h));
+}
+
+// near-pair integrals from the table: cyc = 0 self, cyc = 1 adjacent in either order
+// (f = e - 1 swaps the roles of the segments: (a,b) -> (b,a), J <-> Jt)
+__device__ __forceinline__ void near_from_table(const cplx* __restrict__ near, int N, int e, int f, int cyc,
+                                                cplx I[4], cplx J[4], cplx Jt[4], cplx& M0) {
+    if (cyc == 0) {
+        const cplx* t = near + (size_t)e * NEAR_STRIDE;
+        for (int q = 0; q < 4; ++q) { I[q] = t[q]; J[q] = cmk(0, 0); Jt[q] = cmk(0, 0); }
+        M0 = t[4];
+    } else if (f == (e + 1) % N) {
+        const cplx* t = near + (size_t)e * NEAR_STRIDE;
+        for (int q = 0; q < 4; ++q) { I[q] = t[5 + q]; J[q] = t[10 + q]; Jt[q] = t[14 + q]; }
+        M0 = t[9];
+    } else {
+        const cplx* t = near + (size_t)f * NEAR_STRIDE;
+        const int sw[4] = {0, 2, 1, 3};
+        for (int q = 0; q < 4; ++q) { I[q] = t[5 + sw[q]]; J[q] = t[14 + sw[q]]; Jt[q] = t[10 + sw[q]]; }
+        M0 = t[9];
     }
 }
 
@@ -457,22 +518,9 @@ __device__ void pair_moments(int e, int f, const SegV& se, const SegV& sf, const
     const int N = p.N;
     int d = e - f; if (d < 0) d = -d;
     const int cyc = min(d, N - d);
-    if (cyc == 0) {
-        pair_self(se.h, p.sc, I);
-        if (WD) for (int q = 0; q < 4; ++q) { J[q] = cmk(0, 0); Jt[q] = cmk(0, 0); }
-    } else if (cyc == 1) {
-        if (f == (e + 1) % N) {
-            pair_adjacent_fwd<WD>(se, sf, p.sc, I, J, Jt);
-        } else {
-            cplx I2[4], J2[4], Jt2[4];
-            pair_adjacent_fwd<WD>(sf, se, p.sc, I2, J2, Jt2);
-            // swap the roles of the segments: (a,b) -> (b,a), J <-> Jt
-            I[0] = I2[0]; I[1] = I2[2]; I[2] = I2[1]; I[3] = I2[3];
-            if (WD) {
-                J[0] = Jt2[0]; J[1] = Jt2[2]; J[2] = Jt2[1]; J[3] = Jt2[3];
-                Jt[0] = J2[0]; Jt[1] = J2[2]; Jt[2] = J2[1]; Jt[3] = J2[3];
-            }
-        }
+    if (cyc <= 1) {
+        cplx M0;
+        near_from_table(p.near, N, e, f, cyc, I, J, Jt, M0);
     } else {
         const float mx = (float)(se.x0 - sf.x0) + 0.5f * (float)(se.h * se.tx - sf.h * sf.tx);
         const float my = (float)(se.y0 - sf.y0) + 0.5f * (float)(se.h * se.ty - sf.h * sf.ty);
@@ -626,24 +674,12 @@ __device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, 
     }
 }
 
-// self and adjacent pairs in FP64 (closed forms), returned as double-float
-__device__ __noinline__ void near_pair_df(int e, int f, const AsmParams& p, cdfl I[4], cdfl& M0) {
-    const SegV se = load_seg(p.seg, p.N, e), sf = load_seg(p.seg, p.N, f);
-    cplx Id[4], Jd[4], Jtd[4];
-    unsigned unused = 0;
-    pair_moments<false>(e, f, se, sf, p, Id, Jd, Jtd, unused);
-    const double ihh = 1.0 / (se.h * sf.h);
-    const cplx m = cscale(cadd(cadd(Id[0], Id[1]), cadd(Id[2], Id[3])), ihh);
-    for (int c = 0; c < 4; ++c) I[c] = cdfl_from(Id[c]);
-    M0 = cdfl_from(m);
-}
-
 // S and N tiles with double-float far pairs.  Same decomposition as k_assemble below: one
 // CTA per T x T vertex tile of the upper triangle, (T+1)^2 segment pairs staged in shared
 // memory, entries combined and written with their mirror.  Segment positions are kept as
 // offsets from the tile's first segment on each side, plus one tile offset, so nearby
 // pairs keep their relative geometry to double-float precision.  Self and adjacent pairs
-// use the FP64 closed forms.
+// come from the FP64 table of k_near_pairs.
 template <int T>
 __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     int ti, tj;
@@ -694,7 +730,10 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
         const dfl nd = dfl_mul(k2, dfl_fma(etx, ftx, dfl_mul(ety, fty)));   // nu_e . nu_f = t_e . t_f
         cdfl I[4], M0;
         if (cyc <= 1) {
-            near_pair_df(e, f, p, I, M0);
+            cplx Id[4], Jd[4], Jtd[4], m;
+            near_from_table(p.near, N, e, f, cyc, Id, Jd, Jtd, m);
+            for (int c = 0; c < 4; ++c) I[c] = cdfl_from(Id[c]);
+            M0 = cdfl_from(m);
         } else {
             // y_f(0) - x_e(0) = (f offset) - (e offset) + tile offset
             const dfl bx = dfl_add(dfl_sub(dfl_mk(gF[fl]), dfl_mk(gE[el])), offx);
@@ -898,8 +937,19 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     series_coefficients(h->k, 2.0 * h->hbar, &p.sc);
     bem_status st = bessel_table(h, &p.btab, &p.btabf);
     if (st != BEM_OK) return st;
-    if (ops & BEM_OP_D) return run_assemble<15, true>(h, p);
-    return run_assemble_sn<31>(h, p);
+    cplx* near = nullptr;
+    BEM_CUDA(h, cudaMallocAsync((void**)&near, sizeof(cplx) * NEAR_STRIDE * (size_t)h->N, h->stream));
+    const unsigned gnear = (unsigned)((h->N + 7) / 8);
+    if (ops & BEM_OP_D) {
+        BEM_TIMED(h, "k_near_pairs", (k_near_pairs<true><<<gnear, 256, 0, h->stream>>>(h->seg, (int)h->N, p.sc, near)));
+    } else {
+        BEM_TIMED(h, "k_near_pairs", (k_near_pairs<false><<<gnear, 256, 0, h->stream>>>(h->seg, (int)h->N, p.sc, near)));
+    }
+    BEM_LAUNCH(h, "k_near_pairs");
+    p.near = near;
+    st = (ops & BEM_OP_D) ? run_assemble<15, true>(h, p) : run_assemble_sn<31>(h, p);
+    cudaFreeAsync(near, h->stream);
+    return st;
 }
 
 // ---------------------------------------------------------------------------------------

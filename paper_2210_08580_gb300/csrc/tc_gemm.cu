@@ -12,17 +12,20 @@
 // slice s is stored pre-multiplied by 2^{-7s}, which bf16 holds exactly.  Products of
 // slices (s, t) with s + t <= S - 1 are accumulated by tcgen05.mma (kind::f16, FP32
 // accumulation) into four TMEM accumulators: d = 0, 1, 2 and d >= 3 (d = s + t).  Over a
-// K' chunk of 256 the d = 0, 1, 2 sums are multiples of 2^-7d spanning at most 23 bits, so
-// FP32 accumulation is exact for them (measured on GB300: a group of one magnitude is
-// exact, while mixing groups 7 or more bits apart in one accumulator rounds at 2^-24 of
+// K' chunk of 512 the d = 0, 1, 2 sums are multiples of 2^-7d below 2^24 of that unit
+// (|d0 e0| <= 2^14, |d0 e1| + |d1 e0| <= 2^14, the three d = 2 products <= 2^14 + 2^12 per
+// k), so FP32 accumulation is exact for them (measured on GB300: a group of one magnitude
+// is exact, while mixing groups 7 or more bits apart in one accumulator rounds at 2^-24 of
 // it); the d >= 3 sum carries that 2^-24 rounding on a term 2^-21 below the leading one.
 // After each chunk the epilogue warps add the accumulators into double-float (hi, lo)
 // registers; the result is rescaled by 2^{e_i + f_j - 14} and written in FP64.
 //
 // Kernel: one 128 x 128 tile of C' per CTA, 10 warps: warp 0 issues TMA loads (3D tensor
 // maps over the stacked slices, 64-byte swizzle, 32-element K blocks, 2 stages), warp 1
-// allocates TMEM and issues the MMAs, warps 2..9 drain TMEM (2 warps per TMEM lane
-// quarter, 64 columns each).  Every mbarrier wait is
+// allocates TMEM and issues the MMAs (S is a template parameter, so the S(S+1)/2 x 2 MMAs
+// of a K block are one straight-line sequence with constant descriptor offsets: a loop
+// that rebuilt descriptors per MMA issued slower than the tensor pipe executes), warps
+// 2..9 drain TMEM (2 warps per TMEM lane quarter, 64 columns each).  Every mbarrier wait is
 // bounded; a timeout sets the handle's device error word and the CTA winds down, freeing
 // its TMEM.
 #include <cuda.h>
@@ -39,7 +42,7 @@
 #define TC_BN 128
 #define TC_BK 32
 #define TC_STAGES 2
-#define TC_CHUNK_KB 8               // K' chunk of 8 x 32 = 256 between TMEM flushes
+#define TC_CHUNK_KB 16              // K' chunk of 16 x 32 = 512 between TMEM flushes
 #define TC_SPLIT_TARGET 152         // CTAs to aim for when splitting K' (one per SM)
 #define TC_NACC 4                   // TMEM accumulators (4 x 128 columns = all 512)
 #define TC_SMAX 7
@@ -150,11 +153,11 @@ struct TcGemmArgs {
     double2* part;           // split partials [split][j][i] (M x m each), or null
 };
 
+template <int S>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcGemmArgs p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int S = p.S;
     // layout: [stage][A slices][B slices] tiles (reused as the epilogue stash once the
     // MMAs are done), then the barriers after max(stages, stash)
     const size_t stage_bytes = (size_t)2 * S * TC_TILE_BYTES;
@@ -222,23 +225,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int c = 0; c < nchunks && ok; ++c) {
                 if (c > 0 && !mbar_wait(acc_empty, (uint32_t)((c - 1) & 1), p.err)) { ok = false; break; }
                 tc_fence_after();
-                uint32_t used0 = 0u, used1 = 0u, used2 = 0u, used3 = 0u;   // written in this chunk
                 const int kb_end = min(nkb, (c + 1) * TC_CHUNK_KB);
                 for (int kb = c * TC_CHUNK_KB; kb < kb_end; ++kb) {
                     const int st = kb & 1;
                     if (!mbar_wait(&full[st], (uint32_t)((kb >> 1) & 1), p.err)) { ok = false; break; }
                     tc_fence_after();
+                    // descriptors of slice tile 0 of A and of B in this stage; the start
+                    // address field counts 16-byte units, so tile and K offsets add directly
                     const uint32_t base = smem_u32(smem + st * stage_bytes);
-#pragma unroll 1
+                    const uint64_t dA = sdesc_sw64(base), dB = sdesc_sw64(base + S * TC_TILE_BYTES);
+                    const bool chunk_start = (kb == c * TC_CHUNK_KB);
+#pragma unroll
                     for (int kk = 0; kk < TC_BK / 16; ++kk) {
+#pragma unroll
                         for (int s = 0; s < S; ++s) {
-                            const uint64_t da = sdesc_sw64(base + s * TC_TILE_BYTES + kk * 32);
+#pragma unroll
                             for (int t = 0; s + t < S; ++t) {
-                                const int a = min(s + t, TC_NACC - 1);
-                                const uint64_t db = sdesc_sw64(base + (S + t) * TC_TILE_BYTES + kk * 32);
-                                const uint32_t acc = (a == 0) ? used0 : ((a == 1) ? used1 : ((a == 2) ? used2 : used3));
-                                umma_bf16(tmem + a * TC_BN, da, db, idesc, acc);
-                                if (a == 0) used0 = 1u; else if (a == 1) used1 = 1u; else if (a == 2) used2 = 1u; else used3 = 1u;
+                                const int a = (s + t < TC_NACC - 1) ? s + t : TC_NACC - 1;
+                                // the first MMA into each accumulator of a chunk overwrites it
+                                const bool first = (kk == 0 && s == 0 && t < TC_NACC);
+                                const uint32_t acc = (first && chunk_start) ? 0u : 1u;
+                                umma_bf16(tmem + a * TC_BN, dA + ((s * TC_TILE_BYTES + kk * 32) >> 4),
+                                          dB + ((t * TC_TILE_BYTES + kk * 32) >> 4), idesc, acc);
                             }
                         }
                     }
@@ -417,56 +425,82 @@ __device__ __forceinline__ void split_digits(double val, int e, int S, float* d)
     d[0] = (float)X;
 }
 
-// A' slices: out[s][i][kp], kp = 2k + c, padded with zeros to Kp.  One thread per complex
-// entry (k) writes the (re, im) pair of every slice as one bf16x2.  conj negates Im.
+// A' slices: out[s][i][kp], kp = 2k + c, padded with zeros to Kp.  Each complex entry (k)
+// becomes the (re, im) pair of every slice as one bf16x2.  conj negates Im.
+#define SLICE_VEC 4                  // complex entries per thread in the slicers
 __global__ void k_slice_A(const void* src, int is_real, int conj, int64_t M, int64_t K, int64_t Kp, int64_t sa_i,
                           int64_t sa_k, int band, const int* e, int S, __nv_bfloat16* out) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // SLICE_VEC consecutive k per thread: Kp / 2 is a multiple of 32, so a group never
+    // straddles a row and each slice gets one 16-byte store
+    const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * SLICE_VEC;
     const int64_t i = blockIdx.y;
-    if (2 * k >= Kp || i >= M) return;
-    double re = 0.0, im = 0.0;
-    if (k < K && !in_band(i, k, K, band)) {
-        if (is_real) {
-            re = ((const double*)src)[i * sa_i + k * sa_k];
-        } else {
-            const double2 v = ((const double2*)src)[i * sa_i + k * sa_k];
-            re = v.x; im = conj ? -v.y : v.y;
+    if (2 * k0 >= Kp || i >= M) return;
+    const int ei = e[i];
+    uint32_t packed[TC_SMAX][SLICE_VEC];
+#pragma unroll
+    for (int v = 0; v < SLICE_VEC; ++v) {
+        const int64_t k = k0 + v;
+        double re = 0.0, im = 0.0;
+        if (k < K && !in_band(i, k, K, band)) {
+            if (is_real) {
+                re = ((const double*)src)[i * sa_i + k * sa_k];
+            } else {
+                const double2 x = ((const double2*)src)[i * sa_i + k * sa_k];
+                re = x.x; im = conj ? -x.y : x.y;
+            }
+        }
+        float dr[TC_SMAX], di[TC_SMAX];
+        split_digits(re, ei, S, dr);
+        split_digits(im, ei, S, di);
+#pragma unroll
+        for (int s = 0; s < TC_SMAX; ++s) {
+            const __nv_bfloat162 b = __floats2bfloat162_rn(dr[s], di[s]);
+            packed[s][v] = *reinterpret_cast<const uint32_t*>(&b);
         }
     }
-    float dr[TC_SMAX], di[TC_SMAX];
-    split_digits(re, e[i], S, dr);
-    split_digits(im, e[i], S, di);
-    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + i * Kp + 2 * k);
-    const size_t stride2 = (size_t)M * Kp / 2;
+    uint4* o = reinterpret_cast<uint4*>(out + i * Kp + 2 * k0);
+    const size_t stride16 = (size_t)M * Kp / 8;     // one slice, in 16-byte units
 #pragma unroll
     for (int s = 0; s < TC_SMAX; ++s)
-        if (s < S) o[s * stride2] = __floats2bfloat162_rn(dr[s], di[s]);
+        if (s < S) o[s * stride16] = make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
 }
 
-// B' slices stored K-major: out[s][jp][kp].  One thread per complex entry (k, j) writes rows
+// B' slices stored K-major: out[s][jp][kp].  Each complex entry (k, j) gives rows
 // jp = 2j: (Re, -Im) and jp = 2j + 1: (Im, Re) at kp = 2k, 2k + 1.
 __global__ void k_slice_B(const void* src, int is_real, int64_t K, int64_t m, int64_t Kp, int64_t sb_k,
                           int64_t sb_j, const int* f, int S, __nv_bfloat16* out) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * SLICE_VEC;
     const int64_t j = blockIdx.y;
-    if (2 * k >= Kp || j >= m) return;
-    double re = 0.0, im = 0.0;
-    if (k < K) {
-        if (is_real) { re = ((const double*)src)[k * sb_k + j * sb_j]; }
-        else { const double2 v = ((const double2*)src)[k * sb_k + j * sb_j]; re = v.x; im = v.y; }
-    }
+    if (2 * k0 >= Kp || j >= m) return;
     const int fe = f[2 * j];
-    float dr[TC_SMAX], di[TC_SMAX];
-    split_digits(re, fe, S, dr);
-    split_digits(im, fe, S, di);
-    __nv_bfloat162* o0 = reinterpret_cast<__nv_bfloat162*>(out + (2 * j) * Kp + 2 * k);
-    __nv_bfloat162* o1 = reinterpret_cast<__nv_bfloat162*>(out + (2 * j + 1) * Kp + 2 * k);
-    const size_t stride2 = (size_t)(2 * m) * Kp / 2;
+    uint32_t p0[TC_SMAX][SLICE_VEC], p1[TC_SMAX][SLICE_VEC];
+#pragma unroll
+    for (int v = 0; v < SLICE_VEC; ++v) {
+        const int64_t k = k0 + v;
+        double re = 0.0, im = 0.0;
+        if (k < K) {
+            if (is_real) { re = ((const double*)src)[k * sb_k + j * sb_j]; }
+            else { const double2 x = ((const double2*)src)[k * sb_k + j * sb_j]; re = x.x; im = x.y; }
+        }
+        float dr[TC_SMAX], di[TC_SMAX];
+        split_digits(re, fe, S, dr);
+        split_digits(im, fe, S, di);
+#pragma unroll
+        for (int s = 0; s < TC_SMAX; ++s) {
+            const __nv_bfloat162 b0 = __floats2bfloat162_rn(dr[s], -di[s]);
+            const __nv_bfloat162 b1 = __floats2bfloat162_rn(di[s], dr[s]);
+            p0[s][v] = *reinterpret_cast<const uint32_t*>(&b0);
+            p1[s][v] = *reinterpret_cast<const uint32_t*>(&b1);
+        }
+    }
+    uint4* o0 = reinterpret_cast<uint4*>(out + (2 * j) * Kp + 2 * k0);
+    uint4* o1 = reinterpret_cast<uint4*>(out + (2 * j + 1) * Kp + 2 * k0);
+    const size_t stride16 = (size_t)(2 * m) * Kp / 8;
 #pragma unroll
     for (int s = 0; s < TC_SMAX; ++s) {
         if (s < S) {
-            o0[s * stride2] = __floats2bfloat162_rn(dr[s], -di[s]);
-            o1[s * stride2] = __floats2bfloat162_rn(di[s], dr[s]);
+            o0[s * stride16] = make_uint4(p0[s][0], p0[s][1], p0[s][2], p0[s][3]);
+            o1[s * stride16] = make_uint4(p1[s][0], p1[s][1], p1[s][2], p1[s][3]);
         }
     }
 }
@@ -562,7 +596,7 @@ static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M,
     op.K = K;
     BEM_TIMED(h, "k_exp_rows", (k_exp_rows<<<(unsigned)((M + 7) / 8), 256, 0, h->stream>>>(src, is_real, M, K, sa_i, sa_k, band, op.exps)));
     BEM_LAUNCH(h, "k_exp_rows");
-    dim3 grid((unsigned)((Kp / 2 + 255) / 256), (unsigned)M);
+    dim3 grid((unsigned)((Kp / 2 / SLICE_VEC + 255) / 256), (unsigned)M);
     BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, is_real, conj, M, K, Kp, sa_i, sa_k, band, op.exps, S, op.slices)));
     BEM_LAUNCH(h, "k_slice_A");
     return encode_map(h, op, S);
@@ -578,7 +612,7 @@ static bem_status slice_B(bem_ctx* h, TcOperand& op, const void* src, int is_rea
     op.K = K;
     BEM_TIMED(h, "k_exp_cols", (k_exp_cols<<<(unsigned)((m + 7) / 8), 256, 0, h->stream>>>(src, is_real, K, m, sb_k, sb_j, op.exps)));
     BEM_LAUNCH(h, "k_exp_cols");
-    dim3 grid((unsigned)((Kp / 2 + 255) / 256), (unsigned)m);
+    dim3 grid((unsigned)((Kp / 2 / SLICE_VEC + 255) / 256), (unsigned)m);
     BEM_TIMED(h, "k_slice_B", (k_slice_B<<<grid, 256, 0, h->stream>>>(src, is_real, K, m, Kp, sb_k, sb_j, op.exps, S, op.slices)));
     BEM_LAUNCH(h, "k_slice_B");
     return encode_map(h, op, S);
@@ -632,7 +666,16 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     p.kps = p.nkb;
     p.part = nullptr;
     const size_t smem = gemm_smem(t->S);
-    BEM_CUDA(h, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    void (*kern)(const CUtensorMap, const CUtensorMap, TcGemmArgs) = nullptr;
+    switch (t->S) {
+        case 3: kern = k_tc_gemm<3>; break;
+        case 4: kern = k_tc_gemm<4>; break;
+        case 5: kern = k_tc_gemm<5>; break;
+        case 6: kern = k_tc_gemm<6>; break;
+        case 7: kern = k_tc_gemm<7>; break;
+        default: return bem_fail(h, BEM_E_UNSUPPORTED, "tc_gemm: slices per operand must be 3..7");
+    }
+    BEM_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int mt = (p.M + TC_BM - 1) / TC_BM, nt = (p.Ncols + TC_BN - 1) / TC_BN;
     // skinny outputs (r x nrhs, r x r) fill few SMs: split K' so that about one wave of
     // CTAs runs, each split at least a few accumulation chunks long
@@ -655,7 +698,7 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
         p.part = t->part;
     }
     dim3 grid((unsigned)(mt * nt), (unsigned)splits);
-    BEM_TIMED(h, tag, (k_tc_gemm<<<grid, TC_THREADS, smem, h->stream>>>(A.map, B.map, p)));
+    BEM_TIMED(h, tag, (kern<<<grid, TC_THREADS, smem, h->stream>>>(A.map, B.map, p)));
     BEM_LAUNCH(h, "k_tc_gemm");
     if (splits > 1) {
         const int64_t n = (int64_t)p.M * m;
