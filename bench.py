@@ -31,13 +31,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "factor s + RHS solves/s at N=16384: mixed/batched vs FP64 GPU, rel err ≤1e-8"
-# GB300 FP64 pipe: 2 DFMA per SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma
-# peak_sustained = 2), 152 SMs, 2070 MHz maximum SM clock -> 1.259 TFLOP/s
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# FP64 flops per far-field Gauss point of the assembly (S and N): argument u = k^2 r^2
-# from the two node coordinates (8), J0 and Y0 as degree-10 polynomials in u (2 x 10 FMA =
-# 40), the four lambda-weighted complex moments (8 FMA = 16)
-ASM_FLOPS_PER_POINT = 64
+# GB300 FP32 pipe: 128 lanes per SM, 152 SMs, 2070 MHz maximum SM clock -> 40.3 T
+# FP32 operations per second (an FFMA, FADD or FMUL counts as one operation)
+FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
+# FP32 operations per far-field Gauss point of the S/N assembly, which runs in
+# double-float arithmetic (df fma = 15 FP32 ops, df mul = 7, df add = 11): node offsets
+# 2 fma (30), r^2 1 mul + 1 fma (22), u = k^2 r^2 1 mul (7), t = (u - u_mid)/u_half 1 add +
+# 1 mul (18), J0 and Y0 as degree-10 polynomials 20 fma (300), g = (i/4) H0 4 scalings,
+# the two lambda-weighted row sums 4 fma (60)
+ASM_OPS_PER_POINT = 441
 # DRAM bytes per launch from ncu captures of the kernels as they stand (None = not captured
 # since the kernel last changed); the summaries are under profiles/
 TRAFFIC_BYTES = {}
@@ -67,11 +69,11 @@ def roofline(rep, args, n_modes, r, quad_points):
     avg_s = dom_ms / dom_cnt / 1000.0
     pk = _peaks()
     if dom_name == "k_assemble":
-        ach = quad_points * ASM_FLOPS_PER_POINT / avg_s / 1e12
-        return {"kernel": dom_name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES.get(dom_name),
-                "units_per_launch": quad_points, "flops_per_unit": ASM_FLOPS_PER_POINT,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
+        ach = quad_points * ASM_OPS_PER_POINT / avg_s / 1e12
+        return {"kernel": dom_name, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TOPS,
+                "unit": "TOP/s (FP32 pipe)", "frac": ach / FP32_PEAK_TOPS, "traffic": TRAFFIC_BYTES.get(dom_name),
+                "units_per_launch": quad_points, "ops_per_unit": ASM_OPS_PER_POINT,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
     fl = tc_gemm_flops(dom_name, args.N, args.nrhs, n_modes, r, 6)
     if fl is not None:
         peak = pk.get("bf16_tflops_sustained", 1700.0)
@@ -342,13 +344,21 @@ def main():
 
     fp64_cmp = None
     if not args.no_compare_fp64 and args.prec == "mixed":
+        # the same step on the FP64 path, and the metric's accuracy bar: the mixed solution
+        # against the FP64 one on identical inputs (max over RHS of the relative error)
+        x_mixed = x.clone()
+        v64 = torch.empty_like(v)
+        x64 = torch.empty_like(x)
         s64 = bem.Solver(device=local, prec="fp64", stream=stream)
         t64 = timed(lambda: (s64.assemble(verts, args.k, ops="SW"), s64.filter_apply(n_modes),
                              s64.compress(args.tol), s64.factor(),
-                             s64.L.bem_rhs_planewave(s64.h, ang.data_ptr(), args.nrhs, None, v.data_ptr(), args.N),
-                             s64.solve(v, out=x)))
-        fp64_cmp = {"ms_per_step": t64, "value": args.nrhs / (t64 / 1000.0), "unit": "RHS/s"}
+                             s64.L.bem_rhs_planewave(s64.h, ang.data_ptr(), args.nrhs, None, v64.data_ptr(), args.N),
+                             s64.solve(v64, out=x64)))
+        err = ((x_mixed - x64).abs().amax(dim=1) / x64.abs().amax(dim=1)).max().item()
+        fp64_cmp = {"ms_per_step": t64, "value": args.nrhs / (t64 / 1000.0), "unit": "RHS/s",
+                    "mixed_rel_err_vs_fp64": err, "bar": 1e-8, "pass": bool(err <= 1e-8)}
         s64.close()
+        del v64, x64, x_mixed
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

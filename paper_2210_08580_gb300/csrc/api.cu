@@ -305,16 +305,20 @@ bem_status compress_compact(bem_handle h, double rel_tol, int64_t* rank_out) {
     if ((st = ensure_alloc(h, (void**)&h->Bs, sizeof(cplx) * nc * N)) != BEM_OK) return st;
     cplx *X = nullptr, *R = nullptr;
     double* Qs = nullptr;
+    int* perm = nullptr;
     Carve cv;
     cv.add((void**)&X, sizeof(cplx) * nc * N);
     cv.add((void**)&R, sizeof(cplx) * nc * nc);
     cv.add((void**)&Qs, sizeof(double) * nc * N);
+    cv.add((void**)&perm, sizeof(int) * nc);
     if ((st = cv.commit(h)) != BEM_OK) return st;
     // Bs = diag(sqrt g) B ;  X = (Bs F^-1)^H  (N x nc, stored with row stride nc)
     if ((st = launch_row_scale(h, h->B, h->Bs, h->gm, 1, nc, N, nc)) != BEM_OK) return st;
     if ((st = apply_gram_inverse(h, 1, h->Bs, X, nullptr, N, nc, nc, 1, h->hbar, true)) != BEM_OK) return st;
-    if ((st = launch_house_qr(h, X, N, (int)nc, R)) != BEM_OK) return st;
-    if ((st = launch_jacobi_svd(h, R, (int)nc, h->sigma, h->E)) != BEM_OK) return st;
+    // B^ = X^H: pivoted QR X P = Q R, then the left singular vectors of R^H, rows permuted
+    // back by P, are those of B^
+    if ((st = launch_house_qr(h, X, N, (int)nc, R, perm)) != BEM_OK) return st;
+    if ((st = launch_jacobi_svd(h, R, (int)nc, perm, h->sigma, h->E)) != BEM_OK) return st;
     std::vector<double> sig(nc);
     BEM_CUDA(h, cudaMemcpyAsync(sig.data(), h->sigma, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->stream));
     if ((st = check_dev_err(h)) != BEM_OK) return st;

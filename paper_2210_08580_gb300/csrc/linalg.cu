@@ -337,27 +337,106 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;
 }
 
-__global__ void __launch_bounds__(256) k_house_qr(cplx* X, int64_t N, int n, cplx* R, double* partN, cplx* partW,
-                                                  unsigned* bar, int* err) {
+// Householder QR with column pivoting of X (N x n, row-major, N >= n): X P = Q R.
+// Rows are split evenly over the CTAs; per column two grid barriers.  Pivoting is by the
+// largest trailing column norm, from per-CTA partial norms accumulated while the previous
+// reflector is applied (so no extra pass over X).  For the comparison the partials are
+// summed by integer atomics in 62-bit fixed point (scaled by the largest initial column
+// norm; integer addition keeps the choice independent of arrival order); the reflector
+// uses the FP64 sum of the chosen column's partials.  Columns are never moved:
+// cmap[c] is the storage column of logical column c, identical in every CTA.  On exit
+// perm[c] = cmap[c] (X P has column c = column perm[c] of X) and R (n x n, column-major)
+// holds the upper triangle.  The pivoting grades R so that one-sided Jacobi on R^H needs
+// few sweeps (Drmac and Veselic's preconditioned Jacobi SVD).
+__global__ void __launch_bounds__(256) k_house_qr(cplx* X, int64_t N, int n, cplx* R, int* perm, double* partC,
+                                                  unsigned long long* cnq, cplx* partW, unsigned* bar, int* err) {
     __shared__ double red[32];
     __shared__ cplx wred[8][33];
+    __shared__ double nred[8][33];
     __shared__ cplx wsm[1024];
+    __shared__ int cmap[1024];
+    __shared__ double qscale_s;
+    __shared__ unsigned long long pbest[8];
+    __shared__ int pidx[8];
     const unsigned G = gridDim.x;
     const int64_t rb = (N + G - 1) / G;
     const int64_t r0 = (int64_t)blockIdx.x * rb, r1 = min(N, r0 + rb);
-    const int tid = threadIdx.x, cg = tid & 31, rg = tid >> 5;
+    const int tid = threadIdx.x, cg = tid & 31, rg = tid >> 5, lane = tid & 31;
+    for (int c = tid; c < n; c += blockDim.x) cmap[c] = c;
+    // partial column norms over my rows
+    for (int cb = 0; cb < n; cb += 32) {
+        const int c = cb + cg;
+        double acc = 0.0;
+        if (c < n)
+            for (int64_t i = r0 + rg; i < r1; i += 8) acc += cabs2(X[i * n + c]);
+        nred[rg][cg] = acc;
+        __syncthreads();
+        if (rg == 0 && c < n) {
+            double t = 0.0;
+            for (int q = 0; q < 8; ++q) t += nred[q][cg];
+            partC[(int64_t)blockIdx.x * n + c] = t;
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(bar, G, err)) return;
+    // fixed-point scale from the largest column norm (every CTA alike), then the first
+    // pivot sums (cnq[0] and cnq[1] were zeroed before the launch)
+    {
+        double mx = 0.0;
+        for (int c = tid; c < n; c += blockDim.x) {
+            double t = 0.0;
+            for (unsigned q = 0; q < G; ++q) t += partC[(int64_t)q * n + c];
+            mx = fmax(mx, t);
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) red[rg] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            double m2 = 0.0;
+            for (int q = 0; q < 8; ++q) m2 = fmax(m2, red[q]);
+            qscale_s = (m2 > 0.0) ? 4.0e18 / m2 : 0.0;      // sums stay below 2^62
+        }
+        __syncthreads();
+        for (int c = tid; c < n; c += blockDim.x)
+            atomicAdd(cnq + c, __double2ull_rz(partC[(int64_t)blockIdx.x * n + c] * qscale_s));
+    }
+    const double qscale = qscale_s;
     for (int j = 0; j < n; ++j) {
-        // (1) partial norm of column j over rows >= j
-        double s = 0.0;
-        for (int64_t i = max(r0, (int64_t)j) + tid; i < r1; i += blockDim.x) s += cabs2(X[i * n + j]);
-        s = block_sum(s, red);
-        if (tid == 0) partN[blockIdx.x] = s;
         if (!grid_barrier(bar, G, err)) return;
-        // (2) reflector
+        // (1) pivot: the largest trailing column norm (ties to the lower index)
+        const unsigned long long* cq = cnq + (size_t)(j & 1) * n;
+        unsigned long long best = 0ull;
+        int bi = n;
+        for (int c = j + tid; c < n; c += blockDim.x) {
+            const unsigned long long v = __ldcg(cq + cmap[c]);
+            if (bi == n || v > best) { best = v; bi = c; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oi < n && (bi == n || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { pbest[rg] = best; pidx[rg] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long b2 = pbest[0];
+            int i2 = pidx[0];
+            for (int q = 1; q < 8; ++q)
+                if (pidx[q] < n && (i2 == n || pbest[q] > b2 || (pbest[q] == b2 && pidx[q] < i2))) {
+                    b2 = pbest[q]; i2 = pidx[q];
+                }
+            if (i2 > j && i2 < n) { const int t = cmap[j]; cmap[j] = cmap[i2]; cmap[i2] = t; }
+        }
+        // the other buffer collects the norms after this step's update
+        if (blockIdx.x == 0)
+            for (int c = tid; c < n; c += blockDim.x) cnq[(size_t)((j + 1) & 1) * n + c] = 0ull;
+        __syncthreads();
+        const int pj = cmap[j];
         double nrm2 = 0.0;
-        for (unsigned q = tid; q < G; q += blockDim.x) nrm2 += partN[q];
+        for (unsigned q = tid; q < G; q += blockDim.x) nrm2 += partC[(int64_t)q * n + pj];
         nrm2 = block_sum(nrm2, red);
-        const cplx xjj = X[(int64_t)j * n + j];
+        // (2) reflector
+        const cplx xjj = X[(int64_t)j * n + pj];
         double tau = 0.0;
         cplx alpha = cmk(0, 0), vj = cmk(0, 0);
         if (nrm2 > 0.0) {
@@ -368,14 +447,16 @@ __global__ void __launch_bounds__(256) k_house_qr(cplx* X, int64_t N, int n, cpl
             const double vn2 = nrm2 - ax * ax + cabs2(vj);
             tau = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
         }
+        if (tid == 0 && j >= r0 && j < r1) R[j + (int64_t)j * n] = (nrm2 > 0.0) ? alpha : cmk(0, 0);
         // (3) partial dots w_c = sum_i conj(v_i) X[i, c], c > j
         for (int cb = j + 1; cb < n; cb += 32) {
             const int c = cb + cg;
             cplx acc = cmk(0, 0);
             if (c < n && tau != 0.0) {
+                const int pc = cmap[c];
                 for (int64_t i = max(r0, (int64_t)j) + rg; i < r1; i += 8) {
-                    const cplx vi = (i == j) ? vj : X[i * n + j];
-                    cfma_conj(acc, vi, X[i * n + c]);
+                    const cplx vi = (i == j) ? vj : X[i * n + pj];
+                    cfma_conj(acc, vi, X[i * n + pc]);
                 }
             }
             wred[rg][cg] = acc;
@@ -388,37 +469,46 @@ __global__ void __launch_bounds__(256) k_house_qr(cplx* X, int64_t N, int n, cpl
             __syncthreads();
         }
         if (!grid_barrier(bar, G, err)) return;
-        // (4) reduce w over CTAs, update my rows, write row j of R
+        // (4) reduce w over CTAs; update my rows and accumulate their trailing norms
         for (int c = j + 1 + tid; c < n; c += blockDim.x) {
             cplx t = cmk(0, 0);
             for (unsigned q = 0; q < G; ++q) t = cadd(t, partW[(int64_t)q * n + c]);
             wsm[c] = cscale(t, tau);
         }
         __syncthreads();
-        if (tau != 0.0) {
-            for (int cb = j + 1; cb < n; cb += 32) {
-                const int c = cb + cg;
-                if (c >= n) continue;
+        for (int cb = j + 1; cb < n; cb += 32) {
+            const int c = cb + cg;
+            double acc = 0.0;
+            if (c < n) {
+                const int pc = cmap[c];
                 const cplx wc = wsm[c];
                 for (int64_t i = max(r0, (int64_t)j) + rg; i < r1; i += 8) {
-                    const cplx vi = (i == j) ? vj : X[i * n + j];
-                    cplx x = X[i * n + c];
-                    x = csub(x, cmul(vi, wc));
-                    X[i * n + c] = x;
+                    cplx x = X[i * n + pc];
+                    if (tau != 0.0) {
+                        const cplx vi = (i == j) ? vj : X[i * n + pj];
+                        x = csub(x, cmul(vi, wc));
+                        X[i * n + pc] = x;
+                    }
+                    if (i > j) acc += cabs2(x);
                 }
             }
-        }
-        __syncthreads();
-        if (j >= r0 && j < r1) {
-            for (int c = tid; c < n; c += blockDim.x) {
-                cplx v;
-                if (c < j) v = cmk(0, 0);
-                else if (c == j) v = (nrm2 > 0.0) ? alpha : cmk(0, 0);
-                else v = X[(int64_t)j * n + c];
-                R[j + (int64_t)c * n] = v;
+            nred[rg][cg] = acc;
+            __syncthreads();
+            if (rg == 0 && c < n) {
+                double t = 0.0;
+                for (int q = 0; q < 8; ++q) t += nred[q][cg];
+                partC[(int64_t)blockIdx.x * n + cmap[c]] = t;
+                atomicAdd(cnq + (size_t)((j + 1) & 1) * n + cmap[c], __double2ull_rz(t * qscale));
             }
+            __syncthreads();
         }
     }
+    // R's rows owned here (the diagonal was written at each step)
+    for (int64_t j = max(r0, (int64_t)0); j < min(r1, (int64_t)n); ++j)
+        for (int c = tid; c < n; c += blockDim.x)
+            if (c != j) R[j + (int64_t)c * n] = (c < j) ? cmk(0, 0) : X[j * n + cmap[c]];
+    if (blockIdx.x == 0)
+        for (int c = tid; c < n; c += blockDim.x) perm[c] = cmap[c];
 }
 
 static bem_status coop_launch(bem_ctx* h, const void* fn, int blocks_wanted, int threads, void** args, const char* what) {
@@ -435,19 +525,24 @@ static bem_status coop_launch(bem_ctx* h, const void* fn, int blocks_wanted, int
     return BEM_OK;
 }
 
-bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R) {
+bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* perm) {
     if (n > 1024) return bem_fail(h, BEM_E_UNSUPPORTED, "QR: more than 1024 columns");
+    if (N < n) return bem_fail(h, BEM_E_INVALID, "QR: fewer rows than columns");
     int nsm = 0;
     BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     int G = (int)std::min<int64_t>(nsm, (N + 15) / 16);
     bem_status st;
-    double* partN = nullptr;
+    double* partC = nullptr;
     cplx* partW = nullptr;
-    BEM_CUDA(h, cudaMallocAsync((void**)&partN, sizeof(double) * G, h->stream));
+    unsigned long long* cnq = nullptr;
+    BEM_CUDA(h, cudaMallocAsync((void**)&partC, sizeof(double) * (size_t)G * n, h->stream));
+    BEM_CUDA(h, cudaMallocAsync((void**)&cnq, sizeof(unsigned long long) * 2 * (size_t)n, h->stream));
+    BEM_CUDA(h, cudaMemsetAsync(cnq, 0, sizeof(unsigned long long) * 2 * (size_t)n, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&partW, sizeof(cplx) * (size_t)G * n, h->stream));
-    void* args[] = {&X, &N, &n, &R, &partN, &partW, &h->bar, &h->dev_err};
+    void* args[] = {&X, &N, &n, &R, &perm, &partC, &cnq, &partW, &h->bar, &h->dev_err};
     BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr, G, 256, args, "k_house_qr"));
-    cudaFreeAsync(partN, h->stream);
+    cudaFreeAsync(partC, h->stream);
+    cudaFreeAsync(cnq, h->stream);
     cudaFreeAsync(partW, h->stream);
     return st;
 }
@@ -470,71 +565,110 @@ __device__ __forceinline__ void tourney(int round, int idx, int np, int& p, int&
 // the QR came from); R^H from a QR is close to diagonally dominant, which makes the
 // sweeps few.  128 threads per pair; one pair per CTA per round.
 #define JAC_NT 128
-__global__ void __launch_bounds__(JAC_NT) k_jacobi(cplx* X, int n, int* flags, int max_sweeps, unsigned* bar,
-                                                   int* err) {
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Rounds are ordered by data, not by grid barriers: every column carries a version (the
+// rounds it has been through), a CTA starts its pair of round t of a sweep once both
+// columns have reached version t, and publishes version t + 1 after writing them (release /
+// acquire at GPU scope; column data bypass L1).  A CTA waits only on the two CTAs that
+// last touched its columns, so consecutive rounds overlap across the grid.  One grid
+// barrier per sweep decides convergence.  Waits are bounded (DEVERR_TIMEOUT).
+__global__ void __launch_bounds__(JAC_NT) k_jacobi(cplx* X, int n, int* ver, int* flags, int max_sweeps,
+                                                   unsigned* bar, int* err) {
     __shared__ double red[JAC_NT / 32][4];
+    __shared__ int s_ok;
     const unsigned G = gridDim.x;
     const int np = n + (n & 1);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     constexpr int EPT = 1024 / JAC_NT;            // elements per thread (n <= 1024)
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int round = 0; round < np - 1; ++round) {
+            const int target = sweep * (np - 1) + round;
             for (int idx = blockIdx.x; idx < np / 2; idx += G) {
                 int p, q;
                 tourney(round, idx, np, p, q);
-                if (p >= n || q >= n) continue;
                 if (p > q) { int t = p; p = q; q = t; }
-                cplx* Xp = X + (int64_t)p * n;
-                cplx* Xq = X + (int64_t)q * n;
-                cplx x[EPT], y[EPT];
-                double a = 0.0, b = 0.0, gr = 0.0, gi = 0.0;
-#pragma unroll
-                for (int e = 0; e < EPT; ++e) {
-                    const int i = tid + JAC_NT * e;
-                    x[e] = (i < n) ? Xp[i] : cmk(0, 0);
-                    y[e] = (i < n) ? Xq[i] : cmk(0, 0);
-                    a += cabs2(x[e]); b += cabs2(y[e]);
-                    gr += x[e].x * y[e].x + x[e].y * y[e].y;     // conj(x) y
-                    gi += x[e].x * y[e].y - x[e].y * y[e].x;
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    a += __shfl_xor_sync(0xffffffffu, a, o);
-                    b += __shfl_xor_sync(0xffffffffu, b, o);
-                    gr += __shfl_xor_sync(0xffffffffu, gr, o);
-                    gi += __shfl_xor_sync(0xffffffffu, gi, o);
+                if (tid == 0) {
+                    int ok = 1;
+                    for (long long spins = 0;; ++spins) {
+                        const bool rp = (p >= n) || ld_acquire(ver + p) >= target;
+                        const bool rq = (q >= n) || ld_acquire(ver + q) >= target;
+                        if (rp && rq) break;
+                        if (spins > (1ll << 24)) { atomicOr(err, DEVERR_TIMEOUT); ok = 0; break; }
+                        if ((spins & 255) == 255 && *(volatile int*)err) { ok = 0; break; }
+                        if (spins > 32) __nanosleep(32);
+                    }
+                    s_ok = ok;
                 }
                 __syncthreads();
-                if (lane == 0) { red[wid][0] = a; red[wid][1] = b; red[wid][2] = gr; red[wid][3] = gi; }
-                __syncthreads();
-                a = b = gr = gi = 0.0;
+                if (!s_ok) return;
+                if (q < n) {       // both columns real (p < q)
+                    cplx* Xp = X + (int64_t)p * n;
+                    cplx* Xq = X + (int64_t)q * n;
+                    cplx x[EPT], y[EPT];
+                    double a = 0.0, b = 0.0, gr = 0.0, gi = 0.0;
 #pragma unroll
-                for (int w = 0; w < JAC_NT / 32; ++w) { a += red[w][0]; b += red[w][1]; gr += red[w][2]; gi += red[w][3]; }
-                const double ag = sqrt(gr * gr + gi * gi);
-                // converged pair: |x^H y| <= 1e-14 |x| |y|
-                if (ag <= 1e-14 * sqrt(a * b) || ag == 0.0) continue;
-                if (tid == 0) flags[sweep] = 1;
-                const double zeta = (b - a) / (2.0 * ag);
-                const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                const cplx sem = cmk(s * gr / ag, -s * gi / ag);       // s e^{-i phi}
-                const cplx sep = cmk(s * gr / ag, s * gi / ag);        // s e^{i phi}
+                    for (int e = 0; e < EPT; ++e) {
+                        const int i = tid + JAC_NT * e;
+                        x[e] = (i < n) ? __ldcg(Xp + i) : cmk(0, 0);
+                        y[e] = (i < n) ? __ldcg(Xq + i) : cmk(0, 0);
+                        a += cabs2(x[e]); b += cabs2(y[e]);
+                        gr += x[e].x * y[e].x + x[e].y * y[e].y;     // conj(x) y
+                        gi += x[e].x * y[e].y - x[e].y * y[e].x;
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        a += __shfl_xor_sync(0xffffffffu, a, o);
+                        b += __shfl_xor_sync(0xffffffffu, b, o);
+                        gr += __shfl_xor_sync(0xffffffffu, gr, o);
+                        gi += __shfl_xor_sync(0xffffffffu, gi, o);
+                    }
+                    if (lane == 0) { red[wid][0] = a; red[wid][1] = b; red[wid][2] = gr; red[wid][3] = gi; }
+                    __syncthreads();
+                    a = b = gr = gi = 0.0;
 #pragma unroll
-                for (int e = 0; e < EPT; ++e) {
-                    const int i = tid + JAC_NT * e;
-                    if (i >= n) continue;
-                    Xp[i] = csub(cscale(x[e], c), cmul(sem, y[e]));
-                    Xq[i] = cadd(cmul(sep, x[e]), cscale(y[e], c));
+                    for (int w = 0; w < JAC_NT / 32; ++w) { a += red[w][0]; b += red[w][1]; gr += red[w][2]; gi += red[w][3]; }
+                    const double ag = sqrt(gr * gr + gi * gi);
+                    // converged pair: |x^H y| <= 1e-14 |x| |y|
+                    if (!(ag <= 1e-14 * sqrt(a * b) || ag == 0.0)) {
+                        if (tid == 0) flags[sweep] = 1;
+                        const double zeta = (b - a) / (2.0 * ag);
+                        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                        const cplx sem = cmk(sn * gr / ag, -sn * gi / ag);       // s e^{-i phi}
+                        const cplx sep = cmk(sn * gr / ag, sn * gi / ag);        // s e^{i phi}
+#pragma unroll
+                        for (int e = 0; e < EPT; ++e) {
+                            const int i = tid + JAC_NT * e;
+                            if (i >= n) continue;
+                            __stcg(Xp + i, csub(cscale(x[e], c), cmul(sem, y[e])));
+                            __stcg(Xq + i, cadd(cmul(sep, x[e]), cscale(y[e], c)));
+                        }
+                    }
+                }
+                __syncthreads();              // the pair's stores precede its release
+                if (tid == 0) {
+                    __threadfence();
+                    if (p < n) st_release(ver + p, target + 1);
+                    if (q < n) st_release(ver + q, target + 1);
                 }
             }
-            if (!grid_barrier(bar, G, err)) return;
         }
+        if (!grid_barrier(bar, G, err)) return;
         if (*(volatile int*)(flags + sweep) == 0) return;
     }
 }
 
 // sigma_c = |X_c|, sorted descending; E[:, rank] = X_c / sigma_c (a unit vector e_c when
-// sigma_c = 0, which is then below any truncation threshold)
-__global__ void k_sort_sv(const cplx* X, int n, double* sigma, cplx* E, double* tmp) {
+// sigma_c = 0, which is then below any truncation threshold), with its rows put back in
+// the original order when the QR pivoted (E[perm[i], rank] = X[i, c]; perm may be null)
+__global__ void k_sort_sv(const cplx* X, int n, const int* perm, double* sigma, cplx* E, double* tmp) {
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         double s = 0.0;
         for (int i = 0; i < n; ++i) s += cabs2(X[(int64_t)c * n + i]);
@@ -551,7 +685,8 @@ __global__ void k_sort_sv(const cplx* X, int n, double* sigma, cplx* E, double* 
         sigma[rank] = sc;
         const double inv = (sc > 0.0) ? 1.0 / sc : 0.0;
         for (int i = 0; i < n; ++i)
-            E[(int64_t)rank * n + i] = (sc > 0.0) ? cscale(X[(int64_t)c * n + i], inv) : cmk(i == c ? 1.0 : 0.0, 0.0);
+            E[(int64_t)rank * n + (perm ? perm[i] : i)] =
+                (sc > 0.0) ? cscale(X[(int64_t)c * n + i], inv) : cmk(i == c ? 1.0 : 0.0, 0.0);
     }
 }
 
@@ -563,29 +698,33 @@ __global__ void k_conj_transpose(const cplx* R, cplx* X, int n) {
     X[idx] = cconj(R[j + i * n]);
 }
 
-bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, double* sigma, cplx* E) {
+bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double* sigma, cplx* E) {
     if (n > 1024) return bem_fail(h, BEM_E_UNSUPPORTED, "Jacobi SVD: more than 1024 columns");
     cplx* X = nullptr;
     int* flags = nullptr;
     double* tmp = nullptr;
+    int* ver = nullptr;
     const int max_sweeps = 40;
     BEM_CUDA(h, cudaMallocAsync((void**)&X, sizeof(cplx) * (size_t)n * n, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&flags, sizeof(int) * max_sweeps, h->stream));
+    BEM_CUDA(h, cudaMallocAsync((void**)&ver, sizeof(int) * n, h->stream));
+    BEM_CUDA(h, cudaMemsetAsync(ver, 0, sizeof(int) * n, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&tmp, sizeof(double) * n, h->stream));
     BEM_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(int) * max_sweeps, h->stream));
     BEM_TIMED(h, "k_conj_transpose",
               (k_conj_transpose<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, h->stream>>>(R, X, n)));
     BEM_LAUNCH(h, "k_conj_transpose");
     int ms = max_sweeps;
-    void* args[] = {&X, &n, &flags, &ms, &h->bar, &h->dev_err};
+    void* args[] = {&X, &n, &ver, &flags, &ms, &h->bar, &h->dev_err};
     bem_status st;
     BEM_TIMED(h, "k_jacobi", st = coop_launch(h, (const void*)k_jacobi, (n + 1) / 2, JAC_NT, args, "k_jacobi"));
     if (st == BEM_OK) {
-        BEM_TIMED(h, "k_sort_sv", (k_sort_sv<<<1, 256, 0, h->stream>>>(X, n, sigma, E, tmp)));
+        BEM_TIMED(h, "k_sort_sv", (k_sort_sv<<<1, 256, 0, h->stream>>>(X, n, perm, sigma, E, tmp)));
         BEM_LAUNCH(h, "k_sort_sv");
     }
     cudaFreeAsync(X, h->stream);
     cudaFreeAsync(flags, h->stream);
+    cudaFreeAsync(ver, h->stream);
     cudaFreeAsync(tmp, h->stream);
     return st;
 }
@@ -593,76 +732,85 @@ bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, double* sigma, cplx* E)
 // =========================================================================================
 // Gauss-Jordan inversion with partial pivoting of A (r x r) on the augmented [A | I]
 // (r x 2r, column-major, ld = r).  CTA b owns a block of augmented columns.  Per step j
-// every CTA copies the pivot column and finds the pivot, barrier, then updates its columns.
+// every CTA reads the pivot column from a copy its owner wrote while updating it in step
+// j - 1 (two buffers alternate, so the owner's in-place update never races the readers),
+// finds the pivot and updates its columns: one grid barrier per step.
 // =========================================================================================
-__global__ void __launch_bounds__(256) k_gauss_jordan(cplx* M, int r, unsigned* bar, int* err) {
+__global__ void __launch_bounds__(256) k_gauss_jordan(cplx* M, int r, cplx* colbuf, unsigned* bar, int* err) {
     extern __shared__ cplx colj[];
-    __shared__ double rv[256];
-    __shared__ int ri[256];
-    __shared__ int piv_s;
+    __shared__ double wv[8];
+    __shared__ int wi[8];
     const unsigned G = gridDim.x;
     const int ncol = 2 * r;
     const int cb = (ncol + G - 1) / G;
     const int c0 = blockIdx.x * cb, c1 = min(ncol, c0 + cb);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int j = 0; j < r; ++j) {
-        for (int i = threadIdx.x; i < r; i += blockDim.x) colj[i] = M[i + (int64_t)j * r];
+        // pivot column j as left by step j-1 (a copy, so its owner may update it in place)
+        const cplx* buf = colbuf + (size_t)(j & 1) * r;
+        for (int i = threadIdx.x; i < r; i += blockDim.x) colj[i] = __ldcg(buf + i);
         __syncthreads();
-        // argmax |colj[i]|, i >= j
-        double best = -1.0; int bi = j;
+        // argmax |colj[i]|, i >= j (ties to the lower row)
+        double best = -1.0;
+        int bi = r;
         for (int i = j + threadIdx.x; i < r; i += blockDim.x) {
             const double v = cabs2(colj[i]);
             if (v > best) { best = v; bi = i; }
         }
-        rv[threadIdx.x] = best; ri[threadIdx.x] = bi;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double bb = -1.0; int bbi = j;
-            for (int q = 0; q < (int)blockDim.x; ++q)
-                if (rv[q] > bb || (rv[q] == bb && ri[q] < bbi)) { bb = rv[q]; bbi = ri[q]; }
-            piv_s = bbi;
-            if (!(bb > 0.0)) atomicOr(err, DEVERR_SINGULAR);
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
         }
+        if (lane == 0) { wv[wid] = best; wi[wid] = bi; }
         __syncthreads();
-        const int p = piv_s;
-        if (threadIdx.x == 0 && p != j) { cplx t = colj[j]; colj[j] = colj[p]; colj[p] = t; }
+        double bb = wv[0];
+        int p = wi[0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+            if (wv[q] > bb || (wv[q] == bb && wi[q] < p)) { bb = wv[q]; p = wi[q]; }
+        if (!(bb > 0.0) || p >= r) {
+            if (threadIdx.x == 0) atomicOr(err, DEVERR_SINGULAR);
+            p = j;
+        }
+        const cplx cj = colj[j], cp = colj[p];
         __syncthreads();
-        if (!grid_barrier(bar, G, err)) return;     // everyone has read column j
+        if (threadIdx.x == 0 && p != j) { colj[j] = cp; colj[p] = cj; }
+        __syncthreads();
         const cplx pv = colj[j];
         const bool sing = !(cabs2(pv) > 0.0);
         const cplx ipv = sing ? cmk(0, 0) : cdiv(cmk(1, 0), pv);
-        for (int c = c0 + threadIdx.x / 32; c < c1; c += blockDim.x / 32) {
+        for (int c = c0 + wid; c < c1; c += blockDim.x / 32) {
             cplx* col = M + (int64_t)c * r;
             // swap rows j, p of this column and normalise row j
-            cplx xj = col[p], xp = col[j];
-            xj = cmul(xj, ipv);
+            const cplx xj = cmul(col[p], ipv), xp = col[j];
             __syncwarp();
-            if ((threadIdx.x & 31) == 0) { col[p] = xp; }
-            __syncwarp();
-            for (int i = threadIdx.x & 31; i < r; i += 32) {
-                if (i == j) continue;
-                cplx v = (i == p) ? xp : col[i];
-                v = csub(v, cmul(colj[i], xj));
+            cplx* nxt = (c == j + 1) ? colbuf + (size_t)((j + 1) & 1) * r : nullptr;
+            for (int i = lane; i < r; i += 32) {
+                cplx v;
+                if (i == j) v = xj;
+                else v = csub((i == p) ? xp : col[i], cmul(colj[i], xj));
                 col[i] = v;
+                if (nxt) __stcg(nxt + i, v);
             }
-            __syncwarp();
-            if ((threadIdx.x & 31) == 0) col[j] = xj;
             __syncwarp();
         }
         if (!grid_barrier(bar, G, err)) return;
     }
 }
 
-__global__ void k_augment(const cplx* K, cplx* M, int r) {
+__global__ void k_augment(const cplx* K, cplx* M, cplx* colbuf, int r) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)r * 2 * r) return;
     const int64_t i = idx % r, c = idx / r;
     M[idx] = (c < r) ? K[i + c * r] : cmk((c - r) == i ? 1.0 : 0.0, 0.0);
+    if (c == 0) colbuf[i] = K[i];
 }
 
 bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
-    cplx* M = nullptr;
+    cplx *M = nullptr, *colbuf = nullptr;
     BEM_CUDA(h, cudaMallocAsync((void**)&M, sizeof(cplx) * (size_t)r * 2 * r, h->stream));
-    BEM_TIMED(h, "k_augment", (k_augment<<<(unsigned)(((int64_t)r * 2 * r + 255) / 256), 256, 0, h->stream>>>(K, M, r)));
+    BEM_CUDA(h, cudaMallocAsync((void**)&colbuf, sizeof(cplx) * (size_t)r * 2, h->stream));
+    BEM_TIMED(h, "k_augment", (k_augment<<<(unsigned)(((int64_t)r * 2 * r + 255) / 256), 256, 0, h->stream>>>(K, M, colbuf, r)));
     BEM_LAUNCH(h, "k_augment");
     const size_t smem = sizeof(cplx) * (size_t)r;
     if (smem > 48 * 1024)
@@ -673,7 +821,7 @@ bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
     if (per < 1) return bem_fail(h, BEM_E_CUDA, "k_gauss_jordan cannot be resident");
     int G = std::min(nsm * per, std::max(1, (2 * r + 7) / 8));
     BEM_CUDA(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), h->stream));
-    void* args[] = {&M, &r, &h->bar, &h->dev_err};
+    void* args[] = {&M, &r, &colbuf, &h->bar, &h->dev_err};
     cudaError_t lerr;
     BEM_TIMED(h, "k_gauss_jordan",
               lerr = cudaLaunchCooperativeKernel((const void*)k_gauss_jordan, dim3(G), dim3(256), args, smem, h->stream));
@@ -682,6 +830,7 @@ bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
     BEM_CUDA(h, cudaMemcpy2DAsync(Kinv, sizeof(cplx) * r, M + (size_t)r * r, sizeof(cplx) * r,
                                   sizeof(cplx) * r, r, cudaMemcpyDeviceToDevice, h->stream));
     cudaFreeAsync(M, h->stream);
+    cudaFreeAsync(colbuf, h->stream);
     return BEM_OK;
 }
 

@@ -399,12 +399,22 @@ __global__ void k_exp_cols(const void* src, int is_real, int64_t K, int64_t m, i
     }
 }
 
+// bf16 bits of d 2^{-7s} for an integer |d| <= 128: d becomes a float through the
+// 1.5 2^23 bias (integer add, one FADD; the FP64 pipe's 64-bit integer conversion is
+// avoided), the power of two is exact, and with at most 8 significant bits the upper half
+// of the float is the bf16 value.
+__device__ __forceinline__ uint32_t digit_bf16(int d, int s) {
+    const float f = (__int_as_float(0x4B400000 + d) - 12582912.0f) * __int_as_float((127 - 7 * s) << 23);
+    return __float_as_uint(f) >> 16;
+}
+
 // val 2^-e in (-1, 1) -> S slices: X = round(val 2^{7S - e}) (one rounding, half away from
 // zero), then balanced base-128 digits from the least significant up: d in [-64, 63] for
-// s >= 1 and the leading |d_0| <= 128; slice s stores d_s 2^{-7s} (exact in bf16).  X is
-// formed from the significand and exponent fields with integer shifts: |val| < 2^e makes
-// the right shift 1075 + e - 7S - E at least 53 - 7S > 0.  Zeros and subnormals give 0.
-__device__ __forceinline__ void split_digits(double val, int e, int S, float* d) {
+// s >= 1 and the leading |d_0| <= 128; slice s stores d_s 2^{-7s} (exact in bf16), returned
+// here as bf16 bit patterns.  X is formed from the significand and exponent fields with
+// integer shifts: |val| < 2^e makes the right shift 1075 + e - 7S - E at least 53 - 7S > 0.
+// Zeros and subnormals give 0.
+__device__ __forceinline__ void split_digits(double val, int e, int S, uint32_t* d) {
     const long long b = __double_as_longlong(val);
     const int E = (int)((b >> 52) & 0x7FF);
     const int sh = 1075 + e - 7 * S - E;
@@ -416,13 +426,13 @@ __device__ __forceinline__ void split_digits(double val, int e, int S, float* d)
     }
 #pragma unroll
     for (int s = TC_SMAX - 1; s >= 1; --s) {
-        if (s >= S) { d[s] = 0.f; continue; }
-        long long q = X & 127;
+        if (s >= S) { d[s] = 0u; continue; }
+        int q = (int)(X & 127);
         if (q >= 64) q -= 128;
         X = (X - q) >> 7;
-        d[s] = (float)q * __int_as_float((127 - 7 * s) << 23);
+        d[s] = digit_bf16(q, s);
     }
-    d[0] = (float)X;
+    d[0] = digit_bf16((int)X, 0);
 }
 
 // A' slices: out[s][i][kp], kp = 2k + c, padded with zeros to Kp.  Each complex entry (k)
@@ -449,14 +459,11 @@ __global__ void k_slice_A(const void* src, int is_real, int conj, int64_t M, int
                 re = x.x; im = conj ? -x.y : x.y;
             }
         }
-        float dr[TC_SMAX], di[TC_SMAX];
+        uint32_t dr[TC_SMAX], di[TC_SMAX];
         split_digits(re, ei, S, dr);
         split_digits(im, ei, S, di);
 #pragma unroll
-        for (int s = 0; s < TC_SMAX; ++s) {
-            const __nv_bfloat162 b = __floats2bfloat162_rn(dr[s], di[s]);
-            packed[s][v] = *reinterpret_cast<const uint32_t*>(&b);
-        }
+        for (int s = 0; s < TC_SMAX; ++s) packed[s][v] = dr[s] | (di[s] << 16);   // (re, im) as bf16x2
     }
     uint4* o = reinterpret_cast<uint4*>(out + i * Kp + 2 * k0);
     const size_t stride16 = (size_t)M * Kp / 8;     // one slice, in 16-byte units
@@ -482,15 +489,13 @@ __global__ void k_slice_B(const void* src, int is_real, int64_t K, int64_t m, in
             if (is_real) { re = ((const double*)src)[k * sb_k + j * sb_j]; }
             else { const double2 x = ((const double2*)src)[k * sb_k + j * sb_j]; re = x.x; im = x.y; }
         }
-        float dr[TC_SMAX], di[TC_SMAX];
+        uint32_t dr[TC_SMAX], di[TC_SMAX];
         split_digits(re, fe, S, dr);
         split_digits(im, fe, S, di);
 #pragma unroll
         for (int s = 0; s < TC_SMAX; ++s) {
-            const __nv_bfloat162 b0 = __floats2bfloat162_rn(dr[s], -di[s]);
-            const __nv_bfloat162 b1 = __floats2bfloat162_rn(di[s], dr[s]);
-            p0[s][v] = *reinterpret_cast<const uint32_t*>(&b0);
-            p1[s][v] = *reinterpret_cast<const uint32_t*>(&b1);
+            p0[s][v] = dr[s] | ((di[s] ^ 0x8000u) << 16);   // (Re, -Im): flip the sign bit
+            p1[s][v] = di[s] | (dr[s] << 16);               // (Im, Re)
         }
     }
     uint4* o0 = reinterpret_cast<uint4*>(out + (2 * j) * Kp + 2 * k0);
