@@ -317,7 +317,7 @@ bem_status compress_compact(bem_handle h, double rel_tol, int64_t* rank_out) {
     if ((st = apply_gram_inverse(h, 1, h->Bs, X, nullptr, N, nc, nc, 1, h->hbar, true)) != BEM_OK) return st;
     // B^ = X^H: pivoted QR X P = Q R, then the left singular vectors of R^H, rows permuted
     // back by P, are those of B^
-    if ((st = launch_house_qr(h, X, N, (int)nc, R, perm)) != BEM_OK) return st;
+    if ((st = launch_house_qr(h, X, N, (int)nc, R, perm, h->opt.prec == BEM_MIXED_BF16)) != BEM_OK) return st;
     if ((st = launch_jacobi_svd(h, R, (int)nc, perm, h->sigma, h->E)) != BEM_OK) return st;
     std::vector<double> sig(nc);
     BEM_CUDA(h, cudaMemcpyAsync(sig.data(), h->sigma, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->stream));

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "bessel.cuh"
+#include "dfloat.cuh"
 #include "kernels.h"
 
 #define GL_MAXQ 16
@@ -547,83 +548,19 @@ __device__ __forceinline__ void tile_of(int L, int nT, int& ti, int& tj) {
     tj = ti + d;
 }
 
-// ---------------------------------------------------------------------------------------
-// Double-float arithmetic for the S/N far field.  GB300 issues FP32 at 64x its FP64 rate,
-// so the separated pairs -- nearly all of the N^2/2 pair integrals -- are computed with
-// unevaluated sums hi + lo of two floats (about 48 significant bits): Dekker's product via
-// fmaf and Knuth's two-sum.  The _rn intrinsics keep the compiler from contracting or
-// reassociating the error terms.  Accuracy is relative to the operands' magnitudes, which
-// is what the entry tolerance (relative to max |S|, max |N|) asks for.
-// ---------------------------------------------------------------------------------------
-struct dfl { float hi, lo; };
-struct cdfl { dfl re, im; };
-
-__device__ __forceinline__ dfl dfl_mk(float2 v) { return {v.x, v.y}; }
-__device__ __forceinline__ dfl dfl_from(double x) {
-    const float h = __double2float_rn(x);
-    return {h, __double2float_rn(x - (double)h)};
+// table interval of u = z^2 (BTAB_NINT or beyond, or negative, outside the table)
+__device__ __forceinline__ int btab_index(float uhi) {
+    const float zf = sqrtf(uhi);
+    if (zf < (float)BTAB_ZLIN) {
+        const int bits = __float_as_int(zf);
+        return (((bits >> 23) & 255) - 127 - BTAB_LOG_EMIN) * 8 + ((bits >> 20) & 7);
+    }
+    return BTAB_NLOG + (int)fminf((zf - (float)BTAB_ZLIN) * (float)(1.0 / BTAB_W), (float)BTAB_NINT);
 }
-// exact float -> double by moving the bit fields (the FP64 pipe's conversion is as slow as
-// its arithmetic); subnormal floats become zero
-__device__ __forceinline__ double f2d_exact(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 255u;
-    if (e == 0u) return 0.0;
-    const unsigned hiw = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
-    return __hiloint2double((int)hiw, (int)(u << 29));
-}
-__device__ __forceinline__ double dfl_to(dfl a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
-__device__ __forceinline__ dfl dfl_qts(float s, float e) {    // |s| >= |e|
-    const float h = __fadd_rn(s, e);
-    return {h, __fsub_rn(e, __fsub_rn(h, s))};
-}
-__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
-    const float s = __fadd_rn(a.hi, b.hi);
-    const float bb = __fsub_rn(s, a.hi);
-    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
-    return dfl_qts(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ dfl dfl_neg(dfl a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ dfl dfl_sub(dfl a, dfl b) { return dfl_add(a, dfl_neg(b)); }
-__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    return dfl_qts(p, e);
-}
-// a * b + c
-__device__ __forceinline__ dfl dfl_fma(dfl a, dfl b, dfl c) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float pe = fmaf(a.hi, b.hi, -p);
-    pe = fmaf(a.hi, b.lo, pe);
-    pe = fmaf(a.lo, b.hi, pe);
-    const float s = __fadd_rn(p, c.hi);
-    const float bb = __fsub_rn(s, p);
-    const float e = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.hi, bb));
-    return dfl_qts(s, __fadd_rn(e, __fadd_rn(pe, c.lo)));
-}
-__device__ __forceinline__ dfl dfl_scale(dfl a, float p2) { return {a.hi * p2, a.lo * p2}; }   // p2 a power of 2
-__device__ __forceinline__ cdfl cdfl_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
-__device__ __forceinline__ cdfl cdfl_add(cdfl a, cdfl b) { return {dfl_add(a.re, b.re), dfl_add(a.im, b.im)}; }
-__device__ __forceinline__ cdfl cdfl_fma_real(dfl w, cdfl g, cdfl acc) {   // w g + acc
-    return {dfl_fma(w, g.re, acc.re), dfl_fma(w, g.im, acc.im)};
-}
-__device__ __forceinline__ cdfl cdfl_from(cplx z) { return {dfl_from(z.x), dfl_from(z.y)}; }
-__device__ __forceinline__ cplx cdfl_to(cdfl z) { return cmk(dfl_to(z.re), dfl_to(z.im)); }
-__device__ __forceinline__ float4 cdfl_pack(cdfl z) { return make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo); }
-__device__ __forceinline__ cdfl cdfl_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
 
 // J0(z), Y0(z) at u = z^2 from the double-float table (FP64 routines outside it)
 __device__ __forceinline__ void bessel_u_df(const float4* __restrict__ tab, dfl u, dfl& J0, dfl& Y0) {
-    const float zf = sqrtf(u.hi);
-    int i;
-    if (zf < (float)BTAB_ZLIN) {
-        const int bits = __float_as_int(zf);
-        i = (((bits >> 23) & 255) - 127 - BTAB_LOG_EMIN) * 8 + ((bits >> 20) & 7);
-    } else {
-        i = BTAB_NLOG + (int)((zf - (float)BTAB_ZLIN) * (float)(1.0 / BTAB_W));
-    }
+    const int i = btab_index(u.hi);
     if (i < 0 || i >= BTAB_NINT) {
         const Bessel01 b = bessel01<false>(sqrt(dfl_to(u)));
         J0 = dfl_from(b.J0);
@@ -645,6 +582,34 @@ __device__ __forceinline__ void bessel_u_df(const float4* __restrict__ tab, dfl 
     Y0 = rY;
 }
 
+// two arguments at once: four independent Horner chains keep the FP32 pipe busy
+__device__ __forceinline__ void bessel_u_df2(const float4* __restrict__ tab, dfl ua, dfl ub, dfl& Ja, dfl& Ya,
+                                             dfl& Jb, dfl& Yb) {
+    const int ia = btab_index(ua.hi), ib = btab_index(ub.hi);
+    if (ia < 0 || ia >= BTAB_NINT || ib < 0 || ib >= BTAB_NINT) {
+        bessel_u_df(tab, ua, Ja, Ya);
+        bessel_u_df(tab, ub, Jb, Yb);
+        return;
+    }
+    const float4* ca = tab + (size_t)ia * (BTAB_DF_STRIDE / 4);
+    const float4* cb = tab + (size_t)ib * (BTAB_DF_STRIDE / 4);
+    const float4 ha = __ldg(ca), hb = __ldg(cb);
+    const dfl ta = dfl_mul(dfl_sub(ua, dfl{ha.x, ha.y}), dfl{ha.z, ha.w});
+    const dfl tb = dfl_mul(dfl_sub(ub, dfl{hb.x, hb.y}), dfl{hb.z, hb.w});
+    float4 xa = __ldg(ca + BTAB_NC), xb = __ldg(cb + BTAB_NC);
+    dfl rJa = {xa.x, xa.y}, rYa = {xa.z, xa.w}, rJb = {xb.x, xb.y}, rYb = {xb.z, xb.w};
+#pragma unroll
+    for (int j = BTAB_NC - 2; j >= 0; --j) {
+        xa = __ldg(ca + 1 + j);
+        xb = __ldg(cb + 1 + j);
+        rJa = dfl_fma(rJa, ta, dfl{xa.x, xa.y});
+        rYa = dfl_fma(rYa, ta, dfl{xa.z, xa.w});
+        rJb = dfl_fma(rJb, tb, dfl{xb.x, xb.y});
+        rYb = dfl_fma(rYb, tb, dfl{xb.z, xb.w});
+    }
+    Ja = rJa; Ya = rYa; Jb = rJb; Yb = rYb;
+}
+
 // Separated pair (S/N only), q x q tensor Gauss-Legendre in double-float.  b = y_f(0) -
 // x_e(0), ue = h_e t_e, vf = h_f t_f; returns A_ab with I_ab = h_e h_f A_ab.  The sum over
 // the f-nodes runs first (two row sums R_b), then the e-node weights multiply them.
@@ -656,13 +621,29 @@ __device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, 
         const dfl s = dfl_mk(c_gx_df[o + i]);
         const dfl cx = dfl_sub(bx, dfl_mul(s, uex)), cy = dfl_sub(by, dfl_mul(s, uey));
         cdfl R0 = cdfl_zero(), R1 = cdfl_zero();
-        for (int j = 0; j < q; ++j) {
+        int j = 0;
+        for (; j + 1 < q; j += 2) {          // two nodes per pass
+            const dfl ta = dfl_mk(c_gx_df[o + j]), tb = dfl_mk(c_gx_df[o + j + 1]);
+            const dfl dxa = dfl_fma(ta, vfx, cx), dya = dfl_fma(ta, vfy, cy);
+            const dfl dxb = dfl_fma(tb, vfx, cx), dyb = dfl_fma(tb, vfy, cy);
+            const dfl r2a = dfl_fma(dxa, dxa, dfl_mul(dya, dya));
+            const dfl r2b = dfl_fma(dxb, dxb, dfl_mul(dyb, dyb));
+            dfl Ja, Ya, Jb, Yb;
+            bessel_u_df2(tab, dfl_mul(k2, r2a), dfl_mul(k2, r2b), Ja, Ya, Jb, Yb);
+            const cdfl ga = {dfl_scale(Ya, -0.25f), dfl_scale(Ja, 0.25f)};   // (i/4) (J0 + i Y0)
+            const cdfl gb = {dfl_scale(Yb, -0.25f), dfl_scale(Jb, 0.25f)};
+            R0 = cdfl_fma_real(dfl_mk(c_gw0_df[o + j]), ga, R0);
+            R1 = cdfl_fma_real(dfl_mk(c_gw1_df[o + j]), ga, R1);
+            R0 = cdfl_fma_real(dfl_mk(c_gw0_df[o + j + 1]), gb, R0);
+            R1 = cdfl_fma_real(dfl_mk(c_gw1_df[o + j + 1]), gb, R1);
+        }
+        if (j < q) {
             const dfl t = dfl_mk(c_gx_df[o + j]);
             const dfl dx = dfl_fma(t, vfx, cx), dy = dfl_fma(t, vfy, cy);
             const dfl r2 = dfl_fma(dx, dx, dfl_mul(dy, dy));
             dfl J0, Y0;
             bessel_u_df(tab, dfl_mul(k2, r2), J0, Y0);
-            const cdfl g = {dfl_scale(Y0, -0.25f), dfl_scale(J0, 0.25f)};   // (i/4) (J0 + i Y0)
+            const cdfl g = {dfl_scale(Y0, -0.25f), dfl_scale(J0, 0.25f)};
             R0 = cdfl_fma_real(dfl_mk(c_gw0_df[o + j]), g, R0);
             R1 = cdfl_fma_real(dfl_mk(c_gw1_df[o + j]), g, R1);
         }
@@ -681,7 +662,7 @@ __device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, 
 // pairs keep their relative geometry to double-float precision.  Self and adjacent pairs
 // come from the FP64 table of k_near_pairs.
 template <int T>
-__global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
+__global__ void __launch_bounds__(256, 2) k_assemble_sn(AsmParams p) {
     int ti, tj;
     tile_of((int)blockIdx.x, p.nT, ti, tj);
     constexpr int TP = T + 1;

@@ -1,0 +1,69 @@
+// Double-float arithmetic: unevaluated sums hi + lo of two floats (about 48 significant
+// bits).  GB300 issues FP32 at 64x its FP64 rate, so FP64-accurate work that is bound by
+// arithmetic (the far-field assembly, the mixed path's QR) runs in this form on the FP32
+// pipe.  Dekker's product via fmaf and Knuth's two-sum; the _rn intrinsics keep the
+// compiler from contracting or reassociating the error terms.  Accuracy is relative to the
+// operands' magnitudes.
+#pragma once
+
+#include "common.cuh"
+
+struct dfl { float hi, lo; };
+struct cdfl { dfl re, im; };
+
+__device__ __forceinline__ dfl dfl_mk(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ dfl dfl_from(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+// exact float -> double by moving the bit fields (the FP64 pipe's conversion is as slow as
+// its arithmetic); subnormal floats become zero
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 255u;
+    if (e == 0u) return 0.0;
+    const unsigned hiw = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hiw, (int)(u << 29));
+}
+__device__ __forceinline__ double dfl_to(dfl a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
+__device__ __forceinline__ dfl dfl_qts(float s, float e) {    // |s| >= |e|
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return dfl_qts(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl dfl_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl dfl_sub(dfl a, dfl b) { return dfl_add(a, dfl_neg(b)); }
+__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return dfl_qts(p, e);
+}
+// a * b + c
+__device__ __forceinline__ dfl dfl_fma(dfl a, dfl b, dfl c) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = fmaf(a.hi, b.hi, -p);
+    pe = fmaf(a.hi, b.lo, pe);
+    pe = fmaf(a.lo, b.hi, pe);
+    const float s = __fadd_rn(p, c.hi);
+    const float bb = __fsub_rn(s, p);
+    const float e = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.hi, bb));
+    return dfl_qts(s, __fadd_rn(e, __fadd_rn(pe, c.lo)));
+}
+__device__ __forceinline__ dfl dfl_scale(dfl a, float p2) { return {a.hi * p2, a.lo * p2}; }   // p2 a power of 2
+__device__ __forceinline__ cdfl cdfl_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+__device__ __forceinline__ cdfl cdfl_add(cdfl a, cdfl b) { return {dfl_add(a.re, b.re), dfl_add(a.im, b.im)}; }
+__device__ __forceinline__ cdfl cdfl_fma_real(dfl w, cdfl g, cdfl acc) {   // w g + acc
+    return {dfl_fma(w, g.re, acc.re), dfl_fma(w, g.im, acc.im)};
+}
+__device__ __forceinline__ cdfl cdfl_from(cplx z) { return {dfl_from(z.x), dfl_from(z.y)}; }
+__device__ __forceinline__ cplx cdfl_to(cdfl z) { return cmk(dfl_to(z.re), dfl_to(z.im)); }
+__device__ __forceinline__ float4 cdfl_pack(cdfl z) { return make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo); }
+__device__ __forceinline__ cdfl cdfl_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+

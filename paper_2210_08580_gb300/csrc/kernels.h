@@ -43,7 +43,8 @@ bem_status launch_row_scale(bem_ctx* h, const cplx* in, cplx* out, const double*
                             int64_t rows, int64_t cols, int64_t ld);
 bem_status launch_scale_real_cols(bem_ctx* h, const double* in, double* out, const double* s, int pw,
                                   int64_t rows, int64_t cols);
-bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* perm);
+// dfl_arith: double-float arithmetic on the FP32 pipe (X is overwritten in that format)
+bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* perm, bool dfl_arith);
 bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double* sigma, cplx* E);
 bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r);
 bem_status launch_axpby(bem_ctx* h, cplx* y, int64_t ldy, const cplx* x, int64_t ldx, cplx a, cplx b,

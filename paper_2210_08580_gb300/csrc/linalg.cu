@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "kernels.h"
 
 // =========================================================================================
@@ -525,7 +526,207 @@ static bem_status coop_launch(bem_ctx* h, const void* fn, int blocks_wanted, int
     return BEM_OK;
 }
 
-bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* perm) {
+// The same pivoted QR for the mixed path with X held in double-float (float4 per complex
+// entry: re.hi, re.lo, im.hi, im.lo).  Dots, updates and norms run on the FP32 pipe;
+// cross-CTA partial sums are exchanged in FP64, and the reflector (a handful of FP64
+// operations) is formed by one thread and shared.  Backward error about 1e-13 relative,
+// far below the compression tolerances the path uses.
+__device__ __forceinline__ cdfl cdfl_ld(const float4* p) { return cdfl_unpack(*p); }
+__device__ __forceinline__ void cdfl_conj_fma(cdfl& acc, const cdfl& v, const cdfl& x) {   // acc += conj(v) x
+    acc.re = dfl_fma(v.re, x.re, acc.re);
+    acc.re = dfl_fma(v.im, x.im, acc.re);
+    acc.im = dfl_fma(v.re, x.im, acc.im);
+    acc.im = dfl_fma(dfl_neg(v.im), x.re, acc.im);
+}
+__device__ __forceinline__ dfl dfl_norm_acc(const cdfl& x, dfl acc) {
+    return dfl_fma(x.im, x.im, dfl_fma(x.re, x.re, acc));
+}
+
+__global__ void k_to_dfl(float4* X, int64_t count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double2 v = reinterpret_cast<const double2*>(X)[i];
+    X[i] = cdfl_pack({dfl_from(v.x), dfl_from(v.y)});
+}
+
+__global__ void __launch_bounds__(256) k_house_qr_df(float4* X, int64_t N, int n, cplx* R, int* perm, double* partC,
+                                                     unsigned long long* cnq, cplx* partW, unsigned* bar, int* err) {
+    __shared__ double red[32];
+    __shared__ float4 wred[8][33];
+    __shared__ float2 nred[8][33];
+    __shared__ float4 wsm[1024];
+    __shared__ int cmap[1024];
+    __shared__ double qscale_s, nrm2_s, tau_s;
+    __shared__ cplx alpha_s;
+    __shared__ float4 vj_s;
+    __shared__ unsigned long long pbest[8];
+    __shared__ int pidx[8];
+    const unsigned G = gridDim.x;
+    const int64_t rb = (N + G - 1) / G;
+    const int64_t r0 = (int64_t)blockIdx.x * rb, r1 = min(N, r0 + rb);
+    const int tid = threadIdx.x, cg = tid & 31, rg = tid >> 5, lane = tid & 31;
+    for (int c = tid; c < n; c += blockDim.x) cmap[c] = c;
+    // partial column norms over my rows
+    for (int cb = 0; cb < n; cb += 32) {
+        const int c = cb + cg;
+        dfl acc = {0.f, 0.f};
+        if (c < n)
+            for (int64_t i = r0 + rg; i < r1; i += 8) acc = dfl_norm_acc(cdfl_ld(X + i * n + c), acc);
+        nred[rg][cg] = make_float2(acc.hi, acc.lo);
+        __syncthreads();
+        if (rg == 0 && c < n) {
+            dfl t = dfl_mk(nred[0][cg]);
+            for (int q = 1; q < 8; ++q) t = dfl_add(t, dfl_mk(nred[q][cg]));
+            partC[(int64_t)blockIdx.x * n + c] = dfl_to(t);
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(bar, G, err)) return;
+    {
+        double mx = 0.0;
+        for (int c = tid; c < n; c += blockDim.x) {
+            double t = 0.0;
+            for (unsigned q = 0; q < G; ++q) t += partC[(int64_t)q * n + c];
+            mx = fmax(mx, t);
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) red[rg] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            double m2 = 0.0;
+            for (int q = 0; q < 8; ++q) m2 = fmax(m2, red[q]);
+            qscale_s = (m2 > 0.0) ? 4.0e18 / m2 : 0.0;
+        }
+        __syncthreads();
+        for (int c = tid; c < n; c += blockDim.x)
+            atomicAdd(cnq + c, __double2ull_rz(partC[(int64_t)blockIdx.x * n + c] * qscale_s));
+    }
+    const double qscale = qscale_s;
+    for (int j = 0; j < n; ++j) {
+        if (!grid_barrier(bar, G, err)) return;
+        // (1) pivot
+        const unsigned long long* cq = cnq + (size_t)(j & 1) * n;
+        unsigned long long best = 0ull;
+        int bi = n;
+        for (int c = j + tid; c < n; c += blockDim.x) {
+            const unsigned long long v = __ldcg(cq + cmap[c]);
+            if (bi == n || v > best) { best = v; bi = c; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oi < n && (bi == n || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { pbest[rg] = best; pidx[rg] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long b2 = pbest[0];
+            int i2 = pidx[0];
+            for (int q = 1; q < 8; ++q)
+                if (pidx[q] < n && (i2 == n || pbest[q] > b2 || (pbest[q] == b2 && pidx[q] < i2))) {
+                    b2 = pbest[q]; i2 = pidx[q];
+                }
+            if (i2 > j && i2 < n) { const int t = cmap[j]; cmap[j] = cmap[i2]; cmap[i2] = t; }
+        }
+        if (blockIdx.x == 0)
+            for (int c = tid; c < n; c += blockDim.x) cnq[(size_t)((j + 1) & 1) * n + c] = 0ull;
+        __syncthreads();
+        const int pj = cmap[j];
+        double nrm2 = 0.0;
+        for (unsigned q = tid; q < G; q += blockDim.x) nrm2 += partC[(int64_t)q * n + pj];
+        nrm2 = block_sum(nrm2, red);
+        // (2) reflector, formed once
+        if (tid == 0) {
+            const cdfl xd = cdfl_ld(X + (int64_t)j * n + pj);
+            const cplx xjj = cmk(dfl_to(xd.re), dfl_to(xd.im));
+            double tau = 0.0;
+            cplx alpha = cmk(0, 0), vj = cmk(0, 0);
+            if (nrm2 > 0.0) {
+                const double a = sqrt(nrm2), ax = sqrt(cabs2(xjj));
+                const cplx ph = (ax > 0.0) ? cmk(xjj.x / ax, xjj.y / ax) : cmk(1, 0);
+                alpha = cmk(-ph.x * a, -ph.y * a);
+                vj = csub(xjj, alpha);
+                const double vn2 = nrm2 - ax * ax + cabs2(vj);
+                tau = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
+            }
+            tau_s = tau; alpha_s = alpha; nrm2_s = nrm2;
+            vj_s = cdfl_pack({dfl_from(vj.x), dfl_from(vj.y)});
+            if (j >= r0 && j < r1) R[j + (int64_t)j * n] = (nrm2 > 0.0) ? alpha : cmk(0, 0);
+        }
+        __syncthreads();
+        const double tau = tau_s;
+        const cdfl vjd = cdfl_unpack(vj_s);
+        // (3) partial dots w_c = sum_i conj(v_i) X[i, c], c > j
+        for (int cb = j + 1; cb < n; cb += 32) {
+            const int c = cb + cg;
+            cdfl acc = cdfl_zero();
+            if (c < n && tau != 0.0) {
+                const int pc = cmap[c];
+                for (int64_t i = max(r0, (int64_t)j) + rg; i < r1; i += 8) {
+                    const cdfl vi = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
+                    cdfl_conj_fma(acc, vi, cdfl_ld(X + i * n + pc));
+                }
+            }
+            wred[rg][cg] = cdfl_pack(acc);
+            __syncthreads();
+            if (rg == 0 && c < n) {
+                cdfl t = cdfl_unpack(wred[0][cg]);
+                for (int q = 1; q < 8; ++q) t = cdfl_add(t, cdfl_unpack(wred[q][cg]));
+                partW[(int64_t)blockIdx.x * n + c] = cmk(dfl_to(t.re), dfl_to(t.im));
+            }
+            __syncthreads();
+        }
+        if (!grid_barrier(bar, G, err)) return;
+        // (4) reduce w; update my rows and accumulate their trailing norms
+        for (int c = j + 1 + tid; c < n; c += blockDim.x) {
+            cplx t = cmk(0, 0);
+            for (unsigned q = 0; q < G; ++q) t = cadd(t, __ldcg(partW + (int64_t)q * n + c));
+            // x <- x - v w : store -w so the update is two fused products
+            wsm[c] = cdfl_pack({dfl_from(-tau * t.x), dfl_from(-tau * t.y)});
+        }
+        __syncthreads();
+        for (int cb = j + 1; cb < n; cb += 32) {
+            const int c = cb + cg;
+            dfl acc = {0.f, 0.f};
+            if (c < n) {
+                const int pc = cmap[c];
+                const cdfl nw = cdfl_unpack(wsm[c]);
+                for (int64_t i = max(r0, (int64_t)j) + rg; i < r1; i += 8) {
+                    cdfl x = cdfl_ld(X + i * n + pc);
+                    if (tau != 0.0) {
+                        const cdfl vi = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
+                        // x += v (-w)
+                        x.re = dfl_fma(vi.re, nw.re, dfl_fma(dfl_neg(vi.im), nw.im, x.re));
+                        x.im = dfl_fma(vi.re, nw.im, dfl_fma(vi.im, nw.re, x.im));
+                        X[i * n + pc] = cdfl_pack(x);
+                    }
+                    if (i > j) acc = dfl_norm_acc(x, acc);
+                }
+            }
+            nred[rg][cg] = make_float2(acc.hi, acc.lo);
+            __syncthreads();
+            if (rg == 0 && c < n) {
+                dfl t = dfl_mk(nred[0][cg]);
+                for (int q = 1; q < 8; ++q) t = dfl_add(t, dfl_mk(nred[q][cg]));
+                const double td = dfl_to(t);
+                partC[(int64_t)blockIdx.x * n + cmap[c]] = td;
+                atomicAdd(cnq + (size_t)((j + 1) & 1) * n + cmap[c], __double2ull_rz(td * qscale));
+            }
+            __syncthreads();
+        }
+    }
+    for (int64_t j = max(r0, (int64_t)0); j < min(r1, (int64_t)n); ++j)
+        for (int c = tid; c < n; c += blockDim.x)
+            if (c != j) {
+                cplx v = cmk(0, 0);
+                if (c > j) { const cdfl x = cdfl_ld(X + j * n + cmap[c]); v = cmk(dfl_to(x.re), dfl_to(x.im)); }
+                R[j + (int64_t)c * n] = v;
+            }
+    if (blockIdx.x == 0)
+        for (int c = tid; c < n; c += blockDim.x) perm[c] = cmap[c];
+}
+
+bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* perm, bool dfl_arith) {
     if (n > 1024) return bem_fail(h, BEM_E_UNSUPPORTED, "QR: more than 1024 columns");
     if (N < n) return bem_fail(h, BEM_E_INVALID, "QR: fewer rows than columns");
     int nsm = 0;
@@ -540,7 +741,15 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* 
     BEM_CUDA(h, cudaMemsetAsync(cnq, 0, sizeof(unsigned long long) * 2 * (size_t)n, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&partW, sizeof(cplx) * (size_t)G * n, h->stream));
     void* args[] = {&X, &N, &n, &R, &perm, &partC, &cnq, &partW, &h->bar, &h->dev_err};
-    BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr, G, 256, args, "k_house_qr"));
+    if (dfl_arith) {
+        // X in place as double-float pairs (same 16 bytes per entry)
+        const int64_t cnt = N * (int64_t)n;
+        BEM_TIMED(h, "k_to_dfl", (k_to_dfl<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(reinterpret_cast<float4*>(X), cnt)));
+        BEM_LAUNCH(h, "k_to_dfl");
+        BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr_df, G, 256, args, "k_house_qr_df"));
+    } else {
+        BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr, G, 256, args, "k_house_qr"));
+    }
     cudaFreeAsync(partC, h->stream);
     cudaFreeAsync(cnq, h->stream);
     cudaFreeAsync(partW, h->stream);
@@ -580,10 +789,14 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // acquire at GPU scope; column data bypass L1).  A CTA waits only on the two CTAs that
 // last touched its columns, so consecutive rounds overlap across the grid.  One grid
 // barrier per sweep decides convergence.  Waits are bounded (DEVERR_TIMEOUT).
-__global__ void __launch_bounds__(JAC_NT) k_jacobi(cplx* X, int n, int* ver, int* flags, int max_sweeps,
+// The columns are held in double-float (float4 per complex entry): dot products, their
+// reductions and the rotation run on the FP32 pipe; the rotation parameters are formed
+// once per pair in FP64 by one thread.
+__global__ void __launch_bounds__(JAC_NT) k_jacobi(float4* X, int n, int* ver, int* flags, int max_sweeps,
                                                    unsigned* bar, int* err) {
-    __shared__ double red[JAC_NT / 32][4];
-    __shared__ int s_ok;
+    __shared__ float2 red[JAC_NT / 32][4];
+    __shared__ int s_ok, s_rot;
+    __shared__ float2 s_rotp[5];                  // c, sem (re, im), sep (re, im) as double-float
     const unsigned G = gridDim.x;
     const int np = n + (n & 1);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -610,45 +823,76 @@ __global__ void __launch_bounds__(JAC_NT) k_jacobi(cplx* X, int n, int* ver, int
                 __syncthreads();
                 if (!s_ok) return;
                 if (q < n) {       // both columns real (p < q)
-                    cplx* Xp = X + (int64_t)p * n;
-                    cplx* Xq = X + (int64_t)q * n;
-                    cplx x[EPT], y[EPT];
-                    double a = 0.0, b = 0.0, gr = 0.0, gi = 0.0;
+                    float4* Xp = X + (int64_t)p * n;
+                    float4* Xq = X + (int64_t)q * n;
+                    cdfl x[EPT], y[EPT];
+                    dfl a = {0.f, 0.f}, b = {0.f, 0.f}, gr = {0.f, 0.f}, gi = {0.f, 0.f};
 #pragma unroll
                     for (int e = 0; e < EPT; ++e) {
                         const int i = tid + JAC_NT * e;
-                        x[e] = (i < n) ? __ldcg(Xp + i) : cmk(0, 0);
-                        y[e] = (i < n) ? __ldcg(Xq + i) : cmk(0, 0);
-                        a += cabs2(x[e]); b += cabs2(y[e]);
-                        gr += x[e].x * y[e].x + x[e].y * y[e].y;     // conj(x) y
-                        gi += x[e].x * y[e].y - x[e].y * y[e].x;
+                        x[e] = (i < n) ? cdfl_unpack(__ldcg(Xp + i)) : cdfl_zero();
+                        y[e] = (i < n) ? cdfl_unpack(__ldcg(Xq + i)) : cdfl_zero();
+                        if (i < n) {
+                            a = dfl_fma(x[e].im, x[e].im, dfl_fma(x[e].re, x[e].re, a));
+                            b = dfl_fma(y[e].im, y[e].im, dfl_fma(y[e].re, y[e].re, b));
+                            gr = dfl_fma(x[e].im, y[e].im, dfl_fma(x[e].re, y[e].re, gr));          // conj(x) y
+                            gi = dfl_fma(dfl_neg(x[e].im), y[e].re, dfl_fma(x[e].re, y[e].im, gi));
+                        }
                     }
-                    for (int o = 16; o > 0; o >>= 1) {
-                        a += __shfl_xor_sync(0xffffffffu, a, o);
-                        b += __shfl_xor_sync(0xffffffffu, b, o);
-                        gr += __shfl_xor_sync(0xffffffffu, gr, o);
-                        gi += __shfl_xor_sync(0xffffffffu, gi, o);
-                    }
-                    if (lane == 0) { red[wid][0] = a; red[wid][1] = b; red[wid][2] = gr; red[wid][3] = gi; }
-                    __syncthreads();
-                    a = b = gr = gi = 0.0;
+                    dfl v4[4] = {a, b, gr, gi};
 #pragma unroll
-                    for (int w = 0; w < JAC_NT / 32; ++w) { a += red[w][0]; b += red[w][1]; gr += red[w][2]; gi += red[w][3]; }
-                    const double ag = sqrt(gr * gr + gi * gi);
-                    // converged pair: |x^H y| <= 1e-14 |x| |y|
-                    if (!(ag <= 1e-14 * sqrt(a * b) || ag == 0.0)) {
-                        if (tid == 0) flags[sweep] = 1;
-                        const double zeta = (b - a) / (2.0 * ag);
-                        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-                        const cplx sem = cmk(sn * gr / ag, -sn * gi / ag);       // s e^{-i phi}
-                        const cplx sep = cmk(sn * gr / ag, sn * gi / ag);        // s e^{i phi}
+                    for (int k = 0; k < 4; ++k)
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const dfl t = {__shfl_xor_sync(0xffffffffu, v4[k].hi, o),
+                                           __shfl_xor_sync(0xffffffffu, v4[k].lo, o)};
+                            v4[k] = dfl_add(v4[k], t);
+                        }
+                    if (lane == 0)
+                        for (int k = 0; k < 4; ++k) red[wid][k] = make_float2(v4[k].hi, v4[k].lo);
+                    __syncthreads();
+                    if (tid == 0) {
+                        double sm[4];
+                        for (int k = 0; k < 4; ++k) {
+                            dfl t = dfl_mk(red[0][k]);
+                            for (int w = 1; w < JAC_NT / 32; ++w) t = dfl_add(t, dfl_mk(red[w][k]));
+                            sm[k] = dfl_to(t);
+                        }
+                        const double A = sm[0], B = sm[1], GR = sm[2], GI = sm[3];
+                        const double ag2 = GR * GR + GI * GI;
+                        // converged pair: |x^H y| <= 1e-14 |x| |y|
+                        int rot = !(ag2 <= 1e-28 * A * B || ag2 == 0.0);
+                        if (rot) {
+                            flags[sweep] = 1;
+                            const double rag = rsqrt(ag2);
+                            const double zeta = 0.5 * (B - A) * rag;
+                            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                            const double c = rsqrt(1.0 + t * t), sr = c * t * rag;
+                            // c, s e^{-i phi}, s e^{i phi}
+                            const double rp[5] = {c, sr * GR, -sr * GI, sr * GR, sr * GI};
+                            for (int k = 0; k < 5; ++k) {
+                                const dfl d = dfl_from(rp[k]);
+                                s_rotp[k] = make_float2(d.hi, d.lo);
+                            }
+                        }
+                        s_rot = rot;
+                    }
+                    __syncthreads();
+                    if (s_rot) {
+                        const dfl c = dfl_mk(s_rotp[0]);
+                        const cdfl sem = {dfl_mk(s_rotp[1]), dfl_mk(s_rotp[2])};
+                        const cdfl sep = {dfl_mk(s_rotp[3]), dfl_mk(s_rotp[4])};
 #pragma unroll
                         for (int e = 0; e < EPT; ++e) {
                             const int i = tid + JAC_NT * e;
                             if (i >= n) continue;
-                            __stcg(Xp + i, csub(cscale(x[e], c), cmul(sem, y[e])));
-                            __stcg(Xq + i, cadd(cmul(sep, x[e]), cscale(y[e], c)));
+                            // x' = c x - sem y ;  y' = sep x + c y
+                            cdfl xn, yn;
+                            xn.re = dfl_fma(dfl_neg(sem.re), y[e].re, dfl_fma(sem.im, y[e].im, dfl_mul(c, x[e].re)));
+                            xn.im = dfl_fma(dfl_neg(sem.re), y[e].im, dfl_fma(dfl_neg(sem.im), y[e].re, dfl_mul(c, x[e].im)));
+                            yn.re = dfl_fma(sep.re, x[e].re, dfl_fma(dfl_neg(sep.im), x[e].im, dfl_mul(c, y[e].re)));
+                            yn.im = dfl_fma(sep.re, x[e].im, dfl_fma(sep.im, x[e].re, dfl_mul(c, y[e].im)));
+                            __stcg(Xp + i, cdfl_pack(xn));
+                            __stcg(Xq + i, cdfl_pack(yn));
                         }
                     }
                 }
@@ -665,13 +909,18 @@ __global__ void __launch_bounds__(JAC_NT) k_jacobi(cplx* X, int n, int* ver, int
     }
 }
 
-// sigma_c = |X_c|, sorted descending; E[:, rank] = X_c / sigma_c (a unit vector e_c when
-// sigma_c = 0, which is then below any truncation threshold), with its rows put back in
-// the original order when the QR pivoted (E[perm[i], rank] = X[i, c]; perm may be null)
-__global__ void k_sort_sv(const cplx* X, int n, const int* perm, double* sigma, cplx* E, double* tmp) {
+// sigma_c = |X_c| (X in double-float), sorted descending; E[:, rank] = X_c / sigma_c (a
+// unit vector e_c when sigma_c = 0, which is then below any truncation threshold), with its
+// rows put back in the original order when the QR pivoted (E[perm[i], rank] = X[i, c];
+// perm may be null)
+__global__ void k_sort_sv(const float4* X, int n, const int* perm, double* sigma, cplx* E, double* tmp) {
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         double s = 0.0;
-        for (int i = 0; i < n; ++i) s += cabs2(X[(int64_t)c * n + i]);
+        for (int i = 0; i < n; ++i) {
+            const cdfl x = cdfl_unpack(X[(int64_t)c * n + i]);
+            const double re = dfl_to(x.re), im = dfl_to(x.im);
+            s += re * re + im * im;
+        }
         tmp[c] = sqrt(s);
     }
     __syncthreads();
@@ -684,28 +933,31 @@ __global__ void k_sort_sv(const cplx* X, int n, const int* perm, double* sigma, 
         }
         sigma[rank] = sc;
         const double inv = (sc > 0.0) ? 1.0 / sc : 0.0;
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < n; ++i) {
+            const cdfl x = cdfl_unpack(X[(int64_t)c * n + i]);
             E[(int64_t)rank * n + (perm ? perm[i] : i)] =
-                (sc > 0.0) ? cscale(X[(int64_t)c * n + i], inv) : cmk(i == c ? 1.0 : 0.0, 0.0);
+                (sc > 0.0) ? cmk(dfl_to(x.re) * inv, dfl_to(x.im) * inv) : cmk(i == c ? 1.0 : 0.0, 0.0);
+        }
     }
 }
 
-// X = R^H (n x n)
-__global__ void k_conj_transpose(const cplx* R, cplx* X, int n) {
+// X = R^H (n x n) in double-float
+__global__ void k_conj_transpose(const cplx* R, float4* X, int n) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n * n) return;
     const int64_t i = idx % n, j = idx / n;
-    X[idx] = cconj(R[j + i * n]);
+    const cplx v = R[j + i * n];
+    X[idx] = cdfl_pack({dfl_from(v.x), dfl_from(-v.y)});
 }
 
 bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double* sigma, cplx* E) {
     if (n > 1024) return bem_fail(h, BEM_E_UNSUPPORTED, "Jacobi SVD: more than 1024 columns");
-    cplx* X = nullptr;
+    float4* X = nullptr;
     int* flags = nullptr;
     double* tmp = nullptr;
     int* ver = nullptr;
     const int max_sweeps = 40;
-    BEM_CUDA(h, cudaMallocAsync((void**)&X, sizeof(cplx) * (size_t)n * n, h->stream));
+    BEM_CUDA(h, cudaMallocAsync((void**)&X, sizeof(float4) * (size_t)n * n, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&flags, sizeof(int) * max_sweeps, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&ver, sizeof(int) * n, h->stream));
     BEM_CUDA(h, cudaMemsetAsync(ver, 0, sizeof(int) * n, h->stream));
