@@ -52,6 +52,7 @@ __all__ = [
     "rhs_planewave", "rhs_planewave_h", "fourier_basis", "gram_eigs", "filter_literal",
     "calderon_system", "filtered_solve_literal", "filtered_solve_projected",
     "woodbury_solve", "mie_current", "circle_spectra", "g_norm",
+    "farfield_constant", "farfield_matrix", "mie_farfield", "misfit_and_gradients",
 ]
 
 # --------------------------------------------------------------------------------------
@@ -606,3 +607,67 @@ def g_norm(G, x):
     """||x||_G = sqrt(x^H G x) per column (the L2 norm of the P1 current)."""
     x = np.atleast_2d(x.T).T
     return np.sqrt(np.real(np.einsum("ir,ij,jr->r", np.conj(x), G, x)))
+
+
+# --------------------------------------------------------------------------------------
+# Far field and the adjoint gradient of a far-field misfit (differentiation layer)
+# --------------------------------------------------------------------------------------
+
+
+def farfield_constant(k: float) -> complex:
+    """C0 in g(x, y) ~ C0 e^{i k |x|} / sqrt|x| e^{-i k xhat.y} for g = (i/4) H0^(1)(k r)
+    (large-argument Hankel form): C0 = (i/4) sqrt(2/(pi k)) e^{-i pi/4} = e^{i pi/4}/sqrt(8 pi k)."""
+    return complex(np.exp(0.25j * math.pi) / math.sqrt(8.0 * math.pi * k))
+
+
+def farfield_matrix(verts, k: float, obs_angles):
+    """F (nobs, N) with u_inf(xhat_o) = sum_i F[o, i] x_i for the P1 current x = -u_tot.
+
+    Green's representation of the sound-hard problem (d u_tot/d nu = 0 on the curve):
+    u_s(x) = int u_tot(y) d g(x, y)/d nu_y ds_y, and d/d nu_y e^{-i k xhat.y} =
+    -i k (xhat.nu_y) e^{-i k xhat.y}, so
+        F[o, i] = i k C0 int phi_i(y) (xhat_o.nu_y) e^{-i k xhat_o.y} ds_y,
+    which is C0 times the right-hand side f_i of the plane wave travelling along -xhat_o."""
+    obs = np.asarray(obs_angles, dtype=np.float64)
+    return (farfield_constant(k) * rhs_planewave(verts, k, obs + math.pi)).T
+
+
+def mie_farfield(k: float, a: float, theta, phi_inc: float, mmax: int | None = None):
+    """Exact far field of the sound-hard circle of radius a for u_inc = exp(i k d.x):
+    u_s = -sum_m i^|m| J'_|m|(ka)/H'_|m|(ka) H_|m|(k r) e^{i m (theta - phi)} and
+    H_m(k r) ~ sqrt(2/(pi k r)) e^{i (k r - m pi/2 - pi/4)} give
+    u_inf(theta) = -sqrt(2/(pi k)) e^{-i pi/4} sum_m J'_|m|(ka)/H'_|m|(ka) e^{i m (theta - phi)}."""
+    theta = np.asarray(theta, dtype=np.float64)
+    if mmax is None:
+        mmax = int(k * a + 40)
+    ka = k * a
+    out = np.zeros(theta.shape, dtype=np.complex128)
+    for m in range(-mmax, mmax + 1):
+        out += special.jvp(abs(m), ka) / special.h1vp(abs(m), ka) * np.exp(1j * m * (theta - phi_inc))
+    return -math.sqrt(2.0 / (math.pi * k)) * np.exp(-0.25j * math.pi) * out
+
+
+def misfit_and_gradients(route: dict, F, amplitudes, target):
+    """Misfit J(a, v) = sum_{o,w} |u_ow - t_ow|^2 of the far fields u = F x, x_w = A^-1 (a_w v_w),
+    A = beta I + U_x V_x^H the compressed filtered operator of filtered_solve_projected
+    (x-coordinates), v_w its preconditioned right-hand sides.
+
+    Gradients in the convention dJ/dRe z + i dJ/dIm z (the one torch uses for complex
+    leaves):
+        grad_a_w = 2 (F x0_w)^H r_w,  x0_w = A^-1 v_w,  r = u - t;
+        grad_v_w = 2 A^-H F^H r_w  (the adjoint solve; a_w folded in: d u_w/d v_w = a_w F A^-1,
+                                    so grad_v_w = conj(a_w) 2 A^-H F^H r_w).
+    A^-1 and A^-H are dense LU solves of the N x N operator."""
+    beta = route["beta"]
+    A = beta * np.eye(route["Ux"].shape[0]) + route["Ux"] @ route["Vxh"]
+    v = route["vx"]
+    a = np.asarray(amplitudes, dtype=np.complex128)
+    x0 = np.linalg.solve(A, v)
+    u = F @ (x0 * a[None, :])
+    r = u - target
+    J = float(np.sum(np.abs(r) ** 2))
+    Fx0 = F @ x0
+    grad_a = 2.0 * np.einsum("ow,ow->w", np.conj(Fx0), r)
+    lam = np.linalg.solve(A.conj().T, F.conj().T @ r)
+    grad_v = 2.0 * lam * np.conj(a)[None, :]
+    return dict(J=J, u=u, x0=x0, grad_a=grad_a, grad_v=grad_v, A=A)

@@ -309,3 +309,70 @@ def test_table1_dense_memory_is_complex128():
         assert round(N * N * 16 / 1e6) == int(dense_mb) or abs(N * N * 16 / 1e6 - float(dense_mb)) / float(dense_mb) < 0.01
     m = O.assemble(I.regular_polygon(8), 1.0, "S")
     assert m["S"].dtype == np.complex128
+
+
+# ------------------------------------------------------------------ far field and gradients
+
+
+def test_farfield_matches_mie_at_second_order():
+    """The discrete far field F x of the circle converges to the exact sound-hard far
+    field (Mie series) at second order in h: this fixes the constant C0, the sign of the
+    Green's representation and the current convention x = -u_tot."""
+    k, phi = 1.0, 0.3
+    th = np.linspace(0.0, 2 * np.pi, 36, endpoint=False)
+    ue = O.mie_farfield(k, 1.0, th, phi)
+    errs = []
+    for N in (128, 256):
+        v = I.regular_polygon(N)
+        mats = O.assemble(v, k, "SW")
+        x = np.linalg.solve(mats["W"], O.rhs_planewave(v, k, [phi]))
+        u = (O.farfield_matrix(v, k, th) @ x)[:, 0]
+        errs.append(np.max(np.abs(u - ue)) / np.max(np.abs(ue)))
+    assert errs[0] < 5e-4
+    assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_farfield_reciprocity(star_case):
+    """u_inf(xhat; d) = u_inf(-d; -xhat): exact for the discrete unfiltered problem, since
+    F(xhat) = C0 f(-xhat)^T and N is complex symmetric."""
+    v, k, mats = star_case
+    angs = np.array([0.2, 1.1, 2.5, 4.0])
+    f = O.rhs_planewave(v, k, angs)
+    x = np.linalg.solve(mats["W"], f)
+    U = O.farfield_matrix(v, k, angs + np.pi) @ x     # U[o, w] = u_inf(-d_o; d_w)
+    # u_inf(xhat = d_o + pi; d_w) must equal u_inf(xhat = d_w + pi; d_o)
+    assert np.max(np.abs(U - U.T)) <= 1e-11 * np.max(np.abs(U))
+
+
+def test_misfit_gradients_match_finite_differences(star_case):
+    """The adjoint gradients of the far-field misfit against central differences
+    (h = 1e-6) of the misfit itself, for the amplitudes (real and imaginary directions)
+    and for the preconditioned right-hand side (a random direction)."""
+    v, k, mats = star_case
+    f = O.rhs_planewave(v, k, np.array([0.0, 2.0, 4.0]))
+    route = O.filtered_solve_projected(mats, v, f, 10, 1e-10)
+    th = np.linspace(0.0, 2 * np.pi, 24, endpoint=False)
+    F = O.farfield_matrix(v, k, th)
+    rng = np.random.default_rng(7)
+    a = np.array([1.0 + 0.2j, 0.7 - 0.1j, -0.4 + 0.9j])
+    target = 0.01 * (rng.standard_normal((len(th), 3)) + 1j * rng.standard_normal((len(th), 3)))
+    res = O.misfit_and_gradients(route, F, a, target)
+    h = 1e-6
+    for w in range(3):
+        for unit in (1.0, 1j):
+            ap, am = a.copy(), a.copy()
+            ap[w] += h * unit
+            am[w] -= h * unit
+            fd = (O.misfit_and_gradients(route, F, ap, target)["J"] -
+                  O.misfit_and_gradients(route, F, am, target)["J"]) / (2 * h)
+            g = res["grad_a"][w].real if unit == 1.0 else res["grad_a"][w].imag
+            assert abs(fd - g) <= 1e-6 * max(1.0, abs(g)), (w, unit, fd, g)
+    # direction dv in the right-hand sides
+    dv = rng.standard_normal(route["vx"].shape) + 1j * rng.standard_normal(route["vx"].shape)
+    def J_of(vx):
+        r2 = dict(route)
+        r2["vx"] = vx
+        return O.misfit_and_gradients(r2, F, a, target)["J"]
+    fd = (J_of(route["vx"] + h * dv) - J_of(route["vx"] - h * dv)) / (2 * h)
+    pred = float(np.sum((np.conj(res["grad_v"]) * dv).real))
+    assert abs(fd - pred) <= 1e-6 * max(1.0, abs(pred))
