@@ -40,9 +40,9 @@ FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # 1 mul (18), J0 and Y0 as degree-10 polynomials 20 fma (300), g = (i/4) H0 4 scalings,
 # the two lambda-weighted row sums 4 fma (60)
 ASM_OPS_PER_POINT = 441
-# DRAM bytes per launch from ncu captures of the kernels as they stand (None = not captured
-# since the kernel last changed); the summaries are under profiles/
-TRAFFIC_BYTES = {}
+# DRAM bytes (read + write) per launch from ncu captures of the kernels as they stand
+# (absent = not captured since the kernel last changed); the summaries are under profiles/
+TRAFFIC_BYTES = {"tc_rhs_SY": 18.08e9 + 0.267e9}
 
 
 def _peaks():

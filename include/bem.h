@@ -197,6 +197,23 @@ bem_status solve_backward(bem_handle h, const void* g_dev, int64_t ldg, void* la
 bem_status solve_many_noalloc(bem_handle h, const void* v_dev, int64_t ldv, void* x_dev, int64_t ldx,
                               int64_t nrhs);
 
+/* bem_farfield -- far field of the current x (P1 coefficients, x = -u_tot on the curve)
+ * for the sound-hard problem of Sec. II: Green's representation u_s = int u_tot dg/dnu_y,
+ * and g(x, y) ~ C0 e^{ik|x|}/sqrt|x| e^{-ik xhat.y}, C0 = e^{i pi/4}/sqrt(8 pi k), give
+ *     u_inf(xhat_o) = sum_i F[o, i] x_i,  F[o, i] = i k C0 <phi_i, (xhat_o.nu) e^{-ik xhat_o.y}>,
+ * xhat_o = (cos b_o, sin b_o), b_o = obs_angles_dev[o].  x: N x nrhs (ldx >= N); out:
+ * nobs x nrhs (ldo >= nobs), complex, column-major, device.  1 <= nobs <= 65535.
+ * The paper states no far field; it is the observable of the differentiation layer.
+ * Needs bem_assemble.  Errors: BEM_E_INVALID. */
+bem_status bem_farfield(bem_handle h, const double* obs_angles_dev, int64_t nobs, const void* x_dev,
+                        int64_t ldx, int64_t nrhs, void* out_dev, int64_t ldo);
+
+/* bem_farfield_adjoint -- out = F^H g for g: nobs x nrhs (ldg >= nobs) into out: N x nrhs
+ * (ldo >= N), the vector-Jacobian product of bem_farfield (with solve_backward it gives the
+ * gradient of a far-field misfit with respect to the right-hand side). */
+bem_status bem_farfield_adjoint(bem_handle h, const double* obs_angles_dev, int64_t nobs, const void* g_dev,
+                                int64_t ldg, int64_t nrhs, void* out_dev, int64_t ldo);
+
 /* Copies an internal matrix (BEM_MAT_*) into dst_dev with leading dimension ld (>= rows).
  * For BEM_MAT_SIGMA, dst_dev receives n doubles and ld is ignored. */
 bem_status bem_get_matrix(bem_handle h, int which, void* dst_dev, int64_t ld);

@@ -26,7 +26,7 @@ STATUS = {0: "BEM_OK", 1: "BEM_E_INVALID", 2: "BEM_E_NOMEM", 3: "BEM_E_CUDA", 4:
 EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error", "bem_set_stream",
            "bem_assemble", "filter_apply", "compress_compact", "factor", "bem_rhs_planewave",
            "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info", "bem_timing_enable",
-           "bem_timing_report", "solve_many_noalloc")
+           "bem_timing_report", "solve_many_noalloc", "bem_farfield", "bem_farfield_adjoint")
 
 
 class BemOptions(ctypes.Structure):
@@ -80,11 +80,14 @@ def load_library(path: str = LIB_PATH):
     L.bem_get_info.argtypes = [vp, ctypes.POINTER(BemInfo)]
     L.solve_many_noalloc.argtypes = [vp, vp, i64, vp, i64, i64]
     L.solve_many_noalloc.restype = ctypes.c_int
+    L.bem_farfield.argtypes = [vp, vp, i64, vp, i64, i64, vp, i64]
+    L.bem_farfield_adjoint.argtypes = [vp, vp, i64, vp, i64, i64, vp, i64]
     L.bem_timing_enable.argtypes = [vp, i32]
     L.bem_timing_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     for name in ("bem_create", "bem_destroy", "bem_set_stream", "bem_assemble", "filter_apply",
                  "compress_compact", "factor", "bem_rhs_planewave", "solve_many", "solve_backward",
-                 "bem_get_matrix", "bem_get_info", "bem_timing_enable", "bem_timing_report"):
+                 "bem_get_matrix", "bem_get_info", "bem_timing_enable", "bem_timing_report", "bem_farfield",
+                 "bem_farfield_adjoint"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -188,6 +191,24 @@ class Solver:
         self._check(self.L.solve_backward(self.h, _ptr(g), self.N, _ptr(lam), self.N, g.shape[0]))
         return lam
 
+    def farfield(self, obs_angles, x: torch.Tensor) -> torch.Tensor:
+        """u_inf (nrhs, nobs) of the currents x (nrhs, N)."""
+        obs = torch.as_tensor(obs_angles, dtype=torch.float64).to(self.device).contiguous()
+        x = x.contiguous()
+        out = torch.empty((x.shape[0], obs.numel()), dtype=torch.complex128, device=self.device)
+        self._check(self.L.bem_farfield(self.h, _ptr(obs), obs.numel(), _ptr(x), self.N, x.shape[0],
+                                        _ptr(out), obs.numel()))
+        return out
+
+    def farfield_adjoint(self, obs_angles, g: torch.Tensor) -> torch.Tensor:
+        """F^H g (nrhs, N) for g (nrhs, nobs)."""
+        obs = torch.as_tensor(obs_angles, dtype=torch.float64).to(self.device).contiguous()
+        g = g.contiguous()
+        out = torch.empty((g.shape[0], self.N), dtype=torch.complex128, device=self.device)
+        self._check(self.L.bem_farfield_adjoint(self.h, _ptr(obs), obs.numel(), _ptr(g), obs.numel(), g.shape[0],
+                                                _ptr(out), self.N))
+        return out
+
     # ---------------------------------------------------------------- introspection
     def timing(self, enable: bool):
         self._check(self.L.bem_timing_enable(self.h, 1 if enable else 0))
@@ -223,3 +244,30 @@ class Solver:
 
     def _include_kernel(self) -> bool:
         return self._ik
+
+
+class FarFieldSolve(torch.autograd.Function):
+    """u_inf = F A^-1 v for a factored Solver (A = beta I + U V^H), differentiable in v.
+
+    Forward: solve_many then bem_farfield.  Backward (complex-linear map, torch's
+    conjugate-Wirtinger convention): grad_v = A^-H F^H grad_u, i.e. bem_farfield_adjoint then
+    solve_backward -- the adjoint method, one extra solve per backward pass.  v: (nrhs, N)
+    complex128 on the solver's device; returns (nrhs, nobs)."""
+
+    @staticmethod
+    def forward(ctx, v, solver, obs_angles):
+        ctx.solver = solver
+        ctx.obs = obs_angles
+        x = solver.solve(v.detach())
+        return solver.farfield(obs_angles, x)
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        s = ctx.solver
+        g = s.farfield_adjoint(ctx.obs, grad_u.contiguous())
+        return s.solve_backward(g), None, None
+
+
+def farfield_solve(v: torch.Tensor, solver: "Solver", obs_angles) -> torch.Tensor:
+    """Differentiable u_inf(v) (see FarFieldSolve)."""
+    return FarFieldSolve.apply(v, solver, obs_angles)

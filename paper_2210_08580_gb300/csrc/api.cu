@@ -571,6 +571,66 @@ bem_status bem_timing_report(bem_handle h, char* buf, size_t len) {
     return BEM_OK;
 }
 
+// Far field of the current (sound-hard Green's representation): F[o, i] = C0 f_i(-xhat_o),
+// C0 = e^{i pi/4} / sqrt(8 pi k), f the plane-wave right-hand side.  F is formed per call
+// (N x nobs) and applied with an FP64 product.
+static bem_status farfield_matrix(bem_ctx* h, const double* obs, int64_t nobs, cplx** Fm, double** ang) {
+    Carve cv;
+    cv.add((void**)Fm, sizeof(cplx) * h->N * nobs);
+    cv.add((void**)ang, sizeof(double) * nobs);
+    bem_status st = cv.commit(h);
+    if (st != BEM_OK) return st;
+    if ((st = launch_shift(h, obs, *ang, nobs, BEM_PI)) != BEM_OK) return st;
+    return launch_rhs(h, *ang, nobs, *Fm, nullptr, h->N);
+}
+
+static cplx farfield_c0(double k) {
+    const double a = 1.0 / sqrt(8.0 * BEM_PI * k);
+    return cmk(a * cos(0.25 * BEM_PI), a * sin(0.25 * BEM_PI));
+}
+
+bem_status bem_farfield(bem_handle h, const double* obs_angles, int64_t nobs, const void* x, int64_t ldx,
+                        int64_t nrhs, void* out, int64_t ldo) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 1) return bem_fail(h, BEM_E_INVALID, "bem_farfield: call bem_assemble first");
+    if (!obs_angles || !x || !out || nobs < 1 || nobs > 65535 || nrhs < 1 || ldx < h->N || ldo < nobs)
+        return bem_fail(h, BEM_E_INVALID, "bem_farfield: need 1 <= nobs <= 65535, nrhs >= 1, ldx >= N, ldo >= nobs");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    cplx* Fm = nullptr;
+    double* ang = nullptr;
+    bem_status st = farfield_matrix(h, obs_angles, nobs, &Fm, &ang);
+    if (st != BEM_OK) return st;
+    h->tag = "gemm_farfield";
+    return zgemm(h, OP_T, OP_N, nobs, nrhs, h->N, farfield_c0(h->k), Fm, h->N, (const cplx*)x, ldx, cmk(0, 0),
+                 (cplx*)out, ldo);
+}
+
+bem_status bem_farfield_adjoint(bem_handle h, const double* obs_angles, int64_t nobs, const void* g, int64_t ldg,
+                                int64_t nrhs, void* out, int64_t ldo) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 1) return bem_fail(h, BEM_E_INVALID, "bem_farfield_adjoint: call bem_assemble first");
+    if (!obs_angles || !g || !out || nobs < 1 || nobs > 65535 || nrhs < 1 || ldg < nobs || ldo < h->N)
+        return bem_fail(h, BEM_E_INVALID,
+                        "bem_farfield_adjoint: need 1 <= nobs <= 65535, nrhs >= 1, ldg >= nobs, ldo >= N");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    cplx* Fm = nullptr;
+    double* ang = nullptr;
+    bem_status st = farfield_matrix(h, obs_angles, nobs, &Fm, &ang);
+    if (st != BEM_OK) return st;
+    // F^H g = conj(C0) conj(Fm) g = conj( C0 Fm conj(g) ) : conjugate g into out's storage
+    // is not possible (shapes differ), so go through a scratch copy of conj(g)
+    cplx* gc = nullptr;
+    BEM_CUDA(h, cudaMallocAsync((void**)&gc, sizeof(cplx) * nobs * nrhs, h->stream));
+    if ((st = launch_conj_scale(h, (const cplx*)g, ldg, gc, nobs, cmk(1, 0), nobs, nrhs)) != BEM_OK) return st;
+    h->tag = "gemm_farfield_adjoint";
+    st = zgemm(h, OP_N, OP_N, h->N, nrhs, nobs, farfield_c0(h->k), Fm, h->N, gc, nobs, cmk(0, 0), (cplx*)out, ldo);
+    cudaFreeAsync(gc, h->stream);
+    if (st != BEM_OK) return st;
+    return launch_conj_scale(h, (const cplx*)out, ldo, (cplx*)out, ldo, cmk(1, 0), h->N, nrhs);
+}
+
 bem_status bem_get_info(bem_handle h, bem_info* info) {
     if (!h || !info) return BEM_E_INVALID;
     cudaSetDevice(h->device);

@@ -502,14 +502,16 @@ __device__ void pair_gauss(int q, const SegV& e, const SegV& f, double k, const 
     }
 }
 
-// Gauss order for a separated pair: Bernstein-ellipse bound rho^{-2q} exp(k Im r) <= 1e-15
+// Gauss order for a separated pair: Bernstein-ellipse bound rho^{-2q} exp(k Im r) <= 1e-14
 // with rho = a + sqrt(a^2 - 1), a = 1 + 2 gap/h (log singularity at the gap beyond the end
 // of the segment) and Im r up to about gap + h on that ellipse (the Hankel kernel grows
-// like exp(k Im r) off the real axis).  Only a threshold, so single precision suffices.
+// like exp(k Im r) off the real axis).  1e-14 of a pair's own integral keeps every entry
+// within 1e-13 of the largest (self-pair) entries.  Only a threshold, so single precision
+// suffices.
 __device__ __forceinline__ int q_for_gap(float ratio, float kgap) {
     const float a = 1.0f + 2.0f * fmaxf(ratio, 1e-3f);
     const float rho = a + sqrtf(a * a - 1.0f);
-    const int q = (int)ceilf((34.54f + kgap) / (2.0f * __logf(rho)) + 1e-3f);
+    const int q = (int)ceilf((32.24f + kgap) / (2.0f * __logf(rho)) + 1e-3f);
     return min(16, max(2, q));
 }
 
@@ -582,34 +584,6 @@ __device__ __forceinline__ void bessel_u_df(const float4* __restrict__ tab, dfl 
     Y0 = rY;
 }
 
-// two arguments at once: four independent Horner chains keep the FP32 pipe busy
-__device__ __forceinline__ void bessel_u_df2(const float4* __restrict__ tab, dfl ua, dfl ub, dfl& Ja, dfl& Ya,
-                                             dfl& Jb, dfl& Yb) {
-    const int ia = btab_index(ua.hi), ib = btab_index(ub.hi);
-    if (ia < 0 || ia >= BTAB_NINT || ib < 0 || ib >= BTAB_NINT) {
-        bessel_u_df(tab, ua, Ja, Ya);
-        bessel_u_df(tab, ub, Jb, Yb);
-        return;
-    }
-    const float4* ca = tab + (size_t)ia * (BTAB_DF_STRIDE / 4);
-    const float4* cb = tab + (size_t)ib * (BTAB_DF_STRIDE / 4);
-    const float4 ha = __ldg(ca), hb = __ldg(cb);
-    const dfl ta = dfl_mul(dfl_sub(ua, dfl{ha.x, ha.y}), dfl{ha.z, ha.w});
-    const dfl tb = dfl_mul(dfl_sub(ub, dfl{hb.x, hb.y}), dfl{hb.z, hb.w});
-    float4 xa = __ldg(ca + BTAB_NC), xb = __ldg(cb + BTAB_NC);
-    dfl rJa = {xa.x, xa.y}, rYa = {xa.z, xa.w}, rJb = {xb.x, xb.y}, rYb = {xb.z, xb.w};
-#pragma unroll
-    for (int j = BTAB_NC - 2; j >= 0; --j) {
-        xa = __ldg(ca + 1 + j);
-        xb = __ldg(cb + 1 + j);
-        rJa = dfl_fma(rJa, ta, dfl{xa.x, xa.y});
-        rYa = dfl_fma(rYa, ta, dfl{xa.z, xa.w});
-        rJb = dfl_fma(rJb, tb, dfl{xb.x, xb.y});
-        rYb = dfl_fma(rYb, tb, dfl{xb.z, xb.w});
-    }
-    Ja = rJa; Ya = rYa; Jb = rJb; Yb = rYb;
-}
-
 // Separated pair (S/N only), q x q tensor Gauss-Legendre in double-float.  b = y_f(0) -
 // x_e(0), ue = h_e t_e, vf = h_f t_f; returns A_ab with I_ab = h_e h_f A_ab.  The sum over
 // the f-nodes runs first (two row sums R_b), then the e-node weights multiply them.
@@ -621,29 +595,13 @@ __device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, 
         const dfl s = dfl_mk(c_gx_df[o + i]);
         const dfl cx = dfl_sub(bx, dfl_mul(s, uex)), cy = dfl_sub(by, dfl_mul(s, uey));
         cdfl R0 = cdfl_zero(), R1 = cdfl_zero();
-        int j = 0;
-        for (; j + 1 < q; j += 2) {          // two nodes per pass
-            const dfl ta = dfl_mk(c_gx_df[o + j]), tb = dfl_mk(c_gx_df[o + j + 1]);
-            const dfl dxa = dfl_fma(ta, vfx, cx), dya = dfl_fma(ta, vfy, cy);
-            const dfl dxb = dfl_fma(tb, vfx, cx), dyb = dfl_fma(tb, vfy, cy);
-            const dfl r2a = dfl_fma(dxa, dxa, dfl_mul(dya, dya));
-            const dfl r2b = dfl_fma(dxb, dxb, dfl_mul(dyb, dyb));
-            dfl Ja, Ya, Jb, Yb;
-            bessel_u_df2(tab, dfl_mul(k2, r2a), dfl_mul(k2, r2b), Ja, Ya, Jb, Yb);
-            const cdfl ga = {dfl_scale(Ya, -0.25f), dfl_scale(Ja, 0.25f)};   // (i/4) (J0 + i Y0)
-            const cdfl gb = {dfl_scale(Yb, -0.25f), dfl_scale(Jb, 0.25f)};
-            R0 = cdfl_fma_real(dfl_mk(c_gw0_df[o + j]), ga, R0);
-            R1 = cdfl_fma_real(dfl_mk(c_gw1_df[o + j]), ga, R1);
-            R0 = cdfl_fma_real(dfl_mk(c_gw0_df[o + j + 1]), gb, R0);
-            R1 = cdfl_fma_real(dfl_mk(c_gw1_df[o + j + 1]), gb, R1);
-        }
-        if (j < q) {
+        for (int j = 0; j < q; ++j) {
             const dfl t = dfl_mk(c_gx_df[o + j]);
             const dfl dx = dfl_fma(t, vfx, cx), dy = dfl_fma(t, vfy, cy);
             const dfl r2 = dfl_fma(dx, dx, dfl_mul(dy, dy));
             dfl J0, Y0;
             bessel_u_df(tab, dfl_mul(k2, r2), J0, Y0);
-            const cdfl g = {dfl_scale(Y0, -0.25f), dfl_scale(J0, 0.25f)};
+            const cdfl g = {dfl_scale(Y0, -0.25f), dfl_scale(J0, 0.25f)};   // (i/4) (J0 + i Y0)
             R0 = cdfl_fma_real(dfl_mk(c_gw0_df[o + j]), g, R0);
             R1 = cdfl_fma_real(dfl_mk(c_gw1_df[o + j]), g, R1);
         }
@@ -662,7 +620,7 @@ __device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, 
 // pairs keep their relative geometry to double-float precision.  Self and adjacent pairs
 // come from the FP64 table of k_near_pairs.
 template <int T>
-__global__ void __launch_bounds__(256, 2) k_assemble_sn(AsmParams p) {
+__global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     int ti, tj;
     tile_of((int)blockIdx.x, p.nT, ti, tj);
     constexpr int TP = T + 1;

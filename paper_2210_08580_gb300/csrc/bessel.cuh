@@ -16,7 +16,9 @@
 
 #include <math.h>
 
+#ifndef BEM_PI
 #define BEM_PI 3.14159265358979323846
+#endif
 #define BEM_EULER_GAMMA 0.57721566490153286061
 
 struct Bessel01 { double J0, Y0, J1, Y1; };

@@ -10,6 +10,10 @@
 
 #include "../../include/bem.h"
 
+#ifndef BEM_PI
+#define BEM_PI 3.14159265358979323846
+#endif
+
 typedef double2 cplx;
 
 __host__ __device__ __forceinline__ cplx cmk(double re, double im) { return make_double2(re, im); }

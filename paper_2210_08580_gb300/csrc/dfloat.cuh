@@ -26,6 +26,24 @@ __device__ __forceinline__ double f2d_exact(float f) {
     return __hiloint2double((int)hiw, (int)(u << 29));
 }
 __device__ __forceinline__ double dfl_to(dfl a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
+// double -> double-float from the bit fields (integer operations and one int-to-float
+// conversion): hi = the significand rounded to 24 bits, lo = the remainder (<= 29 bits,
+// rounded to 24).  |x| must lie in the float normal range or be below 2^-74 (-> 0).
+__device__ __forceinline__ dfl dfl_from_bits(double x) {
+    const long long b = __double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E < 949 || E > 1149) return {0.f, 0.f};
+    const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    long long m24 = (m + (1LL << 28)) >> 29;              // 24-bit significand, rounded
+    const int rem = (int)(m - (m24 << 29));                // |rem| <= 2^28
+    int eh = E;
+    if (m24 == (1LL << 24)) { m24 >>= 1; ++eh; }
+    const unsigned sgn = (unsigned)((unsigned long long)b >> 63) << 31;
+    const float hi = __uint_as_float(sgn | ((unsigned)(eh - 896) << 23) | ((unsigned)m24 & 0x7FFFFFu));
+    float lo = __int2float_rn(rem) * __uint_as_float((unsigned)(E - 1075 + 127) << 23);
+    if (sgn) lo = -lo;
+    return {hi, lo};
+}
 __device__ __forceinline__ dfl dfl_qts(float s, float e) {    // |s| >= |e|
     const float h = __fadd_rn(s, e);
     return {h, __fsub_rn(e, __fsub_rn(h, s))};

@@ -52,5 +52,8 @@ bem_status launch_axpby(bem_ctx* h, cplx* y, int64_t ldy, const cplx* x, int64_t
 bem_status launch_add_identity(bem_ctx* h, cplx* A, int64_t ld, int r, cplx d);
 bem_status launch_col_norm_ratio(bem_ctx* h, const cplx* num, int64_t ldn, const cplx* den,
                                  int64_t ldd, int64_t rows, int64_t cols, double* out_max);
+bem_status launch_shift(bem_ctx* h, const double* in, double* out, int64_t n, double shift);
+bem_status launch_conj_scale(bem_ctx* h, const cplx* x, int64_t ldx, cplx* y, int64_t ldy, cplx a, int64_t rows,
+                             int64_t cols);   // y = a conj(x)
 bem_status launch_copy2d(bem_ctx* h, void* dst, int64_t ldd, const void* src, int64_t lds,
                          int64_t rows, int64_t cols, size_t elem);

@@ -549,37 +549,49 @@ __global__ void k_to_dfl(float4* X, int64_t count) {
     X[i] = cdfl_pack({dfl_from(v.x), dfl_from(v.y)});
 }
 
+// Each thread owns up to QR_KC columns (lane + 32 k) over the rows of its row group, so a
+// row's loads for all its columns are independent and in flight together (the row loop
+// is bound by L2 latency otherwise); one cross-warp reduction per phase.  The cross-CTA
+// sums of the dots are split over the grid (a third barrier per column), since repeating
+// them in every CTA kept the FP64 pipe busy.  n <= 32 QR_KC.
+#define QR_KC 8
 __global__ void __launch_bounds__(256) k_house_qr_df(float4* X, int64_t N, int n, cplx* R, int* perm, double* partC,
-                                                     unsigned long long* cnq, cplx* partW, unsigned* bar, int* err) {
+                                                     unsigned long long* cnq, cplx* partW, float4* wdf, unsigned* bar,
+                                                     int* err) {
     __shared__ double red[32];
-    __shared__ float4 wred[8][33];
-    __shared__ float2 nred[8][33];
-    __shared__ float4 wsm[1024];
-    __shared__ int cmap[1024];
-    __shared__ double qscale_s, nrm2_s, tau_s;
-    __shared__ cplx alpha_s;
+    __shared__ float4 wbuf[8][32 * QR_KC];      // per row group partials (dots; norms use .x/.y)
+    __shared__ float4 wsm[32 * QR_KC];
+    __shared__ int cmap[32 * QR_KC];
+    __shared__ double qscale_s, tau_s;
     __shared__ float4 vj_s;
     __shared__ unsigned long long pbest[8];
     __shared__ int pidx[8];
     const unsigned G = gridDim.x;
     const int64_t rb = (N + G - 1) / G;
     const int64_t r0 = (int64_t)blockIdx.x * rb, r1 = min(N, r0 + rb);
-    const int tid = threadIdx.x, cg = tid & 31, rg = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, rg = tid >> 5, lane = tid & 31;
     for (int c = tid; c < n; c += blockDim.x) cmap[c] = c;
+    __syncthreads();
     // partial column norms over my rows
-    for (int cb = 0; cb < n; cb += 32) {
-        const int c = cb + cg;
-        dfl acc = {0.f, 0.f};
-        if (c < n)
-            for (int64_t i = r0 + rg; i < r1; i += 8) acc = dfl_norm_acc(cdfl_ld(X + i * n + c), acc);
-        nred[rg][cg] = make_float2(acc.hi, acc.lo);
+    {
+        dfl acc[QR_KC];
+#pragma unroll
+        for (int k = 0; k < QR_KC; ++k) acc[k] = {0.f, 0.f};
+        for (int64_t i = r0 + rg; i < r1; i += 8) {
+#pragma unroll
+            for (int k = 0; k < QR_KC; ++k) {
+                const int c = lane + 32 * k;
+                if (c < n) acc[k] = dfl_norm_acc(cdfl_ld(X + i * n + c), acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < QR_KC; ++k) wbuf[rg][lane + 32 * k] = make_float4(acc[k].hi, acc[k].lo, 0.f, 0.f);
         __syncthreads();
-        if (rg == 0 && c < n) {
-            dfl t = dfl_mk(nred[0][cg]);
-            for (int q = 1; q < 8; ++q) t = dfl_add(t, dfl_mk(nred[q][cg]));
+        for (int c = tid; c < n; c += blockDim.x) {
+            dfl t = {wbuf[0][c].x, wbuf[0][c].y};
+            for (int q = 1; q < 8; ++q) t = dfl_add(t, dfl{wbuf[q][c].x, wbuf[q][c].y});
             partC[(int64_t)blockIdx.x * n + c] = dfl_to(t);
         }
-        __syncthreads();
     }
     if (!grid_barrier(bar, G, err)) return;
     {
@@ -649,70 +661,94 @@ __global__ void __launch_bounds__(256) k_house_qr_df(float4* X, int64_t N, int n
                 const double vn2 = nrm2 - ax * ax + cabs2(vj);
                 tau = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
             }
-            tau_s = tau; alpha_s = alpha; nrm2_s = nrm2;
+            tau_s = tau;
             vj_s = cdfl_pack({dfl_from(vj.x), dfl_from(vj.y)});
             if (j >= r0 && j < r1) R[j + (int64_t)j * n] = (nrm2 > 0.0) ? alpha : cmk(0, 0);
         }
         __syncthreads();
         const double tau = tau_s;
         const cdfl vjd = cdfl_unpack(vj_s);
+        int pcs[QR_KC];
+#pragma unroll
+        for (int k = 0; k < QR_KC; ++k) {
+            const int c = j + 1 + lane + 32 * k;
+            pcs[k] = (c < n) ? cmap[c] : -1;
+        }
         // (3) partial dots w_c = sum_i conj(v_i) X[i, c], c > j
-        for (int cb = j + 1; cb < n; cb += 32) {
-            const int c = cb + cg;
-            cdfl acc = cdfl_zero();
-            if (c < n && tau != 0.0) {
-                const int pc = cmap[c];
+        {
+            cdfl acc[QR_KC];
+#pragma unroll
+            for (int k = 0; k < QR_KC; ++k) acc[k] = cdfl_zero();
+            if (tau != 0.0) {
                 for (int64_t i = max(r0, (int64_t)j) + rg; i < r1; i += 8) {
                     const cdfl vi = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
-                    cdfl_conj_fma(acc, vi, cdfl_ld(X + i * n + pc));
+#pragma unroll
+                    for (int k = 0; k < QR_KC; ++k)
+                        if (pcs[k] >= 0) cdfl_conj_fma(acc[k], vi, cdfl_ld(X + i * n + pcs[k]));
                 }
             }
-            wred[rg][cg] = cdfl_pack(acc);
+#pragma unroll
+            for (int k = 0; k < QR_KC; ++k) wbuf[rg][lane + 32 * k] = cdfl_pack(acc[k]);
             __syncthreads();
-            if (rg == 0 && c < n) {
-                cdfl t = cdfl_unpack(wred[0][cg]);
-                for (int q = 1; q < 8; ++q) t = cdfl_add(t, cdfl_unpack(wred[q][cg]));
+            for (int c = j + 1 + tid; c < n; c += blockDim.x) {
+                const int l = c - j - 1;
+                cdfl t = cdfl_unpack(wbuf[0][l]);
+                for (int q = 1; q < 8; ++q) t = cdfl_add(t, cdfl_unpack(wbuf[q][l]));
                 partW[(int64_t)blockIdx.x * n + c] = cmk(dfl_to(t.re), dfl_to(t.im));
             }
-            __syncthreads();
         }
         if (!grid_barrier(bar, G, err)) return;
-        // (4) reduce w; update my rows and accumulate their trailing norms
-        for (int c = j + 1 + tid; c < n; c += blockDim.x) {
-            cplx t = cmk(0, 0);
-            for (unsigned q = 0; q < G; ++q) t = cadd(t, __ldcg(partW + (int64_t)q * n + c));
-            // x <- x - v w : store -w so the update is two fused products
-            wsm[c] = cdfl_pack({dfl_from(-tau * t.x), dfl_from(-tau * t.y)});
+        // (3b) each CTA sums the partials of a few columns (the FP64 sums are spread over the
+        // grid instead of repeated in every CTA); -tau w is published in double-float
+        for (int c = j + 1 + (int)blockIdx.x; c < n; c += G) {
+            double re = 0.0, im = 0.0;
+            for (unsigned q = tid; q < G; q += blockDim.x) {
+                const cplx v = __ldcg(partW + (int64_t)q * n + c);
+                re += v.x;
+                im += v.y;
+            }
+            re = block_sum(re, red);
+            im = block_sum(im, red);
+            if (tid == 0) wdf[c] = cdfl_pack({dfl_from(-tau * re), dfl_from(-tau * im)});
         }
+        if (!grid_barrier(bar, G, err)) return;
+        // (4) update my rows (x <- x + v (-tau w)) and accumulate their trailing norms
+        for (int c = j + 1 + tid; c < n; c += blockDim.x) wsm[c - j - 1] = __ldcg(wdf + c);
         __syncthreads();
-        for (int cb = j + 1; cb < n; cb += 32) {
-            const int c = cb + cg;
-            dfl acc = {0.f, 0.f};
-            if (c < n) {
-                const int pc = cmap[c];
-                const cdfl nw = cdfl_unpack(wsm[c]);
-                for (int64_t i = max(r0, (int64_t)j) + rg; i < r1; i += 8) {
-                    cdfl x = cdfl_ld(X + i * n + pc);
+        {
+            cdfl nw[QR_KC];
+            dfl acc[QR_KC];
+#pragma unroll
+            for (int k = 0; k < QR_KC; ++k) {
+                nw[k] = (pcs[k] >= 0) ? cdfl_unpack(wsm[lane + 32 * k]) : cdfl_zero();
+                acc[k] = {0.f, 0.f};
+            }
+            for (int64_t i = max(r0, (int64_t)j) + rg; i < r1; i += 8) {
+                const cdfl vi = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
+#pragma unroll
+                for (int k = 0; k < QR_KC; ++k) {
+                    if (pcs[k] < 0) continue;
+                    cdfl x = cdfl_ld(X + i * n + pcs[k]);
                     if (tau != 0.0) {
-                        const cdfl vi = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
-                        // x += v (-w)
-                        x.re = dfl_fma(vi.re, nw.re, dfl_fma(dfl_neg(vi.im), nw.im, x.re));
-                        x.im = dfl_fma(vi.re, nw.im, dfl_fma(vi.im, nw.re, x.im));
-                        X[i * n + pc] = cdfl_pack(x);
+                        x.re = dfl_fma(vi.re, nw[k].re, dfl_fma(dfl_neg(vi.im), nw[k].im, x.re));
+                        x.im = dfl_fma(vi.re, nw[k].im, dfl_fma(vi.im, nw[k].re, x.im));
+                        X[i * n + pcs[k]] = cdfl_pack(x);
                     }
-                    if (i > j) acc = dfl_norm_acc(x, acc);
+                    if (i > j) acc[k] = dfl_norm_acc(x, acc[k]);
                 }
             }
-            nred[rg][cg] = make_float2(acc.hi, acc.lo);
+            __syncthreads();                      // wbuf reuse (the dots were reduced above)
+#pragma unroll
+            for (int k = 0; k < QR_KC; ++k) wbuf[rg][lane + 32 * k] = make_float4(acc[k].hi, acc[k].lo, 0.f, 0.f);
             __syncthreads();
-            if (rg == 0 && c < n) {
-                dfl t = dfl_mk(nred[0][cg]);
-                for (int q = 1; q < 8; ++q) t = dfl_add(t, dfl_mk(nred[q][cg]));
+            for (int c = j + 1 + tid; c < n; c += blockDim.x) {
+                const int l = c - j - 1;
+                dfl t = {wbuf[0][l].x, wbuf[0][l].y};
+                for (int q = 1; q < 8; ++q) t = dfl_add(t, dfl{wbuf[q][l].x, wbuf[q][l].y});
                 const double td = dfl_to(t);
                 partC[(int64_t)blockIdx.x * n + cmap[c]] = td;
                 atomicAdd(cnq + (size_t)((j + 1) & 1) * n + cmap[c], __double2ull_rz(td * qscale));
             }
-            __syncthreads();
         }
     }
     for (int64_t j = max(r0, (int64_t)0); j < min(r1, (int64_t)n); ++j)
@@ -740,18 +776,22 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* 
     BEM_CUDA(h, cudaMallocAsync((void**)&cnq, sizeof(unsigned long long) * 2 * (size_t)n, h->stream));
     BEM_CUDA(h, cudaMemsetAsync(cnq, 0, sizeof(unsigned long long) * 2 * (size_t)n, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&partW, sizeof(cplx) * (size_t)G * n, h->stream));
+    float4* wdf = nullptr;
+    BEM_CUDA(h, cudaMallocAsync((void**)&wdf, sizeof(float4) * (size_t)n, h->stream));
     void* args[] = {&X, &N, &n, &R, &perm, &partC, &cnq, &partW, &h->bar, &h->dev_err};
-    if (dfl_arith) {
+    void* args_df[] = {&X, &N, &n, &R, &perm, &partC, &cnq, &partW, &wdf, &h->bar, &h->dev_err};
+    if (dfl_arith && n <= 32 * QR_KC) {
         // X in place as double-float pairs (same 16 bytes per entry)
         const int64_t cnt = N * (int64_t)n;
         BEM_TIMED(h, "k_to_dfl", (k_to_dfl<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(reinterpret_cast<float4*>(X), cnt)));
         BEM_LAUNCH(h, "k_to_dfl");
-        BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr_df, G, 256, args, "k_house_qr_df"));
+        BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr_df, G, 256, args_df, "k_house_qr_df"));
     } else {
         BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr, G, 256, args, "k_house_qr"));
     }
     cudaFreeAsync(partC, h->stream);
     cudaFreeAsync(cnq, h->stream);
+    cudaFreeAsync(wdf, h->stream);
     cudaFreeAsync(partW, h->stream);
     return st;
 }
@@ -1089,6 +1129,30 @@ bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
 // =========================================================================================
 // small elementwise helpers
 // =========================================================================================
+// out[i] = in[i] + shift
+__global__ void k_shift(const double* in, double* out, int64_t n, double shift) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i] + shift;
+}
+bem_status launch_shift(bem_ctx* h, const double* in, double* out, int64_t n, double shift) {
+    BEM_TIMED(h, "k_shift", (k_shift<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(in, out, n, shift)));
+    BEM_LAUNCH(h, "k_shift");
+    return BEM_OK;
+}
+// y = a * conj(x) over a rows x cols block (leading dimensions ldx, ldy)
+__global__ void k_conj_scale(const cplx* x, int64_t ldx, cplx* y, int64_t ldy, cplx a, int64_t rows, int64_t cols) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    y[i + j * ldy] = cmul(a, cconj(x[i + j * ldx]));
+}
+bem_status launch_conj_scale(bem_ctx* h, const cplx* x, int64_t ldx, cplx* y, int64_t ldy, cplx a, int64_t rows,
+                             int64_t cols) {
+    const int64_t n = rows * cols;
+    BEM_TIMED(h, "k_conj_scale", (k_conj_scale<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(x, ldx, y, ldy, a, rows, cols)));
+    BEM_LAUNCH(h, "k_conj_scale");
+    return BEM_OK;
+}
 __global__ void k_axpby(cplx* y, int64_t ldy, const cplx* x, int64_t ldx, cplx a, cplx b, int64_t rows, int64_t cols) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * cols) return;

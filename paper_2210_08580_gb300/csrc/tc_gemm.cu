@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "dfloat.cuh"
 #include "kernels.h"
 #include "tc_gemm.h"
 
@@ -734,17 +735,22 @@ bem_status tc_prepare_operators(bem_ctx* h) {
 // |k - j| <= band; FP64.  Thread (m, j): sum over the 2 band + 1 rows k of column j.
 __global__ void k_band_left(const double2* __restrict__ Y, const double2* __restrict__ W, int64_t N, int64_t nc,
                             int band, double2* out) {
+    // double-float products on the FP32 pipe; operands converted from their bit fields
     const int64_t m = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const int64_t j = (int64_t)blockIdx.y * 8 + threadIdx.y;
     if (m >= nc || j >= N) return;
-    double2 acc = make_double2(0.0, 0.0);
+    cdfl acc = cdfl_zero();
     for (int t = -band; t <= band; ++t) {
         int64_t k = j + t;
         if (k < 0) k += N; else if (k >= N) k -= N;
-        cfma(acc, Y[m + k * nc], W[k + j * N]);
+        const double2 y = Y[m + k * nc], w = W[k + j * N];
+        const dfl yr = dfl_from_bits(y.x), yi = dfl_from_bits(y.y);
+        const dfl wr = dfl_from_bits(w.x), wi = dfl_from_bits(w.y);
+        acc.re = dfl_fma(yr, wr, dfl_fma(dfl_neg(yi), wi, acc.re));
+        acc.im = dfl_fma(yr, wi, dfl_fma(yi, wr, acc.im));
     }
     double2* o = out + m + j * nc;
-    *o = cadd(*o, acc);
+    *o = cadd(*o, cdfl_to(acc));
 }
 
 static const TcOperand* op_of(TcState* t, int op) {
