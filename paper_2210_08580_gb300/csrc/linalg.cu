@@ -767,7 +767,9 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* 
     if (N < n) return bem_fail(h, BEM_E_INVALID, "QR: fewer rows than columns");
     int nsm = 0;
     BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    int G = (int)std::min<int64_t>(nsm, (N + 15) / 16);
+    // two CTAs per SM for the double-float kernel (its row loops are latency-bound)
+    const bool use_df = dfl_arith && n <= 32 * QR_KC;
+    int G = (int)std::min<int64_t>((use_df ? 2 : 1) * nsm, (N + 15) / 16);
     bem_status st;
     double* partC = nullptr;
     cplx* partW = nullptr;
@@ -780,7 +782,7 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* 
     BEM_CUDA(h, cudaMallocAsync((void**)&wdf, sizeof(float4) * (size_t)n, h->stream));
     void* args[] = {&X, &N, &n, &R, &perm, &partC, &cnq, &partW, &h->bar, &h->dev_err};
     void* args_df[] = {&X, &N, &n, &R, &perm, &partC, &cnq, &partW, &wdf, &h->bar, &h->dev_err};
-    if (dfl_arith && n <= 32 * QR_KC) {
+    if (use_df) {
         // X in place as double-float pairs (same 16 bytes per entry)
         const int64_t cnt = N * (int64_t)n;
         BEM_TIMED(h, "k_to_dfl", (k_to_dfl<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(reinterpret_cast<float4*>(X), cnt)));
