@@ -102,6 +102,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare-fp64", action="store_true",
                     help="skip timing the FP64 path beside the mixed path")
+    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+                    help="single: one N=16384 star (the headline metric); batch: many uneven stars at once")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--streams", type=int, default=0, help="batch streams (0 = tuned per size bucket)")
     return ap.parse_args()
 
 
@@ -234,6 +238,60 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world):
+    """Many uneven problems at once (random stars, N ~ U{512..8192}, k = 10^U(-2, log10 5),
+    64..512 plane waves each): every problem assembled, filtered, compressed, factored,
+    its right-hand sides formed and solved; value = right-hand sides solved per second."""
+    import torch
+    dist = None
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2210_08580_gb300 import batch, inputs as I
+    specs = I.batch_problems(count=args.batch_count, first_seed=100 + 1000 * rank)
+    problems = batch.problems_from_inputs(specs)
+    nrhs_total = sum(len(p.angles) for p in problems)
+    if args.streams > 0:
+        n_streams = args.streams
+        tuned = None
+    else:
+        tuned = batch.autotune_streams(problems, prec=args.prec, device=local, candidates=(1, 2, 4, 8), sample=4)
+        n_streams = max(set(tuned.values()), key=list(tuned.values()).count)
+    bs = batch.BatchSolver(problems, prec=args.prec, device=local, n_streams=n_streams)
+    for _ in range(args.warmup):
+        bs.run()
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bs.run()
+    torch.cuda.synchronize(dev)
+    dt = reduce_max((time.perf_counter() - t0) / args.steps, dist, dev)
+    clk = clocks.stop()
+    bs.close()
+    if rank == 0:
+        line = {"metric": "batched factor + RHS solves/s, uneven random stars", "value": job_value(nrhs_total, world, dt),
+                "unit": "RHS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000 * dt, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.prec == "fp64" else "bf16-split+f64", "data": "synthetic",
+                "config": {"workload": f"{args.batch_count} random stars (seeds 100.., N ~ U{{512..8192}}, "
+                                       f"k = 10^U(-2, log10 5), 64..512 plane waves)",
+                           "problems": args.batch_count, "rhs_total": nrhs_total, "prec": args.prec,
+                           "streams": n_streams, "tuned": tuned, "parallelism": f"replicas x{world}"},
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def workload_config(args):
     return {"workload": f"random 8-harmonic star (seed=rank), N={args.N}, k={args.k}, n={2 * args.M + 1}, "
                         f"tol={args.tol}, {args.nrhs} plane waves",
@@ -249,6 +307,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch":
+        return run_batch(args, rank, world)
 
     import torch
     dist = None

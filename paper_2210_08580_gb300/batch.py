@@ -1,0 +1,184 @@
+"""Many geometries at once: the batching layer.
+
+A batch of independent problems (uneven N, k and numbers of incident waves) is spread
+over several CUDA streams, one host thread per stream (the C calls release the GIL), so
+that the kernels of small problems fill the GPU side by side.  The cooperative kernels of
+the compression and the Woodbury core (grid barriers that need every CTA resident) run
+one problem at a time under a lock, with their stream synchronised before the lock is
+released, so two of them never share the GPU; everything else overlaps freely.
+
+``autotune_streams`` times a few stream counts on a sample of the batch and keeps the
+fastest per problem-size bucket.  ``SolveGraph`` records the FP64 Woodbury solves of every
+problem (``solve_many_noalloc``, which allocates nothing) into one CUDA graph, replayed
+for each new set of right-hand sides.
+
+Each problem is solved by exactly the kernels a single ``bem.Solver`` uses, so the
+results are those of the problems solved one after another.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import threading
+import time
+
+import numpy as np
+import torch
+
+from . import bem, inputs
+
+
+@dataclasses.dataclass
+class Problem:
+    verts: np.ndarray          # (N, 2) closed counter-clockwise polygon, equal chords
+    k: float
+    angles: np.ndarray         # plane-wave incidence angles (nrhs,)
+    n_modes: int               # filter modes n = 2M + 1
+    tol: float = 1e-10
+
+
+def problems_from_inputs(specs, tol: float = 1e-10) -> list[Problem]:
+    """Problems of ``inputs.batch_problems``: n = min(201, 2 floor(N/8) + 1)."""
+    out = []
+    for s in specs:
+        v, _, _ = inputs.equal_chord_mesh(s.curve, s.N)
+        out.append(Problem(verts=v, k=s.k, angles=inputs.planewave_angles(s.nrhs),
+                           n_modes=min(201, 2 * (s.N // 8) + 1), tol=tol))
+    return out
+
+
+def size_bucket(N: int) -> int:
+    """Problem-size bucket for the tuner: log2 of N rounded down."""
+    return int(math.log2(max(N, 1)))
+
+
+class BatchSolver:
+    """Solves a list of Problems concurrently on ``n_streams`` streams of one device."""
+
+    def __init__(self, problems: list[Problem], prec: str = "mixed", device: int = 0, n_streams: int = 4,
+                 refine_rtol: float = 1e-10):
+        self.problems = problems
+        self.prec = prec
+        self.device = device
+        self.n_streams = max(1, int(n_streams))
+        self.refine_rtol = refine_rtol
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(self.n_streams)]
+        self._coop = threading.Lock()
+        self.solvers: list[bem.Solver | None] = [None] * len(problems)
+        self.results: list[dict | None] = [None] * len(problems)
+
+    def _one(self, i: int, stream: torch.cuda.Stream):
+        p = self.problems[i]
+        dev = torch.device("cuda", self.device)
+        with torch.cuda.stream(stream):
+            s = self.solvers[i]
+            if s is None:
+                s = bem.Solver(device=self.device, prec=self.prec, stream=stream, refine_rtol=self.refine_rtol)
+                self.solvers[i] = s
+            verts = torch.from_numpy(np.ascontiguousarray(p.verts)).to(dev, non_blocking=True)
+            ang = torch.from_numpy(np.ascontiguousarray(p.angles)).to(dev, non_blocking=True)
+            s.assemble(verts, p.k, ops="SW")
+            s.filter_apply(p.n_modes)
+            with self._coop:
+                r = s.compress(p.tol)          # synchronises the stream (returns the rank)
+                s.factor()
+                stream.synchronize()
+            v = s.rhs_planewave(ang)
+            x = s.solve(v)
+            self.results[i] = dict(x=x, v=v, rank=r)
+
+    def run(self) -> list[dict]:
+        """Assemble, filter, compress, factor, form the RHS and solve every problem; returns
+        per problem dict(x=(nrhs, N) complex128, v=..., rank=r)."""
+        order = sorted(range(len(self.problems)), key=lambda i: -self.problems[i].verts.shape[0])
+        queues = [order[q::self.n_streams] for q in range(self.n_streams)]
+        errors = []
+
+        def worker(q):
+            try:
+                for i in queues[q]:
+                    self._one(i, self.streams[q])
+                self.streams[q].synchronize()
+            except Exception as e:          # re-raised on the calling thread
+                errors.append(e)
+
+        threads = [threading.Thread(target=worker, args=(q,)) for q in range(self.n_streams)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        if errors:
+            raise errors[0]
+        return self.results
+
+    def close(self):
+        for s in self.solvers:
+            if s is not None:
+                s.close()
+        self.solvers = [None] * len(self.problems)
+
+
+def autotune_streams(problems: list[Problem], prec: str = "mixed", device: int = 0,
+                     candidates=(1, 2, 4, 8), sample: int = 8) -> dict:
+    """Times ``BatchSolver.run`` on up to ``sample`` problems of each size bucket for every
+    stream count in ``candidates``; returns {bucket: best stream count}."""
+    buckets: dict[int, list[Problem]] = {}
+    for p in problems:
+        buckets.setdefault(size_bucket(p.verts.shape[0]), []).append(p)
+    best = {}
+    for b, ps in sorted(buckets.items()):
+        ps = ps[:sample]
+        times = {}
+        for c in candidates:
+            bs = BatchSolver(ps, prec=prec, device=device, n_streams=min(c, len(ps)))
+            bs.run()                           # warm-up (allocations, tables)
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            bs.run()
+            torch.cuda.synchronize(device)
+            times[c] = time.perf_counter() - t0
+            bs.close()
+        best[b] = min(times, key=times.get)
+    return best
+
+
+class SolveGraph:
+    """One CUDA graph holding the FP64 Woodbury solves x_i = A_i^-1 v_i of every factored
+    problem of a BatchSolver (``solve_many_noalloc``: no allocation, so it can be recorded).
+    ``replay()`` re-runs all of them on whatever the captured v_i buffers hold now.  The
+    solves are recorded one after another on one stream (they share the library's fixed
+    scratch array)."""
+
+    def __init__(self, batch: BatchSolver, device: int = 0):
+        self.batch = batch
+        self.v = []
+        self.x = []
+        dev = torch.device("cuda", device)
+        L = bem.load_library()
+        for i, s in enumerate(batch.solvers):
+            if s is None:
+                raise ValueError("run the batch first")
+            nrhs = len(batch.problems[i].angles)
+            self.v.append(torch.zeros((nrhs, s.N), dtype=torch.complex128, device=dev))
+            self.x.append(torch.zeros((nrhs, s.N), dtype=torch.complex128, device=dev))
+        self.stream = torch.cuda.Stream(device=device)
+        # first call outside capture (looks up the scratch array), then record
+        for i, s in enumerate(batch.solvers):
+            L.bem_set_stream(s.h, torch.cuda.current_stream(dev).cuda_stream)
+            st = L.solve_many_noalloc(s.h, self.v[i].data_ptr(), s.N, self.x[i].data_ptr(), s.N, self.v[i].shape[0])
+            if st != 0:
+                raise bem.BemError(st, L.bem_last_error(s.h).decode())
+        torch.cuda.synchronize(device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            for i, s in enumerate(batch.solvers):
+                L.bem_set_stream(s.h, self.stream.cuda_stream)
+                st = L.solve_many_noalloc(s.h, self.v[i].data_ptr(), s.N, self.x[i].data_ptr(), s.N,
+                                          self.v[i].shape[0])
+                if st != 0:
+                    raise bem.BemError(st, L.bem_last_error(s.h).decode())
+        for s in batch.solvers:
+            L.bem_set_stream(s.h, s.stream.cuda_stream)
+
+    def replay(self):
+        self.graph.replay()

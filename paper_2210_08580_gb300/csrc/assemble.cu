@@ -812,8 +812,9 @@ __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
     }
 }
 
-// per-segment geometry (SoA) and chord statistics: stats[0] = min h, stats[1] = max h,
-// stats[2] = sum h (by atomics on ordered bit patterns of positive doubles)
+// per-segment geometry (SoA) and chord statistics: stats[0] = min h, stats[1] = max h (by
+// atomics on the ordered bit patterns of positive doubles); the sum of h is formed by
+// k_sum_h in a fixed order, so the mean chord is the same on every run
 __global__ void k_geometry(const double* verts, int N, double* seg, double* stats) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N) return;
@@ -825,7 +826,20 @@ __global__ void k_geometry(const double* verts, int N, double* seg, double* stat
     unsigned long long hb = __double_as_longlong(h);
     atomicMin(reinterpret_cast<unsigned long long*>(stats), hb);
     atomicMax(reinterpret_cast<unsigned long long*>(stats + 1), hb);
-    atomicAdd(stats + 2, h);
+}
+
+// stats[2] = sum of h over the N segments, one CTA, fixed summation order
+__global__ void __launch_bounds__(1024) k_sum_h(const double* hseg, int N, double* stats) {
+    __shared__ double part[1024];
+    double s = 0.0;
+    for (int e = threadIdx.x; e < N; e += blockDim.x) s += hseg[e];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) stats[2] = part[0];
 }
 
 bem_status launch_geometry(bem_ctx* h, const double* verts, int64_t N, double* stats_dev) {
@@ -833,6 +847,8 @@ bem_status launch_geometry(bem_ctx* h, const double* verts, int64_t N, double* s
     BEM_CUDA(h, cudaMemcpyAsync(stats_dev, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
     BEM_TIMED(h, "k_geometry", (k_geometry<<<(unsigned)((N + 255) / 256), 256, 0, h->stream>>>(verts, (int)N, h->seg, stats_dev)));
     BEM_LAUNCH(h, "k_geometry");
+    BEM_TIMED(h, "k_sum_h", (k_sum_h<<<1, 1024, 0, h->stream>>>(h->seg + 4 * N, (int)N, stats_dev)));
+    BEM_LAUNCH(h, "k_sum_h");
     return BEM_OK;
 }
 
