@@ -214,6 +214,24 @@ bem_status bem_farfield(bem_handle h, const double* obs_angles_dev, int64_t nobs
 bem_status bem_farfield_adjoint(bem_handle h, const double* obs_angles_dev, int64_t nobs, const void* g_dev,
                                 int64_t ldg, int64_t nrhs, void* out_dev, int64_t ldo);
 
+/* bem_shape_vjp -- gradient with respect to the vertex coordinates of a real far-field
+ * misfit J(u), u = F x, x = A^-1 (a_w v_w): the adjoint (reverse) derivative through the
+ * assembly of S and N (every segment pair's integrals differentiated: the Gauss rule of
+ * separated pairs, the closed forms of self and adjacent pairs), the Gram matrix, the
+ * plane-wave right-hand sides and the far-field operator.  A = I/4 + Q Q^T C_x is the
+ * filtered operator of Sec. IV-A with the compression taken as exact (use compress_compact
+ * with rel_tol = 0), Q the Fourier filter basis (fixed for equal-chord meshes), so the
+ * result is the gradient along equal-chord deformations.  Inputs (device): angles (nrhs
+ * incidence angles of the right-hand sides), amplitudes (nrhs complex a_w, NULL = all 1),
+ * obs_angles (nobs), x (N x nrhs, the solution), gu (nobs x nrhs: dJ/du in the
+ * dJ/dRe + i dJ/dIm convention), lambda = A^-H F^H gu (N x nrhs, from bem_farfield_adjoint
+ * and solve_backward).  Output: grad (2N doubles, (x_i, y_i), overwritten).  EFIE only
+ * (alpha = 0), N >= 5, FP64 arithmetic; synchronises the stream.  The paper states no
+ * derivative; this is the differentiation layer's shape derivative. */
+bem_status bem_shape_vjp(bem_handle h, const double* angles_dev, const void* amplitudes_dev, int64_t nrhs,
+                         const double* obs_angles_dev, int64_t nobs, const void* x_dev, const void* gu_dev,
+                         const void* lambda_dev, double* grad_dev);
+
 /* Copies an internal matrix (BEM_MAT_*) into dst_dev with leading dimension ld (>= rows).
  * For BEM_MAT_SIGMA, dst_dev receives n doubles and ld is ignored. */
 bem_status bem_get_matrix(bem_handle h, int which, void* dst_dev, int64_t ld);

@@ -26,7 +26,8 @@ STATUS = {0: "BEM_OK", 1: "BEM_E_INVALID", 2: "BEM_E_NOMEM", 3: "BEM_E_CUDA", 4:
 EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error", "bem_set_stream",
            "bem_assemble", "filter_apply", "compress_compact", "factor", "bem_rhs_planewave",
            "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info", "bem_timing_enable",
-           "bem_timing_report", "solve_many_noalloc", "bem_farfield", "bem_farfield_adjoint")
+           "bem_timing_report", "solve_many_noalloc", "bem_farfield", "bem_farfield_adjoint",
+           "bem_shape_vjp")
 
 
 class BemOptions(ctypes.Structure):
@@ -82,12 +83,13 @@ def load_library(path: str = LIB_PATH):
     L.solve_many_noalloc.restype = ctypes.c_int
     L.bem_farfield.argtypes = [vp, vp, i64, vp, i64, i64, vp, i64]
     L.bem_farfield_adjoint.argtypes = [vp, vp, i64, vp, i64, i64, vp, i64]
+    L.bem_shape_vjp.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp, vp]
     L.bem_timing_enable.argtypes = [vp, i32]
     L.bem_timing_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     for name in ("bem_create", "bem_destroy", "bem_set_stream", "bem_assemble", "filter_apply",
                  "compress_compact", "factor", "bem_rhs_planewave", "solve_many", "solve_backward",
                  "bem_get_matrix", "bem_get_info", "bem_timing_enable", "bem_timing_report", "bem_farfield",
-                 "bem_farfield_adjoint"):
+                 "bem_farfield_adjoint", "bem_shape_vjp"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -209,6 +211,20 @@ class Solver:
                                                 _ptr(out), self.N))
         return out
 
+    def shape_vjp(self, angles, amplitudes, obs_angles, x: torch.Tensor, gu: torch.Tensor,
+                  lam: torch.Tensor) -> torch.Tensor:
+        """d J / d verts (N, 2) for the misfit whose far-field gradient is gu (nrhs, nobs);
+        x (nrhs, N) the solution, lam (nrhs, N) = A^-H F^H gu."""
+        ang = torch.as_tensor(angles, dtype=torch.float64).to(self.device).contiguous()
+        obs = torch.as_tensor(obs_angles, dtype=torch.float64).to(self.device).contiguous()
+        amp = None if amplitudes is None else \
+            torch.as_tensor(amplitudes, dtype=torch.complex128).to(self.device).contiguous()
+        grad = torch.empty((self.N, 2), dtype=torch.float64, device=self.device)
+        self._check(self.L.bem_shape_vjp(self.h, _ptr(ang), _ptr(amp) if amp is not None else None, ang.numel(),
+                                         _ptr(obs), obs.numel(), _ptr(x.contiguous()), _ptr(gu.contiguous()),
+                                         _ptr(lam.contiguous()), _ptr(grad)))
+        return grad
+
     # ---------------------------------------------------------------- introspection
     def timing(self, enable: bool):
         self._check(self.L.bem_timing_enable(self.h, 1 if enable else 0))
@@ -271,3 +287,56 @@ class FarFieldSolve(torch.autograd.Function):
 def farfield_solve(v: torch.Tensor, solver: "Solver", obs_angles) -> torch.Tensor:
     """Differentiable u_inf(v) (see FarFieldSolve)."""
     return FarFieldSolve.apply(v, solver, obs_angles)
+
+
+class ShapeFarField(torch.autograd.Function):
+    """u_inf (nrhs, nobs) of the star r(theta) = r0 + sum_m c_m cos(m theta) + s_m sin(m theta)
+    on an equal-chord mesh of N vertices, for incident plane waves of angles ``angles`` with
+    complex amplitudes ``amplitudes``; differentiable in the Fourier coefficients
+    ``coef`` = (c_1..c_M, s_1..s_M) (float64) and in the amplitudes.
+
+    Forward: mesh (host), bem_assemble .. factor (FP64, filter n_modes, no truncation),
+    right-hand sides, solve_many, bem_farfield.  Backward (adjoint method): lambda =
+    solve_backward(bem_farfield_adjoint(gu)); d/dverts from bem_shape_vjp; chained to the
+    coefficients through the derivative of the equal-chord mesh (inputs.equal_chord_tangent);
+    the amplitude gradient is sum_i conj(v0_iw) lambda_iw."""
+
+    @staticmethod
+    def forward(ctx, coef, amplitudes, r0, N, k, n_modes, angles, obs_angles, device=0):
+        from . import inputs
+        c = coef.detach().cpu().numpy()
+        M = c.shape[0] // 2
+        curve = inputs.PolarCurve(r0=float(r0), cos_coef=tuple(c[:M]), sin_coef=tuple(c[M:]))
+        verts, theta, h = inputs.equal_chord_mesh(curve, int(N))
+        s = Solver(device=device, prec="fp64")
+        dev = s.device
+        s.assemble(torch.from_numpy(verts).to(dev), float(k), ops="SW")
+        s.filter_apply(int(n_modes))
+        s.compress(0.0)
+        s.factor()
+        ang = torch.as_tensor(angles, dtype=torch.float64).to(dev)
+        obs = torch.as_tensor(obs_angles, dtype=torch.float64).to(dev)
+        amp = amplitudes.detach().to(dev, torch.complex128)
+        v0 = s.rhs_planewave(ang)
+        x = s.solve(amp[:, None] * v0)
+        u = s.farfield(obs, x)
+        ctx.s, ctx.ang, ctx.obs, ctx.amp, ctx.v0, ctx.x = s, ang, obs, amp, v0, x
+        ctx.tangent = torch.from_numpy(inputs.equal_chord_tangent(curve, theta, h))
+        ctx.coef_device = coef.device
+        return u
+
+    @staticmethod
+    def backward(ctx, gu):
+        s = ctx.s
+        gu = gu.contiguous()
+        lam = s.solve_backward(s.farfield_adjoint(ctx.obs, gu))
+        grad_a = (ctx.v0.conj() * lam).sum(dim=1)
+        gv = s.shape_vjp(ctx.ang, ctx.amp, ctx.obs, ctx.x, gu, lam)
+        grad_c = torch.einsum("pnd,nd->p", ctx.tangent, gv.cpu()).to(ctx.coef_device)
+        s.close()
+        return grad_c, grad_a, None, None, None, None, None, None, None
+
+
+def shape_farfield(coef, amplitudes, r0, N, k, n_modes, angles, obs_angles, device=0):
+    """Differentiable far field of a Fourier star (see ShapeFarField)."""
+    return ShapeFarField.apply(coef, amplitudes, r0, N, k, n_modes, angles, obs_angles, device)

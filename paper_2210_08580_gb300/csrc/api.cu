@@ -631,6 +631,109 @@ bem_status bem_farfield_adjoint(bem_handle h, const double* obs_angles, int64_t 
     return launch_conj_scale(h, (const cplx*)out, ldo, (cplx*)out, ldo, cmk(1, 0), h->N, nrhs);
 }
 
+// Shape gradient of a far-field misfit (see bem.h).  Notation: A = I/4 + Q Q^T C_x, C_x =
+// G^-1 S G^-1 N - I/4 (the filtered operator, compression taken as exact), v = G^-1 S G^-1 f,
+// u = F x, x = A^-1 v, lambda = A^-H F^H gu.  With mu = Q Q^T lambda,
+//   dJ = Re gu^H dF x + Re lambda^H dv - Re mu^H dC_x x
+// and, writing a1 = G^-1 lambda, b1 = G^-1 f, a2 = G^-1 mu, b2 = G^-1 N x,
+// a3 = G^-1 conj(S) a2, zeta = G^-1 conj(S) a1 (S is complex symmetric):
+//   S terms   Re sum_ij conj(a1_i) dS_ij b1_j - conj(a2_i) dS_ij b2_j
+//   N terms  -Re sum_ij conj(a3_i) dN_ij x_j
+//   G terms  -Re a1^H dG v - Re zeta^H dG b1 + Re a2^H dG (G^-1 S b2) + Re a3^H dG b2
+//   f terms   Re zeta^H df,   F terms  Re sum_oi (C0 sum_r x_ir conj(gu_or)) df_i(-xhat_o).
+bem_status bem_shape_vjp(bem_handle h, const double* angles, const void* amplitudes, int64_t nrhs,
+                         const double* obs_angles, int64_t nobs, const void* x_dev, const void* gu_dev,
+                         const void* lambda_dev, double* grad_dev) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 2 || !h->S || !h->W)
+        return bem_fail(h, BEM_E_INVALID, "bem_shape_vjp: needs S and N assembled and filter_apply");
+    if (h->alpha != 0.0) return bem_fail(h, BEM_E_UNSUPPORTED, "bem_shape_vjp: EFIE only (alpha = 0)");
+    if (!angles || !obs_angles || !x_dev || !gu_dev || !lambda_dev || !grad_dev || nrhs < 1 || nrhs > 65535 ||
+        nobs < 1 || nobs > 65535)
+        return bem_fail(h, BEM_E_INVALID, "bem_shape_vjp: bad arguments");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    const int64_t N = h->N, nc = h->ncols, R = nrhs;
+    const cplx* x = (const cplx*)x_dev;
+    const cplx* lam = (const cplx*)lambda_dev;
+    const cplx* gu = (const cplx*)gu_dev;
+    bem_status st;
+    cplx *f, *a1, *b1, *mu, *a2, *t1, *b2, *a3, *zeta, *v, *Zx, *AB, *BB, *OmS, *OmW, *Wob, *Tq, *tmp;
+    double *ang2, *sign;
+    const cplx** PQ;
+    Carve cv;
+    for (cplx** p : {&f, &a1, &b1, &mu, &a2, &t1, &b2, &a3, &zeta, &v, &Zx, &tmp}) cv.add((void**)p, sizeof(cplx) * N * R);
+    cv.add((void**)&AB, sizeof(cplx) * N * 2 * R);
+    cv.add((void**)&BB, sizeof(cplx) * N * 2 * R);
+    cv.add((void**)&OmS, sizeof(cplx) * N * N);
+    cv.add((void**)&OmW, sizeof(cplx) * N * N);
+    cv.add((void**)&Wob, sizeof(cplx) * N * nobs);
+    cv.add((void**)&Tq, sizeof(cplx) * nc * R);
+    cv.add((void**)&ang2, sizeof(double) * nobs);
+    cv.add((void**)&sign, sizeof(double) * 4);
+    cv.add((void**)&PQ, sizeof(cplx*) * 8);
+    if ((st = cv.commit(h)) != BEM_OK) return st;
+    BEM_CUDA(h, cudaMemsetAsync(grad_dev, 0, sizeof(double) * 2 * N, h->stream));
+    // f (scaled by the amplitudes) and the G^-1 / Q Q^T / S / N products
+    if ((st = launch_rhs(h, angles, R, f, nullptr, N)) != BEM_OK) return st;
+    if (amplitudes) {
+        if ((st = launch_scale_cols(h, f, N, (const cplx*)amplitudes, N, R)) != BEM_OK) return st;
+    }
+    auto ginv = [&](const cplx* in, cplx* out) { return apply_gram_inverse(h, 0, in, out, tmp, N, R, 1, N, h->hbar, false); };
+    // conj(S) y = conj(S conj(y))
+    auto conjS = [&](const cplx* y, cplx* out) -> bem_status {
+        bem_status s2;
+        if ((s2 = launch_conj_scale(h, y, N, out, N, cmk(1, 0), N, R)) != BEM_OK) return s2;
+        if ((s2 = zgemm(h, OP_N, OP_N, N, R, N, cmk(1, 0), h->S, N, out, N, cmk(0, 0), t1, N)) != BEM_OK) return s2;
+        return launch_conj_scale(h, t1, N, out, N, cmk(1, 0), N, R);
+    };
+    h->tag = "gemm_shape_vjp";
+    if ((st = ginv(lam, a1)) != BEM_OK) return st;
+    if ((st = ginv(f, b1)) != BEM_OK) return st;
+    if ((st = dzgemm_realA(h, OP_T, nc, R, N, 1.0, h->Q, N, lam, N, 0.0, Tq, nc)) != BEM_OK) return st;
+    if ((st = dzgemm_realA(h, OP_N, N, R, nc, 1.0, h->Q, N, Tq, nc, 0.0, mu, N)) != BEM_OK) return st;
+    if ((st = ginv(mu, a2)) != BEM_OK) return st;
+    if ((st = zgemm(h, OP_N, OP_N, N, R, N, cmk(1, 0), h->W, N, x, N, cmk(0, 0), v, N)) != BEM_OK) return st;
+    if ((st = ginv(v, b2)) != BEM_OK) return st;
+    if ((st = conjS(a2, Zx)) != BEM_OK) return st;                 // Zx used as scratch here
+    if ((st = ginv(Zx, a3)) != BEM_OK) return st;
+    if ((st = conjS(a1, Zx)) != BEM_OK) return st;
+    if ((st = ginv(Zx, zeta)) != BEM_OK) return st;
+    if ((st = zgemm(h, OP_N, OP_N, N, R, N, cmk(1, 0), h->S, N, b1, N, cmk(0, 0), t1, N)) != BEM_OK) return st;
+    if ((st = ginv(t1, v)) != BEM_OK) return st;                   // v = G^-1 S G^-1 f
+    if ((st = zgemm(h, OP_N, OP_N, N, R, N, cmk(1, 0), h->S, N, b2, N, cmk(0, 0), t1, N)) != BEM_OK) return st;
+    if ((st = ginv(t1, Zx)) != BEM_OK) return st;                  // Zx = G^-1 S G^-1 N x
+    // Omega^S = conj([a1 a2]) [b1 -b2]^T, Omega^W = -conj(a3) x^T, stored transposed
+    if ((st = launch_copy2d(h, AB, N, a1, N, N, R, sizeof(cplx))) != BEM_OK) return st;
+    if ((st = launch_copy2d(h, AB + N * R, N, a2, N, N, R, sizeof(cplx))) != BEM_OK) return st;
+    if ((st = launch_copy2d(h, BB, N, b1, N, N, R, sizeof(cplx))) != BEM_OK) return st;
+    if ((st = launch_axpby(h, BB + N * R, N, b2, N, cmk(-1, 0), cmk(0, 0), N, R)) != BEM_OK) return st;
+    if ((st = zgemm(h, OP_N, OP_C, N, N, 2 * R, cmk(1, 0), BB, N, AB, N, cmk(0, 0), OmS, N)) != BEM_OK) return st;
+    if ((st = zgemm(h, OP_N, OP_C, N, N, R, cmk(-1, 0), x, N, a3, N, cmk(0, 0), OmW, N)) != BEM_OK) return st;
+    if ((st = launch_assemble_vjp(h, OmS, OmW, grad_dev)) != BEM_OK) return st;
+    // Gram terms
+    const cplx* hp[8] = {a1, zeta, a2, a3, v, b1, Zx, b2};
+    const double hs[4] = {-1.0, -1.0, 1.0, 1.0};
+    BEM_CUDA(h, cudaMemcpyAsync((void*)PQ, hp, sizeof(hp), cudaMemcpyHostToDevice, h->stream));
+    BEM_CUDA(h, cudaMemcpyAsync(sign, hs, sizeof(hs), cudaMemcpyHostToDevice, h->stream));
+    if ((st = launch_gram_vjp(h, (int)R, PQ, PQ + 4, sign, grad_dev)) != BEM_OK) return st;
+    // right-hand sides: weights conj(zeta_iw) a_w
+    if ((st = launch_conj_scale(h, zeta, N, t1, N, cmk(1, 0), N, R)) != BEM_OK) return st;
+    if (amplitudes) {
+        if ((st = launch_scale_cols(h, t1, N, (const cplx*)amplitudes, N, R)) != BEM_OK) return st;
+    }
+    if ((st = launch_rhs_vjp(h, angles, R, t1, N, grad_dev)) != BEM_OK) return st;
+    // far field: weights C0 sum_r x_ir conj(gu_or) at the directions -xhat_o
+    const double a0 = 1.0 / sqrt(8.0 * BEM_PI * h->k);
+    const cplx c0 = cmk(a0 * cos(0.25 * BEM_PI), a0 * sin(0.25 * BEM_PI));
+    if ((st = zgemm(h, OP_N, OP_C, N, nobs, R, c0, x, N, gu, nobs, cmk(0, 0), Wob, N)) != BEM_OK) return st;
+    if ((st = launch_shift(h, obs_angles, ang2, nobs, BEM_PI)) != BEM_OK) return st;
+    if ((st = launch_rhs_vjp(h, ang2, nobs, Wob, N, grad_dev)) != BEM_OK) return st;
+    // the host copies above read hp/hs from this frame: finish before returning
+    BEM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return check_dev_err(h);
+}
+
 bem_status bem_get_info(bem_handle h, bem_info* info) {
     if (!h || !info) return BEM_E_INVALID;
     cudaSetDevice(h->device);

@@ -961,3 +961,361 @@ bem_status launch_rhs(bem_ctx* h, const double* angles, int64_t nrhs, cplx* f, c
     BEM_LAUNCH(h, "k_rhs");
     return BEM_OK;
 }
+
+// =======================================================================================
+// Shape gradient (vector-Jacobian products of the assembly, the right-hand sides and the
+// Gram matrix with respect to the vertex coordinates).  For complex weights Omega (N x N,
+// passed transposed: OmT[j + i N] = Omega_ij) the pair kernel accumulates
+//     grad += d/d verts  Re sum_ij (Omega^S_ij S_ij + Omega^W_ij N_ij),
+// differentiating each segment pair's integrals: separated pairs by differentiating the
+// Gauss rule (dg/dr = -(i/4) k H1(k r), the node positions and the chord lengths), self
+// pairs through the closed form in h, adjacent pairs through the Duffy nodes (the closed
+// rho integrals are functions of |R(w)|^2).  FP64.  Each unordered pair {e, f} is visited
+// once; the two orderings share the integrals (I^{fe}_{ba} = I^{ef}_{ab}).
+// =======================================================================================
+struct VjpParams {
+    int N;
+    double k;
+    const double* seg;
+    const double* btab;
+    SeriesCoef sc;
+    const cplx* OmS;     // transposed: OmS[j + i N] = Omega^S_ij
+    const cplx* OmW;
+    double* grad;        // 2N: (x_i, y_i)
+};
+
+__device__ __forceinline__ cplx om_at(const cplx* OmT, int N, int i, int j) { return OmT[(int64_t)j + (int64_t)i * N]; }
+
+// the four pair weights w_ab (a: node on e, b: node on f), both orderings folded in
+__device__ __forceinline__ void pair_weights(const cplx* OmT, int N, int e, int f, bool self, cplx w[4]) {
+    const int ie[2] = {e, (e + 1) % N}, jf[2] = {f, (f + 1) % N};
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            cplx v = om_at(OmT, N, ie[a], jf[b]);
+            if (!self) v = cadd(v, om_at(OmT, N, jf[b], ie[a]));
+            w[a * 2 + b] = v;
+        }
+}
+
+__device__ __forceinline__ double re_mul(cplx a, cplx b) { return a.x * b.x - a.y * b.y; }   // Re(a b)
+
+// self pair: I_ab(h) closed form and dI_ab/dh
+__device__ void pair_self_dh(double h, const SeriesCoef& sc, cplx I[4], cplx dI[4]) {
+    const double lnh = log(h);
+    cplx i11 = cmk(0, 0), i01 = cmk(0, 0), d11 = cmk(0, 0), d01 = cmk(0, 0);
+    double h2m = h * h;                 // h^{2m+2}
+    for (int m = 0; m < sc.nm; ++m) {
+        const double p = 2.0 * m;
+        const double T11 = (2.0 / 3.0) / (p + 1) - 1.0 / (p + 2) + (1.0 / 3.0) / (p + 4);
+        const double L11 = -(2.0 / 3.0) / ((p + 1) * (p + 1)) + 1.0 / ((p + 2) * (p + 2)) -
+                           (1.0 / 3.0) / ((p + 4) * (p + 4));
+        const double T01 = (1.0 / 3.0) / (p + 1) - (1.0 / 3.0) / (p + 4);
+        const double L01 = -(1.0 / 3.0) / ((p + 1) * (p + 1)) + (1.0 / 3.0) / ((p + 4) * (p + 4));
+        const cplx A = sc.A[m];
+        const double B = sc.B[m];
+        const cplx f11 = cmk(A.x * T11 + B * (lnh * T11 + L11), A.y * T11);
+        const cplx f01 = cmk(A.x * T01 + B * (lnh * T01 + L01), A.y * T01);
+        i11 = cadd(i11, cscale(f11, h2m));
+        i01 = cadd(i01, cscale(f01, h2m));
+        // d/dh [h^{2m+2} f(ln h)] = h^{2m+1} [(2m+2) f + B T]
+        const double h2m1 = h2m / h;
+        d11 = cadd(d11, cscale(cmk((p + 2.0) * f11.x + B * T11, (p + 2.0) * f11.y), h2m1));
+        d01 = cadd(d01, cscale(cmk((p + 2.0) * f01.x + B * T01, (p + 2.0) * f01.y), h2m1));
+        h2m *= h * h;
+    }
+    I[0] = i11; I[3] = i11; I[1] = i01; I[2] = i01;
+    dI[0] = d11; dI[3] = d11; dI[1] = d01; dI[2] = d01;
+}
+
+// G_j(R2) of the adjacent-pair rho integrals and dG_j/dR2 (the series of adjacent_node)
+__device__ void adj_G(double R2, const SeriesCoef& sc, cplx G[3], cplx dG[3]) {
+    const double lnR = 0.5 * log(R2);
+    for (int j = 0; j < 3; ++j) { G[j] = cmk(0, 0); dG[j] = cmk(0, 0); }
+    double R2m = 1.0;
+    for (int m = 0; m < sc.nm; ++m) {
+        for (int j = 0; j < 3; ++j) {
+            const double a = 2.0 + j + 2.0 * m;
+            const cplx term = cmk((sc.A[m].x + sc.B[m] * lnR) / a - sc.B[m] / (a * a), sc.A[m].y / a);
+            G[j] = cadd(G[j], cscale(term, R2m));
+            // d/dR2 [R2^m term(lnR)] = m R2^{m-1} term + R2^m B/(2 a R2)
+            const double dr = (m > 0 ? m * R2m / R2 : 0.0);
+            dG[j] = cadd(dG[j], cmk(dr * term.x + R2m * sc.B[m] / (2.0 * a * R2), dr * term.y));
+        }
+        R2m *= R2;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_assemble_vjp(VjpParams p) {
+    const int N = p.N;
+    const int e = blockIdx.y;
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d > N / 2) return;
+    if ((N % 2) == 0 && d == N / 2 && e >= N / 2) return;    // each unordered pair once
+    const int f = (e + d) % N;
+    const SegV se = load_seg(p.seg, N, e), sf = load_seg(p.seg, N, f);
+    cplx wS[4], wW[4];
+    pair_weights(p.OmS, N, e, f, d == 0, wS);
+    pair_weights(p.OmW, N, e, f, d == 0, wW);
+    const double k2 = p.k * p.k;
+    const double sg[2] = {-1.0, 1.0};
+    cplx wM = cmk(0, 0);                        // sum_ab wW_ab sigma_a sigma_b (Maue's M0 term)
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) wM = cadd(wM, cscale(wW[a * 2 + b], sg[a] * sg[b]));
+    double g[8] = {0, 0, 0, 0, 0, 0, 0, 0};     // d/d (x_e, y_e, x_e+1, y_e+1, x_f, y_f, x_f+1, y_f+1)
+    if (d == 0) {
+        // self pair: a function of h_e only
+        cplx I[4], dI[4];
+        const double h = se.h;
+        pair_self_dh(h, p.sc, I, dI);
+        const cplx sI = cadd(cadd(I[0], I[1]), cadd(I[2], I[3]));
+        const cplx sdI = cadd(cadd(dI[0], dI[1]), cadd(dI[2], dI[3]));
+        double rho = 0.0;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                const int ab = a * 2 + b;
+                // N_ab = sigma_a sigma_b sum I / h^2 - k^2 I_ab
+                const cplx dW = csub(cscale(csub(cscale(sdI, 1.0 / (h * h)), cscale(sI, 2.0 / (h * h * h))), sg[a] * sg[b]),
+                                     cscale(dI[ab], k2));
+                rho += re_mul(wS[ab], dI[ab]) + re_mul(wW[ab], dW);
+            }
+        g[0] -= rho * se.tx; g[1] -= rho * se.ty;
+        g[2] += rho * se.tx; g[3] += rho * se.ty;
+    } else {
+        const double hh = se.h * sf.h;
+        const double c = se.tx * sf.tx + se.ty * sf.ty;              // nu_e . nu_f = t_e . t_f
+        cplx kap[4];
+        for (int ab = 0; ab < 4; ++ab)
+            kap[ab] = cadd(cscale(csub(wS[ab], cscale(wW[ab], k2 * c)), hh), wM);
+        cplx A[4] = {cmk(0, 0), cmk(0, 0), cmk(0, 0), cmk(0, 0)};  // I_ab / (h_e h_f)
+        if (d == 1) {
+            // adjacent pair (f = e + 1): vertices P_A = x_e, P_B = x_e+1, P_C = x_e+2;
+            // R = dE + w dF (tri 0) or w dE + dF (tri 1), dE = P_B - P_A, dF = P_C - P_B
+            const int qw = 16;
+            const double dEx = se.h * se.tx, dEy = se.h * se.ty, dFx = sf.h * sf.tx, dFy = sf.h * sf.ty;
+            double gA[2] = {0, 0}, gB[2] = {0, 0}, gC[2] = {0, 0};
+            for (int tri = 0; tri < 2; ++tri) {
+                for (int iw = 0; iw < qw; ++iw) {
+                    const double w = c_glx[gl_off(qw) + iw], ww = c_glw[gl_off(qw) + iw];
+                    double cc[4][3];
+                    double Rx, Ry, dA, dB, dC;       // dR/dP_A, dR/dP_B, dR/dP_C (scalar multiples of I)
+                    if (tri == 0) {
+                        Rx = dEx + w * dFx; Ry = dEy + w * dFy;
+                        dA = -1.0; dB = 1.0 - w; dC = w;
+                        cc[0][0] = 0; cc[0][1] = 1; cc[0][2] = -w;
+                        cc[1][0] = 0; cc[1][1] = 0; cc[1][2] = w;
+                        cc[2][0] = 1; cc[2][1] = -(1 + w); cc[2][2] = w;
+                        cc[3][0] = 0; cc[3][1] = w; cc[3][2] = -w;
+                    } else {
+                        Rx = w * dEx + dFx; Ry = w * dEy + dFy;
+                        dA = -w; dB = w - 1.0; dC = 1.0;
+                        cc[0][0] = 0; cc[0][1] = w; cc[0][2] = -w;
+                        cc[1][0] = 0; cc[1][1] = 0; cc[1][2] = w;
+                        cc[2][0] = 1; cc[2][1] = -(1 + w); cc[2][2] = w;
+                        cc[3][0] = 0; cc[3][1] = 1; cc[3][2] = -w;
+                    }
+                    cplx G[3], dG[3];
+                    adj_G(Rx * Rx + Ry * Ry, p.sc, G, dG);
+                    cplx xi = cmk(0, 0);
+                    for (int ab = 0; ab < 4; ++ab) {
+                        cplx sG = cmk(0, 0), sdG = cmk(0, 0);
+                        for (int j = 0; j < 3; ++j) {
+                            sG = cadd(sG, cscale(G[j], cc[ab][j]));
+                            sdG = cadd(sdG, cscale(dG[j], cc[ab][j]));
+                        }
+                        A[ab] = cadd(A[ab], cscale(sG, ww));
+                        xi = cadd(xi, cmul(kap[ab], cscale(sdG, ww)));
+                    }
+                    // d|R|^2 = 2 R . dR
+                    const double r2c = 2.0 * xi.x;
+                    gA[0] += r2c * dA * Rx; gA[1] += r2c * dA * Ry;
+                    gB[0] += r2c * dB * Rx; gB[1] += r2c * dB * Ry;
+                    gC[0] += r2c * dC * Rx; gC[1] += r2c * dC * Ry;
+                }
+            }
+            // chord lengths and the tangent product
+            double hpart = 0.0, cpart = 0.0;
+            for (int ab = 0; ab < 4; ++ab) {
+                hpart += re_mul(csub(wS[ab], cscale(wW[ab], k2 * c)), A[ab]);
+                cpart += -k2 * hh * re_mul(wW[ab], A[ab]);
+            }
+            const double ce[2] = {(sf.tx - c * se.tx) / se.h, (sf.ty - c * se.ty) / se.h};   // dc/dP_B via t_e
+            const double cf[2] = {(se.tx - c * sf.tx) / sf.h, (se.ty - c * sf.ty) / sf.h};   // dc/dP_C via t_f
+            const double te[2] = {se.tx, se.ty}, tf[2] = {sf.tx, sf.ty};
+            for (int q = 0; q < 2; ++q) {
+                gA[q] += hpart * (-sf.h * te[q]) + cpart * (-ce[q]);
+                gB[q] += hpart * (sf.h * te[q] - se.h * tf[q]) + cpart * (ce[q] - cf[q]);
+                gC[q] += hpart * (se.h * tf[q]) + cpart * cf[q];
+            }
+            g[0] = gA[0]; g[1] = gA[1]; g[2] = gB[0]; g[3] = gB[1]; g[6] = gC[0]; g[7] = gC[1];
+        } else {
+            // separated pair: q x q Gauss, as in the assembly
+            const float mx = (float)(se.x0 - sf.x0) + 0.5f * (float)(se.h * se.tx - sf.h * sf.tx);
+            const float my = (float)(se.y0 - sf.y0) + 0.5f * (float)(se.h * se.ty - sf.h * sf.ty);
+            const float hmax = (float)fmax(se.h, sf.h);
+            const float gap = fmaxf(sqrtf(mx * mx + my * my) - 0.5f * (float)(se.h + sf.h), 0.0f);
+            const int q = q_for_gap(gap / hmax, (float)p.k * (gap + hmax));
+            const double* xs = c_glx + gl_off(q);
+            const double* ws = c_glw + gl_off(q);
+            const double ux = se.h * se.tx, uy = se.h * se.ty, vx = sf.h * sf.tx, vy = sf.h * sf.ty;
+            for (int i = 0; i < q; ++i) {
+                const double s = xs[i];
+                const double px = se.x0 + s * ux, py = se.y0 + s * uy;
+                for (int j = 0; j < q; ++j) {
+                    const double t = xs[j], wgt = ws[i] * ws[j];
+                    const double Dx = sf.x0 + t * vx - px, Dy = sf.y0 + t * vy - py;
+                    const BesselU bu = bessel_u<true>(p.btab, k2 * (Dx * Dx + Dy * Dy));
+                    const cplx gv = cmk(-0.25 * bu.Y0, 0.25 * bu.J0);                  // (i/4) H0
+                    const cplx gq = cmk(0.25 * k2 * bu.Y1z, -0.25 * k2 * bu.J1z);      // g'(r)/r
+                    const double la[2] = {1.0 - s, s}, lb[2] = {1.0 - t, t};
+                    cplx kp = cmk(0, 0);
+                    for (int a = 0; a < 2; ++a)
+                        for (int b = 0; b < 2; ++b) {
+                            const double l = la[a] * lb[b];
+                            A[a * 2 + b] = cadd(A[a * 2 + b], cscale(gv, wgt * l));
+                            kp = cadd(kp, cscale(kap[a * 2 + b], l));
+                        }
+                    const double co = wgt * re_mul(kp, gq);
+                    // r dr/dx_e = -(1-s) D, r dr/dx_e+1 = -s D, r dr/dx_f = (1-t) D, r dr/dx_f+1 = t D
+                    g[0] -= co * (1.0 - s) * Dx; g[1] -= co * (1.0 - s) * Dy;
+                    g[2] -= co * s * Dx;         g[3] -= co * s * Dy;
+                    g[4] += co * (1.0 - t) * Dx; g[5] += co * (1.0 - t) * Dy;
+                    g[6] += co * t * Dx;         g[7] += co * t * Dy;
+                }
+            }
+            double hpart = 0.0, cpart = 0.0;
+            for (int ab = 0; ab < 4; ++ab) {
+                hpart += re_mul(csub(wS[ab], cscale(wW[ab], k2 * c)), A[ab]);
+                cpart += -k2 * hh * re_mul(wW[ab], A[ab]);
+            }
+            const double te[2] = {se.tx, se.ty}, tf[2] = {sf.tx, sf.ty};
+            for (int q2 = 0; q2 < 2; ++q2) {
+                const double ce = (tf[q2] - c * te[q2]) / se.h, cf = (te[q2] - c * tf[q2]) / sf.h;
+                g[0 + q2] += hpart * (-sf.h * te[q2]) - cpart * ce;
+                g[2 + q2] += hpart * (sf.h * te[q2]) + cpart * ce;
+                g[4 + q2] += hpart * (-se.h * tf[q2]) - cpart * cf;
+                g[6 + q2] += hpart * (se.h * tf[q2]) + cpart * cf;
+            }
+        }
+    }
+    const int v[4] = {e, (e + 1) % N, f, (f + 1) % N};
+    for (int q = 0; q < 4; ++q) {
+        if (g[2 * q] != 0.0) atomicAdd(p.grad + 2 * v[q], g[2 * q]);
+        if (g[2 * q + 1] != 0.0) atomicAdd(p.grad + 2 * v[q] + 1, g[2 * q + 1]);
+    }
+}
+
+// Right-hand-side vector-Jacobian product: f_i(d) = sum over the two segments at vertex i
+// of T_a = -i k (d x Delta) e^{i k d.x_e} phi_a(beta), beta = k d.Delta, Delta = x_e+1 - x_e
+// (d x Delta = d_x Delta_y - d_y Delta_x = h_e (d . nu_e)), phi_0 = int (1-s) e^{i beta s},
+// phi_1 = int s e^{i beta s}; grad += d/dverts Re sum_{i,w} om[i + w ld] f_i(d_w).
+// One thread per (segment, direction).
+__global__ void __launch_bounds__(256) k_rhs_vjp(const double* seg, int N, const double* angles, int nang, double k,
+                                                  const cplx* om, int64_t ld, double* grad) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = blockIdx.y;
+    if (e >= N || w >= nang) return;
+    double dy_, dx_;
+    sincos(angles[w], &dy_, &dx_);
+    const SegV s = load_seg(seg, N, e);
+    const double Dx = s.h * s.tx, Dy = s.h * s.ty;
+    const double beta = k * (dx_ * Dx + dy_ * Dy);
+    const double cr = dx_ * Dy - dy_ * Dx;
+    // phi_a(beta) and phi_a'(beta): sums of (i beta)^n / n! times 1/((n+1)(n+2)), 1/(n+2);
+    // derivatives i sum (i beta)^n/n! times 1/((n+2)(n+3)), 1/(n+3)
+    cplx c = cmk(1, 0), p0 = cmk(0, 0), p1 = cmk(0, 0), q0 = cmk(0, 0), q1 = cmk(0, 0);
+    for (int n = 0; n < 60; ++n) {
+        const double a = n + 1.0, b = n + 2.0, cc = n + 3.0;
+        p0 = cadd(p0, cscale(c, 1.0 / (a * b)));
+        p1 = cadd(p1, cscale(c, 1.0 / b));
+        q0 = cadd(q0, cscale(c, 1.0 / (b * cc)));
+        q1 = cadd(q1, cscale(c, 1.0 / cc));
+        c = cmul(c, cmk(0.0, beta / a));           // (i beta)^{n+1}/(n+1)!
+        if (fabs(c.x) + fabs(c.y) < 1e-20) break;
+    }
+    q0 = cmul(cmk(0, 1), q0);
+    q1 = cmul(cmk(0, 1), q1);
+    double sp, cp;
+    sincos(k * (dx_ * s.x0 + dy_ * s.y0), &sp, &cp);
+    const cplx E = cmk(cp, sp);
+    const cplx mik = cmk(0, -k);                 // -i k
+    const cplx o0 = om[(int64_t)e + (int64_t)w * ld], o1 = om[(int64_t)((e + 1) % N) + (int64_t)w * ld];
+    double gE[2] = {0, 0}, gE1[2] = {0, 0};
+    const cplx phi[2] = {p0, p1}, dphi[2] = {q0, q1}, oo[2] = {o0, o1};
+    for (int a = 0; a < 2; ++a) {
+        const cplx pre = cmul(oo[a], cmul(mik, E));          // om * (-i k) e^{i k d.x_e}
+        const cplx T = cmul(pre, cscale(phi[a], cr));         // om T_a
+        // d/dDelta: (-d_y, d_x) phi + cr phi' k d ; d/dx_e (phase): i k d T
+        const double gDx = re_mul(pre, cadd(cscale(phi[a], -dy_), cscale(dphi[a], cr * k * dx_)));
+        const double gDy = re_mul(pre, cadd(cscale(phi[a], dx_), cscale(dphi[a], cr * k * dy_)));
+        const cplx ikT = cmul(cmk(0, k), T);
+        gE[0] += ikT.x * dx_ - gDx; gE[1] += ikT.x * dy_ - gDy;
+        gE1[0] += gDx; gE1[1] += gDy;
+    }
+    atomicAdd(grad + 2 * e, gE[0]);
+    atomicAdd(grad + 2 * e + 1, gE[1]);
+    atomicAdd(grad + 2 * ((e + 1) % N), gE1[0]);
+    atomicAdd(grad + 2 * ((e + 1) % N) + 1, gE1[1]);
+}
+
+// Gram-matrix term: G_ii = (h_i-1 + h_i)/3, G_i,i+1 = h_i/6, so for a pair (p, q) of
+// N x nrhs blocks d/dh_e Re sum_r p_r^H G q_r = Re sum_r [(conj p_e q_e + conj p_e+1 q_e+1)/3
+// + (conj p_e q_e+1 + conj p_e+1 q_e)/6]; with h_e = |x_e+1 - x_e| this moves grad by
+// +-coef t_e.  Four signed pairs per call (sign[k] = 0 skips).
+__global__ void k_gram_vjp(const double* seg, int N, int nrhs, const cplx* const* P, const cplx* const* Q,
+                           const double* sign, double* grad) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const int e1 = (e + 1) % N;
+    double coef = 0.0;
+    for (int t = 0; t < 4; ++t) {
+        if (sign[t] == 0.0) continue;
+        double acc = 0.0;
+        for (int r = 0; r < nrhs; ++r) {
+            const cplx pe = P[t][e + (int64_t)r * N], pe1 = P[t][e1 + (int64_t)r * N];
+            const cplx qe = Q[t][e + (int64_t)r * N], qe1 = Q[t][e1 + (int64_t)r * N];
+            const cplx d = cadd(cscale(cadd(cmul(cconj(pe), qe), cmul(cconj(pe1), qe1)), 1.0 / 3.0),
+                                cscale(cadd(cmul(cconj(pe), qe1), cmul(cconj(pe1), qe)), 1.0 / 6.0));
+            acc += d.x;
+        }
+        coef += sign[t] * acc;
+    }
+    const double tx = seg[2 * N + e], ty = seg[3 * N + e];
+    atomicAdd(grad + 2 * e1, coef * tx);
+    atomicAdd(grad + 2 * e1 + 1, coef * ty);
+    atomicAdd(grad + 2 * e, -coef * tx);
+    atomicAdd(grad + 2 * e + 1, -coef * ty);
+}
+
+bem_status launch_assemble_vjp(bem_ctx* h, const cplx* OmS, const cplx* OmW, double* grad) {
+    if (h->N < 5) return bem_fail(h, BEM_E_UNSUPPORTED, "shape gradient: N >= 5 required");
+    VjpParams p;
+    p.N = (int)h->N;
+    p.k = h->k;
+    p.seg = h->seg;
+    const float4* tabf = nullptr;
+    bem_status st = bessel_table(h, &p.btab, &tabf);
+    if (st != BEM_OK) return st;
+    series_coefficients(h->k, 2.0 * h->hbar, &p.sc);
+    p.OmS = OmS;
+    p.OmW = OmW;
+    p.grad = grad;
+    dim3 grid((unsigned)((h->N / 2 + 1 + 255) / 256), (unsigned)h->N);
+    BEM_TIMED(h, "k_assemble_vjp", (k_assemble_vjp<<<grid, 256, 0, h->stream>>>(p)));
+    BEM_LAUNCH(h, "k_assemble_vjp");
+    return BEM_OK;
+}
+
+bem_status launch_rhs_vjp(bem_ctx* h, const double* angles, int64_t nang, const cplx* om, int64_t ld, double* grad) {
+    dim3 grid((unsigned)((h->N + 255) / 256), (unsigned)nang);
+    BEM_TIMED(h, "k_rhs_vjp", (k_rhs_vjp<<<grid, 256, 0, h->stream>>>(h->seg, (int)h->N, angles, (int)nang, h->k, om, ld, grad)));
+    BEM_LAUNCH(h, "k_rhs_vjp");
+    return BEM_OK;
+}
+
+bem_status launch_gram_vjp(bem_ctx* h, int nrhs, const cplx* const* P_dev, const cplx* const* Q_dev,
+                           const double* sign_dev, double* grad) {
+    BEM_TIMED(h, "k_gram_vjp", (k_gram_vjp<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(
+                                    h->seg, (int)h->N, nrhs, P_dev, Q_dev, sign_dev, grad)));
+    BEM_LAUNCH(h, "k_gram_vjp");
+    return BEM_OK;
+}

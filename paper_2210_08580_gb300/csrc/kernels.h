@@ -23,6 +23,12 @@ cudaError_t init_gauss_tables();
 bem_status launch_geometry(bem_ctx* h, const double* verts, int64_t N, double* stats_dev);
 bem_status launch_assemble(bem_ctx* h, unsigned ops);
 bem_status launch_rhs(bem_ctx* h, const double* angles, int64_t nrhs, cplx* f, cplx* hz, int64_t ld);
+// shape gradient: d/dverts Re sum(Omega^S .* S + Omega^W .* N) (Omega passed transposed),
+// d/dverts Re sum om .* f(angles), and the Gram terms of four signed (P, Q) block pairs
+bem_status launch_assemble_vjp(bem_ctx* h, const cplx* OmS_T, const cplx* OmW_T, double* grad);
+bem_status launch_rhs_vjp(bem_ctx* h, const double* angles, int64_t nang, const cplx* om, int64_t ld, double* grad);
+bem_status launch_gram_vjp(bem_ctx* h, int nrhs, const cplx* const* P_dev, const cplx* const* Q_dev,
+                           const double* sign_dev, double* grad);
 
 // linalg.cu
 enum { OP_N = 0, OP_T = 1, OP_C = 2 };
@@ -52,6 +58,7 @@ bem_status launch_axpby(bem_ctx* h, cplx* y, int64_t ldy, const cplx* x, int64_t
 bem_status launch_add_identity(bem_ctx* h, cplx* A, int64_t ld, int r, cplx d);
 bem_status launch_col_norm_ratio(bem_ctx* h, const cplx* num, int64_t ldn, const cplx* den,
                                  int64_t ldd, int64_t rows, int64_t cols, double* out_max);
+bem_status launch_scale_cols(bem_ctx* h, cplx* x, int64_t ldx, const cplx* s, int64_t rows, int64_t cols);
 bem_status launch_shift(bem_ctx* h, const double* in, double* out, int64_t n, double shift);
 bem_status launch_conj_scale(bem_ctx* h, const cplx* x, int64_t ldx, cplx* y, int64_t ldy, cplx a, int64_t rows,
                              int64_t cols);   // y = a conj(x)

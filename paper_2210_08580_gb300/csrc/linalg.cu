@@ -1141,6 +1141,19 @@ bem_status launch_shift(bem_ctx* h, const double* in, double* out, int64_t n, do
     BEM_LAUNCH(h, "k_shift");
     return BEM_OK;
 }
+// x[:, j] *= s[j] (complex column scale)
+__global__ void k_scale_cols(cplx* x, int64_t ldx, const cplx* s, int64_t rows, int64_t cols) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    x[i + j * ldx] = cmul(x[i + j * ldx], s[j]);
+}
+bem_status launch_scale_cols(bem_ctx* h, cplx* x, int64_t ldx, const cplx* s, int64_t rows, int64_t cols) {
+    const int64_t n = rows * cols;
+    BEM_TIMED(h, "k_scale_cols", (k_scale_cols<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(x, ldx, s, rows, cols)));
+    BEM_LAUNCH(h, "k_scale_cols");
+    return BEM_OK;
+}
 // y = a * conj(x) over a rows x cols block (leading dimensions ldx, ldy)
 __global__ void k_conj_scale(const cplx* x, int64_t ldx, cplx* y, int64_t ldy, cplx a, int64_t rows, int64_t cols) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -34,7 +34,7 @@ import numpy as np
 __all__ = [
     "PolarCurve", "circle", "cos_star", "random_star", "fourier_star",
     "perturbed_circle", "ellipse", "equal_chord_mesh", "regular_polygon",
-    "planewave_angles", "batch_problems", "BatchProblem",
+    "planewave_angles", "batch_problems", "BatchProblem", "equal_chord_tangent",
 ]
 
 
@@ -202,6 +202,45 @@ def equal_chord_mesh(curve: PolarCurve, N: int, tol: float = 1e-15, max_iter: in
         h += float(delta[-1])
     verts = np.ascontiguousarray(curve.point(th))
     return verts, th, h
+
+
+def equal_chord_tangent(curve: PolarCurve, theta, h: float) -> np.ndarray:
+    """Derivatives of the equal-chord vertices with respect to the curve's Fourier
+    coefficients p = (cos_coef..., sin_coef...): returns (P, N, 2).
+
+    The mesh solves F_i = |P(theta_{i+1}) - P(theta_i)| - h = 0 (theta_0 = 0, theta_N = 2 pi)
+    for theta_1..theta_{N-1} and h; differentiating at fixed p gives
+    J d(theta, h)/dp = -dF/dp with the Newton Jacobian J of ``equal_chord_mesh``, and
+    d r_i/dp = P'(theta_i) d theta_i/dp + dP/dp(theta_i), dP/dp(theta) = basis(theta) (cos, sin)."""
+    from scipy.sparse import csc_matrix
+    from scipy.sparse.linalg import splu
+
+    th = np.asarray(theta, dtype=np.float64)
+    N = th.shape[0]
+    th_ext = np.concatenate([th, [2.0 * math.pi]])
+    P = curve.point(th_ext)
+    dP = curve.dpoint(th_ext)
+    d = P[1:] - P[:-1]
+    u = d / np.linalg.norm(d, axis=-1)[:, None]
+    idx = np.arange(N)
+    a_diag = -np.einsum("ij,ij->i", u, dP[:-1])
+    a_sup = np.einsum("ij,ij->i", u, dP[1:])
+    rows = np.concatenate([idx[1:], idx[:-1], idx])
+    cols = np.concatenate([idx[1:] - 1, idx[:-1], np.full(N, N - 1)])
+    vals = np.concatenate([a_diag[1:], a_sup[:-1], -np.ones(N)])
+    lu = splu(csc_matrix((vals, (rows, cols)), shape=(N, N)))
+    mc, ms = len(curve.cos_coef), len(curve.sin_coef)
+    basis = [(lambda t, m=m: np.cos(m * t)) for m in range(1, mc + 1)] + \
+            [(lambda t, m=m: np.sin(m * t)) for m in range(1, ms + 1)]
+    out = np.zeros((len(basis), N, 2))
+    dir_ext = np.stack([np.cos(th_ext), np.sin(th_ext)], axis=-1)
+    for p_, b in enumerate(basis):
+        dPp = b(th_ext)[:, None] * dir_ext                      # dP/dp at the nodes
+        dF = np.einsum("ij,ij->i", u, dPp[1:] - dPp[:-1])
+        sol = lu.solve(-dF)
+        dth = np.concatenate([[0.0], sol[:-1]])
+        out[p_] = dP[:-1] * dth[:, None] + dPp[:-1]
+    return out
 
 
 def planewave_angles(nrhs: int) -> np.ndarray:
