@@ -3,9 +3,12 @@
 A batch of independent problems (uneven N, k and numbers of incident waves) is spread
 over several CUDA streams, one host thread per stream (the C calls release the GIL), so
 that the kernels of small problems fill the GPU side by side.  The cooperative kernels of
-the compression and the Woodbury core (grid barriers that need every CTA resident) run
-one problem at a time under a lock, with their stream synchronised before the lock is
-released, so two of them never share the GPU; everything else overlaps freely.
+the compression and the Woodbury core (grid barriers that need every CTA resident) draw
+on a budget of one CTA per SM: a problem enters that phase only when the CTAs of its
+largest cooperative grid fit in what the running ones leave, so every grid of the phase
+is resident at once (a problem whose grid alone exceeds the budget waits for an idle GPU
+and runs alone); its stream is synchronised before the budget is returned.  Everything
+else overlaps freely.
 
 ``autotune_streams`` times a few stream counts on a sample of the batch and keeps the
 fastest per problem-size bucket.  ``SolveGraph`` records the FP64 Woodbury solves of every
@@ -63,7 +66,10 @@ class BatchSolver:
         self.n_streams = max(1, int(n_streams))
         self.refine_rtol = refine_rtol
         self.streams = [torch.cuda.Stream(device=device) for _ in range(self.n_streams)]
-        self._coop = threading.Lock()
+        self._coop = threading.Condition()
+        props = torch.cuda.get_device_properties(device)
+        self.nsm = props.multi_processor_count
+        self._budget = self.nsm
         self.solvers: list[bem.Solver | None] = [None] * len(problems)
         self.results: list[dict | None] = [None] * len(problems)
 
@@ -79,13 +85,30 @@ class BatchSolver:
             ang = torch.from_numpy(np.ascontiguousarray(p.angles)).to(dev, non_blocking=True)
             s.assemble(verts, p.k, ops="SW")
             s.filter_apply(p.n_modes)
+            need = self._coop_ctas(p)
             with self._coop:
+                self._coop.wait_for(lambda: self._budget >= need)
+                self._budget -= need
+            try:
                 r = s.compress(p.tol)          # synchronises the stream (returns the rank)
                 s.factor()
                 stream.synchronize()
+            finally:
+                with self._coop:
+                    self._budget += need
+                    self._coop.notify_all()
             v = s.rhs_planewave(ang)
             x = s.solve(v)
             self.results[i] = dict(x=x, v=v, rank=r)
+
+    def _coop_ctas(self, p: Problem) -> int:
+        """CTAs of the problem's largest cooperative grid (QR, Jacobi, Gauss-Jordan), capped
+        at the budget (such a problem then runs its phase alone)."""
+        N, n = p.verts.shape[0], p.n_modes
+        qr = min((2 if (self.prec == "mixed" and n <= 256) else 1) * self.nsm, (N + 15) // 16)
+        jac = (n + 1) // 2
+        gj = max(1, (2 * n + 7) // 8)
+        return min(self.nsm, max(qr, jac, gj))
 
     def run(self) -> list[dict]:
         """Assemble, filter, compress, factor, form the RHS and solve every problem; returns

@@ -1,6 +1,7 @@
 // Dense Galerkin assembly of S, N (Maue form) and D on a closed polygon (Sec. II), and the
-// plane-wave right-hand sides.  FP64 throughout: the Hankel kernels are evaluated by the
-// project's own Bessel routines (bessel.cuh); singular pairs use closed forms.
+// plane-wave right-hand sides.  The Hankel kernels are evaluated by the project's own
+// Bessel routines (bessel.cuh); singular pairs use closed forms (FP64), separated pairs
+// double-float arithmetic (dfloat.cuh).
 //
 // Work decomposition: a CTA owns a T x T tile of vertex pairs (i, j) in the upper
 // triangle of tiles.  It first computes the 2x2 local integrals of the (T+1)^2 segment
@@ -25,6 +26,13 @@ __constant__ double c_glw[GL_MAXQ * (GL_MAXQ + 1) / 2];
 __device__ __forceinline__ int gl_off(int q) { return q * (q - 1) / 2; }
 #define RCP_MAX 72
 __constant__ double c_rcp[RCP_MAX];     // c_rcp[k] = 1/k (c_rcp[0] = 0)
+// double-float constants of the right-hand-side kernel: 1/k, Taylor coefficients of
+// sin and cos ((-1)^j / (2j+1)!, (-1)^j / (2j)!), pi/2
+__constant__ float2 c_rcp_df[RCP_MAX];
+#define SC_TERMS 11
+__constant__ float2 c_sin_df[SC_TERMS];
+__constant__ float2 c_cos_df[SC_TERMS];
+__constant__ float2 c_pio2_df;
 // the same rules as double-float pairs: node x, weights w (1 - x) and w x
 __constant__ float2 c_gx_df[GL_MAXQ * (GL_MAXQ + 1) / 2];
 __constant__ float2 c_gw0_df[GL_MAXQ * (GL_MAXQ + 1) / 2];
@@ -85,6 +93,29 @@ cudaError_t init_gauss_tables() {
     for (int k = 1; k < RCP_MAX; ++k) rc[k] = 1.0 / k;
     e = cudaMemcpyToSymbol(c_rcp, rc, sizeof(rc));
     if (e != cudaSuccess) return e;
+    {
+        float2 rdf[RCP_MAX], sdf[SC_TERMS], cdf[SC_TERMS];
+        for (int k = 0; k < RCP_MAX; ++k) {
+            const long double v = (k == 0) ? 0.0L : 1.0L / k;
+            const float hi = (float)v;
+            rdf[k] = make_float2(hi, (float)(v - (long double)hi));
+        }
+        long double fs = 1.0L, fc = 1.0L;             // (2j+1)!, (2j)!
+        for (int j = 0; j < SC_TERMS; ++j) {
+            if (j > 0) { fc *= (2.0L * j - 1) * (2.0L * j); fs *= (2.0L * j) * (2.0L * j + 1); }
+            const long double vs = ((j & 1) ? -1.0L : 1.0L) / fs, vc = ((j & 1) ? -1.0L : 1.0L) / fc;
+            const float hs = (float)vs, hc = (float)vc;
+            sdf[j] = make_float2(hs, (float)(vs - (long double)hs));
+            cdf[j] = make_float2(hc, (float)(vc - (long double)hc));
+        }
+        const long double pio2 = 1.5707963267948966192313216916397514L;
+        const float hp = (float)pio2;
+        const float2 pdf = make_float2(hp, (float)(pio2 - (long double)hp));
+        if ((e = cudaMemcpyToSymbol(c_rcp_df, rdf, sizeof(rdf))) != cudaSuccess) return e;
+        if ((e = cudaMemcpyToSymbol(c_sin_df, sdf, sizeof(sdf))) != cudaSuccess) return e;
+        if ((e = cudaMemcpyToSymbol(c_cos_df, cdf, sizeof(cdf))) != cudaSuccess) return e;
+        if ((e = cudaMemcpyToSymbol(c_pio2_df, &pdf, sizeof(pdf))) != cudaSuccess) return e;
+    }
     return cudaMemcpyToSymbol(c_glw, hw, sizeof(hw));
 }
 
@@ -915,44 +946,88 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
 //   f-part  -i k (d.nu_e) h_e base phi_a   (f_i = -<phi_i, du/dnu>)
 //   h2-part h_e base phi_a                  ([h2]_i = <phi_i, u_inc>)
 // ---------------------------------------------------------------------------------------
+// e^{i x} in double-float: x = n pi/2 + r, |r| <= pi/4 (n pi/2 formed as a double-float
+// product, good to about 1e-15 |x| for the phases met here), Taylor series of sin r and
+// cos r to r^21 (truncation below 1e-19), then the quadrant.
+__device__ __forceinline__ void dfl_sincos(dfl x, dfl& sn, dfl& cs) {
+    const float nf = rintf(x.hi * 0.636619772367581f);
+    const dfl r = dfl_sub(x, dfl_mul(dfl{nf, 0.f}, dfl_mk(c_pio2_df)));
+    const dfl r2 = dfl_mul(r, r);
+    dfl ps = dfl_mk(c_sin_df[SC_TERMS - 1]), pc = dfl_mk(c_cos_df[SC_TERMS - 1]);
+#pragma unroll
+    for (int j = SC_TERMS - 2; j >= 0; --j) {
+        ps = dfl_fma(ps, r2, dfl_mk(c_sin_df[j]));
+        pc = dfl_fma(pc, r2, dfl_mk(c_cos_df[j]));
+    }
+    const dfl s0 = dfl_mul(ps, r), c0 = pc;
+    switch (((int)nf) & 3) {
+        case 0: sn = s0; cs = c0; break;
+        case 1: sn = c0; cs = dfl_neg(s0); break;
+        case 2: sn = dfl_neg(s0); cs = dfl_neg(c0); break;
+        default: sn = dfl_neg(c0); cs = s0; break;
+    }
+}
+
+// Per segment e and direction d (all in double-float on the FP32 pipe):
+//   beta = k h_e (d.t_e), base = h_e exp(i k d.P0_e),
+//   phi_0 = int_0^1 (1-s) e^{i beta s} ds = sum_n (i beta)^n / (n! (n+1)(n+2)),
+//   phi_1 = int_0^1 s e^{i beta s} ds     = sum_n (i beta)^n / (n! (n+2))
+//   f-part  -i k (d.nu_e) base phi_a                (f_i = -<phi_i, du/dnu>)
+//   h2-part base phi_a                              ([h2]_i = <phi_i, u_inc>)
 __global__ void __launch_bounds__(256) k_rhs(const double* seg, int N, const double* angles, double k,
                                              cplx* f, cplx* hz, int64_t ld) {
-    __shared__ cplx sf0[257], sf1[257], sh0[257], sh1[257];
+    __shared__ float4 sf0[257], sf1[257], sh0[257], sh1[257];
+    __shared__ float2 s_d[3];                 // d_x, d_y, k (double-float)
     const int i0 = blockIdx.x * 256, w = blockIdx.y;
-    double dy_, dx_;
-    sincos(angles[w], &dy_, &dx_);
+    if (threadIdx.x == 0) {
+        double dy_, dx_;
+        sincos(angles[w], &dy_, &dx_);
+        const dfl a = dfl_from(dx_), b = dfl_from(dy_), c = dfl_from(k);
+        s_d[0] = make_float2(a.hi, a.lo); s_d[1] = make_float2(b.hi, b.lo); s_d[2] = make_float2(c.hi, c.lo);
+    }
+    __syncthreads();
+    const dfl dxd = dfl_mk(s_d[0]), dyd = dfl_mk(s_d[1]), kd = dfl_mk(s_d[2]);
     for (int t = threadIdx.x; t < 257; t += 256) {
         const int e = ((i0 - 1 + t) % N + N) % N;
-        const double x0 = seg[e], y0 = seg[N + e], tx = seg[2 * N + e], ty = seg[3 * N + e], he = seg[4 * N + e];
-        const double beta = k * he * (dx_ * tx + dy_ * ty);
-        const double dn = dx_ * ty - dy_ * tx;          // d . nu_e, nu = (ty, -tx)
-        double sb, cb;
-        sincos(k * (dx_ * x0 + dy_ * y0), &sb, &cb);
-        cplx c = cmk(1, 0), p0 = cmk(0, 0), p1 = cmk(0, 0);
+        const dfl x0 = dfl_from_bits(seg[e]), y0 = dfl_from_bits(seg[N + e]);
+        const dfl tx = dfl_from_bits(seg[2 * N + e]), ty = dfl_from_bits(seg[3 * N + e]);
+        const dfl he = dfl_from_bits(seg[4 * N + e]);
+        const dfl beta = dfl_mul(dfl_mul(kd, he), dfl_fma(dxd, tx, dfl_mul(dyd, ty)));
+        const dfl dn = dfl_sub(dfl_mul(dxd, ty), dfl_mul(dyd, tx));          // d . nu_e, nu = (ty, -tx)
+        dfl sb, cb;
+        dfl_sincos(dfl_mul(kd, dfl_fma(dxd, x0, dfl_mul(dyd, y0))), sb, cb);
+        // series: c = (i beta)^n / n!
+        cdfl c = {{1.f, 0.f}, {0.f, 0.f}}, p0 = cdfl_zero(), p1 = cdfl_zero();
         for (int n = 0; n < RCP_MAX - 2; ++n) {
-            const double r1 = c_rcp[n + 1], r2 = c_rcp[n + 2], r12 = r1 * r2;
-            p0.x = fma(c.x, r12, p0.x); p0.y = fma(c.y, r12, p0.y);
-            p1.x = fma(c.x, r2, p1.x); p1.y = fma(c.y, r2, p1.y);
+            const dfl r1 = dfl_mk(c_rcp_df[n + 1]), r2 = dfl_mk(c_rcp_df[n + 2]);
+            const dfl r12 = dfl_mul(r1, r2);
+            p0 = cdfl_fma_real(r12, c, p0);
+            p1 = cdfl_fma_real(r2, c, p1);
             // c <- c * i beta / (n+1)
-            const double br = beta * r1;
-            const double nr = -c.y * br, ni = c.x * br;
-            c.x = nr; c.y = ni;
-            if (fabs(c.x) + fabs(c.y) < 1e-19) break;
+            const dfl br = dfl_mul(beta, r1);
+            const cdfl nc = {dfl_neg(dfl_mul(c.im, br)), dfl_mul(c.re, br)};
+            c = nc;
+            if (fabsf(c.re.hi) + fabsf(c.im.hi) < 1e-19f) break;
         }
-        const cplx base = cmk(cb * he, sb * he);
-        const cplx b0 = cmul(base, p0), b1 = cmul(base, p1);
-        // -i k dn * b = (k dn b.y, -k dn b.x)
-        sf0[t] = cmk(k * dn * b0.y, -k * dn * b0.x);
-        sf1[t] = cmk(k * dn * b1.y, -k * dn * b1.x);
-        sh0[t] = b0; sh1[t] = b1;
+        const cdfl base = {dfl_mul(cb, he), dfl_mul(sb, he)};
+        auto cmul_df = [](const cdfl& a, const cdfl& b) -> cdfl {
+            return {dfl_fma(a.re, b.re, dfl_neg(dfl_mul(a.im, b.im))), dfl_fma(a.re, b.im, dfl_mul(a.im, b.re))};
+        };
+        const cdfl b0 = cmul_df(base, p0), b1 = cmul_df(base, p1);
+        // -i k dn * b = (k dn b.im, -k dn b.re)
+        const dfl kdn = dfl_mul(kd, dn);
+        sf0[t] = cdfl_pack({dfl_mul(kdn, b0.im), dfl_neg(dfl_mul(kdn, b0.re))});
+        sf1[t] = cdfl_pack({dfl_mul(kdn, b1.im), dfl_neg(dfl_mul(kdn, b1.re))});
+        sh0[t] = cdfl_pack(b0);
+        sh1[t] = cdfl_pack(b1);
     }
     __syncthreads();
     const int i = i0 + threadIdx.x;
     if (i >= N) return;
     const int t = threadIdx.x;
     // vertex i: segment i (local t+1) as node 0, segment i-1 (local t) as node 1
-    if (f) f[(int64_t)i + (int64_t)w * ld] = cadd(sf0[t + 1], sf1[t]);
-    if (hz) hz[(int64_t)i + (int64_t)w * ld] = cadd(sh0[t + 1], sh1[t]);
+    if (f) f[(int64_t)i + (int64_t)w * ld] = cdfl_to(cdfl_add(cdfl_unpack(sf0[t + 1]), cdfl_unpack(sf1[t])));
+    if (hz) hz[(int64_t)i + (int64_t)w * ld] = cdfl_to(cdfl_add(cdfl_unpack(sh0[t + 1]), cdfl_unpack(sh1[t])));
 }
 
 bem_status launch_rhs(bem_ctx* h, const double* angles, int64_t nrhs, cplx* f, cplx* hz, int64_t ld) {

@@ -85,3 +85,24 @@ __device__ __forceinline__ cplx cdfl_to(cdfl z) { return cmk(dfl_to(z.re), dfl_t
 __device__ __forceinline__ float4 cdfl_pack(cdfl z) { return make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo); }
 __device__ __forceinline__ cdfl cdfl_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
 
+
+// sqrt, 1/sqrt and division with one Newton correction of the float estimate (about 47
+// bits); arguments in the float normal range, x > 0 for the roots
+__device__ __forceinline__ dfl dfl_sqrt(dfl x) {
+    const float y = sqrtf(x.hi);
+    const dfl y2 = dfl_mul(dfl{y, 0.f}, dfl{y, 0.f});
+    const dfl r = dfl_sub(x, y2);
+    return dfl_qts(y, r.hi * (0.5f / y));
+}
+__device__ __forceinline__ dfl dfl_rsqrt(dfl x) {
+    const float y = rsqrtf(x.hi);
+    // y' = y + y (1 - x y^2) / 2
+    const dfl xy = dfl_mul(x, dfl{y, 0.f});
+    const dfl r = dfl_sub(dfl{1.f, 0.f}, dfl_mul(xy, dfl{y, 0.f}));
+    return dfl_qts(y, y * 0.5f * r.hi);
+}
+__device__ __forceinline__ dfl dfl_div(dfl a, dfl b) {
+    const float q = a.hi / b.hi;
+    const dfl r = dfl_sub(a, dfl_mul(dfl{q, 0.f}, b));
+    return dfl_qts(q, r.hi / b.hi);
+}

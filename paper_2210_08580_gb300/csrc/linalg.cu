@@ -832,8 +832,9 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // last touched its columns, so consecutive rounds overlap across the grid.  One grid
 // barrier per sweep decides convergence.  Waits are bounded (DEVERR_TIMEOUT).
 // The columns are held in double-float (float4 per complex entry): dot products, their
-// reductions and the rotation run on the FP32 pipe; the rotation parameters are formed
-// once per pair in FP64 by one thread.
+// reductions and the rotation run on the FP32 pipe, the rotation scalars included (formed
+// once per pair by one thread with double-float roots and quotients, which keeps the FP64
+// pipe's long dependent latency off the round's critical path).
 __global__ void __launch_bounds__(JAC_NT) k_jacobi(float4* X, int n, int* ver, int* flags, int max_sweeps,
                                                    unsigned* bar, int* err) {
     __shared__ float2 red[JAC_NT / 32][4];
@@ -893,28 +894,43 @@ __global__ void __launch_bounds__(JAC_NT) k_jacobi(float4* X, int n, int* ver, i
                         for (int k = 0; k < 4; ++k) red[wid][k] = make_float2(v4[k].hi, v4[k].lo);
                     __syncthreads();
                     if (tid == 0) {
-                        double sm[4];
+                        // rotation scalars in double-float, on values scaled by 2^-E with 2^E
+                        // near max(A, B) (|g|^2 <= A B keeps everything below 1)
+                        dfl sm[4];
                         for (int k = 0; k < 4; ++k) {
                             dfl t = dfl_mk(red[0][k]);
                             for (int w = 1; w < JAC_NT / 32; ++w) t = dfl_add(t, dfl_mk(red[w][k]));
-                            sm[k] = dfl_to(t);
+                            sm[k] = t;
                         }
-                        const double A = sm[0], B = sm[1], GR = sm[2], GI = sm[3];
-                        const double ag2 = GR * GR + GI * GI;
+                        const float mx = fmaxf(sm[0].hi, sm[1].hi);
+                        const float sc = (mx > 0.f) ? __int_as_float((254 - ((__float_as_int(mx) >> 23) & 255)) << 23) : 1.f;
+                        const dfl A = dfl_scale(sm[0], sc), Bv = dfl_scale(sm[1], sc);
+                        const dfl GR = dfl_scale(sm[2], sc), GI = dfl_scale(sm[3], sc);
+                        const dfl ag2 = dfl_fma(GR, GR, dfl_mul(GI, GI));
                         // converged pair: |x^H y| <= 1e-14 |x| |y|
-                        int rot = !(ag2 <= 1e-28 * A * B || ag2 == 0.0);
+                        const dfl ab = dfl_mul(A, Bv);
+                        int rot = (ag2.hi > 0.f) && !(ag2.hi <= 1e-28f * ab.hi);
                         if (rot) {
                             flags[sweep] = 1;
-                            const double rag = rsqrt(ag2);
-                            const double zeta = 0.5 * (B - A) * rag;
-                            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                            const double c = rsqrt(1.0 + t * t), sr = c * t * rag;
-                            // c, s e^{-i phi}, s e^{i phi}
-                            const double rp[5] = {c, sr * GR, -sr * GI, sr * GR, sr * GI};
-                            for (int k = 0; k < 5; ++k) {
-                                const dfl d = dfl_from(rp[k]);
-                                s_rotp[k] = make_float2(d.hi, d.lo);
+                            const dfl rag = dfl_rsqrt(ag2);                       // 1/|g|
+                            const dfl zeta = dfl_scale(dfl_mul(dfl_sub(Bv, A), rag), 0.5f);
+                            dfl t;
+                            if (fabsf(zeta.hi) > 1e15f) {
+                                t = dfl_div(dfl{0.5f, 0.f}, zeta);               // 1/(2 zeta)
+                            } else {
+                                const dfl den = dfl_add(dfl{fabsf(zeta.hi), zeta.hi < 0.f ? -zeta.lo : zeta.lo},
+                                                        dfl_sqrt(dfl_fma(zeta, zeta, dfl{1.f, 0.f})));
+                                t = dfl_div(dfl{zeta.hi >= 0.f ? 1.f : -1.f, 0.f}, den);
                             }
+                            const dfl c = dfl_rsqrt(dfl_fma(t, t, dfl{1.f, 0.f}));
+                            const dfl sr = dfl_mul(dfl_mul(c, t), rag);
+                            const dfl srGR = dfl_mul(sr, GR), srGI = dfl_mul(sr, GI);
+                            // c, s e^{-i phi}, s e^{i phi}
+                            s_rotp[0] = make_float2(c.hi, c.lo);
+                            s_rotp[1] = make_float2(srGR.hi, srGR.lo);
+                            s_rotp[2] = make_float2(-srGI.hi, -srGI.lo);
+                            s_rotp[3] = make_float2(srGR.hi, srGR.lo);
+                            s_rotp[4] = make_float2(srGI.hi, srGI.lo);
                         }
                         s_rot = rot;
                     }
