@@ -554,8 +554,8 @@ __global__ void k_to_dfl(float4* X, int64_t count) {
 // is bound by L2 latency otherwise); one cross-warp reduction per phase.  The cross-CTA
 // sums of the dots are split over the grid (a third barrier per column), since repeating
 // them in every CTA kept the FP64 pipe busy.  n <= 32 QR_KC.
-#define QR_KC 8
-__global__ void __launch_bounds__(256) k_house_qr_df(float4* X, int64_t N, int n, cplx* R, int* perm, double* partC,
+#define QR_KC 7
+__global__ void __launch_bounds__(256, 2) k_house_qr_df(float4* X, int64_t N, int n, cplx* R, int* perm, double* partC,
                                                      unsigned long long* cnq, cplx* partW, float4* wdf, unsigned* bar,
                                                      int* err) {
     __shared__ double red[32];
@@ -680,7 +680,24 @@ __global__ void __launch_bounds__(256) k_house_qr_df(float4* X, int64_t N, int n
 #pragma unroll
             for (int k = 0; k < QR_KC; ++k) acc[k] = cdfl_zero();
             if (tau != 0.0) {
-                for (int64_t i = max(r0, (int64_t)j) + rg; i < r1; i += 8) {
+                // two rows per pass: all their loads are issued before the arithmetic
+                int64_t i = max(r0, (int64_t)j) + rg;
+                for (; i + 8 < r1; i += 16) {
+                    const cdfl va = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
+                    const cdfl vb = cdfl_ld(X + (i + 8) * n + pj);
+                    cdfl xa[QR_KC], xb[QR_KC];
+#pragma unroll
+                    for (int k = 0; k < QR_KC; ++k) {
+                        xa[k] = (pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
+                        xb[k] = (pcs[k] >= 0) ? cdfl_ld(X + (i + 8) * n + pcs[k]) : cdfl_zero();
+                    }
+#pragma unroll
+                    for (int k = 0; k < QR_KC; ++k) {
+                        cdfl_conj_fma(acc[k], va, xa[k]);
+                        cdfl_conj_fma(acc[k], vb, xb[k]);
+                    }
+                }
+                if (i < r1) {
                     const cdfl vi = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
 #pragma unroll
                     for (int k = 0; k < QR_KC; ++k)
@@ -723,12 +740,11 @@ __global__ void __launch_bounds__(256) k_house_qr_df(float4* X, int64_t N, int n
                 nw[k] = (pcs[k] >= 0) ? cdfl_unpack(wsm[lane + 32 * k]) : cdfl_zero();
                 acc[k] = {0.f, 0.f};
             }
-            for (int64_t i = max(r0, (int64_t)j) + rg; i < r1; i += 8) {
-                const cdfl vi = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
+            auto upd = [&](int64_t i, const cdfl& vi, cdfl* xr) {
 #pragma unroll
                 for (int k = 0; k < QR_KC; ++k) {
                     if (pcs[k] < 0) continue;
-                    cdfl x = cdfl_ld(X + i * n + pcs[k]);
+                    cdfl x = xr[k];
                     if (tau != 0.0) {
                         x.re = dfl_fma(vi.re, nw[k].re, dfl_fma(dfl_neg(vi.im), nw[k].im, x.re));
                         x.im = dfl_fma(vi.re, nw[k].im, dfl_fma(vi.im, nw[k].re, x.im));
@@ -736,6 +752,27 @@ __global__ void __launch_bounds__(256) k_house_qr_df(float4* X, int64_t N, int n
                     }
                     if (i > j) acc[k] = dfl_norm_acc(x, acc[k]);
                 }
+            };
+            // two rows per pass: both rows' loads precede the first store
+            int64_t i = max(r0, (int64_t)j) + rg;
+            for (; i + 8 < r1; i += 16) {
+                const cdfl va = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
+                const cdfl vb = cdfl_ld(X + (i + 8) * n + pj);
+                cdfl xa[QR_KC], xb[QR_KC];
+#pragma unroll
+                for (int k = 0; k < QR_KC; ++k) {
+                    xa[k] = (pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
+                    xb[k] = (pcs[k] >= 0) ? cdfl_ld(X + (i + 8) * n + pcs[k]) : cdfl_zero();
+                }
+                upd(i, va, xa);
+                upd(i + 8, vb, xb);
+            }
+            if (i < r1) {
+                const cdfl vi = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
+                cdfl xr[QR_KC];
+#pragma unroll
+                for (int k = 0; k < QR_KC; ++k) xr[k] = (pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
+                upd(i, vi, xr);
             }
             __syncthreads();                      // wbuf reuse (the dots were reduced above)
 #pragma unroll
