@@ -105,7 +105,7 @@ class BatchSolver:
         """CTAs of the problem's largest cooperative grid (QR, Jacobi, Gauss-Jordan), capped
         at the budget (such a problem then runs its phase alone)."""
         N, n = p.verts.shape[0], p.n_modes
-        qr = min((2 if (self.prec == "mixed" and n <= 256) else 1) * self.nsm, (N + 15) // 16)
+        qr = min(self.nsm, (N + 15) // 16)
         jac = (n + 1) // 2
         gj = max(1, (2 * n + 7) // 8)
         return min(self.nsm, max(qr, jac, gj))

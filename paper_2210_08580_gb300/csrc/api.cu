@@ -142,6 +142,7 @@ bem_status bem_create(bem_handle* out, int device, void* cuda_stream, const bem_
 static void free_stage_buffers(bem_ctx* h, int from_stage) {
     if (from_stage <= 1) {
         free_ptr((void**)&h->S); free_ptr((void**)&h->W); free_ptr((void**)&h->D);
+        free_ptr((void**)&h->rexp); h->rexp_valid = false;
         free_ptr((void**)&h->seg);
         tc_release_operands(h);
     }

@@ -13,6 +13,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -305,6 +306,9 @@ struct AsmParams {
     const float4* btabf;  // its J0, Y0 part as double-float pairs
     unsigned long long* qpts;   // Gauss points of separated pairs (accumulated)
     const cplx* near;     // self / adjacent pair table (k_near_pairs)
+    int* rexpS;           // if set: atomic max of the exponent fields per column of S, W
+    int* rexpW;           //   (W's entries with cyclic |i - j| <= wband left out)
+    int wband;
     SeriesCoef sc;
 };
 
@@ -644,6 +648,8 @@ __device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, 
     }
 }
 
+__device__ __forceinline__ int exp_field_of(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
+
 // S and N tiles with double-float far pairs.  Same decomposition as k_assemble below: one
 // CTA per T x T vertex tile of the upper triangle, (T+1)^2 segment pairs staged in shared
 // memory, entries combined and written with their mirror.  Segment positions are kept as
@@ -728,38 +734,85 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     }
     for (int o = 16; o > 0; o >>= 1) npts += __shfl_xor_sync(0xffffffffu, npts, o);
     if ((threadIdx.x & 31) == 0 && npts) atomicAdd(p.qpts, (unsigned long long)npts);
-    __syncthreads();
     const bool mirror = (ti != tj);
-    for (int pass = 0; pass < (mirror ? 2 : 1); ++pass) {
-        for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-            int il, jl;
-            if (pass == 0) { il = idx % T; jl = idx / T; } else { jl = idx % T; il = idx / T; }
-            const int i = i0 + il, j = j0 + jl;
-            if (i >= N || j >= N) continue;
-            cdfl sv = cdfl_zero(), wv = cdfl_zero();
+    // entry (i0 + il, j0 + jl) of S and N, written at (i, j), or at (j, i) for the mirror
+    auto entry = [&](int il, int jl, bool transposed, double2& ds, double2& dw) -> bool {
+        const int i = i0 + il, j = j0 + jl;
+        if (i >= N || j >= N) return false;
+        cdfl sv = cdfl_zero(), wv = cdfl_zero();
 #pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const int el = il + 1 - a;
+        for (int a = 0; a < 2; ++a) {
+            const int el = il + 1 - a;
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const int fl = jl + 1 - b;
-                    const int pi = el * TP + fl;
-                    const cdfl Iab = cdfl_unpack(sI[pi * 4 + a * 2 + b]);
-                    sv = cdfl_add(sv, Iab);
-                    if (p.W) {
-                        // sigma_a sigma_b sum I/(h_e h_f) - k^2 (nu_e . nu_f) I_ab
-                        cdfl M0 = cdfl_unpack(sM[pi]);
-                        if (a != b) M0 = {dfl_neg(M0.re), dfl_neg(M0.im)};
-                        const dfl nnd = dfl_neg(dfl_mk(sND[pi]));
-                        wv = cdfl_add(wv, cdfl_fma_real(nnd, Iab, M0));
-                    }
+            for (int b = 0; b < 2; ++b) {
+                const int fl = jl + 1 - b;
+                const int pi = el * TP + fl;
+                const cdfl Iab = cdfl_unpack(sI[pi * 4 + a * 2 + b]);
+                sv = cdfl_add(sv, Iab);
+                if (p.W) {
+                    // sigma_a sigma_b sum I/(h_e h_f) - k^2 (nu_e . nu_f) I_ab
+                    cdfl M0 = cdfl_unpack(sM[pi]);
+                    if (a != b) M0 = {dfl_neg(M0.re), dfl_neg(M0.im)};
+                    const dfl nnd = dfl_neg(dfl_mk(sND[pi]));
+                    wv = cdfl_add(wv, cdfl_fma_real(nnd, Iab, M0));
                 }
             }
-            const int64_t off = (pass == 0) ? ((int64_t)i + (int64_t)j * p.ld) : ((int64_t)j + (int64_t)i * p.ld);
-            if (p.S) p.S[off] = cdfl_to(sv);
-            if (p.W) p.W[off] = cdfl_to(wv);
+        }
+        const int64_t off = transposed ? ((int64_t)j + (int64_t)i * p.ld) : ((int64_t)i + (int64_t)j * p.ld);
+        ds = cdfl_to(sv);
+        dw = cdfl_to(wv);
+        if (p.S) p.S[off] = ds;
+        if (p.W) p.W[off] = dw;
+        return true;
+    };
+    // Direct half: one warp per tile column, lane = row.  When asked, the largest exponent
+    // fields of the written entries are gathered per column (a warp reduction) and, for the
+    // mirror, per row (the slices of the split products are scaled per column of S and N;
+    // N's band is left out).
+    const bool track = p.rexpS != nullptr;
+    __shared__ int eRow[2][32];
+    if (threadIdx.x < 64) eRow[threadIdx.x >> 5][threadIdx.x & 31] = 0;
+    __syncthreads();
+    {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        int rS = 0, rW = 0;
+        for (int jl = wid; jl < T; jl += nw) {
+            double2 ds, dw;
+            int fs = 0, fw = 0;
+            if (lane < T && entry(lane, jl, false, ds, dw) && track) {
+                int d = lane + i0 - (jl + j0); if (d < 0) d = -d;
+                fs = max(exp_field_of(ds.x), exp_field_of(ds.y));
+                fw = (min(d, N - d) <= p.wband) ? 0 : max(exp_field_of(dw.x), exp_field_of(dw.y));
+            }
+            if (track) {
+                const int cs = (int)__reduce_max_sync(0xffffffffu, (unsigned)fs);
+                const int cw = (int)__reduce_max_sync(0xffffffffu, (unsigned)fw);
+                if (lane == 0 && j0 + jl < N) {
+                    atomicMax(p.rexpS + j0 + jl, cs);
+                    atomicMax(p.rexpW + j0 + jl, cw);
+                }
+                rS = max(rS, fs);
+                rW = max(rW, fw);
+            }
+        }
+        if (track && mirror) {
+            atomicMax(&eRow[0][lane], rS);
+            atomicMax(&eRow[1][lane], rW);
         }
     }
+    if (track && mirror) {
+        __syncthreads();
+        if (threadIdx.x < 2 * T) {
+            const int m = threadIdx.x / T, l = threadIdx.x % T;
+            if (i0 + l < N) atomicMax((m ? p.rexpW : p.rexpS) + i0 + l, eRow[m][l]);
+        }
+    }
+    // mirror half
+    if (mirror)
+        for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+            double2 ds, dw;
+            entry(idx / T, idx % T, true, ds, dw);
+        }
 }
 
 template <int T, bool WD>
@@ -933,7 +986,18 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     }
     BEM_LAUNCH(h, "k_near_pairs");
     p.near = near;
+    p.rexpS = p.rexpW = nullptr;
+    p.wband = -1;
+    h->rexp_valid = false;
+    if (!(ops & BEM_OP_D) && h->opt.prec == BEM_MIXED_BF16) {
+        if (!h->rexp) BEM_CUDA(h, cudaMalloc((void**)&h->rexp, sizeof(int) * 2 * (size_t)h->N));
+        BEM_CUDA(h, cudaMemsetAsync(h->rexp, 0, sizeof(int) * 2 * (size_t)h->N, h->stream));
+        p.rexpS = h->rexp;
+        p.rexpW = h->rexp + h->N;
+        p.wband = (int)std::min<int64_t>(TC_W_BAND, (h->N - 1) / 2);
+    }
     st = (ops & BEM_OP_D) ? run_assemble<15, true>(h, p) : run_assemble_sn<31>(h, p);
+    if (st == BEM_OK && p.rexpS) h->rexp_valid = true;
     cudaFreeAsync(near, h->stream);
     return st;
 }

@@ -92,6 +92,9 @@ struct bem_ctx {
     unsigned ops = 0;
     double* seg = nullptr;            // 5*N: x0, y0, tx, ty, h (SoA)
     cplx *S = nullptr, *W = nullptr, *D = nullptr;
+    int* rexp = nullptr;              // 2N: largest IEEE exponent field per column of S, W (W
+                                      // without its near band), taken during the assembly
+    bool rexp_valid = false;          // rexp belongs to the S, W now held
 
     // filter
     int64_t n = 0, M = 0, ncols = 0;  // n modes requested, ncols Fourier columns kept

@@ -4,6 +4,9 @@
 #include "common.cuh"
 
 #define BEM_SERIES_MAX 24
+// Entries of N with cyclic |i - j| <= TC_W_BAND (capped at (N - 1)/2) are applied in
+// double-float next to the split-bf16 product of the rest
+#define TC_W_BAND 64
 
 // Small-argument expansions in r of the kernels (coefficients depend on k only):
 //   g2(r)                    = sum_m r^{2m} (A_m + B_m ln r)

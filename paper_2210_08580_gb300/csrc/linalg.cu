@@ -512,16 +512,18 @@ __global__ void __launch_bounds__(256) k_house_qr(cplx* X, int64_t N, int n, cpl
         for (int c = tid; c < n; c += blockDim.x) perm[c] = cmap[c];
 }
 
-static bem_status coop_launch(bem_ctx* h, const void* fn, int blocks_wanted, int threads, void** args, const char* what) {
+static bem_status coop_launch(bem_ctx* h, const void* fn, int blocks_wanted, int threads, void** args, const char* what,
+                              size_t smem = 0) {
     int dev = h->device, nsm = 0, per = 0;
     BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    BEM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0));
+    if (smem > 48 * 1024) BEM_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BEM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem));
     if (per < 1) return bem_fail(h, BEM_E_CUDA, std::string(what) + ": kernel cannot be resident");
     int G = blocks_wanted;
     if (G > nsm * per) G = nsm * per;
     if (G < 1) G = 1;
     BEM_CUDA(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), h->stream));
-    BEM_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(G), dim3(threads), args, 0, h->stream));
+    BEM_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(G), dim3(threads), args, smem, h->stream));
     BEM_LAUNCH(h, what);
     return BEM_OK;
 }
@@ -549,252 +551,352 @@ __global__ void k_to_dfl(float4* X, int64_t count) {
     X[i] = cdfl_pack({dfl_from(v.x), dfl_from(v.y)});
 }
 
-// Each thread owns up to QR_KC columns (lane + 32 k) over the rows of its row group, so a
-// row's loads for all its columns are independent and in flight together (the row loop
-// is bound by L2 latency otherwise); one cross-warp reduction per phase.  The cross-CTA
-// sums of the dots are split over the grid (a third barrier per column), since repeating
-// them in every CTA kept the FP64 pipe busy.  n <= 32 QR_KC.
+// ---- exact fixed-point sums for the cross-CTA reductions of the double-float QR ----
+// A float f = m 2^(e - 150) is added to an integer window whose least significant bit is
+// 2^eb, held in three signed 64-bit limbs: limb l carries bits [l QX_W, (l + 1) QX_W) of
+// the window (the top limb also the carries).  Each CTA adds its partials with integer
+// atomics, so the total is exact and the same in any order of arrival; bits below 2^eb are
+// dropped (the window spans 120 bits under the largest possible sum).
+#define QX_W 40
+__device__ __forceinline__ void qx_add(float f, int eb, long long L[3]) {
+    const unsigned b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 255u);
+    if (e == 0) return;
+    unsigned long long m = (b & 0x7FFFFFu) | 0x800000u;
+    int sh = e - 150 - eb;                       // window position of m's lowest bit
+    if (sh < 0) {
+        if (sh <= -24) return;
+        m >>= -sh;
+        sh = 0;
+    }
+    const bool neg = (b >> 31) != 0;
+    if (sh >= 2 * QX_W) {                        // top limb only (the window bounds sh)
+        const long long v = (long long)(m << min(sh - 2 * QX_W, 38));
+        L[2] += neg ? -v : v;
+        return;
+    }
+    const int k = sh >= QX_W ? 1 : 0, o = sh - k * QX_W;
+    const unsigned long long v = m << o;         // o < 40, m < 2^24
+    const long long lo = (long long)(v & ((1ull << QX_W) - 1)), hi = (long long)(v >> QX_W);
+    if (neg) { L[k] -= lo; L[k + 1] -= hi; } else { L[k] += lo; L[k + 1] += hi; }
+}
+__device__ __forceinline__ float pow2f(int e) {   // 2^e, 0 below the normal range
+    return (e < -126) ? 0.f : __uint_as_float((unsigned)(min(e, 127) + 127) << 23);
+}
+// limbs -> double-float (the two leading 24-bit pieces of the exact integer)
+__device__ __forceinline__ dfl qx_to_dfl(const unsigned long long* L, int eb) {
+    const __int128 v = (__int128)(long long)L[0] + (__int128)(long long)L[1] * ((__int128)1 << QX_W) +
+                       (__int128)(long long)L[2] * ((__int128)1 << (2 * QX_W));
+    if (v == 0) return {0.f, 0.f};
+    const bool neg = v < 0;
+    const unsigned __int128 M = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const unsigned long long h64 = (unsigned long long)(M >> 64), l64 = (unsigned long long)M;
+    const int t = h64 ? 127 - __clzll((long long)h64) : 63 - __clzll((long long)l64);
+    const unsigned __int128 Ms = (t >= 47) ? (M >> (t - 47)) : (M << (47 - t));
+    const unsigned m1 = (unsigned)(Ms >> 24) & 0xFFFFFFu, m2 = (unsigned)Ms & 0xFFFFFFu;
+    const int E = t + eb;
+    float hi = __uint2float_rn(m1) * pow2f(E - 23);
+    float lo = __uint2float_rn(m2) * pow2f(E - 47);
+    if (neg) { hi = -hi; lo = -lo; }
+    return dfl_qts(hi, lo);
+}
+
+// Pivoted Householder QR of X (N x n) in double-float with ONE grid barrier per column.
+// Rows are split over the CTAs; every CTA keeps the column permutation (cmap: position ->
+// column of X).  At the barrier of step j the exact sums over rows i >= j of
+//   d_c = conj(x_{i,p}) x_{i,c}  (p = cmap[j], the pivot)   and   n_c = |x_{i,c}|^2
+// are complete for every trailing column.  Each CTA then forms the reflector of the pivot
+// (alpha = -e^{i arg x_jp} sqrt(n_p), v = x_p - alpha e_j, tau = 1/(|alpha| (|alpha| +
+// |x_jp|))), w_c = tau (d_c - conj(alpha) x_jc), row j of R (R_jc = x_jc - v_j w_c), the
+// downdated norms n_c - |R_jc|^2 and from them the next pivot; then it updates its rows
+// (x_c -= v w_c) and, in the same pass, accumulates the sums of step j + 1 against the
+// updated next pivot column.  n <= 32 QR_KC.
 #define QR_KC 7
-__global__ void __launch_bounds__(256, 2) k_house_qr_df(float4* X, int64_t N, int n, cplx* R, int* perm, double* partC,
-                                                     unsigned long long* cnq, cplx* partW, float4* wdf, unsigned* bar,
-                                                     int* err) {
-    __shared__ double red[32];
-    __shared__ float4 wbuf[8][32 * QR_KC];      // per row group partials (dots; norms use .x/.y)
-    __shared__ float4 wsm[32 * QR_KC];
-    __shared__ int cmap[32 * QR_KC];
-    __shared__ double qscale_s, tau_s;
-    __shared__ float4 vj_s;
-    __shared__ unsigned long long pbest[8];
-    __shared__ int pidx[8];
+#define QR_NP (32 * QR_KC)
+__global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, int n, cplx* R, int* perm,
+                                                     unsigned long long* lim, int* emax, unsigned* bar, int* err) {
+    extern __shared__ float4 qsm[];
+    float4* wbD = qsm;                                    // [8][QR_NP] per-warp dot partials
+    float2* wbN = reinterpret_cast<float2*>(wbD + 8 * QR_NP);   // [8][QR_NP] norm partials
+    float4* sRow = reinterpret_cast<float4*>(wbN + 8 * QR_NP);  // [QR_NP] row j (by position)
+    float4* sW = sRow + QR_NP;                            // [QR_NP] w by position
+    float4* sD = sW + QR_NP;                              // [QR_NP] d by position
+    float2* sN = reinterpret_cast<float2*>(sD + QR_NP);  // [QR_NP] n by position
+    __shared__ int cmap[QR_NP];
+    __shared__ float4 s_ref[2];                           // alpha, v_j
+    __shared__ float2 s_tau;
+    __shared__ float2 s_best[8];
+    __shared__ int s_bidx[8];
+    __shared__ int s_eb;
     const unsigned G = gridDim.x;
     const int64_t rb = (N + G - 1) / G;
     const int64_t r0 = (int64_t)blockIdx.x * rb, r1 = min(N, r0 + rb);
     const int tid = threadIdx.x, rg = tid >> 5, lane = tid & 31;
+    const size_t LS = (size_t)n * 9;                      // limbs per buffer: 9 per column
     for (int c = tid; c < n; c += blockDim.x) cmap[c] = c;
     __syncthreads();
-    // partial column norms over my rows
-    {
-        dfl acc[QR_KC];
-#pragma unroll
-        for (int k = 0; k < QR_KC; ++k) acc[k] = {0.f, 0.f};
-        for (int64_t i = r0 + rg; i < r1; i += 8) {
-#pragma unroll
-            for (int k = 0; k < QR_KC; ++k) {
-                const int c = lane + 32 * k;
-                if (c < n) acc[k] = dfl_norm_acc(cdfl_ld(X + i * n + c), acc[k]);
+
+    // per-warp partials -> per-position sums over the CTA (df), into wbD[0] / wbN[0]
+    auto reduce_warps = [&](int cnt) {
+        __syncthreads();
+        for (int l = tid; l < cnt; l += blockDim.x) {
+            cdfl d = cdfl_unpack(wbD[l]);
+            dfl nn = dfl_mk(wbN[l]);
+            for (int q = 1; q < 8; ++q) {
+                d = cdfl_add(d, cdfl_unpack(wbD[q * QR_NP + l]));
+                nn = dfl_add(nn, dfl_mk(wbN[q * QR_NP + l]));
             }
+            wbD[l] = cdfl_pack(d);
+            wbN[l] = make_float2(nn.hi, nn.lo);
         }
+        __syncthreads();
+    };
+    // adds the CTA's sums for positions c0 + l (l < cnt) to buffer buf (exact, integer atomics)
+    auto publish = [&](int c0, int cnt, int buf, int eb) {
+        for (int l = tid; l < cnt; l += blockDim.x) {
+            const float4 d = wbD[l];
+            const float2 nn = wbN[l];
+            long long L[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            qx_add(d.x, eb, L); qx_add(d.y, eb, L);
+            qx_add(d.z, eb, L + 3); qx_add(d.w, eb, L + 3);
+            qx_add(nn.x, eb, L + 6); qx_add(nn.y, eb, L + 6);
+            unsigned long long* dst = lim + (size_t)buf * LS + (size_t)cmap[c0 + l] * 9;
 #pragma unroll
-        for (int k = 0; k < QR_KC; ++k) wbuf[rg][lane + 32 * k] = make_float4(acc[k].hi, acc[k].lo, 0.f, 0.f);
-        __syncthreads();
-        for (int c = tid; c < n; c += blockDim.x) {
-            dfl t = {wbuf[0][c].x, wbuf[0][c].y};
-            for (int q = 1; q < 8; ++q) t = dfl_add(t, dfl{wbuf[q][c].x, wbuf[q][c].y});
-            partC[(int64_t)blockIdx.x * n + c] = dfl_to(t);
+            for (int u = 0; u < 9; ++u)
+                if (L[u]) atomicAdd(dst + u, (unsigned long long)L[u]);
         }
-    }
-    if (!grid_barrier(bar, G, err)) return;
-    {
-        double mx = 0.0;
-        for (int c = tid; c < n; c += blockDim.x) {
-            double t = 0.0;
-            for (unsigned q = 0; q < G; ++q) t += partC[(int64_t)q * n + c];
-            mx = fmax(mx, t);
-        }
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) red[rg] = mx;
-        __syncthreads();
-        if (tid == 0) {
-            double m2 = 0.0;
-            for (int q = 0; q < 8; ++q) m2 = fmax(m2, red[q]);
-            qscale_s = (m2 > 0.0) ? 4.0e18 / m2 : 0.0;
-        }
-        __syncthreads();
-        for (int c = tid; c < n; c += blockDim.x)
-            atomicAdd(cnq + c, __double2ull_rz(partC[(int64_t)blockIdx.x * n + c] * qscale_s));
-    }
-    const double qscale = qscale_s;
-    for (int j = 0; j < n; ++j) {
-        if (!grid_barrier(bar, G, err)) return;
-        // (1) pivot
-        const unsigned long long* cq = cnq + (size_t)(j & 1) * n;
-        unsigned long long best = 0ull;
-        int bi = n;
-        for (int c = j + tid; c < n; c += blockDim.x) {
-            const unsigned long long v = __ldcg(cq + cmap[c]);
-            if (bi == n || v > best) { best = v; bi = c; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (oi < n && (bi == n || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
-        }
-        if (lane == 0) { pbest[rg] = best; pidx[rg] = bi; }
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long b2 = pbest[0];
-            int i2 = pidx[0];
-            for (int q = 1; q < 8; ++q)
-                if (pidx[q] < n && (i2 == n || pbest[q] > b2 || (pbest[q] == b2 && pidx[q] < i2))) {
-                    b2 = pbest[q]; i2 = pidx[q];
-                }
-            if (i2 > j && i2 < n) { const int t = cmap[j]; cmap[j] = cmap[i2]; cmap[i2] = t; }
-        }
-        if (blockIdx.x == 0)
-            for (int c = tid; c < n; c += blockDim.x) cnq[(size_t)((j + 1) & 1) * n + c] = 0ull;
-        __syncthreads();
-        const int pj = cmap[j];
-        double nrm2 = 0.0;
-        for (unsigned q = tid; q < G; q += blockDim.x) nrm2 += partC[(int64_t)q * n + pj];
-        nrm2 = block_sum(nrm2, red);
-        // (2) reflector, formed once
-        if (tid == 0) {
-            const cdfl xd = cdfl_ld(X + (int64_t)j * n + pj);
-            const cplx xjj = cmk(dfl_to(xd.re), dfl_to(xd.im));
-            double tau = 0.0;
-            cplx alpha = cmk(0, 0), vj = cmk(0, 0);
-            if (nrm2 > 0.0) {
-                const double a = sqrt(nrm2), ax = sqrt(cabs2(xjj));
-                const cplx ph = (ax > 0.0) ? cmk(xjj.x / ax, xjj.y / ax) : cmk(1, 0);
-                alpha = cmk(-ph.x * a, -ph.y * a);
-                vj = csub(xjj, alpha);
-                const double vn2 = nrm2 - ax * ax + cabs2(vj);
-                tau = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
-            }
-            tau_s = tau;
-            vj_s = cdfl_pack({dfl_from(vj.x), dfl_from(vj.y)});
-            if (j >= r0 && j < r1) R[j + (int64_t)j * n] = (nrm2 > 0.0) ? alpha : cmk(0, 0);
-        }
-        __syncthreads();
-        const double tau = tau_s;
-        const cdfl vjd = cdfl_unpack(vj_s);
+    };
+    // one pass over this CTA's rows i >= jp1: optionally x_c -= v_i w_c for the positions
+    // c >= jp1 (v_i = X[i, pj]), then partial sums of conj(x_{i,cmap[jp1]}) x_{i,c} and
+    // |x_{i,c}|^2 with the updated values; leaves the CTA's sums in wbD[0], wbN[0]
+    auto pass = [&](int jp1, bool upd, int pj) {
         int pcs[QR_KC];
+        cdfl w[QR_KC];
 #pragma unroll
         for (int k = 0; k < QR_KC; ++k) {
-            const int c = j + 1 + lane + 32 * k;
+            const int c = jp1 + lane + 32 * k;
             pcs[k] = (c < n) ? cmap[c] : -1;
+            w[k] = (upd && c < n) ? cdfl_unpack(sW[c]) : cdfl_zero();
         }
-        // (3) partial dots w_c = sum_i conj(v_i) X[i, c], c > j
-        {
-            cdfl acc[QR_KC];
+        cdfl accD[QR_KC];
+        dfl accN[QR_KC];
 #pragma unroll
-            for (int k = 0; k < QR_KC; ++k) acc[k] = cdfl_zero();
-            if (tau != 0.0) {
-                // two rows per pass: all their loads are issued before the arithmetic
-                int64_t i = max(r0, (int64_t)j) + rg;
-                for (; i + 8 < r1; i += 16) {
-                    const cdfl va = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
-                    const cdfl vb = cdfl_ld(X + (i + 8) * n + pj);
-                    cdfl xa[QR_KC], xb[QR_KC];
-#pragma unroll
-                    for (int k = 0; k < QR_KC; ++k) {
-                        xa[k] = (pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
-                        xb[k] = (pcs[k] >= 0) ? cdfl_ld(X + (i + 8) * n + pcs[k]) : cdfl_zero();
-                    }
-#pragma unroll
-                    for (int k = 0; k < QR_KC; ++k) {
-                        cdfl_conj_fma(acc[k], va, xa[k]);
-                        cdfl_conj_fma(acc[k], vb, xb[k]);
-                    }
-                }
-                if (i < r1) {
-                    const cdfl vi = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
-#pragma unroll
-                    for (int k = 0; k < QR_KC; ++k)
-                        if (pcs[k] >= 0) cdfl_conj_fma(acc[k], vi, cdfl_ld(X + i * n + pcs[k]));
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < QR_KC; ++k) wbuf[rg][lane + 32 * k] = cdfl_pack(acc[k]);
-            __syncthreads();
-            for (int c = j + 1 + tid; c < n; c += blockDim.x) {
-                const int l = c - j - 1;
-                cdfl t = cdfl_unpack(wbuf[0][l]);
-                for (int q = 1; q < 8; ++q) t = cdfl_add(t, cdfl_unpack(wbuf[q][l]));
-                partW[(int64_t)blockIdx.x * n + c] = cmk(dfl_to(t.re), dfl_to(t.im));
-            }
-        }
-        if (!grid_barrier(bar, G, err)) return;
-        // (3b) each CTA sums the partials of a few columns (the FP64 sums are spread over the
-        // grid instead of repeated in every CTA); -tau w is published in double-float
-        for (int c = j + 1 + (int)blockIdx.x; c < n; c += G) {
-            double re = 0.0, im = 0.0;
-            for (unsigned q = tid; q < G; q += blockDim.x) {
-                const cplx v = __ldcg(partW + (int64_t)q * n + c);
-                re += v.x;
-                im += v.y;
-            }
-            re = block_sum(re, red);
-            im = block_sum(im, red);
-            if (tid == 0) wdf[c] = cdfl_pack({dfl_from(-tau * re), dfl_from(-tau * im)});
-        }
-        if (!grid_barrier(bar, G, err)) return;
-        // (4) update my rows (x <- x + v (-tau w)) and accumulate their trailing norms
-        for (int c = j + 1 + tid; c < n; c += blockDim.x) wsm[c - j - 1] = __ldcg(wdf + c);
-        __syncthreads();
-        {
-            cdfl nw[QR_KC];
-            dfl acc[QR_KC];
-#pragma unroll
-            for (int k = 0; k < QR_KC; ++k) {
-                nw[k] = (pcs[k] >= 0) ? cdfl_unpack(wsm[lane + 32 * k]) : cdfl_zero();
-                acc[k] = {0.f, 0.f};
-            }
-            auto upd = [&](int64_t i, const cdfl& vi, cdfl* xr) {
+        for (int k = 0; k < QR_KC; ++k) { accD[k] = cdfl_zero(); accN[k] = {0.f, 0.f}; }
+        auto row = [&](int64_t i, const cdfl& vi, cdfl* x) {
+            if (upd) {
 #pragma unroll
                 for (int k = 0; k < QR_KC; ++k) {
                     if (pcs[k] < 0) continue;
-                    cdfl x = xr[k];
-                    if (tau != 0.0) {
-                        x.re = dfl_fma(vi.re, nw[k].re, dfl_fma(dfl_neg(vi.im), nw[k].im, x.re));
-                        x.im = dfl_fma(vi.re, nw[k].im, dfl_fma(vi.im, nw[k].re, x.im));
-                        X[i * n + pcs[k]] = cdfl_pack(x);
-                    }
-                    if (i > j) acc[k] = dfl_norm_acc(x, acc[k]);
+                    x[k].re = dfl_fma(dfl_neg(vi.re), w[k].re, dfl_fma(vi.im, w[k].im, x[k].re));
+                    x[k].im = dfl_fma(dfl_neg(vi.re), w[k].im, dfl_fma(dfl_neg(vi.im), w[k].re, x[k].im));
+                    X[i * n + pcs[k]] = cdfl_pack(x[k]);
                 }
-            };
-            // two rows per pass: both rows' loads precede the first store
-            int64_t i = max(r0, (int64_t)j) + rg;
-            for (; i + 8 < r1; i += 16) {
-                const cdfl va = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
-                const cdfl vb = cdfl_ld(X + (i + 8) * n + pj);
-                cdfl xa[QR_KC], xb[QR_KC];
+            }
+            // the next pivot column's new value (position jp1 = lane 0, slot 0)
+            const cdfl p = {{__shfl_sync(0xffffffffu, x[0].re.hi, 0), __shfl_sync(0xffffffffu, x[0].re.lo, 0)},
+                            {__shfl_sync(0xffffffffu, x[0].im.hi, 0), __shfl_sync(0xffffffffu, x[0].im.lo, 0)}};
 #pragma unroll
-                for (int k = 0; k < QR_KC; ++k) {
-                    xa[k] = (pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
-                    xb[k] = (pcs[k] >= 0) ? cdfl_ld(X + (i + 8) * n + pcs[k]) : cdfl_zero();
+            for (int k = 0; k < QR_KC; ++k) {
+                if (pcs[k] < 0) continue;
+                cdfl_conj_fma(accD[k], p, x[k]);
+                accN[k] = dfl_norm_acc(x[k], accN[k]);
+            }
+        };
+        int64_t i = max(r0, (int64_t)jp1) + rg;
+        for (; i + 8 < r1; i += 16) {
+            cdfl va = cdfl_zero(), vb = cdfl_zero();
+            if (upd) { va = cdfl_ld(X + i * n + pj); vb = cdfl_ld(X + (i + 8) * n + pj); }
+            cdfl xa[QR_KC], xb[QR_KC];
+#pragma unroll
+            for (int k = 0; k < QR_KC; ++k) {
+                xa[k] = (pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
+                xb[k] = (pcs[k] >= 0) ? cdfl_ld(X + (i + 8) * n + pcs[k]) : cdfl_zero();
+            }
+            row(i, va, xa);
+            row(i + 8, vb, xb);
+        }
+        if (i < r1) {
+            const cdfl vi = upd ? cdfl_ld(X + i * n + pj) : cdfl_zero();
+            cdfl xr[QR_KC];
+#pragma unroll
+            for (int k = 0; k < QR_KC; ++k) xr[k] = (pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
+            row(i, vi, xr);
+        }
+#pragma unroll
+        for (int k = 0; k < QR_KC; ++k) {
+            wbD[rg * QR_NP + lane + 32 * k] = cdfl_pack(accD[k]);
+            wbN[rg * QR_NP + lane + 32 * k] = make_float2(accN[k].hi, accN[k].lo);
+        }
+        reduce_warps(n - jp1);
+    };
+    // argmax over positions [c0, n) of the df values in sN (ties: lowest position)
+    auto pick = [&](int c0) -> int {
+        float2 best = make_float2(-1.f, 0.f);
+        int bi = n;
+        for (int c = c0 + tid; c < n; c += blockDim.x) {
+            const float2 v = sN[c];
+            if (bi == n || v.x > best.x || (v.x == best.x && v.y > best.y)) { best = v; bi = c; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ox = __shfl_xor_sync(0xffffffffu, best.x, o), oy = __shfl_xor_sync(0xffffffffu, best.y, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            const bool better = oi < n && (bi == n || ox > best.x || (ox == best.x && (oy > best.y || (oy == best.y && oi < bi))));
+            if (better) { best = make_float2(ox, oy); bi = oi; }
+        }
+        if (lane == 0) { s_best[rg] = best; s_bidx[rg] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            float2 b2 = s_best[0];
+            int i2 = s_bidx[0];
+            for (int q = 1; q < 8; ++q) {
+                const float2 v = s_best[q];
+                const int qi = s_bidx[q];
+                if (qi < n && (i2 == n || v.x > b2.x || (v.x == b2.x && (v.y > b2.y || (v.y == b2.y && qi < i2))))) {
+                    b2 = v; i2 = qi;
                 }
-                upd(i, va, xa);
-                upd(i + 8, vb, xb);
             }
-            if (i < r1) {
-                const cdfl vi = (i == j) ? vjd : cdfl_ld(X + i * n + pj);
-                cdfl xr[QR_KC];
+            s_bidx[0] = i2;
+        }
+        __syncthreads();
+        return s_bidx[0];
+    };
+
+    // ---- start: window exponent from the largest partial column norm, then the norms,
+    // the first pivot and the sums of step 0
+    {
+        int pcs[QR_KC];
+        dfl acc[QR_KC];
 #pragma unroll
-                for (int k = 0; k < QR_KC; ++k) xr[k] = (pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
-                upd(i, vi, xr);
+        for (int k = 0; k < QR_KC; ++k) { pcs[k] = (lane + 32 * k < n) ? lane + 32 * k : -1; acc[k] = {0.f, 0.f}; }
+        for (int64_t i = r0 + rg; i < r1; i += 8) {
+#pragma unroll
+            for (int k = 0; k < QR_KC; ++k)
+                if (pcs[k] >= 0) acc[k] = dfl_norm_acc(cdfl_ld(X + i * n + pcs[k]), acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < QR_KC; ++k) {
+            wbD[rg * QR_NP + lane + 32 * k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            wbN[rg * QR_NP + lane + 32 * k] = make_float2(acc[k].hi, acc[k].lo);
+        }
+        reduce_warps(n);
+        int mx = 0;
+        for (int c = tid; c < n; c += blockDim.x) mx = max(mx, (int)((__float_as_uint(wbN[c].x) >> 23) & 255u));
+        mx = __reduce_max_sync(0xffffffffu, (unsigned)mx);
+        if (lane == 0 && mx) atomicMax(emax, mx);
+    }
+    if (!grid_barrier(bar, G, err)) return;
+    if (tid == 0) {
+        // every partial is below 2^(F + 1), F = the largest biased field - 127; sums of up
+        // to 2^11 of them stay below 2^(F + 12), the top of the window
+        const int F = __ldcg(emax) - 127;
+        s_eb = F + 12 - 3 * QX_W;
+    }
+    __syncthreads();
+    const int eb = s_eb;
+    publish(0, n, 2, eb);                                 // norms -> buffer 2 (dots there are 0)
+    if (!grid_barrier(bar, G, err)) return;
+    for (int c = tid; c < n; c += blockDim.x) {
+        unsigned long long Lv[3];
+        const unsigned long long* src = lim + 2 * LS + (size_t)c * 9 + 6;
+        for (int u = 0; u < 3; ++u) Lv[u] = __ldcg(src + u);
+        const dfl v = qx_to_dfl(Lv, eb);
+        sN[c] = make_float2(v.hi, v.lo);
+    }
+    __syncthreads();
+    {
+        const int q = pick(0);
+        if (tid == 0 && q < n && q != 0) { const int t = cmap[0]; cmap[0] = cmap[q]; cmap[q] = t; }
+        __syncthreads();
+    }
+    pass(0, false, 0);
+    publish(0, n, 0, eb);
+    if (!grid_barrier(bar, G, err)) return;
+
+    for (int j = 0; j < n; ++j) {
+        const int buf = j % 3;
+        // (A) the sums of step j and row j, by position
+        for (int c = j + tid; c < n; c += blockDim.x) {
+            const int pc = cmap[c];
+            const unsigned long long* src = lim + (size_t)buf * LS + (size_t)pc * 9;
+            unsigned long long Lv[9];
+#pragma unroll
+            for (int u = 0; u < 9; ++u) Lv[u] = __ldcg(src + u);
+            const dfl dr = qx_to_dfl(Lv, eb), di = qx_to_dfl(Lv + 3, eb), nn = qx_to_dfl(Lv + 6, eb);
+            sD[c] = cdfl_pack({dr, di});
+            sN[c] = make_float2(nn.hi, nn.lo);
+            sRow[c] = __ldcg(X + (int64_t)j * n + pc);
+        }
+        if (blockIdx.x == 0) {
+            unsigned long long* z = lim + (size_t)((j + 2) % 3) * LS;
+            for (size_t u = tid; u < LS; u += blockDim.x) z[u] = 0ull;
+        }
+        __syncthreads();
+        // (B) reflector of the pivot column (one thread, double-float)
+        const bool own_j = (j >= r0 && j < r1);
+        if (tid == 0) {
+            const dfl nrm2 = dfl_mk(sN[j]);
+            const cdfl xjj = cdfl_unpack(sRow[j]);
+            cdfl alpha = cdfl_zero(), vj = cdfl_zero();
+            dfl tau = {0.f, 0.f};
+            if (nrm2.hi > 0.f) {
+                const dfl a = dfl_sqrt(nrm2);
+                const dfl ax2 = dfl_fma(xjj.re, xjj.re, dfl_mul(xjj.im, xjj.im));
+                cdfl ph = {{1.f, 0.f}, {0.f, 0.f}};
+                dfl ax = {0.f, 0.f};
+                if (ax2.hi > 0.f) {
+                    ax = dfl_sqrt(ax2);
+                    const dfl rax = dfl_div(dfl{1.f, 0.f}, ax);
+                    ph = {dfl_mul(xjj.re, rax), dfl_mul(xjj.im, rax)};
+                }
+                const dfl apx = dfl_add(a, ax);
+                alpha = {dfl_neg(dfl_mul(ph.re, a)), dfl_neg(dfl_mul(ph.im, a))};
+                vj = {dfl_mul(ph.re, apx), dfl_mul(ph.im, apx)};
+                tau = dfl_div(dfl{1.f, 0.f}, dfl_mul(a, apx));
             }
-            __syncthreads();                      // wbuf reuse (the dots were reduced above)
-#pragma unroll
-            for (int k = 0; k < QR_KC; ++k) wbuf[rg][lane + 32 * k] = make_float4(acc[k].hi, acc[k].lo, 0.f, 0.f);
-            __syncthreads();
+            s_ref[0] = cdfl_pack(alpha);
+            s_ref[1] = cdfl_pack(vj);
+            s_tau = make_float2(tau.hi, tau.lo);
+            if (own_j) R[j + (int64_t)j * n] = cdfl_to(alpha);
+        }
+        __syncthreads();
+        const int pj = cmap[j];
+        {
+            // (C) w, row j of R, downdated norms
+            const cdfl alpha = cdfl_unpack(s_ref[0]), vj = cdfl_unpack(s_ref[1]);
+            const dfl tau = dfl_mk(s_tau);
             for (int c = j + 1 + tid; c < n; c += blockDim.x) {
-                const int l = c - j - 1;
-                dfl t = {wbuf[0][l].x, wbuf[0][l].y};
-                for (int q = 1; q < 8; ++q) t = dfl_add(t, dfl{wbuf[q][l].x, wbuf[q][l].y});
-                const double td = dfl_to(t);
-                partC[(int64_t)blockIdx.x * n + cmap[c]] = td;
-                atomicAdd(cnq + (size_t)((j + 1) & 1) * n + cmap[c], __double2ull_rz(td * qscale));
+                const cdfl d = cdfl_unpack(sD[c]), x = cdfl_unpack(sRow[c]);
+                // d - conj(alpha) x
+                const dfl tr = dfl_sub(d.re, dfl_fma(alpha.re, x.re, dfl_mul(alpha.im, x.im)));
+                const dfl ti = dfl_sub(d.im, dfl_fma(alpha.re, x.im, dfl_neg(dfl_mul(alpha.im, x.re))));
+                const cdfl wc = {dfl_mul(tau, tr), dfl_mul(tau, ti)};
+                sW[c] = cdfl_pack(wc);
+                // R_jc = x - vj wc
+                const dfl rr = dfl_sub(x.re, dfl_fma(vj.re, wc.re, dfl_neg(dfl_mul(vj.im, wc.im))));
+                const dfl ri = dfl_sub(x.im, dfl_fma(vj.re, wc.im, dfl_mul(vj.im, wc.re)));
+                if (own_j) R[j + (int64_t)c * n] = cmk(dfl_to(rr), dfl_to(ri));
+                dfl nd = dfl_sub(dfl_mk(sN[c]), dfl_fma(rr, rr, dfl_mul(ri, ri)));
+                if (nd.hi < 0.f) nd = {0.f, 0.f};
+                sN[c] = make_float2(nd.hi, nd.lo);
+            }
+            __syncthreads();
+            if (j + 1 < n) {
+                const int q = pick(j + 1);
+                if (tid == 0 && q < n && q != j + 1) { const int t = cmap[j + 1]; cmap[j + 1] = cmap[q]; cmap[q] = t; }
+                __syncthreads();
             }
         }
+        if (j + 1 >= n) break;
+        // (D) update this CTA's rows and accumulate the sums of step j + 1
+        if (max(r0, (int64_t)(j + 1)) < r1) {
+            pass(j + 1, true, pj);
+            publish(j + 1, n - j - 1, (j + 1) % 3, eb);
+        }
+        if (!grid_barrier(bar, G, err)) return;
     }
+    // lower triangle of R (rows owned here)
     for (int64_t j = max(r0, (int64_t)0); j < min(r1, (int64_t)n); ++j)
-        for (int c = tid; c < n; c += blockDim.x)
-            if (c != j) {
-                cplx v = cmk(0, 0);
-                if (c > j) { const cdfl x = cdfl_ld(X + j * n + cmap[c]); v = cmk(dfl_to(x.re), dfl_to(x.im)); }
-                R[j + (int64_t)c * n] = v;
-            }
+        for (int c = tid; c < j; c += blockDim.x) R[j + (int64_t)c * n] = cmk(0, 0);
     if (blockIdx.x == 0)
         for (int c = tid; c < n; c += blockDim.x) perm[c] = cmap[c];
 }
@@ -804,10 +906,27 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* 
     if (N < n) return bem_fail(h, BEM_E_INVALID, "QR: fewer rows than columns");
     int nsm = 0;
     BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    // two CTAs per SM for the double-float kernel (its row loops are latency-bound)
-    const bool use_df = dfl_arith && n <= 32 * QR_KC;
-    int G = (int)std::min<int64_t>((use_df ? 2 : 1) * nsm, (N + 15) / 16);
+    const bool use_df = dfl_arith && n <= QR_NP;
+    const int G = (int)std::min<int64_t>(nsm, (N + 15) / 16);
     bem_status st;
+    if (use_df) {
+        // X in place as double-float pairs (same 16 bytes per entry); three limb buffers
+        // of 9 words per column and the window exponent, all starting at zero
+        unsigned long long* lim = nullptr;
+        const size_t lim_words = (size_t)3 * 9 * n + 1;
+        BEM_CUDA(h, cudaMallocAsync((void**)&lim, sizeof(unsigned long long) * lim_words, h->stream));
+        BEM_CUDA(h, cudaMemsetAsync(lim, 0, sizeof(unsigned long long) * lim_words, h->stream));
+        int* emax = reinterpret_cast<int*>(lim + 27 * (size_t)n);
+        const int64_t cnt = N * (int64_t)n;
+        BEM_TIMED(h, "k_to_dfl", (k_to_dfl<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(reinterpret_cast<float4*>(X), cnt)));
+        BEM_LAUNCH(h, "k_to_dfl");
+        float4* Xf = reinterpret_cast<float4*>(X);
+        void* args_df[] = {&Xf, &N, &n, &R, &perm, &lim, &emax, &h->bar, &h->dev_err};
+        const size_t smem = (size_t)QR_NP * (8 * sizeof(float4) + 8 * sizeof(float2) + 3 * sizeof(float4) + sizeof(float2));
+        BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr_df, G, 256, args_df, "k_house_qr_df", smem));
+        cudaFreeAsync(lim, h->stream);
+        return st;
+    }
     double* partC = nullptr;
     cplx* partW = nullptr;
     unsigned long long* cnq = nullptr;
@@ -815,22 +934,10 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* 
     BEM_CUDA(h, cudaMallocAsync((void**)&cnq, sizeof(unsigned long long) * 2 * (size_t)n, h->stream));
     BEM_CUDA(h, cudaMemsetAsync(cnq, 0, sizeof(unsigned long long) * 2 * (size_t)n, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&partW, sizeof(cplx) * (size_t)G * n, h->stream));
-    float4* wdf = nullptr;
-    BEM_CUDA(h, cudaMallocAsync((void**)&wdf, sizeof(float4) * (size_t)n, h->stream));
     void* args[] = {&X, &N, &n, &R, &perm, &partC, &cnq, &partW, &h->bar, &h->dev_err};
-    void* args_df[] = {&X, &N, &n, &R, &perm, &partC, &cnq, &partW, &wdf, &h->bar, &h->dev_err};
-    if (use_df) {
-        // X in place as double-float pairs (same 16 bytes per entry)
-        const int64_t cnt = N * (int64_t)n;
-        BEM_TIMED(h, "k_to_dfl", (k_to_dfl<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(reinterpret_cast<float4*>(X), cnt)));
-        BEM_LAUNCH(h, "k_to_dfl");
-        BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr_df, G, 256, args_df, "k_house_qr_df"));
-    } else {
-        BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr, G, 256, args, "k_house_qr"));
-    }
+    BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr, G, 256, args, "k_house_qr"));
     cudaFreeAsync(partC, h->stream);
     cudaFreeAsync(cnq, h->stream);
-    cudaFreeAsync(wdf, h->stream);
     cudaFreeAsync(partW, h->stream);
     return st;
 }

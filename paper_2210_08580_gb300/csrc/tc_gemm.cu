@@ -47,7 +47,6 @@
 #define TC_SPLIT_TARGET 152         // CTAs to aim for when splitting K' (one per SM)
 #define TC_NACC 4                   // TMEM accumulators (4 x 128 columns = all 512)
 #define TC_SMAX 7
-#define TC_W_BAND 64                // |i - j| (cyclic) <= band of N applied in FP64
 #define TC_TILE_BYTES (TC_BM * TC_BK * 2)          // 8 KiB per slice tile (A and B alike)
 #define TC_STASH_BYTES (TC_BM * (TC_BN + 1) * 8)   // epilogue staging of (hi, lo) pairs
 #define TC_THREADS 320             // 10 warps: TMA, MMA, 8 epilogue
@@ -378,6 +377,15 @@ __global__ void k_exp_rows(const void* src, int is_real, int64_t M, int64_t K, i
     if ((threadIdx.x & 31) == 0) e[i] = mx ? mx - 1022 : 0;
 }
 
+// Row exponents from the exponent fields gathered during the assembly (the values
+// k_exp_rows gives for those entries)
+__global__ void k_exp_from_fields(const int* fields, int64_t M, int* e) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int mx = fields[i];
+    e[i] = mx ? mx - 1022 : 0;
+}
+
 // B column exponents: B_op[k, j] = src[k*sb_k + j*sb_j] (complex, or real when is_real);
 // columns 2j and 2j+1 of B' share f_j.
 __global__ void k_exp_cols(const void* src, int is_real, int64_t K, int64_t m, int64_t sb_k, int64_t sb_j, int* f) {
@@ -594,13 +602,17 @@ static bem_status reserve(bem_ctx* h, TcOperand& op, int64_t rows, int64_t Kp, i
 // A operand: rows M, K complex columns, A_op[i,k] = src[i*sa_i + k*sa_k]; band >= 0 drops
 // the cyclic band |i - k| <= band (square operators)
 static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k,
-                          int band = -1, int is_real = 0, int conj = 0) {
+                          int band = -1, int is_real = 0, int conj = 0, const int* fields = nullptr) {
     const int S = tcs(h)->S;
     const int64_t Kp = pad64(2 * K);
     bem_status st = reserve(h, op, M, Kp, S);
     if (st != BEM_OK) return st;
     op.K = K;
-    BEM_TIMED(h, "k_exp_rows", (k_exp_rows<<<(unsigned)((M + 7) / 8), 256, 0, h->stream>>>(src, is_real, M, K, sa_i, sa_k, band, op.exps)));
+    if (fields) {
+        BEM_TIMED(h, "k_exp_rows", (k_exp_from_fields<<<(unsigned)((M + 255) / 256), 256, 0, h->stream>>>(fields, M, op.exps)));
+    } else {
+        BEM_TIMED(h, "k_exp_rows", (k_exp_rows<<<(unsigned)((M + 7) / 8), 256, 0, h->stream>>>(src, is_real, M, K, sa_i, sa_k, band, op.exps)));
+    }
     BEM_LAUNCH(h, "k_exp_rows");
     dim3 grid((unsigned)((Kp / 2 / SLICE_VEC + 255) / 256), (unsigned)M);
     BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, is_real, conj, M, K, Kp, sa_i, sa_k, band, op.exps, S, op.slices)));
@@ -721,10 +733,14 @@ bem_status tc_prepare_operators(bem_ctx* h) {
     const int64_t N = h->N;
     bem_status st;
     // slices of X^T: row i of the A operand is column i of X (contiguous)
-    if ((st = slice_A(h, t->opS, h->S, N, N, N, 1)) != BEM_OK) return st;
-    // N's near band (entries up to ~1e4 x its far field) is applied exactly in FP64, so the
-    // split only carries the far part with its own, much smaller row scale
-    if ((st = slice_A(h, t->opW, h->W, N, N, N, 1, (int)std::min<int64_t>(TC_W_BAND, (N - 1) / 2))) != BEM_OK) return st;
+    // (row exponents from the assembly when it gathered them)
+    const int* fS = h->rexp_valid ? h->rexp : nullptr;
+    const int* fW = h->rexp_valid ? h->rexp + N : nullptr;
+    if ((st = slice_A(h, t->opS, h->S, N, N, N, 1, -1, 0, 0, fS)) != BEM_OK) return st;
+    // N's near band (entries up to ~1e4 x its far field) is applied apart in double-float,
+    // so the split only carries the far part with its own, much smaller row scale
+    if ((st = slice_A(h, t->opW, h->W, N, N, N, 1, (int)std::min<int64_t>(TC_W_BAND, (N - 1) / 2), 0, 0, fW)) != BEM_OK)
+        return st;
     if (h->D) {
         if ((st = slice_A(h, t->opD, h->D, N, N, N, 1)) != BEM_OK) return st;
     }
@@ -732,25 +748,58 @@ bem_status tc_prepare_operators(bem_ctx* h) {
 }
 
 // out (nc x N, ld nc) += Y (nc x N, ld nc) * W_band, W_band = entries of W with cyclic
-// |k - j| <= band; FP64.  Thread (m, j): sum over the 2 band + 1 rows k of column j.
-__global__ void k_band_left(const double2* __restrict__ Y, const double2* __restrict__ W, int64_t N, int64_t nc,
-                            int band, double2* out) {
-    // double-float products on the FP32 pipe; operands converted from their bit fields
-    const int64_t m = (int64_t)blockIdx.x * 32 + threadIdx.x;
-    const int64_t j = (int64_t)blockIdx.y * 8 + threadIdx.y;
-    if (m >= nc || j >= N) return;
-    cdfl acc = cdfl_zero();
-    for (int t = -band; t <= band; ++t) {
-        int64_t k = j + t;
-        if (k < 0) k += N; else if (k >= N) k -= N;
-        const double2 y = Y[m + k * nc], w = W[k + j * N];
-        const dfl yr = dfl_from_bits(y.x), yi = dfl_from_bits(y.y);
-        const dfl wr = dfl_from_bits(w.x), wi = dfl_from_bits(w.y);
-        acc.re = dfl_fma(yr, wr, dfl_fma(dfl_neg(yi), wi, acc.re));
-        acc.im = dfl_fma(yr, wi, dfl_fma(yi, wr, acc.im));
+// |k - j| <= band; products and sums in double-float (about 48 bits) on the FP32 pipe.
+// Tiled: a CTA owns 32 rows m and BAND_JB columns j; the Y rows it needs (k within the band
+// of its columns) and the band of those W columns are converted to double-float once and
+// staged in shared memory (Y as [k][m], so the 32 lanes read consecutive entries; W is
+// read by all lanes of a warp at once).  Each thread accumulates BAND_JB/8 outputs.
+#define BAND_JB 32
+__global__ void __launch_bounds__(256, 1) k_band_left(const double2* __restrict__ Y, const double2* __restrict__ W,
+                                                      int64_t N, int64_t nc, int band, double2* out) {
+    extern __shared__ float4 bsm[];
+    const int KT = BAND_JB + 2 * band;                 // k rows of the Y tile
+    float4* Ys = bsm;                                   // [KT][32]
+    float4* Ws = bsm + (size_t)KT * 32;                 // [BAND_JB][2 band + 1]
+    const int64_t m0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * BAND_JB;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int idx = tid; idx < KT * 32; idx += 256) {
+        const int kk = idx / 32, ml = idx % 32;
+        int64_t k = j0 - band + kk;
+        k = ((k % N) + N) % N;
+        const int64_t m = m0 + ml;
+        double2 y = make_double2(0.0, 0.0);
+        if (m < nc) y = Y[m + k * nc];
+        Ys[idx] = cdfl_pack({dfl_from_bits(y.x), dfl_from_bits(y.y)});
     }
-    double2* o = out + m + j * nc;
-    *o = cadd(*o, cdfl_to(acc));
+    const int BW = 2 * band + 1;
+    for (int idx = tid; idx < BAND_JB * BW; idx += 256) {
+        const int jl = idx / BW, t = idx % BW;
+        const int64_t j = j0 + jl;
+        double2 w = make_double2(0.0, 0.0);
+        if (j < N) {
+            int64_t k = j - band + t;
+            k = ((k % N) + N) % N;
+            w = W[k + j * N];
+        }
+        Ws[idx] = cdfl_pack({dfl_from_bits(w.x), dfl_from_bits(w.y)});
+    }
+    __syncthreads();
+    const int ml = threadIdx.x;
+    const int64_t m = m0 + ml;
+    for (int jj = threadIdx.y; jj < BAND_JB; jj += 8) {
+        const int64_t j = j0 + jj;
+        cdfl acc = cdfl_zero();
+        for (int t = 0; t < BW; ++t) {
+            const cdfl y = cdfl_unpack(Ys[(jj + t) * 32 + ml]);
+            const cdfl w = cdfl_unpack(Ws[jj * BW + t]);
+            acc.re = dfl_fma(y.re, w.re, dfl_fma(dfl_neg(y.im), w.im, acc.re));
+            acc.im = dfl_fma(y.re, w.im, dfl_fma(y.im, w.re, acc.im));
+        }
+        if (m < nc && j < N) {
+            double2* o = out + m + j * nc;
+            *o = cadd(*o, cdfl_to(acc));
+        }
+    }
 }
 
 static const TcOperand* op_of(TcState* t, int op) {
@@ -771,8 +820,10 @@ bem_status tc_product_left(bem_ctx* h, int op, const double* Qreal, const cplx* 
     if (st != BEM_OK || op != TC_OP_W) return st;
     if (!Y) return bem_fail(h, BEM_E_INVALID, "tc_product_left: N needs a complex left factor");
     const int band = (int)std::min<int64_t>(TC_W_BAND, (N - 1) / 2);
-    dim3 grid((unsigned)((nc + 31) / 32), (unsigned)((N + 7) / 8));
-    BEM_TIMED(h, "k_band_left", (k_band_left<<<grid, dim3(32, 8), 0, h->stream>>>(Y, h->W, N, nc, band, out)));
+    dim3 grid((unsigned)((nc + 31) / 32), (unsigned)((N + BAND_JB - 1) / BAND_JB));
+    const size_t bsmem = sizeof(float4) * ((size_t)(BAND_JB + 2 * band) * 32 + (size_t)BAND_JB * (2 * band + 1));
+    BEM_CUDA(h, cudaFuncSetAttribute(k_band_left, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+    BEM_TIMED(h, "k_band_left", (k_band_left<<<grid, dim3(32, 8), bsmem, h->stream>>>(Y, h->W, N, nc, band, out)));
     BEM_LAUNCH(h, "k_band_left");
     return BEM_OK;
 }
