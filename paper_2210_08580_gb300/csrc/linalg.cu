@@ -516,7 +516,8 @@ static bem_status coop_launch(bem_ctx* h, const void* fn, int blocks_wanted, int
                               size_t smem = 0) {
     int dev = h->device, nsm = 0, per = 0;
     BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    if (smem > 48 * 1024) BEM_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // dynamic shared memory beyond the default 48 KB (less the static part) needs the opt-in
+    if (smem > 0) BEM_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     BEM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem));
     if (per < 1) return bem_fail(h, BEM_E_CUDA, std::string(what) + ": kernel cannot be resident");
     int G = blocks_wanted;
@@ -540,9 +541,6 @@ __device__ __forceinline__ void cdfl_conj_fma(cdfl& acc, const cdfl& v, const cd
     acc.im = dfl_fma(v.re, x.im, acc.im);
     acc.im = dfl_fma(dfl_neg(v.im), x.re, acc.im);
 }
-__device__ __forceinline__ dfl dfl_norm_acc(const cdfl& x, dfl acc) {
-    return dfl_fma(x.im, x.im, dfl_fma(x.re, x.re, acc));
-}
 
 __global__ void k_to_dfl(float4* X, int64_t count) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -558,7 +556,7 @@ __global__ void k_to_dfl(float4* X, int64_t count) {
 // atomics, so the total is exact and the same in any order of arrival; bits below 2^eb are
 // dropped (the window spans 120 bits under the largest possible sum).
 #define QX_W 40
-__device__ __forceinline__ void qx_add(float f, int eb, long long L[3]) {
+__device__ __forceinline__ void qx_add(float f, int eb, long long& L0, long long& L1, long long& L2) {
     const unsigned b = __float_as_uint(f);
     const int e = (int)((b >> 23) & 255u);
     if (e == 0) return;
@@ -572,33 +570,32 @@ __device__ __forceinline__ void qx_add(float f, int eb, long long L[3]) {
     const bool neg = (b >> 31) != 0;
     if (sh >= 2 * QX_W) {                        // top limb only (the window bounds sh)
         const long long v = (long long)(m << min(sh - 2 * QX_W, 38));
-        L[2] += neg ? -v : v;
+        L2 += neg ? -v : v;
         return;
     }
-    const int k = sh >= QX_W ? 1 : 0, o = sh - k * QX_W;
-    const unsigned long long v = m << o;         // o < 40, m < 2^24
-    const long long lo = (long long)(v & ((1ull << QX_W) - 1)), hi = (long long)(v >> QX_W);
-    if (neg) { L[k] -= lo; L[k + 1] -= hi; } else { L[k] += lo; L[k + 1] += hi; }
+    const bool up = sh >= QX_W;
+    const unsigned long long v = m << (up ? sh - QX_W : sh);     // shift < 40, m < 2^24
+    long long lo = (long long)(v & ((1ull << QX_W) - 1)), hi = (long long)(v >> QX_W);
+    if (neg) { lo = -lo; hi = -hi; }
+    if (up) { L1 += lo; L2 += hi; } else { L0 += lo; L1 += hi; }
 }
 __device__ __forceinline__ float pow2f(int e) {   // 2^e, 0 below the normal range
     return (e < -126) ? 0.f : __uint_as_float((unsigned)(min(e, 127) + 127) << 23);
 }
-// limbs -> double-float (the two leading 24-bit pieces of the exact integer)
+// limbs -> double-float: each limb (|L| < 2^48: at most 2^11 partials of 40-bit digits, or
+// the small top limb) is an exact double-float a 2^24 + b; the three are summed in
+// double-float (relative error about 2^-47 of the total)
+__device__ __forceinline__ dfl qx_limb(long long L, int e) {
+    const long long a = L >> 24;                 // arithmetic: L = a 2^24 + b, 0 <= b < 2^24
+    const float fb = (float)(int)(L - (a << 24));
+    const float fa = (float)(int)a;
+    return dfl_add(dfl{fa * pow2f(e + 24), 0.f}, dfl{fb * pow2f(e), 0.f});
+}
 __device__ __forceinline__ dfl qx_to_dfl(const unsigned long long* L, int eb) {
-    const __int128 v = (__int128)(long long)L[0] + (__int128)(long long)L[1] * ((__int128)1 << QX_W) +
-                       (__int128)(long long)L[2] * ((__int128)1 << (2 * QX_W));
-    if (v == 0) return {0.f, 0.f};
-    const bool neg = v < 0;
-    const unsigned __int128 M = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
-    const unsigned long long h64 = (unsigned long long)(M >> 64), l64 = (unsigned long long)M;
-    const int t = h64 ? 127 - __clzll((long long)h64) : 63 - __clzll((long long)l64);
-    const unsigned __int128 Ms = (t >= 47) ? (M >> (t - 47)) : (M << (47 - t));
-    const unsigned m1 = (unsigned)(Ms >> 24) & 0xFFFFFFu, m2 = (unsigned)Ms & 0xFFFFFFu;
-    const int E = t + eb;
-    float hi = __uint2float_rn(m1) * pow2f(E - 23);
-    float lo = __uint2float_rn(m2) * pow2f(E - 47);
-    if (neg) { hi = -hi; lo = -lo; }
-    return dfl_qts(hi, lo);
+    const dfl t2 = qx_limb((long long)L[2], eb + 2 * QX_W);
+    const dfl t1 = qx_limb((long long)L[1], eb + QX_W);
+    const dfl t0 = qx_limb((long long)L[0], eb);
+    return dfl_add(t2, dfl_add(t1, t0));
 }
 
 // Pivoted Householder QR of X (N x n) in double-float with ONE grid barrier per column.
@@ -617,7 +614,7 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
                                                      unsigned long long* lim, int* emax, unsigned* bar, int* err) {
     extern __shared__ float4 qsm[];
     float4* wbD = qsm;                                    // [8][QR_NP] per-warp dot partials
-    float2* wbN = reinterpret_cast<float2*>(wbD + 8 * QR_NP);   // [8][QR_NP] norm partials
+    float* wbN = reinterpret_cast<float*>(wbD + 8 * QR_NP);     // [8][QR_NP] norm partials (FP32)
     float4* sRow = reinterpret_cast<float4*>(wbN + 8 * QR_NP);  // [QR_NP] row j (by position)
     float4* sW = sRow + QR_NP;                            // [QR_NP] w by position
     float4* sD = sW + QR_NP;                              // [QR_NP] d by position
@@ -641,13 +638,13 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
         __syncthreads();
         for (int l = tid; l < cnt; l += blockDim.x) {
             cdfl d = cdfl_unpack(wbD[l]);
-            dfl nn = dfl_mk(wbN[l]);
+            float nn = wbN[l];
             for (int q = 1; q < 8; ++q) {
                 d = cdfl_add(d, cdfl_unpack(wbD[q * QR_NP + l]));
-                nn = dfl_add(nn, dfl_mk(wbN[q * QR_NP + l]));
+                nn += wbN[q * QR_NP + l];
             }
             wbD[l] = cdfl_pack(d);
-            wbN[l] = make_float2(nn.hi, nn.lo);
+            wbN[l] = nn;
         }
         __syncthreads();
     };
@@ -655,11 +652,10 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
     auto publish = [&](int c0, int cnt, int buf, int eb) {
         for (int l = tid; l < cnt; l += blockDim.x) {
             const float4 d = wbD[l];
-            const float2 nn = wbN[l];
             long long L[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            qx_add(d.x, eb, L); qx_add(d.y, eb, L);
-            qx_add(d.z, eb, L + 3); qx_add(d.w, eb, L + 3);
-            qx_add(nn.x, eb, L + 6); qx_add(nn.y, eb, L + 6);
+            qx_add(d.x, eb, L[0], L[1], L[2]); qx_add(d.y, eb, L[0], L[1], L[2]);
+            qx_add(d.z, eb, L[3], L[4], L[5]); qx_add(d.w, eb, L[3], L[4], L[5]);
+            qx_add(wbN[l], eb, L[6], L[7], L[8]);
             unsigned long long* dst = lim + (size_t)buf * LS + (size_t)cmap[c0 + l] * 9;
 #pragma unroll
             for (int u = 0; u < 9; ++u)
@@ -667,28 +663,35 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
         }
     };
     // one pass over this CTA's rows i >= jp1: optionally x_c -= v_i w_c for the positions
-    // c >= jp1 (v_i = X[i, pj]), then partial sums of conj(x_{i,cmap[jp1]}) x_{i,c} and
-    // |x_{i,c}|^2 with the updated values; leaves the CTA's sums in wbD[0], wbN[0]
+    // c >= jp1 (v_i = X[i, pj]), then partial sums of conj(x_{i,cmap[jp1]}) x_{i,c} (double-
+    // float) and |x_{i,c}|^2 (FP32: the norms only choose pivots) with the updated values;
+    // leaves the CTA's sums in wbD[0], wbN[0].  Rows go in pairs, the next pair's loads
+    // issued before the current pair's arithmetic.
     auto pass = [&](int jp1, bool upd, int pj) {
         int pcs[QR_KC];
-        cdfl w[QR_KC];
 #pragma unroll
         for (int k = 0; k < QR_KC; ++k) {
             const int c = jp1 + lane + 32 * k;
             pcs[k] = (c < n) ? cmap[c] : -1;
-            w[k] = (upd && c < n) ? cdfl_unpack(sW[c]) : cdfl_zero();
         }
         cdfl accD[QR_KC];
-        dfl accN[QR_KC];
+        float accN[QR_KC];
 #pragma unroll
-        for (int k = 0; k < QR_KC; ++k) { accD[k] = cdfl_zero(); accN[k] = {0.f, 0.f}; }
+        for (int k = 0; k < QR_KC; ++k) { accD[k] = cdfl_zero(); accN[k] = 0.f; }
+        auto load = [&](int64_t i, cdfl& v, cdfl* x) {
+            const bool ok = i < r1;
+            v = (upd && ok) ? cdfl_ld(X + i * n + pj) : cdfl_zero();
+#pragma unroll
+            for (int k = 0; k < QR_KC; ++k) x[k] = (ok && pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
+        };
         auto row = [&](int64_t i, const cdfl& vi, cdfl* x) {
-            if (upd) {
+            if (upd && i < r1) {
 #pragma unroll
                 for (int k = 0; k < QR_KC; ++k) {
                     if (pcs[k] < 0) continue;
-                    x[k].re = dfl_fma(dfl_neg(vi.re), w[k].re, dfl_fma(vi.im, w[k].im, x[k].re));
-                    x[k].im = dfl_fma(dfl_neg(vi.re), w[k].im, dfl_fma(dfl_neg(vi.im), w[k].re, x[k].im));
+                    const cdfl wk = cdfl_unpack(sW[jp1 + lane + 32 * k]);
+                    x[k].re = dfl_fma(dfl_neg(vi.re), wk.re, dfl_fma(vi.im, wk.im, x[k].re));
+                    x[k].im = dfl_fma(dfl_neg(vi.re), wk.im, dfl_fma(dfl_neg(vi.im), wk.re, x[k].im));
                     X[i * n + pcs[k]] = cdfl_pack(x[k]);
                 }
             }
@@ -699,33 +702,29 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
             for (int k = 0; k < QR_KC; ++k) {
                 if (pcs[k] < 0) continue;
                 cdfl_conj_fma(accD[k], p, x[k]);
-                accN[k] = dfl_norm_acc(x[k], accN[k]);
+                accN[k] = fmaf(x[k].re.hi, x[k].re.hi, fmaf(x[k].im.hi, x[k].im.hi, accN[k]));
             }
         };
         int64_t i = max(r0, (int64_t)jp1) + rg;
-        for (; i + 8 < r1; i += 16) {
-            cdfl va = cdfl_zero(), vb = cdfl_zero();
-            if (upd) { va = cdfl_ld(X + i * n + pj); vb = cdfl_ld(X + (i + 8) * n + pj); }
-            cdfl xa[QR_KC], xb[QR_KC];
-#pragma unroll
-            for (int k = 0; k < QR_KC; ++k) {
-                xa[k] = (pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
-                xb[k] = (pcs[k] >= 0) ? cdfl_ld(X + (i + 8) * n + pcs[k]) : cdfl_zero();
-            }
-            row(i, va, xa);
-            row(i + 8, vb, xb);
-        }
         if (i < r1) {
-            const cdfl vi = upd ? cdfl_ld(X + i * n + pj) : cdfl_zero();
-            cdfl xr[QR_KC];
+            cdfl va, vb, xa[QR_KC], xb[QR_KC];
+            load(i, va, xa);
+            load(i + 8, vb, xb);
+            for (; i < r1; i += 16) {
+                cdfl na, nb, ya[QR_KC], yb[QR_KC];
+                load(i + 16, na, ya);
+                load(i + 24, nb, yb);
+                row(i, va, xa);
+                row(i + 8, vb, xb);
+                va = na; vb = nb;
 #pragma unroll
-            for (int k = 0; k < QR_KC; ++k) xr[k] = (pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
-            row(i, vi, xr);
+                for (int k = 0; k < QR_KC; ++k) { xa[k] = ya[k]; xb[k] = yb[k]; }
+            }
         }
 #pragma unroll
         for (int k = 0; k < QR_KC; ++k) {
             wbD[rg * QR_NP + lane + 32 * k] = cdfl_pack(accD[k]);
-            wbN[rg * QR_NP + lane + 32 * k] = make_float2(accN[k].hi, accN[k].lo);
+            wbN[rg * QR_NP + lane + 32 * k] = accN[k];
         }
         reduce_warps(n - jp1);
     };
@@ -765,22 +764,25 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
     // the first pivot and the sums of step 0
     {
         int pcs[QR_KC];
-        dfl acc[QR_KC];
+        float acc[QR_KC];
 #pragma unroll
-        for (int k = 0; k < QR_KC; ++k) { pcs[k] = (lane + 32 * k < n) ? lane + 32 * k : -1; acc[k] = {0.f, 0.f}; }
+        for (int k = 0; k < QR_KC; ++k) { pcs[k] = (lane + 32 * k < n) ? lane + 32 * k : -1; acc[k] = 0.f; }
         for (int64_t i = r0 + rg; i < r1; i += 8) {
 #pragma unroll
             for (int k = 0; k < QR_KC; ++k)
-                if (pcs[k] >= 0) acc[k] = dfl_norm_acc(cdfl_ld(X + i * n + pcs[k]), acc[k]);
+                if (pcs[k] >= 0) {
+                    const float4 x = X[i * n + pcs[k]];
+                    acc[k] = fmaf(x.x, x.x, fmaf(x.z, x.z, acc[k]));
+                }
         }
 #pragma unroll
         for (int k = 0; k < QR_KC; ++k) {
             wbD[rg * QR_NP + lane + 32 * k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            wbN[rg * QR_NP + lane + 32 * k] = make_float2(acc[k].hi, acc[k].lo);
+            wbN[rg * QR_NP + lane + 32 * k] = acc[k];
         }
         reduce_warps(n);
         int mx = 0;
-        for (int c = tid; c < n; c += blockDim.x) mx = max(mx, (int)((__float_as_uint(wbN[c].x) >> 23) & 255u));
+        for (int c = tid; c < n; c += blockDim.x) mx = max(mx, (int)((__float_as_uint(wbN[c]) >> 23) & 255u));
         mx = __reduce_max_sync(0xffffffffu, (unsigned)mx);
         if (lane == 0 && mx) atomicMax(emax, mx);
     }
@@ -834,7 +836,7 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
         // (B) reflector of the pivot column (one thread, double-float)
         const bool own_j = (j >= r0 && j < r1);
         if (tid == 0) {
-            const dfl nrm2 = dfl_mk(sN[j]);
+            const dfl nrm2 = cdfl_unpack(sD[j]).re;      // sum |x_{i,p}|^2, i >= j (double-float)
             const cdfl xjj = cdfl_unpack(sRow[j]);
             cdfl alpha = cdfl_zero(), vj = cdfl_zero();
             dfl tau = {0.f, 0.f};
@@ -922,7 +924,7 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* 
         BEM_LAUNCH(h, "k_to_dfl");
         float4* Xf = reinterpret_cast<float4*>(X);
         void* args_df[] = {&Xf, &N, &n, &R, &perm, &lim, &emax, &h->bar, &h->dev_err};
-        const size_t smem = (size_t)QR_NP * (8 * sizeof(float4) + 8 * sizeof(float2) + 3 * sizeof(float4) + sizeof(float2));
+        const size_t smem = (size_t)QR_NP * (8 * sizeof(float4) + 8 * sizeof(float) + 3 * sizeof(float4) + sizeof(float2));
         BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr_df, G, 256, args_df, "k_house_qr_df", smem));
         cudaFreeAsync(lim, h->stream);
         return st;
@@ -1055,7 +1057,9 @@ __global__ void __launch_bounds__(JAC_NT) k_jacobi(float4* X, int n, int* ver, i
                         const dfl ab = dfl_mul(A, Bv);
                         int rot = (ag2.hi > 0.f) && !(ag2.hi <= 1e-28f * ab.hi);
                         if (rot) {
-                            flags[sweep] = 1;
+                            // a sweep whose rotations all have |g| <= 1e-8 |x| |y| is the last
+                            // one: Jacobi's quadratic convergence leaves |g| near 1e-16 after it
+                            if (ag2.hi > 1e-16f * ab.hi) flags[sweep] = 1;
                             const dfl rag = dfl_rsqrt(ag2);                       // 1/|g|
                             const dfl zeta = dfl_scale(dfl_mul(dfl_sub(Bv, A), rag), 0.5f);
                             dfl t;
