@@ -44,7 +44,6 @@
 #define TC_BK 32
 #define TC_STAGES 2
 #define TC_CHUNK_KB 16              // K' chunk of 16 x 32 = 512 between TMEM flushes
-#define TC_SPLIT_TARGET 152         // CTAs to aim for when splitting K' (one per SM)
 #define TC_NACC 4                   // TMEM accumulators (4 x 128 columns = all 512)
 #define TC_SMAX 7
 #define TC_TILE_BYTES (TC_BM * TC_BK * 2)          // 8 KiB per slice tile (A and B alike)
@@ -695,15 +694,24 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     }
     BEM_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int mt = (p.M + TC_BM - 1) / TC_BM, nt = (p.Ncols + TC_BN - 1) / TC_BN;
-    // skinny outputs (r x nrhs, r x r) fill few SMs: split K' so that about one wave of
-    // CTAs runs, each split at least a few accumulation chunks long
+    // split K' across CTAs (FP64 partials summed by k_splitk_reduce) when that fills the
+    // SMs better: every tile costs the same, so the run time is (waves of CTAs) x (chunks
+    // per split); the partials cost their write and read-back (at about 6 TB/s).  This
+    // fills the GPU for skinny outputs (r x nrhs) and evens out the last wave of large ones.
+    int nsm = 0;
+    BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    const int T = mt * nt;
+    const int nch = (p.nkb + TC_CHUNK_KB - 1) / TC_CHUNK_KB;
+    const double chunk_ms = (double)(t->S * (t->S + 1) / 2) * TC_CHUNK_KB * (TC_BK / 16) * 73.0 / 2.0e6;
+    const double part_ms_per_split = (double)p.M * (p.Ncols / 2) * 32.0 / 6.0e9;
     int splits = 1;
-    if (mt * nt < TC_SPLIT_TARGET && p.nkb >= 4 * TC_CHUNK_KB) {
-        splits = std::min((TC_SPLIT_TARGET + mt * nt - 1) / (mt * nt), p.nkb / (4 * TC_CHUNK_KB));
-        if (splits > 1) {
-            p.kps = ((p.nkb + splits - 1) / splits + TC_CHUNK_KB - 1) / TC_CHUNK_KB * TC_CHUNK_KB;
-            splits = (p.nkb + p.kps - 1) / p.kps;
-        }
+    double best = (double)((T + nsm - 1) / nsm) * nch * chunk_ms;
+    for (int s = 2; s <= 32 && s <= nch / 2; ++s) {
+        const int cps = (nch + s - 1) / s;
+        const int sr = (nch + cps - 1) / cps;
+        if (sr != s) continue;
+        const double cost = (double)(((int64_t)T * s + nsm - 1) / nsm) * cps * chunk_ms + s * part_ms_per_split;
+        if (cost < 0.98 * best) { best = cost; splits = s; p.kps = cps * TC_CHUNK_KB; }
     }
     const int m = p.Ncols / 2;
     if (splits > 1) {
