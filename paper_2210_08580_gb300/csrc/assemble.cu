@@ -232,9 +232,9 @@ static void build_bessel_table(std::vector<double>& tab, std::vector<float>& tab
     for (int i = 0; i < BTAB_NINT; ++i) {
         ld za, zb;
         if (i < BTAB_NLOG) {
-            const int m = BTAB_LOG_EMIN + i / 8, j = i % 8;
-            za = ldexpl(1.0L + j / 8.0L, m);
-            zb = ldexpl(1.0L + (j + 1) / 8.0L, m);
+            const int m = BTAB_LOG_EMIN + i / BTAB_PEROCT, j = i % BTAB_PEROCT;
+            za = ldexpl(1.0L + j / (ld)BTAB_PEROCT, m);
+            zb = ldexpl(1.0L + (j + 1) / (ld)BTAB_PEROCT, m);
         } else {
             za = (ld)BTAB_ZLIN + (i - BTAB_NLOG) * (ld)BTAB_W;
             zb = za + (ld)BTAB_W;
@@ -590,7 +590,7 @@ __device__ __forceinline__ int btab_index(float uhi) {
     const float zf = sqrtf(uhi);
     if (zf < (float)BTAB_ZLIN) {
         const int bits = __float_as_int(zf);
-        return (((bits >> 23) & 255) - 127 - BTAB_LOG_EMIN) * 8 + ((bits >> 20) & 7);
+        return (((bits >> 23) & 255) - 127 - BTAB_LOG_EMIN) * BTAB_PEROCT + ((bits >> (23 - BTAB_OCT_LOG2)) & (BTAB_PEROCT - 1));
     }
     return BTAB_NLOG + (int)fminf((zf - (float)BTAB_ZLIN) * (float)(1.0 / BTAB_W), (float)BTAB_NINT);
 }
