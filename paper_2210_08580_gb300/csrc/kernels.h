@@ -35,6 +35,9 @@ bem_status launch_gram_vjp(bem_ctx* h, int nrhs, const cplx* const* P_dev, const
 
 // linalg.cu
 enum { OP_N = 0, OP_T = 1, OP_C = 2 };
+// C = A B in double-float (complex FP64 storage, no transposes, alpha = 1, beta = 0)
+bem_status zgemm_df(bem_ctx* h, int64_t M, int64_t Nc, int64_t K, const cplx* A, int64_t lda, const cplx* B,
+                    int64_t ldb, cplx* C, int64_t ldc);
 bem_status zgemm(bem_ctx* h, int opa, int opb, int64_t M, int64_t Nc, int64_t K, cplx alpha,
                  const cplx* A, int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc);
 bem_status dzgemm_realA(bem_ctx* h, int opa, int64_t M, int64_t Nc, int64_t K, double alpha,

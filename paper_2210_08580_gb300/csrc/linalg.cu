@@ -119,6 +119,65 @@ static void zgemm_launch(cudaStream_t st, int64_t M, int64_t Nc, int64_t K, cplx
     k_zgemm<OPA, OPB, AREAL><<<grid, 256, 0, st>>>((int)M, (int)Nc, (int)K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
+// C = A B (no transposes; column-major complex FP64 in and out) with double-float
+// products and sums on the FP32 pipe: 32 x 32 output tiles, K in steps of 16 staged in
+// shared memory, each thread four outputs of one column.  For the small dense products of
+// the mixed path (the r x r Woodbury core times r x nrhs), where FP64 issue dominates.
+#define ZDF_T 32
+#define ZDF_K 16
+__global__ void __launch_bounds__(256) k_zgemm_df(int64_t M, int64_t Nc, int64_t K, const cplx* __restrict__ A,
+                                                  int64_t lda, const cplx* __restrict__ B, int64_t ldb, cplx* C,
+                                                  int64_t ldc) {
+    __shared__ float4 sA[ZDF_K][ZDF_T + 1];     // [k][row]
+    __shared__ float4 sB[ZDF_T][ZDF_K + 1];     // [col][k]
+    const int64_t i0 = (int64_t)blockIdx.x * ZDF_T, j0 = (int64_t)blockIdx.y * ZDF_T;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // row tx, columns ty + 8 q
+    cdfl acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = cdfl_zero();
+    for (int64_t k0 = 0; k0 < K; k0 += ZDF_K) {
+        for (int e = threadIdx.x; e < ZDF_T * ZDF_K; e += 256) {
+            const int r = e % ZDF_T, kk = e / ZDF_T;
+            const int64_t gi = i0 + r, gk = k0 + kk;
+            const cplx a = (gi < M && gk < K) ? A[gi + gk * lda] : cmk(0, 0);
+            sA[kk][r] = cdfl_pack({dfl_from_bits(a.x), dfl_from_bits(a.y)});
+            const int kb = e % ZDF_K, cb = e / ZDF_K;
+            const int64_t gj = j0 + cb, gk2 = k0 + kb;
+            const cplx b = (gj < Nc && gk2 < K) ? B[gk2 + gj * ldb] : cmk(0, 0);
+            sB[cb][kb] = cdfl_pack({dfl_from_bits(b.x), dfl_from_bits(b.y)});
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < ZDF_K; ++kk) {
+            const cdfl a = cdfl_unpack(sA[kk][tx]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const cdfl b = cdfl_unpack(sB[ty + 8 * q][kk]);
+                acc[q].re = dfl_fma(a.re, b.re, dfl_fma(dfl_neg(a.im), b.im, acc[q].re));
+                acc[q].im = dfl_fma(a.re, b.im, dfl_fma(a.im, b.re, acc[q].im));
+            }
+        }
+        __syncthreads();
+    }
+    const int64_t gi = i0 + tx;
+    if (gi >= M) return;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t gj = j0 + ty + 8 * q;
+        if (gj < Nc) C[gi + gj * ldc] = cdfl_to(acc[q]);
+    }
+}
+bem_status zgemm_df(bem_ctx* h, int64_t M, int64_t Nc, int64_t K, const cplx* A, int64_t lda, const cplx* B,
+                    int64_t ldb, cplx* C, int64_t ldc) {
+    if (M <= 0 || Nc <= 0) return BEM_OK;
+    if ((Nc + ZDF_T - 1) / ZDF_T > 65535) return bem_fail(h, BEM_E_UNSUPPORTED, "zgemm_df: too many columns");
+    dim3 grid((unsigned)((M + ZDF_T - 1) / ZDF_T), (unsigned)((Nc + ZDF_T - 1) / ZDF_T));
+    BEM_TIMED(h, h->tag, (k_zgemm_df<<<grid, 256, 0, h->stream>>>(M, Nc, K, A, lda, B, ldb, C, ldc)));
+    h->tag = "kernel";
+    BEM_LAUNCH(h, "k_zgemm_df");
+    return BEM_OK;
+}
+
 bem_status zgemm(bem_ctx* h, int opa, int opb, int64_t M, int64_t Nc, int64_t K, cplx alpha,
                  const cplx* A, int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc) {
     if (M <= 0 || Nc <= 0) return BEM_OK;
@@ -1341,11 +1400,32 @@ __global__ void k_axpby(cplx* y, int64_t ldy, const cplx* x, int64_t ldx, cplx a
     if (b.x != 0.0 || b.y != 0.0) v = cadd(v, cmul(b, y[rr + cc * ldy]));
     y[rr + cc * ldy] = v;
 }
+// y = a x + b y with real a, b: a 2D grid (no index division) and two FP64 operations per
+// component, which keeps it at the memory rate (complex coefficients cost the FP64 pipe)
+__global__ void k_axpby_real(cplx* y, int64_t ldy, const cplx* x, int64_t ldx, double a, double b, int64_t rows,
+                             int64_t cols) {
+    const int64_t rr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (rr >= rows) return;
+    for (int64_t cc = blockIdx.y; cc < cols; cc += gridDim.y) {
+        const cplx xv = x[rr + cc * ldx];
+        cplx v = cmk(a * xv.x, a * xv.y);
+        if (b != 0.0) {
+            const cplx yv = y[rr + cc * ldy];
+            v = cmk(fma(b, yv.x, v.x), fma(b, yv.y, v.y));
+        }
+        y[rr + cc * ldy] = v;
+    }
+}
 bem_status launch_axpby(bem_ctx* h, cplx* y, int64_t ldy, const cplx* x, int64_t ldx, cplx a, cplx b,
                         int64_t rows, int64_t cols) {
     const int64_t tot = rows * cols;
     if (tot == 0) return BEM_OK;
-    BEM_TIMED(h, "k_axpby", (k_axpby<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(y, ldy, x, ldx, a, b, rows, cols)));
+    if (a.y == 0.0 && b.y == 0.0) {
+        dim3 grid((unsigned)((rows + 255) / 256), (unsigned)std::min<int64_t>(cols, 65535));
+        BEM_TIMED(h, "k_axpby", (k_axpby_real<<<grid, 256, 0, h->stream>>>(y, ldy, x, ldx, a.x, b.x, rows, cols)));
+    } else {
+        BEM_TIMED(h, "k_axpby", (k_axpby<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(y, ldy, x, ldx, a, b, rows, cols)));
+    }
     BEM_LAUNCH(h, "k_axpby");
     return BEM_OK;
 }
@@ -1361,18 +1441,41 @@ bem_status launch_add_identity(bem_ctx* h, cplx* A, int64_t ld, int r, cplx d) {
     return BEM_OK;
 }
 
-// out_max = max over columns of |num_c| / |den_c| (2-norms); one CTA per column, then max
+// double -> float from the bit fields, significand truncated (a norm estimate needs no
+// more; FP64 conversions and squares would run on the slow FP64 pipe); values outside
+// the float range saturate or flush
+__device__ __forceinline__ float d2f_trunc(double v) {
+    const long long b = __double_as_longlong(v);
+    const int E = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+    if (E <= 0) return 0.f;
+    const unsigned sgn = (unsigned)((unsigned long long)b >> 63) << 31;
+    if (E >= 255) return __uint_as_float(sgn | 0x7F7FFFFFu);
+    return __uint_as_float(sgn | ((unsigned)E << 23) | (unsigned)((b >> 29) & 0x7FFFFF));
+}
+// out_max = max over columns of |num_c| / |den_c| (2-norms, FP32 accumulation: the ratio
+// is a convergence test, far looser than FP32's precision); one CTA per column, then max
 __global__ void k_col_ratio(const cplx* num, int64_t ldn, const cplx* den, int64_t ldd, int64_t rows, double* ratios) {
-    __shared__ double red[32];
+    __shared__ float red[2][32];
     const int64_t c = blockIdx.x;
-    double a = 0.0, b = 0.0;
+    float a = 0.f, b = 0.f;
     for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) {
-        a += cabs2(num[i + c * ldn]);
-        b += cabs2(den[i + c * ldd]);
+        const cplx u = num[i + c * ldn], w = den[i + c * ldd];
+        const float ur = d2f_trunc(u.x), ui = d2f_trunc(u.y), wr = d2f_trunc(w.x), wi = d2f_trunc(w.y);
+        a = fmaf(ur, ur, fmaf(ui, ui, a));
+        b = fmaf(wr, wr, fmaf(wi, wi, b));
     }
-    a = block_sum(a, red);
-    b = block_sum(b, red);
-    if (threadIdx.x == 0) ratios[c] = (b > 0.0) ? sqrt(a / b) : sqrt(a);
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { red[0][wid] = a; red[1][wid] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { A += red[0][q]; B += red[1][q]; }
+        ratios[c] = (B > 0.0) ? sqrt(A / B) : sqrt(A);
+    }
 }
 __global__ void k_max(const double* v, int64_t n, double* out) {
     __shared__ double red[32];

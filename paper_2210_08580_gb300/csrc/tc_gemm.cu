@@ -386,21 +386,30 @@ __global__ void k_exp_from_fields(const int* fields, int64_t M, int* e) {
 }
 
 // B column exponents: B_op[k, j] = src[k*sb_k + j*sb_j] (complex, or real when is_real);
-// columns 2j and 2j+1 of B' share f_j.
-__global__ void k_exp_cols(const void* src, int is_real, int64_t K, int64_t m, int64_t sb_k, int64_t sb_j, int* f) {
-    const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (j >= m) return;
+// columns 2j and 2j+1 of B' share f_j.  One CTA per column, four loads in flight per thread.
+__global__ void __launch_bounds__(256) k_exp_cols(const void* src, int is_real, int64_t K, int64_t m, int64_t sb_k,
+                                                  int64_t sb_j, int* f) {
+    __shared__ int red[8];
+    const int64_t j = blockIdx.x;
     int mx = 0;
-    for (int64_t k = threadIdx.x & 31; k < K; k += 32) {
-        if (is_real) {
-            mx = max(mx, exp_field(((const double*)src)[k * sb_k + j * sb_j]));
-        } else {
-            const double2 v = ((const double2*)src)[k * sb_k + j * sb_j];
-            mx = max(mx, max(exp_field(v.x), exp_field(v.y)));
+    for (int64_t k0 = threadIdx.x; k0 < K; k0 += 4 * (int64_t)blockDim.x) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + (int64_t)u * blockDim.x;
+            if (k >= K) break;
+            if (is_real) {
+                mx = max(mx, exp_field(((const double*)src)[k * sb_k + j * sb_j]));
+            } else {
+                const double2 v = ((const double2*)src)[k * sb_k + j * sb_j];
+                mx = max(mx, max(exp_field(v.x), exp_field(v.y)));
+            }
         }
     }
-    mx = __reduce_max_sync(0xffffffffu, mx);
-    if ((threadIdx.x & 31) == 0) {
+    mx = (int)__reduce_max_sync(0xffffffffu, (unsigned)mx);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) mx = max(mx, red[q]);
         const int ex = mx ? mx - 1022 : 0;
         f[2 * j] = ex;
         f[2 * j + 1] = ex;
@@ -627,7 +636,7 @@ static bem_status slice_B(bem_ctx* h, TcOperand& op, const void* src, int is_rea
     bem_status st = reserve(h, op, 2 * m, Kp, S);
     if (st != BEM_OK) return st;
     op.K = K;
-    BEM_TIMED(h, "k_exp_cols", (k_exp_cols<<<(unsigned)((m + 7) / 8), 256, 0, h->stream>>>(src, is_real, K, m, sb_k, sb_j, op.exps)));
+    BEM_TIMED(h, "k_exp_cols", (k_exp_cols<<<(unsigned)m, 256, 0, h->stream>>>(src, is_real, K, m, sb_k, sb_j, op.exps)));
     BEM_LAUNCH(h, "k_exp_cols");
     dim3 grid((unsigned)((Kp / 2 / SLICE_VEC + 255) / 256), (unsigned)m);
     BEM_TIMED(h, "k_slice_B", (k_slice_B<<<grid, 256, 0, h->stream>>>(src, is_real, K, m, Kp, sb_k, sb_j, op.exps, S, op.slices)));
@@ -887,7 +896,7 @@ static bem_status woodbury_tc(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x, i
     if ((st = slice_B(h, t->bbuf, v, 0, N, nrhs, 1, ldv)) != BEM_OK) return st;
     if ((st = tc_gemm(h, t->opVh, t->bbuf, T, r, 0, 1.0, 0.0, "tc_solve_Vhv")) != BEM_OK) return st;
     h->tag = "gemm_solve_core";
-    if ((st = zgemm(h, OP_N, OP_N, r, nrhs, r, cmk(1, 0), h->K, r, T, r, cmk(0, 0), T2, r)) != BEM_OK) return st;
+    if ((st = zgemm_df(h, r, nrhs, r, h->K, r, T, r, T2, r)) != BEM_OK) return st;
     // x <- xscale x + vscale v / beta ; then x -= beta^-2 U T2
     if ((st = launch_axpby(h, x, ldx, v, ldv, cmk(vscale / h->beta, 0), cmk(xscale, 0), N, nrhs)) != BEM_OK) return st;
     if ((st = slice_B(h, t->bbuf, T2, 0, r, nrhs, 1, r)) != BEM_OK) return st;
