@@ -441,6 +441,26 @@ __device__ __forceinline__ void split_digits(double val, int e, int S, uint32_t*
         X = (m + (1LL << (sh - 1))) >> sh;
         if (b < 0) X = -X;
     }
+    if (S >= 4) {
+        // |X| < 2^(7S) <= 2^49: the three lowest digits come from the low 21 bits and the rest
+        // from the upper part plus the carry, all in 32-bit integers
+        int cur = (int)(X & 0x1FFFFF);
+        const int hi = (int)(X >> 21);
+        int t = 0;
+#pragma unroll
+        for (int s = TC_SMAX - 1; s >= 1; --s) {
+            if (s >= S) { d[s] = 0u; continue; }
+            if (t == 3) cur += hi;
+            int q = cur & 127;
+            if (q >= 64) q -= 128;
+            cur = (cur - q) >> 7;
+            d[s] = digit_bf16(q, s);
+            ++t;
+        }
+        if (t == 3) cur += hi;                  // S = 4: the upper part is the leading digit
+        d[0] = digit_bf16(cur, 0);
+        return;
+    }
 #pragma unroll
     for (int s = TC_SMAX - 1; s >= 1; --s) {
         if (s >= S) { d[s] = 0u; continue; }
