@@ -37,12 +37,12 @@ FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # FP32 operations per far-field Gauss point of the S/N assembly, which runs in
 # double-float arithmetic (df fma = 15 FP32 ops, df mul = 7, df add = 11): node offsets
 # 2 fma (30), r^2 1 mul + 1 fma (22), u = k^2 r^2 1 mul (7), t = (u - u_mid)/u_half 1 add +
-# 1 mul (18), J0 and Y0 as degree-10 polynomials 20 fma (300), g = (i/4) H0 4 scalings,
+# 1 mul (18), J0 and Y0 as degree-7 polynomials 14 fma (210), g = (i/4) H0 4 scalings,
 # the two lambda-weighted row sums 4 fma (60)
-ASM_OPS_PER_POINT = 441
+ASM_OPS_PER_POINT = 351
 # DRAM bytes (read + write) per launch from ncu captures of the kernels as they stand
 # (absent = not captured since the kernel last changed); the summaries are under profiles/
-TRAFFIC_BYTES = {"tc_rhs_SY": 18.08e9 + 0.267e9, "k_assemble": 0.0346e9 + 8.55e9}
+TRAFFIC_BYTES = {}
 
 
 def _peaks():
