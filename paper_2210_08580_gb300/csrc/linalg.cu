@@ -668,9 +668,12 @@ __device__ __forceinline__ dfl qx_to_dfl(const unsigned long long* L, int eb) {
 // (x_c -= v w_c) and, in the same pass, accumulates the sums of step j + 1 against the
 // updated next pivot column.  n <= 32 QR_KC.
 #define QR_KC 7
+#define QR_KS ((QR_KC + 1) / 2)      // slots per thread (two column groups)
 #define QR_NP (32 * QR_KC)
-__global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, int n, cplx* R, int* perm,
-                                                     unsigned long long* lim, int* emax, unsigned* bar, int* err) {
+#define QR_NT 512
+__global__ void __launch_bounds__(QR_NT, 1) k_house_qr_df(float4* X, int64_t N, int n, cplx* R, int* perm,
+                                                       unsigned long long* lim, int* emax, float4* Pc, unsigned* bar,
+                                                       int* err) {
     extern __shared__ float4 qsm[];
     float4* wbD = qsm;                                    // [8][QR_NP] per-warp dot partials
     float* wbN = reinterpret_cast<float*>(wbD + 8 * QR_NP);     // [8][QR_NP] norm partials (FP32)
@@ -681,13 +684,14 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
     __shared__ int cmap[QR_NP];
     __shared__ float4 s_ref[2];                           // alpha, v_j
     __shared__ float2 s_tau;
-    __shared__ float2 s_best[8];
-    __shared__ int s_bidx[8];
+    __shared__ float2 s_best[QR_NT / 32];
+    __shared__ int s_bidx[QR_NT / 32];
     __shared__ int s_eb;
     const unsigned G = gridDim.x;
     const int64_t rb = (N + G - 1) / G;
     const int64_t r0 = (int64_t)blockIdx.x * rb, r1 = min(N, r0 + rb);
-    const int tid = threadIdx.x, rg = tid >> 5, lane = tid & 31;
+    // warp w: row group w & 7, column group w >> 3 (slots k = 2 kk + column group)
+    const int tid = threadIdx.x, warp = tid >> 5, rg = warp & 7, cgp = warp >> 3, lane = tid & 31;
     const size_t LS = (size_t)n * 9;                      // limbs per buffer: 9 per column
     for (int c = tid; c < n; c += blockDim.x) cmap[c] = c;
     __syncthreads();
@@ -722,68 +726,69 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
         }
     };
     // one pass over this CTA's rows i >= jp1: optionally x_c -= v_i w_c for the positions
-    // c >= jp1 (v_i = X[i, pj]), then partial sums of conj(x_{i,cmap[jp1]}) x_{i,c} (double-
-    // float) and |x_{i,c}|^2 (FP32: the norms only choose pivots) with the updated values;
-    // leaves the CTA's sums in wbD[0], wbN[0].  Rows go in pairs, the next pair's loads
-    // issued before the current pair's arithmetic.
-    auto pass = [&](int jp1, bool upd, int pj) {
-        int pcs[QR_KC];
+    // c >= jp1 (v_i: the pivot column as updated by the previous pass, kept in Pc), then
+    // partial sums of conj(x_{i,p'}) x_{i,c} (double-float; p' = cmap[jp1], the next pivot)
+    // and |x_{i,c}|^2 (FP32: the norms only choose pivots) with the updated values; leaves
+    // the CTA's sums in wbD[0], wbN[0].  The next pivot column's new values go to Pc, not to
+    // X, so that column of X is read-only during the pass: column group 0 has it in slot 0
+    // (lane 0) and shares it by a shuffle, column group 1 recomputes it from X.
+    auto pass = [&](int jp1, bool upd) {
+        int pcs[QR_KS];
 #pragma unroll
-        for (int k = 0; k < QR_KC; ++k) {
-            const int c = jp1 + lane + 32 * k;
-            pcs[k] = (c < n) ? cmap[c] : -1;
+        for (int kk = 0; kk < QR_KS; ++kk) {
+            const int k = 2 * kk + cgp, c = jp1 + lane + 32 * k;
+            pcs[kk] = (k < QR_KC && c < n) ? cmap[c] : -1;
         }
-        cdfl accD[QR_KC];
-        float accN[QR_KC];
+        const int pn = (jp1 < n) ? cmap[jp1] : -1;
+        const float4* pin = Pc + (size_t)((jp1 & 1) ^ 1) * N;
+        float4* pout = Pc + (size_t)(jp1 & 1) * N;
+        const cdfl wn = (upd && pn >= 0) ? cdfl_unpack(sW[jp1]) : cdfl_zero();
+        cdfl accD[QR_KS];
+        float accN[QR_KS];
 #pragma unroll
-        for (int k = 0; k < QR_KC; ++k) { accD[k] = cdfl_zero(); accN[k] = 0.f; }
-        auto load = [&](int64_t i, cdfl& v, cdfl* x) {
-            const bool ok = i < r1;
-            v = (upd && ok) ? cdfl_ld(X + i * n + pj) : cdfl_zero();
-#pragma unroll
-            for (int k = 0; k < QR_KC; ++k) x[k] = (ok && pcs[k] >= 0) ? cdfl_ld(X + i * n + pcs[k]) : cdfl_zero();
+        for (int kk = 0; kk < QR_KS; ++kk) { accD[kk] = cdfl_zero(); accN[kk] = 0.f; }
+        auto upd1 = [&](cdfl x, const cdfl& vi, const cdfl& wk) {
+            x.re = dfl_fma(dfl_neg(vi.re), wk.re, dfl_fma(vi.im, wk.im, x.re));
+            x.im = dfl_fma(dfl_neg(vi.re), wk.im, dfl_fma(dfl_neg(vi.im), wk.re, x.im));
+            return x;
         };
-        auto row = [&](int64_t i, const cdfl& vi, cdfl* x) {
-            if (upd && i < r1) {
+        for (int64_t i = max(r0, (int64_t)jp1) + rg; i < r1; i += 8) {
+            const cdfl vi = upd ? cdfl_unpack(pin[i]) : cdfl_zero();
+            cdfl x[QR_KS];
 #pragma unroll
-                for (int k = 0; k < QR_KC; ++k) {
-                    if (pcs[k] < 0) continue;
-                    const cdfl wk = cdfl_unpack(sW[jp1 + lane + 32 * k]);
-                    x[k].re = dfl_fma(dfl_neg(vi.re), wk.re, dfl_fma(vi.im, wk.im, x[k].re));
-                    x[k].im = dfl_fma(dfl_neg(vi.re), wk.im, dfl_fma(dfl_neg(vi.im), wk.re, x[k].im));
-                    X[i * n + pcs[k]] = cdfl_pack(x[k]);
+            for (int kk = 0; kk < QR_KS; ++kk) x[kk] = (pcs[kk] >= 0) ? cdfl_ld(X + i * n + pcs[kk]) : cdfl_zero();
+            cdfl xo = cdfl_zero();
+            if (cgp == 1 && pn >= 0) xo = cdfl_ld(X + i * n + pn);
+            if (upd) {
+#pragma unroll
+                for (int kk = 0; kk < QR_KS; ++kk) {
+                    if (pcs[kk] < 0) continue;
+                    x[kk] = upd1(x[kk], vi, cdfl_unpack(sW[jp1 + lane + 32 * (2 * kk + cgp)]));
+                    if (pcs[kk] != pn) X[i * n + pcs[kk]] = cdfl_pack(x[kk]);
                 }
+                if (cgp == 1 && pn >= 0) xo = upd1(xo, vi, wn);
             }
-            // the next pivot column's new value (position jp1 = lane 0, slot 0)
-            const cdfl p = {{__shfl_sync(0xffffffffu, x[0].re.hi, 0), __shfl_sync(0xffffffffu, x[0].re.lo, 0)},
-                            {__shfl_sync(0xffffffffu, x[0].im.hi, 0), __shfl_sync(0xffffffffu, x[0].im.lo, 0)}};
-#pragma unroll
-            for (int k = 0; k < QR_KC; ++k) {
-                if (pcs[k] < 0) continue;
-                cdfl_conj_fma(accD[k], p, x[k]);
-                accN[k] = fmaf(x[k].re.hi, x[k].re.hi, fmaf(x[k].im.hi, x[k].im.hi, accN[k]));
+            cdfl p;
+            if (cgp == 0) {
+                p = {{__shfl_sync(0xffffffffu, x[0].re.hi, 0), __shfl_sync(0xffffffffu, x[0].re.lo, 0)},
+                     {__shfl_sync(0xffffffffu, x[0].im.hi, 0), __shfl_sync(0xffffffffu, x[0].im.lo, 0)}};
+                if (lane == 0 && pn >= 0) pout[i] = cdfl_pack(p);
+            } else {
+                p = xo;
             }
-        };
-        int64_t i = max(r0, (int64_t)jp1) + rg;
-        if (i < r1) {
-            cdfl va, vb, xa[QR_KC], xb[QR_KC];
-            load(i, va, xa);
-            load(i + 8, vb, xb);
-            for (; i < r1; i += 16) {
-                cdfl na, nb, ya[QR_KC], yb[QR_KC];
-                load(i + 16, na, ya);
-                load(i + 24, nb, yb);
-                row(i, va, xa);
-                row(i + 8, vb, xb);
-                va = na; vb = nb;
 #pragma unroll
-                for (int k = 0; k < QR_KC; ++k) { xa[k] = ya[k]; xb[k] = yb[k]; }
+            for (int kk = 0; kk < QR_KS; ++kk) {
+                if (pcs[kk] < 0) continue;
+                cdfl_conj_fma(accD[kk], p, x[kk]);
+                accN[kk] = fmaf(x[kk].re.hi, x[kk].re.hi, fmaf(x[kk].im.hi, x[kk].im.hi, accN[kk]));
             }
         }
 #pragma unroll
-        for (int k = 0; k < QR_KC; ++k) {
-            wbD[rg * QR_NP + lane + 32 * k] = cdfl_pack(accD[k]);
-            wbN[rg * QR_NP + lane + 32 * k] = accN[k];
+        for (int kk = 0; kk < QR_KS; ++kk) {
+            const int k = 2 * kk + cgp;
+            if (k >= QR_KC) continue;
+            wbD[rg * QR_NP + lane + 32 * k] = cdfl_pack(accD[kk]);
+            wbN[rg * QR_NP + lane + 32 * k] = accN[kk];
         }
         reduce_warps(n - jp1);
     };
@@ -801,12 +806,12 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
             const bool better = oi < n && (bi == n || ox > best.x || (ox == best.x && (oy > best.y || (oy == best.y && oi < bi))));
             if (better) { best = make_float2(ox, oy); bi = oi; }
         }
-        if (lane == 0) { s_best[rg] = best; s_bidx[rg] = bi; }
+        if (lane == 0) { s_best[warp] = best; s_bidx[warp] = bi; }
         __syncthreads();
         if (tid == 0) {
             float2 b2 = s_best[0];
             int i2 = s_bidx[0];
-            for (int q = 1; q < 8; ++q) {
+            for (int q = 1; q < QR_NT / 32; ++q) {
                 const float2 v = s_best[q];
                 const int qi = s_bidx[q];
                 if (qi < n && (i2 == n || v.x > b2.x || (v.x == b2.x && (v.y > b2.y || (v.y == b2.y && qi < i2))))) {
@@ -822,22 +827,28 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
     // ---- start: window exponent from the largest partial column norm, then the norms,
     // the first pivot and the sums of step 0
     {
-        int pcs[QR_KC];
-        float acc[QR_KC];
+        int pcs[QR_KS];
+        float acc[QR_KS];
 #pragma unroll
-        for (int k = 0; k < QR_KC; ++k) { pcs[k] = (lane + 32 * k < n) ? lane + 32 * k : -1; acc[k] = 0.f; }
+        for (int kk = 0; kk < QR_KS; ++kk) {
+            const int k = 2 * kk + cgp, c = lane + 32 * k;
+            pcs[kk] = (k < QR_KC && c < n) ? c : -1;
+            acc[kk] = 0.f;
+        }
         for (int64_t i = r0 + rg; i < r1; i += 8) {
 #pragma unroll
-            for (int k = 0; k < QR_KC; ++k)
-                if (pcs[k] >= 0) {
-                    const float4 x = X[i * n + pcs[k]];
-                    acc[k] = fmaf(x.x, x.x, fmaf(x.z, x.z, acc[k]));
+            for (int kk = 0; kk < QR_KS; ++kk)
+                if (pcs[kk] >= 0) {
+                    const float4 x = X[i * n + pcs[kk]];
+                    acc[kk] = fmaf(x.x, x.x, fmaf(x.z, x.z, acc[kk]));
                 }
         }
 #pragma unroll
-        for (int k = 0; k < QR_KC; ++k) {
+        for (int kk = 0; kk < QR_KS; ++kk) {
+            const int k = 2 * kk + cgp;
+            if (k >= QR_KC) continue;
             wbD[rg * QR_NP + lane + 32 * k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            wbN[rg * QR_NP + lane + 32 * k] = acc[k];
+            wbN[rg * QR_NP + lane + 32 * k] = acc[kk];
         }
         reduce_warps(n);
         int mx = 0;
@@ -869,7 +880,7 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
         if (tid == 0 && q < n && q != 0) { const int t = cmap[0]; cmap[0] = cmap[q]; cmap[q] = t; }
         __syncthreads();
     }
-    pass(0, false, 0);
+    pass(0, false);
     publish(0, n, 0, eb);
     if (!grid_barrier(bar, G, err)) return;
 
@@ -885,7 +896,8 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
             const dfl dr = qx_to_dfl(Lv, eb), di = qx_to_dfl(Lv + 3, eb), nn = qx_to_dfl(Lv + 6, eb);
             sD[c] = cdfl_pack({dr, di});
             sN[c] = make_float2(nn.hi, nn.lo);
-            sRow[c] = __ldcg(X + (int64_t)j * n + pc);
+            // row j; the pivot's entry from Pc (the previous pass kept that column there)
+            sRow[c] = (c == j) ? __ldcg(Pc + (size_t)(j & 1) * N + j) : __ldcg(X + (int64_t)j * n + pc);
         }
         if (blockIdx.x == 0) {
             unsigned long long* z = lim + (size_t)((j + 2) % 3) * LS;
@@ -920,7 +932,6 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
             if (own_j) R[j + (int64_t)j * n] = cdfl_to(alpha);
         }
         __syncthreads();
-        const int pj = cmap[j];
         {
             // (C) w, row j of R, downdated norms
             const cdfl alpha = cdfl_unpack(s_ref[0]), vj = cdfl_unpack(s_ref[1]);
@@ -950,7 +961,7 @@ __global__ void __launch_bounds__(256, 1) k_house_qr_df(float4* X, int64_t N, in
         if (j + 1 >= n) break;
         // (D) update this CTA's rows and accumulate the sums of step j + 1
         if (max(r0, (int64_t)(j + 1)) < r1) {
-            pass(j + 1, true, pj);
+            pass(j + 1, true);
             publish(j + 1, n - j - 1, (j + 1) % 3, eb);
         }
         if (!grid_barrier(bar, G, err)) return;
@@ -978,14 +989,17 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* 
         BEM_CUDA(h, cudaMallocAsync((void**)&lim, sizeof(unsigned long long) * lim_words, h->stream));
         BEM_CUDA(h, cudaMemsetAsync(lim, 0, sizeof(unsigned long long) * lim_words, h->stream));
         int* emax = reinterpret_cast<int*>(lim + 27 * (size_t)n);
+        float4* Pc = nullptr;                   // the next pivot column, two buffers
+        BEM_CUDA(h, cudaMallocAsync((void**)&Pc, sizeof(float4) * 2 * (size_t)N, h->stream));
         const int64_t cnt = N * (int64_t)n;
         BEM_TIMED(h, "k_to_dfl", (k_to_dfl<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(reinterpret_cast<float4*>(X), cnt)));
         BEM_LAUNCH(h, "k_to_dfl");
         float4* Xf = reinterpret_cast<float4*>(X);
-        void* args_df[] = {&Xf, &N, &n, &R, &perm, &lim, &emax, &h->bar, &h->dev_err};
+        void* args_df[] = {&Xf, &N, &n, &R, &perm, &lim, &emax, &Pc, &h->bar, &h->dev_err};
         const size_t smem = (size_t)QR_NP * (8 * sizeof(float4) + 8 * sizeof(float) + 3 * sizeof(float4) + sizeof(float2));
-        BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr_df, G, 256, args_df, "k_house_qr_df", smem));
+        BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr_df, G, QR_NT, args_df, "k_house_qr_df", smem));
         cudaFreeAsync(lim, h->stream);
+        cudaFreeAsync(Pc, h->stream);
         return st;
     }
     double* partC = nullptr;
@@ -1014,6 +1028,37 @@ __device__ __forceinline__ void tourney(int round, int idx, int np, int& p, int&
     auto pos = [&](int k) { return (k == 0) ? 0 : ((round + k - 1) % (np - 1)) + 1; };
     p = pos(idx);
     q = pos(np - 1 - idx);
+}
+
+// Rotation of a column pair from A = |x|^2, B = |y|^2, G = x^H y (double-float sums), on
+// values scaled by 2^-E with 2^E near max(A, B) (|G|^2 <= A B keeps everything below 1).
+// Returns 0 for a converged pair (|G| <= 1e-14 |x| |y|), 1 for a rotation, 2 for a rotation
+// with |G| > 1e-8 |x| |y| (a sweep with none of those is the last one: Jacobi's quadratic
+// convergence leaves |G| near 1e-16 after it).  c, sem = s e^{-i phi}, sep = s e^{i phi}.
+__device__ __forceinline__ int jac_rotation(const dfl sm[4], dfl& c, cdfl& sem, cdfl& sep) {
+    const float mx = fmaxf(sm[0].hi, sm[1].hi);
+    const float sc = (mx > 0.f) ? __int_as_float((254 - ((__float_as_int(mx) >> 23) & 255)) << 23) : 1.f;
+    const dfl A = dfl_scale(sm[0], sc), Bv = dfl_scale(sm[1], sc);
+    const dfl GR = dfl_scale(sm[2], sc), GI = dfl_scale(sm[3], sc);
+    const dfl ag2 = dfl_fma(GR, GR, dfl_mul(GI, GI));
+    const dfl ab = dfl_mul(A, Bv);
+    if (!(ag2.hi > 0.f) || ag2.hi <= 1e-28f * ab.hi) return 0;
+    const dfl rag = dfl_rsqrt(ag2);                       // 1/|g|
+    const dfl zeta = dfl_scale(dfl_mul(dfl_sub(Bv, A), rag), 0.5f);
+    dfl t;
+    if (fabsf(zeta.hi) > 1e15f) {
+        t = dfl_div(dfl{0.5f, 0.f}, zeta);               // 1/(2 zeta)
+    } else {
+        const dfl den = dfl_add(dfl{fabsf(zeta.hi), zeta.hi < 0.f ? -zeta.lo : zeta.lo},
+                                dfl_sqrt(dfl_fma(zeta, zeta, dfl{1.f, 0.f})));
+        t = dfl_div(dfl{zeta.hi >= 0.f ? 1.f : -1.f, 0.f}, den);
+    }
+    c = dfl_rsqrt(dfl_fma(t, t, dfl{1.f, 0.f}));
+    const dfl sr = dfl_mul(dfl_mul(c, t), rag);
+    const dfl srGR = dfl_mul(sr, GR), srGI = dfl_mul(sr, GI);
+    sem = {srGR, dfl_neg(srGI)};
+    sep = {srGR, srGI};
+    return (ag2.hi > 1e-16f * ab.hi) ? 2 : 1;
 }
 
 // One-sided Jacobi on the columns of X (n x n, column-major).  Applied to X = R^H it
@@ -1099,45 +1144,22 @@ __global__ void __launch_bounds__(JAC_NT) k_jacobi(float4* X, int n, int* ver, i
                         for (int k = 0; k < 4; ++k) red[wid][k] = make_float2(v4[k].hi, v4[k].lo);
                     __syncthreads();
                     if (tid == 0) {
-                        // rotation scalars in double-float, on values scaled by 2^-E with 2^E
-                        // near max(A, B) (|g|^2 <= A B keeps everything below 1)
                         dfl sm[4];
                         for (int k = 0; k < 4; ++k) {
                             dfl t = dfl_mk(red[0][k]);
                             for (int w = 1; w < JAC_NT / 32; ++w) t = dfl_add(t, dfl_mk(red[w][k]));
                             sm[k] = t;
                         }
-                        const float mx = fmaxf(sm[0].hi, sm[1].hi);
-                        const float sc = (mx > 0.f) ? __int_as_float((254 - ((__float_as_int(mx) >> 23) & 255)) << 23) : 1.f;
-                        const dfl A = dfl_scale(sm[0], sc), Bv = dfl_scale(sm[1], sc);
-                        const dfl GR = dfl_scale(sm[2], sc), GI = dfl_scale(sm[3], sc);
-                        const dfl ag2 = dfl_fma(GR, GR, dfl_mul(GI, GI));
-                        // converged pair: |x^H y| <= 1e-14 |x| |y|
-                        const dfl ab = dfl_mul(A, Bv);
-                        int rot = (ag2.hi > 0.f) && !(ag2.hi <= 1e-28f * ab.hi);
+                        dfl c;
+                        cdfl sem, sep;
+                        const int rot = jac_rotation(sm, c, sem, sep);
                         if (rot) {
-                            // a sweep whose rotations all have |g| <= 1e-8 |x| |y| is the last
-                            // one: Jacobi's quadratic convergence leaves |g| near 1e-16 after it
-                            if (ag2.hi > 1e-16f * ab.hi) flags[sweep] = 1;
-                            const dfl rag = dfl_rsqrt(ag2);                       // 1/|g|
-                            const dfl zeta = dfl_scale(dfl_mul(dfl_sub(Bv, A), rag), 0.5f);
-                            dfl t;
-                            if (fabsf(zeta.hi) > 1e15f) {
-                                t = dfl_div(dfl{0.5f, 0.f}, zeta);               // 1/(2 zeta)
-                            } else {
-                                const dfl den = dfl_add(dfl{fabsf(zeta.hi), zeta.hi < 0.f ? -zeta.lo : zeta.lo},
-                                                        dfl_sqrt(dfl_fma(zeta, zeta, dfl{1.f, 0.f})));
-                                t = dfl_div(dfl{zeta.hi >= 0.f ? 1.f : -1.f, 0.f}, den);
-                            }
-                            const dfl c = dfl_rsqrt(dfl_fma(t, t, dfl{1.f, 0.f}));
-                            const dfl sr = dfl_mul(dfl_mul(c, t), rag);
-                            const dfl srGR = dfl_mul(sr, GR), srGI = dfl_mul(sr, GI);
-                            // c, s e^{-i phi}, s e^{i phi}
+                            if (rot == 2) flags[sweep] = 1;
                             s_rotp[0] = make_float2(c.hi, c.lo);
-                            s_rotp[1] = make_float2(srGR.hi, srGR.lo);
-                            s_rotp[2] = make_float2(-srGI.hi, -srGI.lo);
-                            s_rotp[3] = make_float2(srGR.hi, srGR.lo);
-                            s_rotp[4] = make_float2(srGI.hi, srGI.lo);
+                            s_rotp[1] = make_float2(sem.re.hi, sem.re.lo);
+                            s_rotp[2] = make_float2(sem.im.hi, sem.im.lo);
+                            s_rotp[3] = make_float2(sep.re.hi, sep.re.lo);
+                            s_rotp[4] = make_float2(sep.im.hi, sep.im.lo);
                         }
                         s_rot = rot;
                     }
