@@ -42,7 +42,7 @@ FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 ASM_OPS_PER_POINT = 351
 # DRAM bytes (read + write) per launch from ncu captures of the kernels as they stand
 # (absent = not captured since the kernel last changed); the summaries are under profiles/
-TRAFFIC_BYTES = {"tc_rhs_SY": 18.064e9 + 0.529e9, "k_assemble": 0.0301e9 + 8.548e9}
+TRAFFIC_BYTES = {"k_assemble": 0.0301e9 + 8.548e9}
 
 
 def _peaks():
@@ -74,12 +74,14 @@ def roofline(rep, args, n_modes, r, quad_points):
                 "unit": "TOP/s (FP32 pipe)", "frac": ach / FP32_PEAK_TOPS, "traffic": TRAFFIC_BYTES.get(dom_name),
                 "units_per_launch": quad_points, "ops_per_unit": ASM_OPS_PER_POINT,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
-    fl = tc_gemm_flops(dom_name, args.N, args.nrhs, n_modes, r, 6)
+    # digit slices per operand: 6, the right-hand-side product 5 (bem_options.rhs_slices default)
+    S = 5 if dom_name == "tc_rhs_SY" else 6
+    fl = tc_gemm_flops(dom_name, args.N, args.nrhs, n_modes, r, S)
     if fl is not None:
         peak = pk.get("bf16_tflops_sustained", 1700.0)
         ach = fl / avg_s / 1e12
         return {"kernel": dom_name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": TRAFFIC_BYTES.get(dom_name),
+                "frac": ach / peak, "traffic": TRAFFIC_BYTES.get(dom_name), "slice_pairs": S * (S + 1) // 2,
                 "peak_source": "of measured (bf16_tflops_sustained)" if "bf16_tflops_sustained" in pk
                 else "of fallback (1.7 PFLOP/s sustained)"}
     return {"kernel": dom_name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,

@@ -75,6 +75,11 @@ typedef struct {
     double refine_rtol;       /* mixed path: target max relative residual (default 1e-10)  */
     int max_refine;           /* mixed path: maximum refinement sweeps (default 6)         */
     int split_slices;         /* mixed path: bf16 slices per operand, 0 = default (6)      */
+    int rhs_slices;           /* mixed path: slices used by the right-hand-side product S Y:
+                                 0 = default, one fewer than split_slices (5).  Its error (about
+                                 5e-11 of max|S Y| with 5 slices) reaches the solution unrefined
+                                 but far inside the mixed path's 1e-8 accuracy bar; the filter
+                                 and compression products keep all slices                     */
 } bem_options;
 
 typedef struct {

