@@ -735,8 +735,8 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     for (int o = 16; o > 0; o >>= 1) npts += __shfl_xor_sync(0xffffffffu, npts, o);
     if ((threadIdx.x & 31) == 0 && npts) atomicAdd(p.qpts, (unsigned long long)npts);
     const bool mirror = (ti != tj);
-    // entry (i0 + il, j0 + jl) of S and N, written at (i, j), or at (j, i) for the mirror
-    auto entry = [&](int il, int jl, bool transposed, double2& ds, double2& dw) -> bool {
+    // entry (i0 + il, j0 + jl) of S and N, written at (i, j)
+    auto entry = [&](int il, int jl, double2& ds, double2& dw) -> bool {
         const int i = i0 + il, j = j0 + jl;
         if (i >= N || j >= N) return false;
         cdfl sv = cdfl_zero(), wv = cdfl_zero();
@@ -758,32 +758,39 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
                 }
             }
         }
-        const int64_t off = transposed ? ((int64_t)j + (int64_t)i * p.ld) : ((int64_t)i + (int64_t)j * p.ld);
+        const int64_t off = (int64_t)i + (int64_t)j * p.ld;
         ds = cdfl_to(sv);
         dw = cdfl_to(wv);
         if (p.S) p.S[off] = ds;
         if (p.W) p.W[off] = dw;
         return true;
     };
-    // Direct half: one warp per tile column, lane = row.  When asked, the largest exponent
-    // fields of the written entries are gathered per column (a warp reduction) and, for the
-    // mirror, per row (the slices of the split products are scaled per column of S and N;
-    // N's band is left out).
+    // Direct half: one warp per tile column, lane = row; the entries stay in registers for
+    // the mirror.  When asked, the largest exponent fields of the written entries are
+    // gathered per column (a warp reduction) and, for the mirror, per row (the slices of the
+    // split products are scaled per column of S and N; N's band is left out).
     const bool track = p.rexpS != nullptr;
     __shared__ int eRow[2][32];
     if (threadIdx.x < 64) eRow[threadIdx.x >> 5][threadIdx.x & 31] = 0;
     __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int NQ = (T + 7) / 8;                      // columns per warp (8 warps)
+    double2 keepS[NQ], keepW[NQ];
     {
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
         int rS = 0, rW = 0;
-        for (int jl = wid; jl < T; jl += nw) {
-            double2 ds, dw;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int jl = wid + 8 * q;
+            if (jl >= T) break;
+            double2 ds = make_double2(0.0, 0.0), dw = make_double2(0.0, 0.0);
             int fs = 0, fw = 0;
-            if (lane < T && entry(lane, jl, false, ds, dw) && track) {
+            if (lane < T && entry(lane, jl, ds, dw) && track) {
                 int d = lane + i0 - (jl + j0); if (d < 0) d = -d;
                 fs = max(exp_field_of(ds.x), exp_field_of(ds.y));
                 fw = (min(d, N - d) <= p.wband) ? 0 : max(exp_field_of(dw.x), exp_field_of(dw.y));
             }
+            keepS[q] = ds;
+            keepW[q] = dw;
             if (track) {
                 const int cs = (int)__reduce_max_sync(0xffffffffu, (unsigned)fs);
                 const int cw = (int)__reduce_max_sync(0xffffffffu, (unsigned)fw);
@@ -800,19 +807,33 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
             atomicMax(&eRow[1][lane], rW);
         }
     }
-    if (track && mirror) {
+    __syncthreads();                                     // sI is no longer read
+    if (track && mirror && threadIdx.x < 2 * T) {
+        const int m = threadIdx.x / T, l = threadIdx.x % T;
+        if (i0 + l < N) atomicMax((m ? p.rexpW : p.rexpS) + i0 + l, eRow[m][l]);
+    }
+    // mirror half: the same entries staged through shared memory (over sI), stored transposed
+    if (mirror) {
+        double2* stage = reinterpret_cast<double2*>(sI);   // [(jl T + il) 2 + (0: S, 1: N)]
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int jl = wid + 8 * q;
+            if (jl >= T) break;
+            if (lane < T) {
+                stage[(jl * T + lane) * 2] = keepS[q];
+                stage[(jl * T + lane) * 2 + 1] = keepW[q];
+            }
+        }
         __syncthreads();
-        if (threadIdx.x < 2 * T) {
-            const int m = threadIdx.x / T, l = threadIdx.x % T;
-            if (i0 + l < N) atomicMax((m ? p.rexpW : p.rexpS) + i0 + l, eRow[m][l]);
+        for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+            const int il = idx / T, jl = idx % T;
+            const int i = i0 + il, j = j0 + jl;
+            if (i >= N || j >= N) continue;
+            const int64_t off = (int64_t)j + (int64_t)i * p.ld;
+            if (p.S) p.S[off] = stage[(jl * T + il) * 2];
+            if (p.W) p.W[off] = stage[(jl * T + il) * 2 + 1];
         }
     }
-    // mirror half
-    if (mirror)
-        for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-            double2 ds, dw;
-            entry(idx / T, idx % T, true, ds, dw);
-        }
 }
 
 template <int T, bool WD>
