@@ -1092,8 +1092,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 __global__ void __launch_bounds__(JAC_NT) k_jacobi(float4* X, int n, int* ver, int* flags, int max_sweeps,
                                                    unsigned* bar, int* err) {
     __shared__ float2 red[JAC_NT / 32][4];
-    __shared__ int s_ok, s_rot;
-    __shared__ float2 s_rotp[5];                  // c, sem (re, im), sep (re, im) as double-float
+    __shared__ int s_ok;
     const unsigned G = gridDim.x;
     const int np = n + (n & 1);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1147,31 +1146,19 @@ __global__ void __launch_bounds__(JAC_NT) k_jacobi(float4* X, int n, int* ver, i
                     if (lane == 0)
                         for (int k = 0; k < 4; ++k) red[wid][k] = make_float2(v4[k].hi, v4[k].lo);
                     __syncthreads();
-                    if (tid == 0) {
-                        dfl sm[4];
-                        for (int k = 0; k < 4; ++k) {
-                            dfl t = dfl_mk(red[0][k]);
-                            for (int w = 1; w < JAC_NT / 32; ++w) t = dfl_add(t, dfl_mk(red[w][k]));
-                            sm[k] = t;
-                        }
-                        dfl c;
-                        cdfl sem, sep;
-                        const int rot = jac_rotation(sm, c, sem, sep);
-                        if (rot) {
-                            if (rot == 2) flags[sweep] = 1;
-                            s_rotp[0] = make_float2(c.hi, c.lo);
-                            s_rotp[1] = make_float2(sem.re.hi, sem.re.lo);
-                            s_rotp[2] = make_float2(sem.im.hi, sem.im.lo);
-                            s_rotp[3] = make_float2(sep.re.hi, sep.re.lo);
-                            s_rotp[4] = make_float2(sep.im.hi, sep.im.lo);
-                        }
-                        s_rot = rot;
+                    // every thread sums the warps' partials in the same order and forms the
+                    // same rotation (no second barrier, no broadcast)
+                    dfl sm[4];
+                    for (int k = 0; k < 4; ++k) {
+                        dfl t = dfl_mk(red[0][k]);
+                        for (int w = 1; w < JAC_NT / 32; ++w) t = dfl_add(t, dfl_mk(red[w][k]));
+                        sm[k] = t;
                     }
-                    __syncthreads();
-                    if (s_rot) {
-                        const dfl c = dfl_mk(s_rotp[0]);
-                        const cdfl sem = {dfl_mk(s_rotp[1]), dfl_mk(s_rotp[2])};
-                        const cdfl sep = {dfl_mk(s_rotp[3]), dfl_mk(s_rotp[4])};
+                    dfl c;
+                    cdfl sem, sep;
+                    const int rot = jac_rotation(sm, c, sem, sep);
+                    if (rot == 2 && tid == 0) flags[sweep] = 1;
+                    if (rot) {
 #pragma unroll
                         for (int e = 0; e < EPT; ++e) {
                             const int i = tid + JAC_NT * e;
@@ -1189,7 +1176,7 @@ __global__ void __launch_bounds__(JAC_NT) k_jacobi(float4* X, int n, int* ver, i
                 }
                 __syncthreads();              // the pair's stores precede its release
                 if (tid == 0) {
-                    __threadfence();
+                    // the release orders the CTA's stores (made cumulative by the barrier above)
                     if (p < n) st_release(ver + p, target + 1);
                     if (q < n) st_release(ver + q, target + 1);
                 }
