@@ -54,14 +54,17 @@ def _peaks():
 
 
 def tc_gemm_flops(name, N, nrhs, n_modes, r, S):
-    """bf16 tensor flops of one split-slice launch: S(S+1)/2 slice pairs, each a real GEMM
-    of the complex product in 2x2 real block form (M x 2Nc x 2K real -> 8 M Nc K flops)."""
+    """bf16 tensor flops of one split-slice launch: S(S+1)/2 slice pairs, each the real
+    products of the parts (2 M Nc K flops per real product)."""
     dims = {"tc_rhs_SY": (N, nrhs, N), "tc_filter_QtS": (n_modes, N, N),
             "tc_filter_YN": (n_modes, N, N)}
     if name not in dims:
         return None
     M, Nc, K = dims[name]
-    return S * (S + 1) / 2 * 8.0 * M * Nc * K
+    # planar parts: complex x complex = four real products, complex x real (the real
+    # Fourier basis Q of the filter) = two
+    parts = 2.0 if name == "tc_filter_QtS" else 4.0
+    return S * (S + 1) / 2 * 2.0 * parts * M * Nc * K
 
 
 def roofline(rep, args, n_modes, r, quad_points):

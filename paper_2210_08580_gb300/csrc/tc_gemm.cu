@@ -138,7 +138,9 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
 }
 
 struct TcGemmArgs {
-    int M, Ncols;            // rows of C', columns of C' (= 2 m)
+    int M, Ncols;            // rows of the A and B part matrices (tiles run over these)
+    int Ml, ml;              // logical rows / columns of the complex result
+    int aC, bC;              // A / B complex (two part rows each) or real
     int nkb;                 // K' blocks of 32
     int S;                   // slices per operand
     const int* ea;           // M row exponents
@@ -298,30 +300,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         asm volatile("bar.sync 1, 256;" ::: "memory");          // the 8 epilogue warps
         if (ok) {
+            // combine the part products: complex A and B: re = RR - II, im = RI + IR; one
+            // complex operand: its two part rows (or columns) are re and im
             const int et = threadIdx.x - 64;                       // 0..255
-            const int ncw = min(TC_BN, p.Ncols - n0) >> 1;         // complex columns in this tile
-            const int mrows = min(TC_BM, p.M - m0);
+            const int rdiv = p.aC ? 2 : 1, cdiv = p.bC ? 2 : 1;
+            const int NLR = TC_BM / rdiv, NLC = TC_BN / cdiv;      // logical outputs per tile
+            const int lr0 = m0 / rdiv, lc0 = n0 / cdiv;
+            const int nlr = min(NLR, p.Ml - lr0), nlc = min(NLC, p.ml - lc0);
+            auto V = [&](int rr, int cc) {
+                const float2 v = stash[rr * (TC_BN + 1) + cc];
+                return dfl{v.x, v.y};
+            };
+            const bool plain = (p.alpha == 1.0 && p.beta == 0.0);
 #pragma unroll 1
-            for (int idx = et; idx < TC_BM * (TC_BN / 2); idx += 256) {
-                int r_, cw;
-                if (p.transposed) { cw = idx % (TC_BN / 2); r_ = idx / (TC_BN / 2); }
-                else { r_ = idx % TC_BM; cw = idx / TC_BM; }
-                if (r_ >= mrows || cw >= ncw) continue;
-                const int gi = m0 + r_, gc = n0 + 2 * cw;
-                const float2 a = stash[r_ * (TC_BN + 1) + 2 * cw];
-                const float2 b = stash[r_ * (TC_BN + 1) + 2 * cw + 1];
-                // 2^(e_i + f_j - 14) built from its exponent bits (normal range)
-                const long long eb = (long long)(1023 + p.ea[gi] + p.eb[gc] - 14);
-                const double sc = __longlong_as_double(eb << 52);
-                const double re = ((double)a.x + (double)a.y) * sc;
-                const double im = ((double)b.x + (double)b.y) * sc;
-                const int j = gc >> 1;
+            for (int idx = et; idx < NLR * NLC; idx += 256) {
+                int lr, lc;
+                if (p.transposed) { lc = idx % NLC; lr = idx / NLC; }
+                else { lr = idx % NLR; lc = idx / NLR; }
+                if (lr >= nlr || lc >= nlc) continue;
+                const int gi = lr0 + lr, gj = lc0 + lc;
+                dfl dre, dim;
+                if (p.aC && p.bC) {
+                    dre = dfl_sub(V(2 * lr, 2 * lc), V(2 * lr + 1, 2 * lc + 1));
+                    dim = dfl_add(V(2 * lr, 2 * lc + 1), V(2 * lr + 1, 2 * lc));
+                } else if (p.aC) {
+                    dre = V(2 * lr, lc);
+                    dim = V(2 * lr + 1, lc);
+                } else {
+                    dre = V(lr, 2 * lc);
+                    dim = V(lr, 2 * lc + 1);
+                }
+                // times 2^(e_i + f_j - 14), exactly, on the exponent fields (normal values)
+                const long long sh = (long long)(p.ea[gi] + p.eb[gj] - 14) << 52;
+                const double r0 = dfl_to(dre), i0 = dfl_to(dim);
+                const long long br = __double_as_longlong(r0), bi = __double_as_longlong(i0);
+                const double re = (br & 0x7FF0000000000000LL) ? __longlong_as_double(br + sh) : 0.0;
+                const double im = (bi & 0x7FF0000000000000LL) ? __longlong_as_double(bi + sh) : 0.0;
                 if (p.part) {
-                    p.part[((int64_t)blockIdx.y * (p.Ncols >> 1) + j) * p.M + gi] = make_double2(re, im);
+                    p.part[((int64_t)blockIdx.y * p.ml + gj) * p.Ml + gi] = make_double2(re, im);
                     continue;
                 }
-                double2* o = p.transposed ? (p.out + (int64_t)j + (int64_t)gi * p.ldo)
-                                          : (p.out + (int64_t)gi + (int64_t)j * p.ldo);
+                double2* o = p.transposed ? (p.out + (int64_t)gj + (int64_t)gi * p.ldo)
+                                          : (p.out + (int64_t)gi + (int64_t)gj * p.ldo);
+                if (plain) { *o = make_double2(re, im); continue; }
                 double2 val = make_double2(p.alpha * re, p.alpha * im);
                 if (p.beta != 0.0) {
                     const double2 old = *o;
@@ -386,7 +407,7 @@ __global__ void k_exp_from_fields(const int* fields, int64_t M, int* e) {
 }
 
 // B column exponents: B_op[k, j] = src[k*sb_k + j*sb_j] (complex, or real when is_real);
-// columns 2j and 2j+1 of B' share f_j.  One CTA per column, four loads in flight per thread.
+// f_j scales both part rows of column j.  One CTA per column, four loads in flight per thread.
 __global__ void __launch_bounds__(256) k_exp_cols(const void* src, int is_real, int64_t K, int64_t m, int64_t sb_k,
                                                   int64_t sb_j, int* f) {
     __shared__ int red[8];
@@ -410,9 +431,7 @@ __global__ void __launch_bounds__(256) k_exp_cols(const void* src, int is_real, 
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int q = 1; q < (int)(blockDim.x >> 5); ++q) mx = max(mx, red[q]);
-        const int ex = mx ? mx - 1022 : 0;
-        f[2 * j] = ex;
-        f[2 * j + 1] = ex;
+        f[j] = mx ? mx - 1022 : 0;
     }
 }
 
@@ -472,79 +491,81 @@ __device__ __forceinline__ void split_digits(double val, int e, int S, uint32_t*
     d[0] = digit_bf16((int)X, 0);
 }
 
-// A' slices: out[s][i][kp], kp = 2k + c, padded with zeros to Kp.  Each complex entry (k)
-// becomes the (re, im) pair of every slice as one bf16x2.  conj negates Im.
-#define SLICE_VEC 4                  // complex entries per thread in the slicers
-__global__ void k_slice_A(const void* src, int is_real, int conj, int64_t M, int64_t K, int64_t Kp, int64_t sa_i,
-                          int64_t sa_k, int band, const int* e, int S, __nv_bfloat16* out) {
-    // SLICE_VEC consecutive k per thread: Kp / 2 is a multiple of 32, so a group never
-    // straddles a row and each slice gets one 16-byte store
-    const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * SLICE_VEC;
-    const int64_t i = blockIdx.y;
-    if (2 * k0 >= Kp || i >= M) return;
-    const int ei = e[i];
-    uint32_t packed[TC_SMAX][SLICE_VEC];
-#pragma unroll
-    for (int v = 0; v < SLICE_VEC; ++v) {
-        const int64_t k = k0 + v;
-        double re = 0.0, im = 0.0;
-        if (k < K && !in_band(i, k, K, band)) {
-            if (is_real) {
-                re = ((const double*)src)[i * sa_i + k * sa_k];
-            } else {
-                const double2 x = ((const double2*)src)[i * sa_i + k * sa_k];
-                re = x.x; im = conj ? -x.y : x.y;
-            }
-        }
-        uint32_t dr[TC_SMAX], di[TC_SMAX];
-        split_digits(re, ei, S, dr);
-        split_digits(im, ei, S, di);
-#pragma unroll
-        for (int s = 0; s < TC_SMAX; ++s) packed[s][v] = dr[s] | (di[s] << 16);   // (re, im) as bf16x2
-    }
-    uint4* o = reinterpret_cast<uint4*>(out + i * Kp + 2 * k0);
-    const size_t stride16 = (size_t)M * Kp / 8;     // one slice, in 16-byte units
+// Planar slices.  A operand (M x K): a complex row i becomes rows 2i (real part) and 2i+1
+// (imaginary part, negated when conj), a real row i stays row i; B operand (K x m) likewise
+// by columns (stored K-major: out[s][row][k]).  The product of the part matrices gives the
+// four (or two) real products the epilogue combines, so a real operand costs half of a
+// complex one.  Each thread takes SLICE_VEC consecutive k (Kp is a multiple of 32, so a
+// group never straddles a row) and writes 16 bytes per part row and slice.
+#define SLICE_VEC 8
+// digits of SLICE_VEC values (one part row) packed as bf16 pairs, then one 16-byte store per slice
+__device__ __forceinline__ void slice_part(const double* v, int e, int S, __nv_bfloat16* out, int64_t row, int64_t Kp,
+                                           int64_t k0, size_t stride) {
+    uint32_t w[TC_SMAX][SLICE_VEC / 2];
 #pragma unroll
     for (int s = 0; s < TC_SMAX; ++s)
-        if (s < S) o[s * stride16] = make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
+#pragma unroll
+        for (int q = 0; q < SLICE_VEC / 2; ++q) w[s][q] = 0u;
+#pragma unroll
+    for (int u = 0; u < SLICE_VEC; ++u) {
+        uint32_t d[TC_SMAX];
+        split_digits(v[u], e, S, d);
+#pragma unroll
+        for (int s = 0; s < TC_SMAX; ++s) w[s][u >> 1] |= d[s] << (16 * (u & 1));
+    }
+    uint4* o = reinterpret_cast<uint4*>(out + row * Kp + k0);
+    const size_t st16 = stride / 8;                // one slice, in 16-byte units
+#pragma unroll
+    for (int s = 0; s < TC_SMAX; ++s)
+        if (s < S) o[s * st16] = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
 }
 
-// B' slices stored K-major: out[s][jp][kp].  Each complex entry (k, j) gives rows
-// jp = 2j: (Re, -Im) and jp = 2j + 1: (Im, Re) at kp = 2k, 2k + 1.
+__global__ void k_slice_A(const void* src, int is_real, int conj, int64_t M, int64_t K, int64_t Kp, int64_t sa_i,
+                          int64_t sa_k, int band, const int* e, int S, __nv_bfloat16* out) {
+    const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * SLICE_VEC;
+    const int64_t i = blockIdx.y;
+    if (k0 >= Kp || i >= M) return;
+    const int ei = e[i];
+    double re[SLICE_VEC], im[SLICE_VEC];
+#pragma unroll
+    for (int u = 0; u < SLICE_VEC; ++u) {
+        const int64_t k = k0 + u;
+        re[u] = 0.0; im[u] = 0.0;
+        if (k < K && !in_band(i, k, K, band)) {
+            if (is_real) {
+                re[u] = ((const double*)src)[i * sa_i + k * sa_k];
+            } else {
+                const double2 x = ((const double2*)src)[i * sa_i + k * sa_k];
+                re[u] = x.x; im[u] = conj ? -x.y : x.y;
+            }
+        }
+    }
+    const int64_t rows = is_real ? M : 2 * M;
+    const size_t stride = (size_t)rows * Kp;
+    slice_part(re, ei, S, out, is_real ? i : 2 * i, Kp, k0, stride);
+    if (!is_real) slice_part(im, ei, S, out, 2 * i + 1, Kp, k0, stride);
+}
+
 __global__ void k_slice_B(const void* src, int is_real, int64_t K, int64_t m, int64_t Kp, int64_t sb_k,
                           int64_t sb_j, const int* f, int S, __nv_bfloat16* out) {
     const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * SLICE_VEC;
     const int64_t j = blockIdx.y;
-    if (2 * k0 >= Kp || j >= m) return;
-    const int fe = f[2 * j];
-    uint32_t p0[TC_SMAX][SLICE_VEC], p1[TC_SMAX][SLICE_VEC];
+    if (k0 >= Kp || j >= m) return;
+    const int fe = f[j];
+    double re[SLICE_VEC], im[SLICE_VEC];
 #pragma unroll
-    for (int v = 0; v < SLICE_VEC; ++v) {
-        const int64_t k = k0 + v;
-        double re = 0.0, im = 0.0;
+    for (int u = 0; u < SLICE_VEC; ++u) {
+        const int64_t k = k0 + u;
+        re[u] = 0.0; im[u] = 0.0;
         if (k < K) {
-            if (is_real) { re = ((const double*)src)[k * sb_k + j * sb_j]; }
-            else { const double2 x = ((const double2*)src)[k * sb_k + j * sb_j]; re = x.x; im = x.y; }
-        }
-        uint32_t dr[TC_SMAX], di[TC_SMAX];
-        split_digits(re, fe, S, dr);
-        split_digits(im, fe, S, di);
-#pragma unroll
-        for (int s = 0; s < TC_SMAX; ++s) {
-            p0[s][v] = dr[s] | ((di[s] ^ 0x8000u) << 16);   // (Re, -Im): flip the sign bit
-            p1[s][v] = di[s] | (dr[s] << 16);               // (Im, Re)
+            if (is_real) { re[u] = ((const double*)src)[k * sb_k + j * sb_j]; }
+            else { const double2 x = ((const double2*)src)[k * sb_k + j * sb_j]; re[u] = x.x; im[u] = x.y; }
         }
     }
-    uint4* o0 = reinterpret_cast<uint4*>(out + (2 * j) * Kp + 2 * k0);
-    uint4* o1 = reinterpret_cast<uint4*>(out + (2 * j + 1) * Kp + 2 * k0);
-    const size_t stride16 = (size_t)(2 * m) * Kp / 8;
-#pragma unroll
-    for (int s = 0; s < TC_SMAX; ++s) {
-        if (s < S) {
-            o0[s * stride16] = make_uint4(p0[s][0], p0[s][1], p0[s][2], p0[s][3]);
-            o1[s * stride16] = make_uint4(p1[s][0], p1[s][1], p1[s][2], p1[s][3]);
-        }
-    }
+    const int64_t rows = is_real ? m : 2 * m;
+    const size_t stride = (size_t)rows * Kp;
+    slice_part(re, fe, S, out, is_real ? j : 2 * j, Kp, k0, stride);
+    if (!is_real) slice_part(im, fe, S, out, 2 * j + 1, Kp, k0, stride);
 }
 
 // ------------------------------------------------------------------------------ host side
@@ -572,6 +593,8 @@ struct TcOperand {
     int64_t rows = 0, Kp = 0, K = 0;
     size_t cap = 0;                   // bytes allocated for slices
     size_t exp_cap = 0;
+    int cplx = 1;                     // complex operand: real and imaginary parts in separate rows
+    int64_t lrows = 0;                // logical rows (A) / columns (B): rows = (cplx ? 2 : 1) lrows
     CUtensorMap map;
 };
 
@@ -594,7 +617,7 @@ static TcState* tcs(bem_ctx* h) {
     return (TcState*)h->tc;
 }
 
-static int64_t pad64(int64_t x) { return (x + 63) / 64 * 64; }
+static int64_t pad32(int64_t x) { return (x + 31) / 32 * 32; }   // K, padded to whole 32-wide K blocks
 
 static bem_status encode_map(bem_ctx* h, TcOperand& op, int S) {
     bem_status st = get_encode(h);
@@ -632,17 +655,19 @@ static bem_status reserve(bem_ctx* h, TcOperand& op, int64_t rows, int64_t Kp, i
 static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k,
                           int band = -1, int is_real = 0, int conj = 0, const int* fields = nullptr) {
     const int S = tcs(h)->S;
-    const int64_t Kp = pad64(2 * K);
-    bem_status st = reserve(h, op, M, Kp, S);
+    const int64_t Kp = pad32(K);
+    bem_status st = reserve(h, op, is_real ? M : 2 * M, Kp, S);
     if (st != BEM_OK) return st;
     op.K = K;
+    op.cplx = is_real ? 0 : 1;
+    op.lrows = M;
     if (fields) {
         BEM_TIMED(h, "k_exp_rows", (k_exp_from_fields<<<(unsigned)((M + 255) / 256), 256, 0, h->stream>>>(fields, M, op.exps)));
     } else {
         BEM_TIMED(h, "k_exp_rows", (k_exp_rows<<<(unsigned)((M + 7) / 8), 256, 0, h->stream>>>(src, is_real, M, K, sa_i, sa_k, band, op.exps)));
     }
     BEM_LAUNCH(h, "k_exp_rows");
-    dim3 grid((unsigned)((Kp / 2 / SLICE_VEC + 255) / 256), (unsigned)M);
+    dim3 grid((unsigned)((Kp / SLICE_VEC + 255) / 256), (unsigned)M);
     BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, is_real, conj, M, K, Kp, sa_i, sa_k, band, op.exps, S, op.slices)));
     BEM_LAUNCH(h, "k_slice_A");
     return encode_map(h, op, S);
@@ -652,13 +677,15 @@ static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M,
 static bem_status slice_B(bem_ctx* h, TcOperand& op, const void* src, int is_real, int64_t K, int64_t m, int64_t sb_k,
                           int64_t sb_j, int S_over = 0) {
     const int S = S_over ? S_over : tcs(h)->S;
-    const int64_t Kp = pad64(2 * K);
-    bem_status st = reserve(h, op, 2 * m, Kp, S);
+    const int64_t Kp = pad32(K);
+    bem_status st = reserve(h, op, is_real ? m : 2 * m, Kp, S);
     if (st != BEM_OK) return st;
     op.K = K;
+    op.cplx = is_real ? 0 : 1;
+    op.lrows = m;
     BEM_TIMED(h, "k_exp_cols", (k_exp_cols<<<(unsigned)m, 256, 0, h->stream>>>(src, is_real, K, m, sb_k, sb_j, op.exps)));
     BEM_LAUNCH(h, "k_exp_cols");
-    dim3 grid((unsigned)((Kp / 2 / SLICE_VEC + 255) / 256), (unsigned)m);
+    dim3 grid((unsigned)((Kp / SLICE_VEC + 255) / 256), (unsigned)m);
     BEM_TIMED(h, "k_slice_B", (k_slice_B<<<grid, 256, 0, h->stream>>>(src, is_real, K, m, Kp, sb_k, sb_j, op.exps, S, op.slices)));
     BEM_LAUNCH(h, "k_slice_B");
     return encode_map(h, op, S);
@@ -703,6 +730,11 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     TcGemmArgs p;
     p.M = (int)A.rows;
     p.Ncols = (int)B.rows;
+    p.Ml = (int)A.lrows;
+    p.ml = (int)B.lrows;
+    p.aC = A.cplx;
+    p.bC = B.cplx;
+    if (!A.cplx && !B.cplx) return bem_fail(h, BEM_E_INVALID, "tc_gemm: at least one operand must be complex");
     p.nkb = (int)(A.Kp / TC_BK);
     p.S = Sg;
     p.ea = A.exps;
@@ -736,7 +768,7 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     const int T = mt * nt;
     const int nch = (p.nkb + TC_CHUNK_KB - 1) / TC_CHUNK_KB;
     const double chunk_ms = (double)(Sg * (Sg + 1) / 2) * TC_CHUNK_KB * (TC_BK / 16) * 73.0 / 2.0e6;
-    const double part_ms_per_split = (double)p.M * (p.Ncols / 2) * 32.0 / 6.0e9;
+    const double part_ms_per_split = (double)p.Ml * p.ml * 32.0 / 6.0e9;
     int splits = 1;
     double best = (double)((T + nsm - 1) / nsm) * nch * chunk_ms;
     for (int s = 2; s <= 32 && s <= nch / 2; ++s) {
@@ -746,9 +778,8 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
         const double cost = (double)(((int64_t)T * s + nsm - 1) / nsm) * cps * chunk_ms + s * part_ms_per_split;
         if (cost < 0.98 * best) { best = cost; splits = s; p.kps = cps * TC_CHUNK_KB; }
     }
-    const int m = p.Ncols / 2;
     if (splits > 1) {
-        const size_t need = (size_t)splits * p.M * m * sizeof(double2);
+        const size_t need = (size_t)splits * p.Ml * p.ml * sizeof(double2);
         if (need > t->part_cap) {
             if (t->part) { cudaStreamSynchronize(h->stream); cudaFree(t->part); t->part = nullptr; t->part_cap = 0; }
             BEM_CUDA(h, cudaMalloc((void**)&t->part, need));
@@ -760,9 +791,9 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     BEM_TIMED(h, tag, (kern<<<grid, TC_THREADS, smem, h->stream>>>(A.map, B.map, p)));
     BEM_LAUNCH(h, "k_tc_gemm");
     if (splits > 1) {
-        const int64_t n = (int64_t)p.M * m;
+        const int64_t n = (int64_t)p.Ml * p.ml;
         BEM_TIMED(h, "k_splitk_reduce", (k_splitk_reduce<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
-                                            p.part, splits, p.M, m, out, ldo, transposed, alpha, beta)));
+                                            p.part, splits, p.Ml, p.ml, out, ldo, transposed, alpha, beta)));
         BEM_LAUNCH(h, "k_splitk_reduce");
     }
     return BEM_OK;
