@@ -1,14 +1,15 @@
 // Mixed-precision dense products on the GB300 tensor cores (tcgen05, TMEM, TMA).
 //
-// A complex product C = A B (A: M x K, B: K x m, FP64 complex) is evaluated as one real
-// GEMM C' = A' B' with K' = 2K interleaved (re, im) and 2m output columns:
-//   A'[i, 2k+c] = component c of A[i, k];
-//   B'[2k, 2j] = Re B, B'[2k+1, 2j] = -Im B, B'[2k, 2j+1] = Im B, B'[2k+1, 2j+1] = Re B,
-// so C'[i, 2j] = Re C[i, j] and C'[i, 2j+1] = Im C[i, j].
+// A complex product C = A B (A: M x K, B: K x m, FP64) is evaluated as one real GEMM of
+// planar part matrices: a complex row i of A becomes part rows 2i (Re) and 2i+1 (Im), a
+// complex column j of B part columns 2j (Re) and 2j+1 (Im); a real operand keeps one part.
+// The GEMM C' = A' B' then holds Re A Re B, Re A Im B, Im A Re B and Im A Im B in adjacent
+// rows and columns, and the epilogue forms Re C = RR - II, Im C = RI + IR (or takes the two
+// parts directly when one operand is real, which halves the work).
 //
 // Each operand is split into S bf16 slices (error-free splitting after Ozaki et al.,
 // Numer. Algorithms 2012): with a power-of-two scale per row of A' (2^e_i) and per column
-// of B' (2^f_j), x 2^-e = sum_s a_s 2^{-7(s+1)} with integers |a_0| <= 128, |a_s| <= 64;
+// of B (2^f_j, shared by the parts), x 2^-e = sum_s a_s 2^{-7(s+1)} with integers |a_0| <= 128, |a_s| <= 64;
 // slice s is stored pre-multiplied by 2^{-7s}, which bf16 holds exactly.  Products of
 // slices (s, t) with s + t <= S - 1 are accumulated by tcgen05.mma (kind::f16, FP32
 // accumulation) into four TMEM accumulators: d = 0, 1, 2 and d >= 3 (d = s + t).  Over a
@@ -20,7 +21,7 @@
 // After each chunk the epilogue warps add the accumulators into double-float (hi, lo)
 // registers; the result is rescaled by 2^{e_i + f_j - 14} and written in FP64.
 //
-// Kernel: one 128 x 128 tile of C' per CTA, 10 warps: warp 0 issues TMA loads (3D tensor
+// Kernel: one 128 x 128 tile of C' per CTA (split over K' when that fills the GPU better), 10 warps: warp 0 issues TMA loads (3D tensor
 // maps over the stacked slices, 64-byte swizzle, 32-element K blocks, 2 stages), warp 1
 // allocates TMEM and issues the MMAs (S is a template parameter, so the S(S+1)/2 x 2 MMAs
 // of a K block are one straight-line sequence with constant descriptor offsets: a loop
