@@ -756,13 +756,20 @@ __global__ void __launch_bounds__(QR_NT, 1) k_house_qr_df(float4* X, int64_t N, 
             x.im = dfl_fma(dfl_neg(vi.re), wk.im, dfl_fma(dfl_neg(vi.im), wk.re, x.im));
             return x;
         };
-        for (int64_t i = max(r0, (int64_t)jp1) + rg; i < r1; i += 8) {
-            const cdfl vi = upd ? cdfl_unpack(pin[i]) : cdfl_zero();
-            cdfl x[QR_KS];
+        // one row per iteration; the next row's loads are issued before this row's arithmetic
+        auto load = [&](int64_t i, cdfl& vi, cdfl* x, cdfl& xo) {
+            const bool ok = i < r1;
+            vi = (upd && ok) ? cdfl_unpack(pin[i]) : cdfl_zero();
 #pragma unroll
-            for (int kk = 0; kk < QR_KS; ++kk) x[kk] = (pcs[kk] >= 0) ? cdfl_ld(X + i * n + pcs[kk]) : cdfl_zero();
-            cdfl xo = cdfl_zero();
-            if (cgp == 1 && pn >= 0) xo = cdfl_ld(X + i * n + pn);
+            for (int kk = 0; kk < QR_KS; ++kk) x[kk] = (ok && pcs[kk] >= 0) ? cdfl_ld(X + i * n + pcs[kk]) : cdfl_zero();
+            xo = (ok && cgp == 1 && pn >= 0) ? cdfl_ld(X + i * n + pn) : cdfl_zero();
+        };
+        int64_t i = max(r0, (int64_t)jp1) + rg;
+        cdfl vi, x[QR_KS], xo;
+        load(i, vi, x, xo);
+        for (; i < r1; i += 8) {
+            cdfl vn, xn[QR_KS], xon;
+            load(i + 8, vn, xn, xon);
             if (upd) {
 #pragma unroll
                 for (int kk = 0; kk < QR_KS; ++kk) {
@@ -786,6 +793,10 @@ __global__ void __launch_bounds__(QR_NT, 1) k_house_qr_df(float4* X, int64_t N, 
                 cdfl_conj_fma(accD[kk], p, x[kk]);
                 accN[kk] = fmaf(x[kk].re.hi, x[kk].re.hi, fmaf(x[kk].im.hi, x[kk].im.hi, accN[kk]));
             }
+            vi = vn;
+            xo = xon;
+#pragma unroll
+            for (int kk = 0; kk < QR_KS; ++kk) x[kk] = xn[kk];
         }
 #pragma unroll
         for (int kk = 0; kk < QR_KS; ++kk) {
