@@ -11,12 +11,8 @@
 #include <algorithm>
 #include <type_traits>
 
-#include <cooperative_groups.h>
-
 #include "dfloat.cuh"
 #include "kernels.h"
-
-namespace cg = cooperative_groups;
 
 // =========================================================================================
 // GEMM: C = alpha op(A) op(B) + beta C, column-major, 64x64 tiles, 16-deep K slices
@@ -1347,132 +1343,7 @@ __global__ void k_augment(const cplx* K, cplx* M, cplx* colbuf, int r) {
     if (c == 0) colbuf[i] = K[i];
 }
 
-// The mixed path's Gauss-Jordan inversion inside one thread-block cluster, in double-float:
-// augmented column c (of [A | I], r x 2r) lives in the shared memory of CTA c mod CS.  Step
-// j: every CTA copies column j from its owner (distributed shared memory), picks the pivot
-// row from its copy (identically everywhere), and eliminates in its own columns that can
-// still change (left columns beyond j, all right columns); the pivot column itself is left
-// alone, so the copies made during the step never race its owner.  One cluster barrier
-// per step (a hardware barrier: no spin-waits).  A zero pivot sets DEVERR_SINGULAR.
-#define GJC_NT 256
-__global__ void __launch_bounds__(GJC_NT, 1) k_gauss_jordan_cl(const cplx* __restrict__ K, cplx* Kinv, int r, int* err) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int CS = (int)cl.num_blocks(), b = (int)cl.block_rank();
-    const int ncol = 2 * r;
-    const int cn = (ncol - b + CS - 1) / CS;          // my columns: c = b + CS l, l < cn
-    extern __shared__ float4 gcol[];                   // [cn][r], then the pivot copy [r]
-    float4* piv = gcol + (size_t)cn * r;
-    __shared__ float s_bv[GJC_NT / 32];
-    __shared__ int s_bi[GJC_NT / 32];
-    __shared__ int s_p;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int e = tid; e < cn * r; e += blockDim.x) {
-        const int l = e / r, i = e % r, c = b + CS * l;
-        const cplx v = (c < r) ? K[i + (int64_t)c * r] : cmk((c - r) == i ? 1.0 : 0.0, 0.0);
-        gcol[e] = cdfl_pack({dfl_from_bits(v.x), dfl_from_bits(v.y)});
-    }
-    cl.sync();
-    for (int j = 0; j < r; ++j) {
-        const float4* src = cl.map_shared_rank(gcol, j % CS) + (size_t)(j / CS) * r;
-        for (int i = tid; i < r; i += blockDim.x) piv[i] = src[i];
-        __syncthreads();
-        // pivot: largest |x|^2 over rows i >= j (the leading floats decide; ties to the lower row)
-        float best = -1.f;
-        int bi = r;
-        for (int i = j + tid; i < r; i += blockDim.x) {
-            const float4 v = piv[i];
-            const float a = v.x * v.x + v.z * v.z;
-            if (a > best) { best = a; bi = i; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if (lane == 0) { s_bv[wid] = best; s_bi[wid] = bi; }
-        __syncthreads();
-        if (tid == 0) {
-            float bb = s_bv[0];
-            int p = s_bi[0];
-            for (int q = 1; q < GJC_NT / 32; ++q)
-                if (s_bv[q] > bb || (s_bv[q] == bb && s_bi[q] < p)) { bb = s_bv[q]; p = s_bi[q]; }
-            if (!(bb > 0.f) || p >= r) {
-                if (b == 0) atomicOr(err, DEVERR_SINGULAR);
-                p = j;
-            }
-            if (p != j) { const float4 t = piv[j]; piv[j] = piv[p]; piv[p] = t; }
-            s_p = p;
-        }
-        __syncthreads();
-        const int p = s_p;
-        const cdfl pv = cdfl_unpack(piv[j]);
-        // 1 / pv = conj(pv) / |pv|^2
-        const dfl n2 = dfl_fma(pv.re, pv.re, dfl_mul(pv.im, pv.im));
-        cdfl ipv = cdfl_zero();
-        if (n2.hi > 0.f) {
-            const dfl inv = dfl_div(dfl{1.f, 0.f}, n2);
-            ipv = {dfl_mul(pv.re, inv), dfl_neg(dfl_mul(pv.im, inv))};
-        }
-        for (int l = wid; l < cn; l += GJC_NT / 32) {
-            const int c = b + CS * l;
-            if (c <= j) continue;                      // eliminated already, or the pivot column
-            float4* col = gcol + (size_t)l * r;
-            const cdfl a = cdfl_unpack(col[p]), xp = cdfl_unpack(col[j]);
-            cdfl xj;                                    // (row p of c) / pivot
-            xj.re = dfl_fma(a.re, ipv.re, dfl_neg(dfl_mul(a.im, ipv.im)));
-            xj.im = dfl_fma(a.re, ipv.im, dfl_mul(a.im, ipv.re));
-            __syncwarp();
-            for (int i = lane; i < r; i += 32) {
-                if (i == j) { col[i] = cdfl_pack(xj); continue; }
-                const cdfl x = (i == p) ? xp : cdfl_unpack(col[i]);
-                const cdfl m = cdfl_unpack(piv[i]);
-                cdfl v;
-                v.re = dfl_sub(x.re, dfl_fma(m.re, xj.re, dfl_neg(dfl_mul(m.im, xj.im))));
-                v.im = dfl_sub(x.im, dfl_fma(m.re, xj.im, dfl_mul(m.im, xj.re)));
-                col[i] = cdfl_pack(v);
-            }
-            __syncwarp();
-        }
-        cl.sync();
-    }
-    for (int e = tid; e < cn * r; e += blockDim.x) {
-        const int l = e / r, i = e % r, c = b + CS * l;
-        if (c >= r) Kinv[i + (int64_t)(c - r) * r] = cdfl_to(cdfl_unpack(gcol[e]));
-    }
-}
-
 bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
-    if (h->opt.prec == BEM_MIXED_BF16 && r >= 2) {
-        // one cluster of up to 16 CTAs when the augmented columns fit their shared memory
-        int CS = 16;
-        for (; CS >= 2; CS /= 2) {
-            const size_t smem = ((size_t)(2 * r + CS - 1) / CS + 1) * r * sizeof(float4);
-            if (smem > 200 * 1024) { CS = 0; break; }
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = (unsigned)CS;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3((unsigned)CS);
-            cfg.blockDim = dim3(GJC_NT);
-            cfg.dynamicSmemBytes = smem;
-            cfg.stream = h->stream;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            int ncl = 0;
-            bool ok = cudaFuncSetAttribute(k_gauss_jordan_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
-            if (ok && CS > 8) ok = cudaFuncSetAttribute(k_gauss_jordan_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
-            if (ok) ok = cudaOccupancyMaxActiveClusters(&ncl, k_gauss_jordan_cl, &cfg) == cudaSuccess && ncl >= 1;
-            cudaGetLastError();             // a refused query only selects a smaller cluster or the fallback
-            if (!ok) continue;
-            cudaError_t le = cudaSuccess;
-            BEM_TIMED(h, "k_gauss_jordan", le = cudaLaunchKernelEx(&cfg, k_gauss_jordan_cl, K, Kinv, r, h->dev_err));
-            BEM_CUDA(h, le);
-            BEM_LAUNCH(h, "k_gauss_jordan_cl");
-            return BEM_OK;
-        }
-    }
     cplx *M = nullptr, *colbuf = nullptr;
     BEM_CUDA(h, cudaMallocAsync((void**)&M, sizeof(cplx) * (size_t)r * 2 * r, h->stream));
     BEM_CUDA(h, cudaMallocAsync((void**)&colbuf, sizeof(cplx) * (size_t)r * 2, h->stream));
