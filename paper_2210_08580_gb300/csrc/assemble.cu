@@ -628,10 +628,11 @@ __device__ __forceinline__ void bessel_u_df(const float4* __restrict__ tab, dfl 
     Y0 = rY;
 }
 
-// Separated pair (S/N only), q x q tensor Gauss-Legendre in double-float.  b = y_f(0) -
-// x_e(0), ue = h_e t_e, vf = h_f t_f; returns A_ab with I_ab = h_e h_f A_ab.  The sum over
+// Separated pair (S/N only), q x q tensor Gauss-Legendre in double-float.  b = k (y_f(0) -
+// x_e(0)), ue = k h_e t_e, vf = k h_f t_f (lengths in units of 1/k, so |b + t vf - s ue|^2 is
+// the Bessel argument u = (k r)^2); returns A_ab with I_ab = h_e h_f A_ab.  The sum over
 // the f-nodes runs first (two row sums R_b), then the e-node weights multiply them.
-__device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, dfl vfy, dfl k2,
+__device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, dfl vfy,
                               const float4* __restrict__ tab, cdfl A[4]) {
     const int o = gl_off(q);
     A[0] = A[1] = A[2] = A[3] = cdfl_zero();
@@ -642,9 +643,9 @@ __device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, 
         for (int j = 0; j < q; ++j) {
             const dfl t = dfl_mk(c_gx_df[o + j]);
             const dfl dx = dfl_fma(t, vfx, cx), dy = dfl_fma(t, vfy, cy);
-            const dfl r2 = dfl_fma(dx, dx, dfl_mul(dy, dy));
+            const dfl u = dfl_fma(dx, dx, dfl_mul(dy, dy));   // (k r)^2: the geometry is scaled by k
             dfl J0, Y0;
-            bessel_u_df(tab, dfl_mul(k2, r2), J0, Y0);
+            bessel_u_df(tab, u, J0, Y0);
             const cdfl g = {dfl_scale(Y0, -0.25f), dfl_scale(J0, 0.25f)};   // (i/4) (J0 + i Y0)
             R0 = cdfl_fma_real(dfl_mk(c_gw0_df[o + j]), g, R0);
             R1 = cdfl_fma_real(dfl_mk(c_gw1_df[o + j]), g, R1);
@@ -681,8 +682,10 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     const int i0 = ti * T, j0 = tj * T;
     const int e0 = (i0 - 1 + N) % N, f0 = (j0 - 1 + N) % N;
     const double ex0 = p.seg[e0], ey0 = p.seg[N + e0], fx0 = p.seg[f0], fy0 = p.seg[N + f0];
+    // positions and segment vectors are kept multiplied by k, so (k r)^2 comes out directly
+    const double kk = p.k;
     if (threadIdx.x == 0) {
-        const dfl ox = dfl_from(fx0 - ex0), oy = dfl_from(fy0 - ey0);
+        const dfl ox = dfl_from(kk * (fx0 - ex0)), oy = dfl_from(kk * (fy0 - ey0));
         sOff[0] = make_float2(ox.hi, ox.lo);
         sOff[1] = make_float2(oy.hi, oy.lo);
     }
@@ -692,8 +695,8 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
         const int s = ((isE ? i0 : j0) - 1 + l + N) % N;
         const SegV a = load_seg(p.seg, N, s);
         float2* g = isE ? gE : gF;
-        const double vals[7] = {a.x0 - (isE ? ex0 : fx0), a.y0 - (isE ? ey0 : fy0), a.h * a.tx, a.h * a.ty,
-                                a.tx, a.ty, a.h};
+        const double vals[7] = {kk * (a.x0 - (isE ? ex0 : fx0)), kk * (a.y0 - (isE ? ey0 : fy0)), kk * a.h * a.tx,
+                                kk * a.h * a.ty, a.tx, a.ty, a.h};
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
             const dfl v = dfl_from(vals[c]);
@@ -725,14 +728,16 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
             const dfl by = dfl_add(dfl_sub(dfl_mk(gF[TP + fl]), dfl_mk(gE[TP + el])), offy);
             const dfl uex = dfl_mk(gE[2 * TP + el]), uey = dfl_mk(gE[3 * TP + el]);
             const dfl vfx = dfl_mk(gF[2 * TP + fl]), vfy = dfl_mk(gF[3 * TP + fl]);
-            const float he = gE[6 * TP + el].x, hf = gF[6 * TP + fl].x;
+            // (scaled by k: kgap = k (gap + h_max) directly)
+            const float kf = (float)p.k;
+            const float he = kf * gE[6 * TP + el].x, hf = kf * gF[6 * TP + fl].x;
             const float mx = bx.hi + 0.5f * (vfx.hi - uex.hi), my = by.hi + 0.5f * (vfy.hi - uey.hi);
             const float hmax = fmaxf(he, hf);
             const float gap = fmaxf(sqrtf(mx * mx + my * my) - 0.5f * (he + hf), 0.0f);
-            const int q = q_for_gap(gap / hmax, (float)p.k * (gap + hmax));
+            const int q = q_for_gap(gap / hmax, gap + hmax);
             npts += (unsigned)(q * q);
             cdfl A[4];
-            pair_gauss_df(q, bx, by, uex, uey, vfx, vfy, k2, p.btabf, A);
+            pair_gauss_df(q, bx, by, uex, uey, vfx, vfy, p.btabf, A);
             const dfl hh = dfl_mul(dfl_mk(gE[6 * TP + el]), dfl_mk(gF[6 * TP + fl]));
             for (int c = 0; c < 4; ++c) I[c] = {dfl_mul(hh, A[c].re), dfl_mul(hh, A[c].im)};
             M0 = cdfl_add(cdfl_add(A[0], A[1]), cdfl_add(A[2], A[3]));

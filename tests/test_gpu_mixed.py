@@ -65,6 +65,23 @@ def test_mixed_blocks_and_solve_match_oracle(B, star301_ref):
     s.close()
 
 
+def test_rhs_slices_option(B, star301_ref):
+    """bem_options.rhs_slices: the right-hand-side product S Y with all six digit slices is
+    about two orders more accurate than with the default five (the leading five of the
+    same split); both stay inside their tolerances against the oracle."""
+    ref = star301_ref["efie"]
+    err = {}
+    for rs in (5, 6):
+        s = B.Solver(device=0, prec="mixed", rhs_slices=rs)
+        s.assemble(_cuda(star301_ref["v"]), star301_ref["k"], ops="SW")
+        vv = s.rhs_planewave(_cuda(star301_ref["ang"]))
+        err[rs] = _rel(vv.cpu().numpy().T, ref["vx"])
+        s.close()
+    assert err[5] <= MIXED_RHS_TOL, err
+    assert err[6] <= 1e-10, err
+    assert err[6] < 0.25 * err[5], err
+
+
 def test_mixed_cfie(B, star301_ref):
     ref = star301_ref["cfie"]
     s = B.Solver(device=0, prec="mixed")
