@@ -607,8 +607,9 @@ __device__ __forceinline__ void bessel_u_df(const float4* __restrict__ tab, dfl 
     const float4* c = tab + (size_t)i * (BTAB_DF_STRIDE / 4);
     const float4 h = __ldg(c);
     const dfl t = dfl_mul(dfl_sub(u, dfl{h.x, h.y}), dfl{h.z, h.w});
-    // degrees 7..5 in FP32: their coefficients are below 2.3e-9 on every interval (|t| <= 1),
-    // so FP32 rounding there stays below 1.4e-16 of the result; degrees 4..0 in double-float
+    // the highest degrees in FP32: Y0's coefficients of degree >= 5 are below 2.3e-9 and
+    // J0's of degree >= 4 below 1.1e-8 on every interval (|t| <= 1), so FP32 rounding there
+    // stays below 7e-16 of the result; the lower degrees in double-float
     float4 cc = __ldg(c + BTAB_NC);
     float pJ = cc.x, pY = cc.z;
 #pragma unroll
@@ -617,9 +618,12 @@ __device__ __forceinline__ void bessel_u_df(const float4* __restrict__ tab, dfl 
         pJ = fmaf(pJ, t.hi, cc.x);
         pY = fmaf(pY, t.hi, cc.z);
     }
-    dfl rJ = {pJ, 0.f}, rY = {pY, 0.f};
+    cc = __ldg(c + BTAB_FP32_DEG);                       // degree BTAB_FP32_DEG - 1
+    pJ = fmaf(pJ, t.hi, cc.x);
+    dfl rJ = {pJ, 0.f};
+    dfl rY = dfl_fma(dfl{pY, 0.f}, t, dfl{cc.z, cc.w});
 #pragma unroll
-    for (int j = BTAB_FP32_DEG - 1; j >= 0; --j) {
+    for (int j = BTAB_FP32_DEG - 2; j >= 0; --j) {
         cc = __ldg(c + 1 + j);
         rJ = dfl_fma(rJ, t, dfl{cc.x, cc.y});
         rY = dfl_fma(rY, t, dfl{cc.z, cc.w});

@@ -175,7 +175,8 @@ __device__ __forceinline__ Bessel01 bessel01(double z) {
 // double-float copy for the S/N far field: per interval 4 + 4 * BTAB_NC floats,
 // [u_mid (hi, lo), 1/u_half (hi, lo)], then per power j: [J0_j (hi, lo), Y0_j (hi, lo)]
 #define BTAB_DF_STRIDE (4 + 4 * BTAB_NC)
-// lowest degree whose J0 / Y0 coefficients the far field evaluates in FP32 (all below 2.3e-9)
+// lowest degree whose Y0 coefficients the far field evaluates in FP32 (all below 2.3e-9); J0 one
+// degree lower (below 1.1e-8)
 #define BTAB_FP32_DEG 5
 
 struct BesselU { double J0, Y0, J1z, Y1z; };   // J1z = J1(z)/z, Y1z = Y1(z)/z
