@@ -107,7 +107,7 @@ class BatchSolver:
         N, n = p.verts.shape[0], p.n_modes
         qr = min(self.nsm, (N + 15) // 16)
         jac = (n + 1) // 2
-        gj = max(1, (2 * n + 7) // 8)
+        gj = max(1, (2 * n + 2) // 3)
         return min(self.nsm, max(qr, jac, gj))
 
     def run(self) -> list[dict]:

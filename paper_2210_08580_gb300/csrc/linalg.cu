@@ -1317,6 +1317,7 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(cplx* M, int r, cplx* colb
         const bool sing = !(cabs2(pv) > 0.0);
         const cplx ipv = sing ? cmk(0, 0) : cdiv(cmk(1, 0), pv);
         for (int c = c0 + wid; c < c1; c += blockDim.x / 32) {
+            if (c < j) continue;                   // eliminated already (a unit column stays one)
             cplx* col = M + (int64_t)c * r;
             // swap rows j, p of this column and normalise row j
             const cplx xj = cmul(col[p], ipv), xp = col[j];
@@ -1356,7 +1357,8 @@ bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
     BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     BEM_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gauss_jordan, 256, smem));
     if (per < 1) return bem_fail(h, BEM_E_CUDA, "k_gauss_jordan cannot be resident");
-    int G = std::min(nsm * per, std::max(1, (2 * r + 7) / 8));
+    // three augmented columns per CTA: the per-step FP64 update spreads over about 2r/3 SMs
+    int G = std::min(nsm * per, std::max(1, (2 * r + 2) / 3));
     BEM_CUDA(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), h->stream));
     void* args[] = {&M, &r, &colbuf, &h->bar, &h->dev_err};
     cudaError_t lerr;

@@ -500,7 +500,8 @@ __device__ __forceinline__ void split_digits(double val, int e, int S, uint32_t*
 // group never straddles a row) and writes 16 bytes per part row and slice.
 #define SLICE_VEC 8
 // digits of SLICE_VEC values (one part row) packed as bf16 pairs, then one 16-byte store per slice
-__device__ __forceinline__ void slice_part(const double* v, int e, int S, __nv_bfloat16* out, int64_t row, int64_t Kp,
+template <class Get>
+__device__ __forceinline__ void slice_part(Get v, int e, int S, __nv_bfloat16* out, int64_t row, int64_t Kp,
                                            int64_t k0, size_t stride) {
     uint32_t w[TC_SMAX][SLICE_VEC / 2];
 #pragma unroll
@@ -510,7 +511,7 @@ __device__ __forceinline__ void slice_part(const double* v, int e, int S, __nv_b
 #pragma unroll
     for (int u = 0; u < SLICE_VEC; ++u) {
         uint32_t d[TC_SMAX];
-        split_digits(v[u], e, S, d);
+        split_digits(v(u), e, S, d);
 #pragma unroll
         for (int s = 0; s < TC_SMAX; ++s) w[s][u >> 1] |= d[s] << (16 * (u & 1));
     }
@@ -521,10 +522,41 @@ __device__ __forceinline__ void slice_part(const double* v, int e, int S, __nv_b
         if (s < S) o[s * st16] = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
 }
 
+// Contiguous complex rows (unit stride along k): the warp reads its 32 * SLICE_VEC values
+// coalesced (one 512-byte run per load) into shared memory, then each lane takes SLICE_VEC
+// consecutive values.  One pad slot per 8 keeps both phases free of bank conflicts.
+__global__ void __launch_bounds__(256, 4) k_slice_A_rows(const double2* src, int conj, int64_t M, int64_t K, int64_t Kp,
+                                                   int64_t sa_i, int band, const int* e, int S, __nv_bfloat16* out) {
+    const int64_t i = blockIdx.y;
+    __shared__ double2 stage[8][32 * SLICE_VEC + 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t kw = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * SLICE_VEC;
+    const double2* rowp = src + i * sa_i;
+#pragma unroll
+    for (int u = 0; u < SLICE_VEC; ++u) {
+        const int q = u * 32 + lane;
+        const int64_t k = kw + q;
+        double2 x = make_double2(0.0, 0.0);
+        if (k < K && !in_band(i, k, K, band)) x = rowp[k];
+        stage[w][q + (q >> 3)] = x;
+    }
+    __syncwarp();
+    const int64_t k0 = kw + lane * SLICE_VEC;
+    if (k0 >= Kp) return;
+    const int ei = e[i];
+    const size_t stride = (size_t)(2 * M) * Kp;
+    // real parts, then imaginary parts, each value read from shared memory when it is split
+    const double2* st = stage[w];
+    slice_part([&](int u) { const int q = lane * SLICE_VEC + u; return st[q + (q >> 3)].x; }, ei, S, out, 2 * i, Kp,
+               k0, stride);
+    slice_part([&](int u) { const int q = lane * SLICE_VEC + u; const double y = st[q + (q >> 3)].y; return conj ? -y : y; },
+               ei, S, out, 2 * i + 1, Kp, k0, stride);
+}
+
 __global__ void k_slice_A(const void* src, int is_real, int conj, int64_t M, int64_t K, int64_t Kp, int64_t sa_i,
                           int64_t sa_k, int band, const int* e, int S, __nv_bfloat16* out) {
-    const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * SLICE_VEC;
     const int64_t i = blockIdx.y;
+    const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * SLICE_VEC;
     if (k0 >= Kp || i >= M) return;
     const int ei = e[i];
     double re[SLICE_VEC], im[SLICE_VEC];
@@ -543,8 +575,8 @@ __global__ void k_slice_A(const void* src, int is_real, int conj, int64_t M, int
     }
     const int64_t rows = is_real ? M : 2 * M;
     const size_t stride = (size_t)rows * Kp;
-    slice_part(re, ei, S, out, is_real ? i : 2 * i, Kp, k0, stride);
-    if (!is_real) slice_part(im, ei, S, out, 2 * i + 1, Kp, k0, stride);
+    slice_part([&](int u) { return re[u]; }, ei, S, out, is_real ? i : 2 * i, Kp, k0, stride);
+    if (!is_real) slice_part([&](int u) { return im[u]; }, ei, S, out, 2 * i + 1, Kp, k0, stride);
 }
 
 __global__ void k_slice_B(const void* src, int is_real, int64_t K, int64_t m, int64_t Kp, int64_t sb_k,
@@ -565,8 +597,8 @@ __global__ void k_slice_B(const void* src, int is_real, int64_t K, int64_t m, in
     }
     const int64_t rows = is_real ? m : 2 * m;
     const size_t stride = (size_t)rows * Kp;
-    slice_part(re, fe, S, out, is_real ? j : 2 * j, Kp, k0, stride);
-    if (!is_real) slice_part(im, fe, S, out, 2 * j + 1, Kp, k0, stride);
+    slice_part([&](int u) { return re[u]; }, fe, S, out, is_real ? j : 2 * j, Kp, k0, stride);
+    if (!is_real) slice_part([&](int u) { return im[u]; }, fe, S, out, 2 * j + 1, Kp, k0, stride);
 }
 
 // ------------------------------------------------------------------------------ host side
@@ -669,7 +701,10 @@ static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M,
     }
     BEM_LAUNCH(h, "k_exp_rows");
     dim3 grid((unsigned)((Kp / SLICE_VEC + 255) / 256), (unsigned)M);
-    BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, is_real, conj, M, K, Kp, sa_i, sa_k, band, op.exps, S, op.slices)));
+    if (!is_real && sa_k == 1)
+        BEM_TIMED(h, "k_slice_A", (k_slice_A_rows<<<grid, 256, 0, h->stream>>>((const double2*)src, conj, M, K, Kp, sa_i, band, op.exps, S, op.slices)));
+    else
+        BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, is_real, conj, M, K, Kp, sa_i, sa_k, band, op.exps, S, op.slices)));
     BEM_LAUNCH(h, "k_slice_A");
     return encode_map(h, op, S);
 }
