@@ -550,6 +550,22 @@ __device__ __forceinline__ int q_for_gap(float ratio, float kgap) {
     return min(16, max(2, q));
 }
 
+// single MUFU square root (relative error about 2^-22): for the threshold decisions of the
+// double-float kernel (Gauss order, table interval), where only the choice depends on it
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// q_for_gap with approximate square root and division: the same bound, evaluated to about
+// 2^-20, so only pairs whose bound lands within that of an integer can change order
+__device__ __forceinline__ int q_for_gap_fast(float ratio, float kgap) {
+    const float a = 1.0f + 2.0f * fmaxf(ratio, 1e-3f);
+    const float rho = a + sqrt_approx(a * a - 1.0f);
+    const int q = (int)ceilf(__fdividef(32.24f + kgap, 2.0f * __logf(rho)) + 1e-3f);
+    return min(16, max(2, q));
+}
+
 template <bool WD>
 __device__ void pair_moments(int e, int f, const SegV& se, const SegV& sf, const AsmParams& p,
                              cplx I[4], cplx J[4], cplx Jt[4], unsigned& npts) {
@@ -587,7 +603,8 @@ __device__ __forceinline__ void tile_of(int L, int nT, int& ti, int& tj) {
 
 // table interval of u = z^2 (BTAB_NINT or beyond, or negative, outside the table)
 __device__ __forceinline__ int btab_index(float uhi) {
-    const float zf = sqrtf(uhi);
+    // an interval chosen one off at its edge is evaluated at |t| within 2^-17 of 1
+    const float zf = sqrt_approx(uhi);
     if (zf < (float)BTAB_ZLIN) {
         const int bits = __float_as_int(zf);
         return (((bits >> 23) & 255) - 127 - BTAB_LOG_EMIN) * BTAB_PEROCT + ((bits >> (23 - BTAB_OCT_LOG2)) & (BTAB_PEROCT - 1));
@@ -713,15 +730,16 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     unsigned npts = 0;
     for (int pi = threadIdx.x; pi < TP * TP; pi += blockDim.x) {
         const int el = pi / TP, fl = pi % TP;
-        if (i0 - 1 + el >= N || j0 - 1 + fl >= N) continue;
-        const int e = (i0 - 1 + el + N) % N, f = (j0 - 1 + fl + N) % N;
-        int d = e - f; if (d < 0) d = -d;
-        const int cyc = min(d, N - d);
+        const int er = i0 - 1 + el, fr = j0 - 1 + fl;     // in [-1, N): -1 is segment N - 1
+        if (er >= N || fr >= N) continue;
+        int d = er - fr; if (d < 0) d = -d;               // |d| <= N, so the cyclic distance is
+        const int cyc = min(d, N - d);                    // min(|d|, N - |d|) without a modulo
         const dfl etx = dfl_mk(gE[4 * TP + el]), ety = dfl_mk(gE[5 * TP + el]);
         const dfl ftx = dfl_mk(gF[4 * TP + fl]), fty = dfl_mk(gF[5 * TP + fl]);
         const dfl nd = dfl_mul(k2, dfl_fma(etx, ftx, dfl_mul(ety, fty)));   // nu_e . nu_f = t_e . t_f
         cdfl I[4], M0;
         if (cyc <= 1) {
+            const int e = er < 0 ? er + N : er, f = fr < 0 ? fr + N : fr;
             cplx Id[4], Jd[4], Jtd[4], m;
             near_from_table(p.near, N, e, f, cyc, Id, Jd, Jtd, m);
             for (int c = 0; c < 4; ++c) I[c] = cdfl_from(Id[c]);
@@ -737,8 +755,8 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
             const float he = kf * gE[6 * TP + el].x, hf = kf * gF[6 * TP + fl].x;
             const float mx = bx.hi + 0.5f * (vfx.hi - uex.hi), my = by.hi + 0.5f * (vfy.hi - uey.hi);
             const float hmax = fmaxf(he, hf);
-            const float gap = fmaxf(sqrtf(mx * mx + my * my) - 0.5f * (he + hf), 0.0f);
-            const int q = q_for_gap(gap / hmax, gap + hmax);
+            const float gap = fmaxf(sqrt_approx(mx * mx + my * my) - 0.5f * (he + hf), 0.0f);
+            const int q = q_for_gap_fast(__fdividef(gap, hmax), gap + hmax);
             npts += (unsigned)(q * q);
             cdfl A[4];
             pair_gauss_df(q, bx, by, uex, uey, vfx, vfy, p.btabf, A);
@@ -757,7 +775,7 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     auto entry = [&](int il, int jl, double2& ds, double2& dw) -> bool {
         const int i = i0 + il, j = j0 + jl;
         if (i >= N || j >= N) return false;
-        cdfl sv = cdfl_zero(), wv = cdfl_zero();
+        cdfl sv, wv;
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
             const int el = il + 1 - a;
@@ -766,16 +784,18 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
                 const int fl = jl + 1 - b;
                 const int pi = el * TP + fl;
                 const cdfl Iab = cdfl_unpack(sI[pi * 4 + a * 2 + b]);
-                sv = cdfl_add(sv, Iab);
+                sv = (a | b) ? cdfl_add(sv, Iab) : Iab;
                 if (p.W) {
                     // sigma_a sigma_b sum I/(h_e h_f) - k^2 (nu_e . nu_f) I_ab
                     cdfl M0 = cdfl_unpack(sM[pi]);
                     if (a != b) M0 = {dfl_neg(M0.re), dfl_neg(M0.im)};
                     const dfl nnd = dfl_neg(dfl_mk(sND[pi]));
-                    wv = cdfl_add(wv, cdfl_fma_real(nnd, Iab, M0));
+                    const cdfl term = cdfl_fma_real(nnd, Iab, M0);
+                    wv = (a | b) ? cdfl_add(wv, term) : term;
                 }
             }
         }
+        if (!p.W) wv = cdfl_zero();
         const int64_t off = (int64_t)i + (int64_t)j * p.ld;
         ds = cdfl_to(sv);
         dw = cdfl_to(wv);
