@@ -652,30 +652,64 @@ __device__ __forceinline__ void bessel_u_df(const float4* __restrict__ tab, dfl 
 // Separated pair (S/N only), q x q tensor Gauss-Legendre in double-float.  b = k (y_f(0) -
 // x_e(0)), ue = k h_e t_e, vf = k h_f t_f (lengths in units of 1/k, so |b + t vf - s ue|^2 is
 // the Bessel argument u = (k r)^2); returns A_ab with I_ab = h_e h_f A_ab.  The sum over
-// the f-nodes runs first (two row sums R_b), then the e-node weights multiply them.
-__device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, dfl vfy,
-                              const float4* __restrict__ tab, cdfl A[4]) {
-    const int o = gl_off(q);
-    A[0] = A[1] = A[2] = A[3] = cdfl_zero();
-    for (int i = 0; i < q; ++i) {
-        const dfl s = dfl_mk(c_gx_df[o + i]);
-        const dfl cx = dfl_sub(bx, dfl_mul(s, uex)), cy = dfl_sub(by, dfl_mul(s, uey));
-        cdfl R0 = cdfl_zero(), R1 = cdfl_zero();
-        for (int j = 0; j < q; ++j) {
-            const dfl t = dfl_mk(c_gx_df[o + j]);
-            const dfl dx = dfl_fma(t, vfx, cx), dy = dfl_fma(t, vfy, cy);
-            const dfl u = dfl_fma(dx, dx, dfl_mul(dy, dy));   // (k r)^2: the geometry is scaled by k
-            dfl J0, Y0;
-            bessel_u_df(tab, u, J0, Y0);
-            const cdfl g = {dfl_scale(Y0, -0.25f), dfl_scale(J0, 0.25f)};   // (i/4) (J0 + i Y0)
-            R0 = cdfl_fma_real(dfl_mk(c_gw0_df[o + j]), g, R0);
-            R1 = cdfl_fma_real(dfl_mk(c_gw1_df[o + j]), g, R1);
-        }
-        const dfl w0 = dfl_mk(c_gw0_df[o + i]), w1 = dfl_mk(c_gw1_df[o + i]);
+// the f-nodes runs first (two row sums R_b), then the e-node weights multiply them.  Every
+// sum starts from its first product (dfl_mul, the same bits as dfl_fma onto zero).
+__device__ __forceinline__ void gauss_point_df(int o, int j, dfl cx, dfl cy, dfl vfx, dfl vfy,
+                                               const float4* __restrict__ tab, bool first, cdfl& R0, cdfl& R1) {
+    const dfl t = dfl_mk(c_gx_df[o + j]);
+    const dfl dx = dfl_fma(t, vfx, cx), dy = dfl_fma(t, vfy, cy);
+    const dfl u = dfl_fma(dx, dx, dfl_mul(dy, dy));   // (k r)^2: the geometry is scaled by k
+    dfl J0, Y0;
+    bessel_u_df(tab, u, J0, Y0);
+    const cdfl g = {dfl_scale(Y0, -0.25f), dfl_scale(J0, 0.25f)};   // (i/4) (J0 + i Y0)
+    const dfl w0 = dfl_mk(c_gw0_df[o + j]), w1 = dfl_mk(c_gw1_df[o + j]);
+    if (first) {
+        R0 = {dfl_mul(w0, g.re), dfl_mul(w0, g.im)};
+        R1 = {dfl_mul(w1, g.re), dfl_mul(w1, g.im)};
+    } else {
+        R0 = cdfl_fma_real(w0, g, R0);
+        R1 = cdfl_fma_real(w1, g, R1);
+    }
+}
+__device__ __forceinline__ void gauss_row_df(int o, int i, const cdfl& R0, const cdfl& R1, bool first, cdfl A[4]) {
+    const dfl w0 = dfl_mk(c_gw0_df[o + i]), w1 = dfl_mk(c_gw1_df[o + i]);
+    if (first) {
+        A[0] = {dfl_mul(w0, R0.re), dfl_mul(w0, R0.im)};
+        A[1] = {dfl_mul(w0, R1.re), dfl_mul(w0, R1.im)};
+        A[2] = {dfl_mul(w1, R0.re), dfl_mul(w1, R0.im)};
+        A[3] = {dfl_mul(w1, R1.re), dfl_mul(w1, R1.im)};
+    } else {
         A[0] = cdfl_fma_real(w0, R0, A[0]);
         A[1] = cdfl_fma_real(w0, R1, A[1]);
         A[2] = cdfl_fma_real(w1, R0, A[2]);
         A[3] = cdfl_fma_real(w1, R1, A[3]);
+    }
+}
+// order fixed at compile time (fully unrolled: nodes and weights become constant operands)
+template <int Q>
+__device__ __forceinline__ void pair_gauss_df_q(dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, dfl vfy,
+                                                const float4* __restrict__ tab, cdfl A[4]) {
+    constexpr int o = Q * (Q - 1) / 2;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const dfl s = dfl_mk(c_gx_df[o + i]);
+        const dfl cx = dfl_sub(bx, dfl_mul(s, uex)), cy = dfl_sub(by, dfl_mul(s, uey));
+        cdfl R0, R1;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) gauss_point_df(o, j, cx, cy, vfx, vfy, tab, j == 0, R0, R1);
+        gauss_row_df(o, i, R0, R1, i == 0, A);
+    }
+}
+__device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, dfl vfy,
+                              const float4* __restrict__ tab, cdfl A[4]) {
+    const int o = gl_off(q);
+    for (int i = 0; i < q; ++i) {
+        const dfl s = dfl_mk(c_gx_df[o + i]);
+        const dfl cx = dfl_sub(bx, dfl_mul(s, uex)), cy = dfl_sub(by, dfl_mul(s, uey));
+        cdfl R0, R1;
+        gauss_point_df(o, 0, cx, cy, vfx, vfy, tab, true, R0, R1);
+        for (int j = 1; j < q; ++j) gauss_point_df(o, j, cx, cy, vfx, vfy, tab, false, R0, R1);
+        gauss_row_df(o, i, R0, R1, i == 0, A);
     }
 }
 
@@ -759,7 +793,8 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
             const int q = q_for_gap_fast(__fdividef(gap, hmax), gap + hmax);
             npts += (unsigned)(q * q);
             cdfl A[4];
-            pair_gauss_df(q, bx, by, uex, uey, vfx, vfy, p.btabf, A);
+            if (q == 2) pair_gauss_df_q<2>(bx, by, uex, uey, vfx, vfy, p.btabf, A);   // the far-field bulk
+            else pair_gauss_df(q, bx, by, uex, uey, vfx, vfy, p.btabf, A);
             const dfl hh = dfl_mul(dfl_mk(gE[6 * TP + el]), dfl_mk(gF[6 * TP + fl]));
             for (int c = 0; c < 4; ++c) I[c] = {dfl_mul(hh, A[c].re), dfl_mul(hh, A[c].im)};
             M0 = cdfl_add(cdfl_add(A[0], A[1]), cdfl_add(A[2], A[3]));
