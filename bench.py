@@ -400,9 +400,8 @@ def main():
         xds = [x, torch.empty_like(x)]
         copy_stream = torch.cuda.Stream(dev)
         copied = [None, None]
-        barrier()
-        t0 = time.perf_counter()
-        for it in range(args.steps):
+
+        def e2e_step(it):
             b = it % 2
             vd = vh.to(dev, non_blocking=True)
             ad = ah.to(dev, non_blocking=True)
@@ -416,6 +415,13 @@ def main():
                 xhs[b].copy_(xds[b], non_blocking=True)
             copied[b] = torch.cuda.Event()
             copied[b].record(copy_stream)
+
+        for it in range(2):                         # one untimed pass through both buffers
+            e2e_step(it)
+        barrier()
+        t0 = time.perf_counter()
+        for it in range(args.steps):
+            e2e_step(it)
         barrier()
         e2e_s = reduce_max((time.perf_counter() - t0) / args.steps, dist, dev)
         e2e = {"value": job_value(args.nrhs, world, e2e_s), "unit": "RHS/s",

@@ -264,8 +264,11 @@ static void build_bessel_table(std::vector<double>& tab, std::vector<float>& tab
             for (int k = 0; k < n; ++k)
                 for (int j = 0; j < n; ++j) mono[j] += a[k] * tk[(size_t)k * n + j];
             for (int j = 0; j < n; ++j) tab[(size_t)i * BTAB_STRIDE + 2 + (size_t)q * n + j] = (double)mono[j];
+            // the double-float copy holds the kernel's factors: J0 / 4 and -Y0 / 4, so that its
+            // two polynomials give (i/4) H0 = (-Y0/4, J0/4) directly (exact power-of-two scaling)
             if (q < 2)
-                for (int j = 0; j < n; ++j) put_df((size_t)i * BTAB_DF_STRIDE + 4 * (j + 1) + 2 * q, mono[j]);
+                for (int j = 0; j < n; ++j)
+                    put_df((size_t)i * BTAB_DF_STRIDE + 4 * (j + 1) + 2 * q, (q == 0 ? 0.25L : -0.25L) * mono[j]);
         }
     }
 }
@@ -612,21 +615,21 @@ __device__ __forceinline__ int btab_index(float uhi) {
     return BTAB_NLOG + (int)fminf((zf - (float)BTAB_ZLIN) * (float)(1.0 / BTAB_W), (float)BTAB_NINT);
 }
 
-// J0(z), Y0(z) at u = z^2 from the double-float table (FP64 routines outside it)
-__device__ __forceinline__ void bessel_u_df(const float4* __restrict__ tab, dfl u, dfl& J0, dfl& Y0) {
+// (i/4) H0(z) = (-Y0(z)/4, J0(z)/4) at u = z^2 from the double-float table, which holds
+// J0/4 and -Y0/4 (FP64 routines outside it)
+__device__ __forceinline__ cdfl hankel_u_df(const float4* __restrict__ tab, dfl u) {
     const int i = btab_index(u.hi);
     if (i < 0 || i >= BTAB_NINT) {
         const Bessel01 b = bessel01<false>(sqrt(dfl_to(u)));
-        J0 = dfl_from(b.J0);
-        Y0 = dfl_from(b.Y0);
-        return;
+        return {dfl_from(-0.25 * b.Y0), dfl_from(0.25 * b.J0)};
     }
     const float4* c = tab + (size_t)i * (BTAB_DF_STRIDE / 4);
     const float4 h = __ldg(c);
     const dfl t = dfl_mul(dfl_sub(u, dfl{h.x, h.y}), dfl{h.z, h.w});
     // the highest degrees in FP32: Y0's coefficients of degree >= 5 are below 2.3e-9 and
-    // J0's of degree >= 4 below 1.1e-8 on every interval (|t| <= 1), so FP32 rounding there
-    // stays below 7e-16 of the result; the lower degrees in double-float
+    // J0's of degree >= 4 below 1.1e-8 on every interval (|t| <= 1; a quarter of that in the
+    // table), so FP32 rounding there stays below 7e-16 of the result; the lower degrees in
+    // double-float
     float4 cc = __ldg(c + BTAB_NC);
     float pJ = cc.x, pY = cc.z;
 #pragma unroll
@@ -645,8 +648,7 @@ __device__ __forceinline__ void bessel_u_df(const float4* __restrict__ tab, dfl 
         rJ = dfl_fma(rJ, t, dfl{cc.x, cc.y});
         rY = dfl_fma(rY, t, dfl{cc.z, cc.w});
     }
-    J0 = rJ;
-    Y0 = rY;
+    return {rY, rJ};
 }
 
 // Separated pair (S/N only), q x q tensor Gauss-Legendre in double-float.  b = k (y_f(0) -
@@ -659,9 +661,7 @@ __device__ __forceinline__ void gauss_point_df(int o, int j, dfl cx, dfl cy, dfl
     const dfl t = dfl_mk(c_gx_df[o + j]);
     const dfl dx = dfl_fma(t, vfx, cx), dy = dfl_fma(t, vfy, cy);
     const dfl u = dfl_fma(dx, dx, dfl_mul(dy, dy));   // (k r)^2: the geometry is scaled by k
-    dfl J0, Y0;
-    bessel_u_df(tab, u, J0, Y0);
-    const cdfl g = {dfl_scale(Y0, -0.25f), dfl_scale(J0, 0.25f)};   // (i/4) (J0 + i Y0)
+    const cdfl g = hankel_u_df(tab, u);                  // (i/4) (J0 + i Y0)
     const dfl w0 = dfl_mk(c_gw0_df[o + j]), w1 = dfl_mk(c_gw1_df[o + j]);
     if (first) {
         R0 = {dfl_mul(w0, g.re), dfl_mul(w0, g.im)};
@@ -730,20 +730,18 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     float4* sI = reinterpret_cast<float4*>(smem_raw);               // TP*TP*4 complex df
     float4* sM = sI + TP * TP * 4;                                   // TP*TP: sum_ab I / (h_e h_f)
     float2* sND = reinterpret_cast<float2*>(sM + TP * TP);          // TP*TP: k^2 nu_e . nu_f
-    float2* gE = sND + TP * TP;                                      // 7*TP: ox, oy, ux, uy, tx, ty, h
+    float2* gE = sND + TP * TP;                                      // 7*TP: ox, oy, ux, uy, k tx, k ty, h
     float2* gF = gE + 7 * TP;
-    __shared__ float2 sOff[2];
     const int N = p.N;
     const int i0 = ti * T, j0 = tj * T;
     const int e0 = (i0 - 1 + N) % N, f0 = (j0 - 1 + N) % N;
     const double ex0 = p.seg[e0], ey0 = p.seg[N + e0], fx0 = p.seg[f0], fy0 = p.seg[N + f0];
-    // positions and segment vectors are kept multiplied by k, so (k r)^2 comes out directly
+    // positions, segment vectors and tangents are kept multiplied by k, so (k r)^2 and
+    // k^2 t_e . t_f come out directly; e-side positions are offsets from the tile's first
+    // e-segment, f-side ones offsets from its first f-segment plus the tile offset (added
+    // here once per segment: it carries the same rounding as when added per pair)
     const double kk = p.k;
-    if (threadIdx.x == 0) {
-        const dfl ox = dfl_from(kk * (fx0 - ex0)), oy = dfl_from(kk * (fy0 - ey0));
-        sOff[0] = make_float2(ox.hi, ox.lo);
-        sOff[1] = make_float2(oy.hi, oy.lo);
-    }
+    const dfl offx = dfl_from(kk * (fx0 - ex0)), offy = dfl_from(kk * (fy0 - ey0));
     for (int t = threadIdx.x; t < 2 * TP; t += blockDim.x) {
         const bool isE = t < TP;
         const int l = isE ? t : t - TP;
@@ -751,16 +749,16 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
         const SegV a = load_seg(p.seg, N, s);
         float2* g = isE ? gE : gF;
         const double vals[7] = {kk * (a.x0 - (isE ? ex0 : fx0)), kk * (a.y0 - (isE ? ey0 : fy0)), kk * a.h * a.tx,
-                                kk * a.h * a.ty, a.tx, a.ty, a.h};
+                                kk * a.h * a.ty, kk * a.tx, kk * a.ty, a.h};
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
-            const dfl v = dfl_from(vals[c]);
+            dfl v = dfl_from(vals[c]);
+            if (!isE && c == 0) v = dfl_add(v, offx);
+            if (!isE && c == 1) v = dfl_add(v, offy);
             g[c * TP + l] = make_float2(v.hi, v.lo);
         }
     }
     __syncthreads();
-    const dfl k2 = dfl_from(p.k * p.k);
-    const dfl offx = dfl_mk(sOff[0]), offy = dfl_mk(sOff[1]);
     unsigned npts = 0;
     for (int pi = threadIdx.x; pi < TP * TP; pi += blockDim.x) {
         const int el = pi / TP, fl = pi % TP;
@@ -770,7 +768,7 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
         const int cyc = min(d, N - d);                    // min(|d|, N - |d|) without a modulo
         const dfl etx = dfl_mk(gE[4 * TP + el]), ety = dfl_mk(gE[5 * TP + el]);
         const dfl ftx = dfl_mk(gF[4 * TP + fl]), fty = dfl_mk(gF[5 * TP + fl]);
-        const dfl nd = dfl_mul(k2, dfl_fma(etx, ftx, dfl_mul(ety, fty)));   // nu_e . nu_f = t_e . t_f
+        const dfl nd = dfl_fma(etx, ftx, dfl_mul(ety, fty));   // k^2 nu_e . nu_f = k^2 t_e . t_f
         cdfl I[4], M0;
         if (cyc <= 1) {
             const int e = er < 0 ? er + N : er, f = fr < 0 ? fr + N : fr;
@@ -779,9 +777,9 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
             for (int c = 0; c < 4; ++c) I[c] = cdfl_from(Id[c]);
             M0 = cdfl_from(m);
         } else {
-            // y_f(0) - x_e(0) = (f offset) - (e offset) + tile offset
-            const dfl bx = dfl_add(dfl_sub(dfl_mk(gF[fl]), dfl_mk(gE[el])), offx);
-            const dfl by = dfl_add(dfl_sub(dfl_mk(gF[TP + fl]), dfl_mk(gE[TP + el])), offy);
+            // y_f(0) - x_e(0) = (f offset + tile offset) - (e offset)
+            const dfl bx = dfl_sub(dfl_mk(gF[fl]), dfl_mk(gE[el]));
+            const dfl by = dfl_sub(dfl_mk(gF[TP + fl]), dfl_mk(gE[TP + el]));
             const dfl uex = dfl_mk(gE[2 * TP + el]), uey = dfl_mk(gE[3 * TP + el]);
             const dfl vfx = dfl_mk(gF[2 * TP + fl]), vfy = dfl_mk(gF[3 * TP + fl]);
             // (scaled by k: kgap = k (gap + h_max) directly)
