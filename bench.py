@@ -35,14 +35,15 @@ METRIC = "factor s + RHS solves/s at N=16384: mixed/batched vs FP64 GPU, rel err
 # FP32 operations per second (an FFMA, FADD or FMUL counts as one operation)
 FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # FP32 operations per far-field Gauss point of the S/N assembly, which runs in
-# double-float arithmetic (df fma = 15 FP32 ops, df mul = 7, df add = 11): node offsets
-# 2 fma (30), r^2 1 mul + 1 fma (22), u = k^2 r^2 1 mul (7), t = (u - u_mid)/u_half 1 add +
-# 1 mul (18), J0 and Y0 as degree-7 polynomials 14 fma (210), g = (i/4) H0 4 scalings,
-# the two lambda-weighted row sums 4 fma (60)
-ASM_OPS_PER_POINT = 351
+# double-float arithmetic (df fma = 15 FP32 ops, df mul = 7, df add = 11) on geometry
+# scaled by k: node offsets 2 fma (30), u = (k r)^2 1 mul + 1 fma (22), t = (u - u_mid) /
+# u_half 1 add + 1 mul (18), J0/4 and -Y0/4 as degree-7 polynomials (the degrees whose
+# coefficients are below 1.1e-8 in 5 FP32 fma, the rest in 9 df fma: 140), the two
+# lambda-weighted row sums 4 fma (60)
+ASM_OPS_PER_POINT = 270
 # DRAM bytes (read + write) per launch from ncu captures of the kernels as they stand
 # (absent = not captured since the kernel last changed); the summaries are under profiles/
-TRAFFIC_BYTES = {"tc_rhs_SY": 14.704e9 + 0.275e9, "k_assemble": 0.0305e9 + 8.548e9}
+TRAFFIC_BYTES = {"tc_rhs_SY": 14.703e9 + 0.275e9, "k_assemble": 0.0315e9 + 8.548e9}
 
 
 def _peaks():
