@@ -41,7 +41,7 @@
 #include "tc_gemm.h"
 
 #define TC_BM 128
-#define TC_BN 128
+#define TC_BN 128                   // tile width (B part rows); 112 where it pads less (201, 402)
 #define TC_BK 32
 #define TC_STAGES 2
 #define TC_CHUNK_KB 16              // K' chunk of 16 x 32 = 512 between TMEM flushes
@@ -155,14 +155,18 @@ struct TcGemmArgs {
     double2* part;           // split partials [split][j][i] (M x m each), or null
 };
 
-template <int S>
+template <int S, int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcGemmArgs p) {
+    static_assert(BN == 128 || BN == 112, "tile width");
+    // a B slice tile fills BN rows of its 8 KiB slot (the descriptors' offsets stay those
+    // of 128-row tiles); the MMA's N and the accumulators' column stride are BN
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     // layout: [stage][A slices][B slices] tiles (reused as the epilogue stash once the
     // MMAs are done), then the barriers after max(stages, stash)
     const size_t stage_bytes = (size_t)2 * S * TC_TILE_BYTES;
+    const uint32_t stage_tx = (uint32_t)(S * TC_TILE_BYTES + S * (BN * TC_BK * 2));   // bytes TMA brings per stage
     const size_t data_bytes = max((size_t)TC_STAGES * stage_bytes, (size_t)TC_STASH_BYTES);
     uint64_t* bars = (uint64_t*)(smem + data_bytes);
     uint64_t* full = bars;                 // [2]
@@ -172,9 +176,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t* tmem_holder = (uint32_t*)(bars + 6);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = (p.Ncols + TC_BN - 1) / TC_BN;
+    const int n_tiles = (p.Ncols + BN - 1) / BN;
     const int m0 = (blockIdx.x / n_tiles) * TC_BM;
-    const int n0 = (blockIdx.x % n_tiles) * TC_BN;
+    const int n0 = (blockIdx.x % n_tiles) * BN;
     // this CTA's K' range (split-K over blockIdx.y)
     const int kb0 = blockIdx.y * p.kps;
     const int nkb = min(p.nkb - kb0, p.kps);
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t use = (uint32_t)(kb >> 1);
                 if (!mbar_wait(&empty[st], (use & 1u) ^ 1u, p.err)) break;
                 unsigned char* base = smem + st * stage_bytes;
-                mbar_expect_tx(&full[st], (uint32_t)stage_bytes);
+                mbar_expect_tx(&full[st], stage_tx);
                 for (int s = 0; s < S; ++s)
                     tma_load_3d(base + s * TC_TILE_BYTES, &mapA, &full[st], (kb0 + kb) * TC_BK, m0, s);
                 for (int t = 0; t < S; ++t)
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------------------------------------ MMA issuer
-            constexpr uint32_t idesc = idesc_bf16_f32(TC_BM, TC_BN);
+            constexpr uint32_t idesc = idesc_bf16_f32(TC_BM, BN);
             bool ok = true;
             for (int c = 0; c < nchunks && ok; ++c) {
                 if (c > 0 && !mbar_wait(acc_empty, (uint32_t)((c - 1) & 1), p.err)) { ok = false; break; }
@@ -247,7 +251,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 // the first MMA into each accumulator of a chunk overwrites it
                                 const bool first = (kk == 0 && s == 0 && t < TC_NACC);
                                 const uint32_t acc = (first && chunk_start) ? 0u : 1u;
-                                umma_bf16(tmem + a * TC_BN, dA + ((s * TC_TILE_BYTES + kk * 32) >> 4),
+                                umma_bf16(tmem + a * BN, dA + ((s * TC_TILE_BYTES + kk * 32) >> 4),
                                           dB + ((t * TC_TILE_BYTES + kk * 32) >> 4), idesc, acc);
                             }
                         }
@@ -260,56 +264,62 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else {
         // ---------------------------------------------------------------- epilogue
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        const int half = (warp - 2) >> 2;       // column half: 64 columns of the tile
+        const int half = (warp - 2) >> 2;       // column half: columns [64 half, min(BN, 64 half + 64))
         const int row = 32 * q + lane;
-        float hi[64], lo[64];
+        float2* stash = reinterpret_cast<float2*>(smem);           // [128][BN + 1]
+        // drains the accumulators chunk by chunk into (hi, lo) and stages them in the stash;
+        // NCB 16-column blocks (compile time: 4, or (BN - 64) / 16 in the second half)
+        auto drain = [&](auto ncb_c) -> bool {
+            constexpr int NCB = decltype(ncb_c)::value;
+            float hi[16 * NCB], lo[16 * NCB];
 #pragma unroll
-        for (int j = 0; j < 64; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
-        bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            if (!mbar_wait(acc_full, (uint32_t)(c & 1), p.err)) { ok = false; break; }
-            tc_fence_after();
-            const int nacc = min(S, TC_NACC);   // accumulators the MMAs wrote (TMEM is not zeroed)
+            for (int j = 0; j < 16 * NCB; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+            for (int c = 0; c < nchunks; ++c) {
+                if (!mbar_wait(acc_full, (uint32_t)(c & 1), p.err)) return false;
+                tc_fence_after();
+                const int nacc = min(S, TC_NACC);   // accumulators the MMAs wrote (TMEM is not zeroed)
 #pragma unroll
-            for (int a = 0; a < TC_NACC; ++a) {
+                for (int a = 0; a < TC_NACC; ++a) {
 #pragma unroll
-                for (int cb = 0; cb < 4; ++cb) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + a * TC_BN + 64 * half + 16 * cb, v);
-                    if (a < nacc) {
+                    for (int cb = 0; cb < NCB; ++cb) {
+                        float v[16];
+                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + a * BN + 64 * half + 16 * cb, v);
+                        if (a < nacc) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) df_add(hi[16 * cb + j], lo[16 * cb + j], v[j]);
+                            for (int j = 0; j < 16; ++j) df_add(hi[16 * cb + j], lo[16 * cb + j], v[j]);
+                        }
                     }
                 }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty);
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {      // renormalise (hi, lo)
-                const float s = __fadd_rn(hi[j], lo[j]);
-                lo[j] = __fsub_rn(lo[j], __fsub_rn(s, hi[j]));
-                hi[j] = s;
+                for (int j = 0; j < 16 * NCB; ++j) {      // renormalise (hi, lo)
+                    const float s = __fadd_rn(hi[j], lo[j]);
+                    lo[j] = __fsub_rn(lo[j], __fsub_rn(s, hi[j]));
+                    hi[j] = s;
+                }
             }
-        }
-        // stage (hi, lo) through the idle stage buffers (all TMA loads and MMAs are done),
-        // then write out with a plain coalesced loop
-        float2* stash = reinterpret_cast<float2*>(smem);           // [128][TC_BN + 1]
-        if (ok) {
+            // stage (hi, lo) through the idle stage buffers (all TMA loads and MMAs are
+            // done), then write out with a plain coalesced loop
 #pragma unroll
-            for (int j = 0; j < 64; ++j) stash[row * (TC_BN + 1) + 64 * half + j] = make_float2(hi[j], lo[j]);
-        }
+            for (int j = 0; j < 16 * NCB; ++j) stash[row * (BN + 1) + 64 * half + j] = make_float2(hi[j], lo[j]);
+            return true;
+        };
+        bool ok;
+        if constexpr (BN == 128) ok = drain(std::integral_constant<int, 4>{});
+        else ok = (half == 0) ? drain(std::integral_constant<int, 4>{}) : drain(std::integral_constant<int, (BN - 64) / 16>{});
         asm volatile("bar.sync 1, 256;" ::: "memory");          // the 8 epilogue warps
         if (ok) {
             // combine the part products: complex A and B: re = RR - II, im = RI + IR; one
             // complex operand: its two part rows (or columns) are re and im
             const int et = threadIdx.x - 64;                       // 0..255
             const int rdiv = p.aC ? 2 : 1, cdiv = p.bC ? 2 : 1;
-            const int NLR = TC_BM / rdiv, NLC = TC_BN / cdiv;      // logical outputs per tile
+            const int NLR = TC_BM / rdiv, NLC = BN / cdiv;         // logical outputs per tile
             const int lr0 = m0 / rdiv, lc0 = n0 / cdiv;
             const int nlr = min(NLR, p.Ml - lr0), nlc = min(NLC, p.ml - lc0);
             auto V = [&](int rr, int cc) {
-                const float2 v = stash[rr * (TC_BN + 1) + cc];
+                const float2 v = stash[rr * (BN + 1) + cc];
                 return dfl{v.x, v.y};
             };
             const bool plain = (p.alpha == 1.0 && p.beta == 0.0);
@@ -628,6 +638,7 @@ struct TcOperand {
     size_t exp_cap = 0;
     int cplx = 1;                     // complex operand: real and imaginary parts in separate rows
     int64_t lrows = 0;                // logical rows (A) / columns (B): rows = (cplx ? 2 : 1) lrows
+    int nslices = 0;                  // slices the map spans
     CUtensorMap map;
 };
 
@@ -652,18 +663,23 @@ static TcState* tcs(bem_ctx* h) {
 
 static int64_t pad32(int64_t x) { return (x + 31) / 32 * 32; }   // K, padded to whole 32-wide K blocks
 
-static bem_status encode_map(bem_ctx* h, TcOperand& op, int S) {
+// tensor map of an operand's slices: boxes of TC_BK (K') x box_rows (rows) x 1 (slice)
+static bem_status encode_map_box(bem_ctx* h, const TcOperand& op, int S, int box_rows, CUtensorMap* map) {
     bem_status st = get_encode(h);
     if (st != BEM_OK) return st;
     cuuint64_t dims[3] = {(cuuint64_t)op.Kp, (cuuint64_t)op.rows, (cuuint64_t)S};
     cuuint64_t strides[2] = {(cuuint64_t)(op.Kp * 2), (cuuint64_t)(op.Kp * op.rows * 2)};
-    cuuint32_t box[3] = {TC_BK, TC_BM, 1};
+    cuuint32_t box[3] = {TC_BK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = g_encode(&op.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.slices, dims, strides, box, estr,
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.slices, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return bem_fail(h, BEM_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
     return BEM_OK;
+}
+static bem_status encode_map(bem_ctx* h, TcOperand& op, int S) {
+    op.nslices = S;
+    return encode_map_box(h, op, S, TC_BM, &op.map);
 }
 
 static bem_status reserve(bem_ctx* h, TcOperand& op, int64_t rows, int64_t Kp, int S) {
@@ -784,17 +800,28 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     p.kps = p.nkb;
     p.part = nullptr;
     const size_t smem = gemm_smem(Sg);
+    // tile width: 112 when it pads the B part rows less than 128 does (the filter's 201 real
+    // or 2 x 201 complex columns: 224 and 448 instead of 256 and 512), for the usual slice counts
+    const int pad128 = (p.Ncols + 127) / 128 * 128, pad112 = (p.Ncols + 111) / 112 * 112;
+    const int BN = (pad112 < pad128 && (Sg == 5 || Sg == 6)) ? 112 : 128;
     void (*kern)(const CUtensorMap, const CUtensorMap, TcGemmArgs) = nullptr;
-    switch (Sg) {
-        case 3: kern = k_tc_gemm<3>; break;
-        case 4: kern = k_tc_gemm<4>; break;
-        case 5: kern = k_tc_gemm<5>; break;
-        case 6: kern = k_tc_gemm<6>; break;
-        case 7: kern = k_tc_gemm<7>; break;
+    switch (Sg * 1000 + BN) {
+        case 3128: kern = k_tc_gemm<3, 128>; break;
+        case 4128: kern = k_tc_gemm<4, 128>; break;
+        case 5128: kern = k_tc_gemm<5, 128>; break;
+        case 6128: kern = k_tc_gemm<6, 128>; break;
+        case 7128: kern = k_tc_gemm<7, 128>; break;
+        case 5112: kern = k_tc_gemm<5, 112>; break;
+        case 6112: kern = k_tc_gemm<6, 112>; break;
         default: return bem_fail(h, BEM_E_UNSUPPORTED, "tc_gemm: slices per operand must be 3..7");
     }
+    CUtensorMap mapB = B.map;
+    if (BN != TC_BM) {
+        bem_status st = encode_map_box(h, B, B.nslices, BN, &mapB);
+        if (st != BEM_OK) return st;
+    }
     BEM_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int mt = (p.M + TC_BM - 1) / TC_BM, nt = (p.Ncols + TC_BN - 1) / TC_BN;
+    const int mt = (p.M + TC_BM - 1) / TC_BM, nt = (p.Ncols + BN - 1) / BN;
     // split K' across CTAs (FP64 partials summed by k_splitk_reduce) when that fills the
     // SMs better: every tile costs the same, so the run time is (waves of CTAs) x (chunks
     // per split); the partials cost their write and read-back (at about 6 TB/s).  This
@@ -803,7 +830,7 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     const int T = mt * nt;
     const int nch = (p.nkb + TC_CHUNK_KB - 1) / TC_CHUNK_KB;
-    const double chunk_ms = (double)(Sg * (Sg + 1) / 2) * TC_CHUNK_KB * (TC_BK / 16) * 73.0 / 2.0e6;
+    const double chunk_ms = (double)(Sg * (Sg + 1) / 2) * TC_CHUNK_KB * (TC_BK / 16) * 73.0 / 2.0e6 * BN / 128.0;
     const double part_ms_per_split = (double)p.Ml * p.ml * 32.0 / 6.0e9;
     int splits = 1;
     double best = (double)((T + nsm - 1) / nsm) * nch * chunk_ms;
@@ -824,7 +851,7 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
         p.part = t->part;
     }
     dim3 grid((unsigned)(mt * nt), (unsigned)splits);
-    BEM_TIMED(h, tag, (kern<<<grid, TC_THREADS, smem, h->stream>>>(A.map, B.map, p)));
+    BEM_TIMED(h, tag, (kern<<<grid, TC_THREADS, smem, h->stream>>>(A.map, mapB, p)));
     BEM_LAUNCH(h, "k_tc_gemm");
     if (splits > 1) {
         const int64_t n = (int64_t)p.Ml * p.ml;
