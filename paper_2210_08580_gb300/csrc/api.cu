@@ -55,13 +55,22 @@ struct Carve {
     }
 };
 
-static void free_ptr(void** p) {
+static void free_ptr(bem_ctx* h, void** p) {
     if (*p) { cudaFree(*p); *p = nullptr; }
+    h->caps.erase(p);
 }
 
+// stage buffers keep their allocation from step to step (cudaFree would wait for the whole
+// device, other streams included); a buffer is reallocated only when it has to grow
 static bem_status ensure_alloc(bem_ctx* h, void** p, size_t bytes) {
-    if (*p) return BEM_OK;
+    auto it = h->caps.find(p);
+    if (*p && it != h->caps.end() && it->second >= bytes) return BEM_OK;
+    if (*p) {
+        BEM_CUDA(h, cudaStreamSynchronize(h->stream));
+        free_ptr(h, p);
+    }
     BEM_CUDA(h, cudaMalloc(p, bytes));
+    h->caps[p] = bytes;
     return BEM_OK;
 }
 
@@ -140,25 +149,21 @@ bem_status bem_create(bem_handle* out, int device, void* cuda_stream, const bem_
     return BEM_OK;
 }
 
+// Releases the buffers of the stages from from_stage on.  Recomputing a stage on a problem
+// of the same size keeps them (the stage counter says what they hold; ensure_alloc reuses or
+// grows them), so a step frees nothing; a new N (from_stage <= 1) or bem_destroy frees all.
 static void free_stage_buffers(bem_ctx* h, int from_stage) {
-    if (from_stage <= 1) {
-        free_ptr((void**)&h->S); free_ptr((void**)&h->W); free_ptr((void**)&h->D);
-        free_ptr((void**)&h->rexp); h->rexp_valid = false;
-        free_ptr((void**)&h->seg);
-        tc_release_operands(h);
-    }
-    if (from_stage <= 2) {
-        free_ptr((void**)&h->B); free_ptr((void**)&h->gm); free_ptr((void**)&h->Q);
-        free_ptr((void**)&h->Bs);
-    }
-    if (from_stage <= 3) {
-        free_ptr((void**)&h->sigma); free_ptr((void**)&h->E);
-        free_ptr((void**)&h->U); free_ptr((void**)&h->Vh);
-    }
-    if (from_stage <= 4) {
-        free_ptr((void**)&h->K); free_ptr((void**)&h->piv);
-        tc_release_solve(h);
-    }
+    if (from_stage > 1) return;
+    free_ptr(h, (void**)&h->S); free_ptr(h, (void**)&h->W); free_ptr(h, (void**)&h->D);
+    free_ptr(h, (void**)&h->rexp); h->rexp_valid = false;
+    free_ptr(h, (void**)&h->seg);
+    tc_release_operands(h);
+    free_ptr(h, (void**)&h->B); free_ptr(h, (void**)&h->gm); free_ptr(h, (void**)&h->Q);
+    free_ptr(h, (void**)&h->Bs);
+    free_ptr(h, (void**)&h->sigma); free_ptr(h, (void**)&h->E);
+    free_ptr(h, (void**)&h->U); free_ptr(h, (void**)&h->Vh);
+    free_ptr(h, (void**)&h->K); free_ptr(h, (void**)&h->piv);
+    tc_release_solve(h);
 }
 
 bem_status bem_destroy(bem_handle h) {
@@ -167,10 +172,10 @@ bem_status bem_destroy(bem_handle h) {
     cudaStreamSynchronize(h->stream);
     free_stage_buffers(h, 0);
     tc_destroy(h);
-    free_ptr(&h->work);
-    free_ptr((void**)&h->dev_err);
-    free_ptr((void**)&h->bar);
-    free_ptr((void**)&h->qpts);
+    free_ptr(h, &h->work);
+    free_ptr(h, (void**)&h->dev_err);
+    free_ptr(h, (void**)&h->bar);
+    free_ptr(h, (void**)&h->qpts);
     delete h;
     return BEM_OK;
 }
@@ -201,7 +206,7 @@ bem_status bem_assemble(bem_handle h, const double* verts, int64_t N, double k, 
     if (ops & BEM_OP_D) {
         if ((st = ensure_alloc(h, (void**)&h->D, sizeof(cplx) * NN)) != BEM_OK) return st;
     } else {
-        free_ptr((void**)&h->D);
+        free_ptr(h, (void**)&h->D);
     }
     h->N = N;
     h->k = k;

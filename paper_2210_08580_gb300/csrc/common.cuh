@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -95,6 +96,7 @@ struct bem_ctx {
     int* rexp = nullptr;              // 2N: largest IEEE exponent field per column of S, W (W
                                       // without its near band), taken during the assembly
     bool rexp_valid = false;          // rexp belongs to the S, W now held
+    std::map<void**, size_t> caps;   // bytes allocated behind each stage buffer (reused while large enough)
 
     // filter
     int64_t n = 0, M = 0, ncols = 0;  // n modes requested, ncols Fourier columns kept

@@ -1054,10 +1054,10 @@ bem_status tc_solve_refined(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x, int
         if ((st = slice_B(h, t->bbuf, T, 0, r, nrhs, 1, r)) != BEM_OK) return st;
         if ((st = tc_gemm(h, t->opU, t->bbuf, rho, N, 0, -1.0, 1.0, "tc_resid_UT")) != BEM_OK) return st;
         if ((st = launch_col_norm_ratio(h, rho, N, v, ldv, N, nrhs, dres)) != BEM_OK) return st;
-        BEM_CUDA(h, cudaMemcpyAsync(&res, dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        BEM_CUDA(h, cudaStreamSynchronize(h->stream));
         int e = 0;
-        BEM_CUDA(h, cudaMemcpy(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+        BEM_CUDA(h, cudaMemcpyAsync(&res, dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        BEM_CUDA(h, cudaMemcpyAsync(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        BEM_CUDA(h, cudaStreamSynchronize(h->stream));   // this stream only (not the whole device)
         if (e) {
             cudaMemset(h->dev_err, 0, sizeof(int));
             return bem_fail(h, (e & DEVERR_TIMEOUT) ? BEM_E_TIMEOUT : BEM_E_CUDA, "tensor-core solve: device error");
