@@ -446,19 +446,19 @@ __global__ void __launch_bounds__(256) k_exp_cols(const void* src, int is_real, 
     }
 }
 
-// bf16 bits of d 2^{-7s} for an integer |d| <= 128: d becomes a float through the
-// 1.5 2^23 bias (integer add, one FADD; the FP64 pipe's 64-bit integer conversion is
-// avoided), the power of two is exact, and with at most 8 significant bits the upper half
-// of the float is the bf16 value.
-__device__ __forceinline__ uint32_t digit_bf16(int d, int s) {
-    const float f = (__int_as_float(0x4B400000 + d) - 12582912.0f) * __int_as_float((127 - 7 * s) << 23);
-    return __float_as_uint(f) >> 16;
+// float bits of d 2^{-7s} for an integer |d| <= 128, whose upper half is the bf16 value
+// (at most 8 significant bits): adding d to the bit pattern of C = 1.5 2^{23-7s}, whose
+// ulp is 2^{-7s}, gives C + d 2^{-7s} exactly, and subtracting C leaves d 2^{-7s} (one
+// integer add and one FADD; checked against the scaled conversion for every d and s)
+__device__ __forceinline__ uint32_t digit_bits(int d, int s) {
+    const float c = __int_as_float((127 + 23 - 7 * s) << 23) * 1.5f;   // a constant per unrolled s
+    return __float_as_uint(__fsub_rn(__int_as_float(__float_as_int(c) + d), c));
 }
 
 // val 2^-e in (-1, 1) -> S slices: X = round(val 2^{7S - e}) (one rounding, half away from
 // zero), then balanced base-128 digits from the least significant up: d in [-64, 63] for
 // s >= 1 and the leading |d_0| <= 128; slice s stores d_s 2^{-7s} (exact in bf16), returned
-// here as bf16 bit patterns.  X is formed from the significand and exponent fields with
+// here as float bit patterns whose upper halves are the bf16 values.  X is formed from the significand and exponent fields with
 // integer shifts: |val| < 2^e makes the right shift 1075 + e - 7S - E at least 53 - 7S > 0.
 // Zeros and subnormals give 0.
 __device__ __forceinline__ void split_digits(double val, int e, int S, uint32_t* d) {
@@ -484,11 +484,11 @@ __device__ __forceinline__ void split_digits(double val, int e, int S, uint32_t*
             int q = cur & 127;
             if (q >= 64) q -= 128;
             cur = (cur - q) >> 7;
-            d[s] = digit_bf16(q, s);
+            d[s] = digit_bits(q, s);
             ++t;
         }
         if (t == 3) cur += hi;                  // S = 4: the upper part is the leading digit
-        d[0] = digit_bf16(cur, 0);
+        d[0] = digit_bits(cur, 0);
         return;
     }
 #pragma unroll
@@ -497,9 +497,9 @@ __device__ __forceinline__ void split_digits(double val, int e, int S, uint32_t*
         int q = (int)(X & 127);
         if (q >= 64) q -= 128;
         X = (X - q) >> 7;
-        d[s] = digit_bf16(q, s);
+        d[s] = digit_bits(q, s);
     }
-    d[0] = digit_bf16((int)X, 0);
+    d[0] = digit_bits((int)X, 0);
 }
 
 // Planar slices.  A operand (M x K): a complex row i becomes rows 2i (real part) and 2i+1
@@ -514,16 +514,17 @@ template <class Get>
 __device__ __forceinline__ void slice_part(Get v, int e, int S, __nv_bfloat16* out, int64_t row, int64_t Kp,
                                            int64_t k0, size_t stride) {
     uint32_t w[TC_SMAX][SLICE_VEC / 2];
-#pragma unroll
-    for (int s = 0; s < TC_SMAX; ++s)
-#pragma unroll
-        for (int q = 0; q < SLICE_VEC / 2; ++q) w[s][q] = 0u;
+    uint32_t ev[TC_SMAX];
 #pragma unroll
     for (int u = 0; u < SLICE_VEC; ++u) {
         uint32_t d[TC_SMAX];
         split_digits(v(u), e, S, d);
+        // two values' bf16 halves into one word: the even value low, the odd one high
 #pragma unroll
-        for (int s = 0; s < TC_SMAX; ++s) w[s][u >> 1] |= d[s] << (16 * (u & 1));
+        for (int s = 0; s < TC_SMAX; ++s) {
+            if ((u & 1) == 0) ev[s] = d[s];
+            else w[s][u >> 1] = __byte_perm(ev[s], d[s], 0x7632);
+        }
     }
     uint4* o = reinterpret_cast<uint4*>(out + row * Kp + k0);
     const size_t st16 = stride / 8;                // one slice, in 16-byte units
