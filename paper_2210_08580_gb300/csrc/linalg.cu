@@ -227,7 +227,8 @@ __global__ void k_iir(const cplx* __restrict__ in, cplx* __restrict__ out, int64
         cplx acc = cmk(0, 0);
         double c = 1.0;
         for (int j = 0; j < IIR_LOOK; ++j) {
-            int64_t ii = a - j; ii %= N; if (ii < 0) ii += N;
+            int64_t ii = a - j;                  // >= -IIR_LOOK: wrapped by adding N
+            while (ii < 0) ii += N;
             const cplx v = x[ii * si];
             acc.x += c * v.x; acc.y += c * v.y;
             c *= -r;
@@ -244,7 +245,8 @@ __global__ void k_iir(const cplx* __restrict__ in, cplx* __restrict__ out, int64
         cplx acc = cmk(0, 0);
         double c = 1.0;
         for (int j = 0; j < IIR_LOOK; ++j) {
-            int64_t ii = (last + j) % N;
+            int64_t ii = last + j;               // < N + IIR_LOOK: wrapped by subtracting N
+            while (ii >= N) ii -= N;
             const cplx v = x[ii * si];
             acc.x += c * v.x; acc.y += c * v.y;
             c *= -r;

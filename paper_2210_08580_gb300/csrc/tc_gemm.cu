@@ -898,42 +898,59 @@ __global__ void __launch_bounds__(256, 1) k_band_left(const double2* __restrict_
     float4* Ws = bsm + (size_t)KT * 32;                 // [BAND_JB][2 band + 1]
     const int64_t m0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * BAND_JB;
     const int tid = threadIdx.y * 32 + threadIdx.x;
+    // cyclic indices wrapped by adding or subtracting N (one step when N exceeds the tile's
+    // reach, a few for the smallest N); four iterations unrolled so their loads are in
+    // flight together
+#pragma unroll 4
     for (int idx = tid; idx < KT * 32; idx += 256) {
         const int kk = idx / 32, ml = idx % 32;
         int64_t k = j0 - band + kk;
-        k = ((k % N) + N) % N;
+        while (k < 0) k += N;
+        while (k >= N) k -= N;
         const int64_t m = m0 + ml;
         double2 y = make_double2(0.0, 0.0);
         if (m < nc) y = Y[m + k * nc];
         Ys[idx] = cdfl_pack({dfl_from_bits(y.x), dfl_from_bits(y.y)});
     }
     const int BW = 2 * band + 1;
+#pragma unroll 4
     for (int idx = tid; idx < BAND_JB * BW; idx += 256) {
         const int jl = idx / BW, t = idx % BW;
         const int64_t j = j0 + jl;
         double2 w = make_double2(0.0, 0.0);
         if (j < N) {
             int64_t k = j - band + t;
-            k = ((k % N) + N) % N;
+            while (k < 0) k += N;
+            while (k >= N) k -= N;
             w = W[k + j * N];
         }
         Ws[idx] = cdfl_pack({dfl_from_bits(w.x), dfl_from_bits(w.y)});
     }
     __syncthreads();
+    // each thread accumulates its BAND_JB / 8 outputs (columns jj = threadIdx.y + 8 i)
+    // together, so their independent double-float chains hide each other's latency
+    constexpr int NJ = BAND_JB / 8;
     const int ml = threadIdx.x;
     const int64_t m = m0 + ml;
-    for (int jj = threadIdx.y; jj < BAND_JB; jj += 8) {
-        const int64_t j = j0 + jj;
-        cdfl acc = cdfl_zero();
-        for (int t = 0; t < BW; ++t) {
+    cdfl acc[NJ];
+#pragma unroll
+    for (int i = 0; i < NJ; ++i) acc[i] = cdfl_zero();
+    for (int t = 0; t < BW; ++t) {
+#pragma unroll
+        for (int i = 0; i < NJ; ++i) {
+            const int jj = threadIdx.y + 8 * i;
             const cdfl y = cdfl_unpack(Ys[(jj + t) * 32 + ml]);
             const cdfl w = cdfl_unpack(Ws[jj * BW + t]);
-            acc.re = dfl_fma(y.re, w.re, dfl_fma(dfl_neg(y.im), w.im, acc.re));
-            acc.im = dfl_fma(y.re, w.im, dfl_fma(y.im, w.re, acc.im));
+            acc[i].re = dfl_fma(y.re, w.re, dfl_fma(dfl_neg(y.im), w.im, acc[i].re));
+            acc[i].im = dfl_fma(y.re, w.im, dfl_fma(y.im, w.re, acc[i].im));
         }
+    }
+#pragma unroll
+    for (int i = 0; i < NJ; ++i) {
+        const int64_t j = j0 + threadIdx.y + 8 * i;
         if (m < nc && j < N) {
             double2* o = out + m + j * nc;
-            *o = cadd(*o, cdfl_to(acc));
+            *o = cadd(*o, cdfl_to(acc[i]));
         }
     }
 }
