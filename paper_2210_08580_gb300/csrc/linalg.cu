@@ -1084,8 +1084,8 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(int* p, int v) {
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Rounds are ordered by data, not by grid barriers: every column carries a version (the
@@ -1114,11 +1114,14 @@ __global__ void __launch_bounds__(JAC_NT) k_jacobi(float4* X, int n, int* ver, i
                 tourney(round, idx, np, p, q);
                 if (p > q) { int t = p; p = q; q = t; }
                 if (tid == 0) {
+                    // wait for one column's version, then the other's: one acquire load per
+                    // poll (an acquire orders the loads after it, so two per poll would run
+                    // one after the other)
                     int ok = 1;
+                    bool rp = (p >= n);
                     for (long long spins = 0;; ++spins) {
-                        const bool rp = (p >= n) || ld_acquire(ver + p) >= target;
-                        const bool rq = (q >= n) || ld_acquire(ver + q) >= target;
-                        if (rp && rq) break;
+                        if (!rp) rp = ld_acquire(ver + p) >= target;
+                        if (rp && ((q >= n) || ld_acquire(ver + q) >= target)) break;
                         if (spins > (1ll << 24)) { atomicOr(err, DEVERR_TIMEOUT); ok = 0; break; }
                         if ((spins & 255) == 255 && *(volatile int*)err) { ok = 0; break; }
                         if (spins > 32) __nanosleep(32);
@@ -1185,9 +1188,11 @@ __global__ void __launch_bounds__(JAC_NT) k_jacobi(float4* X, int n, int* ver, i
                 }
                 __syncthreads();              // the pair's stores precede its release
                 if (tid == 0) {
-                    // the release orders the CTA's stores (made cumulative by the barrier above)
-                    if (p < n) st_release(ver + p, target + 1);
-                    if (q < n) st_release(ver + q, target + 1);
+                    // one release fence orders the CTA's stores (made cumulative by the barrier
+                    // above) before both versions; a second st.release would wait for the first
+                    __threadfence();
+                    if (p < n) st_relaxed(ver + p, target + 1);
+                    if (q < n) st_relaxed(ver + q, target + 1);
                 }
             }
         }
