@@ -49,31 +49,28 @@ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
 enum { DEVERR_TIMEOUT = 1, DEVERR_SINGULAR = 2, DEVERR_BOUNDS = 4, DEVERR_NAN = 8 };
 
 // Bounded grid barrier for kernels launched with cudaLaunchCooperativeKernel (all CTAs
-// co-resident).  `bar[0]` counts arrivals, `bar[1]` is the generation.  A CTA that waits
+// co-resident).  `bar[0]` counts the arrivals of the launch.  A CTA that waits
 // longer than the spin limit sets DEVERR_TIMEOUT in *err and returns false; callers then
 // return, so every CTA ends (the others time out as well).
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+    // bar[0] counts arrivals over the whole launch (zeroed before it): the CTAs of barrier g
+    // are through once the count reaches (g + 1) nblocks, so the last arrival releases the
+    // others by its own increment (no reset, no second word on the critical path)
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned* vgen = bar + 1;
-        unsigned gen = *vgen;
-        __threadfence();
-        unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == gen) {
-                if (++spins > (1ll << 26)) { atomicOr(err, DEVERR_TIMEOUT); ok = 0; break; }
-                if ((spins & 1023) == 0 && *(volatile int*)err) { ok = 0; break; }
-                if (spins > 64) __nanosleep(64);
-            }
+        __threadfence();                                   // this CTA's writes before its arrival
+        const unsigned arrived = atomicAdd(bar, 1u);
+        const unsigned target = (arrived / nblocks + 1) * nblocks;
+        volatile unsigned* vcount = bar;
+        long long spins = 0;
+        while ((int)(*vcount - target) < 0) {
+            if (++spins > (1ll << 26)) { atomicOr(err, DEVERR_TIMEOUT); ok = 0; break; }
+            if ((spins & 1023) == 0 && *(volatile int*)err) { ok = 0; break; }
+            if (spins > 64) __nanosleep(64);
         }
-        __threadfence();
+        __threadfence();                                   // the others' writes after it
         if (*(volatile int*)err) ok = 0;
         s_ok = ok;
     }
