@@ -21,12 +21,14 @@
 // After each chunk the epilogue warps add the accumulators into double-float (hi, lo)
 // registers; the result is rescaled by 2^{e_i + f_j - 14} and written in FP64.
 //
-// Kernel: one 128 x 128 tile of C' per CTA (split over K' when that fills the GPU better), 10 warps: warp 0 issues TMA loads (3D tensor
+// Kernel: one 128 x BN tile of C' per CTA, BN = 128, or 112 when that pads the B part rows
+// less (the filter's 201 and 402 columns), split over K' when that fills the GPU better;
+// 10 warps: warp 0 issues TMA loads (3D tensor
 // maps over the stacked slices, 64-byte swizzle, 32-element K blocks, 2 stages), warp 1
 // allocates TMEM and issues the MMAs (S is a template parameter, so the S(S+1)/2 x 2 MMAs
 // of a K block are one straight-line sequence with constant descriptor offsets: a loop
 // that rebuilt descriptors per MMA issued slower than the tensor pipe executes), warps
-// 2..9 drain TMEM (2 warps per TMEM lane quarter, 64 columns each).  Every mbarrier wait is
+// 2..9 drain TMEM (2 warps per TMEM lane quarter, 64 and BN - 64 columns).  Every mbarrier wait is
 // bounded; a timeout sets the handle's device error word and the CTA winds down, freeing
 // its TMEM.
 #include <cuda.h>
