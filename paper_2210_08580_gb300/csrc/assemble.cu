@@ -1132,9 +1132,10 @@ __device__ __forceinline__ void dfl_sincos(dfl x, dfl& sn, dfl& cs) {
 //   h2-part base phi_a                              ([h2]_i = <phi_i, u_inc>)
 __global__ void __launch_bounds__(256) k_rhs(const double* seg, int N, const double* angles, double k,
                                              cplx* f, cplx* hz, int64_t ld) {
-    __shared__ float4 sf0[257], sf1[257], sh0[257], sh1[257];
+    // a CTA writes 255 vertices from the 256 segments around them (one per thread)
+    __shared__ float4 sf0[256], sf1[256], sh0[256], sh1[256];
     __shared__ float2 s_d[3];                 // d_x, d_y, k (double-float)
-    const int i0 = blockIdx.x * 256, w = blockIdx.y;
+    const int i0 = blockIdx.x * 255, w = blockIdx.y;
     if (threadIdx.x == 0) {
         double dy_, dx_;
         sincos(angles[w], &dy_, &dx_);
@@ -1143,8 +1144,11 @@ __global__ void __launch_bounds__(256) k_rhs(const double* seg, int N, const dou
     }
     __syncthreads();
     const dfl dxd = dfl_mk(s_d[0]), dyd = dfl_mk(s_d[1]), kd = dfl_mk(s_d[2]);
-    for (int t = threadIdx.x; t < 257; t += 256) {
-        const int e = ((i0 - 1 + t) % N + N) % N;
+    {
+        const int t = threadIdx.x;
+        int e = i0 - 1 + t;                   // in [-1, N + 254]: wrapped by adding or subtracting N
+        while (e < 0) e += N;
+        while (e >= N) e -= N;
         const dfl x0 = dfl_from_bits(seg[e]), y0 = dfl_from_bits(seg[N + e]);
         const dfl tx = dfl_from_bits(seg[2 * N + e]), ty = dfl_from_bits(seg[3 * N + e]);
         const dfl he = dfl_from_bits(seg[4 * N + e]);
@@ -1179,7 +1183,7 @@ __global__ void __launch_bounds__(256) k_rhs(const double* seg, int N, const dou
     }
     __syncthreads();
     const int i = i0 + threadIdx.x;
-    if (i >= N) return;
+    if (threadIdx.x >= 255 || i >= N) return;
     const int t = threadIdx.x;
     // vertex i: segment i (local t+1) as node 0, segment i-1 (local t) as node 1
     if (f) f[(int64_t)i + (int64_t)w * ld] = cdfl_to(cdfl_add(cdfl_unpack(sf0[t + 1]), cdfl_unpack(sf1[t])));
@@ -1187,7 +1191,7 @@ __global__ void __launch_bounds__(256) k_rhs(const double* seg, int N, const dou
 }
 
 bem_status launch_rhs(bem_ctx* h, const double* angles, int64_t nrhs, cplx* f, cplx* hz, int64_t ld) {
-    dim3 grid((unsigned)((h->N + 255) / 256), (unsigned)nrhs);
+    dim3 grid((unsigned)((h->N + 254) / 255), (unsigned)nrhs);
     BEM_TIMED(h, "k_rhs", (k_rhs<<<grid, 256, 0, h->stream>>>(h->seg, (int)h->N, angles, h->k, f, hz, ld)));
     BEM_LAUNCH(h, "k_rhs");
     return BEM_OK;
