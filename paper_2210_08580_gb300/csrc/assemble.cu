@@ -336,12 +336,13 @@ __device__ void pair_self(double h, const SeriesCoef& sc, cplx I[4]) {
     cplx i11 = cmk(0, 0), i01 = cmk(0, 0);
     double h2m = h * h;
     for (int m = 0; m < sc.nm; ++m) {
-        const double p = 2.0 * m;
-        const double T11 = (2.0 / 3.0) / (p + 1) - 1.0 / (p + 2) + (1.0 / 3.0) / (p + 4);
-        const double L11 = -(2.0 / 3.0) / ((p + 1) * (p + 1)) + 1.0 / ((p + 2) * (p + 2)) -
-                           (1.0 / 3.0) / ((p + 4) * (p + 4));
-        const double T01 = (1.0 / 3.0) / (p + 1) - (1.0 / 3.0) / (p + 4);
-        const double L01 = -(1.0 / 3.0) / ((p + 1) * (p + 1)) + (1.0 / 3.0) / ((p + 4) * (p + 4));
+        // 1/(p + i) from the reciprocal table (p = 2m; FP64 division is a long sequence on
+        // GB300's narrow FP64 pipe)
+        const double r1 = c_rcp[2 * m + 1], r2 = c_rcp[2 * m + 2], r4 = c_rcp[2 * m + 4];
+        const double T11 = (2.0 / 3.0) * r1 - r2 + (1.0 / 3.0) * r4;
+        const double L11 = -(2.0 / 3.0) * (r1 * r1) + r2 * r2 - (1.0 / 3.0) * (r4 * r4);
+        const double T01 = (1.0 / 3.0) * r1 - (1.0 / 3.0) * r4;
+        const double L01 = -(1.0 / 3.0) * (r1 * r1) + (1.0 / 3.0) * (r4 * r4);
         const cplx A = sc.A[m];
         const double B = sc.B[m];
         i11.x += h2m * (A.x * T11 + B * (lnh * T11 + L11));
@@ -393,13 +394,14 @@ __device__ void adjacent_node(const SegV& e, const SegV& f, const SeriesCoef& sc
     double R2m = 1.0;
     for (int m = 0; m < sc.nm; ++m) {
         for (int j = 0; j < 3; ++j) {
-            const double a = 2.0 + j + 2.0 * m;
-            Gj[j].x += R2m * ((sc.A[m].x + sc.B[m] * lnR) / a - sc.B[m] / (a * a));
-            Gj[j].y += R2m * (sc.A[m].y / a);
+            // 1/a and 1/b (a = 2 + j + 2m, b = a + 1) from the reciprocal table
+            const double ra = c_rcp[2 + j + 2 * m];
+            Gj[j].x += R2m * ((sc.A[m].x + sc.B[m] * lnR) * ra - sc.B[m] * (ra * ra));
+            Gj[j].y += R2m * (sc.A[m].y * ra);
             if (WD) {
-                const double b = 3.0 + j + 2.0 * m;
-                Hj[j].x += R2m * ((sc.E[m].x + sc.F[m] * lnR) / b - sc.F[m] / (b * b));
-                Hj[j].y += R2m * (sc.E[m].y / b);
+                const double rb = c_rcp[3 + j + 2 * m];
+                Hj[j].x += R2m * ((sc.E[m].x + sc.F[m] * lnR) * rb - sc.F[m] * (rb * rb));
+                Hj[j].y += R2m * (sc.E[m].y * rb);
             }
         }
         R2m *= R2;
@@ -412,7 +414,7 @@ __device__ void adjacent_node(const SegV& e, const SegV& f, const SeriesCoef& sc
         if (WD) {
             cplx sd = cmk(0, 0);
             for (int j = 0; j < 3; ++j) {
-                sd.x += c[ab][j] * (Hs / (j + 1.0) + Hj[j].x);
+                sd.x += c[ab][j] * (Hs * c_rcp[j + 1] + Hj[j].x);
                 sd.y += c[ab][j] * Hj[j].y;
             }
             const double fJ = wt * e.h * sfac * cef, fJt = wt * f.h * tfac * cfe;
