@@ -14,6 +14,9 @@
  *    contiguous torch tensor of shape (nrhs, N).
  *  - A handle owns all internal matrices (S, N, D, the filtered block B, the skeleton
  *    U, V^H and the LU of the Woodbury core) and its workspace; bem_destroy frees them.
+ *    Repeating a stage on a problem of the same size reuses these allocations (a call
+ *    that needs larger ones reallocates them, after synchronising the handle's stream);
+ *    bem_assemble with a new N releases them first.
  *  - All work is enqueued on the handle's CUDA stream.  Calls return after enqueueing,
  *    except where a host-side result is requested (noted per call), in which case the
  *    call synchronises that stream.
