@@ -1,0 +1,42 @@
+"""bench.py's roofline arithmetic on made-up per-kernel reports (host logic only): the
+dominant kernel, the bf16 flop count of the split products (slice pairs times the real
+part products) and the FP32-operation count of the assembly."""
+import types
+
+import pytest
+
+import bench
+
+
+def _args(N=16384, nrhs=1024):
+    return types.SimpleNamespace(N=N, nrhs=nrhs)
+
+
+def test_tensor_roofline_of_the_rhs_product():
+    rep = {"tc_rhs_SY": (3, 3 * 18.4), "k_assemble": (3, 3 * 16.7), "k_jacobi": (3, 3 * 5.3)}
+    roof = bench.roofline(rep, _args(), 201, 201, 6.7e8)
+    assert roof["kernel"] == "tc_rhs_SY" and roof["bound"] == "tensor"
+    assert roof["slice_pairs"] == 15                      # five slices per operand
+    flops = 15 * 2 * 4 * 16384 * 1024 * 16384              # complex x complex: four part products
+    assert roof["achieved"] == pytest.approx(flops / 18.4e-3 / 1e12)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    assert roof["traffic"] == pytest.approx(bench.TRAFFIC_BYTES["tc_rhs_SY"])
+
+
+def test_alu_roofline_of_the_assembly():
+    rep = {"k_assemble": (2, 2 * 16.7), "tc_rhs_SY": (2, 2 * 10.0)}
+    roof = bench.roofline(rep, _args(), 201, 201, 6.7e8)
+    assert roof["kernel"] == "k_assemble" and roof["bound"] == "alu"
+    assert roof["ops_per_unit"] == bench.ASM_OPS_PER_POINT and roof["units_per_launch"] == 6.7e8
+    assert roof["achieved"] == pytest.approx(6.7e8 * bench.ASM_OPS_PER_POINT / 16.7e-3 / 1e12)
+    assert roof["peak"] == pytest.approx(152 * 128 * 2.07e9 / 1e12)
+
+
+def test_filter_products_count_real_and_complex_parts():
+    # Q^T S: the real Fourier basis times a complex operator, two part products per pair;
+    # Y N: complex times complex, four
+    a = bench.tc_gemm_flops("tc_filter_QtS", 1024, 64, 21, 21, 6)
+    b = bench.tc_gemm_flops("tc_filter_YN", 1024, 64, 21, 21, 6)
+    assert a == pytest.approx(21 * 2 * 2 * 21 * 1024 * 1024)
+    assert b == pytest.approx(2 * a)
+    assert bench.tc_gemm_flops("k_iir", 1024, 64, 21, 21, 6) is None
