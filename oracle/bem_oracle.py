@@ -53,6 +53,8 @@ __all__ = [
     "calderon_system", "filtered_solve_literal", "filtered_solve_projected",
     "woodbury_solve", "mie_current", "circle_spectra", "g_norm",
     "farfield_constant", "farfield_matrix", "mie_farfield", "misfit_and_gradients",
+    "chord_length", "gram_dft_eigs", "gram_power_rows", "gram_power_cols", "filtered_block",
+    "compress_block", "filtered_condition", "filtered_solve_blocks", "assembled_column_blocks",
 ]
 
 # --------------------------------------------------------------------------------------
@@ -323,22 +325,63 @@ def _scatter(mesh, k, e, f, I, J, ops):
     return out
 
 
-def assemble(verts, k: float, ops: str = "SWD"):
-    """Dense Galerkin matrices {'S','W','D'} (complex128, N x N), by looping over all
-    ordered segment pairs.  W is the hypersingular operator N of the paper."""
+def _assemble_columns(verts, k, f0, f1, ops):
+    """Contributions of the segment pairs (e, f), every e and f0 <= f < f1, to the vertex
+    columns j = f + b, i.e. columns f0 .. f1 (mod N): a dict of N x (f1 - f0 + 1) blocks."""
     mesh = Mesh(verts)
     N = mesh.N
-    mats = {op: np.zeros((N, N), dtype=np.complex128) for op in ops}
-    need_d = "D" in ops
-    E, F = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
-    E = E.ravel(); F = F.ravel()
-    for c0 in range(0, len(E), 200000):
-        e = E[c0:c0 + 200000]; f = F[c0:c0 + 200000]
-        I, J, _ = pair_integrals(mesh, k, e, f, need_d)
-        for op, lst in _scatter(mesh, k, e, f, I, J, ops).items():
+    nb = f1 - f0 + 1
+    out = {op: np.zeros((N, nb), dtype=np.complex128) for op in ops}
+    e = np.tile(np.arange(N), f1 - f0)
+    f = np.repeat(np.arange(f0, f1), N)
+    for c0 in range(0, len(e), 200000):
+        ec = e[c0:c0 + 200000]; fc = f[c0:c0 + 200000]
+        I, J, _ = pair_integrals(mesh, k, ec, fc, "D" in ops)
+        for op, lst in _scatter(mesh, k, ec, fc, I, J, ops).items():
             for ii, jj, val in lst:
-                np.add.at(mats[op], (ii, jj), val)
+                # column jj = f + b (mod N) sits at block column f - f0 + b
+                np.add.at(out[op], (ii, (jj - f0) % N), val)
+    return out
+
+
+def assembled_column_blocks(verts, k: float, starts, block: int = 32, ops: str = "SW", workers: int = 1,
+                            pool=None):
+    """Yields (f0, blocks) for the segment columns f0 .. f0 + block - 1 of each f0 in
+    ``starts`` (see _assemble_columns), in order; ``pool`` (a multiprocessing pool) or
+    ``workers`` > 1 (a pool started with ``spawn``) spreads the blocks over processes."""
+    verts = np.ascontiguousarray(np.asarray(verts, dtype=np.float64))
+    N = verts.shape[0]
+    jobs = [(verts, k, f0, min(f0 + block, N), ops) for f0 in starts]
+    if pool is not None:
+        for j, blk in zip(jobs, pool.imap(_assemble_star, jobs)):
+            yield j[2], blk
+    elif workers <= 1:
+        for j in jobs:
+            yield j[2], _assemble_columns(*j)
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as p:
+            for j, blk in zip(jobs, p.imap(_assemble_star, jobs)):
+                yield j[2], blk
+
+
+def assemble(verts, k: float, ops: str = "SWD", workers: int = 1, block: int = 32, pool=None):
+    """Dense Galerkin matrices {'S','W','D'} (complex128, N x N), by looping over all
+    ordered segment pairs, in blocks of ``block`` segment columns.  W is the hypersingular
+    operator N of the paper.  ``workers`` > 1 (or a ``pool``) spreads the blocks over
+    processes; the sum over pairs is the same."""
+    verts = np.ascontiguousarray(np.asarray(verts, dtype=np.float64))
+    N = verts.shape[0]
+    mats = {op: np.zeros((N, N), dtype=np.complex128) for op in ops}
+    for f0, blk in assembled_column_blocks(verts, k, range(0, N, block), block, ops, workers, pool):
+        for op in ops:
+            for c in range(blk[op].shape[1]):
+                mats[op][:, (f0 + c) % N] += blk[op][:, c]
     return mats
+
+
+def _assemble_star(args):
+    return _assemble_columns(*args)
 
 
 def assemble_entries(verts, k: float, rows, cols, ops: str = "SWD"):
@@ -567,6 +610,118 @@ def filtered_solve_projected(mats, verts, f, M, tol, alpha=0.0, h2=None, include
     B = Q.T @ Cx
     return dict(x=Gmh @ j2, j2=j2, rank=r, sigma=s, B=B, Bhat=Bhat, Q=Q, beta=beta,
                 Ux=Gmh @ U2, Vxh=V2h @ Gh, vx=Gmh @ v2, Gh=Gh, Gmh=Gmh)
+
+
+# --------------------------------------------------------------------------------------
+# Block route (Sec. III-A, IV on an equal-chord mesh): the same filtered operator and
+# compressed solution as the projected route, formed from the n x N block
+#     B = Q^T (G^-1 S G^-1 N - I/4 - alpha G^-1 D)
+# without any N x N product or dense factor, so it reaches the large meshes
+# (O(n N^2) work after the assembly).
+# --------------------------------------------------------------------------------------
+
+
+def chord_length(verts) -> float:
+    """The common chord h of an equal-chord mesh, as the mean chord.  The vertex coordinates
+    of a generated equal-chord mesh are rounded, so its chords agree only to about
+    1e-16 |r| / h relative (6e-12 at 16384 vertices on a unit-size curve); spreads up to
+    1e-10 are accepted and read as one chord h."""
+    h = Mesh(verts).h
+    assert np.max(h) - np.min(h) <= 1e-10 * np.mean(h), "mesh is not equal-chord"
+    return float(np.mean(h))
+
+
+def gram_dft_eigs(N: int, h: float):
+    """Eigenvalues of the equal-chord Gram matrix G = circ(2h/3; h/6) in DFT order:
+    G e_m = lambda_m e_m for e_m = (exp(2 pi i m j / N))_j, lambda_m = h (2 + cos(2 pi m/N)) / 3."""
+    return h * (2.0 + np.cos(2.0 * math.pi * np.arange(N) / N)) / 3.0
+
+
+def gram_power_rows(X, h: float, p: float):
+    """X G^p for the rows of X (..., N): G is circulant and symmetric, so G^p is the
+    circulant with eigenvalues lambda_m^p and x G^p = ifft(fft(x) lambda^p)."""
+    X = np.asarray(X)
+    lam = gram_dft_eigs(X.shape[-1], h) ** p
+    return np.fft.ifft(np.fft.fft(X, axis=-1) * lam, axis=-1)
+
+
+def gram_power_cols(X, h: float, p: float):
+    """G^p X for the columns of X (N, ...)."""
+    return gram_power_rows(np.asarray(X).T, h, p).T
+
+
+def filtered_block(mats, verts, M: int, alpha: float = 0.0, include_kernel: bool = True):
+    """B = Q^T C_x (n x N), C_x = G^-1 S G^-1 N - I/4 - alpha G^-1 D the compact part in
+    nodal coordinates, so that the filtered operator (Sec. IV-A) is P C_x = Q B.  The columns
+    of Q are eigenvectors of G (Q^T G^-1 = diag(1/g) Q^T), hence
+        B = diag(1/g) (Q^T S) G^-1 N - alpha diag(1/g) Q^T D - Q^T / 4."""
+    verts = np.asarray(verts)
+    N = verts.shape[0]
+    h = chord_length(verts)
+    Q = fourier_basis(N, M, include_kernel)
+    g = gram_eigs(N, h, M, include_kernel)
+    Y = gram_power_rows(Q.T @ mats["S"], h, -1.0)             # (Q^T S) G^-1
+    B = (Y @ mats["W"]) / g[:, None] - Q.T / 4.0
+    if alpha != 0.0:
+        B = B - alpha * (Q.T @ mats["D"]) / g[:, None]
+    return B, Q, g, h
+
+
+def compress_block(B, Q, g, h, tol: float):
+    """Compression in the paper's orthonormal basis (Sec. IV-C, j2 = G^1/2 x): the filtered
+    compact part there is Q B^ with B^ = diag(g^1/2) B G^-1/2.  With the SVD
+    B^ = E diag(sigma) F^H and r = #{sigma_i >= tol sigma_1}, the truncation Q E_r E_r^H B^
+    reads, back in nodal coordinates, Q B ~= U V^H with
+        U = Q diag(g^-1/2) E_r,   V^H = E_r^H diag(g^1/2) B."""
+    Bhat = gram_power_rows(np.sqrt(g)[:, None] * B, h, -0.5)
+    E, s, _ = np.linalg.svd(Bhat, full_matrices=False)
+    r = int(np.sum(s >= tol * s[0])) if tol > 0 else int(np.sum(s > 0))
+    U = (Q / np.sqrt(g)[None, :]) @ E[:, :r]
+    Vh = E[:, :r].conj().T @ (np.sqrt(g)[:, None] * B)
+    return U, Vh, s, r, Bhat
+
+
+def filtered_condition(beta, Bhat, Q):
+    """2-norm condition number of the filtered operator A2 = beta I + Q B^ in the
+    orthonormal basis, exactly, from a 2n x 2n matrix.  In an orthonormal basis [Q, Q_perp]
+    A2 = [[beta I + B^ Q, B^ Q_perp], [0, beta I]]; with the SVD B^ Q_perp = U_c diag(s_c) V_c^H
+    the span of Q_perp V_c carries [[beta I + B^ Q, U_c diag(s_c)], [0, beta I]] and the rest of
+    Q_perp (N - 2n dimensions) is mapped to beta times itself."""
+    N, n = Q.shape
+    if N < 2 * n:
+        return float(np.linalg.cond(beta * np.eye(N) + Q @ Bhat))
+    C = Bhat - (Bhat @ Q) @ Q.T                                # B^ Q_perp Q_perp^T
+    Uc, sc, _ = np.linalg.svd(C, full_matrices=False)
+    T = np.zeros((2 * n, 2 * n), dtype=np.complex128)
+    T[:n, :n] = beta * np.eye(n) + Bhat @ Q
+    T[:n, n:] = Uc * sc[None, :]
+    T[n:, n:] = beta * np.eye(n)
+    sv = np.linalg.svd(T, compute_uv=False)
+    if N > 2 * n:
+        sv = np.append(sv, abs(beta))
+    return float(np.max(sv) / np.min(sv))
+
+
+def filtered_solve_blocks(mats, verts, f, M: int, tol: float, alpha: float = 0.0, h2=None,
+                          include_kernel: bool = True):
+    """The filtered fast direct solver of Sec. IV on an equal-chord mesh, in nodal
+    coordinates x (j2 = G^1/2 x):
+        v = G^-1 S G^-1 f - alpha G^-1 h2          (right-hand side, Sec. II / IV-A)
+        B = Q^T C_x                                (filtered_block)
+        U V^H ~= Q B at tol                        (compress_block)
+        x = (beta I + U V^H)^-1 v                  (Woodbury, Sec. IV-C)
+    Also returns the uncompressed filtered solution x_full = (beta I + Q B)^-1 v (Woodbury
+    with the rank-n factors Q, B) and the condition number of the filtered operator."""
+    B, Q, g, h = filtered_block(mats, verts, M, alpha, include_kernel)
+    beta = (1.0 + 2.0 * alpha) / 4.0
+    v = gram_power_cols(mats["S"] @ gram_power_cols(f, h, -1.0), h, -1.0)
+    if alpha != 0.0:
+        v = v - alpha * gram_power_cols(h2, h, -1.0)
+    U, Vh, s, r, Bhat = compress_block(B, Q, g, h, tol)
+    x = woodbury_solve(beta, U, Vh, v)
+    x_full = woodbury_solve(beta, Q.astype(np.complex128), B, v)
+    kappa = filtered_condition(beta, Bhat, Q)
+    return dict(x=x, x_full=x_full, rank=r, sigma=s, B=B, U=U, Vh=Vh, vx=v, beta=beta, kappa=kappa, h=h)
 
 
 # --------------------------------------------------------------------------------------

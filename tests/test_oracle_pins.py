@@ -376,3 +376,81 @@ def test_misfit_gradients_match_finite_differences(star_case):
     fd = (J_of(route["vx"] + h * dv) - J_of(route["vx"] - h * dv)) / (2 * h)
     pred = float(np.sum((np.conj(res["grad_v"]) * dv).real))
     assert abs(fd - pred) <= 1e-6 * max(1.0, abs(pred))
+
+
+# ------------------------------------------------------------------ block route (large meshes)
+
+
+def test_assemble_entries_matches_assemble(star_case):
+    """assemble_entries (the four segment pairs around (i, j), used on the large meshes)
+    gives every entry of the dense assembly, for S, N and D."""
+    v40, _, _ = I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), 40)
+    k = 1.7
+    mats = O.assemble(v40, k, "SWD")
+    rows, cols = np.meshgrid(np.arange(40), np.arange(40), indexing="ij")
+    ent = O.assemble_entries(v40, k, rows.ravel(), cols.ravel(), "SWD")
+    for op in "SWD":
+        err = np.max(np.abs(ent[op] - mats[op].ravel())) / np.max(np.abs(mats[op]))
+        assert err <= 1e-15, (op, err)
+
+
+def test_assemble_parallel_blocks_equal_serial():
+    v, _, _ = I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), 37)
+    a = O.assemble(v, 1.1, "SWD", block=37)
+    b = O.assemble(v, 1.1, "SWD", workers=2, block=5)
+    for op in "SWD":
+        assert np.max(np.abs(a[op] - b[op])) <= 1e-15 * np.max(np.abs(a[op]))
+
+
+def test_gram_powers_match_dense():
+    """G^-1 and G^-1/2 of the equal-chord Gram matrix by its DFT eigenvalues equal the dense
+    solve and the dense symmetric square root of G (Sec. III-A, G^-1/2)."""
+    v, _, h = I.equal_chord_mesh(I.random_star(4), 50)
+    G = O.gram(v)
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((50, 3)) + 1j * rng.standard_normal((50, 3))
+    hh = O.chord_length(v)
+    assert abs(hh - h) <= 1e-14 * h
+    assert np.max(np.abs(O.gram_power_cols(X, hh, -1.0) - np.linalg.solve(G, X))) <= 1e-12 * np.max(np.abs(X)) / hh
+    w, V = np.linalg.eigh(G)
+    Gm12 = (V * w ** -0.5) @ V.T
+    assert np.max(np.abs(O.gram_power_cols(X, hh, -0.5) - Gm12 @ X)) <= 1e-12 * np.max(np.abs(Gm12 @ X))
+    assert np.max(np.abs(O.gram_power_rows(X.T, hh, -0.5) - X.T @ Gm12)) <= 1e-12 * np.max(np.abs(Gm12 @ X))
+    assert np.allclose(np.sort(O.gram_dft_eigs(50, hh)), w, rtol=1e-13, atol=0)
+
+
+@pytest.fixture(scope="module")
+def star384():
+    v, _, _ = I.equal_chord_mesh(I.random_star(2), 384)
+    k = 2.0
+    return v, k, O.assemble(v, k, "SWD", workers=4)
+
+
+@pytest.mark.parametrize("alpha,tol", [(0.0, 1e-10), (0.0, 1e-4), (0.5, 1e-10)])
+def test_block_route_matches_literal(star384, alpha, tol):
+    """The block route (n x N block B, FFT Gram powers, 2n x 2n condition number) reproduces
+    the literal route of the paper (dense G^-1/2, eigenvectors of L~, the full N x N Z and
+    P C2, Sec. III-A / IV) on a 384-vertex random star, EFIE and CFIE."""
+    v, k, mats = star384
+    ang = I.planewave_angles(5)
+    f = O.rhs_planewave(v, k, ang)
+    h2 = O.rhs_planewave_h(v, k, ang) if alpha else None
+    M = 20
+    lit = O.filtered_solve_literal(mats, v, f, 2 * M + 1, tol, alpha=alpha, h2=h2)
+    blk = O.filtered_solve_blocks(mats, v, f, M, tol, alpha=alpha, h2=h2)
+    assert blk["rank"] == lit["rank"]
+    n = 2 * M + 1
+    assert np.max(np.abs(blk["sigma"] - lit["sigma"][:n])) <= 1e-12 * lit["sigma"][0]
+    assert np.all(lit["sigma"][n:] <= 1e-13 * lit["sigma"][0])
+    for key in ("x", "x_full"):
+        err = np.max(np.abs(blk[key] - lit[key])) / np.max(np.abs(lit[key]))
+        assert err <= 1e-12, (key, err)
+    # x-coordinate right-hand side and the condition number of the filtered operator
+    assert np.max(np.abs(blk["vx"] - lit["Gmh"] @ lit["v2"])) <= 1e-12 * np.max(np.abs(blk["vx"]))
+    A2 = lit["beta"] * np.eye(v.shape[0]) + lit["PC"]
+    kd = np.linalg.cond(A2)
+    assert abs(blk["kappa"] - kd) <= 1e-9 * kd, (blk["kappa"], kd)
+    # B against the projected route's x-coordinate block (formed there as Q^T G^-1/2 C2 G^1/2
+    # from dense square roots, which costs about two more digits of rounding)
+    pro = O.filtered_solve_projected(mats, v, f, M, tol, alpha=alpha, h2=h2)
+    assert np.max(np.abs(blk["B"] - pro["B"])) <= 1e-11 * np.max(np.abs(pro["B"]))
