@@ -49,12 +49,13 @@ from scipy import special
 __all__ = [
     "Mesh", "green", "green_dnu_factor", "gauss01", "graded_gauss01",
     "pair_integrals", "assemble", "assemble_entries", "gram", "laplacian",
-    "rhs_planewave", "rhs_planewave_h", "fourier_basis", "gram_eigs", "filter_literal",
+    "rhs_planewave", "rhs_planewave_h", "rhs_pointsource", "rhs_pointsource_h", "fourier_basis", "gram_eigs", "filter_literal",
     "calderon_system", "filtered_solve_literal", "filtered_solve_projected",
     "woodbury_solve", "mie_current", "circle_spectra", "g_norm",
     "farfield_constant", "farfield_matrix", "mie_farfield", "misfit_and_gradients",
     "chord_length", "gram_dft_eigs", "gram_power_rows", "gram_power_cols", "filtered_block",
     "compress_block", "filtered_condition", "filtered_solve_blocks", "assembled_column_blocks",
+    "segment_pair_means", "maue_second_difference",
 ]
 
 # --------------------------------------------------------------------------------------
@@ -302,15 +303,16 @@ def pair_integrals(mesh: Mesh, k: float, e, f, need_d: bool = True):
 # Galerkin matrices (Sec. II):  S, N (= W here, Maue form) and D
 # --------------------------------------------------------------------------------------
 
-_SIG = np.array([-1.0, 1.0])        # d lambda_a / ds = _SIG[a] / h
 
 
 def _scatter(mesh, k, e, f, I, J, ops):
-    """Vertex-matrix contributions of segment pairs (e, f): i = e + a, j = f + b."""
+    """Vertex-matrix contributions of segment pairs (e, f): i = e + a, j = f + b.  For N
+    (Maue's form) only the k^2 term -k^2 (nu_e . nu_f) I_ab is scattered here ('K'); its
+    derivative term is kept per segment pair (segment_pair_means) and applied as an exact
+    second difference (maue_second_difference)."""
     N = mesh.N
     out = {}
     nudot = np.einsum("pc,pc->p", mesh.nu[e], mesh.nu[f])
-    M0 = I.sum(axis=(1, 2)) / (mesh.h[e] * mesh.h[f])           # int int g / (h_e h_f)
     for a in range(2):
         for b in range(2):
             ii = (e + a) % N
@@ -318,20 +320,45 @@ def _scatter(mesh, k, e, f, I, J, ops):
             if "S" in ops:
                 out.setdefault("S", []).append((ii, jj, I[:, a, b]))
             if "W" in ops:
-                out.setdefault("W", []).append(
-                    (ii, jj, _SIG[a] * _SIG[b] * M0 - (k * k) * nudot * I[:, a, b]))
+                out.setdefault("K", []).append((ii, jj, -(k * k) * nudot * I[:, a, b]))
             if "D" in ops:
                 out.setdefault("D", []).append((ii, jj, J[:, a, b]))
     return out
 
 
+def segment_pair_means(mesh, e, f, I):
+    """M0(e, f) = int_e int_f g2 / (h_e h_f) = sum_ab I_ab / (h_e h_f): with phi_i' = sigma / h
+    on the segments around vertex i, the derivative term of Maue's form for the pair is
+    sigma_a sigma_b M0(e, f)."""
+    return I.sum(axis=(1, 2)) / (mesh.h[e] * mesh.h[f])
+
+
+def maue_second_difference(Mg):
+    """Derivative term of Maue's form, sum_{a,b} sigma_a sigma_b Mg[i - a, j - b] with
+    sigma_0 = -1, sigma_1 = +1 (phi_i' = -1/h on segment i, +1/h on segment i - 1), for the
+    N x N matrix of segment-pair means Mg[e, f] = M0(e, f), evaluated as
+        (Mg[i-1, j-1] - Mg[i-1, j]) - (Mg[i, j-1] - Mg[i, j]).
+    Away from the diagonal the four means agree to many digits, and the difference of two
+    close doubles is exact (Sterbenz), so the term's rounding is that of the small
+    differences rather than of the means: its row sums, which vanish identically
+    (sum_b sigma_b = 0), stay at that level.  At low k the row sums of N are O(k^2) of the
+    means and carry the Calderon product's smallest eigenvalue."""
+    R = np.roll(Mg, 1, axis=1) - Mg                                # R[e, j] = Mg[e, j-1] - Mg[e, j]
+    return np.roll(R, 1, axis=0) - R                               # R[i-1, j] - R[i, j]
+
+
 def _assemble_columns(verts, k, f0, f1, ops):
     """Contributions of the segment pairs (e, f), every e and f0 <= f < f1, to the vertex
-    columns j = f + b, i.e. columns f0 .. f1 (mod N): a dict of N x (f1 - f0 + 1) blocks."""
+    columns j = f + b, i.e. columns f0 .. f1 (mod N): a dict of N x (f1 - f0 + 1) blocks
+    ('S', 'D', and 'K' the k^2 term of N), plus 'Mg' (N x (f1 - f0)), the segment-pair means
+    of the segment columns f0 .. f1 - 1."""
     mesh = Mesh(verts)
     N = mesh.N
     nb = f1 - f0 + 1
-    out = {op: np.zeros((N, nb), dtype=np.complex128) for op in ops}
+    keys = [op for op in ops if op != "W"] + (["K"] if "W" in ops else [])
+    out = {op: np.zeros((N, nb), dtype=np.complex128) for op in keys}
+    if "W" in ops:
+        out["Mg"] = np.zeros((N, f1 - f0), dtype=np.complex128)
     e = np.tile(np.arange(N), f1 - f0)
     f = np.repeat(np.arange(f0, f1), N)
     for c0 in range(0, len(e), 200000):
@@ -341,6 +368,8 @@ def _assemble_columns(verts, k, f0, f1, ops):
             for ii, jj, val in lst:
                 # column jj = f + b (mod N) sits at block column f - f0 + b
                 np.add.at(out[op], (ii, (jj - f0) % N), val)
+        if "W" in ops:
+            out["Mg"][ec, fc - f0] = segment_pair_means(mesh, ec, fc, I)
     return out
 
 
@@ -373,10 +402,17 @@ def assemble(verts, k: float, ops: str = "SWD", workers: int = 1, block: int = 3
     verts = np.ascontiguousarray(np.asarray(verts, dtype=np.float64))
     N = verts.shape[0]
     mats = {op: np.zeros((N, N), dtype=np.complex128) for op in ops}
+    Mg = np.zeros((N, N), dtype=np.complex128) if "W" in ops else None
     for f0, blk in assembled_column_blocks(verts, k, range(0, N, block), block, ops, workers, pool):
         for op in ops:
-            for c in range(blk[op].shape[1]):
-                mats[op][:, (f0 + c) % N] += blk[op][:, c]
+            src = blk["K"] if op == "W" else blk[op]                # N: its k^2 term first
+            for c in range(src.shape[1]):
+                mats[op][:, (f0 + c) % N] += src[:, c]
+        if Mg is not None:
+            Mg[:, f0:f0 + blk["Mg"].shape[1]] = blk["Mg"]
+    if Mg is not None:
+        # Maue's form: N = (second difference of the segment-pair means) + k^2 term
+        mats["W"] = maue_second_difference(Mg) + mats["W"]
     return mats
 
 
@@ -392,20 +428,23 @@ def assemble_entries(verts, k: float, rows, cols, ops: str = "SWD"):
     rows = np.asarray(rows, dtype=np.int64); cols = np.asarray(cols, dtype=np.int64)
     out = {op: np.zeros(len(rows), dtype=np.complex128) for op in ops}
     need_d = "D" in ops
-    nudot_cache = {}
+    M = {}
     for a in range(2):
         for b in range(2):
             e = (rows - a) % N
             f = (cols - b) % N
             I, J, _ = pair_integrals(mesh, k, e, f, need_d)
             nudot = np.einsum("pc,pc->p", mesh.nu[e], mesh.nu[f])
-            M0 = I.sum(axis=(1, 2)) / (mesh.h[e] * mesh.h[f])
+            M[a, b] = segment_pair_means(mesh, e, f, I)               # Mg[i - a, j - b]
             if "S" in ops:
                 out["S"] += I[:, a, b]
             if "W" in ops:
-                out["W"] += _SIG[a] * _SIG[b] * M0 - (k * k) * nudot * I[:, a, b]
+                out["W"] += -(k * k) * nudot * I[:, a, b]
             if "D" in ops:
                 out["D"] += J[:, a, b]
+    if "W" in ops:
+        # the derivative term in the order of maue_second_difference
+        out["W"] = ((M[1, 1] - M[1, 0]) - (M[0, 1] - M[0, 0])) + out["W"]
     return out
 
 
@@ -472,6 +511,40 @@ def rhs_planewave_h(verts, k: float, angles):
     val = np.exp(1j * k * np.einsum("eqc,wc->eqw", x, d))
     wgt = (mesh.h[:, None] * ws[None, :])
     out = np.zeros((N, len(ang)), dtype=np.complex128)
+    for a, lam in enumerate((1.0 - s, s)):
+        out += np.roll(np.einsum("eq,eqw->ew", wgt * lam[None, :], val), a, axis=0)
+    return out
+
+
+def rhs_pointsource(verts, k: float, sources):
+    """f_i = -<phi_i, d u_inc / d nu> for the line source u_inc(x) = g2(|x - r0|) (the paper's
+    2D "dipole" source of Sec. V read as a z-directed line source): d u_inc / d nu =
+    green_dnu_factor(k, rho) ((x - r0).nu) with rho = |x - r0|.  Returns (N, nsrc); 16-point
+    Gauss-Legendre per segment (the source lies off the curve)."""
+    mesh = Mesh(verts)
+    N = mesh.N
+    src = np.asarray(sources, dtype=np.float64).reshape(-1, 2)
+    s, ws, x = _segment_gauss(mesh)
+    diff = x[:, :, None, :] - src[None, None, :, :]                  # x - r0, (N, q, nsrc, 2)
+    rho = np.linalg.norm(diff, axis=-1)
+    val = green_dnu_factor(k, rho) * np.einsum("eqwc,ec->eqw", diff, mesh.nu)
+    wgt = (mesh.h[:, None] * ws[None, :])
+    f = np.zeros((N, src.shape[0]), dtype=np.complex128)
+    for a, lam in enumerate((1.0 - s, s)):
+        f += np.roll(-np.einsum("eq,eqw->ew", wgt * lam[None, :], val), a, axis=0)
+    return f
+
+
+def rhs_pointsource_h(verts, k: float, sources):
+    """[h2]_i = <phi_i, u_inc> for the line source u_inc = g2(|x - r0|)."""
+    mesh = Mesh(verts)
+    N = mesh.N
+    src = np.asarray(sources, dtype=np.float64).reshape(-1, 2)
+    s, ws, x = _segment_gauss(mesh)
+    rho = np.linalg.norm(src[None, None, :, :] - x[:, :, None, :], axis=-1)
+    val = green(k, rho)
+    wgt = (mesh.h[:, None] * ws[None, :])
+    out = np.zeros((N, src.shape[0]), dtype=np.complex128)
     for a, lam in enumerate((1.0 - s, s)):
         out += np.roll(np.einsum("eq,eqw->ew", wgt * lam[None, :], val), a, axis=0)
     return out

@@ -454,3 +454,91 @@ def test_block_route_matches_literal(star384, alpha, tol):
     # from dense square roots, which costs about two more digits of rounding)
     pro = O.filtered_solve_projected(mats, v, f, M, tol, alpha=alpha, h2=h2)
     assert np.max(np.abs(blk["B"] - pro["B"])) <= 1e-11 * np.max(np.abs(pro["B"]))
+
+
+def test_pointsource_rhs_divergence_theorem():
+    """Line source outside the curve: u = g2(|x - r0|) solves the Helmholtz equation inside,
+    so sum_i f_i = -int_Gamma du/dnu = k^2 int_Omega u over the polygon (triangle fan,
+    collapsed Gauss); and <phi, u> sums to the boundary integral of u."""
+    for verts in (I.regular_polygon(48), I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), 64)[0]):
+        k = 1.7
+        src = np.array([[3.0, 0.0], [-1.2, 2.5]])
+        f = O.rhs_pointsource(verts, k, src)
+        xs, ws = O.gauss01(24)
+        U, V = np.meshgrid(xs, xs, indexing="ij")
+        W2 = np.outer(ws, ws) * U
+        P1 = np.roll(verts, -1, axis=0)
+        area = []
+        for r0 in src:
+            tot = 0j
+            for a_, b_ in zip(verts, P1):
+                pts = U[..., None] * (a_[None, None, :] + V[..., None] * (b_ - a_)[None, None, :])
+                jac = abs(a_[0] * b_[1] - a_[1] * b_[0])
+                tot += jac * np.sum(W2 * O.green(k, np.linalg.norm(pts - r0, axis=-1)))
+            area.append(tot)
+        assert np.allclose(f.sum(axis=0), k * k * np.array(area), rtol=1e-12, atol=0)
+
+
+def test_pointsource_rhs_is_the_planewave_limit():
+    """Far away, the line source looks like a plane wave: g2(|x - R d|) ~ C0 e^{ikR}/sqrt(R)
+    e^{-ik d.x} (large-argument Hankel form), so the source at R(cos p, sin p) gives the
+    plane wave travelling along -(cos p, sin p), times C0 e^{ikR}/sqrt(R), to O(1/R)."""
+    verts = I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), 64)[0]
+    k, p = 1.3, 0.7
+    errs = []
+    for R in (1e3, 1e4):
+        src = R * np.array([[math.cos(p), math.sin(p)]])
+        fp = O.rhs_pointsource(verts, k, src)[:, 0]
+        fw = O.rhs_planewave(verts, k, [p + math.pi])[:, 0]
+        scale = O.farfield_constant(k) * np.exp(1j * k * R) / math.sqrt(R)
+        errs.append(np.max(np.abs(fp - scale * fw)) / np.max(np.abs(scale * fw)))
+    assert errs[1] < 2e-3 and 7 < errs[0] / errs[1] < 13, errs
+
+
+def test_fig2_spectral_claims_on_the_ellipse():
+    """Fig. 2 (Sec. V), ellipse 1.42 x 1.32, k = 0.4, line source at (3, 0), filtering point
+    21: projected on the singular vectors q_m of the filter (eigenvectors of L~, smoothest
+    first), (a) the compact part C2 grows with the index (the discretisation's spectral
+    deviation), (b) the filtered part P C2 has no component beyond the n kept modes, and
+    (c) the right-hand side is band-limited with respect to the filter."""
+    N, k, n = 128, 0.4, 21
+    v, _, _ = I.equal_chord_mesh(I.ellipse(1.42, 1.32), N)
+    mats = O.assemble(v, k, "SW")
+    f = O.rhs_pointsource(v, k, [[3.0, 0.0]])
+    G, L = O.gram(v), O.laplacian(v)
+    Z2, v2, Gh, Gmh = O.calderon_system(mats, G, f)
+    C2 = Z2 - np.eye(N) / 4.0
+    lam, V = np.linalg.eigh(Gmh @ L @ Gmh)
+    p = np.linalg.norm(V.T @ C2, axis=1)
+    # past the lowest few modes (where the low-frequency part of C2 is O(ka)^2) the projected
+    # magnitude grows with the index, by about two orders towards the mesh's Nyquist end
+    assert np.mean(p[N // 2:]) > 30.0 * np.mean(p[8:n]), (np.mean(p[N // 2:]), np.mean(p[8:n]))
+    assert np.all(np.diff(p[8:N // 2:8]) > 0)
+    P, _ = O.filter_literal(v, n)
+    pf = np.linalg.norm(V.T @ (P @ C2), axis=1)
+    assert np.max(pf[n:]) <= 1e-12 * np.max(pf)
+    pv = np.abs(V.T @ v2[:, 0])
+    assert np.max(pv[n:]) <= 1e-3 * np.max(pv)
+    assert np.max(pv[3 * n:]) <= 1e-11 * np.max(pv)
+    assert np.linalg.norm(v2[:, 0] - P @ v2[:, 0]) <= 1e-4 * np.linalg.norm(v2[:, 0])
+
+
+def test_hypersingular_null_space_at_low_frequency():
+    """Maue's form: the derivative term of N has vanishing row sums (sum_b sigma_b = 0), so
+    N 1 equals the k^2 term -k^2 sum <phi_i, (nu_x . nu_y) g2 phi_j> exactly.  At k = 1e-3 that
+    row sum is O(k^2) of the entries' segment-pair means, so it survives only if the
+    derivative term is formed without rounding the means against each other (the exact
+    second difference)."""
+    N, k = 256, 1e-3
+    v, _, _ = I.equal_chord_mesh(I.cos_star(1.0, 0.3, 5), N)
+    W = O.assemble(v, k, "W")["W"]
+    mesh = O.Mesh(v)
+    E, F = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    E, F = E.ravel(), F.ravel()
+    Iq, _, _ = O.pair_integrals(mesh, k, E, F, False)
+    nud = np.einsum("pc,pc->p", mesh.nu[E], mesh.nu[F])
+    K1 = np.zeros(N, dtype=np.complex128)
+    for a in range(2):
+        np.add.at(K1, (E + a) % N, -(k * k) * nud * Iq[:, a, :].sum(axis=1))
+    err = np.max(np.abs(W.sum(axis=1) - K1)) / np.max(np.abs(K1))
+    assert err <= 1e-7, err
