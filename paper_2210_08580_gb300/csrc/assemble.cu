@@ -273,28 +273,26 @@ static void build_bessel_table(std::vector<double>& tab, std::vector<float>& tab
     }
 }
 
+// The tables depend on nothing but the fit, so the host copy is built once per process;
+// each handle uploads its own device copy (from its memory provider) at its first assembly.
 static std::mutex g_btab_mutex;
-static double* g_btab[64] = {nullptr};
-static float4* g_btabf[64] = {nullptr};
+static std::vector<double> g_btab_host;
+static std::vector<float> g_btabf_host;
 
 static bem_status bessel_table(bem_ctx* h, const double** out, const float4** outf) {
-    std::lock_guard<std::mutex> lk(g_btab_mutex);
-    if (h->device < 0 || h->device >= 64) return bem_fail(h, BEM_E_INVALID, "bad device");
-    if (!g_btab[h->device]) {
-        std::vector<double> tab;
-        std::vector<float> tabf;
-        build_bessel_table(tab, tabf);
-        double* d = nullptr;
-        float* df = nullptr;
-        BEM_CUDA(h, cudaMalloc((void**)&d, tab.size() * sizeof(double)));
-        BEM_CUDA(h, cudaMemcpy(d, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
-        BEM_CUDA(h, cudaMalloc((void**)&df, tabf.size() * sizeof(float)));
-        BEM_CUDA(h, cudaMemcpy(df, tabf.data(), tabf.size() * sizeof(float), cudaMemcpyHostToDevice));
-        g_btab[h->device] = d;
-        g_btabf[h->device] = reinterpret_cast<float4*>(df);
+    if (!h->btab) {
+        {
+            std::lock_guard<std::mutex> lk(g_btab_mutex);
+            if (g_btab_host.empty()) build_bessel_table(g_btab_host, g_btabf_host);
+        }
+        const size_t nb = g_btab_host.size() * sizeof(double), nf = g_btabf_host.size() * sizeof(float);
+        BEM_CUDA(h, bem_dmalloc(h, (void**)&h->btab, nb));
+        BEM_CUDA(h, bem_dmalloc(h, (void**)&h->btabf, nf));
+        BEM_CUDA(h, cudaMemcpy(h->btab, g_btab_host.data(), nb, cudaMemcpyHostToDevice));
+        BEM_CUDA(h, cudaMemcpy(h->btabf, g_btabf_host.data(), nf, cudaMemcpyHostToDevice));
     }
-    *out = g_btab[h->device];
-    *outf = g_btabf[h->device];
+    *out = h->btab;
+    *outf = h->btabf;
     return BEM_OK;
 }
 
@@ -732,36 +730,59 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     float4* sI = reinterpret_cast<float4*>(smem_raw);               // TP*TP*4 complex df
     float4* sM = sI + TP * TP * 4;                                   // TP*TP: sum_ab I / (h_e h_f)
     float2* sND = reinterpret_cast<float2*>(sM + TP * TP);          // TP*TP: k^2 nu_e . nu_f
-    float2* gE = sND + TP * TP;                                      // 7*TP: ox, oy, ux, uy, k tx, k ty, h
+    // e side: 7*TP (ox, oy, ux, uy, k tx, k ty, h); f side: 9*TP (the same, then ox, oy for
+    // the tile's second e-anchor)
+    float2* gE = sND + TP * TP;
     float2* gF = gE + 7 * TP;
+    __shared__ int s_mexp;                                           // largest exponent field of the means
+    __shared__ unsigned char eSel[TP];                               // e-anchor of each e-segment (0, 1)
+    if (threadIdx.x == 0) s_mexp = 0;
     const int N = p.N;
     const int i0 = ti * T, j0 = tj * T;
-    const int e0 = (i0 - 1 + N) % N, f0 = (j0 - 1 + N) % N;
-    const double ex0 = p.seg[e0], ey0 = p.seg[N + e0], fx0 = p.seg[f0], fy0 = p.seg[N + f0];
-    // positions, segment vectors and tangents are kept multiplied by k, so (k r)^2 and
-    // k^2 t_e . t_f come out directly; e-side positions are offsets from the tile's first
-    // e-segment, f-side ones offsets from its first f-segment plus the tile offset (added
-    // here once per segment: it carries the same rounding as when added per pair)
+    // Positions, segment vectors and tangents are kept multiplied by k, so (k r)^2 and
+    // k^2 t_e . t_f come out directly.  Positions are offsets from the segment's anchor (the
+    // first segment of its block of 32), and a pair's separation is (anchor difference +
+    // f offset) - e offset: the same operations on the same operands whichever tile holds
+    // the pair, so a segment pair on a tile boundary gets the same integrals in both tiles
+    // (N's second differences then telescope exactly), while nearby pairs keep their relative
+    // geometry to double-float precision.  A tile's 32 segments span at most two anchors
+    // per side; the f offsets are stored with each e-anchor's difference already added.
     const double kk = p.k;
-    const dfl offx = dfl_from(kk * (fx0 - ex0)), offy = dfl_from(kk * (fy0 - ey0));
+    const int aE0 = ((i0 - 1 + N) % N) & ~31;                     // e-segments in use: anchors aE0, aE1
+    const int aE1 = (aE0 + 32 < N) ? aE0 + 32 : 0;
     for (int t = threadIdx.x; t < 2 * TP; t += blockDim.x) {
         const bool isE = t < TP;
         const int l = isE ? t : t - TP;
         const int s = ((isE ? i0 : j0) - 1 + l + N) % N;
+        const int a_s = s & ~31;
         const SegV a = load_seg(p.seg, N, s);
+        const double ax = p.seg[a_s], ay = p.seg[N + a_s];
         float2* g = isE ? gE : gF;
-        const double vals[7] = {kk * (a.x0 - (isE ? ex0 : fx0)), kk * (a.y0 - (isE ? ey0 : fy0)), kk * a.h * a.tx,
-                                kk * a.h * a.ty, kk * a.tx, kk * a.ty, a.h};
+        const double vals[7] = {kk * (a.x0 - ax), kk * (a.y0 - ay), kk * a.h * a.tx, kk * a.h * a.ty, kk * a.tx,
+                                kk * a.ty, a.h};
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
-            dfl v = dfl_from(vals[c]);
-            if (!isE && c == 0) v = dfl_add(v, offx);
-            if (!isE && c == 1) v = dfl_add(v, offy);
+            const dfl v = dfl_from(vals[c]);
             g[c * TP + l] = make_float2(v.hi, v.lo);
+        }
+        if (isE) {
+            eSel[l] = (a_s == aE0) ? 0 : 1;
+        } else {
+            // f offset + (anchor of f - e-anchor), for both e-anchors of the tile
+            const dfl ox = dfl_mk(g[l]), oy = dfl_mk(g[TP + l]);
+#pragma unroll
+            for (int ae = 0; ae < 2; ++ae) {
+                const int aEs = ae ? aE1 : aE0;
+                const dfl adx = dfl_from(kk * (ax - p.seg[aEs])), ady = dfl_from(kk * (ay - p.seg[N + aEs]));
+                const dfl bx = dfl_add(adx, ox), by = dfl_add(ady, oy);
+                g[(ae ? 7 : 0) * TP + l] = make_float2(bx.hi, bx.lo);
+                g[(ae ? 8 : 1) * TP + l] = make_float2(by.hi, by.lo);
+            }
         }
     }
     __syncthreads();
     unsigned npts = 0;
+    int mexp = 0;
     for (int pi = threadIdx.x; pi < TP * TP; pi += blockDim.x) {
         const int el = pi / TP, fl = pi % TP;
         const int er = i0 - 1 + el, fr = j0 - 1 + fl;     // in [-1, N): -1 is segment N - 1
@@ -779,14 +800,36 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
             for (int c = 0; c < 4; ++c) I[c] = cdfl_from(Id[c]);
             M0 = cdfl_from(m);
         } else {
-            // y_f(0) - x_e(0) = (f offset + tile offset) - (e offset)
-            const dfl bx = dfl_sub(dfl_mk(gF[fl]), dfl_mk(gE[el]));
-            const dfl by = dfl_sub(dfl_mk(gF[TP + fl]), dfl_mk(gE[TP + el]));
-            const dfl uex = dfl_mk(gE[2 * TP + el]), uey = dfl_mk(gE[3 * TP + el]);
-            const dfl vfx = dfl_mk(gF[2 * TP + fl]), vfy = dfl_mk(gF[3 * TP + fl]);
+            // Every unordered segment pair is integrated in one orientation, the lower segment
+            // index on the x side, so that its integrals have the same bits wherever they
+            // are used (the pairs of a diagonal tile below its diagonal, and those of the
+            // wrapped segment N - 1, are the swapped ones); then y_x'(0) - x_e'(0) =
+            // (anchor difference + y-side offset) - x-side offset.
+            const int e = er < 0 ? er + N : er, f = fr < 0 ? fr + N : fr;
+            const bool sw = e > f;
+            dfl bx, by, uex, uey, vfx, vfy, hx, hy;
+            if (!sw) {
+                const int fo = eSel[el] ? 7 * TP : 0;
+                bx = dfl_sub(dfl_mk(gF[fo + fl]), dfl_mk(gE[el]));
+                by = dfl_sub(dfl_mk(gF[fo + TP + fl]), dfl_mk(gE[TP + el]));
+                uex = dfl_mk(gE[2 * TP + el]); uey = dfl_mk(gE[3 * TP + el]);
+                vfx = dfl_mk(gF[2 * TP + fl]); vfy = dfl_mk(gF[3 * TP + fl]);
+                hx = dfl_mk(gE[6 * TP + el]); hy = dfl_mk(gF[6 * TP + fl]);
+            } else {
+                // x side: segment f (offset from its anchor recomputed: the staged one holds
+                // the tile's anchor difference); y side: segment e
+                const int af = f & ~31, ae = e & ~31;
+                const dfl adx = dfl_from(kk * (p.seg[ae] - p.seg[af])), ady = dfl_from(kk * (p.seg[N + ae] - p.seg[N + af]));
+                const dfl ofx = dfl_from(kk * (p.seg[f] - p.seg[af])), ofy = dfl_from(kk * (p.seg[N + f] - p.seg[N + af]));
+                bx = dfl_sub(dfl_add(adx, dfl_mk(gE[el])), ofx);
+                by = dfl_sub(dfl_add(ady, dfl_mk(gE[TP + el])), ofy);
+                uex = dfl_mk(gF[2 * TP + fl]); uey = dfl_mk(gF[3 * TP + fl]);
+                vfx = dfl_mk(gE[2 * TP + el]); vfy = dfl_mk(gE[3 * TP + el]);
+                hx = dfl_mk(gF[6 * TP + fl]); hy = dfl_mk(gE[6 * TP + el]);
+            }
             // (scaled by k: kgap = k (gap + h_max) directly)
             const float kf = (float)p.k;
-            const float he = kf * gE[6 * TP + el].x, hf = kf * gF[6 * TP + fl].x;
+            const float he = kf * hx.hi, hf = kf * hy.hi;
             const float mx = bx.hi + 0.5f * (vfx.hi - uex.hi), my = by.hi + 0.5f * (vfy.hi - uey.hi);
             const float hmax = fmaxf(he, hf);
             const float gap = fmaxf(sqrt_approx(mx * mx + my * my) - 0.5f * (he + hf), 0.0f);
@@ -795,22 +838,43 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
             cdfl A[4];
             if (q == 2) pair_gauss_df_q<2>(bx, by, uex, uey, vfx, vfy, p.btabf, A);   // the far-field bulk
             else pair_gauss_df(q, bx, by, uex, uey, vfx, vfy, p.btabf, A);
-            const dfl hh = dfl_mul(dfl_mk(gE[6 * TP + el]), dfl_mk(gF[6 * TP + fl]));
-            for (int c = 0; c < 4; ++c) I[c] = {dfl_mul(hh, A[c].re), dfl_mul(hh, A[c].im)};
+            const dfl hh = dfl_mul(hx, hy);
             M0 = cdfl_add(cdfl_add(A[0], A[1]), cdfl_add(A[2], A[3]));
+            if (sw) { const cdfl t = A[1]; A[1] = A[2]; A[2] = t; }   // I_ab(e, f) = I_ba(f, e)
+            for (int c = 0; c < 4; ++c) I[c] = {dfl_mul(hh, A[c].re), dfl_mul(hh, A[c].im)};
         }
         for (int c = 0; c < 4; ++c) sI[pi * 4 + c] = cdfl_pack(I[c]);
         sM[pi] = cdfl_pack(M0);
         sND[pi] = make_float2(nd.hi, nd.lo);
+        mexp = max(mexp, max((__float_as_int(M0.re.hi) >> 23) & 255, (__float_as_int(M0.im.hi) >> 23) & 255));
     }
     for (int o = 16; o > 0; o >>= 1) npts += __shfl_xor_sync(0xffffffffu, npts, o);
     if ((threadIdx.x & 31) == 0 && npts) atomicAdd(p.qpts, (unsigned long long)npts);
+    // N's derivative term is the second difference of the segment-pair means M0 (Maue's
+    // form): at low k its row sums are O(k^2) of the means, so the differences are taken
+    // exactly, in fixed point with one scale per tile (|M0| 2^msh < 2^59, leaving room for
+    // the k^2 term, at most 4 |M0| with k h <= 2), and every entry of N is rounded once, to
+    // FP64, from that exact sum; each mean is rounded once too, which perturbs the means,
+    // not the null space of the differences
+    mexp = (int)__reduce_max_sync(0xffffffffu, (unsigned)mexp);
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_mexp, mexp);
+    __syncthreads();
+    const int msh = 185 - s_mexp;
+    longlong2* sMx = reinterpret_cast<longlong2*>(sM);    // the means in fixed point, in place
+    if (p.W) {
+        for (int pi = threadIdx.x; pi < TP * TP; pi += blockDim.x) {
+            const int el = pi / TP, fl = pi % TP;
+            if (i0 - 1 + el >= N || j0 - 1 + fl >= N) continue;
+            const cdfl m = cdfl_unpack(sM[pi]);
+            sMx[pi] = make_longlong2(dfl_to_fixed(m.re, msh), dfl_to_fixed(m.im, msh));
+        }
+    }
     const bool mirror = (ti != tj);
     // entry (i0 + il, j0 + jl) of S and N, written at (i, j)
     auto entry = [&](int il, int jl, double2& ds, double2& dw) -> bool {
         const int i = i0 + il, j = j0 + jl;
         if (i >= N || j >= N) return false;
-        cdfl sv, wv;
+        cdfl sv, wv = cdfl_zero();
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
             const int el = il + 1 - a;
@@ -820,20 +884,22 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
                 const int pi = el * TP + fl;
                 const cdfl Iab = cdfl_unpack(sI[pi * 4 + a * 2 + b]);
                 sv = (a | b) ? cdfl_add(sv, Iab) : Iab;
-                if (p.W) {
-                    // sigma_a sigma_b sum I/(h_e h_f) - k^2 (nu_e . nu_f) I_ab
-                    cdfl M0 = cdfl_unpack(sM[pi]);
-                    if (a != b) M0 = {dfl_neg(M0.re), dfl_neg(M0.im)};
-                    const dfl nnd = dfl_neg(dfl_mk(sND[pi]));
-                    const cdfl term = cdfl_fma_real(nnd, Iab, M0);
-                    wv = (a | b) ? cdfl_add(wv, term) : term;
-                }
+                // the k^2 term: - k^2 (nu_e . nu_f) I_ab
+                if (p.W) wv = cdfl_fma_real(dfl_neg(dfl_mk(sND[pi])), Iab, wv);
             }
         }
-        if (!p.W) wv = cdfl_zero();
         const int64_t off = (int64_t)i + (int64_t)j * p.ld;
         ds = cdfl_to(sv);
-        dw = cdfl_to(wv);
+        dw = make_double2(0.0, 0.0);
+        if (p.W) {
+            // sum_ab sigma_a sigma_b M0(i-a, j-b) = (M0[i-1][j-1] - M0[i-1][j]) - (M0[i][j-1] - M0[i][j]),
+            // plus the k^2 term, exactly in fixed point; one rounding to FP64
+            const longlong2 m00 = sMx[il * TP + jl], m01 = sMx[il * TP + jl + 1];
+            const longlong2 m10 = sMx[(il + 1) * TP + jl], m11 = sMx[(il + 1) * TP + jl + 1];
+            const long long wr = ((m00.x - m01.x) - (m10.x - m11.x)) + dfl_to_fixed(wv.re, msh);
+            const long long wi = ((m00.y - m01.y) - (m10.y - m11.y)) + dfl_to_fixed(wv.im, msh);
+            dw = make_double2(fixed_to_double(wr, msh), fixed_to_double(wi, msh));
+        }
         if (p.S) p.S[off] = ds;
         if (p.W) p.W[off] = dw;
         return true;
@@ -941,15 +1007,27 @@ __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
         SegV se = {sgE[el], sgE[TP + el], sgE[2 * TP + el], sgE[3 * TP + el], sgE[4 * TP + el]};
         SegV sf = {sgF[fl], sgF[TP + fl], sgF[2 * TP + fl], sgF[3 * TP + fl], sgF[4 * TP + fl]};
         cplx I[4], J[4], Jt[4];
-        pair_moments<WD>(e, f, se, sf, p, I, J, Jt, npts);
+        // every unordered pair in one orientation (lower segment index first), so its
+        // integrals have the same bits in every tile that uses them (N's second differences
+        // then telescope exactly); I_ab(e, f) = I_ba(f, e), J and Jt trade places
+        const bool sw = e > f;
+        if (!sw) pair_moments<WD>(e, f, se, sf, p, I, J, Jt, npts);
+        else pair_moments<WD>(f, e, sf, se, p, I, J, Jt, npts);
+        // per-pair terms of N's Maue form: sum_ab I / (h_e h_f) and k^2 nu_e . nu_f
+        const double ihh = sw ? 1.0 / (sf.h * se.h) : 1.0 / (se.h * sf.h);
+        const cplx M0 = cadd(cadd(I[0], I[1]), cadd(I[2], I[3]));
+        sM[pi] = cscale(M0, ihh);
+        if (sw) {
+            cplx t = I[1]; I[1] = I[2]; I[2] = t;
+            if (WD) {
+                cplx Jn[4] = {Jt[0], Jt[2], Jt[1], Jt[3]}, Jtn[4] = {J[0], J[2], J[1], J[3]};
+                for (int q = 0; q < 4; ++q) { J[q] = Jn[q]; Jt[q] = Jtn[q]; }
+            }
+        }
         for (int q = 0; q < 4; ++q) {
             sI[pi * 4 + q] = I[q];
             if (WD) { sJ[pi * 4 + q] = J[q]; sJt[pi * 4 + q] = Jt[q]; }
         }
-        // per-pair terms of N's Maue form: sum_ab I / (h_e h_f) and k^2 nu_e . nu_f
-        const double ihh = 1.0 / (se.h * sf.h);
-        const cplx M0 = cadd(cadd(I[0], I[1]), cadd(I[2], I[3]));
-        sM[pi] = cscale(M0, ihh);
         sND[pi] = k2 * (se.ty * sf.ty + se.tx * sf.tx);   // nu = (t_y, -t_x): nu_e . nu_f = t_e . t_f
     }
     for (int o = 16; o > 0; o >>= 1) npts += __shfl_xor_sync(0xffffffffu, npts, o);
@@ -973,14 +1051,24 @@ __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
                     const cplx Iab = sI[pi * 4 + a * 2 + b];
                     s = cadd(s, Iab);
                     if (p.W) {
-                        // sigma_a sigma_b sum I/(h_e h_f) - k^2 (nu_e . nu_f) I_ab
-                        const cplx M0 = sM[pi];
+                        // the k^2 term: - k^2 (nu_e . nu_f) I_ab
                         const double nd = sND[pi];
-                        if (a == b) { w.x += M0.x - nd * Iab.x; w.y += M0.y - nd * Iab.y; }
-                        else { w.x += -M0.x - nd * Iab.x; w.y += -M0.y - nd * Iab.y; }
+                        w.x -= nd * Iab.x;
+                        w.y -= nd * Iab.y;
                     }
                     if (WD) dd = cadd(dd, (pass == 0 ? sJ : sJt)[pi * 4 + a * 2 + b]);
                 }
+            }
+            if (p.W) {
+                // the derivative term sum_ab sigma_a sigma_b M0(i-a, j-b) as the second
+                // difference (M0[i-1][j-1] - M0[i-1][j]) - (M0[i][j-1] - M0[i][j]): each
+                // difference of two close means is exact, so N's vanishing row sums of this
+                // term are kept to the rounding of the small differences (at low k they
+                // carry the O(k^2) row sums of N)
+                const cplx m00 = sM[il * TP + jl], m01 = sM[il * TP + jl + 1];
+                const cplx m10 = sM[(il + 1) * TP + jl], m11 = sM[(il + 1) * TP + jl + 1];
+                w.x += (m00.x - m01.x) - (m10.x - m11.x);
+                w.y += (m00.y - m01.y) - (m10.y - m11.y);
             }
             const int64_t off = (pass == 0) ? ((int64_t)i + (int64_t)j * p.ld) : ((int64_t)j + (int64_t)i * p.ld);
             if (p.S) p.S[off] = s;
@@ -1047,7 +1135,7 @@ template <int T>
 static bem_status run_assemble_sn(bem_ctx* h, AsmParams& p) {
     constexpr int TP = T + 1;
     const size_t smem = (size_t)TP * TP * (4 * sizeof(float4) + sizeof(float4) + sizeof(float2)) +
-                        (size_t)14 * TP * sizeof(float2);
+                        (size_t)16 * TP * sizeof(float2);
     BEM_CUDA(h, cudaFuncSetAttribute(k_assemble_sn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     p.nT = (p.N + T - 1) / T;
     const unsigned grid = (unsigned)((int64_t)p.nT * (p.nT + 1) / 2);
@@ -1071,7 +1159,7 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     bem_status st = bessel_table(h, &p.btab, &p.btabf);
     if (st != BEM_OK) return st;
     cplx* near = nullptr;
-    BEM_CUDA(h, cudaMallocAsync((void**)&near, sizeof(cplx) * NEAR_STRIDE * (size_t)h->N, h->stream));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&near, sizeof(cplx) * NEAR_STRIDE * (size_t)h->N));
     const unsigned gnear = (unsigned)((h->N + 7) / 8);
     if (ops & BEM_OP_D) {
         BEM_TIMED(h, "k_near_pairs", (k_near_pairs<true><<<gnear, 256, 0, h->stream>>>(h->seg, (int)h->N, p.sc, near)));
@@ -1084,7 +1172,7 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     p.wband = -1;
     h->rexp_valid = false;
     if (!(ops & BEM_OP_D) && h->opt.prec == BEM_MIXED_BF16) {
-        if (!h->rexp) BEM_CUDA(h, cudaMalloc((void**)&h->rexp, sizeof(int) * 2 * (size_t)h->N));
+        if (!h->rexp) BEM_CUDA(h, bem_dmalloc(h, (void**)&h->rexp, sizeof(int) * 2 * (size_t)h->N));
         BEM_CUDA(h, cudaMemsetAsync(h->rexp, 0, sizeof(int) * 2 * (size_t)h->N, h->stream));
         p.rexpS = h->rexp;
         p.rexpW = h->rexp + h->N;
@@ -1092,7 +1180,7 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     }
     st = (ops & BEM_OP_D) ? run_assemble<15, true>(h, p) : run_assemble_sn<31>(h, p);
     if (st == BEM_OK && p.rexpS) h->rexp_valid = true;
-    cudaFreeAsync(near, h->stream);
+    bem_dfree_async(h, near);
     return st;
 }
 
@@ -1196,6 +1284,54 @@ bem_status launch_rhs(bem_ctx* h, const double* angles, int64_t nrhs, cplx* f, c
     dim3 grid((unsigned)((h->N + 254) / 255), (unsigned)nrhs);
     BEM_TIMED(h, "k_rhs", (k_rhs<<<grid, 256, 0, h->stream>>>(h->seg, (int)h->N, angles, h->k, f, hz, ld)));
     BEM_LAUNCH(h, "k_rhs");
+    return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// line-source right-hand sides: u_inc(x) = g2(|x - r0|) = (i/4) H0^(1)(k |x - r0|), the field
+// of a z-directed line source at r0 (the 2D source of the TE problem), with
+//   d u_inc / d nu = -(i k / 4) H1^(1)(k rho) (x - r0).nu / rho,  rho = |x - r0|,
+//   f_i = -<phi_i, d u_inc / d nu>,  [h2]_i = <phi_i, u_inc>,
+// by 8-point Gauss-Legendre on each segment (the source lies off the curve, at a distance of
+// many segment lengths, so the integrand is smooth there).  One thread per vertex i and
+// source w: segment i carries lambda_0 = 1 - s, segment i - 1 carries lambda_1 = s.
+// ---------------------------------------------------------------------------------------
+#define PS_Q 8
+__global__ void __launch_bounds__(256) k_rhs_point(const double* __restrict__ seg, int N,
+                                                   const double* __restrict__ src, double k, cplx* f, cplx* hz,
+                                                   int64_t ld) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = blockIdx.y;
+    if (i >= N) return;
+    const double sx = src[2 * w], sy = src[2 * w + 1];
+    double fr = 0.0, fi = 0.0, hr = 0.0, hi = 0.0;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int e = side == 0 ? i : (i == 0 ? N - 1 : i - 1);
+        const double x0 = seg[e], y0 = seg[N + e], tx = seg[2 * N + e], ty = seg[3 * N + e], he = seg[4 * N + e];
+        for (int j = 0; j < PS_Q; ++j) {
+            const double s = c_glx[gl_off(PS_Q) + j];
+            const double lam = side == 0 ? 1.0 - s : s;
+            const double wl = c_glw[gl_off(PS_Q) + j] * lam * he;
+            const double dx = x0 + s * he * tx - sx, dy = y0 + s * he * ty - sy;
+            const double rho = sqrt(dx * dx + dy * dy);
+            const Bessel01 b = bessel01<true>(k * rho);
+            // u = (i/4)(J0 + i Y0) ;  du/dnu = -(i k/4)(J1 + i Y1) (d.nu)/rho = (k/4)(Y1 - i J1) (d.nu)/rho
+            const double dn = (dx * ty - dy * tx) / rho;
+            hr += wl * (-0.25 * b.Y0);
+            hi += wl * (0.25 * b.J0);
+            fr -= wl * (0.25 * k * b.Y1 * dn);
+            fi -= wl * (-0.25 * k * b.J1 * dn);
+        }
+    }
+    if (f) f[(int64_t)i + (int64_t)w * ld] = cmk(fr, fi);
+    if (hz) hz[(int64_t)i + (int64_t)w * ld] = cmk(hr, hi);
+}
+
+bem_status launch_rhs_point(bem_ctx* h, const double* src, int64_t nsrc, cplx* f, cplx* hz, int64_t ld) {
+    dim3 grid((unsigned)((h->N + 255) / 256), (unsigned)nsrc);
+    BEM_TIMED(h, "k_rhs_point", (k_rhs_point<<<grid, 256, 0, h->stream>>>(h->seg, (int)h->N, src, h->k, f, hz, ld)));
+    BEM_LAUNCH(h, "k_rhs_point");
     return BEM_OK;
 }
 

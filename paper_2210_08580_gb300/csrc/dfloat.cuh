@@ -86,6 +86,41 @@ __device__ __forceinline__ float4 cdfl_pack(cdfl z) { return make_float4(z.re.hi
 __device__ __forceinline__ cdfl cdfl_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
 
 
+// Fixed point: exact sums and differences of double-floats of one scale.
+// round(v 2^sh) of a float as a 64-bit integer, from its bit fields (the caller keeps
+// |v| 2^sh below 2^62; bits below 2^-sh are rounded off)
+__device__ __forceinline__ long long f32_to_fixed(float v, int sh) {
+    const int b = __float_as_int(v);
+    const int ex = (b >> 23) & 255;
+    if (ex == 0) return 0;
+    const long long m = (long long)((b & 0x7FFFFF) | 0x800000);
+    const int s = ex - 150 + sh;                            // v = m 2^(ex - 150)
+    long long r;
+    if (s >= 0) r = m << s;
+    else if (s >= -25) r = (m + (1LL << (-s - 1))) >> (-s);
+    else r = 0;
+    return b < 0 ? -r : r;
+}
+__device__ __forceinline__ long long dfl_to_fixed(dfl a, int sh) { return f32_to_fixed(a.hi, sh) + f32_to_fixed(a.lo, sh); }
+// v 2^-sh as a double, rounded to nearest (ties to even), from the bit fields (integer
+// operations only); results below the double normal range become 0
+__device__ __forceinline__ double fixed_to_double(long long v, int sh) {
+    if (v == 0) return 0.0;
+    const unsigned long long sgn = v < 0 ? (1ULL << 63) : 0ULL;
+    unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int lz = __clzll((long long)u);
+    u <<= lz;                                               // bit 63 set: value u 2^(-lz - sh)
+    unsigned long long m = u >> 11;                         // 53 bits, bit 52 set
+    const unsigned long long rest = u & 0x7FFULL;
+    int E = 63 - lz - sh;
+    if (rest > 0x400ULL || (rest == 0x400ULL && (m & 1ULL))) {
+        ++m;
+        if (m == (1ULL << 53)) { m >>= 1; ++E; }
+    }
+    if (E + 1023 < 1) return 0.0;
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(E + 1023) << 52) | (m & ((1ULL << 52) - 1))));
+}
+
 // sqrt, 1/sqrt and division with one Newton correction of the float estimate (about 47
 // bits); arguments in the float normal range, x > 0 for the roots
 __device__ __forceinline__ dfl dfl_sqrt(dfl x) {
