@@ -26,6 +26,8 @@ cudaError_t init_gauss_tables();
 bem_status launch_geometry(bem_ctx* h, const double* verts, int64_t N, double* stats_dev);
 bem_status launch_assemble(bem_ctx* h, unsigned ops);
 bem_status launch_rhs(bem_ctx* h, const double* angles, int64_t nrhs, cplx* f, cplx* hz, int64_t ld);
+// line sources at src (2 nsrc doubles, (x, y) pairs): f = -<phi, d g2(|x - r0|)/d nu>, hz = <phi, g2>
+bem_status launch_rhs_point(bem_ctx* h, const double* src, int64_t nsrc, cplx* f, cplx* hz, int64_t ld);
 // shape gradient: d/dverts Re sum(Omega^S .* S + Omega^W .* N) (Omega passed transposed),
 // d/dverts Re sum om .* f(angles), and the Gram terms of four signed (P, Q) block pairs
 bem_status launch_assemble_vjp(bem_ctx* h, const cplx* OmS_T, const cplx* OmW_T, double* grad);
@@ -68,5 +70,8 @@ bem_status launch_scale_cols(bem_ctx* h, cplx* x, int64_t ldx, const cplx* s, in
 bem_status launch_shift(bem_ctx* h, const double* in, double* out, int64_t n, double shift);
 bem_status launch_conj_scale(bem_ctx* h, const cplx* x, int64_t ldx, cplx* y, int64_t ldy, cplx a, int64_t rows,
                              int64_t cols);   // y = a conj(x)
+// P <- P + (Y (W 1) - P 1) 1^T / N for the n x N product P = Y W (ld = nc); scratch: N + nc
+bem_status launch_const_correction(bem_ctx* h, const cplx* Wm, const cplx* Y, cplx* P, int64_t nc, int64_t N,
+                                   cplx* scratch);
 bem_status launch_copy2d(bem_ctx* h, void* dst, int64_t ldd, const void* src, int64_t lds,
                          int64_t rows, int64_t cols, size_t elem);

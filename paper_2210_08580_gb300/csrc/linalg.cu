@@ -942,7 +942,7 @@ __global__ void __launch_bounds__(QR_NT, 1) k_house_qr_df(float4* X, int64_t N, 
             s_ref[0] = cdfl_pack(alpha);
             s_ref[1] = cdfl_pack(vj);
             s_tau = make_float2(tau.hi, tau.lo);
-            if (own_j) R[j + (int64_t)j * n] = cdfl_to(alpha);
+            if (own_j) R[j + (int64_t)cmap[j] * n] = cdfl_to(alpha);
         }
         __syncthreads();
         {
@@ -959,7 +959,7 @@ __global__ void __launch_bounds__(QR_NT, 1) k_house_qr_df(float4* X, int64_t N, 
                 // R_jc = x - vj wc
                 const dfl rr = dfl_sub(x.re, dfl_fma(vj.re, wc.re, dfl_neg(dfl_mul(vj.im, wc.im))));
                 const dfl ri = dfl_sub(x.im, dfl_fma(vj.re, wc.im, dfl_mul(vj.im, wc.re)));
-                if (own_j) R[j + (int64_t)c * n] = cmk(dfl_to(rr), dfl_to(ri));
+                if (own_j) R[j + (int64_t)cmap[c] * n] = cmk(dfl_to(rr), dfl_to(ri));
                 dfl nd = dfl_sub(dfl_mk(sN[c]), dfl_fma(rr, rr, dfl_mul(ri, ri)));
                 if (nd.hi < 0.f) nd = {0.f, 0.f};
                 sN[c] = make_float2(nd.hi, nd.lo);
@@ -967,7 +967,11 @@ __global__ void __launch_bounds__(QR_NT, 1) k_house_qr_df(float4* X, int64_t N, 
             __syncthreads();
             if (j + 1 < n) {
                 const int q = pick(j + 1);
-                if (tid == 0 && q < n && q != j + 1) { const int t = cmap[j + 1]; cmap[j + 1] = cmap[q]; cmap[q] = t; }
+                if (tid == 0 && q < n && q != j + 1) {
+                    // the next pivot moves to position j + 1; w is held by position, so it moves along
+                    const int t = cmap[j + 1]; cmap[j + 1] = cmap[q]; cmap[q] = t;
+                    const float4 tw = sW[j + 1]; sW[j + 1] = sW[q]; sW[q] = tw;
+                }
                 __syncthreads();
             }
         }
@@ -979,11 +983,17 @@ __global__ void __launch_bounds__(QR_NT, 1) k_house_qr_df(float4* X, int64_t N, 
         }
         if (!grid_barrier(bar, G, err)) return;
     }
-    // lower triangle of R (rows owned here)
-    for (int64_t j = max(r0, (int64_t)0); j < min(r1, (int64_t)n); ++j)
-        for (int c = tid; c < j; c += blockDim.x) R[j + (int64_t)c * n] = cmk(0, 0);
     if (blockIdx.x == 0)
         for (int c = tid; c < n; c += blockDim.x) perm[c] = cmap[c];
+}
+
+// R by position from R held by column (row j of column pc at Rc[j + pc n]), with the final
+// permutation: R[j + c n] = Rc[j + perm[c] n] for c >= j, zero below the diagonal
+__global__ void k_qr_place_R(const cplx* __restrict__ Rc, cplx* R, const int* __restrict__ perm, int n) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * n) return;
+    const int j = (int)(idx % n), c = (int)(idx / n);
+    R[idx] = (c < j) ? cmk(0, 0) : Rc[j + (int64_t)perm[c] * n];
 }
 
 bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* perm, bool dfl_arith) {
@@ -999,34 +1009,43 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* 
         // of 9 words per column and the window exponent, all starting at zero
         unsigned long long* lim = nullptr;
         const size_t lim_words = (size_t)3 * 9 * n + 1;
-        BEM_CUDA(h, cudaMallocAsync((void**)&lim, sizeof(unsigned long long) * lim_words, h->stream));
+        BEM_CUDA(h, bem_dmalloc_async(h, (void**)&lim, sizeof(unsigned long long) * lim_words));
         BEM_CUDA(h, cudaMemsetAsync(lim, 0, sizeof(unsigned long long) * lim_words, h->stream));
         int* emax = reinterpret_cast<int*>(lim + 27 * (size_t)n);
         float4* Pc = nullptr;                   // the next pivot column, two buffers
-        BEM_CUDA(h, cudaMallocAsync((void**)&Pc, sizeof(float4) * 2 * (size_t)N, h->stream));
+        BEM_CUDA(h, bem_dmalloc_async(h, (void**)&Pc, sizeof(float4) * 2 * (size_t)N));
         const int64_t cnt = N * (int64_t)n;
         BEM_TIMED(h, "k_to_dfl", (k_to_dfl<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(reinterpret_cast<float4*>(X), cnt)));
         BEM_LAUNCH(h, "k_to_dfl");
+        // rows of R are written by column as the steps go (the pivots move columns between
+        // positions after their earlier rows are known) and placed by position afterwards
+        cplx* Rc = nullptr;
+        BEM_CUDA(h, bem_dmalloc_async(h, (void**)&Rc, sizeof(cplx) * (size_t)n * n));
         float4* Xf = reinterpret_cast<float4*>(X);
-        void* args_df[] = {&Xf, &N, &n, &R, &perm, &lim, &emax, &Pc, &h->bar, &h->dev_err};
+        void* args_df[] = {&Xf, &N, &n, &Rc, &perm, &lim, &emax, &Pc, &h->bar, &h->dev_err};
         const size_t smem = (size_t)QR_NP * (8 * sizeof(float4) + 8 * sizeof(float) + 3 * sizeof(float4) + sizeof(float2));
         BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr_df, G, QR_NT, args_df, "k_house_qr_df", smem));
-        cudaFreeAsync(lim, h->stream);
-        cudaFreeAsync(Pc, h->stream);
+        if (st == BEM_OK) {
+            BEM_TIMED(h, "k_qr_place_R", (k_qr_place_R<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, h->stream>>>(Rc, R, perm, n)));
+            BEM_LAUNCH(h, "k_qr_place_R");
+        }
+        bem_dfree_async(h, Rc);
+        bem_dfree_async(h, lim);
+        bem_dfree_async(h, Pc);
         return st;
     }
     double* partC = nullptr;
     cplx* partW = nullptr;
     unsigned long long* cnq = nullptr;
-    BEM_CUDA(h, cudaMallocAsync((void**)&partC, sizeof(double) * (size_t)G * n, h->stream));
-    BEM_CUDA(h, cudaMallocAsync((void**)&cnq, sizeof(unsigned long long) * 2 * (size_t)n, h->stream));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&partC, sizeof(double) * (size_t)G * n));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&cnq, sizeof(unsigned long long) * 2 * (size_t)n));
     BEM_CUDA(h, cudaMemsetAsync(cnq, 0, sizeof(unsigned long long) * 2 * (size_t)n, h->stream));
-    BEM_CUDA(h, cudaMallocAsync((void**)&partW, sizeof(cplx) * (size_t)G * n, h->stream));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&partW, sizeof(cplx) * (size_t)G * n));
     void* args[] = {&X, &N, &n, &R, &perm, &partC, &cnq, &partW, &h->bar, &h->dev_err};
     BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr, G, 256, args, "k_house_qr"));
-    cudaFreeAsync(partC, h->stream);
-    cudaFreeAsync(cnq, h->stream);
-    cudaFreeAsync(partW, h->stream);
+    bem_dfree_async(h, partC);
+    bem_dfree_async(h, cnq);
+    bem_dfree_async(h, partW);
     return st;
 }
 
@@ -1249,11 +1268,11 @@ bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double
     double* tmp = nullptr;
     int* ver = nullptr;
     const int max_sweeps = 40;
-    BEM_CUDA(h, cudaMallocAsync((void**)&X, sizeof(float4) * (size_t)n * n, h->stream));
-    BEM_CUDA(h, cudaMallocAsync((void**)&flags, sizeof(int) * max_sweeps, h->stream));
-    BEM_CUDA(h, cudaMallocAsync((void**)&ver, sizeof(int) * n, h->stream));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&X, sizeof(float4) * (size_t)n * n));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&flags, sizeof(int) * max_sweeps));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&ver, sizeof(int) * n));
     BEM_CUDA(h, cudaMemsetAsync(ver, 0, sizeof(int) * n, h->stream));
-    BEM_CUDA(h, cudaMallocAsync((void**)&tmp, sizeof(double) * n, h->stream));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&tmp, sizeof(double) * n));
     BEM_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(int) * max_sweeps, h->stream));
     BEM_TIMED(h, "k_conj_transpose",
               (k_conj_transpose<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, h->stream>>>(R, X, n)));
@@ -1266,10 +1285,10 @@ bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double
         BEM_TIMED(h, "k_sort_sv", (k_sort_sv<<<1, 256, 0, h->stream>>>(X, n, perm, sigma, E, tmp)));
         BEM_LAUNCH(h, "k_sort_sv");
     }
-    cudaFreeAsync(X, h->stream);
-    cudaFreeAsync(flags, h->stream);
-    cudaFreeAsync(ver, h->stream);
-    cudaFreeAsync(tmp, h->stream);
+    bem_dfree_async(h, X);
+    bem_dfree_async(h, flags);
+    bem_dfree_async(h, ver);
+    bem_dfree_async(h, tmp);
     return st;
 }
 
@@ -1353,8 +1372,8 @@ __global__ void k_augment(const cplx* K, cplx* M, cplx* colbuf, int r) {
 
 bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
     cplx *M = nullptr, *colbuf = nullptr;
-    BEM_CUDA(h, cudaMallocAsync((void**)&M, sizeof(cplx) * (size_t)r * 2 * r, h->stream));
-    BEM_CUDA(h, cudaMallocAsync((void**)&colbuf, sizeof(cplx) * (size_t)r * 2, h->stream));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&M, sizeof(cplx) * (size_t)r * 2 * r));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&colbuf, sizeof(cplx) * (size_t)r * 2));
     BEM_TIMED(h, "k_augment", (k_augment<<<(unsigned)(((int64_t)r * 2 * r + 255) / 256), 256, 0, h->stream>>>(K, M, colbuf, r)));
     BEM_LAUNCH(h, "k_augment");
     const size_t smem = sizeof(cplx) * (size_t)r;
@@ -1375,8 +1394,8 @@ bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
     BEM_LAUNCH(h, "k_gauss_jordan");
     BEM_CUDA(h, cudaMemcpy2DAsync(Kinv, sizeof(cplx) * r, M + (size_t)r * r, sizeof(cplx) * r,
                                   sizeof(cplx) * r, r, cudaMemcpyDeviceToDevice, h->stream));
-    cudaFreeAsync(M, h->stream);
-    cudaFreeAsync(colbuf, h->stream);
+    bem_dfree_async(h, M);
+    bem_dfree_async(h, colbuf);
     return BEM_OK;
 }
 
@@ -1522,12 +1541,12 @@ __global__ void k_max(const double* v, int64_t n, double* out) {
 bem_status launch_col_norm_ratio(bem_ctx* h, const cplx* num, int64_t ldn, const cplx* den, int64_t ldd,
                                  int64_t rows, int64_t cols, double* out_max) {
     double* ratios = nullptr;
-    BEM_CUDA(h, cudaMallocAsync((void**)&ratios, sizeof(double) * cols, h->stream));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&ratios, sizeof(double) * cols));
     BEM_TIMED(h, "k_col_ratio", (k_col_ratio<<<(unsigned)cols, 256, 0, h->stream>>>(num, ldn, den, ldd, rows, ratios)));
     BEM_LAUNCH(h, "k_col_ratio");
     BEM_TIMED(h, "k_max", (k_max<<<1, 256, 0, h->stream>>>(ratios, cols, out_max)));
     BEM_LAUNCH(h, "k_max");
-    cudaFreeAsync(ratios, h->stream);
+    bem_dfree_async(h, ratios);
     return BEM_OK;
 }
 
@@ -1535,5 +1554,64 @@ bem_status launch_copy2d(bem_ctx* h, void* dst, int64_t ldd, const void* src, in
                          int64_t cols, size_t elem) {
     BEM_CUDA(h, cudaMemcpy2DAsync(dst, elem * ldd, src, elem * lds, elem * rows, cols,
                                   cudaMemcpyDeviceToDevice, h->stream));
+    return BEM_OK;
+}
+
+// =========================================================================================
+// Constant-vector correction of the filtered product (mixed path).  N's row sums are O(k^2)
+// of its entries (Maue's form: the derivative term's row sums vanish), so at low k the
+// split products lose B's action on the constant vector 1 to their rounding, which is
+// relative to the entries, while that action carries the Calderon product's smallest
+// eigenvalue.  With w = N 1 summed in FP64 from the assembled N, the n x N product P = Y N
+// is corrected along 1 only:  P <- P + (Y w - P 1) 1^T / N  (P's action on the
+// complement of 1 is unchanged).
+// =========================================================================================
+__device__ __forceinline__ cplx block_csum(cplx v, double* red) {
+    return cmk(block_sum(v.x, red), block_sum(v.y, red));
+}
+
+// w[j] = sum_i A[i + j lda], one CTA per column (A = N is complex symmetric: w = N 1)
+__global__ void __launch_bounds__(256) k_col_sums(const cplx* __restrict__ A, int64_t lda, int64_t rows, cplx* w) {
+    __shared__ double red[32];
+    const int64_t j = blockIdx.x;
+    cplx acc = cmk(0, 0);
+    for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) acc = cadd(acc, A[i + j * lda]);
+    acc = block_csum(acc, red);
+    if (threadIdx.x == 0) w[j] = acc;
+}
+
+// c_i = (sum_j Y[i + j ld] w_j - sum_j P[i + j ld]) / N, one CTA per row i
+__global__ void __launch_bounds__(256) k_const_defect(const cplx* __restrict__ Y, const cplx* __restrict__ P,
+                                                      int64_t ld, int64_t N, const cplx* __restrict__ w, cplx* c) {
+    __shared__ double red[32];
+    const int64_t i = blockIdx.x;
+    cplx t = cmk(0, 0), s = cmk(0, 0);
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+        t = cadd(t, cmul(Y[i + j * ld], w[j]));
+        s = cadd(s, P[i + j * ld]);
+    }
+    t = block_csum(t, red);
+    s = block_csum(s, red);
+    if (threadIdx.x == 0) c[i] = cscale(csub(t, s), 1.0 / (double)N);
+}
+
+// P[i + j ld] += c_i
+__global__ void k_add_row_const(cplx* P, int64_t ld, int64_t rows, int64_t N, const cplx* __restrict__ c) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * N) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    P[i + j * ld] = cadd(P[i + j * ld], c[i]);
+}
+
+bem_status launch_const_correction(bem_ctx* h, const cplx* Wm, const cplx* Y, cplx* P, int64_t nc, int64_t N,
+                                   cplx* scratch) {
+    cplx* w = scratch;              // N
+    cplx* c = scratch + N;          // nc
+    BEM_TIMED(h, "k_col_sums", (k_col_sums<<<(unsigned)N, 256, 0, h->stream>>>(Wm, N, N, w)));
+    BEM_LAUNCH(h, "k_col_sums");
+    BEM_TIMED(h, "k_const_defect", (k_const_defect<<<(unsigned)nc, 256, 0, h->stream>>>(Y, P, nc, N, w, c)));
+    BEM_LAUNCH(h, "k_const_defect");
+    BEM_TIMED(h, "k_add_row_const", (k_add_row_const<<<(unsigned)((nc * N + 255) / 256), 256, 0, h->stream>>>(P, nc, nc, N, c)));
+    BEM_LAUNCH(h, "k_add_row_const");
     return BEM_OK;
 }
