@@ -14,6 +14,8 @@
  *    contiguous torch tensor of shape (nrhs, N).
  *  - A handle owns all internal matrices (S, N, D, the filtered block B, the skeleton
  *    U, V^H and the LU of the Woodbury core) and its workspace; bem_destroy frees them.
+ *    Their device memory comes from the memory provider given to bem_create (the caller's
+ *    allocator hooks, or the CUDA runtime).
  *    Repeating a stage on a problem of the same size reuses these allocations (a call
  *    that needs larger ones reallocates them, after synchronising the handle's stream);
  *    bem_assemble with a new N releases them first.
@@ -83,6 +85,12 @@ typedef struct {
                                  5e-11 of max|S Y| with 5 slices) reaches the solution unrefined
                                  but far inside the mixed path's 1e-8 accuracy bar; the filter
                                  and compression products keep all slices                     */
+    int solve_slices;         /* mixed path: slices used by the Woodbury solves of solve_many
+                                 (the first solve and each refinement correction), 3 ..
+                                 split_slices; 0 = default, all of them.  The residual
+                                 products always use all slices, so fewer slices here trade
+                                 a cheaper solve for refinement sweeps (about one per 2^-7
+                                 digit dropped below the refine_rtol accuracy)              */
 } bem_options;
 
 typedef struct {
@@ -105,9 +113,27 @@ typedef struct bem_ctx* bem_handle;
 /* Fills *opt with the defaults listed in bem_options. */
 void bem_default_options(bem_options* opt);
 
+/* Device memory provider of a handle: dev_alloc(bytes, alloc_ctx) returns a device pointer
+ * on the handle's device (at least 256-byte aligned) or NULL when it cannot; dev_free(ptr,
+ * alloc_ctx) takes it back.  The library calls them from the thread that makes the bem_* call.
+ * Buffers kept across calls (the assembled matrices, B, U, V^H, the slices and workspace) are
+ * freed only when the handle's stream has finished with them.  Temporaries of one call are
+ * handed back as soon as the work that uses them is enqueued on the handle's stream, so the
+ * provider must reuse a freed block only for work ordered after that stream's enqueued work,
+ * as a stream-ordered caching allocator bound to the handle's stream does (PyTorch's, which the
+ * Python binding passes by default). */
+typedef void* (*bem_dev_alloc_fn)(size_t bytes, void* alloc_ctx);
+typedef void (*bem_dev_free_fn)(void* ptr, void* alloc_ctx);
+
 /* Creates a solver handle on CUDA device `device`, enqueueing on `cuda_stream`
- * (a cudaStream_t; NULL = the legacy default stream).  `opt` may be NULL (defaults). */
-bem_status bem_create(bem_handle* h, int device, void* cuda_stream, const bem_options* opt);
+ * (a cudaStream_t; NULL = the legacy default stream).  `opt` may be NULL (defaults).
+ * dev_alloc / dev_free / alloc_ctx: the memory provider above; with both hooks every byte of
+ * device memory the handle uses comes from dev_alloc and is returned through dev_free by the
+ * time bem_destroy returns; with both NULL the library uses cudaMalloc / cudaMallocAsync
+ * itself.  Errors: BEM_E_INVALID (NULL h, exactly one hook NULL, bad options or device),
+ * BEM_E_NOMEM, BEM_E_CUDA. */
+bem_status bem_create(bem_handle* h, int device, void* cuda_stream, const bem_options* opt,
+                      bem_dev_alloc_fn dev_alloc, bem_dev_free_fn dev_free, void* alloc_ctx);
 
 /* Frees everything the handle owns (synchronises its stream first).  NULL is accepted. */
 bem_status bem_destroy(bem_handle h);
@@ -166,6 +192,18 @@ bem_status factor(bem_handle h);
 bem_status bem_rhs_planewave(bem_handle h, const double* angles_dev, int64_t nrhs,
                              void* f_out_dev, void* v_out_dev, int64_t ld);
 
+/* bem_rhs_pointsource -- right-hand sides for line sources: the incident field of source w is
+ * the 2D free-space field u_inc(x) = g2(|x - r0_w|) = (i/4) H0^(1)(k |x - r0_w|) (the "dipole"
+ * source of Sec. V, read as a z-directed line source, which radiates a TE field H_z = u_inc),
+ * r0_w = (src_xy_dev[2w], src_xy_dev[2w+1]) (device doubles), off the curve:
+ *     f_i = -<phi_i, d u_inc / d nu>,   v = G^-1 S G^-1 f - alpha G^-1 h2,  [h2]_i = <phi_i, u_inc>,
+ * as bem_rhs_planewave for plane waves (8-point Gauss-Legendre per segment, FP64).  f_out,
+ * v_out: N x nsrc blocks (ld >= N), either may be NULL; 1 <= nsrc <= 65535.  The sources
+ * must lie at a distance of several chords from the curve (the rule is exact to rounding for
+ * distances above about 4 h).  Needs bem_assemble. */
+bem_status bem_rhs_pointsource(bem_handle h, const double* src_xy_dev, int64_t nsrc, void* f_out_dev,
+                               void* v_out_dev, int64_t ld);
+
 /* solve_many -- x = (beta I + U V^H)^-1 v by the Woodbury identity (Sec. IV-C):
  *     x = v/beta - beta^-2 U (I_r + beta^-1 V^H U)^-1 V^H v,
  * for nrhs columns v (ldv >= N) into x (ldx >= N).  x may not alias v.
@@ -200,8 +238,12 @@ bem_status solve_backward(bem_handle h, const void* g_dev, int64_t ldg, void* la
  *  - All calls share the one array and it keeps the last call's contents (nothing in it
  *    needs to start at zero).  Calls whose work overlaps on the GPU -- two streams, or two
  *    handles -- race on the array: serialise them.
- *  - Layouts and aliasing rules are those of solve_many; no refinement and no residual
- *    report (use solve_many for those).  Needs factor. */
+ *  - Layouts, aliasing rules and the limit 1 <= nrhs <= 2^24 are those of solve_many; no
+ *    refinement and no residual report (use solve_many for those).  Needs factor.
+ *  - On a BEM_MIXED_BF16 handle it solves with the factors that handle built (U, V^H and
+ *    the core from tensor-core products) in FP64, without refinement: the result is the
+ *    exact inverse of that handle's compressed operator up to FP64 rounding, which is what
+ *    solve_many's refinement converges to. */
 bem_status solve_many_noalloc(bem_handle h, const void* v_dev, int64_t ldv, void* x_dev, int64_t ldx,
                               int64_t nrhs);
 

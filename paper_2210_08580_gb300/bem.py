@@ -27,13 +27,13 @@ EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error",
            "bem_assemble", "filter_apply", "compress_compact", "factor", "bem_rhs_planewave",
            "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info", "bem_timing_enable",
            "bem_timing_report", "solve_many_noalloc", "bem_farfield", "bem_farfield_adjoint",
-           "bem_shape_vjp")
+           "bem_shape_vjp", "bem_rhs_pointsource")
 
 
 class BemOptions(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("include_kernel_mode", ctypes.c_int),
                 ("refine_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
-                ("split_slices", ctypes.c_int), ("rhs_slices", ctypes.c_int)]
+                ("split_slices", ctypes.c_int), ("rhs_slices", ctypes.c_int), ("solve_slices", ctypes.c_int)]
 
 
 class BemInfo(ctypes.Structure):
@@ -41,6 +41,48 @@ class BemInfo(ctypes.Structure):
                 ("k", ctypes.c_double), ("h", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("beta", ctypes.c_double), ("sigma_max", ctypes.c_double), ("stage", ctypes.c_int),
                 ("prec", ctypes.c_int), ("quad_points", ctypes.c_int64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class TorchDeviceMemory:
+    """Device memory provider of a handle backed by PyTorch's caching allocator: blocks are
+    taken on the handle's current stream (``stream_of()``), so a block the library hands back
+    is reused only by work ordered after that stream's (what bem_create asks of a provider).
+    ``allocated`` is the number of bytes currently held by the library."""
+
+    def __init__(self, device: int, stream_of):
+        self.device = device
+        self.stream_of = stream_of
+        self.sizes = {}
+        self.allocated = 0
+        self.peak = 0
+        self.calls = 0
+
+        def _alloc(nbytes, _ctx):
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream_of())
+            except Exception:
+                return None
+            self.sizes[ptr] = int(nbytes)
+            self.allocated += int(nbytes)
+            self.peak = max(self.peak, self.allocated)
+            self.calls += 1
+            return ptr
+
+        def _free(ptr, _ctx):
+            if not ptr:
+                return
+            self.allocated -= self.sizes.pop(ptr, 0)
+            try:
+                torch.cuda.caching_allocator_delete(ptr)
+            except Exception:       # interpreter shutdown: the allocator is gone already
+                pass
+
+        self.alloc_fn = ALLOC_FN(_alloc)        # kept alive as long as the provider
+        self.free_fn = FREE_FN(_free)
 
 
 class BemError(RuntimeError):
@@ -64,7 +106,7 @@ def load_library(path: str = LIB_PATH):
     vp, i64, dbl, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
     L.bem_default_options.argtypes = [ctypes.POINTER(BemOptions)]
     L.bem_default_options.restype = None
-    L.bem_create.argtypes = [ctypes.POINTER(vp), i32, vp, ctypes.POINTER(BemOptions)]
+    L.bem_create.argtypes = [ctypes.POINTER(vp), i32, vp, ctypes.POINTER(BemOptions), ALLOC_FN, FREE_FN, vp]
     L.bem_destroy.argtypes = [vp]
     L.bem_last_error.argtypes = [vp]
     L.bem_last_error.restype = ctypes.c_char_p
@@ -74,6 +116,7 @@ def load_library(path: str = LIB_PATH):
     L.compress_compact.argtypes = [vp, dbl, ctypes.POINTER(i64)]
     L.factor.argtypes = [vp]
     L.bem_rhs_planewave.argtypes = [vp, vp, i64, vp, vp, i64]
+    L.bem_rhs_pointsource.argtypes = [vp, vp, i64, vp, vp, i64]
     L.solve_many.argtypes = [vp, vp, i64, vp, i64, i64, ctypes.POINTER(ctypes.c_int32),
                              ctypes.POINTER(ctypes.c_double)]
     L.solve_backward.argtypes = [vp, vp, i64, vp, i64, i64]
@@ -87,7 +130,7 @@ def load_library(path: str = LIB_PATH):
     L.bem_timing_enable.argtypes = [vp, i32]
     L.bem_timing_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     for name in ("bem_create", "bem_destroy", "bem_set_stream", "bem_assemble", "filter_apply",
-                 "compress_compact", "factor", "bem_rhs_planewave", "solve_many", "solve_backward",
+                 "compress_compact", "factor", "bem_rhs_planewave", "bem_rhs_pointsource", "solve_many", "solve_backward",
                  "bem_get_matrix", "bem_get_info", "bem_timing_enable", "bem_timing_report", "bem_farfield",
                  "bem_farfield_adjoint", "bem_shape_vjp"):
         getattr(L, name).restype = ctypes.c_int
@@ -108,7 +151,11 @@ class Solver:
 
     def __init__(self, device: int = 0, prec: str = "fp64", include_kernel_mode: bool = True,
                  refine_rtol: float = 1e-10, max_refine: int = 6, stream: torch.cuda.Stream | None = None,
-                 split_slices: int = 0, rhs_slices: int = 0):
+                 split_slices: int = 0, rhs_slices: int = 0, solve_slices: int = 0,
+                 memory: str = "torch"):
+        """memory: "torch" (default) -- every device buffer of the handle comes from
+        PyTorch's caching allocator through the bem_create hooks; "cuda" -- the library
+        allocates with the CUDA runtime itself."""
         self.L = load_library()
         self.device = torch.device("cuda", device)
         opt = BemOptions()
@@ -119,10 +166,19 @@ class Solver:
         opt.max_refine = max_refine
         opt.split_slices = split_slices
         opt.rhs_slices = rhs_slices
+        opt.solve_slices = solve_slices
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = ctypes.c_void_p()
+        if memory == "torch":
+            self.memory = TorchDeviceMemory(device, lambda: self.stream)
+            hooks = (self.memory.alloc_fn, self.memory.free_fn, None)
+        elif memory == "cuda":
+            self.memory = None
+            hooks = (ALLOC_FN(), FREE_FN(), None)
+        else:
+            raise ValueError("memory must be 'torch' or 'cuda'")
         self._check(self.L.bem_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream),
-                                      ctypes.byref(opt)), None)
+                                      ctypes.byref(opt), *hooks), None)
         self.h = h
         self.N = None
         self._ik = bool(include_kernel_mode)
@@ -143,6 +199,11 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        """Enqueue later calls (and take later device memory) on ``stream``."""
+        self.stream = stream
+        self._check(self.L.bem_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)))
 
     # ---------------------------------------------------------------- stages
     def assemble(self, verts: torch.Tensor, k: float, ops: str = "SW"):
@@ -173,6 +234,16 @@ class Solver:
         v = torch.empty((nrhs, self.N), dtype=torch.complex128, device=self.device) if want_v else None
         self._check(self.L.bem_rhs_planewave(self.h, _ptr(ang), nrhs, _ptr(f) if f is not None else None,
                                              _ptr(v) if v is not None else None, self.N))
+        return (f, v) if want_f else v
+
+    def rhs_pointsource(self, sources, want_f: bool = False, want_v: bool = True):
+        """Right-hand sides of line sources at ``sources`` ((nsrc, 2) positions off the curve)."""
+        src = torch.as_tensor(sources, dtype=torch.float64).to(self.device).reshape(-1, 2).contiguous()
+        nsrc = src.shape[0]
+        f = torch.empty((nsrc, self.N), dtype=torch.complex128, device=self.device) if want_f else None
+        v = torch.empty((nsrc, self.N), dtype=torch.complex128, device=self.device) if want_v else None
+        self._check(self.L.bem_rhs_pointsource(self.h, _ptr(src), nsrc, _ptr(f) if f is not None else None,
+                                               _ptr(v) if v is not None else None, self.N))
         return (f, v) if want_f else v
 
     def solve(self, v: torch.Tensor, report: bool = False, out: torch.Tensor | None = None):

@@ -24,16 +24,44 @@ bem_status bem_cuda_check(bem_ctx* h, cudaError_t e, const char* what) {
     return bem_fail(h, BEM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+cudaError_t bem_dmalloc(bem_ctx* h, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    if (!h->dev_alloc) return cudaMalloc(p, bytes);
+    *p = h->dev_alloc(bytes, h->alloc_ctx);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+
+void bem_dfree(bem_ctx* h, void* p) {
+    if (!p) return;
+    if (h->dev_free) h->dev_free(p, h->alloc_ctx);
+    else cudaFree(p);
+}
+
+cudaError_t bem_dmalloc_async(bem_ctx* h, void** p, size_t bytes) {
+    if (!h->dev_alloc) {
+        *p = nullptr;
+        return cudaMallocAsync(p, bytes ? bytes : 256, h->stream);
+    }
+    return bem_dmalloc(h, p, bytes);
+}
+
+void bem_dfree_async(bem_ctx* h, void* p) {
+    if (!p) return;
+    if (h->dev_free) h->dev_free(p, h->alloc_ctx);
+    else cudaFreeAsync(p, h->stream);
+}
+
 bem_status bem_workspace(bem_ctx* h, size_t bytes, void** out) {
     if (bytes > h->work_bytes) {
         if (h->work) {
             cudaStreamSynchronize(h->stream);
-            cudaFree(h->work);
+            bem_dfree(h, h->work);
             h->work = nullptr;
             h->work_bytes = 0;
         }
         size_t want = std::max(bytes, (size_t)1 << 20);
-        BEM_CUDA(h, cudaMalloc(&h->work, want));
+        BEM_CUDA(h, bem_dmalloc(h, &h->work, want));
         h->work_bytes = want;
     }
     *out = h->work;
@@ -56,7 +84,7 @@ struct Carve {
 };
 
 static void free_ptr(bem_ctx* h, void** p) {
-    if (*p) { cudaFree(*p); *p = nullptr; }
+    if (*p) { bem_dfree(h, *p); *p = nullptr; }
     h->caps.erase(p);
 }
 
@@ -69,7 +97,7 @@ static bem_status ensure_alloc(bem_ctx* h, void** p, size_t bytes) {
         BEM_CUDA(h, cudaStreamSynchronize(h->stream));
         free_ptr(h, p);
     }
-    BEM_CUDA(h, cudaMalloc(p, bytes));
+    BEM_CUDA(h, bem_dmalloc(h, p, bytes));
     h->caps[p] = bytes;
     return BEM_OK;
 }
@@ -111,13 +139,19 @@ void bem_default_options(bem_options* opt) {
     opt->max_refine = 6;
     opt->split_slices = 0;
     opt->rhs_slices = 0;
+    opt->solve_slices = 0;
 }
 
-bem_status bem_create(bem_handle* out, int device, void* cuda_stream, const bem_options* opt) {
+bem_status bem_create(bem_handle* out, int device, void* cuda_stream, const bem_options* opt,
+                      bem_dev_alloc_fn dev_alloc, bem_dev_free_fn dev_free, void* alloc_ctx) {
     if (!out) return BEM_E_INVALID;
     *out = nullptr;
+    if ((dev_alloc == nullptr) != (dev_free == nullptr)) return BEM_E_INVALID;
     bem_ctx* h = new (std::nothrow) bem_ctx();
     if (!h) return BEM_E_NOMEM;
+    h->dev_alloc = dev_alloc;
+    h->dev_free = dev_free;
+    h->alloc_ctx = alloc_ctx;
     if (opt) h->opt = *opt; else bem_default_options(&h->opt);
     if (h->opt.prec != BEM_FP64 && h->opt.prec != BEM_MIXED_BF16) { delete h; return BEM_E_INVALID; }
     if (h->opt.refine_rtol <= 0.0) h->opt.refine_rtol = 1e-10;
@@ -134,11 +168,12 @@ bem_status bem_create(bem_handle* out, int device, void* cuda_stream, const bem_
             g_tab_done[device] = true;
         }
     }
-    if (cudaMalloc((void**)&h->dev_err, sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&h->bar, 4 * sizeof(unsigned)) != cudaSuccess ||
-        cudaMalloc((void**)&h->qpts, sizeof(unsigned long long)) != cudaSuccess) {
-        cudaFree(h->dev_err);
-        cudaFree(h->bar);
+    if (bem_dmalloc(h, (void**)&h->dev_err, sizeof(int)) != cudaSuccess ||
+        bem_dmalloc(h, (void**)&h->bar, 4 * sizeof(unsigned)) != cudaSuccess ||
+        bem_dmalloc(h, (void**)&h->qpts, sizeof(unsigned long long)) != cudaSuccess) {
+        bem_dfree(h, h->dev_err);
+        bem_dfree(h, h->bar);
+        bem_dfree(h, h->qpts);
         delete h;
         return BEM_E_NOMEM;
     }
@@ -173,6 +208,8 @@ bem_status bem_destroy(bem_handle h) {
     free_stage_buffers(h, 0);
     tc_destroy(h);
     free_ptr(h, &h->work);
+    free_ptr(h, (void**)&h->btab);
+    free_ptr(h, (void**)&h->btabf);
     free_ptr(h, (void**)&h->dev_err);
     free_ptr(h, (void**)&h->bar);
     free_ptr(h, (void**)&h->qpts);
@@ -261,10 +298,11 @@ bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha) {
     h->alpha = alpha;
     h->beta = (1.0 + 2.0 * alpha) / 4.0;
     if ((st = launch_fourier_basis(h, h->Q, N, nc, inc, h->gm, h->hbar)) != BEM_OK) return st;
-    cplx *Y1 = nullptr, *tmp = nullptr;
+    cplx *Y1 = nullptr, *tmp = nullptr, *cfix = nullptr;
     Carve cv;
     cv.add((void**)&Y1, sizeof(cplx) * nc * N);
     cv.add((void**)&tmp, sizeof(cplx) * nc * N);
+    cv.add((void**)&cfix, sizeof(cplx) * (N + nc));
     if ((st = cv.commit(h)) != BEM_OK) return st;
     if (h->opt.prec == BEM_MIXED_BF16) {
         // Y1 = Q^T S and B = Y2 N as split-bf16 tensor-core products
@@ -278,6 +316,8 @@ bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha) {
     if ((st = apply_gram_inverse(h, 0, Y1, Y1, tmp, N, nc, nc, 1, h->hbar, false)) != BEM_OK) return st;
     if (h->opt.prec == BEM_MIXED_BF16) {
         if ((st = tc_product_left(h, TC_OP_W, nullptr, Y1, nc, h->B)) != BEM_OK) return st;
+        // the split product's action on the constant vector, from N's FP64 row sums
+        if ((st = launch_const_correction(h, h->W, Y1, h->B, nc, N, cfix)) != BEM_OK) return st;
         if (alpha != 0.0) {
             if ((st = tc_product_left(h, TC_OP_D, h->Q, nullptr, nc, tmp)) != BEM_OK) return st;
             if ((st = launch_axpby(h, h->B, nc, tmp, nc, cmk(-alpha, 0), cmk(1, 0), nc, N)) != BEM_OK) return st;
@@ -384,15 +424,13 @@ bem_status factor(bem_handle h) {
     return BEM_OK;
 }
 
-bem_status bem_rhs_planewave(bem_handle h, const double* angles, int64_t nrhs, void* f_out, void* v_out, int64_t ld) {
-    if (!h) return BEM_E_INVALID;
-    h->err.clear();
-    if (h->stage < 1) return bem_fail(h, BEM_E_INVALID, "bem_rhs_planewave: call bem_assemble first");
+}  // extern "C"
+
+// f (and hz for the CFIE) by `make`, then v = G^-1 S G^-1 f - alpha G^-1 hz
+template <class Make>
+static bem_status rhs_common(bem_ctx* h, const char* who, int64_t nrhs, void* f_out, void* v_out, int64_t ld,
+                             Make make) {
     const int64_t N = h->N;
-    if (!angles || nrhs < 1 || nrhs > 65535 || ld < N)
-        return bem_fail(h, BEM_E_INVALID, "bem_rhs_planewave: need angles, 1 <= nrhs <= 65535, ld >= N");
-    if (!f_out && !v_out) return BEM_OK;
-    BEM_CUDA(h, cudaSetDevice(h->device));
     bem_status st;
     // every internal block uses the caller's leading dimension ld
     cplx *f = (cplx*)f_out, *hz = nullptr, *y = nullptr, *tmp = nullptr;
@@ -404,7 +442,7 @@ bem_status bem_rhs_planewave(bem_handle h, const double* angles, int64_t nrhs, v
         cv.add((void**)&tmp, sizeof(cplx) * ld * nrhs);
     }
     if ((st = cv.commit(h)) != BEM_OK) return st;
-    if ((st = launch_rhs(h, angles, nrhs, f, hz, ld)) != BEM_OK) return st;
+    if ((st = make(f, hz)) != BEM_OK) return st;
     if (!v_out) return BEM_OK;
     cplx* v = (cplx*)v_out;
     // y = G^-1 f
@@ -419,8 +457,35 @@ bem_status bem_rhs_planewave(bem_handle h, const double* angles, int64_t nrhs, v
     if (hz) {
         if ((st = launch_axpby(h, v, ld, hz, ld, cmk(-h->alpha, 0), cmk(1, 0), N, nrhs)) != BEM_OK) return st;
     }
-    if ((st = apply_gram_inverse(h, 0, v, v, tmp, N, nrhs, 1, ld, h->hbar, false)) != BEM_OK) return st;
-    return BEM_OK;
+    (void)who;
+    return apply_gram_inverse(h, 0, v, v, tmp, N, nrhs, 1, ld, h->hbar, false);
+}
+
+extern "C" {
+
+bem_status bem_rhs_planewave(bem_handle h, const double* angles, int64_t nrhs, void* f_out, void* v_out, int64_t ld) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 1) return bem_fail(h, BEM_E_INVALID, "bem_rhs_planewave: call bem_assemble first");
+    if (!angles || nrhs < 1 || nrhs > 65535 || ld < h->N)
+        return bem_fail(h, BEM_E_INVALID, "bem_rhs_planewave: need angles, 1 <= nrhs <= 65535, ld >= N");
+    if (!f_out && !v_out) return BEM_OK;
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    return rhs_common(h, "bem_rhs_planewave", nrhs, f_out, v_out, ld,
+                      [&](cplx* f, cplx* hz) { return launch_rhs(h, angles, nrhs, f, hz, ld); });
+}
+
+bem_status bem_rhs_pointsource(bem_handle h, const double* src_xy, int64_t nsrc, void* f_out, void* v_out,
+                               int64_t ld) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 1) return bem_fail(h, BEM_E_INVALID, "bem_rhs_pointsource: call bem_assemble first");
+    if (!src_xy || nsrc < 1 || nsrc > 65535 || ld < h->N)
+        return bem_fail(h, BEM_E_INVALID, "bem_rhs_pointsource: need sources, 1 <= nsrc <= 65535, ld >= N");
+    if (!f_out && !v_out) return BEM_OK;
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    return rhs_common(h, "bem_rhs_pointsource", nsrc, f_out, v_out, ld,
+                      [&](cplx* f, cplx* hz) { return launch_rhs_point(h, src_xy, nsrc, f, hz, ld); });
 }
 
 // x = v/beta - beta^-2 U Kinv V^H v, all FP64 products
@@ -629,11 +694,11 @@ bem_status bem_farfield_adjoint(bem_handle h, const double* obs_angles, int64_t 
     // F^H g = conj(C0) conj(Fm) g = conj( C0 Fm conj(g) ) : conjugate g into out's storage
     // is not possible (shapes differ), so go through a scratch copy of conj(g)
     cplx* gc = nullptr;
-    BEM_CUDA(h, cudaMallocAsync((void**)&gc, sizeof(cplx) * nobs * nrhs, h->stream));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&gc, sizeof(cplx) * nobs * nrhs));
     if ((st = launch_conj_scale(h, (const cplx*)g, ldg, gc, nobs, cmk(1, 0), nobs, nrhs)) != BEM_OK) return st;
     h->tag = "gemm_farfield_adjoint";
     st = zgemm(h, OP_N, OP_N, h->N, nrhs, nobs, farfield_c0(h->k), Fm, h->N, gc, nobs, cmk(0, 0), (cplx*)out, ldo);
-    cudaFreeAsync(gc, h->stream);
+    bem_dfree_async(h, gc);
     if (st != BEM_OK) return st;
     return launch_conj_scale(h, (const cplx*)out, ldo, (cplx*)out, ldo, cmk(1, 0), h->N, nrhs);
 }

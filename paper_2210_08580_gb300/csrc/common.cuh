@@ -84,6 +84,13 @@ struct bem_ctx {
     bem_options opt{};
     std::string err;
 
+    // device memory provider: the caller's hooks (bem_create), or the CUDA runtime when NULL
+    void* (*dev_alloc)(size_t, void*) = nullptr;
+    void (*dev_free)(void*, void*) = nullptr;
+    void* alloc_ctx = nullptr;
+    double* btab = nullptr;           // far-field Bessel tables (this handle's copy)
+    float4* btabf = nullptr;
+
     // geometry and assembly
     int64_t N = 0;
     double k = 0.0, hbar = 0.0;
@@ -161,3 +168,15 @@ bem_status bem_cuda_check(bem_ctx* h, cudaError_t e, const char* what);
 
 // workspace: returns a device pointer of at least `bytes`, growing the handle's buffer
 bem_status bem_workspace(bem_ctx* h, size_t bytes, void** out);
+
+// Device memory of a handle.  With the caller's hooks (bem_create) every byte comes from
+// dev_alloc and goes back through dev_free; without them from the CUDA runtime.
+// bem_dmalloc/bem_dfree: buffers kept across calls (freed only after the stream is idle).
+// bem_dmalloc_async/bem_dfree_async: stream-ordered temporaries of one call on h->stream
+// (cudaMallocAsync/cudaFreeAsync; with hooks, dev_free is called once the work using the
+// block is enqueued, and the provider must order reuse after it, as a stream-ordered
+// caching allocator on that stream does).  A failed allocation is cudaErrorMemoryAllocation.
+cudaError_t bem_dmalloc(bem_ctx* h, void** p, size_t bytes);
+void bem_dfree(bem_ctx* h, void* p);
+cudaError_t bem_dmalloc_async(bem_ctx* h, void** p, size_t bytes);
+void bem_dfree_async(bem_ctx* h, void* p);

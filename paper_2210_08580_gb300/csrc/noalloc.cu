@@ -41,8 +41,9 @@ extern "C" bem_status solve_many_noalloc(bem_handle h, const void* v_dev, int64_
     h->err.clear();
     if (h->stage < 4) return bem_fail(h, BEM_E_INVALID, "solve_many_noalloc: call factor first");
     const int64_t N = h->N, r = h->r;
-    if (!v_dev || !x_dev || nrhs < 1 || ldv < N || ldx < N || v_dev == x_dev)
-        return bem_fail(h, BEM_E_INVALID, "solve_many_noalloc: need v, x (not aliased), nrhs >= 1, ld >= N");
+    if (!v_dev || !x_dev || nrhs < 1 || nrhs > (1 << 24) || ldv < N || ldx < N || v_dev == x_dev)
+        return bem_fail(h, BEM_E_INVALID,
+                        "solve_many_noalloc: need v, x (not aliased), 1 <= nrhs <= 2^24, ld >= N");
     if (r * nrhs > BEM_NOALLOC_MAX)
         return bem_fail(h, BEM_E_UNSUPPORTED,
                         "solve_many_noalloc: rank * nrhs exceeds the fixed scratch of 262144 complex "

@@ -688,13 +688,13 @@ static bem_status encode_map(bem_ctx* h, TcOperand& op, int S) {
 static bem_status reserve(bem_ctx* h, TcOperand& op, int64_t rows, int64_t Kp, int S) {
     const size_t need = (size_t)S * rows * Kp * sizeof(__nv_bfloat16);
     if (need > op.cap) {
-        if (op.slices) { cudaStreamSynchronize(h->stream); cudaFree(op.slices); op.slices = nullptr; op.cap = 0; }
-        BEM_CUDA(h, cudaMalloc((void**)&op.slices, need));
+        if (op.slices) { cudaStreamSynchronize(h->stream); bem_dfree(h, op.slices); op.slices = nullptr; op.cap = 0; }
+        BEM_CUDA(h, bem_dmalloc(h, (void**)&op.slices, need));
         op.cap = need;
     }
     if ((size_t)rows * sizeof(int) > op.exp_cap) {
-        if (op.exps) { cudaStreamSynchronize(h->stream); cudaFree(op.exps); op.exps = nullptr; }
-        BEM_CUDA(h, cudaMalloc((void**)&op.exps, (size_t)rows * sizeof(int)));
+        if (op.exps) { cudaStreamSynchronize(h->stream); bem_dfree(h, op.exps); op.exps = nullptr; }
+        BEM_CUDA(h, bem_dmalloc(h, (void**)&op.exps, (size_t)rows * sizeof(int)));
         op.exp_cap = (size_t)rows * sizeof(int);
     }
     op.rows = rows;
@@ -847,8 +847,8 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     if (splits > 1) {
         const size_t need = (size_t)splits * p.Ml * p.ml * sizeof(double2);
         if (need > t->part_cap) {
-            if (t->part) { cudaStreamSynchronize(h->stream); cudaFree(t->part); t->part = nullptr; t->part_cap = 0; }
-            BEM_CUDA(h, cudaMalloc((void**)&t->part, need));
+            if (t->part) { cudaStreamSynchronize(h->stream); bem_dfree(h, t->part); t->part = nullptr; t->part_cap = 0; }
+            BEM_CUDA(h, bem_dmalloc(h, (void**)&t->part, need));
             t->part_cap = need;
         }
         p.part = t->part;
@@ -1029,19 +1029,21 @@ bem_status tc_core_product(bem_ctx* h, cplx* Kt) {
 }
 
 // x = v/beta - beta^-2 U Kinv V^H v with tensor-core products (T, T2: r x nrhs scratch)
+// Ss: digit slices of the two products (the leading Ss of U's and V^H's, v and T2 sliced
+// with Ss), 0 = all of them
 static bem_status woodbury_tc(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x, int64_t ldx, int64_t nrhs, cplx* T,
-                              cplx* T2, double xscale, double vscale) {
+                              cplx* T2, double xscale, double vscale, int Ss) {
     TcState* t = tcs(h);
     const int64_t N = h->N, r = h->r;
     bem_status st;
-    if ((st = slice_B(h, t->bbuf, v, 0, N, nrhs, 1, ldv)) != BEM_OK) return st;
-    if ((st = tc_gemm(h, t->opVh, t->bbuf, T, r, 0, 1.0, 0.0, "tc_solve_Vhv")) != BEM_OK) return st;
+    if ((st = slice_B(h, t->bbuf, v, 0, N, nrhs, 1, ldv, Ss)) != BEM_OK) return st;
+    if ((st = tc_gemm(h, t->opVh, t->bbuf, T, r, 0, 1.0, 0.0, "tc_solve_Vhv", Ss)) != BEM_OK) return st;
     h->tag = "gemm_solve_core";
     if ((st = zgemm_df(h, r, nrhs, r, h->K, r, T, r, T2, r)) != BEM_OK) return st;
     // x <- xscale x + vscale v / beta ; then x -= beta^-2 U T2
     if ((st = launch_axpby(h, x, ldx, v, ldv, cmk(vscale / h->beta, 0), cmk(xscale, 0), N, nrhs)) != BEM_OK) return st;
-    if ((st = slice_B(h, t->bbuf, T2, 0, r, nrhs, 1, r)) != BEM_OK) return st;
-    return tc_gemm(h, t->opU, t->bbuf, x, ldx, 0, -vscale / (h->beta * h->beta), 1.0, "tc_solve_UT");
+    if ((st = slice_B(h, t->bbuf, T2, 0, r, nrhs, 1, r, Ss)) != BEM_OK) return st;
+    return tc_gemm(h, t->opU, t->bbuf, x, ldx, 0, -vscale / (h->beta * h->beta), 1.0, "tc_solve_UT", Ss);
 }
 
 bem_status tc_solve_refined(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x, int64_t ldx, int64_t nrhs, int32_t* iters,
@@ -1061,8 +1063,12 @@ bem_status tc_solve_refined(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x, int
         rho = (cplx*)((char*)base + 2 * bT);
         dres = (double*)((char*)base + 2 * bT + bR);
     }
+    // the Woodbury solves (initial and corrections) may use fewer digit slices than the
+    // residual products (bem_options.solve_slices); the refinement then recovers the digits
+    int Ss = h->opt.solve_slices;
+    if (Ss < 3 || Ss > t->S) Ss = 0;
     // initial solve
-    if ((st = woodbury_tc(h, v, ldv, x, ldx, nrhs, T, T2, 0.0, 1.0)) != BEM_OK) return st;
+    if ((st = woodbury_tc(h, v, ldv, x, ldx, nrhs, T, T2, 0.0, 1.0, Ss)) != BEM_OK) return st;
     int it = 0;
     double res = 0.0;
     for (;;) {
@@ -1084,7 +1090,7 @@ bem_status tc_solve_refined(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x, int
         }
         if (!(res > h->opt.refine_rtol) || it >= h->opt.max_refine) break;
         // x += Woodbury(rho)
-        if ((st = woodbury_tc(h, rho, N, x, ldx, nrhs, T, T2, 1.0, 1.0)) != BEM_OK) return st;
+        if ((st = woodbury_tc(h, rho, N, x, ldx, nrhs, T, T2, 1.0, 1.0, Ss)) != BEM_OK) return st;
         ++it;
     }
     if (iters) *iters = it;
@@ -1094,28 +1100,29 @@ bem_status tc_solve_refined(bem_ctx* h, const cplx* v, int64_t ldv, cplx* x, int
     return BEM_OK;
 }
 
-static void free_op(TcOperand& op) {
-    if (op.slices) cudaFree(op.slices);
-    if (op.exps) cudaFree(op.exps);
+static void free_op(bem_ctx* h, TcOperand& op) {
+    bem_dfree(h, op.slices);
+    bem_dfree(h, op.exps);
     op = TcOperand();
 }
 
 void tc_release_operands(bem_ctx* h) {
     if (!h->tc) return;
     TcState* t = (TcState*)h->tc;
-    free_op(t->opS); free_op(t->opW); free_op(t->opD);
+    free_op(h, t->opS); free_op(h, t->opW); free_op(h, t->opD);
 }
 void tc_release_solve(bem_ctx* h) {
     if (!h->tc) return;
     TcState* t = (TcState*)h->tc;
-    free_op(t->opVh); free_op(t->opU);
+    free_op(h, t->opVh); free_op(h, t->opU);
 }
 void tc_destroy(bem_ctx* h) {
     if (!h->tc) return;
     TcState* t = (TcState*)h->tc;
-    free_op(t->opS); free_op(t->opW); free_op(t->opD); free_op(t->opVh); free_op(t->opU); free_op(t->bbuf);
-    free_op(t->tmpA);
-    if (t->part) cudaFree(t->part);
+    free_op(h, t->opS); free_op(h, t->opW); free_op(h, t->opD); free_op(h, t->opVh); free_op(h, t->opU);
+    free_op(h, t->bbuf);
+    free_op(h, t->tmpA);
+    bem_dfree(h, t->part);
     delete t;
     h->tc = nullptr;
 }

@@ -115,3 +115,43 @@ def test_mixed_matches_fp64_c3_16384(B):
         s.close()
     err = float((xs["mixed"] - xs["fp64"]).abs().max() / xs["fp64"].abs().max())
     assert err <= MIXED_SOLVE_TOL, err
+
+
+def test_refinement_sweeps_recover_a_crude_solve(B, star301_ref):
+    """bem_options.solve_slices = 3: the Woodbury solves run on 3 digit slices (about 21
+    bits) while the residual products keep all six, so the first iterate misses
+    refine_rtol and the FP64-residual refinement (Sec. IV-C solve, mixed path) has to
+    sweep; the refined solution meets the same bars as the default path."""
+    ref = star301_ref["efie"]
+    s = B.Solver(device=0, prec="mixed", solve_slices=3)
+    s.assemble(_cuda(star301_ref["v"]), star301_ref["k"], ops="SW")
+    s.filter_apply(41)
+    assert s.compress(1e-10) == ref["rank"]
+    s.factor()
+    vv = s.rhs_planewave(_cuda(star301_ref["ang"]))
+    x, it, res = s.solve(vv, report=True)
+    assert it >= 1, it
+    assert res <= 1e-10, res
+    assert _rel(x.cpu().numpy().T, ref["x"]) <= MIXED_SOLVE_TOL
+    s.close()
+
+
+def test_refinement_budget_exhausted_reports_not_converged(B, star301_ref):
+    """With the crude 3-slice solve and max_refine = 0 the residual stays above
+    refine_rtol: solve_many returns BEM_E_NOT_CONVERGED, reports the residual, and leaves
+    the unrefined iterate in x (close to the oracle at the 3-slice accuracy)."""
+    ref = star301_ref["efie"]
+    s = B.Solver(device=0, prec="mixed", solve_slices=3, max_refine=0)
+    s.assemble(_cuda(star301_ref["v"]), star301_ref["k"], ops="SW")
+    s.filter_apply(41)
+    s.compress(1e-10)
+    s.factor()
+    vv = s.rhs_planewave(_cuda(star301_ref["ang"]))
+    x = torch.zeros_like(vv)
+    with pytest.raises(B.BemError) as e:
+        s.solve(vv, report=True, out=x)
+    assert e.value.status == 6                       # BEM_E_NOT_CONVERGED
+    assert "residual" in str(e.value)
+    err = _rel(x.cpu().numpy().T, ref["x"])
+    assert 1e-12 < err <= 1e-3, err
+    s.close()
