@@ -310,6 +310,8 @@ struct AsmParams {
     int* rexpS;           // if set: atomic max of the exponent fields per column of S, W
     int* rexpW;           //   (W's entries with cyclic |i - j| <= wband left out)
     int wband;
+    double2* kpart;       // if set: per tile column slot s and row i, the sum over the tile's
+                          //   columns of N's k^2 term (kpart[s N + i]; see k_assemble_sn)
     SeriesCoef sc;
 };
 
@@ -871,7 +873,7 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     }
     const bool mirror = (ti != tj);
     // entry (i0 + il, j0 + jl) of S and N, written at (i, j)
-    auto entry = [&](int il, int jl, double2& ds, double2& dw) -> bool {
+    auto entry = [&](int il, int jl, double2& ds, double2& dw, cdfl& kt) -> bool {
         const int i = i0 + il, j = j0 + jl;
         if (i >= N || j >= N) return false;
         cdfl sv, wv = cdfl_zero();
@@ -891,6 +893,7 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
         const int64_t off = (int64_t)i + (int64_t)j * p.ld;
         ds = cdfl_to(sv);
         dw = make_double2(0.0, 0.0);
+        kt = wv;
         if (p.W) {
             // sum_ab sigma_a sigma_b M0(i-a, j-b) = (M0[i-1][j-1] - M0[i-1][j]) - (M0[i][j-1] - M0[i][j]),
             // plus the k^2 term, exactly in fixed point; one rounding to FP64
@@ -910,6 +913,7 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     // split products are scaled per column of S and N; N's band is left out).
     const bool track = p.rexpS != nullptr;
     __shared__ int eRow[2][32];
+    float4* sK = reinterpret_cast<float4*>(gF + 9 * TP);  // T*T: the entries' k^2 terms [jl T + il]
     if (threadIdx.x < 64) eRow[threadIdx.x >> 5][threadIdx.x & 31] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -922,14 +926,18 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
             const int jl = wid + 8 * q;
             if (jl >= T) break;
             double2 ds = make_double2(0.0, 0.0), dw = make_double2(0.0, 0.0);
+            cdfl kt = cdfl_zero();
             int fs = 0, fw = 0;
-            if (lane < T && entry(lane, jl, ds, dw) && track) {
+            const bool ok = lane < T && entry(lane, jl, ds, dw, kt);
+            if (!ok) kt = cdfl_zero();
+            if (ok && track) {
                 int d = lane + i0 - (jl + j0); if (d < 0) d = -d;
                 fs = max(exp_field_of(ds.x), exp_field_of(ds.y));
                 fw = (min(d, N - d) <= p.wband) ? 0 : max(exp_field_of(dw.x), exp_field_of(dw.y));
             }
             keepS[q] = ds;
             keepW[q] = dw;
+            if (p.kpart && lane < T) sK[jl * T + lane] = cdfl_pack(kt);
             if (track) {
                 const int cs = (int)__reduce_max_sync(0xffffffffu, (unsigned)fs);
                 const int cw = (int)__reduce_max_sync(0xffffffffu, (unsigned)fw);
@@ -947,6 +955,22 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
         }
     }
     __syncthreads();                                     // sI is no longer read
+    // N 1 = the row sums of the k^2 term exactly (the derivative term's vanish): the tile's
+    // share, summed in a fixed order, goes to the slot of its tile column (its rows) and,
+    // mirrored, of its tile row (the columns' sums are the mirror's row sums)
+    if (p.kpart) {
+        const int t = threadIdx.x;
+        if (t < T && i0 + t < N) {
+            cdfl acc = cdfl_unpack(sK[t]);
+            for (int jl = 1; jl < T; ++jl) acc = cdfl_add(acc, cdfl_unpack(sK[jl * T + t]));
+            p.kpart[(int64_t)tj * N + i0 + t] = cdfl_to(acc);
+        } else if (mirror && t >= 32 && t < 32 + T && j0 + t - 32 < N) {
+            const int jl = t - 32;
+            cdfl acc = cdfl_unpack(sK[jl * T]);
+            for (int il = 1; il < T; ++il) acc = cdfl_add(acc, cdfl_unpack(sK[jl * T + il]));
+            p.kpart[(int64_t)ti * N + j0 + jl] = cdfl_to(acc);
+        }
+    }
     if (track && mirror && threadIdx.x < 2 * T) {
         const int m = threadIdx.x / T, l = threadIdx.x % T;
         if (i0 + l < N) atomicMax((m ? p.rexpW : p.rexpS) + i0 + l, eRow[m][l]);
@@ -1131,16 +1155,29 @@ static bem_status run_assemble(bem_ctx* h, AsmParams& p) {
     return BEM_OK;
 }
 
+// k1[i] = sum over the tile slots s of kpart[s N + i], in slot order
+__global__ void k_sum_slots(const double2* __restrict__ kpart, int nslots, int N, cplx* k1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    cplx t = cmk(0, 0);
+    for (int s = 0; s < nslots; ++s) t = cadd(t, kpart[(int64_t)s * N + i]);
+    k1[i] = t;
+}
+
 template <int T>
 static bem_status run_assemble_sn(bem_ctx* h, AsmParams& p) {
     constexpr int TP = T + 1;
     const size_t smem = (size_t)TP * TP * (4 * sizeof(float4) + sizeof(float4) + sizeof(float2)) +
-                        (size_t)16 * TP * sizeof(float2);
+                        (size_t)16 * TP * sizeof(float2) + (size_t)T * T * sizeof(float4);
     BEM_CUDA(h, cudaFuncSetAttribute(k_assemble_sn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     p.nT = (p.N + T - 1) / T;
     const unsigned grid = (unsigned)((int64_t)p.nT * (p.nT + 1) / 2);
     BEM_TIMED(h, "k_assemble", (k_assemble_sn<T><<<grid, 256, smem, h->stream>>>(p)));
     BEM_LAUNCH(h, "k_assemble");
+    if (p.kpart) {
+        BEM_TIMED(h, "k_sum_slots", (k_sum_slots<<<(unsigned)((p.N + 255) / 256), 256, 0, h->stream>>>(p.kpart, p.nT, p.N, h->k1)));
+        BEM_LAUNCH(h, "k_sum_slots");
+    }
     return BEM_OK;
 }
 
@@ -1170,7 +1207,17 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     p.near = near;
     p.rexpS = p.rexpW = nullptr;
     p.wband = -1;
+    p.kpart = nullptr;
     h->rexp_valid = false;
+    h->k1_valid = false;
+    if (!(ops & BEM_OP_D)) {
+        // N's row sums (exact: those of its k^2 term), per tile slot, for the filter's
+        // constant-vector correction
+        const int64_t nT = (h->N + 30) / 31;
+        if (!h->k1) BEM_CUDA(h, bem_dmalloc(h, (void**)&h->k1, sizeof(cplx) * (size_t)h->N));
+        if (!h->kpart) BEM_CUDA(h, bem_dmalloc(h, (void**)&h->kpart, sizeof(double2) * (size_t)nT * h->N));
+        p.kpart = h->kpart;
+    }
     if (!(ops & BEM_OP_D) && h->opt.prec == BEM_MIXED_BF16) {
         if (!h->rexp) BEM_CUDA(h, bem_dmalloc(h, (void**)&h->rexp, sizeof(int) * 2 * (size_t)h->N));
         BEM_CUDA(h, cudaMemsetAsync(h->rexp, 0, sizeof(int) * 2 * (size_t)h->N, h->stream));
@@ -1180,6 +1227,7 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     }
     st = (ops & BEM_OP_D) ? run_assemble<15, true>(h, p) : run_assemble_sn<31>(h, p);
     if (st == BEM_OK && p.rexpS) h->rexp_valid = true;
+    if (st == BEM_OK && p.kpart) h->k1_valid = true;
     bem_dfree_async(h, near);
     return st;
 }
