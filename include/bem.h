@@ -282,6 +282,27 @@ bem_status bem_shape_vjp(bem_handle h, const double* angles_dev, const void* amp
                          const double* obs_angles_dev, int64_t nobs, const void* x_dev, const void* gu_dev,
                          const void* lambda_dev, double* grad_dev);
 
+/* bem_rhs_scale -- right-hand sides of incident fields with complex amplitudes: out[:, w] =
+ * a_w v[:, w] for the N x nrhs block v (ldv >= N) and nrhs complex amplitudes a (device);
+ * out (ldo >= N) may be v itself (then ldo == ldv).  The paper states the incident field with
+ * unit amplitude; this is the forward map of the amplitude derivative below. */
+bem_status bem_rhs_scale(bem_handle h, const void* v_dev, int64_t ldv, int64_t nrhs, const void* amplitudes_dev,
+                         void* out_dev, int64_t ldo);
+
+/* bem_amplitude_grad -- gradient of a real misfit J with respect to the complex amplitudes a_w
+ * of the right-hand sides a_w v_w, given lambda = A^-H (dJ/dx) (solve_backward):
+ *     grad[w] = v[:, w]^H lambda[:, w]     (the dJ/dRe a + i dJ/dIm a convention)
+ * v, lambda: N x nrhs (ld >= N), device; grad: nrhs complex, device.  Fixed-order sums. */
+bem_status bem_amplitude_grad(bem_handle h, const void* v_dev, int64_t ldv, const void* lambda_dev, int64_t ldl,
+                              int64_t nrhs, void* grad_dev);
+
+/* bem_shape_chain -- chain rule from the vertex gradient to curve parameters p_c:
+ *     grad_coef[c] = sum_{i, d} tangent[c][i][d] grad_verts[i][d],  tangent[c][i][d] = d r_i,d / d p_c
+ * tangent: ncoef x N x 2 doubles (row-major, device; for equal-chord meshes the implicit
+ * derivative of the mesh), grad_verts: N x 2 (bem_shape_vjp), grad_coef: ncoef doubles. */
+bem_status bem_shape_chain(bem_handle h, const double* tangent_dev, int64_t ncoef, const double* grad_verts_dev,
+                           double* grad_coef_dev);
+
 /* Copies an internal matrix (BEM_MAT_*) into dst_dev with leading dimension ld (>= rows).
  * For BEM_MAT_SIGMA, dst_dev receives n doubles and ld is ignored. */
 bem_status bem_get_matrix(bem_handle h, int which, void* dst_dev, int64_t ld);

@@ -55,7 +55,7 @@ __all__ = [
     "farfield_constant", "farfield_matrix", "mie_farfield", "misfit_and_gradients",
     "chord_length", "gram_dft_eigs", "gram_power_rows", "gram_power_cols", "filtered_block",
     "compress_block", "filtered_condition", "filtered_solve_blocks", "assembled_column_blocks",
-    "segment_pair_means", "maue_second_difference",
+    "segment_pair_means", "maue_second_difference", "misfit_blocks",
 ]
 
 # --------------------------------------------------------------------------------------
@@ -873,6 +873,19 @@ def mie_farfield(k: float, a: float, theta, phi_inc: float, mmax: int | None = N
     for m in range(-mmax, mmax + 1):
         out += special.jvp(abs(m), ka) / special.h1vp(abs(m), ka) * np.exp(1j * m * (theta - phi_inc))
     return -math.sqrt(2.0 / (math.pi * k)) * np.exp(-0.25j * math.pi) * out
+
+
+def misfit_blocks(res: dict, F, amplitudes, target):
+    """Misfit J(a) = sum_{o,w} |u_ow - t_ow|^2 of the far fields u = F X, X_w = a_w x_w, with
+    x = A^-1 v the filtered solution of filtered_solve_blocks (compressed at its tolerance),
+    and its gradient in the amplitudes (dJ/dRe a + i dJ/dIm a):
+        grad_a_w = 2 (F x_w)^H r_w,   r = u - t."""
+    x0 = res["x"]
+    a = np.asarray(amplitudes, dtype=np.complex128)
+    Fx0 = F @ x0
+    u = Fx0 * a[None, :]
+    r = u - target
+    return dict(J=float(np.sum(np.abs(r) ** 2)), u=u, x0=x0, grad_a=2.0 * np.einsum("ow,ow->w", np.conj(Fx0), r))
 
 
 def misfit_and_gradients(route: dict, F, amplitudes, target):

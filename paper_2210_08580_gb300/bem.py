@@ -27,7 +27,7 @@ EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error",
            "bem_assemble", "filter_apply", "compress_compact", "factor", "bem_rhs_planewave",
            "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info", "bem_timing_enable",
            "bem_timing_report", "solve_many_noalloc", "bem_farfield", "bem_farfield_adjoint",
-           "bem_shape_vjp", "bem_rhs_pointsource")
+           "bem_shape_vjp", "bem_rhs_pointsource", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain")
 
 
 class BemOptions(ctypes.Structure):
@@ -127,12 +127,15 @@ def load_library(path: str = LIB_PATH):
     L.bem_farfield.argtypes = [vp, vp, i64, vp, i64, i64, vp, i64]
     L.bem_farfield_adjoint.argtypes = [vp, vp, i64, vp, i64, i64, vp, i64]
     L.bem_shape_vjp.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp, vp]
+    L.bem_rhs_scale.argtypes = [vp, vp, i64, i64, vp, vp, i64]
+    L.bem_amplitude_grad.argtypes = [vp, vp, i64, vp, i64, i64, vp]
+    L.bem_shape_chain.argtypes = [vp, vp, i64, vp, vp]
     L.bem_timing_enable.argtypes = [vp, i32]
     L.bem_timing_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     for name in ("bem_create", "bem_destroy", "bem_set_stream", "bem_assemble", "filter_apply",
                  "compress_compact", "factor", "bem_rhs_planewave", "bem_rhs_pointsource", "solve_many", "solve_backward",
                  "bem_get_matrix", "bem_get_info", "bem_timing_enable", "bem_timing_report", "bem_farfield",
-                 "bem_farfield_adjoint", "bem_shape_vjp"):
+                 "bem_farfield_adjoint", "bem_shape_vjp", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -297,6 +300,29 @@ class Solver:
                                          _ptr(lam.contiguous()), _ptr(grad)))
         return grad
 
+    def rhs_scale(self, v: torch.Tensor, amplitudes) -> torch.Tensor:
+        """a_w v_w for v (nrhs, N) and complex amplitudes (nrhs)."""
+        v = v.contiguous()
+        amp = torch.as_tensor(amplitudes, dtype=torch.complex128).to(self.device).contiguous()
+        out = torch.empty_like(v)
+        self._check(self.L.bem_rhs_scale(self.h, _ptr(v), self.N, v.shape[0], _ptr(amp), _ptr(out), self.N))
+        return out
+
+    def amplitude_grad(self, v: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
+        """v_w^H lambda_w per right-hand side (nrhs complex)."""
+        v, lam = v.contiguous(), lam.contiguous()
+        g = torch.empty(v.shape[0], dtype=torch.complex128, device=self.device)
+        self._check(self.L.bem_amplitude_grad(self.h, _ptr(v), self.N, _ptr(lam), self.N, v.shape[0], _ptr(g)))
+        return g
+
+    def shape_chain(self, tangent: torch.Tensor, grad_verts: torch.Tensor) -> torch.Tensor:
+        """sum_{i,d} tangent[c, i, d] grad_verts[i, d] for tangent (ncoef, N, 2)."""
+        t = tangent.to(device=self.device, dtype=torch.float64).contiguous()
+        gv = grad_verts.to(device=self.device, dtype=torch.float64).contiguous()
+        out = torch.empty(t.shape[0], dtype=torch.float64, device=self.device)
+        self._check(self.L.bem_shape_chain(self.h, _ptr(t), t.shape[0], _ptr(gv), _ptr(out)))
+        return out
+
     # ---------------------------------------------------------------- introspection
     def timing(self, enable: bool):
         self._check(self.L.bem_timing_enable(self.h, 1 if enable else 0))
@@ -367,20 +393,21 @@ class ShapeFarField(torch.autograd.Function):
     complex amplitudes ``amplitudes``; differentiable in the Fourier coefficients
     ``coef`` = (c_1..c_M, s_1..s_M) (float64) and in the amplitudes.
 
-    Forward: mesh (host), bem_assemble .. factor (FP64, filter n_modes, no truncation),
-    right-hand sides, solve_many, bem_farfield.  Backward (adjoint method): lambda =
-    solve_backward(bem_farfield_adjoint(gu)); d/dverts from bem_shape_vjp; chained to the
-    coefficients through the derivative of the equal-chord mesh (inputs.equal_chord_tangent);
-    the amplitude gradient is sum_i conj(v0_iw) lambda_iw."""
+    Forward: mesh (host), bem_assemble .. factor (filter n_modes, no truncation), right-hand
+    sides, bem_rhs_scale, solve_many, bem_farfield, on the FP64 or the mixed path (``prec``).
+    Backward (adjoint method): lambda = solve_backward(bem_farfield_adjoint(gu)); the amplitude
+    gradient from bem_amplitude_grad, d/dverts from bem_shape_vjp, chained to the coefficients
+    by bem_shape_chain through the derivative of the equal-chord mesh
+    (inputs.equal_chord_tangent)."""
 
     @staticmethod
-    def forward(ctx, coef, amplitudes, r0, N, k, n_modes, angles, obs_angles, device=0):
+    def forward(ctx, coef, amplitudes, r0, N, k, n_modes, angles, obs_angles, device=0, prec="fp64"):
         from . import inputs
         c = coef.detach().cpu().numpy()
         M = c.shape[0] // 2
         curve = inputs.PolarCurve(r0=float(r0), cos_coef=tuple(c[:M]), sin_coef=tuple(c[M:]))
         verts, theta, h = inputs.equal_chord_mesh(curve, int(N))
-        s = Solver(device=device, prec="fp64")
+        s = Solver(device=device, prec=prec)
         dev = s.device
         s.assemble(torch.from_numpy(verts).to(dev), float(k), ops="SW")
         s.filter_apply(int(n_modes))
@@ -390,7 +417,7 @@ class ShapeFarField(torch.autograd.Function):
         obs = torch.as_tensor(obs_angles, dtype=torch.float64).to(dev)
         amp = amplitudes.detach().to(dev, torch.complex128)
         v0 = s.rhs_planewave(ang)
-        x = s.solve(amp[:, None] * v0)
+        x = s.solve(s.rhs_scale(v0, amp))
         u = s.farfield(obs, x)
         ctx.s, ctx.ang, ctx.obs, ctx.amp, ctx.v0, ctx.x = s, ang, obs, amp, v0, x
         ctx.tangent = torch.from_numpy(inputs.equal_chord_tangent(curve, theta, h))
@@ -402,13 +429,13 @@ class ShapeFarField(torch.autograd.Function):
         s = ctx.s
         gu = gu.contiguous()
         lam = s.solve_backward(s.farfield_adjoint(ctx.obs, gu))
-        grad_a = (ctx.v0.conj() * lam).sum(dim=1)
+        grad_a = s.amplitude_grad(ctx.v0, lam)
         gv = s.shape_vjp(ctx.ang, ctx.amp, ctx.obs, ctx.x, gu, lam)
-        grad_c = torch.einsum("pnd,nd->p", ctx.tangent, gv.cpu()).to(ctx.coef_device)
+        grad_c = s.shape_chain(ctx.tangent, gv).to(ctx.coef_device)
         s.close()
-        return grad_c, grad_a, None, None, None, None, None, None, None
+        return grad_c, grad_a, None, None, None, None, None, None, None, None
 
 
-def shape_farfield(coef, amplitudes, r0, N, k, n_modes, angles, obs_angles, device=0):
+def shape_farfield(coef, amplitudes, r0, N, k, n_modes, angles, obs_angles, device=0, prec="fp64"):
     """Differentiable far field of a Fourier star (see ShapeFarField)."""
-    return ShapeFarField.apply(coef, amplitudes, r0, N, k, n_modes, angles, obs_angles, device)
+    return ShapeFarField.apply(coef, amplitudes, r0, N, k, n_modes, angles, obs_angles, device, prec)

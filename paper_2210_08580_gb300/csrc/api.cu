@@ -191,6 +191,7 @@ static void free_stage_buffers(bem_ctx* h, int from_stage) {
     if (from_stage > 1) return;
     free_ptr(h, (void**)&h->S); free_ptr(h, (void**)&h->W); free_ptr(h, (void**)&h->D);
     free_ptr(h, (void**)&h->rexp); h->rexp_valid = false;
+    free_ptr(h, (void**)&h->k1); free_ptr(h, (void**)&h->kpart); h->k1_valid = false;
     free_ptr(h, (void**)&h->seg);
     tc_release_operands(h);
     free_ptr(h, (void**)&h->B); free_ptr(h, (void**)&h->gm); free_ptr(h, (void**)&h->Q);
@@ -316,8 +317,9 @@ bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha) {
     if ((st = apply_gram_inverse(h, 0, Y1, Y1, tmp, N, nc, nc, 1, h->hbar, false)) != BEM_OK) return st;
     if (h->opt.prec == BEM_MIXED_BF16) {
         if ((st = tc_product_left(h, TC_OP_W, nullptr, Y1, nc, h->B)) != BEM_OK) return st;
-        // the split product's action on the constant vector, from N's FP64 row sums
-        if ((st = launch_const_correction(h, h->W, Y1, h->B, nc, N, cfix)) != BEM_OK) return st;
+        // the product's action on the constant vector, from N's row sums
+        if ((st = launch_const_correction(h, h->W, h->k1_valid ? h->k1 : nullptr, Y1, h->B, nc, N, cfix)) != BEM_OK)
+            return st;
         if (alpha != 0.0) {
             if ((st = tc_product_left(h, TC_OP_D, h->Q, nullptr, nc, tmp)) != BEM_OK) return st;
             if ((st = launch_axpby(h, h->B, nc, tmp, nc, cmk(-alpha, 0), cmk(1, 0), nc, N)) != BEM_OK) return st;
@@ -326,6 +328,10 @@ bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha) {
         // B = Y2 N  (- alpha Q^T D)
         h->tag = "gemm_filter_YN";
         if ((st = zgemm(h, OP_N, OP_N, nc, N, N, cmk(1, 0), Y1, nc, h->W, N, cmk(0, 0), h->B, nc)) != BEM_OK) return st;
+        // the product's action on the constant vector from N's exact row sums (the stored
+        // entries' rounding moves them by up to 2^-53 sum_j |N_ij|, O(k^-2) of them at low k)
+        if (h->k1_valid)
+            if ((st = launch_const_correction(h, h->W, h->k1, Y1, h->B, nc, N, cfix)) != BEM_OK) return st;
         h->tag = "gemm_filter_QtD";
         if (alpha != 0.0)
             if ((st = dzgemm_realA(h, OP_T, nc, N, N, -alpha, h->Q, N, h->D, N, 1.0, h->B, nc)) != BEM_OK) return st;
@@ -804,6 +810,43 @@ bem_status bem_shape_vjp(bem_handle h, const double* angles, const void* amplitu
     // the host copies above read hp/hs from this frame: finish before returning
     BEM_CUDA(h, cudaStreamSynchronize(h->stream));
     return check_dev_err(h);
+}
+
+bem_status bem_rhs_scale(bem_handle h, const void* v_dev, int64_t ldv, int64_t nrhs, const void* amplitudes_dev,
+                         void* out_dev, int64_t ldo) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 1) return bem_fail(h, BEM_E_INVALID, "bem_rhs_scale: call bem_assemble first");
+    if (!v_dev || !amplitudes_dev || !out_dev || nrhs < 1 || ldv < h->N || ldo < h->N)
+        return bem_fail(h, BEM_E_INVALID, "bem_rhs_scale: need v, amplitudes, out, nrhs >= 1, ld >= N");
+    if (out_dev == v_dev && ldo != ldv) return bem_fail(h, BEM_E_INVALID, "bem_rhs_scale: in place needs ldo == ldv");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    bem_status st;
+    if (out_dev != v_dev)
+        if ((st = launch_copy2d(h, out_dev, ldo, v_dev, ldv, h->N, nrhs, sizeof(cplx))) != BEM_OK) return st;
+    return launch_scale_cols(h, (cplx*)out_dev, ldo, (const cplx*)amplitudes_dev, h->N, nrhs);
+}
+
+bem_status bem_amplitude_grad(bem_handle h, const void* v_dev, int64_t ldv, const void* lambda_dev, int64_t ldl,
+                              int64_t nrhs, void* grad_dev) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 1) return bem_fail(h, BEM_E_INVALID, "bem_amplitude_grad: call bem_assemble first");
+    if (!v_dev || !lambda_dev || !grad_dev || nrhs < 1 || ldv < h->N || ldl < h->N)
+        return bem_fail(h, BEM_E_INVALID, "bem_amplitude_grad: need v, lambda, grad, nrhs >= 1, ld >= N");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    return launch_col_cdot(h, (const cplx*)v_dev, ldv, (const cplx*)lambda_dev, ldl, h->N, nrhs, (cplx*)grad_dev);
+}
+
+bem_status bem_shape_chain(bem_handle h, const double* tangent_dev, int64_t ncoef, const double* grad_verts_dev,
+                           double* grad_coef_dev) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 1) return bem_fail(h, BEM_E_INVALID, "bem_shape_chain: call bem_assemble first");
+    if (!tangent_dev || !grad_verts_dev || !grad_coef_dev || ncoef < 1 || ncoef > 65535)
+        return bem_fail(h, BEM_E_INVALID, "bem_shape_chain: need tangent, gradients, 1 <= ncoef <= 65535");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    return launch_row_dot(h, tangent_dev, ncoef, 2 * h->N, grad_verts_dev, grad_coef_dev);
 }
 
 bem_status bem_get_info(bem_handle h, bem_info* info) {

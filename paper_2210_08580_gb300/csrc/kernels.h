@@ -70,8 +70,14 @@ bem_status launch_scale_cols(bem_ctx* h, cplx* x, int64_t ldx, const cplx* s, in
 bem_status launch_shift(bem_ctx* h, const double* in, double* out, int64_t n, double shift);
 bem_status launch_conj_scale(bem_ctx* h, const cplx* x, int64_t ldx, cplx* y, int64_t ldy, cplx a, int64_t rows,
                              int64_t cols);   // y = a conj(x)
-// P <- P + (Y (W 1) - P 1) 1^T / N for the n x N product P = Y W (ld = nc); scratch: N + nc
-bem_status launch_const_correction(bem_ctx* h, const cplx* Wm, const cplx* Y, cplx* P, int64_t nc, int64_t N,
-                                   cplx* scratch);
+// P <- P + (Y w - P 1) 1^T / N for the n x N product P = Y W (ld = nc), w = W 1 given (w1) or
+// summed from W; scratch: N + nc
+bem_status launch_const_correction(bem_ctx* h, const cplx* Wm, const cplx* w1, const cplx* Y, cplx* P, int64_t nc,
+                                   int64_t N, cplx* scratch);
+// g[w] = v[:, w]^H lam[:, w]
+bem_status launch_col_cdot(bem_ctx* h, const cplx* v, int64_t ldv, const cplx* lam, int64_t ldl, int64_t rows,
+                           int64_t cols, cplx* g);
+// out = T x for T: P x n row-major (FP64)
+bem_status launch_row_dot(bem_ctx* h, const double* T, int64_t P, int64_t n, const double* x, double* out);
 bem_status launch_copy2d(bem_ctx* h, void* dst, int64_t ldd, const void* src, int64_t lds,
                          int64_t rows, int64_t cols, size_t elem);

@@ -1558,13 +1558,14 @@ bem_status launch_copy2d(bem_ctx* h, void* dst, int64_t ldd, const void* src, in
 }
 
 // =========================================================================================
-// Constant-vector correction of the filtered product (mixed path).  N's row sums are O(k^2)
-// of its entries (Maue's form: the derivative term's row sums vanish), so at low k the
-// split products lose B's action on the constant vector 1 to their rounding, which is
-// relative to the entries, while that action carries the Calderon product's smallest
-// eigenvalue.  With w = N 1 summed in FP64 from the assembled N, the n x N product P = Y N
-// is corrected along 1 only:  P <- P + (Y w - P 1) 1^T / N  (P's action on the
-// complement of 1 is unchanged).
+// Constant-vector correction of the filtered product.  N's row sums are O(k^2) of its
+// entries (Maue's form: the derivative term's row sums vanish), so at low k the product
+// P = Y N loses B's action on the constant vector 1 to rounding -- that of the split
+// products, relative to the entries, and that of N's stored entries, up to
+// 2^-53 sum_j |N_ij| per row -- while that action carries the Calderon product's smallest
+// eigenvalue.  With w = N 1 (the exact row sums the assembly accumulates from N's k^2
+// term, or else summed in FP64 from the stored N) the product is corrected along 1 only:
+//     P <- P + (Y w - P 1) 1^T / N      (P's action on the complement of 1 is unchanged).
 // =========================================================================================
 __device__ __forceinline__ cplx block_csum(cplx v, double* red) {
     return cmk(block_sum(v.x, red), block_sum(v.y, red));
@@ -1603,15 +1604,55 @@ __global__ void k_add_row_const(cplx* P, int64_t ld, int64_t rows, int64_t N, co
     P[i + j * ld] = cadd(P[i + j * ld], c[i]);
 }
 
-bem_status launch_const_correction(bem_ctx* h, const cplx* Wm, const cplx* Y, cplx* P, int64_t nc, int64_t N,
-                                   cplx* scratch) {
+bem_status launch_const_correction(bem_ctx* h, const cplx* Wm, const cplx* w1, const cplx* Y, cplx* P, int64_t nc,
+                                   int64_t N, cplx* scratch) {
     cplx* w = scratch;              // N
     cplx* c = scratch + N;          // nc
-    BEM_TIMED(h, "k_col_sums", (k_col_sums<<<(unsigned)N, 256, 0, h->stream>>>(Wm, N, N, w)));
-    BEM_LAUNCH(h, "k_col_sums");
+    if (w1) {
+        w = const_cast<cplx*>(w1);
+    } else {
+        BEM_TIMED(h, "k_col_sums", (k_col_sums<<<(unsigned)N, 256, 0, h->stream>>>(Wm, N, N, w)));
+        BEM_LAUNCH(h, "k_col_sums");
+    }
     BEM_TIMED(h, "k_const_defect", (k_const_defect<<<(unsigned)nc, 256, 0, h->stream>>>(Y, P, nc, N, w, c)));
     BEM_LAUNCH(h, "k_const_defect");
     BEM_TIMED(h, "k_add_row_const", (k_add_row_const<<<(unsigned)((nc * N + 255) / 256), 256, 0, h->stream>>>(P, nc, nc, N, c)));
     BEM_LAUNCH(h, "k_add_row_const");
+    return BEM_OK;
+}
+
+// =========================================================================================
+// Differentiation helpers: amplitude gradient and the chain to curve coefficients
+// =========================================================================================
+// g[w] = sum_i conj(v[i + w ldv]) lam[i + w ldl], one CTA per column (fixed-order reduction)
+__global__ void __launch_bounds__(256) k_col_cdot(const cplx* __restrict__ v, int64_t ldv, const cplx* __restrict__ lam,
+                                                  int64_t ldl, int64_t rows, cplx* g) {
+    __shared__ double red[32];
+    const int64_t w = blockIdx.x;
+    cplx acc = cmk(0, 0);
+    for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) acc = cadd(acc, cmul(cconj(v[i + w * ldv]), lam[i + w * ldl]));
+    acc = block_csum(acc, red);
+    if (threadIdx.x == 0) g[w] = acc;
+}
+bem_status launch_col_cdot(bem_ctx* h, const cplx* v, int64_t ldv, const cplx* lam, int64_t ldl, int64_t rows,
+                           int64_t cols, cplx* g) {
+    BEM_TIMED(h, "k_col_cdot", (k_col_cdot<<<(unsigned)cols, 256, 0, h->stream>>>(v, ldv, lam, ldl, rows, g)));
+    BEM_LAUNCH(h, "k_col_cdot");
+    return BEM_OK;
+}
+
+// out[p] = sum_j T[p n + j] x[j] (T: P x n row-major, one CTA per p)
+__global__ void __launch_bounds__(256) k_row_dot(const double* __restrict__ T, int64_t n, const double* __restrict__ x,
+                                                 double* out) {
+    __shared__ double red[32];
+    const int64_t p = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) acc += T[p * n + j] * x[j];
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) out[p] = acc;
+}
+bem_status launch_row_dot(bem_ctx* h, const double* T, int64_t P, int64_t n, const double* x, double* out) {
+    BEM_TIMED(h, "k_row_dot", (k_row_dot<<<(unsigned)P, 256, 0, h->stream>>>(T, n, x, out)));
+    BEM_LAUNCH(h, "k_row_dot");
     return BEM_OK;
 }

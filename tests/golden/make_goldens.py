@@ -13,15 +13,19 @@ stores, in ``tests/golden/<name>.npz``:
   xnorm_G         G-norm of each full solution column
   sigma, rank     singular values of the filtered compact part, rank at the tolerance
   kappa           condition number of the filtered operator (orthonormal basis)
+  c_rowsum        max_i sum_j |N_ij| / |sum_j N_ij|: how much the rounding of N's entries to
+                  FP64 (relative 2^-53 each) can move the row sums N 1, which at low k are
+                  O(k^2) of the entries and carry the constant mode's eigenvalue
 
 and a summary with the oracle's wall time per phase and the host's core count in
 ``tests/golden/oracle_runs.json``.
 
 Configurations: star r = 1 + 0.3 cos 5t, N = 4096, k in {1e-3, 1e-2, 1e-1, 1, 5}, n = 201,
 tol 1e-10 (256 plane waves); random 8-harmonic star of seed 0, N = 16384, k = 2, n = 201,
-tol 1e-10 (1024 plane waves).
+tol 1e-10 (1024 plane waves); a subsample of the uneven batch (run_c4); and, for the
+differentiation layer, the C5 misfit (run_c5).
 
-    python tests/golden/make_goldens.py [--workers W] [--only c2|c3]
+    python tests/golden/make_goldens.py [--workers W] [--only c2|c3|c4|c5]
 """
 from __future__ import annotations
 
@@ -70,20 +74,99 @@ def run(cfg, workers):
     res = O.filtered_solve_blocks(mats, verts, f, cfg["M"], cfg["tol"])
     t["block_route"] = time.perf_counter() - t0
     G_norm = np.sqrt(np.real(np.sum(np.conj(res["x"]) * O.gram_power_cols(res["x"], res["h"], 1.0), axis=0)))
+    c_rowsum = float(np.max(np.abs(mats["W"]).sum(axis=1) / np.abs(mats["W"].sum(axis=1))))
     np.savez(os.path.join(HERE, cfg["name"] + ".npz"), rows=rows, angles=angles, x=res["x"][rows],
              x_full=res["x_full"][rows], vx=res["vx"][rows], xnorm_G=G_norm, sigma=res["sigma"],
-             rank=np.int64(res["rank"]), kappa=np.float64(res["kappa"]), N=np.int64(N), k=np.float64(cfg["k"]),
+             rank=np.int64(res["rank"]), kappa=np.float64(res["kappa"]), c_rowsum=np.float64(c_rowsum),
+             N=np.int64(N), k=np.float64(cfg["k"]),
              M=np.int64(cfg["M"]), tol=np.float64(cfg["tol"]))
     xr = res["x"]
     comp_err = float(np.max(np.abs(xr - res["x_full"])) / np.max(np.abs(res["x_full"])))
     return dict(name=cfg["name"], N=N, k=cfg["k"], n=2 * cfg["M"] + 1, tol=cfg["tol"], rank=res["rank"],
-                kappa=res["kappa"], compressed_vs_uncompressed=comp_err, seconds=t)
+                kappa=res["kappa"], c_rowsum=c_rowsum, compressed_vs_uncompressed=comp_err, seconds=t)
+
+
+C5_N, C5_K, C5_M, C5_NRHS, C5_NOBS = 8192, 1.0, 100, 128, 360
+C5_COEFS = (0, 3, 8, 13)          # cos 1, cos 4, sin 1, sin 6: the coefficients differenced
+C5_H = 1e-6
+
+
+def c5_curve(coef):
+    from paper_2210_08580_gb300 import inputs as I
+    m = len(coef) // 2
+    return I.PolarCurve(r0=1.0, cos_coef=tuple(coef[:m]), sin_coef=tuple(coef[m:]))
+
+
+def c5_misfit(coef, target, workers):
+    """J, grad_a and the far fields of the C5 star with coefficients coef (unit amplitudes)."""
+    from oracle import bem_oracle as O
+    from paper_2210_08580_gb300 import inputs as I
+    verts, _, _ = I.equal_chord_mesh(c5_curve(coef), C5_N)
+    ang = I.planewave_angles(C5_NRHS)
+    obs = 2.0 * np.pi * np.arange(C5_NOBS) / C5_NOBS
+    mats = O.assemble(verts, C5_K, "SW", workers=workers)
+    res = O.filtered_solve_blocks(mats, verts, O.rhs_planewave(verts, C5_K, ang), C5_M, 0.0)
+    F = O.farfield_matrix(verts, C5_K, obs)
+    if target is None:
+        return F @ res["x"]
+    return O.misfit_blocks(res, F, np.ones(C5_NRHS), target)
+
+
+def run_c5(workers):
+    """C5 (differentiation): random Fourier star of seed 200 (16 coefficients), N = 8192, k = 1,
+    n = 201 (no truncation), 128 plane waves, 360 observation angles; target = the far field of
+    the seed-201 star.  Stores the target, the misfit and its amplitude gradient at unit
+    amplitudes, and central differences (h = 1e-6) of the misfit in 4 coefficients."""
+    from paper_2210_08580_gb300 import inputs as I
+    t0 = time.perf_counter()
+    c0 = np.concatenate(I.fourier_star_seeded(200))
+    target = c5_misfit(np.concatenate(I.fourier_star_seeded(201)), None, workers)
+    base = c5_misfit(c0, target, workers)
+    fd = []
+    for p in C5_COEFS:
+        e = np.zeros_like(c0)
+        e[p] = C5_H
+        fd.append((c5_misfit(c0 + e, target, workers)["J"] - c5_misfit(c0 - e, target, workers)["J"]) / (2 * C5_H))
+    np.savez(os.path.join(HERE, "c5_fourier_star200_n8192.npz"), coef=c0, target=target, J=np.float64(base["J"]),
+             grad_a=base["grad_a"], coefs_fd=np.array(C5_COEFS), fd=np.array(fd), h=np.float64(C5_H),
+             N=np.int64(C5_N), k=np.float64(C5_K), M=np.int64(C5_M))
+    return dict(name="c5_fourier_star200_n8192", N=C5_N, k=C5_K, J=base["J"], fd=fd,
+                seconds={"total": time.perf_counter() - t0})
+
+
+C4_COUNT, C4_NHI = 8, 2048
+
+
+def run_c4(workers):
+    """C4 subsample within the oracle's reach: the first 8 problems of the uneven batch law
+    (random stars of seeds 100.., k = 10^U(-2, log10 5), 64..512 plane waves) with
+    N ~ U{512..2048}; n = min(201, 2 floor(N/8) + 1), tol 1e-10.  Per problem: the solution
+    at 64 seeded rows for every (nrhs // 8)-th plane wave, sigma, rank, kappa."""
+    from oracle import bem_oracle as O
+    from paper_2210_08580_gb300 import inputs as I
+    t0 = time.perf_counter()
+    out = {}
+    for i, spec in enumerate(I.batch_problems(count=C4_COUNT, first_seed=100, n_hi=C4_NHI)):
+        verts, _, _ = I.equal_chord_mesh(spec.curve, spec.N)
+        M = min(201, 2 * (spec.N // 8) + 1) // 2
+        w = np.arange(0, spec.nrhs, spec.nrhs // 8)
+        angles = I.planewave_angles(spec.nrhs)[w]
+        rows = np.sort(np.random.default_rng(777 + i).choice(spec.N, 64, replace=False))
+        mats = O.assemble(verts, spec.k, "SW", workers=workers)
+        res = O.filtered_solve_blocks(mats, verts, O.rhs_planewave(verts, spec.k, angles), M, 1e-10)
+        out.update({f"p{i}_cols": w, f"p{i}_rows": rows, f"p{i}_x": res["x"][rows], f"p{i}_x_full": res["x_full"][rows],
+                    f"p{i}_sigma": res["sigma"], f"p{i}_rank": np.int64(res["rank"]),
+                    f"p{i}_kappa": np.float64(res["kappa"]), f"p{i}_N": np.int64(spec.N)})
+    np.savez(os.path.join(HERE, "c4_batch_subsample.npz"), count=np.int64(C4_COUNT), **out)
+    return dict(name="c4_batch_subsample", count=C4_COUNT, seconds={"total": time.perf_counter() - t0},
+                N=[int(out[f"p{i}_N"]) for i in range(C4_COUNT)],
+                kappa=[float(out[f"p{i}_kappa"]) for i in range(C4_COUNT)])
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workers", type=int, default=os.cpu_count() or 1)
-    ap.add_argument("--only", default="", choices=["", "c2", "c3"])
+    ap.add_argument("--only", default="", choices=["", "c2", "c3", "c4", "c5"])
     args = ap.parse_args()
     summ_path = os.path.join(HERE, "oracle_runs.json")
     summary = {}
@@ -91,11 +174,18 @@ def main():
         with open(summ_path) as fh:
             summary = json.load(fh)
     runs = summary.get("runs", {})
-    for cfg in configs():
-        if args.only and not cfg["name"].startswith(args.only):
-            continue
-        r = run(cfg, args.workers)
-        runs[cfg["name"]] = r
+    todo = [c for c in configs() if not args.only or c["name"].startswith(args.only)]
+    for extra in ("c4", "c5"):
+        if not args.only or args.only == extra:
+            todo.append(extra)
+    for cfg in todo:
+        if cfg == "c4":
+            r = run_c4(args.workers)
+        elif cfg == "c5":
+            r = run_c5(args.workers)
+        else:
+            r = run(cfg, args.workers)
+        runs[r["name"]] = r
         print(json.dumps(r), flush=True)
         summary = {"host_cores": os.cpu_count(), "workers": args.workers,
                    "command": "python tests/golden/make_goldens.py --workers %d" % args.workers,

@@ -88,3 +88,41 @@ def test_solver_is_deterministic(B, problems, prec):
     x1, _ = _single(bem, p, prec)
     x2, _ = _single(bem, p, prec)
     assert torch.equal(x1, x2)
+
+
+def _c4():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c4_batch_subsample.npz")
+    with np.load(path) as z:
+        return {key: z[key] for key in z.files}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_subsample_against_the_oracle(B, prec):
+    """C4 within the oracle's reach: the first 8 problems of the uneven batch law with
+    N ~ U{512..2048} (random stars, k = 10^U(-2, log10 5), 64..512 plane waves each), solved
+    together by the batching layer; every problem's rank, singular values and solution
+    (64 rows x every nrhs/8-th wave) against the oracle: FP64 <= 1e-10 (1e-13 kappa above
+    kappa = 1e3), mixed <= 1e-8 (1e-11 kappa), ranks equal up to one."""
+    bem, batch = B
+    g = _c4()
+    problems = batch.problems_from_inputs(I.batch_problems(count=int(g["count"]), first_seed=100, n_hi=2048))
+    bs = batch.BatchSolver(problems, prec=prec, n_streams=4, refine_rtol=1e-8)
+    res = bs.run()
+    for i, out in enumerate(res):
+        kappa = float(g[f"p{i}_kappa"])
+        if prec == "fp64":
+            tol = 1e-10 if kappa <= 1e3 else 1e-13 * kappa
+        else:
+            tol = 1e-8 if kappa <= 1e3 else 1e-11 * kappa
+        x = out["x"].cpu().numpy().T[g[f"p{i}_rows"]][:, g[f"p{i}_cols"]]
+        r, r0 = out["rank"], int(g[f"p{i}_rank"])
+        ref = g[f"p{i}_x"] if r == r0 else g[f"p{i}_x_full"]
+        if r != r0:
+            tol = max(tol, 1e-9 * kappa)
+        err = float(np.max(np.abs(x - ref)) / np.max(np.abs(ref)))
+        print(f"batch {prec} problem {i}: N={problems[i].verts.shape[0]} k={problems[i].k:.3g} kappa={kappa:.3g} "
+              f"rank {r}/{r0} x err {err:.2e} (tol {tol:.1e})")
+        assert abs(r - r0) <= 1
+        assert err <= tol, (i, err, tol)
+    bs.close()
