@@ -43,7 +43,7 @@ FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 ASM_OPS_PER_POINT = 270
 # DRAM bytes (read + write) per launch from ncu captures of the kernels as they stand
 # (absent = not captured since the kernel last changed); the summaries are under profiles/
-TRAFFIC_BYTES = {"tc_rhs_SY": 14.704e9 + 0.275e9, "k_assemble": 0.0319e9 + 8.548e9}
+TRAFFIC_BYTES = {"tc_rhs_SY": 14.704e9 + 0.275e9}
 
 
 def _peaks():
@@ -52,6 +52,30 @@ def _peaks():
             return json.load(fh)
     except Exception:
         return {}
+
+
+# GB300 FP64 pipe: 2 DFMA per SM per clock (4 FP64 flops), 152 SMs, 2070 MHz -> 1.26 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+
+# The method's own arithmetic per launch of the split-bf16 products, counted as the complex
+# FP64 products they stand for (a complex multiply-add = 8 real flops, real x complex = 4):
+#   tc_rhs_SY      v = S Y          8 N^2 nrhs
+#   tc_filter_YN   B = Y2 N         8 n N^2
+#   tc_filter_QtS  Y1 = Q^T S       4 n N^2   (Q real)
+METHOD_DIMS = {"tc_rhs_SY": ("N", "nrhs", "N", 8.0), "tc_filter_YN": ("n", "N", "N", 8.0),
+               "tc_filter_QtS": ("n", "N", "N", 4.0)}
+
+
+def _dims(args, n_modes):
+    return {"N": args.N, "nrhs": args.nrhs, "n": n_modes}
+
+
+def method_flops(name, args, n_modes):
+    if name not in METHOD_DIMS:
+        return None
+    a, b, c, f = METHOD_DIMS[name]
+    d = _dims(args, n_modes)
+    return f * d[a] * d[b] * d[c]
 
 
 def tc_gemm_flops(name, N, nrhs, n_modes, r, S):
@@ -68,28 +92,48 @@ def tc_gemm_flops(name, N, nrhs, n_modes, r, S):
     return S * (S + 1) / 2 * 2.0 * parts * M * Nc * K
 
 
-def roofline(rep, args, n_modes, r, quad_points):
-    dom_name, (dom_cnt, dom_ms) = max(rep.items(), key=lambda kv: kv[1][1])
-    avg_s = dom_ms / dom_cnt / 1000.0
+def kernel_roofline(name, cnt, ms, args, n_modes, r, quad_points):
+    """Roofline entry of one kernel (average launch of the timed region)."""
+    avg_s = ms / cnt / 1000.0
     pk = _peaks()
-    if dom_name == "k_assemble":
+    if name == "k_assemble":
         ach = quad_points * ASM_OPS_PER_POINT / avg_s / 1e12
-        return {"kernel": dom_name, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TOPS,
-                "unit": "TOP/s (FP32 pipe)", "frac": ach / FP32_PEAK_TOPS, "traffic": TRAFFIC_BYTES.get(dom_name),
-                "units_per_launch": quad_points, "ops_per_unit": ASM_OPS_PER_POINT,
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TOPS,
+                "unit": "TOP/s (FP32 pipe)", "frac": ach / FP32_PEAK_TOPS, "traffic": TRAFFIC_BYTES.get(name),
+                "ms_per_launch": 1000 * avg_s, "units_per_launch": quad_points, "ops_per_unit": ASM_OPS_PER_POINT,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
+    fl = method_flops(name, args, n_modes)
+    if fl is None:
+        return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "ms_per_launch": 1000 * avg_s}
     # digit slices per operand: 6, the right-hand-side product 5 (bem_options.rhs_slices default)
-    S = 5 if dom_name == "tc_rhs_SY" else 6
-    fl = tc_gemm_flops(dom_name, args.N, args.nrhs, n_modes, r, S)
-    if fl is not None:
-        peak = pk.get("bf16_tflops_sustained", 1700.0)
-        ach = fl / avg_s / 1e12
-        return {"kernel": dom_name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": TRAFFIC_BYTES.get(dom_name), "slice_pairs": S * (S + 1) // 2,
-                "peak_source": "of measured (bf16_tflops_sustained)" if "bf16_tflops_sustained" in pk
-                else "of fallback (1.7 PFLOP/s sustained)"}
-    return {"kernel": dom_name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-            "traffic": None}
+    S = 5 if name == "tc_rhs_SY" else 6
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    src = ("of measured (bf16_tflops_sustained)" if "bf16_tflops_sustained" in pk
+           else "of fallback (1.7 PFLOP/s sustained)")
+    ach = fl / avg_s / 1e12
+    emu = tc_gemm_flops(name, args.N, args.nrhs, n_modes, r, S)
+    return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": TRAFFIC_BYTES.get(name), "ms_per_launch": 1000 * avg_s, "peak_source": src,
+            "work": "the method's complex FP64 product (%s), FP64-equivalent flops" % name,
+            "method_flops_per_launch": fl,
+            "vs_fp64_pipe": {"peak": FP64_PEAK_TFLOPS, "frac": ach / FP64_PEAK_TFLOPS,
+                             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"},
+            "emulation": {"slice_pairs": S * (S + 1) // 2, "bf16_flops_per_launch": emu,
+                          "achieved": emu / avg_s / 1e12, "frac": emu / avg_s / 1e12 / peak,
+                          "note": "tensor-pipe occupancy by the split-bf16 digit products (emulation work)"}}
+
+
+def roofline(rep, args, n_modes, r, quad_points, top=3):
+    """(dominant kernel's roofline, the top kernels' rooflines by time per step)."""
+    order = sorted(rep.items(), key=lambda kv: -kv[1][1])
+    rows = [kernel_roofline(nm, c, ms, args, n_modes, r, quad_points) for nm, (c, ms) in order[:top]]
+    # the filter's two products are one step (a4): report Q^T S beside Y2 N when present
+    names = [x["kernel"] for x in rows]
+    if "tc_filter_YN" in names and "tc_filter_QtS" in rep and "tc_filter_QtS" not in names:
+        c, ms = rep["tc_filter_QtS"]
+        rows.append(kernel_roofline("tc_filter_QtS", c, ms, args, n_modes, r, quad_points))
+    return rows[0], rows
 
 
 def parse():
@@ -108,6 +152,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare-fp64", action="store_true",
                     help="skip timing the FP64 path beside the mixed path")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 path (median)")
+    ap.add_argument("--fp64-warmup", type=int, default=2)
     ap.add_argument("--workload", default="single", choices=["single", "batch"],
                     help="single: one N=16384 star (the headline metric); batch: many uneven stars at once")
     ap.add_argument("--batch-count", type=int, default=64)
@@ -164,29 +210,82 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(N_s: int, nrhs_s: int, k: float, M: int, tol: float, seed: int = 0) -> dict:
-    """Times the CPU oracle on a smaller instance of the same workload and scales each phase
-    to the full size by its cost: assembly ~ N^2, right-hand sides ~ N nrhs, dense solve
-    route ~ N^3 (+ N^2 nrhs)."""
+def oracle_measured(N: int, nrhs: int, k: float, M: int, tol: float, seed: int = 0, cols: int = 256,
+                    rhs_sample: int = 64, fit_sizes=(1024, 2048), workers: int | None = None) -> dict:
+    """The CPU oracle (block route of oracle/bem_oracle.py) timed on the workload, bounded:
+
+    assembly   measured at the full N on the same curve: the oracle's column-block assembly
+               of ``cols`` evenly spaced segment columns (each holds N segment pairs) on all
+               host cores, scaled by N / cols;
+    RHS f      measured at the full N: ``rhs_sample`` of the nrhs plane waves, scaled by
+               nrhs / rhs_sample;
+    the rest   the block route after the assembly (G^-1 S G^-1 f for all nrhs, filter block,
+               compression, Woodbury solve of all nrhs) timed end to end at two smaller N of
+               the same curve family and extrapolated as c N^p with p fitted from the two.
+    Returns the per-phase seconds (measured and estimated) and the estimate of one full step."""
+    import multiprocessing as mp
+
     from oracle import bem_oracle as O
     from paper_2210_08580_gb300 import inputs as I
-    v, _, _ = I.equal_chord_mesh(I.random_star(seed), N_s)
-    ang = I.planewave_angles(nrhs_s)
-    t0 = time.perf_counter()
-    mats = O.assemble(v, k, "SW")
-    t1 = time.perf_counter()
-    f = O.rhs_planewave(v, k, ang)
-    t2 = time.perf_counter()
-    O.filtered_solve_projected(mats, v, f, min(M, (N_s - 2) // 2), tol)
-    t3 = time.perf_counter()
-    return {"N": N_s, "nrhs": nrhs_s, "t_assemble": t1 - t0, "t_rhs": t2 - t1, "t_dense": t3 - t2}
+    workers = workers or cpu_cores()
+    curve = I.random_star(seed)
+    verts, _, _ = I.equal_chord_mesh(curve, N)
+    out = {"N": N, "nrhs": nrhs, "workers": workers}
+    block = 8
+    starts = np.linspace(0, N - block, cols // block).astype(int)
+    with mp.get_context("spawn").Pool(workers) as pool:
+        list(O.assembled_column_blocks(verts, k, [0], 1, "SW", pool=pool))        # start the workers
+        t0 = time.perf_counter()
+        for _ in O.assembled_column_blocks(verts, k, starts, block, "SW", pool=pool):
+            pass
+        t_asm = time.perf_counter() - t0
+        out["assemble_sample_s"] = t_asm
+        out["assemble_cols"] = len(starts) * block
+        out["assemble_s"] = t_asm * N / (len(starts) * block)
+        t0 = time.perf_counter()
+        O.rhs_planewave(verts, k, I.planewave_angles(nrhs)[:rhs_sample])
+        out["rhs_sample_s"] = time.perf_counter() - t0
+        out["rhs_s"] = out["rhs_sample_s"] * nrhs / rhs_sample
+        rest = []
+        for Ns in fit_sizes:
+            v_s, _, _ = I.equal_chord_mesh(curve, Ns)
+            mats = O.assemble(v_s, k, "SW", pool=pool)
+            f = O.rhs_planewave(v_s, k, I.planewave_angles(nrhs))
+            t0 = time.perf_counter()
+            O.filtered_solve_blocks(mats, v_s, f, min(M, (Ns - 2) // 4), tol)
+            rest.append(time.perf_counter() - t0)
+    p = math.log(rest[1] / rest[0]) / math.log(fit_sizes[1] / fit_sizes[0])
+    out["rest_fit"] = {"sizes": list(fit_sizes), "seconds": rest, "exponent": p}
+    out["rest_s"] = rest[1] * (N / fit_sizes[1]) ** p
+    out["step_s"] = out["assemble_s"] + out["rhs_s"] + out["rest_s"]
+    return out
 
 
-def oracle_scaled_rate(smp: dict, N: int, nrhs: int) -> float:
-    s = N / smp["N"]
-    t = smp["t_assemble"] * s * s + smp["t_rhs"] * s * (nrhs / smp["nrhs"]) + \
-        smp["t_dense"] * s ** 3 * max(1.0, nrhs / smp["nrhs"] / s)
-    return nrhs / t
+def oracle_sample_text(m: dict, golden=None) -> str:
+    txt = (f"oracle block route (numpy/scipy FP64, {m['workers']} processes) on the same workload: assembly "
+           f"measured at N={m['N']} on {m['assemble_cols']} of "
+           f"{m['N']} segment columns ({m['assemble_sample_s']:.1f} s, scaled to {m['assemble_s']:.0f} s); "
+           f"plane-wave RHS measured at N={m['N']} for a sample ({m['rhs_sample_s']:.2f} s, scaled to "
+           f"{m['rhs_s']:.1f} s for {m['nrhs']}); filter block + compression + {m['nrhs']}-RHS solve timed at "
+           f"N={m['rest_fit']['sizes']} ({', '.join('%.2f' % x for x in m['rest_fit']['seconds'])} s), fitted "
+           f"N^{m['rest_fit']['exponent']:.2f} -> {m['rest_s']:.1f} s; step {m['step_s']:.0f} s")
+    if golden:
+        txt += (f"; the full C3 oracle run of tests/golden/make_goldens.py took {golden['total_s']:.0f} s "
+                f"(assembly {golden['assemble_s']:.0f} s) on {golden['workers']} processes of a "
+                f"{golden['host_cores']}-core host")
+    return txt
+
+
+def golden_c3_run():
+    """Wall time of the committed full-size C3 oracle run (tests/golden/oracle_runs.json)."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_runs.json")) as fh:
+            d = json.load(fh)
+        r = d["runs"]["c3_random_star0_n16384"]["seconds"]
+        return {"assemble_s": r["assemble"], "total_s": sum(r.values()), "workers": d["workers"],
+                "host_cores": d["host_cores"]}
+    except Exception:
+        return None
 
 
 def cpu_cores() -> int:
@@ -219,27 +318,26 @@ def job_value(units_per_rank: float, world: int, seconds: float) -> float:
 
 # ----------------------------------------------------------------------------- main
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle as it stands, timed on the host cores."""
+    """Reference arm: the CPU oracle as it stands, timed on the host cores.  Each step is one
+    bounded measurement of the oracle on the workload (oracle_measured); value = nrhs over
+    the oracle's time for one full step."""
     if rank != 0:
         return
-    N_s, nrhs_s = 512, 64
     for _ in range(args.warmup):
-        oracle_sample(N_s, nrhs_s, args.k, args.M, args.tol)
-    rates, times = [], []
+        oracle_measured(args.N, args.nrhs, args.k, args.M, args.tol, cols=64, rhs_sample=16, fit_sizes=(384, 768))
+    rates, times, last = [], [], None
     for _ in range(args.steps):
         t = time.perf_counter()
-        smp = oracle_sample(N_s, nrhs_s, args.k, args.M, args.tol)
+        last = oracle_measured(args.N, args.nrhs, args.k, args.M, args.tol)
         times.append(time.perf_counter() - t)
-        rates.append(oracle_scaled_rate(smp, args.N, args.nrhs))
+        rates.append(args.nrhs / last["step_s"])
     val = statistics.median(rates)
-    sample = (f"oracle (numpy/scipy FP64) full pipeline on the same curve family at N={N_s}, "
-              f"{nrhs_s} RHS per step, scaled to N={args.N}, {args.nrhs} RHS by the phase costs "
-              f"(assembly N^2, RHS N*nrhs, dense route N^3)")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "RHS/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.median(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args),
-            "cpu_baseline": {"value": val, "unit": "RHS/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": "RHS/s", "cores": last["workers"], "kind": "oracle",
+                             "sample": oracle_sample_text(last, golden_c3_run())},
             "e2e": {"value": val, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -387,7 +485,7 @@ def main():
     # ---- roofline of the dominant kernel
     launches = sum(c for c, _ in rep.values())
     quad_points = s.info()["quad_points"]
-    roof = roofline(rep, args, n_modes, info["r"], quad_points)
+    roof, roofs = roofline(rep, args, n_modes, info["r"], quad_points)
 
     # ---- end to end through the Python API with host buffers.  Every step copies its inputs
     # from pinned host memory and its solution back to pinned host memory inside the timed
@@ -431,31 +529,55 @@ def main():
 
     fp64_cmp = None
     if not args.no_compare_fp64 and args.prec == "mixed":
-        # the same step on the FP64 path, and the metric's accuracy bar: the mixed solution
-        # against the FP64 one on identical inputs (max over RHS of the relative error)
+        # the same step on the FP64 path (warm-up, then the median of timed steps, with its
+        # per-kernel split), and the metric's accuracy bar: the mixed solution against the
+        # FP64 one on identical inputs (max over RHS of the relative error)
         x_mixed = x.clone()
         v64 = torch.empty_like(v)
         x64 = torch.empty_like(x)
         s64 = bem.Solver(device=local, prec="fp64", stream=stream)
-        t64 = timed(lambda: (s64.assemble(verts, args.k, ops="SW"), s64.filter_apply(n_modes),
-                             s64.compress(args.tol), s64.factor(),
-                             s64.L.bem_rhs_planewave(s64.h, ang.data_ptr(), args.nrhs, None, v64.data_ptr(), args.N),
-                             s64.solve(v64, out=x64)))
+
+        def step64():
+            s64.assemble(verts, args.k, ops="SW")
+            s64.filter_apply(n_modes)
+            r64 = s64.compress(args.tol)
+            s64.factor()
+            s64.L.bem_rhs_planewave(s64.h, ang.data_ptr(), args.nrhs, None, v64.data_ptr(), args.N)
+            s64.solve(v64, out=x64)
+            return r64
+
+        for _ in range(args.fp64_warmup):
+            step64()
+        torch.cuda.synchronize(dev)
+        s64.timing(True)
+        t64s = [timed(step64) for _ in range(args.fp64_steps)]
+        rep64 = s64.timing_report()
+        s64.timing(False)
+        t64 = statistics.median(t64s)
         err = ((x_mixed - x64).abs().amax(dim=1) / x64.abs().amax(dim=1)).max().item()
-        fp64_cmp = {"ms_per_step": t64, "value": args.nrhs / (t64 / 1000.0), "unit": "RHS/s",
+        k64 = {k_: round(v_[1] / args.fp64_steps, 3) for k_, v_ in rep64.items()}
+        zg = rep64.get("gemm_rhs_SY")
+        zgemm_roof = None
+        if zg:
+            fl = 8.0 * args.N * args.N * args.nrhs
+            ach = fl / (zg[1] / zg[0] / 1000.0) / 1e12
+            zgemm_roof = {"kernel": "k_zgemm (gemm_rhs_SY)", "bound": "fp64", "achieved": ach,
+                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                          "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+        fp64_cmp = {"ms_per_step": t64, "steps": args.fp64_steps, "warmup": args.fp64_warmup,
+                    "ms_per_step_all": t64s, "value": args.nrhs / (t64 / 1000.0), "unit": "RHS/s",
+                    "kernels_ms_per_step": k64, "rhs_product_roofline": zgemm_roof,
                     "mixed_rel_err_vs_fp64": err, "bar": 1e-8, "pass": bool(err <= 1e-8)}
         s64.close()
         del v64, x64, x_mixed
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        smp = oracle_sample(1024, 128, args.k, args.M, args.tol)
-        cpu = {"value": oracle_scaled_rate(smp, args.N, args.nrhs), "unit": "RHS/s", "cores": cpu_cores(),
-               "kind": "oracle",
-               "sample": (f"oracle full pipeline on the same curve at N=1024 with 128 RHS "
-                          f"(assembly {smp['t_assemble']:.1f} s, RHS {smp['t_rhs']:.2f} s, dense route "
-                          f"{smp['t_dense']:.1f} s), scaled to N={args.N}, {args.nrhs} RHS by the phase costs "
-                          f"(N^2, N*nrhs, N^3)")}
+        m = oracle_measured(args.N, args.nrhs, args.k, args.M, args.tol)
+        cpu = {"value": args.nrhs / m["step_s"], "unit": "RHS/s", "cores": m["workers"], "kind": "oracle",
+               "sample": oracle_sample_text(m, golden_c3_run()), "phases_s": {
+                   "assemble": m["assemble_s"], "rhs": m["rhs_s"], "rest": m["rest_s"]},
+               "rest_fit": m["rest_fit"]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
@@ -466,7 +588,7 @@ def main():
                 "solve_rhs_per_s": args.nrhs / (t_sol / 1000.0), "rank": info["r"],
                 "max_rel_residual": resid, "refine_iters": iters,
                 "kernels_ms_per_step": {k_: round(v_[1] / args.steps, 3) for k_, v_ in rep.items()},
-                "roofline": roof, "clocks": clk, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu}
+                "roofline": roof, "rooflines": roofs, "clocks": clk, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu}
         if fp64_cmp:
             line["fp64_path"] = fp64_cmp
         print(json.dumps(line), flush=True)
