@@ -43,7 +43,7 @@ FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 ASM_OPS_PER_POINT = 270
 # DRAM bytes (read + write) per launch from ncu captures of the kernels as they stand
 # (absent = not captured since the kernel last changed); the summaries are under profiles/
-TRAFFIC_BYTES = {"tc_rhs_SY": 14.704e9 + 0.275e9}
+TRAFFIC_BYTES = {"tc_rhs_SY": 14.704e9 + 0.275e9, "k_assemble": 0.0324e9 + 8.687e9}
 
 
 def _peaks():
@@ -359,13 +359,14 @@ def run_batch(args, rank, world):
     specs = I.batch_problems(count=args.batch_count, first_seed=100 + 1000 * rank)
     problems = batch.problems_from_inputs(specs)
     nrhs_total = sum(len(p.angles) for p in problems)
+    tiles = batch.autotune_tiles(problems, device=local, reps=1) if args.prec == "mixed" else None
     if args.streams > 0:
         n_streams = args.streams
         tuned = None
     else:
         tuned = batch.autotune_streams(problems, prec=args.prec, device=local, candidates=(1, 2, 4, 8), sample=4)
         n_streams = max(set(tuned.values()), key=list(tuned.values()).count)
-    bs = batch.BatchSolver(problems, prec=args.prec, device=local, n_streams=n_streams)
+    bs = batch.BatchSolver(problems, prec=args.prec, device=local, n_streams=n_streams, tiles=tiles)
     for _ in range(args.warmup):
         bs.run()
     torch.cuda.synchronize(dev)
@@ -388,7 +389,11 @@ def run_batch(args, rank, world):
                 "config": {"workload": f"{args.batch_count} random stars (seeds 100.., N ~ U{{512..8192}}, "
                                        f"k = 10^U(-2, log10 5), 64..512 plane waves)",
                            "problems": args.batch_count, "rhs_total": nrhs_total, "prec": args.prec,
-                           "streams": n_streams, "tuned": tuned, "parallelism": f"replicas x{world}"},
+                           "streams": n_streams, "tuned_streams": tuned,
+                           "tuned_tiles": {str(b): {k: v for k, v in c.items() if k != "times_ms"}
+                                           for b, c in (tiles or {}).items()},
+                           "assembly": "one persistent launch over a global tile queue (bem_assemble_batch)",
+                           "parallelism": f"replicas x{world}"},
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     if dist is not None:

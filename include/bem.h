@@ -91,6 +91,13 @@ typedef struct {
                                  products always use all slices, so fewer slices here trade
                                  a cheaper solve for refinement sweeps (about one per 2^-7
                                  digit dropped below the refine_rtol accuracy)              */
+    int filter_tile_n;        /* mixed path, tile shapes of the split-bf16 products (the
+                                 batching layer's tuner sets them per problem size): tile
+                                 width of the filter products (112 or 128; 0 = the one that
+                                 pads the filter's columns least)                           */
+    int filter_split_k;       /*   K splits of the filter products (0 = the cost model's)     */
+    int rhs_tile_n;           /*   tile width of the right-hand-side product (0 = automatic)  */
+    int rhs_split_k;          /*   K splits of the right-hand-side product (0 = cost model)  */
 } bem_options;
 
 typedef struct {
@@ -157,6 +164,19 @@ bem_status bem_set_stream(bem_handle h, void* cuda_stream);
  * BEM_E_UNSUPPORTED (chords not equal to 1e-10, k h > 2), BEM_E_NOMEM, BEM_E_CUDA. */
 bem_status bem_assemble(bem_handle h, const double* verts_xy_dev, int64_t N, double k,
                         unsigned ops);
+
+/* bem_assemble_batch -- bem_assemble (S and N) for nprob independent problems at once: handle
+ * hs[q] (all on one device, each its own stream and options, none twice) assembles the polygon
+ * verts_dev[q] (2 Ns[q] device doubles) at wavenumber ks[q] (host arrays of nprob pointers /
+ * values).  The checks and the per-problem preparation run as in bem_assemble (one stream sync
+ * per problem for the mesh check); the tiles of all problems then run in ONE persistent launch
+ * on hs[0]'s stream, CTAs taking tiles from a global queue (largest problems first), so that
+ * small problems fill the GPU beside large ones; each handle's stream waits for that launch
+ * before its own later work.  Synchronises hs[0]'s stream.  The batching layer's assembly
+ * stage; the paper solves one problem at a time.  Errors as bem_assemble (the message of a
+ * failing problem q > 0 is also left on hs[0]). */
+bem_status bem_assemble_batch(bem_handle* hs, int64_t nprob, const double* const* verts_dev, const int64_t* Ns,
+                              const double* ks);
 
 /* filter_apply -- the Laplacian filter of eq. (LapFilter) applied to the compact part of
  * the Calderon-preconditioned equation (Sec. IV-A).  With the equal-chord mesh the filter

@@ -15,8 +15,11 @@ fastest per problem-size bucket.  ``SolveGraph`` records the FP64 Woodbury solve
 problem (``solve_many_noalloc``, which allocates nothing) into one CUDA graph, replayed
 for each new set of right-hand sides.
 
-Each problem is solved by exactly the kernels a single ``bem.Solver`` uses, so the
-results are those of the problems solved one after another.
+By default the assembly stage of all problems is one persistent launch
+(``bem_assemble_batch``): CTAs take tiles from a global queue over every problem, largest
+first, so the tiles of small problems fill the GPU beside those of large ones.  Each problem
+is solved by exactly the kernels a single ``bem.Solver`` uses (the batched assembly runs the
+same tile code), so the results are those of the problems solved one after another.
 """
 from __future__ import annotations
 
@@ -59,12 +62,18 @@ class BatchSolver:
     """Solves a list of Problems concurrently on ``n_streams`` streams of one device."""
 
     def __init__(self, problems: list[Problem], prec: str = "mixed", device: int = 0, n_streams: int = 4,
-                 refine_rtol: float = 1e-10):
+                 refine_rtol: float = 1e-10, persistent: bool = True, tiles: dict | None = None):
+        """persistent: assemble every problem's S and N in one launch over a global tile queue
+        (bem_assemble_batch) before the per-problem stages; False: each problem assembles on
+        its own stream.  tiles: {size bucket: tile options} from ``autotune_tiles`` (mixed
+        path), applied to each problem by its bucket."""
         self.problems = problems
         self.prec = prec
         self.device = device
         self.n_streams = max(1, int(n_streams))
         self.refine_rtol = refine_rtol
+        self.persistent = persistent
+        self.tiles = tiles or {}
         self.streams = [torch.cuda.Stream(device=device) for _ in range(self.n_streams)]
         self._coop = threading.Condition()
         props = torch.cuda.get_device_properties(device)
@@ -73,17 +82,24 @@ class BatchSolver:
         self.solvers: list[bem.Solver | None] = [None] * len(problems)
         self.results: list[dict | None] = [None] * len(problems)
 
-    def _one(self, i: int, stream: torch.cuda.Stream):
+    def _solver(self, i: int, stream: torch.cuda.Stream) -> bem.Solver:
+        s = self.solvers[i]
+        if s is None:
+            tiles = self.tiles.get(size_bucket(self.problems[i].verts.shape[0])) if self.prec == "mixed" else None
+            s = bem.Solver(device=self.device, prec=self.prec, stream=stream, refine_rtol=self.refine_rtol,
+                           tiles=tiles)
+            self.solvers[i] = s
+        return s
+
+    def _one(self, i: int, stream: torch.cuda.Stream, assembled: bool = False):
         p = self.problems[i]
         dev = torch.device("cuda", self.device)
         with torch.cuda.stream(stream):
-            s = self.solvers[i]
-            if s is None:
-                s = bem.Solver(device=self.device, prec=self.prec, stream=stream, refine_rtol=self.refine_rtol)
-                self.solvers[i] = s
-            verts = torch.from_numpy(np.ascontiguousarray(p.verts)).to(dev, non_blocking=True)
+            s = self._solver(i, stream)
             ang = torch.from_numpy(np.ascontiguousarray(p.angles)).to(dev, non_blocking=True)
-            s.assemble(verts, p.k, ops="SW")
+            if not assembled:
+                verts = torch.from_numpy(np.ascontiguousarray(p.verts)).to(dev, non_blocking=True)
+                s.assemble(verts, p.k, ops="SW")
             s.filter_apply(p.n_modes)
             need = self._coop_ctas(p)
             with self._coop:
@@ -116,11 +132,20 @@ class BatchSolver:
         order = sorted(range(len(self.problems)), key=lambda i: -self.problems[i].verts.shape[0])
         queues = [order[q::self.n_streams] for q in range(self.n_streams)]
         errors = []
+        if self.persistent:
+            dev = torch.device("cuda", self.device)
+            sv = []
+            for q in range(self.n_streams):
+                for i in queues[q]:
+                    sv.append((i, self._solver(i, self.streams[q])))
+            bem.assemble_batch([s for _, s in sv],
+                               [torch.from_numpy(np.ascontiguousarray(self.problems[i].verts)).to(dev) for i, _ in sv],
+                               [self.problems[i].k for i, _ in sv])
 
         def worker(q):
             try:
                 for i in queues[q]:
-                    self._one(i, self.streams[q])
+                    self._one(i, self.streams[q], assembled=self.persistent)
                 self.streams[q].synchronize()
             except Exception as e:          # re-raised on the calling thread
                 errors.append(e)
@@ -163,6 +188,65 @@ def autotune_streams(problems: list[Problem], prec: str = "mixed", device: int =
             bs.close()
         best[b] = min(times, key=times.get)
     return best
+
+
+# candidate tile shapes (tile width, K splits; 0 = the library's own choice) per stage of the
+# mixed path's split-bf16 products
+TILE_CANDIDATES = {
+    "filter": ((0, 0), (112, 0), (128, 0), (112, 1), (128, 1), (112, 2), (112, 4)),
+    "rhs": ((0, 0), (128, 1), (128, 2), (128, 4), (112, 1), (112, 2)),
+}
+_STAGE_KERNELS = {"filter": ("tc_filter_QtS", "tc_filter_YN", "k_splitk_reduce"),
+                  "rhs": ("tc_rhs_SY", "k_splitk_reduce")}
+
+
+def _stage_ms(p: Problem, stage: str, bn: int, sk: int, device: int, reps: int) -> float:
+    """Kernel time of one stage of the mixed path on problem p with the given tile shape."""
+    dev = torch.device("cuda", device)
+    s = bem.Solver(device=device, prec="mixed", tiles={f"{stage}_tile_n": bn, f"{stage}_split_k": sk})
+    try:
+        s.assemble(torch.from_numpy(np.ascontiguousarray(p.verts)).to(dev), p.k, ops="SW")
+        ang = torch.from_numpy(np.ascontiguousarray(p.angles)).to(dev)
+        best = float("inf")
+        for _ in range(reps + 1):                # the first pass warms up (allocations)
+            s.timing(True)
+            if stage == "filter":
+                s.filter_apply(p.n_modes)
+            else:
+                s.rhs_planewave(ang)
+            rep = s.timing_report()
+            s.timing(False)
+            best = min(best, sum(rep.get(k, (0, 0.0))[1] for k in _STAGE_KERNELS[stage]))
+        return best
+    finally:
+        s.close()
+
+
+def autotune_tiles(problems: list[Problem], device: int = 0, candidates: dict | None = None,
+                   reps: int = 2) -> dict:
+    """The batching layer's tile-shape tuner: for each size bucket it takes the bucket's largest
+    problem, times every candidate (tile width, K splits) of each stage's split-bf16 products
+    (the filter products Q^T S, Y2 N; the right-hand-side product S Y) by the kernels' own
+    events, and keeps the fastest.  Returns {bucket: {"filter_tile_n", "filter_split_k",
+    "rhs_tile_n", "rhs_split_k"}, with "times_ms": {stage: {candidate: ms}}}."""
+    cands = candidates or TILE_CANDIDATES
+    buckets: dict[int, Problem] = {}
+    for p in problems:
+        b = size_bucket(p.verts.shape[0])
+        if b not in buckets or p.verts.shape[0] > buckets[b].verts.shape[0]:
+            buckets[b] = p
+    out = {}
+    for b, p in sorted(buckets.items()):
+        choice, times = {}, {}
+        for stage, cs in cands.items():
+            t = {c: _stage_ms(p, stage, c[0], c[1], device, reps) for c in cs}
+            bn, sk = min(t, key=t.get)
+            choice[f"{stage}_tile_n"] = bn
+            choice[f"{stage}_split_k"] = sk
+            times[stage] = {f"{c[0]}x{c[1]}": round(v, 4) for c, v in t.items()}
+        choice["times_ms"] = times
+        out[b] = choice
+    return out
 
 
 class SolveGraph:

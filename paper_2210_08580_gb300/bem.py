@@ -27,13 +27,16 @@ EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error",
            "bem_assemble", "filter_apply", "compress_compact", "factor", "bem_rhs_planewave",
            "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info", "bem_timing_enable",
            "bem_timing_report", "solve_many_noalloc", "bem_farfield", "bem_farfield_adjoint",
-           "bem_shape_vjp", "bem_rhs_pointsource", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain")
+           "bem_shape_vjp", "bem_rhs_pointsource", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain",
+           "bem_assemble_batch")
 
 
 class BemOptions(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("include_kernel_mode", ctypes.c_int),
                 ("refine_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
-                ("split_slices", ctypes.c_int), ("rhs_slices", ctypes.c_int), ("solve_slices", ctypes.c_int)]
+                ("split_slices", ctypes.c_int), ("rhs_slices", ctypes.c_int), ("solve_slices", ctypes.c_int),
+                ("filter_tile_n", ctypes.c_int), ("filter_split_k", ctypes.c_int), ("rhs_tile_n", ctypes.c_int),
+                ("rhs_split_k", ctypes.c_int)]
 
 
 class BemInfo(ctypes.Structure):
@@ -130,12 +133,15 @@ def load_library(path: str = LIB_PATH):
     L.bem_rhs_scale.argtypes = [vp, vp, i64, i64, vp, vp, i64]
     L.bem_amplitude_grad.argtypes = [vp, vp, i64, vp, i64, i64, vp]
     L.bem_shape_chain.argtypes = [vp, vp, i64, vp, vp]
+    L.bem_assemble_batch.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                     ctypes.POINTER(dbl)]
     L.bem_timing_enable.argtypes = [vp, i32]
     L.bem_timing_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     for name in ("bem_create", "bem_destroy", "bem_set_stream", "bem_assemble", "filter_apply",
                  "compress_compact", "factor", "bem_rhs_planewave", "bem_rhs_pointsource", "solve_many", "solve_backward",
                  "bem_get_matrix", "bem_get_info", "bem_timing_enable", "bem_timing_report", "bem_farfield",
-                 "bem_farfield_adjoint", "bem_shape_vjp", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain"):
+                 "bem_farfield_adjoint", "bem_shape_vjp", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain",
+                 "bem_assemble_batch"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -155,10 +161,11 @@ class Solver:
     def __init__(self, device: int = 0, prec: str = "fp64", include_kernel_mode: bool = True,
                  refine_rtol: float = 1e-10, max_refine: int = 6, stream: torch.cuda.Stream | None = None,
                  split_slices: int = 0, rhs_slices: int = 0, solve_slices: int = 0,
-                 memory: str = "torch"):
+                 memory: str = "torch", tiles: dict | None = None):
         """memory: "torch" (default) -- every device buffer of the handle comes from
         PyTorch's caching allocator through the bem_create hooks; "cuda" -- the library
-        allocates with the CUDA runtime itself."""
+        allocates with the CUDA runtime itself.  tiles: optional tile shapes of the mixed
+        path's products, {"filter_tile_n", "filter_split_k", "rhs_tile_n", "rhs_split_k"}."""
         self.L = load_library()
         self.device = torch.device("cuda", device)
         opt = BemOptions()
@@ -170,6 +177,9 @@ class Solver:
         opt.split_slices = split_slices
         opt.rhs_slices = rhs_slices
         opt.solve_slices = solve_slices
+        for key in ("filter_tile_n", "filter_split_k", "rhs_tile_n", "rhs_split_k"):
+            if tiles and key in tiles:
+                setattr(opt, key, int(tiles[key]))
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = ctypes.c_void_p()
         if memory == "torch":
@@ -358,6 +368,25 @@ class Solver:
 
     def _include_kernel(self) -> bool:
         return self._ik
+
+
+def assemble_batch(solvers: list, verts_list: list, ks: list):
+    """bem_assemble_batch: S and N of every solver's problem in one persistent launch (the
+    solvers on one device; verts (N, 2) each, wavenumbers ks)."""
+    L = load_library()
+    n = len(solvers)
+    vs = [v.to(device=solvers[i].device, dtype=torch.float64).contiguous() for i, v in enumerate(verts_list)]
+    hs = (ctypes.c_void_p * n)(*[s.h.value for s in solvers])
+    vp = (ctypes.c_void_p * n)(*[v.data_ptr() for v in vs])
+    Ns = (ctypes.c_int64 * n)(*[v.shape[0] for v in vs])
+    kk = (ctypes.c_double * n)(*[float(k) for k in ks])
+    st = L.bem_assemble_batch(hs, n, vp, Ns, kk)
+    if st != 0:
+        raise BemError(st, L.bem_last_error(solvers[0].h).decode())
+    for s, v, k in zip(solvers, vs, ks):
+        s._verts = v
+        s.N = v.shape[0]
+        s.k = float(k)
 
 
 class FarFieldSolve(torch.autograd.Function):

@@ -140,6 +140,10 @@ void bem_default_options(bem_options* opt) {
     opt->split_slices = 0;
     opt->rhs_slices = 0;
     opt->solve_slices = 0;
+    opt->filter_tile_n = 0;
+    opt->filter_split_k = 0;
+    opt->rhs_tile_n = 0;
+    opt->rhs_split_k = 0;
 }
 
 bem_status bem_create(bem_handle* out, int device, void* cuda_stream, const bem_options* opt,
@@ -226,9 +230,9 @@ bem_status bem_set_stream(bem_handle h, void* s) {
     return BEM_OK;
 }
 
-bem_status bem_assemble(bem_handle h, const double* verts, int64_t N, double k, unsigned ops) {
-    if (!h) return BEM_E_INVALID;
-    h->err.clear();
+// everything of bem_assemble before the tiles: checks, buffers, geometry (one stream sync for
+// the mesh check)
+static bem_status assemble_begin(bem_handle h, const double* verts, int64_t N, double k, unsigned ops) {
     if (!verts || N < 16 || N > (1 << 20) || !(k > 0.0) || !std::isfinite(k) || (ops & ~7u) || !(ops & 3u))
         return bem_fail(h, BEM_E_INVALID, "bem_assemble: need verts, 16 <= N <= 2^20, k > 0, ops with S or W");
     BEM_CUDA(h, cudaSetDevice(h->device));
@@ -265,11 +269,51 @@ bem_status bem_assemble(bem_handle h, const double* verts, int64_t N, double k, 
         return bem_fail(h, BEM_E_UNSUPPORTED, "bem_assemble: k h > 2 (mesh too coarse for this frequency)");
     h->hbar = hmean;
     h->ops = BEM_OP_S | BEM_OP_W | (ops & BEM_OP_D);
-    if ((st = launch_assemble(h, h->ops)) != BEM_OK) return st;
+    return BEM_OK;
+}
+
+// after the tiles: the mixed path's digit slices
+static bem_status assemble_end(bem_handle h) {
     if (h->opt.prec == BEM_MIXED_BF16) {
-        if ((st = tc_prepare_operators(h)) != BEM_OK) return st;
+        bem_status st = tc_prepare_operators(h);
+        if (st != BEM_OK) return st;
     }
     h->stage = 1;
+    return BEM_OK;
+}
+
+bem_status bem_assemble(bem_handle h, const double* verts, int64_t N, double k, unsigned ops) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    bem_status st;
+    if ((st = assemble_begin(h, verts, N, k, ops)) != BEM_OK) return st;
+    if ((st = launch_assemble(h, h->ops)) != BEM_OK) return st;
+    return assemble_end(h);
+}
+
+bem_status bem_assemble_batch(bem_handle* hs, int64_t nprob, const double* const* verts, const int64_t* Ns,
+                              const double* ks) {
+    if (!hs || !verts || !Ns || !ks || nprob < 1 || nprob > 65536) return BEM_E_INVALID;
+    for (int64_t q = 0; q < nprob; ++q) {
+        if (!hs[q]) return BEM_E_INVALID;
+        if (hs[q]->device != hs[0]->device)
+            return bem_fail(hs[q], BEM_E_INVALID, "bem_assemble_batch: every handle must be on the same device");
+        for (int64_t r = 0; r < q; ++r)
+            if (hs[r] == hs[q]) return bem_fail(hs[q], BEM_E_INVALID, "bem_assemble_batch: a handle appears twice");
+    }
+    for (int64_t q = 0; q < nprob; ++q) {
+        hs[q]->err.clear();
+        bem_status st = assemble_begin(hs[q], verts[q], Ns[q], ks[q], BEM_OP_S | BEM_OP_W);
+        if (st != BEM_OK) {
+            if (q > 0) bem_fail(hs[0], st, "bem_assemble_batch: problem " + std::to_string(q) + ": " + hs[q]->err);
+            return st;
+        }
+    }
+    BEM_CUDA(hs[0], cudaSetDevice(hs[0]->device));
+    bem_status st = launch_assemble_batch(hs, (int)nprob);
+    if (st != BEM_OK) return st;
+    for (int64_t q = 0; q < nprob; ++q)
+        if ((st = assemble_end(hs[q])) != BEM_OK) return st;
     return BEM_OK;
 }
 

@@ -724,9 +724,9 @@ __device__ __forceinline__ int exp_field_of(double v) { return (int)((__double_a
 // pairs keep their relative geometry to double-float precision.  Self and adjacent pairs
 // come from the FP64 table of k_near_pairs.
 template <int T>
-__global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
+__device__ __forceinline__ void assemble_sn_tile(const AsmParams& p, int L) {
     int ti, tj;
-    tile_of((int)blockIdx.x, p.nT, ti, tj);
+    tile_of(L, p.nT, ti, tj);
     constexpr int TP = T + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* sI = reinterpret_cast<float4*>(smem_raw);               // TP*TP*4 complex df
@@ -999,6 +999,46 @@ __global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) {
     }
 }
 
+static_assert(sizeof(AsmParams) % 4 == 0, "AsmParams is copied to shared memory in 4-byte words");
+
+// one CTA per tile of one problem
+template <int T>
+__global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) { assemble_sn_tile<T>(p, (int)blockIdx.x); }
+
+// Many problems in one launch: persistent CTAs take tiles from one global queue (an atomic
+// counter over the problems' tiles in order, the problems sorted largest first by the caller
+// and each one's tiles diagonal-first), so small problems fill the GPU behind large ones.
+// first[q] is the queue position of problem q's first tile; the tiles need no waits.
+template <int T>
+__global__ void __launch_bounds__(256) k_assemble_sn_batch(const AsmParams* __restrict__ ps,
+                                                           const long long* __restrict__ first, int nprob,
+                                                           long long total, unsigned long long* queue) {
+    __shared__ AsmParams sp;
+    __shared__ long long s_L;
+    __shared__ int s_q;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long L = (long long)atomicAdd(queue, 1ull);
+            int lo = 0, hi = nprob - 1;                  // the last problem with first[q] <= L
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (first[mid] <= L) lo = mid; else hi = mid - 1;
+            }
+            s_L = L;
+            s_q = lo;
+        }
+        __syncthreads();
+        const long long L = s_L;
+        if (L >= total) return;
+        const int q = s_q;
+        for (int w = threadIdx.x; w < (int)(sizeof(AsmParams) / 4); w += blockDim.x)
+            reinterpret_cast<int*>(&sp)[w] = reinterpret_cast<const int*>(ps + q)[w];
+        __syncthreads();
+        assemble_sn_tile<T>(sp, (int)(L - first[q]));
+        __syncthreads();                                 // shared state is reused by the next tile
+    }
+}
+
 template <int T, bool WD>
 __global__ void __launch_bounds__(256) k_assemble(AsmParams p) {
     int ti, tj;
@@ -1181,8 +1221,9 @@ static bem_status run_assemble_sn(bem_ctx* h, AsmParams& p) {
     return BEM_OK;
 }
 
-bem_status launch_assemble(bem_ctx* h, unsigned ops) {
-    AsmParams p;
+// Tables, near-pair integrals and output buffers of one assembly on h's stream; *near is a
+// stream-ordered temporary the caller frees (asm_finish) after the tiles have run.
+static bem_status asm_prepare(bem_ctx* h, unsigned ops, AsmParams& p, cplx** near_out) {
     p.N = (int)h->N;
     p.k = h->k;
     p.seg = h->seg;
@@ -1197,6 +1238,7 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     if (st != BEM_OK) return st;
     cplx* near = nullptr;
     BEM_CUDA(h, bem_dmalloc_async(h, (void**)&near, sizeof(cplx) * NEAR_STRIDE * (size_t)h->N));
+    *near_out = near;
     const unsigned gnear = (unsigned)((h->N + 7) / 8);
     if (ops & BEM_OP_D) {
         BEM_TIMED(h, "k_near_pairs", (k_near_pairs<true><<<gnear, 256, 0, h->stream>>>(h->seg, (int)h->N, p.sc, near)));
@@ -1225,10 +1267,107 @@ bem_status launch_assemble(bem_ctx* h, unsigned ops) {
         p.rexpW = h->rexp + h->N;
         p.wband = (int)std::min<int64_t>(TC_W_BAND, (h->N - 1) / 2);
     }
-    st = (ops & BEM_OP_D) ? run_assemble<15, true>(h, p) : run_assemble_sn<31>(h, p);
+    return BEM_OK;
+}
+
+static void asm_finish(bem_ctx* h, const AsmParams& p, cplx* near, bem_status st) {
     if (st == BEM_OK && p.rexpS) h->rexp_valid = true;
     if (st == BEM_OK && p.kpart) h->k1_valid = true;
     bem_dfree_async(h, near);
+}
+
+bem_status launch_assemble(bem_ctx* h, unsigned ops) {
+    AsmParams p;
+    cplx* near = nullptr;
+    bem_status st = asm_prepare(h, ops, p, &near);
+    if (st == BEM_OK) st = (ops & BEM_OP_D) ? run_assemble<15, true>(h, p) : run_assemble_sn<31>(h, p);
+    asm_finish(h, p, near, st);
+    return st;
+}
+
+// S and N of several problems (one device, each handle on its own stream) with one
+// persistent launch over a global tile queue, on hs[0]'s stream; synchronises that stream.
+bem_status launch_assemble_batch(bem_ctx** hs, int nprob) {
+    constexpr int T = 31, TP = T + 1;
+    bem_ctx* h0 = hs[0];
+    std::vector<AsmParams> ps(nprob);
+    std::vector<cplx*> nears(nprob, nullptr);
+    bem_status st = BEM_OK;
+    for (int q = 0; q < nprob && st == BEM_OK; ++q) {
+        st = asm_prepare(hs[q], BEM_OP_S | BEM_OP_W, ps[q], &nears[q]);
+        ps[q].nT = (ps[q].N + T - 1) / T;
+    }
+    // the largest problems' tiles first
+    std::vector<int> order(nprob);
+    for (int q = 0; q < nprob; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ps[a].N > ps[b].N; });
+    std::vector<AsmParams> sorted(nprob);
+    std::vector<long long> first(nprob);
+    long long total = 0;
+    for (int r = 0; r < nprob; ++r) {
+        sorted[r] = ps[order[r]];
+        first[r] = total;
+        total += (long long)sorted[r].nT * (sorted[r].nT + 1) / 2;
+    }
+    AsmParams* dps = nullptr;
+    long long* dfirst = nullptr;
+    unsigned long long* queue = nullptr;
+    std::vector<cudaEvent_t> evs;
+    if (st == BEM_OK) {
+        const size_t bytes = sizeof(AsmParams) * nprob + sizeof(long long) * nprob + 256;
+        void* buf = nullptr;
+        const cudaError_t ae = bem_dmalloc_async(h0, &buf, bytes);
+        if (ae != cudaSuccess) {
+            st = bem_cuda_check(h0, ae, "batch assembly parameters");
+        } else {
+            dps = (AsmParams*)buf;
+            dfirst = (long long*)((char*)buf + sizeof(AsmParams) * nprob);
+            queue = (unsigned long long*)((char*)dfirst + sizeof(long long) * nprob);
+        }
+    }
+    if (st == BEM_OK) {
+        // the other handles' preparation before the launch
+        for (int q = 1; q < nprob; ++q) {
+            cudaEvent_t e = bem_event_get(hs[q]);
+            cudaEventRecord(e, hs[q]->stream);
+            cudaStreamWaitEvent(h0->stream, e, 0);
+            evs.push_back(e);
+        }
+        cudaMemcpyAsync(dps, sorted.data(), sizeof(AsmParams) * nprob, cudaMemcpyHostToDevice, h0->stream);
+        cudaMemcpyAsync(dfirst, first.data(), sizeof(long long) * nprob, cudaMemcpyHostToDevice, h0->stream);
+        cudaMemsetAsync(queue, 0, sizeof(unsigned long long), h0->stream);
+        const size_t smem = (size_t)TP * TP * (4 * sizeof(float4) + sizeof(float4) + sizeof(float2)) +
+                            (size_t)16 * TP * sizeof(float2) + (size_t)T * T * sizeof(float4);
+        cudaError_t e = cudaFuncSetAttribute(k_assemble_sn_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per = 0, nsm = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_assemble_sn_batch<T>, 256, smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h0->device);
+        if (e != cudaSuccess) st = bem_cuda_check(h0, e, "batch assembly launch setup");
+        if (st == BEM_OK) {
+            const long long ctas = std::min<long long>(total, (long long)std::max(per, 1) * nsm);
+            BEM_TIMED(h0, "k_assemble_batch", (k_assemble_sn_batch<T><<<(unsigned)ctas, 256, smem, h0->stream>>>(
+                                                   dps, dfirst, nprob, total, queue)));
+            cudaError_t le = cudaGetLastError();
+            if (le != cudaSuccess) st = bem_cuda_check(h0, le, "k_assemble_sn_batch");
+        }
+        // everything after the launch, per handle, waits for it
+        cudaEvent_t done = bem_event_get(h0);
+        cudaEventRecord(done, h0->stream);
+        for (int q = 1; q < nprob; ++q) cudaStreamWaitEvent(hs[q]->stream, done, 0);
+        evs.push_back(done);
+        for (int q = 0; q < nprob && st == BEM_OK; ++q) {
+            bem_ctx* h = hs[q];
+            BEM_TIMED(h, "k_sum_slots", (k_sum_slots<<<(unsigned)((ps[q].N + 255) / 256), 256, 0, h->stream>>>(
+                                             ps[q].kpart, ps[q].nT, ps[q].N, h->k1)));
+            cudaError_t le = cudaGetLastError();
+            if (le != cudaSuccess) st = bem_cuda_check(h, le, "k_sum_slots");
+        }
+        bem_dfree_async(h0, dps);
+        cudaStreamSynchronize(h0->stream);         // the host-side parameter arrays
+    }
+    for (int q = 0; q < nprob; ++q) asm_finish(hs[q], ps[q], nears[q], st);
+    for (size_t i = 0; i + 1 < evs.size(); ++i) hs[i + 1]->evpool.push_back(evs[i]);
+    if (!evs.empty()) h0->evpool.push_back(evs.back());
     return st;
 }
 

@@ -25,6 +25,8 @@ cudaError_t init_gauss_tables();
 // assemble.cu
 bem_status launch_geometry(bem_ctx* h, const double* verts, int64_t N, double* stats_dev);
 bem_status launch_assemble(bem_ctx* h, unsigned ops);
+// S and N of nprob prepared handles in one persistent launch (global tile queue) on hs[0]'s stream
+bem_status launch_assemble_batch(bem_ctx** hs, int nprob);
 bem_status launch_rhs(bem_ctx* h, const double* angles, int64_t nrhs, cplx* f, cplx* hz, int64_t ld);
 // line sources at src (2 nsrc doubles, (x, y) pairs): f = -<phi, d g2(|x - r0|)/d nu>, hz = <phi, g2>
 bem_status launch_rhs_point(bem_ctx* h, const double* src, int64_t nsrc, cplx* f, cplx* hz, int64_t ld);

@@ -34,6 +34,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <mutex>
@@ -803,10 +804,16 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     p.kps = p.nkb;
     p.part = nullptr;
     const size_t smem = gemm_smem(Sg);
+    // the stage's tile choice (bem_options): the filter products, the right-hand-side product,
+    // or automatic for the others
+    const bool is_filter = strncmp(tag, "tc_filter", 9) == 0, is_rhs = strcmp(tag, "tc_rhs_SY") == 0;
+    const int want_bn = is_filter ? h->opt.filter_tile_n : (is_rhs ? h->opt.rhs_tile_n : 0);
+    const int want_split = is_filter ? h->opt.filter_split_k : (is_rhs ? h->opt.rhs_split_k : 0);
     // tile width: 112 when it pads the B part rows less than 128 does (the filter's 201 real
     // or 2 x 201 complex columns: 224 and 448 instead of 256 and 512), for the usual slice counts
     const int pad128 = (p.Ncols + 127) / 128 * 128, pad112 = (p.Ncols + 111) / 112 * 112;
-    const int BN = (pad112 < pad128 && (Sg == 5 || Sg == 6)) ? 112 : 128;
+    int BN = (pad112 < pad128 && (Sg == 5 || Sg == 6)) ? 112 : 128;
+    if (want_bn == 128 || (want_bn == 112 && (Sg == 5 || Sg == 6))) BN = want_bn;
     void (*kern)(const CUtensorMap, const CUtensorMap, TcGemmArgs) = nullptr;
     switch (Sg * 1000 + BN) {
         case 3128: kern = k_tc_gemm<3, 128>; break;
@@ -836,13 +843,20 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     const double chunk_ms = (double)(Sg * (Sg + 1) / 2) * TC_CHUNK_KB * (TC_BK / 16) * 73.0 / 2.0e6 * BN / 128.0;
     const double part_ms_per_split = (double)p.Ml * p.ml * 32.0 / 6.0e9;
     int splits = 1;
-    double best = (double)((T + nsm - 1) / nsm) * nch * chunk_ms;
-    for (int s = 2; s <= 32 && s <= nch / 2; ++s) {
-        const int cps = (nch + s - 1) / s;
-        const int sr = (nch + cps - 1) / cps;
-        if (sr != s) continue;
-        const double cost = (double)(((int64_t)T * s + nsm - 1) / nsm) * cps * chunk_ms + s * part_ms_per_split;
-        if (cost < 0.98 * best) { best = cost; splits = s; p.kps = cps * TC_CHUNK_KB; }
+    if (want_split >= 1) {
+        // the stage's split count (at most one K' chunk per split, no empty splits)
+        const int cps = (nch + std::min(want_split, nch) - 1) / std::min(want_split, nch);
+        splits = (nch + cps - 1) / cps;
+        if (splits > 1) p.kps = cps * TC_CHUNK_KB;
+    } else {
+        double best = (double)((T + nsm - 1) / nsm) * nch * chunk_ms;
+        for (int s = 2; s <= 32 && s <= nch / 2; ++s) {
+            const int cps = (nch + s - 1) / s;
+            const int sr = (nch + cps - 1) / cps;
+            if (sr != s) continue;
+            const double cost = (double)(((int64_t)T * s + nsm - 1) / nsm) * cps * chunk_ms + s * part_ms_per_split;
+            if (cost < 0.98 * best) { best = cost; splits = s; p.kps = cps * TC_CHUNK_KB; }
+        }
     }
     if (splits > 1) {
         const size_t need = (size_t)splits * p.Ml * p.ml * sizeof(double2);

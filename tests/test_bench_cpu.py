@@ -1,6 +1,7 @@
 """bench.py's roofline arithmetic on made-up per-kernel reports (host logic only): the
-dominant kernel, the bf16 flop count of the split products (slice pairs times the real
-part products) and the FP32-operation count of the assembly."""
+dominant kernel, the method's own flop count of the split products (the complex FP64
+products they stand for) beside the bf16 emulation count (slice pairs times the real part
+products), the FP32-operation count of the assembly, and the oracle timing fit."""
 import types
 
 import pytest
@@ -12,20 +13,26 @@ def _args(N=16384, nrhs=1024):
     return types.SimpleNamespace(N=N, nrhs=nrhs)
 
 
-def test_tensor_roofline_of_the_rhs_product():
+def test_tensor_roofline_of_the_rhs_product_counts_the_method_work():
     rep = {"tc_rhs_SY": (3, 3 * 18.4), "k_assemble": (3, 3 * 16.7), "k_jacobi": (3, 3 * 5.3)}
-    roof = bench.roofline(rep, _args(), 201, 201, 6.7e8)
+    roof, rows = bench.roofline(rep, _args(), 201, 201, 6.7e8)
     assert roof["kernel"] == "tc_rhs_SY" and roof["bound"] == "tensor"
-    assert roof["slice_pairs"] == 15                      # five slices per operand
-    flops = 15 * 2 * 4 * 16384 * 1024 * 16384              # complex x complex: four part products
-    assert roof["achieved"] == pytest.approx(flops / 18.4e-3 / 1e12)
+    method = 8 * 16384 * 16384 * 1024                       # v = S Y, complex FP64 product
+    assert roof["method_flops_per_launch"] == pytest.approx(method)
+    assert roof["achieved"] == pytest.approx(method / 18.4e-3 / 1e12)
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    emu = roof["emulation"]
+    assert emu["slice_pairs"] == 15                        # five slices per operand
+    flops = 15 * 2 * 4 * 16384 * 1024 * 16384              # complex x complex: four part products
+    assert emu["bf16_flops_per_launch"] == pytest.approx(flops)
+    assert emu["frac"] == pytest.approx(15 * roof["frac"])
     assert roof["traffic"] == pytest.approx(bench.TRAFFIC_BYTES["tc_rhs_SY"])
+    assert [r["kernel"] for r in rows] == ["tc_rhs_SY", "k_assemble", "k_jacobi"]
 
 
 def test_alu_roofline_of_the_assembly():
     rep = {"k_assemble": (2, 2 * 16.7), "tc_rhs_SY": (2, 2 * 10.0)}
-    roof = bench.roofline(rep, _args(), 201, 201, 6.7e8)
+    roof, _ = bench.roofline(rep, _args(), 201, 201, 6.7e8)
     assert roof["kernel"] == "k_assemble" and roof["bound"] == "alu"
     assert roof["ops_per_unit"] == bench.ASM_OPS_PER_POINT and roof["units_per_launch"] == 6.7e8
     assert roof["achieved"] == pytest.approx(6.7e8 * bench.ASM_OPS_PER_POINT / 16.7e-3 / 1e12)
@@ -40,3 +47,12 @@ def test_filter_products_count_real_and_complex_parts():
     assert a == pytest.approx(21 * 2 * 2 * 21 * 1024 * 1024)
     assert b == pytest.approx(2 * a)
     assert bench.tc_gemm_flops("k_iir", 1024, 64, 21, 21, 6) is None
+    args = _args(N=1024, nrhs=64)
+    assert bench.method_flops("tc_filter_QtS", args, 21) == pytest.approx(4 * 21 * 1024 * 1024)
+    assert bench.method_flops("tc_filter_YN", args, 21) == pytest.approx(8 * 21 * 1024 * 1024)
+
+
+def test_filter_pair_reported_together():
+    rep = {"tc_rhs_SY": (1, 18.0), "k_assemble": (1, 16.0), "tc_filter_YN": (1, 6.0), "tc_filter_QtS": (1, 3.0)}
+    _, rows = bench.roofline(rep, _args(), 201, 201, 6.7e8)
+    assert [r["kernel"] for r in rows] == ["tc_rhs_SY", "k_assemble", "tc_filter_YN", "tc_filter_QtS"]

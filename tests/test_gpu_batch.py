@@ -126,3 +126,43 @@ def test_batch_subsample_against_the_oracle(B, prec):
         assert abs(r - r0) <= 1
         assert err <= tol, (i, err, tol)
     bs.close()
+
+
+def test_persistent_batch_assembly_equals_one_by_one(B, problems):
+    """bem_assemble_batch (one launch over a global tile queue) writes the same S and N bits
+    as one bem_assemble per problem, on both paths."""
+    bem, _ = B
+    for prec in ("fp64", "mixed"):
+        ss = [bem.Solver(device=0, prec=prec) for _ in problems]
+        bem.assemble_batch(ss, [torch.from_numpy(p.verts) for p in problems], [p.k for p in problems])
+        for p, s in zip(problems, ss):
+            one = bem.Solver(device=0, prec=prec)
+            one.assemble(torch.from_numpy(p.verts).cuda(), p.k, ops="SW")
+            for op in "SW":
+                assert torch.equal(s.matrix(op), one.matrix(op)), (prec, op, p.verts.shape[0])
+            assert s.info()["quad_points"] == one.info()["quad_points"]
+            one.close()
+        for s in ss:
+            s.close()
+
+
+def test_tile_tuner_picks_a_shape_per_bucket_and_stage(B, problems):
+    """autotune_tiles: one (tile width, K splits) per size bucket and stage, among the
+    candidates, chosen by measured kernel time; a batch run with the tuned shapes gives the
+    one-by-one results (split changes only the order of FP64 partial sums)."""
+    bem, batch = B
+    tuned = batch.autotune_tiles(problems, reps=1)
+    buckets = {batch.size_bucket(p.verts.shape[0]) for p in problems}
+    assert set(tuned) == buckets
+    for b, ch in tuned.items():
+        for stage in ("filter", "rhs"):
+            assert (ch[f"{stage}_tile_n"], ch[f"{stage}_split_k"]) in batch.TILE_CANDIDATES[stage]
+            t = ch["times_ms"][stage]
+            assert min(t.values()) == t[f"{ch[f'{stage}_tile_n']}x{ch[f'{stage}_split_k']}"]
+    bs = batch.BatchSolver(problems, prec="mixed", n_streams=2, tiles=tuned)
+    res = bs.run()
+    for p, out in zip(problems, res):
+        x, r = _single(bem, p, "mixed")
+        assert out["rank"] == r
+        assert float((out["x"] - x).abs().max() / x.abs().max()) <= 1e-10
+    bs.close()
