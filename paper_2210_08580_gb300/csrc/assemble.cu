@@ -38,6 +38,8 @@ __constant__ float2 c_pio2_df;
 __constant__ float2 c_gx_df[GL_MAXQ * (GL_MAXQ + 1) / 2];
 __constant__ float2 c_gw0_df[GL_MAXQ * (GL_MAXQ + 1) / 2];
 __constant__ float2 c_gw1_df[GL_MAXQ * (GL_MAXQ + 1) / 2];
+// the q = 2 rule's combination weights 1/12, 1/24, 1/(8 sqrt 3) as double-float pairs
+__constant__ float2 c_q2_df[3];
 
 static float2 host_df(double v) {
     const float hi = (float)v;
@@ -89,6 +91,15 @@ cudaError_t init_gauss_tables() {
     if ((e = cudaMemcpyToSymbol(c_gx_df, fx, sizeof(fx))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_gw0_df, fw0, sizeof(fw0))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_gw1_df, fw1, sizeof(fw1))) != cudaSuccess) return e;
+    {
+        const long double q2[3] = {1.0L / 12.0L, 1.0L / 24.0L, 1.0L / (8.0L * sqrtl(3.0L))};
+        float2 f[3];
+        for (int i = 0; i < 3; ++i) {
+            const float hi = (float)q2[i];
+            f[i] = make_float2(hi, (float)(q2[i] - (long double)hi));
+        }
+        if ((e = cudaMemcpyToSymbol(c_q2_df, f, sizeof(f))) != cudaSuccess) return e;
+    }
     double rc[RCP_MAX];
     rc[0] = 0.0;
     for (int k = 1; k < RCP_MAX; ++k) rc[k] = 1.0 / k;
@@ -687,21 +698,39 @@ __device__ __forceinline__ void gauss_row_df(int o, int i, const cdfl& R0, const
         A[3] = cdfl_fma_real(w1, R1, A[3]);
     }
 }
-// order fixed at compile time (fully unrolled: nodes and weights become constant operands)
-template <int Q>
-__device__ __forceinline__ void pair_gauss_df_q(dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, dfl vfy,
-                                                const float4* __restrict__ tab, cdfl A[4]) {
-    constexpr int o = Q * (Q - 1) / 2;
+// q = 2, the far-field bulk: the four kernel values g_ij (node i on e, j on f) combine with
+// the weights W_0 = (a, b), W_1 = (b, a), a = (1 + 1/sqrt 3)/4, b = (1 - 1/sqrt 3)/4, as
+//   I_00 = X + Y, I_11 = X - Y, I_01 = Z + V, I_10 = Z - V,
+//   X = s/12 + p/24, Z = s/24 + p/12, Y = d/(8 sqrt 3), V = q/(8 sqrt 3),
+// s = g11 + g22, d = g11 - g22, p = g12 + g21, q = g12 - g21 (a^2 + b^2 = 1/6, ab = 1/24,
+// a^2 - b^2 = 1/(4 sqrt 3)); and sum_ab I_ab = (s + p)/4.
+__device__ __forceinline__ void pair_gauss_df_2(dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, dfl vfy,
+                                                const float4* __restrict__ tab, cdfl A[4], cdfl& M0) {
+    cdfl g[2][2];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const dfl s = dfl_mk(c_gx_df[o + i]);
-        const dfl cx = dfl_sub(bx, dfl_mul(s, uex)), cy = dfl_sub(by, dfl_mul(s, uey));
-        cdfl R0, R1;
+    for (int i = 0; i < 2; ++i) {
+        const dfl sn = dfl_mk(c_gx_df[1 + i]);
+        const dfl cx = dfl_sub(bx, dfl_mul(sn, uex)), cy = dfl_sub(by, dfl_mul(sn, uey));
 #pragma unroll
-        for (int j = 0; j < Q; ++j) gauss_point_df(o, j, cx, cy, vfx, vfy, tab, j == 0, R0, R1);
-        gauss_row_df(o, i, R0, R1, i == 0, A);
+        for (int j = 0; j < 2; ++j) {
+            const dfl t = dfl_mk(c_gx_df[1 + j]);
+            const dfl dx = dfl_fma(t, vfx, cx), dy = dfl_fma(t, vfy, cy);
+            g[i][j] = hankel_u_df(tab, dfl_fma(dx, dx, dfl_mul(dy, dy)));
+        }
     }
+    const cdfl sm = cdfl_add(g[0][0], g[1][1]), df = cdfl_sub(g[0][0], g[1][1]);
+    const cdfl pp = cdfl_add(g[0][1], g[1][0]), qq = cdfl_sub(g[0][1], g[1][0]);
+    const dfl c12 = dfl_mk(c_q2_df[0]), c24 = dfl_mk(c_q2_df[1]), c83 = dfl_mk(c_q2_df[2]);
+    const cdfl X = cdfl_fma_real(c24, pp, cdfl_scale(c12, sm)), Z = cdfl_fma_real(c12, pp, cdfl_scale(c24, sm));
+    const cdfl Y = cdfl_scale(c83, df), V = cdfl_scale(c83, qq);
+    A[0] = cdfl_add(X, Y);
+    A[3] = cdfl_sub(X, Y);
+    A[1] = cdfl_add(Z, V);
+    A[2] = cdfl_sub(Z, V);
+    const cdfl t = cdfl_add(sm, pp);
+    M0 = {dfl_scale(t.re, 0.25f), dfl_scale(t.im, 0.25f)};
 }
+
 __device__ void pair_gauss_df(int q, dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, dfl vfy,
                               const float4* __restrict__ tab, cdfl A[4]) {
     const int o = gl_off(q);
@@ -838,10 +867,13 @@ __device__ __forceinline__ void assemble_sn_tile(const AsmParams& p, int L) {
             const int q = q_for_gap_fast(__fdividef(gap, hmax), gap + hmax);
             npts += (unsigned)(q * q);
             cdfl A[4];
-            if (q == 2) pair_gauss_df_q<2>(bx, by, uex, uey, vfx, vfy, p.btabf, A);   // the far-field bulk
-            else pair_gauss_df(q, bx, by, uex, uey, vfx, vfy, p.btabf, A);
+            if (q == 2) {
+                pair_gauss_df_2(bx, by, uex, uey, vfx, vfy, p.btabf, A, M0);   // the far-field bulk
+            } else {
+                pair_gauss_df(q, bx, by, uex, uey, vfx, vfy, p.btabf, A);
+                M0 = cdfl_add(cdfl_add(A[0], A[1]), cdfl_add(A[2], A[3]));
+            }
             const dfl hh = dfl_mul(hx, hy);
-            M0 = cdfl_add(cdfl_add(A[0], A[1]), cdfl_add(A[2], A[3]));
             if (sw) { const cdfl t = A[1]; A[1] = A[2]; A[2] = t; }   // I_ab(e, f) = I_ba(f, e)
             for (int c = 0; c < 4; ++c) I[c] = {dfl_mul(hh, A[c].re), dfl_mul(hh, A[c].im)};
         }
@@ -959,15 +991,27 @@ __device__ __forceinline__ void assemble_sn_tile(const AsmParams& p, int L) {
     // share, summed in a fixed order, goes to the slot of its tile column (its rows) and,
     // mirrored, of its tile row (the columns' sums are the mirror's row sums)
     if (p.kpart) {
+        // two stages: 4 groups of 8 columns (rows' sums) or rows (columns' sums), then the 4
+        // group partials (in sND's space, free now), each in a fixed order
+        float4* part = reinterpret_cast<float4*>(sND);   // [2][4][T]
         const int t = threadIdx.x;
+        if (t < 4 * T || (mirror && t >= 128 && t < 128 + 4 * T)) {
+            const bool col = t >= 128;
+            const int u = col ? t - 128 : t, g = u / T, l = u % T;
+            const int m0 = 8 * g, m1 = min(T, m0 + 8);
+            cdfl acc = cdfl_zero();
+            for (int m = m0; m < m1; ++m) acc = cdfl_add(acc, cdfl_unpack(col ? sK[l * T + m] : sK[m * T + l]));
+            part[(col ? 4 * T : 0) + g * T + l] = cdfl_pack(acc);
+        }
+        __syncthreads();
         if (t < T && i0 + t < N) {
-            cdfl acc = cdfl_unpack(sK[t]);
-            for (int jl = 1; jl < T; ++jl) acc = cdfl_add(acc, cdfl_unpack(sK[jl * T + t]));
+            cdfl acc = cdfl_unpack(part[t]);
+            for (int g = 1; g < 4; ++g) acc = cdfl_add(acc, cdfl_unpack(part[g * T + t]));
             p.kpart[(int64_t)tj * N + i0 + t] = cdfl_to(acc);
         } else if (mirror && t >= 32 && t < 32 + T && j0 + t - 32 < N) {
             const int jl = t - 32;
-            cdfl acc = cdfl_unpack(sK[jl * T]);
-            for (int il = 1; il < T; ++il) acc = cdfl_add(acc, cdfl_unpack(sK[jl * T + il]));
+            cdfl acc = cdfl_unpack(part[4 * T + jl]);
+            for (int g = 1; g < 4; ++g) acc = cdfl_add(acc, cdfl_unpack(part[4 * T + g * T + jl]));
             p.kpart[(int64_t)ti * N + j0 + jl] = cdfl_to(acc);
         }
     }

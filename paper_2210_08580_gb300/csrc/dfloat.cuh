@@ -77,6 +77,8 @@ __device__ __forceinline__ dfl dfl_fma(dfl a, dfl b, dfl c) {
 __device__ __forceinline__ dfl dfl_scale(dfl a, float p2) { return {a.hi * p2, a.lo * p2}; }   // p2 a power of 2
 __device__ __forceinline__ cdfl cdfl_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
 __device__ __forceinline__ cdfl cdfl_add(cdfl a, cdfl b) { return {dfl_add(a.re, b.re), dfl_add(a.im, b.im)}; }
+__device__ __forceinline__ cdfl cdfl_sub(cdfl a, cdfl b) { return {dfl_sub(a.re, b.re), dfl_sub(a.im, b.im)}; }
+__device__ __forceinline__ cdfl cdfl_scale(dfl w, cdfl g) { return {dfl_mul(w, g.re), dfl_mul(w, g.im)}; }   // w g
 __device__ __forceinline__ cdfl cdfl_fma_real(dfl w, cdfl g, cdfl acc) {   // w g + acc
     return {dfl_fma(w, g.re, acc.re), dfl_fma(w, g.im, acc.im)};
 }
