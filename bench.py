@@ -43,7 +43,7 @@ FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 ASM_OPS_PER_POINT = 270
 # DRAM bytes (read + write) per launch from ncu captures of the kernels as they stand
 # (absent = not captured since the kernel last changed); the summaries are under profiles/
-TRAFFIC_BYTES = {"tc_rhs_SY": 14.704e9 + 0.275e9, "k_assemble": 0.0324e9 + 8.687e9}
+TRAFFIC_BYTES = {"k_assemble": 0.0324e9 + 8.687e9}
 
 
 def _peaks():
@@ -86,9 +86,9 @@ def tc_gemm_flops(name, N, nrhs, n_modes, r, S):
     if name not in dims:
         return None
     M, Nc, K = dims[name]
-    # planar parts: complex x complex = four real products, complex x real (the real
-    # Fourier basis Q of the filter) = two
-    parts = 2.0 if name == "tc_filter_QtS" else 4.0
+    # real products of the operands' row blocks: complex x complex = three (Gauss's form,
+    # blocks Re, Im, Re + Im), complex x real (the real Fourier basis Q of the filter) = two
+    parts = 2.0 if name == "tc_filter_QtS" else 3.0
     return S * (S + 1) / 2 * 2.0 * parts * M * Nc * K
 
 

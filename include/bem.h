@@ -98,6 +98,11 @@ typedef struct {
     int filter_split_k;       /*   K splits of the filter products (0 = the cost model's)     */
     int rhs_tile_n;           /*   tile width of the right-hand-side product (0 = automatic)  */
     int rhs_split_k;          /*   K splits of the right-hand-side product (0 = cost model)  */
+    int asm_tile;             /* S/N assembly (both paths, ops without D): vertex tile edge T
+                                 of one CTA, 15, 23 or 31 (0 = the default, 31).  Smaller
+                                 tiles hold fewer segment pairs in shared memory, so more CTAs
+                                 share an SM, at (T+1)^2/T^2 pairs per entry; any other value
+                                 makes bem_create return BEM_E_INVALID                      */
 } bem_options;
 
 typedef struct {

@@ -36,7 +36,7 @@ class BemOptions(ctypes.Structure):
                 ("refine_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("split_slices", ctypes.c_int), ("rhs_slices", ctypes.c_int), ("solve_slices", ctypes.c_int),
                 ("filter_tile_n", ctypes.c_int), ("filter_split_k", ctypes.c_int), ("rhs_tile_n", ctypes.c_int),
-                ("rhs_split_k", ctypes.c_int)]
+                ("rhs_split_k", ctypes.c_int), ("asm_tile", ctypes.c_int)]
 
 
 class BemInfo(ctypes.Structure):
@@ -165,7 +165,8 @@ class Solver:
         """memory: "torch" (default) -- every device buffer of the handle comes from
         PyTorch's caching allocator through the bem_create hooks; "cuda" -- the library
         allocates with the CUDA runtime itself.  tiles: optional tile shapes of the mixed
-        path's products, {"filter_tile_n", "filter_split_k", "rhs_tile_n", "rhs_split_k"}."""
+        path's products, {"filter_tile_n", "filter_split_k", "rhs_tile_n", "rhs_split_k"},
+        and the assembly's vertex tile edge {"asm_tile": 15 | 23 | 31}."""
         self.L = load_library()
         self.device = torch.device("cuda", device)
         opt = BemOptions()
@@ -177,7 +178,7 @@ class Solver:
         opt.split_slices = split_slices
         opt.rhs_slices = rhs_slices
         opt.solve_slices = solve_slices
-        for key in ("filter_tile_n", "filter_split_k", "rhs_tile_n", "rhs_split_k"):
+        for key in ("filter_tile_n", "filter_split_k", "rhs_tile_n", "rhs_split_k", "asm_tile"):
             if tiles and key in tiles:
                 setattr(opt, key, int(tiles[key]))
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -144,6 +144,7 @@ void bem_default_options(bem_options* opt) {
     opt->filter_split_k = 0;
     opt->rhs_tile_n = 0;
     opt->rhs_split_k = 0;
+    opt->asm_tile = 0;
 }
 
 bem_status bem_create(bem_handle* out, int device, void* cuda_stream, const bem_options* opt,
@@ -160,6 +161,10 @@ bem_status bem_create(bem_handle* out, int device, void* cuda_stream, const bem_
     if (h->opt.prec != BEM_FP64 && h->opt.prec != BEM_MIXED_BF16) { delete h; return BEM_E_INVALID; }
     if (h->opt.refine_rtol <= 0.0) h->opt.refine_rtol = 1e-10;
     if (h->opt.max_refine < 0) h->opt.max_refine = 0;
+    if (h->opt.asm_tile != 0 && h->opt.asm_tile != 15 && h->opt.asm_tile != 23 && h->opt.asm_tile != 31) {
+        delete h;
+        return BEM_E_INVALID;
+    }
     h->device = device;
     h->stream = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaSetDevice(device);
@@ -195,7 +200,7 @@ static void free_stage_buffers(bem_ctx* h, int from_stage) {
     if (from_stage > 1) return;
     free_ptr(h, (void**)&h->S); free_ptr(h, (void**)&h->W); free_ptr(h, (void**)&h->D);
     free_ptr(h, (void**)&h->rexp); h->rexp_valid = false;
-    free_ptr(h, (void**)&h->k1); free_ptr(h, (void**)&h->kpart); h->k1_valid = false;
+    free_ptr(h, (void**)&h->k1); free_ptr(h, (void**)&h->kpart); h->kpart_slots = 0; h->k1_valid = false;
     free_ptr(h, (void**)&h->seg);
     tc_release_operands(h);
     free_ptr(h, (void**)&h->B); free_ptr(h, (void**)&h->gm); free_ptr(h, (void**)&h->Q);

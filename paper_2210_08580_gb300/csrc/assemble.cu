@@ -1045,16 +1045,31 @@ __device__ __forceinline__ void assemble_sn_tile(const AsmParams& p, int L) {
 
 static_assert(sizeof(AsmParams) % 4 == 0, "AsmParams is copied to shared memory in 4-byte words");
 
+// Shared memory of one S/N tile of edge T: (T+1)^2 segment pairs (four integrals, the mean,
+// k^2 nu_e . nu_f), the staged geometry and the entries' k^2 terms.  107 KB at T = 31 admits
+// two CTAs per SM, 62 KB at T = 23 three and 28 KB at T = 15 four.  The smaller tiles are
+// compiled for that many CTAs (at most 85 and 64 registers per thread); T = 31 is left to
+// the compiler's choice (108 registers, two CTAs).
+__host__ __device__ constexpr size_t asm_sn_smem(int T) {
+    return (size_t)(T + 1) * (T + 1) * (4 * sizeof(float4) + sizeof(float4) + sizeof(float2)) +
+           (size_t)16 * (T + 1) * sizeof(float2) + (size_t)T * T * sizeof(float4);
+}
+__host__ __device__ constexpr int asm_min_blocks(int T) { return T <= 15 ? 4 : (T <= 23 ? 3 : 1); }
+#define ASM_TILE_DEFAULT 31
+static int asm_tile_of(const bem_ctx* h) { return h->opt.asm_tile ? h->opt.asm_tile : ASM_TILE_DEFAULT; }
+
 // one CTA per tile of one problem
 template <int T>
-__global__ void __launch_bounds__(256) k_assemble_sn(AsmParams p) { assemble_sn_tile<T>(p, (int)blockIdx.x); }
+__global__ void __launch_bounds__(256, asm_min_blocks(T)) k_assemble_sn(AsmParams p) {
+    assemble_sn_tile<T>(p, (int)blockIdx.x);
+}
 
 // Many problems in one launch: persistent CTAs take tiles from one global queue (an atomic
 // counter over the problems' tiles in order, the problems sorted largest first by the caller
 // and each one's tiles diagonal-first), so small problems fill the GPU behind large ones.
 // first[q] is the queue position of problem q's first tile; the tiles need no waits.
 template <int T>
-__global__ void __launch_bounds__(256) k_assemble_sn_batch(const AsmParams* __restrict__ ps,
+__global__ void __launch_bounds__(256, asm_min_blocks(T)) k_assemble_sn_batch(const AsmParams* __restrict__ ps,
                                                            const long long* __restrict__ first, int nprob,
                                                            long long total, unsigned long long* queue) {
     __shared__ AsmParams sp;
@@ -1250,9 +1265,7 @@ __global__ void k_sum_slots(const double2* __restrict__ kpart, int nslots, int N
 
 template <int T>
 static bem_status run_assemble_sn(bem_ctx* h, AsmParams& p) {
-    constexpr int TP = T + 1;
-    const size_t smem = (size_t)TP * TP * (4 * sizeof(float4) + sizeof(float4) + sizeof(float2)) +
-                        (size_t)16 * TP * sizeof(float2) + (size_t)T * T * sizeof(float4);
+    const size_t smem = asm_sn_smem(T);
     BEM_CUDA(h, cudaFuncSetAttribute(k_assemble_sn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     p.nT = (p.N + T - 1) / T;
     const unsigned grid = (unsigned)((int64_t)p.nT * (p.nT + 1) / 2);
@@ -1267,7 +1280,7 @@ static bem_status run_assemble_sn(bem_ctx* h, AsmParams& p) {
 
 // Tables, near-pair integrals and output buffers of one assembly on h's stream; *near is a
 // stream-ordered temporary the caller frees (asm_finish) after the tiles have run.
-static bem_status asm_prepare(bem_ctx* h, unsigned ops, AsmParams& p, cplx** near_out) {
+static bem_status asm_prepare(bem_ctx* h, unsigned ops, AsmParams& p, cplx** near_out, int T) {
     p.N = (int)h->N;
     p.k = h->k;
     p.seg = h->seg;
@@ -1299,9 +1312,17 @@ static bem_status asm_prepare(bem_ctx* h, unsigned ops, AsmParams& p, cplx** nea
     if (!(ops & BEM_OP_D)) {
         // N's row sums (exact: those of its k^2 term), per tile slot, for the filter's
         // constant-vector correction
-        const int64_t nT = (h->N + 30) / 31;
+        const int64_t nT = (h->N + T - 1) / T;
         if (!h->k1) BEM_CUDA(h, bem_dmalloc(h, (void**)&h->k1, sizeof(cplx) * (size_t)h->N));
-        if (!h->kpart) BEM_CUDA(h, bem_dmalloc(h, (void**)&h->kpart, sizeof(double2) * (size_t)nT * h->N));
+        if (h->kpart && h->kpart_slots < nT) {
+            bem_dfree(h, h->kpart);
+            h->kpart = nullptr;
+            h->kpart_slots = 0;
+        }
+        if (!h->kpart) {
+            BEM_CUDA(h, bem_dmalloc(h, (void**)&h->kpart, sizeof(double2) * (size_t)nT * h->N));
+            h->kpart_slots = nT;
+        }
         p.kpart = h->kpart;
     }
     if (!(ops & BEM_OP_D) && h->opt.prec == BEM_MIXED_BF16) {
@@ -1323,22 +1344,27 @@ static void asm_finish(bem_ctx* h, const AsmParams& p, cplx* near, bem_status st
 bem_status launch_assemble(bem_ctx* h, unsigned ops) {
     AsmParams p;
     cplx* near = nullptr;
-    bem_status st = asm_prepare(h, ops, p, &near);
-    if (st == BEM_OK) st = (ops & BEM_OP_D) ? run_assemble<15, true>(h, p) : run_assemble_sn<31>(h, p);
+    const int T = (ops & BEM_OP_D) ? 15 : asm_tile_of(h);
+    bem_status st = asm_prepare(h, ops, p, &near, T);
+    if (st == BEM_OK) {
+        if (ops & BEM_OP_D) st = run_assemble<15, true>(h, p);
+        else if (T == 15) st = run_assemble_sn<15>(h, p);
+        else if (T == 23) st = run_assemble_sn<23>(h, p);
+        else st = run_assemble_sn<31>(h, p);
+    }
     asm_finish(h, p, near, st);
     return st;
 }
 
-// S and N of several problems (one device, each handle on its own stream) with one
-// persistent launch over a global tile queue, on hs[0]'s stream; synchronises that stream.
-bem_status launch_assemble_batch(bem_ctx** hs, int nprob) {
-    constexpr int T = 31, TP = T + 1;
+// The batched assembly with tile edge T (launch_assemble_batch below).
+template <int T>
+static bem_status assemble_batch_tiles(bem_ctx** hs, int nprob) {
     bem_ctx* h0 = hs[0];
     std::vector<AsmParams> ps(nprob);
     std::vector<cplx*> nears(nprob, nullptr);
     bem_status st = BEM_OK;
     for (int q = 0; q < nprob && st == BEM_OK; ++q) {
-        st = asm_prepare(hs[q], BEM_OP_S | BEM_OP_W, ps[q], &nears[q]);
+        st = asm_prepare(hs[q], BEM_OP_S | BEM_OP_W, ps[q], &nears[q], T);
         ps[q].nT = (ps[q].N + T - 1) / T;
     }
     // the largest problems' tiles first
@@ -1380,8 +1406,7 @@ bem_status launch_assemble_batch(bem_ctx** hs, int nprob) {
         cudaMemcpyAsync(dps, sorted.data(), sizeof(AsmParams) * nprob, cudaMemcpyHostToDevice, h0->stream);
         cudaMemcpyAsync(dfirst, first.data(), sizeof(long long) * nprob, cudaMemcpyHostToDevice, h0->stream);
         cudaMemsetAsync(queue, 0, sizeof(unsigned long long), h0->stream);
-        const size_t smem = (size_t)TP * TP * (4 * sizeof(float4) + sizeof(float4) + sizeof(float2)) +
-                            (size_t)16 * TP * sizeof(float2) + (size_t)T * T * sizeof(float4);
+        const size_t smem = asm_sn_smem(T);
         cudaError_t e = cudaFuncSetAttribute(k_assemble_sn_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per = 0, nsm = 0;
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_assemble_sn_batch<T>, 256, smem);
@@ -1413,6 +1438,16 @@ bem_status launch_assemble_batch(bem_ctx** hs, int nprob) {
     for (size_t i = 0; i + 1 < evs.size(); ++i) hs[i + 1]->evpool.push_back(evs[i]);
     if (!evs.empty()) h0->evpool.push_back(evs.back());
     return st;
+}
+
+// S and N of several problems (one device, each handle on its own stream) with one
+// persistent launch over a global tile queue, on hs[0]'s stream; synchronises that stream.
+// The tile edge is the first handle's.
+bem_status launch_assemble_batch(bem_ctx** hs, int nprob) {
+    const int T = asm_tile_of(hs[0]);
+    if (T == 15) return assemble_batch_tiles<15>(hs, nprob);
+    if (T == 23) return assemble_batch_tiles<23>(hs, nprob);
+    return assemble_batch_tiles<31>(hs, nprob);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -102,6 +102,7 @@ struct bem_ctx {
     bool rexp_valid = false;          // rexp belongs to the S, W now held
     cplx* k1 = nullptr;               // N: row sums of N (its k^2 term's, exact in Maue's form)
     double2* kpart = nullptr;         // per-tile partials of k1 (tile slots x N)
+    int64_t kpart_slots = 0;          // tile slots kpart holds
     bool k1_valid = false;            // k1 belongs to the N now held
     std::map<void**, size_t> caps;   // bytes allocated behind each stage buffer (reused while large enough)
 

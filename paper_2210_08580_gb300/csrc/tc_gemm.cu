@@ -156,6 +156,13 @@ struct TcGemmArgs {
     int* err;
     int kps;                 // K' blocks per split (blockIdx.y); == nkb without split
     double2* part;           // split partials [split][j][i] (M x m each), or null
+    // blocked products (zmode 1): A and B hold real row blocks (Re, Im, Re + Im of a complex
+    // operand, or one real block); product z = blockIdx.z multiplies row block zA[z] of A
+    // by row block zB[z] of B (rows per block Ml and ml) and writes its real result, scaled,
+    // to outr[((z splits + split) ml + j) Ml + i]; the caller combines the products
+    int zmode;
+    int zA[3], zB[3];
+    double* outr;
 };
 
 template <int S, int BN>
@@ -186,6 +193,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int kb0 = blockIdx.y * p.kps;
     const int nkb = min(p.nkb - kb0, p.kps);
     const int nchunks = (nkb + TC_CHUNK_KB - 1) / TC_CHUNK_KB;
+    // first row of this product's blocks in the A and B maps (blocked products)
+    const int rowA = p.zmode ? p.zA[blockIdx.z] * p.Ml : 0;
+    const int rowB = p.zmode ? p.zB[blockIdx.z] * p.ml : 0;
 
     if (threadIdx.x == 0) {
         mbar_init(&full[0], 1); mbar_init(&full[1], 1);
@@ -215,9 +225,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 unsigned char* base = smem + st * stage_bytes;
                 mbar_expect_tx(&full[st], stage_tx);
                 for (int s = 0; s < S; ++s)
-                    tma_load_3d(base + s * TC_TILE_BYTES, &mapA, &full[st], (kb0 + kb) * TC_BK, m0, s);
+                    tma_load_3d(base + s * TC_TILE_BYTES, &mapA, &full[st], (kb0 + kb) * TC_BK, m0 + rowA, s);
                 for (int t = 0; t < S; ++t)
-                    tma_load_3d(base + (S + t) * TC_TILE_BYTES, &mapB, &full[st], (kb0 + kb) * TC_BK, n0, t);
+                    tma_load_3d(base + (S + t) * TC_TILE_BYTES, &mapB, &full[st], (kb0 + kb) * TC_BK, n0 + rowB, t);
                 kb_issued = kb + 1;
             }
             // on an early exit, let the copies already issued land before the CTA ends
@@ -313,7 +323,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if constexpr (BN == 128) ok = drain(std::integral_constant<int, 4>{});
         else ok = (half == 0) ? drain(std::integral_constant<int, 4>{}) : drain(std::integral_constant<int, (BN - 64) / 16>{});
         asm volatile("bar.sync 1, 256;" ::: "memory");          // the 8 epilogue warps
-        if (ok) {
+        if (ok && p.zmode) {
+            // one real product: the tile's values, scaled by 2^(e_i + f_j - 14) of its blocks
+            const int et = threadIdx.x - 64;
+            const int z = blockIdx.z;
+            const int* ea = p.ea + (int64_t)p.zA[z] * p.Ml;
+            const int* eb = p.eb + (int64_t)p.zB[z] * p.ml;
+            double* o = p.outr + (int64_t)(z * gridDim.y + blockIdx.y) * p.ml * p.Ml;
+            const int nlr = min(TC_BM, p.Ml - m0), nlc = min(BN, p.ml - n0);
+#pragma unroll 1
+            for (int idx = et; idx < TC_BM * BN; idx += 256) {
+                const int lr = idx % TC_BM, lc = idx / TC_BM;
+                if (lr >= nlr || lc >= nlc) continue;
+                const float2 v = stash[lr * (BN + 1) + lc];
+                const int gi = m0 + lr, gj = n0 + lc;
+                const long long sh = (long long)(ea[gi] + eb[gj] - 14) << 52;
+                const long long b = __double_as_longlong(dfl_to(dfl{v.x, v.y}));
+                o[(int64_t)gj * p.Ml + gi] = (b & 0x7FF0000000000000LL) ? __longlong_as_double(b + sh) : 0.0;
+            }
+        } else if (ok) {
             // combine the part products: complex A and B: re = RR - II, im = RI + IR; one
             // complex operand: its two part rows (or columns) are re and im
             const int et = threadIdx.x - 64;                       // 0..255
@@ -539,8 +567,14 @@ __device__ __forceinline__ void slice_part(Get v, int e, int S, __nv_bfloat16* o
 // Contiguous complex rows (unit stride along k): the warp reads its 32 * SLICE_VEC values
 // coalesced (one 512-byte run per load) into shared memory, then each lane takes SLICE_VEC
 // consecutive values.  One pad slot per 8 keeps both phases free of bank conflicts.
-__global__ void __launch_bounds__(256, 4) k_slice_A_rows(const double2* src, int conj, int64_t M, int64_t K, int64_t Kp,
-                                                   int64_t sa_i, int band, const int* e, int S, __nv_bfloat16* out) {
+// BLOCKS 0: part rows 2i (Re) and 2i+1 (Im); BLOCKS 3: row blocks [Re; Im; Re + Im] of M
+// rows each, block b of row i scaled by e[b M + i], the sum block with its leading S3 <= S
+// slices only (the products that use it take no more; the rest of its slices stay unwritten)
+template <int BLOCKS>
+__global__ void __launch_bounds__(256, BLOCKS ? 3 : 4) k_slice_A_rows(const double2* src, int conj, int64_t M, int64_t K,
+                                                                    int64_t Kp, int64_t sa_i, int band, const int* e,
+                                                                    int S, __nv_bfloat16* out, int S3) {
+    constexpr int blocks = BLOCKS;
     const int64_t i = blockIdx.y;
     __shared__ double2 stage[8][32 * SLICE_VEC + 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -557,14 +591,22 @@ __global__ void __launch_bounds__(256, 4) k_slice_A_rows(const double2* src, int
     __syncwarp();
     const int64_t k0 = kw + lane * SLICE_VEC;
     if (k0 >= Kp) return;
-    const int ei = e[i];
-    const size_t stride = (size_t)(2 * M) * Kp;
-    // real parts, then imaginary parts, each value read from shared memory when it is split
+    const size_t stride = (size_t)((blocks ? blocks : 2) * M) * Kp;
+    // real parts, then imaginary parts (then their sums), each value read from shared
+    // memory when it is split
     const double2* st = stage[w];
-    slice_part([&](int u) { const int q = lane * SLICE_VEC + u; return st[q + (q >> 3)].x; }, ei, S, out, 2 * i, Kp,
-               k0, stride);
+    const int64_t rre = blocks ? i : 2 * i, rim = blocks ? M + i : 2 * i + 1;
+    slice_part([&](int u) { const int q = lane * SLICE_VEC + u; return st[q + (q >> 3)].x; }, e[i], S, out,
+               rre, Kp, k0, stride);
     slice_part([&](int u) { const int q = lane * SLICE_VEC + u; const double y = st[q + (q >> 3)].y; return conj ? -y : y; },
-               ei, S, out, 2 * i + 1, Kp, k0, stride);
+               e[blocks ? M + i : i], S, out, rim, Kp, k0, stride);
+    if (BLOCKS == 3)
+        slice_part([&](int u) {
+                       const int q = lane * SLICE_VEC + u;
+                       const double2 x = st[q + (q >> 3)];
+                       return x.x + (conj ? -x.y : x.y);
+                   },
+                   e[2 * M + i], S3, out, 2 * M + i, Kp, k0, stride);
 }
 
 __global__ void k_slice_A(const void* src, int is_real, int conj, int64_t M, int64_t K, int64_t Kp, int64_t sa_i,
@@ -593,8 +635,9 @@ __global__ void k_slice_A(const void* src, int is_real, int conj, int64_t M, int
     if (!is_real) slice_part([&](int u) { return im[u]; }, ei, S, out, 2 * i + 1, Kp, k0, stride);
 }
 
+// blocks as in k_slice_A_rows, by columns (complex B only)
 __global__ void k_slice_B(const void* src, int is_real, int64_t K, int64_t m, int64_t Kp, int64_t sb_k,
-                          int64_t sb_j, const int* f, int S, __nv_bfloat16* out) {
+                          int64_t sb_j, const int* f, int S, __nv_bfloat16* out, int blocks) {
     const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * SLICE_VEC;
     const int64_t j = blockIdx.y;
     if (k0 >= Kp || j >= m) return;
@@ -609,10 +652,27 @@ __global__ void k_slice_B(const void* src, int is_real, int64_t K, int64_t m, in
             else { const double2 x = ((const double2*)src)[k * sb_k + j * sb_j]; re[u] = x.x; im[u] = x.y; }
         }
     }
+    if (blocks) {
+        const size_t stride = (size_t)(blocks * m) * Kp;
+        slice_part([&](int u) { return re[u]; }, fe, S, out, j, Kp, k0, stride);
+        slice_part([&](int u) { return im[u]; }, f[m + j], S, out, m + j, Kp, k0, stride);
+        if (blocks == 3) slice_part([&](int u) { return re[u] + im[u]; }, f[2 * m + j], S, out, 2 * m + j, Kp, k0, stride);
+        return;
+    }
     const int64_t rows = is_real ? m : 2 * m;
     const size_t stride = (size_t)rows * Kp;
     slice_part([&](int u) { return re[u]; }, fe, S, out, is_real ? j : 2 * j, Kp, k0, stride);
     if (!is_real) slice_part([&](int u) { return im[u]; }, fe, S, out, 2 * j + 1, Kp, k0, stride);
+}
+
+// exponents of the row blocks from those of the complex rows (e[0..M)): the Re and Im
+// blocks keep e_i (max(|Re|, |Im|) < 2^e_i), the sum block takes e_i + 1 (|Re + Im| < 2^(e_i + 1))
+__global__ void k_exp_blocks(int* e, int64_t M, int blocks) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int v = e[i];
+    e[M + i] = v;
+    if (blocks == 3) e[2 * M + i] = v + 1;
 }
 
 // ------------------------------------------------------------------------------ host side
@@ -643,7 +703,20 @@ struct TcOperand {
     int cplx = 1;                     // complex operand: real and imaginary parts in separate rows
     int64_t lrows = 0;                // logical rows (A) / columns (B): rows = (cplx ? 2 : 1) lrows
     int nslices = 0;                  // slices the map spans
+    int blocks = 0;                   // 0: part rows (above); 2, 3: real row blocks of lrows rows
+                                      // each (Re, Im, and Re + Im for 3), cplx = 0
+    int s3 = 0;                       // slices the Re + Im block holds (A operands)
     CUtensorMap map;
+};
+
+// The real products of blocked operands that make one complex product: product z
+// multiplies row block zA[z] of A by row block zB[z] of B; gauss = 1 combines three as
+// C = (P0 - P1) + i (P2 - P0 - P1) (Gauss's three-multiplication form, A and B blocked
+// [Re; Im; Re + Im]), gauss = 0 two as C = P0 + i P1 (A blocked [Re; Im], B real).
+struct TcBlocks {
+    int nz;
+    int zA[3], zB[3];
+    int gauss;
 };
 
 struct TcState {
@@ -654,6 +727,8 @@ struct TcState {
     TcOperand tmpA;                   // A operand scratch (reused)
     double2* part = nullptr;          // split-K partials
     size_t part_cap = 0;
+    double* zbuf = nullptr;           // real products of the blocked path
+    size_t zbuf_cap = 0;
 };
 
 static TcState* tcs(bem_ctx* h) {
@@ -705,14 +780,21 @@ static bem_status reserve(bem_ctx* h, TcOperand& op, int64_t rows, int64_t Kp, i
 
 // A operand: rows M, K complex columns, A_op[i,k] = src[i*sa_i + k*sa_k]; band >= 0 drops
 // the cyclic band |i - k| <= band (square operators)
+// blocks 2 or 3: real row blocks [Re; Im] or [Re; Im; Re + Im] (complex rows with unit
+// stride along k only)
 static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k,
-                          int band = -1, int is_real = 0, int conj = 0, const int* fields = nullptr) {
+                          int band = -1, int is_real = 0, int conj = 0, const int* fields = nullptr, int blocks = 0,
+                          int S3 = 0) {
     const int S = tcs(h)->S;
     const int64_t Kp = pad32(K);
-    bem_status st = reserve(h, op, is_real ? M : 2 * M, Kp, S);
+    if (blocks && (is_real || sa_k != 1 || blocks != 3 || S3 < 1 || S3 > S))
+        return bem_fail(h, BEM_E_INVALID, "slice_A: row blocks need complex rows with unit stride");
+    bem_status st = reserve(h, op, blocks ? blocks * M : (is_real ? M : 2 * M), Kp, S);
     if (st != BEM_OK) return st;
     op.K = K;
-    op.cplx = is_real ? 0 : 1;
+    op.cplx = (is_real || blocks) ? 0 : 1;
+    op.blocks = blocks;
+    op.s3 = blocks == 3 ? S3 : S;
     op.lrows = M;
     if (fields) {
         BEM_TIMED(h, "k_exp_rows", (k_exp_from_fields<<<(unsigned)((M + 255) / 256), 256, 0, h->stream>>>(fields, M, op.exps)));
@@ -720,9 +802,15 @@ static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M,
         BEM_TIMED(h, "k_exp_rows", (k_exp_rows<<<(unsigned)((M + 7) / 8), 256, 0, h->stream>>>(src, is_real, M, K, sa_i, sa_k, band, op.exps)));
     }
     BEM_LAUNCH(h, "k_exp_rows");
+    if (blocks) {
+        BEM_TIMED(h, "k_exp_rows", (k_exp_blocks<<<(unsigned)((M + 255) / 256), 256, 0, h->stream>>>(op.exps, M, blocks)));
+        BEM_LAUNCH(h, "k_exp_blocks");
+    }
     dim3 grid((unsigned)((Kp / SLICE_VEC + 255) / 256), (unsigned)M);
-    if (!is_real && sa_k == 1)
-        BEM_TIMED(h, "k_slice_A", (k_slice_A_rows<<<grid, 256, 0, h->stream>>>((const double2*)src, conj, M, K, Kp, sa_i, band, op.exps, S, op.slices)));
+    if (blocks)
+        BEM_TIMED(h, "k_slice_A", (k_slice_A_rows<3><<<grid, 256, 0, h->stream>>>((const double2*)src, conj, M, K, Kp, sa_i, band, op.exps, S, op.slices, S3)));
+    else if (!is_real && sa_k == 1)
+        BEM_TIMED(h, "k_slice_A", (k_slice_A_rows<0><<<grid, 256, 0, h->stream>>>((const double2*)src, conj, M, K, Kp, sa_i, band, op.exps, S, op.slices, 0)));
     else
         BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, is_real, conj, M, K, Kp, sa_i, sa_k, band, op.exps, S, op.slices)));
     BEM_LAUNCH(h, "k_slice_A");
@@ -730,19 +818,28 @@ static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M,
 }
 
 // B operand: K x m (complex or real), B_op[k,j] = src[k*sb_k + j*sb_j]
+// (blocks 2 or 3: real row blocks of the columns, as in slice_A; complex B only)
 static bem_status slice_B(bem_ctx* h, TcOperand& op, const void* src, int is_real, int64_t K, int64_t m, int64_t sb_k,
-                          int64_t sb_j, int S_over = 0) {
+                          int64_t sb_j, int S_over = 0, int blocks = 0) {
     const int S = S_over ? S_over : tcs(h)->S;
     const int64_t Kp = pad32(K);
-    bem_status st = reserve(h, op, is_real ? m : 2 * m, Kp, S);
+    if (blocks && (is_real || blocks < 2 || blocks > 3))
+        return bem_fail(h, BEM_E_INVALID, "slice_B: row blocks need a complex operand");
+    bem_status st = reserve(h, op, blocks ? blocks * m : (is_real ? m : 2 * m), Kp, S);
     if (st != BEM_OK) return st;
     op.K = K;
-    op.cplx = is_real ? 0 : 1;
+    op.cplx = (is_real || blocks) ? 0 : 1;
+    op.blocks = blocks;
+    op.s3 = S;
     op.lrows = m;
     BEM_TIMED(h, "k_exp_cols", (k_exp_cols<<<(unsigned)m, 256, 0, h->stream>>>(src, is_real, K, m, sb_k, sb_j, op.exps)));
     BEM_LAUNCH(h, "k_exp_cols");
+    if (blocks) {
+        BEM_TIMED(h, "k_exp_cols", (k_exp_blocks<<<(unsigned)((m + 255) / 256), 256, 0, h->stream>>>(op.exps, m, blocks)));
+        BEM_LAUNCH(h, "k_exp_blocks");
+    }
     dim3 grid((unsigned)((Kp / SLICE_VEC + 255) / 256), (unsigned)m);
-    BEM_TIMED(h, "k_slice_B", (k_slice_B<<<grid, 256, 0, h->stream>>>(src, is_real, K, m, Kp, sb_k, sb_j, op.exps, S, op.slices)));
+    BEM_TIMED(h, "k_slice_B", (k_slice_B<<<grid, 256, 0, h->stream>>>(src, is_real, K, m, Kp, sb_k, sb_j, op.exps, S, op.slices, blocks)));
     BEM_LAUNCH(h, "k_slice_B");
     return encode_map(h, op, S);
 }
@@ -775,10 +872,35 @@ __global__ void k_splitk_reduce(const double2* __restrict__ part, int splits, in
     *o = val;
 }
 
+// out = alpha C + beta out from the real products of blocked operands (TcBlocks), summed
+// over the K' splits: P[(z splits + s) M m + j M + i]
+__global__ void k_combine_blocks(const double* __restrict__ P, int splits, int gauss, int M, int m, double2* out,
+                                 int64_t ldo, int transposed, double alpha, double beta) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t plane = (int64_t)M * m;
+    if (idx >= plane) return;
+    const int i = (int)(idx % M), j = (int)(idx / M);
+    double pz[3] = {0.0, 0.0, 0.0};
+    const int nz = gauss ? 3 : 2;
+    for (int z = 0; z < nz; ++z)
+        for (int s = 0; s < splits; ++s) pz[z] += P[(int64_t)(z * splits + s) * plane + idx];
+    const double re = gauss ? pz[0] - pz[1] : pz[0];
+    const double im = gauss ? (pz[2] - pz[0]) - pz[1] : pz[1];
+    double2* o = transposed ? (out + (int64_t)j + (int64_t)i * ldo) : (out + (int64_t)i + (int64_t)j * ldo);
+    double2 val = make_double2(alpha * re, alpha * im);
+    if (beta != 0.0) {
+        const double2 old = *o;
+        val.x += beta * old.x;
+        val.y += beta * old.y;
+    }
+    *o = val;
+}
+
 // S_use > 0: multiply with the leading S_use digit slices only (B sliced with S_use, A with
-// at least that many)
+// at least that many).  zb: the complex product as real products of blocked operands
+// (A.blocks > every zA, B blocked likewise or real).
 static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cplx* out, int64_t ldo, int transposed,
-                          double alpha, double beta, const char* tag, int S_use = 0) {
+                          double alpha, double beta, const char* tag, int S_use = 0, const TcBlocks* zb = nullptr) {
     TcState* t = tcs(h);
     if (A.Kp != B.Kp) return bem_fail(h, BEM_E_INVALID, "tc_gemm: K mismatch");
     const int Sg = S_use ? S_use : t->S;
@@ -790,7 +912,27 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     p.ml = (int)B.lrows;
     p.aC = A.cplx;
     p.bC = B.cplx;
-    if (!A.cplx && !B.cplx) return bem_fail(h, BEM_E_INVALID, "tc_gemm: at least one operand must be complex");
+    p.zmode = 0;
+    p.outr = nullptr;
+    const int nz = zb ? zb->nz : 1;
+    if (zb) {
+        if (zb->nz != (zb->gauss ? 3 : 2)) return bem_fail(h, BEM_E_INVALID, "tc_gemm: blocked product count");
+        for (int z = 0; z < nz; ++z) {
+            const int bb = B.blocks ? B.blocks : (B.cplx ? 0 : 1);
+            if (zb->zA[z] < 0 || zb->zA[z] >= A.blocks || zb->zB[z] < 0 || zb->zB[z] >= bb)
+                return bem_fail(h, BEM_E_INVALID, "tc_gemm: operand blocks do not match the products");
+            if ((zb->zA[z] == 2 && Sg > A.s3) || (zb->zB[z] == 2 && Sg > B.s3))
+                return bem_fail(h, BEM_E_INVALID, "tc_gemm: the sum block holds fewer slices");
+            p.zA[z] = zb->zA[z];
+            p.zB[z] = zb->zB[z];
+        }
+        p.zmode = 1;
+        p.M = p.Ml;
+        p.Ncols = p.ml;
+    } else {
+        if (A.blocks || B.blocks) return bem_fail(h, BEM_E_INVALID, "tc_gemm: blocked operands need their products");
+        if (!A.cplx && !B.cplx) return bem_fail(h, BEM_E_INVALID, "tc_gemm: at least one operand must be complex");
+    }
     p.nkb = (int)(A.Kp / TC_BK);
     p.S = Sg;
     p.ea = A.exps;
@@ -838,10 +980,11 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     // fills the GPU for skinny outputs (r x nrhs) and evens out the last wave of large ones.
     int nsm = 0;
     BEM_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    const int T = mt * nt;
+    const int T = mt * nt * nz;
     const int nch = (p.nkb + TC_CHUNK_KB - 1) / TC_CHUNK_KB;
     const double chunk_ms = (double)(Sg * (Sg + 1) / 2) * TC_CHUNK_KB * (TC_BK / 16) * 73.0 / 2.0e6 * BN / 128.0;
-    const double part_ms_per_split = (double)p.Ml * p.ml * 32.0 / 6.0e9;
+    // bytes per output per split written and read back: complex partials, or the real products
+    const double part_ms_per_split = (double)p.Ml * p.ml * (zb ? 16.0 * nz : 32.0) / 6.0e9;
     int splits = 1;
     if (want_split >= 1) {
         // the stage's split count (at most one K' chunk per split, no empty splits)
@@ -858,7 +1001,15 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
             if (cost < 0.98 * best) { best = cost; splits = s; p.kps = cps * TC_CHUNK_KB; }
         }
     }
-    if (splits > 1) {
+    if (zb) {
+        const size_t need = (size_t)nz * splits * p.Ml * p.ml * sizeof(double);
+        if (need > t->zbuf_cap) {
+            if (t->zbuf) { cudaStreamSynchronize(h->stream); bem_dfree(h, t->zbuf); t->zbuf = nullptr; t->zbuf_cap = 0; }
+            BEM_CUDA(h, bem_dmalloc(h, (void**)&t->zbuf, need));
+            t->zbuf_cap = need;
+        }
+        p.outr = t->zbuf;
+    } else if (splits > 1) {
         const size_t need = (size_t)splits * p.Ml * p.ml * sizeof(double2);
         if (need > t->part_cap) {
             if (t->part) { cudaStreamSynchronize(h->stream); bem_dfree(h, t->part); t->part = nullptr; t->part_cap = 0; }
@@ -867,9 +1018,17 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
         }
         p.part = t->part;
     }
-    dim3 grid((unsigned)(mt * nt), (unsigned)splits);
+    dim3 grid((unsigned)(mt * nt), (unsigned)splits, (unsigned)nz);
     BEM_TIMED(h, tag, (kern<<<grid, TC_THREADS, smem, h->stream>>>(A.map, mapB, p)));
     BEM_LAUNCH(h, "k_tc_gemm");
+    if (zb) {
+        const int64_t n = (int64_t)p.Ml * p.ml;
+        BEM_TIMED(h, "k_combine_blocks", (k_combine_blocks<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+                                             p.outr, splits, zb->gauss, p.Ml, p.ml, out, ldo,
+                                             transposed, alpha, beta)));
+        BEM_LAUNCH(h, "k_combine_blocks");
+        return BEM_OK;
+    }
     if (splits > 1) {
         const int64_t n = (int64_t)p.Ml * p.ml;
         BEM_TIMED(h, "k_splitk_reduce", (k_splitk_reduce<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
@@ -880,15 +1039,28 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
 }
 
 // ------------------------------------------------------------------------------ interface
+// digit slices of the right-hand-side product (bem_options.rhs_slices; default one fewer
+// than the operands hold)
+static int rhs_slices(bem_ctx* h) {
+    const int S = tcs(h)->S;
+    const int Sr = h->opt.rhs_slices;
+    return (Sr < 3 || Sr > S) ? std::max(3, S - 1) : Sr;
+}
+
 bem_status tc_prepare_operators(bem_ctx* h) {
     TcState* t = tcs(h);
     const int64_t N = h->N;
     bem_status st;
-    // slices of X^T: row i of the A operand is column i of X (contiguous)
-    // (row exponents from the assembly when it gathered them)
+    // slices of X^T: row i of the A operand is column i of X (contiguous); row exponents
+    // from the assembly when it gathered them.  S as row blocks [Re; Im; Re + Im]: its
+    // product with the right-hand sides (nrhs wide, the largest of the path) then takes
+    // Gauss's three real products instead of four, for one more block written here (with
+    // the right-hand-side product's slices only); Q^T S takes the Re and Im blocks.  N and
+    // D keep the part rows: their products are n wide, where the extra block would cost
+    // about what it saves.
     const int* fS = h->rexp_valid ? h->rexp : nullptr;
     const int* fW = h->rexp_valid ? h->rexp + N : nullptr;
-    if ((st = slice_A(h, t->opS, h->S, N, N, N, 1, -1, 0, 0, fS)) != BEM_OK) return st;
+    if ((st = slice_A(h, t->opS, h->S, N, N, N, 1, -1, 0, 0, fS, 3, rhs_slices(h))) != BEM_OK) return st;
     // N's near band (entries up to ~1e4 x its far field) is applied apart in double-float,
     // so the split only carries the far part with its own, much smaller row scale
     if ((st = slice_A(h, t->opW, h->W, N, N, N, 1, (int)std::min<int64_t>(TC_W_BAND, (N - 1) / 2), 0, 0, fW)) != BEM_OK)
@@ -981,11 +1153,15 @@ bem_status tc_product_left(bem_ctx* h, int op, const double* Qreal, const cplx* 
     const TcOperand* A = op_of(t, op);
     if (!A->slices) return bem_fail(h, BEM_E_INVALID, "tc_product_left: operator not sliced");
     bem_status st;
-    // out^T = X^T L^T: B = Q (N x nc real) or Y^T (B[k, j] = Y[j + k nc])
+    // out^T = X^T L^T: B = Q (N x nc real) or Y^T (B[k, j] = Y[j + k nc]); a blocked A takes
+    // two real products with the real Q (its Re and Im blocks), Gauss's three with Y^T
     if (Qreal) st = slice_B(h, t->bbuf, Qreal, 1, N, nc, 1, N);
-    else st = slice_B(h, t->bbuf, Y, 0, N, nc, nc, 1);
+    else st = slice_B(h, t->bbuf, Y, 0, N, nc, nc, 1, 0, A->blocks ? 3 : 0);
     if (st != BEM_OK) return st;
-    st = tc_gemm(h, *A, t->bbuf, out, nc, 1, 1.0, 0.0, op == TC_OP_S ? "tc_filter_QtS" : (op == TC_OP_W ? "tc_filter_YN" : "tc_filter_QtD"));
+    const TcBlocks zr = {2, {0, 1, 0}, {0, 0, 0}, 0}, zg = {3, {0, 1, 2}, {0, 1, 2}, 1};
+    st = tc_gemm(h, *A, t->bbuf, out, nc, 1, 1.0, 0.0,
+                 op == TC_OP_S ? "tc_filter_QtS" : (op == TC_OP_W ? "tc_filter_YN" : "tc_filter_QtD"), 0,
+                 A->blocks ? (Qreal ? &zr : &zg) : nullptr);
     if (st != BEM_OK || op != TC_OP_W) return st;
     if (!Y) return bem_fail(h, BEM_E_INVALID, "tc_product_left: N needs a complex left factor");
     const int band = (int)std::min<int64_t>(TC_W_BAND, (N - 1) / 2);
@@ -1001,12 +1177,13 @@ bem_status tc_product_right(bem_ctx* h, int op, const cplx* y, int64_t ldy, int6
     TcState* t = tcs(h);
     const TcOperand* A = op_of(t, op);
     if (!A->slices) return bem_fail(h, BEM_E_INVALID, "tc_product_right: operator not sliced");
-    // the right-hand sides take one digit slice fewer by default (see bem_options.rhs_slices)
-    int Sr = h->opt.rhs_slices;
-    if (Sr < 3 || Sr > t->S) Sr = std::max(3, t->S - 1);
-    bem_status st = slice_B(h, t->bbuf, y, 0, h->N, nrhs, 1, ldy, Sr);
+    // the right-hand sides take one digit slice fewer by default (see bem_options.rhs_slices);
+    // a blocked A (S) takes Gauss's three real products
+    const int Sr = rhs_slices(h);
+    bem_status st = slice_B(h, t->bbuf, y, 0, h->N, nrhs, 1, ldy, Sr, A->blocks ? 3 : 0);
     if (st != BEM_OK) return st;
-    return tc_gemm(h, *A, t->bbuf, out, ld, 0, 1.0, 0.0, "tc_rhs_SY", Sr);
+    const TcBlocks zg = {3, {0, 1, 2}, {0, 1, 2}, 1};
+    return tc_gemm(h, *A, t->bbuf, out, ld, 0, 1.0, 0.0, "tc_rhs_SY", Sr, A->blocks ? &zg : nullptr);
 }
 
 bem_status tc_prepare_solve(bem_ctx* h) {
@@ -1137,6 +1314,7 @@ void tc_destroy(bem_ctx* h) {
     free_op(h, t->bbuf);
     free_op(h, t->tmpA);
     bem_dfree(h, t->part);
+    bem_dfree(h, t->zbuf);
     delete t;
     h->tc = nullptr;
 }
