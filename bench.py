@@ -524,13 +524,21 @@ def main():
             e2e_step(it)
         barrier()
         t0 = time.perf_counter()
+        marks = []
         for it in range(args.steps):
             e2e_step(it)
+            marks.append(time.perf_counter())       # host time when the step's work is enqueued
         barrier()
-        e2e_s = reduce_max((time.perf_counter() - t0) / args.steps, dist, dev)
+        t1 = time.perf_counter()
+        e2e_s = reduce_max((t1 - t0) / args.steps, dist, dev)
+        # per-step host intervals (the compression's rank read-back makes each step wait for
+        # the device, so these follow the device's progress up to one step of lag)
+        per = [1000.0 * (b - a) for a, b in zip([t0] + marks[:-1], marks)]
         e2e = {"value": job_value(args.nrhs, world, e2e_s), "unit": "RHS/s",
                "h2d_bytes_per_step": int(vh.numel() * 8 + ah.numel() * 8),
-               "d2h_bytes_per_step": int(xhs[0].numel() * 16)}
+               "d2h_bytes_per_step": int(xhs[0].numel() * 16),
+               "ms_per_step": 1000.0 * e2e_s, "host_ms_per_step_all": [round(v, 3) for v in per],
+               "drain_ms": round(1000.0 * (t1 - marks[-1]), 3) if marks else None}
 
     fp64_cmp = None
     if not args.no_compare_fp64 and args.prec == "mixed":

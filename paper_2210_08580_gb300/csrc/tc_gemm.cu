@@ -541,15 +541,43 @@ __device__ __forceinline__ void split_digits(double val, int e, int S, uint32_t*
 // group never straddles a row) and writes 16 bytes per part row and slice.
 #define SLICE_VEC 8
 // digits of SLICE_VEC values (one part row) packed as bf16 pairs, then one 16-byte store per slice
-template <class Get>
+// The same digits with the slice count SC known at compile time: below the leading digit,
+// the balanced digits of X are the plain base-128 digits of X + 64 (1 + 128 + ... +
+// 128^(SC-2)), less 64 each, and the leading digit is what lies above them (an arithmetic
+// shift), so every digit is one shift, one mask and one subtraction of the biased integer
+// (equal digit for digit to the carry loop above, for every |X| <= 2^(7 SC)).
+template <int SC>
+__device__ __forceinline__ void split_digits_c(double val, int e, uint32_t* d) {
+    const long long b = __double_as_longlong(val);
+    const int E = (int)((b >> 52) & 0x7FF);
+    const int sh = 1075 + e - 7 * SC - E;
+    long long X = 0;
+    if (E != 0 && sh < 63) {
+        const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+        X = (m + (1LL << (sh - 1))) >> sh;
+        if (b < 0) X = -X;
+    }
+    constexpr long long C = 64LL * ((1LL << (7 * (SC - 1))) - 1) / 127;
+    const long long Y = X + C;
+    d[0] = digit_bits((int)(Y >> (7 * (SC - 1))), 0);
+#pragma unroll
+    for (int s = 1; s < SC; ++s) d[s] = digit_bits((int)((Y >> (7 * (SC - 1 - s))) & 127) - 64, s);
+#pragma unroll
+    for (int s = SC; s < TC_SMAX; ++s) d[s] = 0u;
+}
+
+// SC > 0: the slice count is SC (compile time; S is ignored); SC = 0: S at run time
+template <int SC = 0, class Get>
 __device__ __forceinline__ void slice_part(Get v, int e, int S, __nv_bfloat16* out, int64_t row, int64_t Kp,
                                            int64_t k0, size_t stride) {
+    if (SC > 0) S = SC;
     uint32_t w[TC_SMAX][SLICE_VEC / 2];
     uint32_t ev[TC_SMAX];
 #pragma unroll
     for (int u = 0; u < SLICE_VEC; ++u) {
         uint32_t d[TC_SMAX];
-        split_digits(v(u), e, S, d);
+        if constexpr (SC > 0) split_digits_c<SC>(v(u), e, d);
+        else split_digits(v(u), e, S, d);
         // two values' bf16 halves into one word: the even value low, the odd one high
 #pragma unroll
         for (int s = 0; s < TC_SMAX; ++s) {
@@ -570,7 +598,8 @@ __device__ __forceinline__ void slice_part(Get v, int e, int S, __nv_bfloat16* o
 // BLOCKS 0: part rows 2i (Re) and 2i+1 (Im); BLOCKS 3: row blocks [Re; Im; Re + Im] of M
 // rows each, block b of row i scaled by e[b M + i], the sum block with its leading S3 <= S
 // slices only (the products that use it take no more; the rest of its slices stay unwritten)
-template <int BLOCKS>
+// SC, SC3 > 0: the slice counts S and S3 at compile time (the common ones), 0: at run time
+template <int BLOCKS, int SC, int SC3>
 __global__ void __launch_bounds__(256, BLOCKS ? 3 : 4) k_slice_A_rows(const double2* src, int conj, int64_t M, int64_t K,
                                                                     int64_t Kp, int64_t sa_i, int band, const int* e,
                                                                     int S, __nv_bfloat16* out, int S3) {
@@ -596,12 +625,12 @@ __global__ void __launch_bounds__(256, BLOCKS ? 3 : 4) k_slice_A_rows(const doub
     // memory when it is split
     const double2* st = stage[w];
     const int64_t rre = blocks ? i : 2 * i, rim = blocks ? M + i : 2 * i + 1;
-    slice_part([&](int u) { const int q = lane * SLICE_VEC + u; return st[q + (q >> 3)].x; }, e[i], S, out,
+    slice_part<SC>([&](int u) { const int q = lane * SLICE_VEC + u; return st[q + (q >> 3)].x; }, e[i], S, out,
                rre, Kp, k0, stride);
-    slice_part([&](int u) { const int q = lane * SLICE_VEC + u; const double y = st[q + (q >> 3)].y; return conj ? -y : y; },
+    slice_part<SC>([&](int u) { const int q = lane * SLICE_VEC + u; const double y = st[q + (q >> 3)].y; return conj ? -y : y; },
                e[blocks ? M + i : i], S, out, rim, Kp, k0, stride);
     if (BLOCKS == 3)
-        slice_part([&](int u) {
+        slice_part<SC3>([&](int u) {
                        const int q = lane * SLICE_VEC + u;
                        const double2 x = st[q + (q >> 3)];
                        return x.x + (conj ? -x.y : x.y);
@@ -780,6 +809,22 @@ static bem_status reserve(bem_ctx* h, TcOperand& op, int64_t rows, int64_t Kp, i
 
 // A operand: rows M, K complex columns, A_op[i,k] = src[i*sa_i + k*sa_k]; band >= 0 drops
 // the cyclic band |i - k| <= band (square operators)
+// k_slice_A_rows with the slice counts of the defaults (6 per operand, 5 for the
+// right-hand-side product) compiled in, any other at run time
+static void launch_slice_rows(int blocks, const double2* src, int conj, int64_t M, int64_t K, int64_t Kp, int64_t sa_i,
+                              int band, const int* e, int S, __nv_bfloat16* out, int S3, dim3 grid, cudaStream_t st) {
+    if (blocks) {
+        if (S == 6 && S3 == 5) k_slice_A_rows<3, 6, 5><<<grid, 256, 0, st>>>(src, conj, M, K, Kp, sa_i, band, e, S, out, S3);
+        else if (S == 6 && S3 == 6) k_slice_A_rows<3, 6, 6><<<grid, 256, 0, st>>>(src, conj, M, K, Kp, sa_i, band, e, S, out, S3);
+        else if (S == 5 && S3 == 5) k_slice_A_rows<3, 5, 5><<<grid, 256, 0, st>>>(src, conj, M, K, Kp, sa_i, band, e, S, out, S3);
+        else k_slice_A_rows<3, 0, 0><<<grid, 256, 0, st>>>(src, conj, M, K, Kp, sa_i, band, e, S, out, S3);
+    } else {
+        if (S == 6) k_slice_A_rows<0, 6, 0><<<grid, 256, 0, st>>>(src, conj, M, K, Kp, sa_i, band, e, S, out, 0);
+        else if (S == 5) k_slice_A_rows<0, 5, 0><<<grid, 256, 0, st>>>(src, conj, M, K, Kp, sa_i, band, e, S, out, 0);
+        else k_slice_A_rows<0, 0, 0><<<grid, 256, 0, st>>>(src, conj, M, K, Kp, sa_i, band, e, S, out, 0);
+    }
+}
+
 // blocks 2 or 3: real row blocks [Re; Im] or [Re; Im; Re + Im] (complex rows with unit
 // stride along k only)
 static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M, int64_t K, int64_t sa_i, int64_t sa_k,
@@ -807,10 +852,9 @@ static bem_status slice_A(bem_ctx* h, TcOperand& op, const void* src, int64_t M,
         BEM_LAUNCH(h, "k_exp_blocks");
     }
     dim3 grid((unsigned)((Kp / SLICE_VEC + 255) / 256), (unsigned)M);
-    if (blocks)
-        BEM_TIMED(h, "k_slice_A", (k_slice_A_rows<3><<<grid, 256, 0, h->stream>>>((const double2*)src, conj, M, K, Kp, sa_i, band, op.exps, S, op.slices, S3)));
-    else if (!is_real && sa_k == 1)
-        BEM_TIMED(h, "k_slice_A", (k_slice_A_rows<0><<<grid, 256, 0, h->stream>>>((const double2*)src, conj, M, K, Kp, sa_i, band, op.exps, S, op.slices, 0)));
+    if (blocks || (!is_real && sa_k == 1))
+        BEM_TIMED(h, "k_slice_A", (launch_slice_rows(blocks, (const double2*)src, conj, M, K, Kp, sa_i, band, op.exps, S,
+                                                     op.slices, S3, grid, h->stream)));
     else
         BEM_TIMED(h, "k_slice_A", (k_slice_A<<<grid, 256, 0, h->stream>>>(src, is_real, conj, M, K, Kp, sa_i, sa_k, band, op.exps, S, op.slices)));
     BEM_LAUNCH(h, "k_slice_A");
@@ -839,7 +883,13 @@ static bem_status slice_B(bem_ctx* h, TcOperand& op, const void* src, int is_rea
         BEM_LAUNCH(h, "k_exp_blocks");
     }
     dim3 grid((unsigned)((Kp / SLICE_VEC + 255) / 256), (unsigned)m);
-    BEM_TIMED(h, "k_slice_B", (k_slice_B<<<grid, 256, 0, h->stream>>>(src, is_real, K, m, Kp, sb_k, sb_j, op.exps, S, op.slices, blocks)));
+    // contiguous complex columns have the layout of contiguous A rows: the row slicer's
+    // coalesced staging serves them (column j as row j, no band, no conjugation)
+    if (!is_real && sb_k == 1)
+        BEM_TIMED(h, "k_slice_B", (launch_slice_rows(blocks, (const double2*)src, 0, m, K, Kp, sb_j, -1, op.exps, S,
+                                                     op.slices, S, grid, h->stream)));
+    else
+        BEM_TIMED(h, "k_slice_B", (k_slice_B<<<grid, 256, 0, h->stream>>>(src, is_real, K, m, Kp, sb_k, sb_j, op.exps, S, op.slices, blocks)));
     BEM_LAUNCH(h, "k_slice_B");
     return encode_map(h, op, S);
 }
@@ -873,27 +923,50 @@ __global__ void k_splitk_reduce(const double2* __restrict__ part, int splits, in
 }
 
 // out = alpha C + beta out from the real products of blocked operands (TcBlocks), summed
-// over the K' splits: P[(z splits + s) M m + j M + i]
-__global__ void k_combine_blocks(const double* __restrict__ P, int splits, int gauss, int M, int m, double2* out,
-                                 int64_t ldo, int transposed, double alpha, double beta) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// over the K' splits: P[(z splits + s) M m + j M + i].  32 x 32 tiles of (i, j) per CTA of
+// 32 x 8 threads: the products are read along i; a transposed output (out[j + i ldo]) is
+// staged through shared memory so that it is written along j.
+__global__ void __launch_bounds__(256) k_combine_blocks(const double* __restrict__ P, int splits, int gauss, int M, int m,
+                                                        double2* out, int64_t ldo, int transposed, double alpha,
+                                                        double beta) {
+    __shared__ double2 tile[32][33];
     const int64_t plane = (int64_t)M * m;
-    if (idx >= plane) return;
-    const int i = (int)(idx % M), j = (int)(idx / M);
-    double pz[3] = {0.0, 0.0, 0.0};
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const int nz = gauss ? 3 : 2;
-    for (int z = 0; z < nz; ++z)
-        for (int s = 0; s < splits; ++s) pz[z] += P[(int64_t)(z * splits + s) * plane + idx];
-    const double re = gauss ? pz[0] - pz[1] : pz[0];
-    const double im = gauss ? (pz[2] - pz[0]) - pz[1] : pz[1];
-    double2* o = transposed ? (out + (int64_t)j + (int64_t)i * ldo) : (out + (int64_t)i + (int64_t)j * ldo);
-    double2 val = make_double2(alpha * re, alpha * im);
-    if (beta != 0.0) {
-        const double2 old = *o;
-        val.x += beta * old.x;
-        val.y += beta * old.y;
+    auto value = [&](int i, int j) {
+        double pz[3] = {0.0, 0.0, 0.0};
+        const int64_t idx = (int64_t)j * M + i;
+        for (int z = 0; z < nz; ++z)
+            for (int s = 0; s < splits; ++s) pz[z] += P[(int64_t)(z * splits + s) * plane + idx];
+        const double re = gauss ? pz[0] - pz[1] : pz[0];
+        const double im = gauss ? (pz[2] - pz[0]) - pz[1] : pz[1];
+        return make_double2(alpha * re, alpha * im);
+    };
+    auto store = [&](double2* o, double2 val) {
+        if (beta != 0.0) {
+            const double2 old = *o;
+            val.x += beta * old.x;
+            val.y += beta * old.y;
+        }
+        *o = val;
+    };
+    if (!transposed) {
+        for (int r = ty; r < 32; r += 8) {
+            const int i = i0 + tx, j = j0 + r;
+            if (i < M && j < m) store(out + (int64_t)i + (int64_t)j * ldo, value(i, j));
+        }
+        return;
     }
-    *o = val;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + tx, j = j0 + r;
+        if (i < M && j < m) tile[r][tx] = value(i, j);
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, j = j0 + tx;
+        if (i < M && j < m) store(out + (int64_t)j + (int64_t)i * ldo, tile[tx][r]);
+    }
 }
 
 // S_use > 0: multiply with the leading S_use digit slices only (B sliced with S_use, A with
@@ -1022,8 +1095,8 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     BEM_TIMED(h, tag, (kern<<<grid, TC_THREADS, smem, h->stream>>>(A.map, mapB, p)));
     BEM_LAUNCH(h, "k_tc_gemm");
     if (zb) {
-        const int64_t n = (int64_t)p.Ml * p.ml;
-        BEM_TIMED(h, "k_combine_blocks", (k_combine_blocks<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+        const dim3 cgrid((unsigned)((p.Ml + 31) / 32), (unsigned)((p.ml + 31) / 32));
+        BEM_TIMED(h, "k_combine_blocks", (k_combine_blocks<<<cgrid, dim3(32, 8), 0, h->stream>>>(
                                              p.outr, splits, zb->gauss, p.Ml, p.ml, out, ldo,
                                              transposed, alpha, beta)));
         BEM_LAUNCH(h, "k_combine_blocks");
@@ -1052,18 +1125,18 @@ bem_status tc_prepare_operators(bem_ctx* h) {
     const int64_t N = h->N;
     bem_status st;
     // slices of X^T: row i of the A operand is column i of X (contiguous); row exponents
-    // from the assembly when it gathered them.  S as row blocks [Re; Im; Re + Im]: its
-    // product with the right-hand sides (nrhs wide, the largest of the path) then takes
-    // Gauss's three real products instead of four, for one more block written here (with
-    // the right-hand-side product's slices only); Q^T S takes the Re and Im blocks.  N and
-    // D keep the part rows: their products are n wide, where the extra block would cost
-    // about what it saves.
+    // from the assembly when it gathered them.  S and N as row blocks [Re; Im; Re + Im]:
+    // their products with complex factors (S Y with the right-hand sides, Y2 N in the
+    // filter) then take Gauss's three real products instead of four, for one more block
+    // written here (S's with the right-hand-side product's slices only); Q^T S takes S's
+    // Re and Im blocks.  D keeps the part rows: it only meets the real Q^T.
     const int* fS = h->rexp_valid ? h->rexp : nullptr;
     const int* fW = h->rexp_valid ? h->rexp + N : nullptr;
     if ((st = slice_A(h, t->opS, h->S, N, N, N, 1, -1, 0, 0, fS, 3, rhs_slices(h))) != BEM_OK) return st;
     // N's near band (entries up to ~1e4 x its far field) is applied apart in double-float,
     // so the split only carries the far part with its own, much smaller row scale
-    if ((st = slice_A(h, t->opW, h->W, N, N, N, 1, (int)std::min<int64_t>(TC_W_BAND, (N - 1) / 2), 0, 0, fW)) != BEM_OK)
+    if ((st = slice_A(h, t->opW, h->W, N, N, N, 1, (int)std::min<int64_t>(TC_W_BAND, (N - 1) / 2), 0, 0, fW, 3,
+                      t->S)) != BEM_OK)
         return st;
     if (h->D) {
         if ((st = slice_A(h, t->opD, h->D, N, N, N, 1)) != BEM_OK) return st;
