@@ -1294,23 +1294,37 @@ bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double
 
 // =========================================================================================
 // Gauss-Jordan inversion with partial pivoting of A (r x r) on the augmented [A | I]
-// (r x 2r, column-major, ld = r).  CTA b owns a block of augmented columns.  Per step j
-// every CTA reads the pivot column from a copy its owner wrote while updating it in step
-// j - 1 (two buffers alternate, so the owner's in-place update never races the readers),
-// finds the pivot and updates its columns: one grid barrier per step.
+// (r x 2r, column-major, ld = r).  CTA b owns a block of augmented columns.  Step j needs
+// only the pivot column j as left by step j - 1: its owner publishes that copy in a buffer
+// of its own (colbuf + j r, all r kept, so no copy is ever overwritten) and then a flag
+// (release); every CTA waits for that flag alone (acquire, bounded), finds the pivot and
+// updates its columns, the owner of column j + 1 first.  Steps chain through the pivot
+// columns instead of grid barriers, so a CTA runs ahead as far as the pivots allow.
 // =========================================================================================
-__global__ void __launch_bounds__(256) k_gauss_jordan(cplx* M, int r, cplx* colbuf, unsigned* bar, int* err) {
+__global__ void __launch_bounds__(256) k_gauss_jordan(cplx* M, int r, cplx* colbuf, int* ready, int* err) {
     extern __shared__ cplx colj[];
     __shared__ double wv[8];
     __shared__ int wi[8];
+    __shared__ int s_ok;
     const unsigned G = gridDim.x;
     const int ncol = 2 * r;
     const int cb = (ncol + G - 1) / G;
     const int c0 = blockIdx.x * cb, c1 = min(ncol, c0 + cb);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = 0; j < r; ++j) {
-        // pivot column j as left by step j-1 (a copy, so its owner may update it in place)
-        const cplx* buf = colbuf + (size_t)(j & 1) * r;
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            for (long long spins = 0; ld_acquire(ready + j) == 0; ++spins) {
+                if (spins > (1ll << 24)) { atomicOr(err, DEVERR_TIMEOUT); ok = 0; break; }
+                if ((spins & 255) == 255 && *(volatile int*)err) { ok = 0; break; }
+                if (spins > 32) __nanosleep(32);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        // pivot column j as left by step j - 1
+        const cplx* buf = colbuf + (size_t)j * r;
         for (int i = threadIdx.x; i < r; i += blockDim.x) colj[i] = __ldcg(buf + i);
         __syncthreads();
         // argmax |colj[i]|, i >= j (ties to the lower row)
@@ -1329,7 +1343,7 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(cplx* M, int r, cplx* colb
         __syncthreads();
         double bb = wv[0];
         int p = wi[0];
-        for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+        for (int q = 1; q < nw; ++q)
             if (wv[q] > bb || (wv[q] == bb && wi[q] < p)) { bb = wv[q]; p = wi[q]; }
         if (!(bb > 0.0) || p >= r) {
             if (threadIdx.x == 0) atomicOr(err, DEVERR_SINGULAR);
@@ -1342,13 +1356,19 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(cplx* M, int r, cplx* colb
         const cplx pv = colj[j];
         const bool sing = !(cabs2(pv) > 0.0);
         const cplx ipv = sing ? cmk(0, 0) : cdiv(cmk(1, 0), pv);
-        for (int c = c0 + wid; c < c1; c += blockDim.x / 32) {
-            if (c < j) continue;                   // eliminated already (a unit column stays one)
+        // this CTA's columns c >= j (eliminated ones stay unit columns), column j + 1 first
+        const int lo = max(c0, j);
+        const int first = (j + 1 >= lo && j + 1 < c1) ? j + 1 : -1;
+        const int cnt = c1 - lo;
+        for (int t = wid; t < cnt; t += nw) {
+            int c;
+            if (first < 0) c = lo + t;
+            else c = (t == 0) ? first : ((lo + t - 1 >= first) ? lo + t : lo + t - 1);
             cplx* col = M + (int64_t)c * r;
             // swap rows j, p of this column and normalise row j
             const cplx xj = cmul(col[p], ipv), xp = col[j];
             __syncwarp();
-            cplx* nxt = (c == j + 1) ? colbuf + (size_t)((j + 1) & 1) * r : nullptr;
+            cplx* nxt = (c == j + 1 && j + 1 < r) ? colbuf + (size_t)(j + 1) * r : nullptr;
             for (int i = lane; i < r; i += 32) {
                 cplx v;
                 if (i == j) v = xj;
@@ -1357,24 +1377,33 @@ __global__ void __launch_bounds__(256) k_gauss_jordan(cplx* M, int r, cplx* colb
                 if (nxt) __stcg(nxt + i, v);
             }
             __syncwarp();
+            if (nxt && lane == 0) {
+                // the warp's copy before the flag: one fence, made cumulative by the warp barrier
+                __threadfence();
+                st_relaxed(ready + j + 1, 1);
+            }
         }
-        if (!grid_barrier(bar, G, err)) return;
+        // (the next step reloads colj only after its first barrier, which every warp of this
+        // step reaches after its updates)
     }
 }
 
-__global__ void k_augment(const cplx* K, cplx* M, cplx* colbuf, int r) {
+__global__ void k_augment(const cplx* K, cplx* M, cplx* colbuf, int* ready, int r) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)r * 2 * r) return;
     const int64_t i = idx % r, c = idx / r;
     M[idx] = (c < r) ? K[i + c * r] : cmk((c - r) == i ? 1.0 : 0.0, 0.0);
     if (c == 0) colbuf[i] = K[i];
+    if (c < r && i == 0) ready[c] = (c == 0) ? 1 : 0;   // step 0's pivot column is K's first
 }
 
 bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
     cplx *M = nullptr, *colbuf = nullptr;
+    int* ready = nullptr;
     BEM_CUDA(h, bem_dmalloc_async(h, (void**)&M, sizeof(cplx) * (size_t)r * 2 * r));
-    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&colbuf, sizeof(cplx) * (size_t)r * 2));
-    BEM_TIMED(h, "k_augment", (k_augment<<<(unsigned)(((int64_t)r * 2 * r + 255) / 256), 256, 0, h->stream>>>(K, M, colbuf, r)));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&colbuf, sizeof(cplx) * (size_t)r * r));
+    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&ready, sizeof(int) * (size_t)r));
+    BEM_TIMED(h, "k_augment", (k_augment<<<(unsigned)(((int64_t)r * 2 * r + 255) / 256), 256, 0, h->stream>>>(K, M, colbuf, ready, r)));
     BEM_LAUNCH(h, "k_augment");
     const size_t smem = sizeof(cplx) * (size_t)r;
     if (smem > 48 * 1024)
@@ -1385,8 +1414,7 @@ bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
     if (per < 1) return bem_fail(h, BEM_E_CUDA, "k_gauss_jordan cannot be resident");
     // three augmented columns per CTA: the per-step FP64 update spreads over about 2r/3 SMs
     int G = std::min(nsm * per, std::max(1, (2 * r + 2) / 3));
-    BEM_CUDA(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), h->stream));
-    void* args[] = {&M, &r, &colbuf, &h->bar, &h->dev_err};
+    void* args[] = {&M, &r, &colbuf, &ready, &h->dev_err};
     cudaError_t lerr;
     BEM_TIMED(h, "k_gauss_jordan",
               lerr = cudaLaunchCooperativeKernel((const void*)k_gauss_jordan, dim3(G), dim3(256), args, smem, h->stream));
@@ -1396,6 +1424,7 @@ bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
                                   sizeof(cplx) * r, r, cudaMemcpyDeviceToDevice, h->stream));
     bem_dfree_async(h, M);
     bem_dfree_async(h, colbuf);
+    bem_dfree_async(h, ready);
     return BEM_OK;
 }
 
