@@ -6,6 +6,8 @@
 // at start-up, or hosts embedding the library under an allocator they do not control.
 // They factor once (which allocates), then solve any number of times through this call,
 // which allocates nothing.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "kernels.h"
@@ -18,18 +20,50 @@ static __device__ __align__(256) double2 g_noalloc_scratch[2 * BEM_NOALLOC_MAX];
 
 static std::mutex g_noalloc_mutex;
 static double2* g_noalloc_ptr[64] = {nullptr};
+static unsigned long long g_noalloc_ctx[64] = {0};
+
+typedef CUresult (*PFN_ctxGetCurrent)(CUcontext*);
+typedef CUresult (*PFN_ctxGetId)(CUcontext, unsigned long long*);
+
+// Unique id of the current context (0 when the driver cannot give one).  A device reset
+// ends the context the array's address belongs to; the context created after it has a new
+// id.  Caller holds g_noalloc_mutex.
+static unsigned long long current_ctx_id() {
+    static PFN_ctxGetCurrent get_cur = nullptr;
+    static PFN_ctxGetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = (PFN_ctxGetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PFN_ctxGetId)f;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // Device address of the scratch array for the current device.  In host code the array's
 // name is only a host-side stand-in, so the address must come from cudaGetSymbolAddress,
-// once per device, with that device current.
+// once per device and context, with that device current (a context created after a
+// device reset looks it up again).
 static bem_status noalloc_scratch(bem_ctx* h, double2** out) {
     if (h->device < 0 || h->device >= 64) return bem_fail(h, BEM_E_INVALID, "solve_many_noalloc: bad device");
     std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-    if (!g_noalloc_ptr[h->device]) {
+    const unsigned long long ctx = current_ctx_id();
+    if (!g_noalloc_ptr[h->device] || (ctx != 0 && ctx != g_noalloc_ctx[h->device])) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return bem_cuda_check(h, e, "solve_many_noalloc: cudaGetSymbolAddress");
         g_noalloc_ptr[h->device] = (double2*)p;
+        g_noalloc_ctx[h->device] = ctx;
     }
     *out = g_noalloc_ptr[h->device];
     return BEM_OK;
