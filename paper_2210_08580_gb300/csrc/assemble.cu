@@ -758,12 +758,15 @@ __device__ __forceinline__ void assemble_sn_tile(const AsmParams& p, int L) {
     tile_of(L, p.nT, ti, tj);
     constexpr int TP = T + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* sI = reinterpret_cast<float4*>(smem_raw);               // TP*TP*4 complex df
-    float4* sM = sI + TP * TP * 4;                                   // TP*TP: sum_ab I / (h_e h_f)
-    float2* sND = reinterpret_cast<float2*>(sM + TP * TP);          // TP*TP: k^2 nu_e . nu_f
+    // pair arrays by row el and column fl, rows RS = TP + 1 apart: the entries read them with
+    // one row per lane, and the padded stride puts consecutive rows in different banks
+    constexpr int RS = TP + 1, PL = TP * RS;
+    float4* sI = reinterpret_cast<float4*>(smem_raw);               // 4 planes [ab][el][fl], complex df
+    float4* sM = sI + 4 * PL;                                        // [el][fl]: sum_ab I / (h_e h_f)
+    float2* sND = reinterpret_cast<float2*>(sM + PL);               // [el][fl]: k^2 nu_e . nu_f
     // e side: 7*TP (ox, oy, ux, uy, k tx, k ty, h); f side: 9*TP (the same, then ox, oy for
     // the tile's second e-anchor)
-    float2* gE = sND + TP * TP;
+    float2* gE = sND + PL;
     float2* gF = gE + 7 * TP;
     __shared__ int s_mexp;                                           // largest exponent field of the means
     __shared__ unsigned char eSel[TP];                               // e-anchor of each e-segment (0, 1)
@@ -877,9 +880,10 @@ __device__ __forceinline__ void assemble_sn_tile(const AsmParams& p, int L) {
             if (sw) { const cdfl t = A[1]; A[1] = A[2]; A[2] = t; }   // I_ab(e, f) = I_ba(f, e)
             for (int c = 0; c < 4; ++c) I[c] = {dfl_mul(hh, A[c].re), dfl_mul(hh, A[c].im)};
         }
-        for (int c = 0; c < 4; ++c) sI[pi * 4 + c] = cdfl_pack(I[c]);
-        sM[pi] = cdfl_pack(M0);
-        sND[pi] = make_float2(nd.hi, nd.lo);
+        const int ps = el * RS + fl;
+        for (int c = 0; c < 4; ++c) sI[c * PL + ps] = cdfl_pack(I[c]);
+        sM[ps] = cdfl_pack(M0);
+        sND[ps] = make_float2(nd.hi, nd.lo);
         mexp = max(mexp, max((__float_as_int(M0.re.hi) >> 23) & 255, (__float_as_int(M0.im.hi) >> 23) & 255));
     }
     for (int o = 16; o > 0; o >>= 1) npts += __shfl_xor_sync(0xffffffffu, npts, o);
@@ -899,8 +903,8 @@ __device__ __forceinline__ void assemble_sn_tile(const AsmParams& p, int L) {
         for (int pi = threadIdx.x; pi < TP * TP; pi += blockDim.x) {
             const int el = pi / TP, fl = pi % TP;
             if (i0 - 1 + el >= N || j0 - 1 + fl >= N) continue;
-            const cdfl m = cdfl_unpack(sM[pi]);
-            sMx[pi] = make_longlong2(dfl_to_fixed(m.re, msh), dfl_to_fixed(m.im, msh));
+            const cdfl m = cdfl_unpack(sM[el * RS + fl]);
+            sMx[el * RS + fl] = make_longlong2(dfl_to_fixed(m.re, msh), dfl_to_fixed(m.im, msh));
         }
     }
     const bool mirror = (ti != tj);
@@ -915,11 +919,11 @@ __device__ __forceinline__ void assemble_sn_tile(const AsmParams& p, int L) {
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 const int fl = jl + 1 - b;
-                const int pi = el * TP + fl;
-                const cdfl Iab = cdfl_unpack(sI[pi * 4 + a * 2 + b]);
+                const int ps = el * RS + fl;
+                const cdfl Iab = cdfl_unpack(sI[(a * 2 + b) * PL + ps]);
                 sv = (a | b) ? cdfl_add(sv, Iab) : Iab;
                 // the k^2 term: - k^2 (nu_e . nu_f) I_ab
-                if (p.W) wv = cdfl_fma_real(dfl_neg(dfl_mk(sND[pi])), Iab, wv);
+                if (p.W) wv = cdfl_fma_real(dfl_neg(dfl_mk(sND[ps])), Iab, wv);
             }
         }
         const int64_t off = (int64_t)i + (int64_t)j * p.ld;
@@ -929,8 +933,8 @@ __device__ __forceinline__ void assemble_sn_tile(const AsmParams& p, int L) {
         if (p.W) {
             // sum_ab sigma_a sigma_b M0(i-a, j-b) = (M0[i-1][j-1] - M0[i-1][j]) - (M0[i][j-1] - M0[i][j]),
             // plus the k^2 term, exactly in fixed point; one rounding to FP64
-            const longlong2 m00 = sMx[il * TP + jl], m01 = sMx[il * TP + jl + 1];
-            const longlong2 m10 = sMx[(il + 1) * TP + jl], m11 = sMx[(il + 1) * TP + jl + 1];
+            const longlong2 m00 = sMx[il * RS + jl], m01 = sMx[il * RS + jl + 1];
+            const longlong2 m10 = sMx[(il + 1) * RS + jl], m11 = sMx[(il + 1) * RS + jl + 1];
             const long long wr = ((m00.x - m01.x) - (m10.x - m11.x)) + dfl_to_fixed(wv.re, msh);
             const long long wi = ((m00.y - m01.y) - (m10.y - m11.y)) + dfl_to_fixed(wv.im, msh);
             dw = make_double2(fixed_to_double(wr, msh), fixed_to_double(wi, msh));
@@ -1045,13 +1049,13 @@ __device__ __forceinline__ void assemble_sn_tile(const AsmParams& p, int L) {
 
 static_assert(sizeof(AsmParams) % 4 == 0, "AsmParams is copied to shared memory in 4-byte words");
 
-// Shared memory of one S/N tile of edge T: (T+1)^2 segment pairs (four integrals, the mean,
-// k^2 nu_e . nu_f), the staged geometry and the entries' k^2 terms.  107 KB at T = 31 admits
-// two CTAs per SM, 62 KB at T = 23 three and 28 KB at T = 15 four.  The smaller tiles are
+// Shared memory of one S/N tile of edge T: (T+1)^2 segment pairs in rows of T+2 (four
+// integrals, the mean, k^2 nu_e . nu_f), the staged geometry and the entries' k^2 terms.
+// 110 KB at T = 31 admits two CTAs per SM, 64 KB at T = 23 three and 30 KB at T = 15 four.  The smaller tiles are
 // compiled for that many CTAs (at most 85 and 64 registers per thread); T = 31 is left to
 // the compiler's choice (108 registers, two CTAs).
 __host__ __device__ constexpr size_t asm_sn_smem(int T) {
-    return (size_t)(T + 1) * (T + 1) * (4 * sizeof(float4) + sizeof(float4) + sizeof(float2)) +
+    return (size_t)(T + 1) * (T + 2) * (4 * sizeof(float4) + sizeof(float4) + sizeof(float2)) +
            (size_t)16 * (T + 1) * sizeof(float2) + (size_t)T * T * sizeof(float4);
 }
 __host__ __device__ constexpr int asm_min_blocks(int T) { return T <= 15 ? 4 : (T <= 23 ? 3 : 1); }
