@@ -79,6 +79,26 @@ def test_assembly_matches_oracle(B, star301, ops):
     s.close()
 
 
+def test_assembly_tile_edges_agree(B, star301):
+    """bem_options.asm_tile: S and N from tiles of edge 15, 23 and 31 (ragged tails at
+    N = 301) all match the oracle, and each other up to the summation order of entries that
+    a diagonal tile computes directly and another edge takes from the mirror; any other edge
+    is refused at handle creation."""
+    v, k, mats = star301
+    got = {}
+    for T in (15, 23, 31):
+        s = _solver(B, v, k, "SW", tiles={"asm_tile": T})
+        got[T] = {op: _np(s.matrix(op)) for op in "SW"}
+        s.close()
+        for op in "SW":
+            assert _rel(got[T][op], mats[op]) <= ENTRY_TOL, (T, op, _rel(got[T][op], mats[op]))
+    for T in (15, 23):
+        for op in "SW":
+            assert _rel(got[T][op], got[31][op]) <= 1e-14, (T, op)
+    with pytest.raises(B.BemError):
+        B.Solver(device=0, tiles={"asm_tile": 16})
+
+
 @pytest.mark.parametrize("k", [12.0, 24.0])
 def test_assembly_bessel_regimes(B, k):
     """k r up to ~24 (Miller recurrence) and ~48 (Hankel asymptotics) on a circle."""
