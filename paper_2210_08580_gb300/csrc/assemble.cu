@@ -717,12 +717,13 @@ __device__ __forceinline__ void gauss_row_df(int o, int i, const cdfl& R0, const
 }
 // q = 2, the far-field bulk: the four kernel values g_ij (node i on e, j on f) combine with
 // the weights W_0 = (a, b), W_1 = (b, a), a = (1 + 1/sqrt 3)/4, b = (1 - 1/sqrt 3)/4, as
-//   I_00 = X + Y, I_11 = X - Y, I_01 = Z + V, I_10 = Z - V,
-//   X = s/12 + p/24, Z = s/24 + p/12, Y = d/(8 sqrt 3), V = q/(8 sqrt 3),
+//   A_00 = X + Y, A_11 = X - Y, A_01 = Z + V, A_10 = Z - V,
+//   X = s/12 + p/24 = (2 s + p)/24, Z = s/24 + p/12 = (s + 2 p)/24, Y = d/(8 sqrt 3), V = q/(8 sqrt 3),
 // s = g11 + g22, d = g11 - g22, p = g12 + g21, q = g12 - g21 (a^2 + b^2 = 1/6, ab = 1/24,
-// a^2 - b^2 = 1/(4 sqrt 3)); and sum_ab I_ab = (s + p)/4.
+// a^2 - b^2 = 1/(4 sqrt 3)); and M0 = sum_ab A_ab = (s + p)/4.  Returns the integrals
+// I_ab = h_e h_f A_ab, the pair's hh = h_e h_f folded into the weights 1/24 and 1/(8 sqrt 3).
 __device__ __forceinline__ void pair_gauss_df_2(dfl bx, dfl by, dfl uex, dfl uey, dfl vfx, dfl vfy,
-                                                const float4* __restrict__ tab, cdfl A[4], cdfl& M0) {
+                                                const float4* __restrict__ tab, dfl hh, cdfl I[4], cdfl& M0) {
     cdfl g[2][2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -737,13 +738,14 @@ __device__ __forceinline__ void pair_gauss_df_2(dfl bx, dfl by, dfl uex, dfl uey
     }
     const cdfl sm = cdfl_add(g[0][0], g[1][1]), df = cdfl_sub(g[0][0], g[1][1]);
     const cdfl pp = cdfl_add(g[0][1], g[1][0]), qq = cdfl_sub(g[0][1], g[1][0]);
-    const dfl c12 = dfl_mk(c_q2_df[0]), c24 = dfl_mk(c_q2_df[1]), c83 = dfl_mk(c_q2_df[2]);
-    const cdfl X = cdfl_fma_real(c24, pp, cdfl_scale(c12, sm)), Z = cdfl_fma_real(c12, pp, cdfl_scale(c24, sm));
-    const cdfl Y = cdfl_scale(c83, df), V = cdfl_scale(c83, qq);
-    A[0] = cdfl_add(X, Y);
-    A[3] = cdfl_sub(X, Y);
-    A[1] = cdfl_add(Z, V);
-    A[2] = cdfl_sub(Z, V);
+    const dfl w24 = dfl_mul(hh, dfl_mk(c_q2_df[1])), w83 = dfl_mul(hh, dfl_mk(c_q2_df[2]));
+    const cdfl sm2 = {dfl_scale(sm.re, 2.f), dfl_scale(sm.im, 2.f)}, pp2 = {dfl_scale(pp.re, 2.f), dfl_scale(pp.im, 2.f)};
+    const cdfl X = cdfl_scale(w24, cdfl_add(sm2, pp)), Z = cdfl_scale(w24, cdfl_add(sm, pp2));
+    const cdfl Y = cdfl_scale(w83, df), V = cdfl_scale(w83, qq);
+    I[0] = cdfl_add(X, Y);
+    I[3] = cdfl_sub(X, Y);
+    I[1] = cdfl_add(Z, V);
+    I[2] = cdfl_sub(Z, V);
     const cdfl t = cdfl_add(sm, pp);
     M0 = {dfl_scale(t.re, 0.25f), dfl_scale(t.im, 0.25f)};
 }
@@ -886,16 +888,16 @@ __device__ __forceinline__ void assemble_sn_tile(const AsmParams& p, int L) {
             const float gap = fmaxf(sqrt_approx(mx * mx + my * my) - 0.5f * (he + hf), 0.0f);
             const int q = q_for_gap_fast(__fdividef(gap, hmax), gap + hmax);
             npts += (unsigned)(q * q);
-            cdfl A[4];
+            const dfl hh = dfl_mul(hx, hy);
             if (q == 2) {
-                pair_gauss_df_2(bx, by, uex, uey, vfx, vfy, p.btabf, A, M0);   // the far-field bulk
+                pair_gauss_df_2(bx, by, uex, uey, vfx, vfy, p.btabf, hh, I, M0);   // the far-field bulk
             } else {
+                cdfl A[4];
                 pair_gauss_df(q, bx, by, uex, uey, vfx, vfy, p.btabf, A);
                 M0 = cdfl_add(cdfl_add(A[0], A[1]), cdfl_add(A[2], A[3]));
+                for (int c = 0; c < 4; ++c) I[c] = {dfl_mul(hh, A[c].re), dfl_mul(hh, A[c].im)};
             }
-            const dfl hh = dfl_mul(hx, hy);
-            if (sw) { const cdfl t = A[1]; A[1] = A[2]; A[2] = t; }   // I_ab(e, f) = I_ba(f, e)
-            for (int c = 0; c < 4; ++c) I[c] = {dfl_mul(hh, A[c].re), dfl_mul(hh, A[c].im)};
+            if (sw) { const cdfl t = I[1]; I[1] = I[2]; I[2] = t; }   // I_ab(e, f) = I_ba(f, e)
         }
         const int ps = el * RS + fl;
         for (int c = 0; c < 4; ++c) sI[c * PL + ps] = cdfl_pack(I[c]);
