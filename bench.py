@@ -45,7 +45,7 @@ ASM_OPS_PER_POINT = 270
 # (absent = not captured since the kernel last changed); the summaries are under profiles/
 # (the RHS product's from its N = 4096, 1024-RHS capture: reads x 16 (S's slices and the
 # right-hand sides' re-reads grow with N^2), writes x 4 (with N nrhs))
-TRAFFIC_BYTES = {"k_assemble": 0.0324e9 + 8.687e9, "tc_rhs_SY": 0.8303e9 * 16 + 0.0845e9 * 4}
+TRAFFIC_BYTES = {"k_assemble": 0.0308e9 + 8.6866e9, "tc_rhs_SY": 0.8303e9 * 16 + 0.0845e9 * 4}
 
 
 def _peaks():
