@@ -16,6 +16,7 @@ end-to-end number through the Python API with host buffers, and the CPU oracle b
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -151,6 +152,9 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--nrhs", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-overlap", action="store_true",
+                    help="compress, factor and the right-hand sides one after another (default: "
+                         "bem_factor_rhs_planewave, the right-hand sides on a second stream)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare-fp64", action="store_true",
                     help="skip timing the FP64 path beside the mixed path")
@@ -408,6 +412,8 @@ def workload_config(args):
                         f"tol={args.tol}, {args.nrhs} plane waves",
             "N": args.N, "k": args.k, "n_modes": 2 * args.M + 1, "tol": args.tol, "nrhs": args.nrhs,
             "prec": args.prec, "parallelism": f"replicas x{args.gpus}",
+            "schedule": ("compress, factor, right-hand sides in turn" if args.no_overlap else
+                         "right-hand sides on a second stream beside compress and factor"),
             "l2": "working set > L2: S and N (4.3 GB each at N=16384) are rewritten and read every step"}
 
 
@@ -442,12 +448,22 @@ def main():
     x = torch.empty_like(v)
     info = {}
 
+    def factor_and_rhs(sv, ang_in, v_out):
+        """compression, factor and right-hand sides: overlapped in one call, or one after another"""
+        if args.no_overlap:
+            r = sv.compress(args.tol)
+            sv.factor()
+            sv.L.bem_rhs_planewave(sv.h, ang_in.data_ptr(), args.nrhs, None, v_out.data_ptr(), args.N)
+            return r
+        r = ctypes.c_int64()
+        sv._check(sv.L.bem_factor_rhs_planewave(sv.h, float(args.tol), ang_in.data_ptr(), args.nrhs, None,
+                                                v_out.data_ptr(), args.N, ctypes.byref(r)))
+        return r.value
+
     def step(verts_in, ang_in, x_out=None):
         s.assemble(verts_in, args.k, ops="SW")
         s.filter_apply(n_modes)
-        info["r"] = s.compress(args.tol)
-        s.factor()
-        s.L.bem_rhs_planewave(s.h, ang_in.data_ptr(), args.nrhs, None, v.data_ptr(), args.N)
+        info["r"] = factor_and_rhs(s, ang_in, v)
         s.solve(v, out=x if x_out is None else x_out)
 
     def barrier():
@@ -478,7 +494,7 @@ def main():
     ms_step = ms / args.steps
     value = job_value(args.nrhs, world, ms_step / 1000.0)
 
-    # ---- phase split of one extra instrumented step (factor vs RHS vs solve)
+    # ---- phase split of one extra instrumented step (factor vs RHS vs solve, one after another)
     def timed(fn):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream); fn(); b.record(stream); torch.cuda.synchronize(dev)
@@ -555,9 +571,7 @@ def main():
         def step64():
             s64.assemble(verts, args.k, ops="SW")
             s64.filter_apply(n_modes)
-            r64 = s64.compress(args.tol)
-            s64.factor()
-            s64.L.bem_rhs_planewave(s64.h, ang.data_ptr(), args.nrhs, None, v64.data_ptr(), args.N)
+            r64 = factor_and_rhs(s64, ang, v64)
             s64.solve(v64, out=x64)
             return r64
 

@@ -229,6 +229,17 @@ bem_status bem_rhs_planewave(bem_handle h, const double* angles_dev, int64_t nrh
 bem_status bem_rhs_pointsource(bem_handle h, const double* src_xy_dev, int64_t nsrc, void* f_out_dev,
                                void* v_out_dev, int64_t ld);
 
+/* bem_factor_rhs_planewave -- compress_compact(rel_tol), factor and bem_rhs_planewave in one
+ * call (Sec. IV-C and Sec. II), with the same results: the right-hand sides (their product
+ * with S is the largest of the path) run on a second stream of the handle, started once the
+ * compression's QR is enqueued and joined to the handle's stream before the call returns,
+ * so they overlap the Jacobi SVD, the compression products and the factor.  Arguments as
+ * for those calls; v_out_dev is required (f_out_dev may be NULL).  Needs filter_apply.
+ * Writes the rank to *rank_out; synchronises the handle's stream as compress_compact does.
+ * Errors: those of the three calls (the first one met is returned). */
+bem_status bem_factor_rhs_planewave(bem_handle h, double rel_tol, const double* angles_dev, int64_t nrhs,
+                                    void* f_out_dev, void* v_out_dev, int64_t ld, int64_t* rank_out);
+
 /* solve_many -- x = (beta I + U V^H)^-1 v by the Woodbury identity (Sec. IV-C):
  *     x = v/beta - beta^-2 U (I_r + beta^-1 V^H U)^-1 V^H v,
  * for nrhs columns v (ldv >= N) into x (ldx >= N).  x may not alias v.

@@ -28,7 +28,7 @@ EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error",
            "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info", "bem_timing_enable",
            "bem_timing_report", "solve_many_noalloc", "bem_farfield", "bem_farfield_adjoint",
            "bem_shape_vjp", "bem_rhs_pointsource", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain",
-           "bem_assemble_batch")
+           "bem_assemble_batch", "bem_factor_rhs_planewave")
 
 
 class BemOptions(ctypes.Structure):
@@ -119,6 +119,7 @@ def load_library(path: str = LIB_PATH):
     L.compress_compact.argtypes = [vp, dbl, ctypes.POINTER(i64)]
     L.factor.argtypes = [vp]
     L.bem_rhs_planewave.argtypes = [vp, vp, i64, vp, vp, i64]
+    L.bem_factor_rhs_planewave.argtypes = [vp, dbl, vp, i64, vp, vp, i64, ctypes.POINTER(i64)]
     L.bem_rhs_pointsource.argtypes = [vp, vp, i64, vp, vp, i64]
     L.solve_many.argtypes = [vp, vp, i64, vp, i64, i64, ctypes.POINTER(ctypes.c_int32),
                              ctypes.POINTER(ctypes.c_double)]
@@ -141,7 +142,7 @@ def load_library(path: str = LIB_PATH):
                  "compress_compact", "factor", "bem_rhs_planewave", "bem_rhs_pointsource", "solve_many", "solve_backward",
                  "bem_get_matrix", "bem_get_info", "bem_timing_enable", "bem_timing_report", "bem_farfield",
                  "bem_farfield_adjoint", "bem_shape_vjp", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain",
-                 "bem_assemble_batch"):
+                 "bem_assemble_batch", "bem_factor_rhs_planewave"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -240,6 +241,18 @@ class Solver:
 
     def factor(self):
         self._check(self.L.factor(self.h))
+
+    def factor_rhs_planewave(self, rel_tol: float, angles, out: torch.Tensor | None = None):
+        """compress(rel_tol), factor() and rhs_planewave(angles) in one call, the right-hand
+        sides overlapping the compression and the factor on a second stream; returns
+        (rank, v)."""
+        ang = torch.as_tensor(angles, dtype=torch.float64).to(self.device).contiguous()
+        nrhs = ang.numel()
+        v = out if out is not None else torch.empty((nrhs, self.N), dtype=torch.complex128, device=self.device)
+        r = ctypes.c_int64()
+        self._check(self.L.bem_factor_rhs_planewave(self.h, float(rel_tol), _ptr(ang), nrhs, None, _ptr(v), self.N,
+                                                    ctypes.byref(r)))
+        return r.value, v
 
     def rhs_planewave(self, angles, want_f: bool = False, want_v: bool = True):
         ang = torch.as_tensor(angles, dtype=torch.float64).to(self.device).contiguous()

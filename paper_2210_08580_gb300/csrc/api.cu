@@ -53,18 +53,20 @@ void bem_dfree_async(bem_ctx* h, void* p) {
 }
 
 bem_status bem_workspace(bem_ctx* h, size_t bytes, void** out) {
-    if (bytes > h->work_bytes) {
-        if (h->work) {
-            cudaStreamSynchronize(h->stream);
-            bem_dfree(h, h->work);
-            h->work = nullptr;
-            h->work_bytes = 0;
+    void** w = h->rhs_aux ? &h->work2 : &h->work;
+    size_t* wb = h->rhs_aux ? &h->work2_bytes : &h->work_bytes;
+    if (bytes > *wb) {
+        if (*w) {
+            cudaStreamSynchronize(h->stream);          // the stream that uses this workspace
+            bem_dfree(h, *w);
+            *w = nullptr;
+            *wb = 0;
         }
         size_t want = std::max(bytes, (size_t)1 << 20);
-        BEM_CUDA(h, bem_dmalloc(h, &h->work, want));
-        h->work_bytes = want;
+        BEM_CUDA(h, bem_dmalloc(h, w, want));
+        *wb = want;
     }
-    *out = h->work;
+    *out = *w;
     return BEM_OK;
 }
 
@@ -215,9 +217,12 @@ bem_status bem_destroy(bem_handle h) {
     if (!h) return BEM_OK;
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
+    if (h->aux) cudaStreamSynchronize(h->aux);
     free_stage_buffers(h, 0);
     tc_destroy(h);
     free_ptr(h, &h->work);
+    free_ptr(h, &h->work2);
+    if (h->aux) cudaStreamDestroy(h->aux);
     free_ptr(h, (void**)&h->btab);
     free_ptr(h, (void**)&h->btabf);
     free_ptr(h, (void**)&h->dev_err);
@@ -391,9 +396,12 @@ bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha) {
     return BEM_OK;
 }
 
-bem_status compress_compact(bem_handle h, double rel_tol, int64_t* rank_out) {
-    if (!h) return BEM_E_INVALID;
-    h->err.clear();
+}  // extern "C"
+
+// compress_compact's work; after_qr runs once the pivoted QR is enqueued (the fork point of
+// bem_factor_rhs_planewave: nothing after it reads what the right-hand sides write)
+template <class AfterQR>
+static bem_status compress_impl(bem_ctx* h, double rel_tol, int64_t* rank_out, AfterQR after_qr) {
     if (h->stage < 2) return bem_fail(h, BEM_E_INVALID, "compress_compact: call filter_apply first");
     if (!std::isfinite(rel_tol) || rel_tol >= 1.0)
         return bem_fail(h, BEM_E_INVALID, "compress_compact: rel_tol must be < 1");
@@ -420,6 +428,7 @@ bem_status compress_compact(bem_handle h, double rel_tol, int64_t* rank_out) {
     // B^ = X^H: pivoted QR X P = Q R, then the left singular vectors of R^H, rows permuted
     // back by P, are those of B^
     if ((st = launch_house_qr(h, X, N, (int)nc, R, perm, h->opt.prec == BEM_MIXED_BF16)) != BEM_OK) return st;
+    if ((st = after_qr()) != BEM_OK) return st;
     if ((st = launch_jacobi_svd(h, R, (int)nc, perm, h->sigma, h->E)) != BEM_OK) return st;
     std::vector<double> sig(nc);
     BEM_CUDA(h, cudaMemcpyAsync(sig.data(), h->sigma, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->stream));
@@ -446,6 +455,14 @@ bem_status compress_compact(bem_handle h, double rel_tol, int64_t* rank_out) {
     if (rank_out) *rank_out = r;
     h->stage = 3;
     return BEM_OK;
+}
+
+extern "C" {
+
+bem_status compress_compact(bem_handle h, double rel_tol, int64_t* rank_out) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    return compress_impl(h, rel_tol, rank_out, [] { return BEM_OK; });
 }
 
 bem_status factor(bem_handle h) {
@@ -541,6 +558,55 @@ bem_status bem_rhs_pointsource(bem_handle h, const double* src_xy, int64_t nsrc,
     BEM_CUDA(h, cudaSetDevice(h->device));
     return rhs_common(h, "bem_rhs_pointsource", nsrc, f_out, v_out, ld,
                       [&](cplx* f, cplx* hz) { return launch_rhs_point(h, src_xy, nsrc, f, hz, ld); });
+}
+
+// compress_compact, factor and bem_rhs_planewave in one call, with the right-hand sides on a
+// second stream of the handle: forked once the pivoted QR is enqueued, they run beside the
+// Jacobi SVD, the compression products and the Gauss-Jordan factor (kernels small enough to
+// share SMs with the split product's CTAs), and are joined to the handle's stream before
+// the call returns.  Their scratch (workspace, the product's B operand) is their own.
+bem_status bem_factor_rhs_planewave(bem_handle h, double rel_tol, const double* angles, int64_t nrhs, void* f_out,
+                                    void* v_out, int64_t ld, int64_t* rank_out) {
+    if (!h) return BEM_E_INVALID;
+    h->err.clear();
+    if (h->stage < 2) return bem_fail(h, BEM_E_INVALID, "bem_factor_rhs_planewave: call filter_apply first");
+    if (!angles || !v_out || nrhs < 1 || nrhs > 65535 || ld < h->N)
+        return bem_fail(h, BEM_E_INVALID, "bem_factor_rhs_planewave: need angles, v, 1 <= nrhs <= 65535, ld >= N");
+    BEM_CUDA(h, cudaSetDevice(h->device));
+    if (!h->aux) BEM_CUDA(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    cudaStream_t mainst = h->stream;
+    cudaEvent_t done = nullptr;
+    bem_status rst = BEM_OK;
+    std::string rerr;
+    auto fork_rhs = [&]() -> bem_status {
+        cudaEvent_t qr = bem_event_get(h);
+        BEM_CUDA(h, cudaEventRecord(qr, mainst));
+        BEM_CUDA(h, cudaStreamWaitEvent(h->aux, qr, 0));
+        h->evpool.push_back(qr);            // the wait took the record; the event may be reused
+        h->stream = h->aux;
+        h->rhs_aux = true;
+        rst = rhs_common(h, "bem_factor_rhs_planewave", nrhs, f_out, v_out, ld,
+                         [&](cplx* f, cplx* hz) { return launch_rhs(h, angles, nrhs, f, hz, ld); });
+        if (rst != BEM_OK) rerr = h->err;
+        done = bem_event_get(h);
+        cudaEventRecord(done, h->aux);
+        h->stream = mainst;
+        h->rhs_aux = false;
+        return BEM_OK;                      // the right-hand sides' status is reported after the join
+    };
+    bem_status st = compress_impl(h, rel_tol, rank_out, fork_rhs);
+    h->stream = mainst;
+    h->rhs_aux = false;
+    if (st == BEM_OK) st = factor(h);
+    if (done) {
+        cudaStreamWaitEvent(mainst, done, 0);
+        h->evpool.push_back(done);
+    }
+    if (st == BEM_OK && rst != BEM_OK) {
+        h->err = rerr;
+        st = rst;
+    }
+    return st;
 }
 
 // x = v/beta - beta^-2 U Kinv V^H v, all FP64 products

@@ -126,6 +126,13 @@ struct bem_ctx {
     // workspace
     void* work = nullptr;
     size_t work_bytes = 0;
+    // bem_factor_rhs_planewave: the right-hand sides run on aux beside the compression and
+    // the factor; while they are enqueued (rhs_aux), their scratch comes from work2 and the
+    // split products' B operand from its own buffer, so nothing is shared with the other chain
+    cudaStream_t aux = nullptr;
+    void* work2 = nullptr;
+    size_t work2_bytes = 0;
+    bool rhs_aux = false;
     int* dev_err = nullptr;           // device status word
     unsigned* bar = nullptr;          // grid barrier words (2)
     unsigned long long* qpts = nullptr;   // Gauss points of separated pairs, last assembly
@@ -171,7 +178,7 @@ bem_status bem_cuda_check(bem_ctx* h, cudaError_t e, const char* what);
     } while (0)
 
 // workspace: returns a device pointer of at least `bytes`, growing the handle's buffer
-bem_status bem_workspace(bem_ctx* h, size_t bytes, void** out);
+bem_status bem_workspace(bem_ctx* h, size_t bytes, void** out);   // work2 while rhs_aux is set
 
 // Device memory of a handle.  With the caller's hooks (bem_create) every byte comes from
 // dev_alloc and goes back through dev_free; without them from the CUDA runtime.

@@ -1117,14 +1117,17 @@ __device__ __forceinline__ void st_relaxed(int* p, int v) {
 // reductions and the rotation run on the FP32 pipe, the rotation scalars included (formed
 // once per pair by one thread with double-float roots and quotients, which keeps the FP64
 // pipe's long dependent latency off the round's critical path).
-__global__ void __launch_bounds__(JAC_NT) k_jacobi(float4* X, int n, int* ver, int* flags, int max_sweeps,
+// EPT column entries per thread (n <= EPT JAC_NT).  The instance for n <= 256 is held to 85
+// registers (six CTAs' worth per SM), so that one of its CTAs fits on an SM beside a CTA of
+// the split-bf16 GEMM (320 threads x 168 registers) and the two can run at the same time.
+template <int EPT>
+__global__ void __launch_bounds__(JAC_NT, EPT <= 2 ? 6 : 1) k_jacobi(float4* X, int n, int* ver, int* flags, int max_sweeps,
                                                    unsigned* bar, int* err) {
     __shared__ float2 red[JAC_NT / 32][4];
     __shared__ int s_ok;
     const unsigned G = gridDim.x;
     const int np = n + (n & 1);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    constexpr int EPT = 1024 / JAC_NT;            // elements per thread (n <= 1024)
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int round = 0; round < np - 1; ++round) {
             const int target = sweep * (np - 1) + round;
@@ -1280,7 +1283,9 @@ bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double
     int ms = max_sweeps;
     void* args[] = {&X, &n, &ver, &flags, &ms, &h->bar, &h->dev_err};
     bem_status st;
-    BEM_TIMED(h, "k_jacobi", st = coop_launch(h, (const void*)k_jacobi, (n + 1) / 2, JAC_NT, args, "k_jacobi"));
+    const void* jk = (n <= 2 * JAC_NT) ? (const void*)k_jacobi<2>
+                     : (n <= 4 * JAC_NT) ? (const void*)k_jacobi<4> : (const void*)k_jacobi<8>;
+    BEM_TIMED(h, "k_jacobi", st = coop_launch(h, jk, (n + 1) / 2, JAC_NT, args, "k_jacobi"));
     if (st == BEM_OK) {
         BEM_TIMED(h, "k_sort_sv", (k_sort_sv<<<1, 256, 0, h->stream>>>(X, n, perm, sigma, E, tmp)));
         BEM_LAUNCH(h, "k_sort_sv");

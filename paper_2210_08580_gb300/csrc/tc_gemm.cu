@@ -753,6 +753,8 @@ struct TcState {
     TcOperand opS, opW, opD;          // A operands: X^T of the assembled matrices
     TcOperand opVh, opU;              // Woodbury factors
     TcOperand bbuf;                   // B operand scratch (reused)
+    TcOperand bbuf_rhs;               // the right-hand sides' B operand while they run on the
+                                      // auxiliary stream (bem_factor_rhs_planewave)
     TcOperand tmpA;                   // A operand scratch (reused)
     double2* part = nullptr;          // split-K partials
     size_t part_cap = 0;
@@ -969,6 +971,51 @@ __global__ void __launch_bounds__(256) k_combine_blocks(const double* __restrict
     }
 }
 
+// The same for an output stored in the products' own order (out[i + j ldo]): a flat grid,
+// two consecutive entries per thread, every plane's loads issued before they are combined
+// (the splits summed in the same order as above).
+__global__ void __launch_bounds__(256) k_combine_blocks_flat(const double* __restrict__ P, int splits, int gauss,
+                                                             int M, int m, double2* out, int64_t ldo, double alpha,
+                                                             double beta) {
+    const int64_t plane = (int64_t)M * m;
+    const int64_t base = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (base >= plane) return;
+    const bool two = base + 1 < plane;
+    const int nz = gauss ? 3 : 2;
+    double v0[3] = {0.0, 0.0, 0.0}, v1[3] = {0.0, 0.0, 0.0};
+    for (int s = 0; s < splits; ++s) {
+#pragma unroll
+        for (int z = 0; z < 3; ++z) {
+            if (z >= nz) break;
+            const double* q = P + (int64_t)(z * splits + s) * plane + base;
+            v0[z] += __ldcs(q);
+            if (two) v1[z] += __ldcs(q + 1);
+        }
+    }
+    for (int u = 0; u < (two ? 2 : 1); ++u) {
+        const double* v = u ? v1 : v0;
+        const double re = gauss ? v[0] - v[1] : v[0];
+        const double im = gauss ? (v[2] - v[0]) - v[1] : v[1];
+        const int64_t e = base + u;
+        int64_t i, j;
+        if (plane < (1LL << 32)) {                      // 32-bit division where it suffices
+            i = (unsigned)e % (unsigned)M;
+            j = (unsigned)e / (unsigned)M;
+        } else {
+            i = e % M;
+            j = e / M;
+        }
+        double2* o = out + i + j * ldo;
+        double2 val = make_double2(alpha * re, alpha * im);
+        if (beta != 0.0) {
+            const double2 old = *o;
+            val.x += beta * old.x;
+            val.y += beta * old.y;
+        }
+        *o = val;
+    }
+}
+
 // S_use > 0: multiply with the leading S_use digit slices only (B sliced with S_use, A with
 // at least that many).  zb: the complex product as real products of blocked operands
 // (A.blocks > every zA, B blocked likewise or real).
@@ -1095,10 +1142,16 @@ static bem_status tc_gemm(bem_ctx* h, const TcOperand& A, const TcOperand& B, cp
     BEM_TIMED(h, tag, (kern<<<grid, TC_THREADS, smem, h->stream>>>(A.map, mapB, p)));
     BEM_LAUNCH(h, "k_tc_gemm");
     if (zb) {
-        const dim3 cgrid((unsigned)((p.Ml + 31) / 32), (unsigned)((p.ml + 31) / 32));
-        BEM_TIMED(h, "k_combine_blocks", (k_combine_blocks<<<cgrid, dim3(32, 8), 0, h->stream>>>(
-                                             p.outr, splits, zb->gauss, p.Ml, p.ml, out, ldo,
-                                             transposed, alpha, beta)));
+        if (transposed) {
+            const dim3 cgrid((unsigned)((p.Ml + 31) / 32), (unsigned)((p.ml + 31) / 32));
+            BEM_TIMED(h, "k_combine_blocks", (k_combine_blocks<<<cgrid, dim3(32, 8), 0, h->stream>>>(
+                                                 p.outr, splits, zb->gauss, p.Ml, p.ml, out, ldo,
+                                                 transposed, alpha, beta)));
+        } else {
+            const int64_t pairs = ((int64_t)p.Ml * p.ml + 1) / 2;
+            BEM_TIMED(h, "k_combine_blocks", (k_combine_blocks_flat<<<(unsigned)((pairs + 255) / 256), 256, 0, h->stream>>>(
+                                                 p.outr, splits, zb->gauss, p.Ml, p.ml, out, ldo, alpha, beta)));
+        }
         BEM_LAUNCH(h, "k_combine_blocks");
         return BEM_OK;
     }
@@ -1253,10 +1306,11 @@ bem_status tc_product_right(bem_ctx* h, int op, const cplx* y, int64_t ldy, int6
     // the right-hand sides take one digit slice fewer by default (see bem_options.rhs_slices);
     // a blocked A (S) takes Gauss's three real products
     const int Sr = rhs_slices(h);
-    bem_status st = slice_B(h, t->bbuf, y, 0, h->N, nrhs, 1, ldy, Sr, A->blocks ? 3 : 0);
+    TcOperand& Bop = h->rhs_aux ? t->bbuf_rhs : t->bbuf;
+    bem_status st = slice_B(h, Bop, y, 0, h->N, nrhs, 1, ldy, Sr, A->blocks ? 3 : 0);
     if (st != BEM_OK) return st;
     const TcBlocks zg = {3, {0, 1, 2}, {0, 1, 2}, 1};
-    return tc_gemm(h, *A, t->bbuf, out, ld, 0, 1.0, 0.0, "tc_rhs_SY", Sr, A->blocks ? &zg : nullptr);
+    return tc_gemm(h, *A, Bop, out, ld, 0, 1.0, 0.0, "tc_rhs_SY", Sr, A->blocks ? &zg : nullptr);
 }
 
 bem_status tc_prepare_solve(bem_ctx* h) {
@@ -1385,6 +1439,7 @@ void tc_destroy(bem_ctx* h) {
     TcState* t = (TcState*)h->tc;
     free_op(h, t->opS); free_op(h, t->opW); free_op(h, t->opD); free_op(h, t->opVh); free_op(h, t->opU);
     free_op(h, t->bbuf);
+    free_op(h, t->bbuf_rhs);
     free_op(h, t->tmpA);
     bem_dfree(h, t->part);
     bem_dfree(h, t->zbuf);
