@@ -218,11 +218,13 @@ bem_status bem_destroy(bem_handle h) {
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
     if (h->aux) cudaStreamSynchronize(h->aux);
+    if (h->hi) cudaStreamSynchronize(h->hi);
     free_stage_buffers(h, 0);
     tc_destroy(h);
     free_ptr(h, &h->work);
     free_ptr(h, &h->work2);
     if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->hi) cudaStreamDestroy(h->hi);
     free_ptr(h, (void**)&h->btab);
     free_ptr(h, (void**)&h->btabf);
     free_ptr(h, (void**)&h->dev_err);
@@ -416,11 +418,13 @@ static bem_status compress_impl(bem_ctx* h, double rel_tol, int64_t* rank_out, A
     cplx *X = nullptr, *R = nullptr;
     double* Qs = nullptr;
     int* perm = nullptr;
+    void* jac = nullptr;
     Carve cv;
     cv.add((void**)&X, sizeof(cplx) * nc * N);
     cv.add((void**)&R, sizeof(cplx) * nc * nc);
     cv.add((void**)&Qs, sizeof(double) * nc * N);
     cv.add((void**)&perm, sizeof(int) * nc);
+    cv.add(&jac, jacobi_scratch_bytes((int)nc));
     if ((st = cv.commit(h)) != BEM_OK) return st;
     // Bs = diag(sqrt g) B ;  X = (Bs F^-1)^H  (N x nc, stored with row stride nc)
     if ((st = launch_row_scale(h, h->B, h->Bs, h->gm, 1, nc, N, nc)) != BEM_OK) return st;
@@ -429,7 +433,7 @@ static bem_status compress_impl(bem_ctx* h, double rel_tol, int64_t* rank_out, A
     // back by P, are those of B^
     if ((st = launch_house_qr(h, X, N, (int)nc, R, perm, h->opt.prec == BEM_MIXED_BF16)) != BEM_OK) return st;
     if ((st = after_qr()) != BEM_OK) return st;
-    if ((st = launch_jacobi_svd(h, R, (int)nc, perm, h->sigma, h->E)) != BEM_OK) return st;
+    if ((st = launch_jacobi_svd(h, R, (int)nc, perm, h->sigma, h->E, jac)) != BEM_OK) return st;
     std::vector<double> sig(nc);
     BEM_CUDA(h, cudaMemcpyAsync(sig.data(), h->sigma, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->stream));
     if ((st = check_dev_err(h)) != BEM_OK) return st;
@@ -476,8 +480,10 @@ bem_status factor(bem_handle h) {
     bem_status st;
     if ((st = ensure_alloc(h, (void**)&h->K, sizeof(cplx) * r * r)) != BEM_OK) return st;
     cplx* Kt = nullptr;
+    void* gj = nullptr;
     Carve cv;
     cv.add((void**)&Kt, sizeof(cplx) * r * r);
+    cv.add(&gj, gauss_jordan_scratch_bytes((int)r));
     if ((st = cv.commit(h)) != BEM_OK) return st;
     // K = I_r + beta^-1 V^H U, stored as its inverse
     if (h->opt.prec == BEM_MIXED_BF16) {
@@ -490,7 +496,7 @@ bem_status factor(bem_handle h) {
             return st;
     }
     if ((st = launch_add_identity(h, Kt, r, (int)r, cmk(1, 0))) != BEM_OK) return st;
-    if ((st = launch_gauss_jordan(h, Kt, h->K, (int)r)) != BEM_OK) return st;
+    if ((st = launch_gauss_jordan(h, Kt, h->K, (int)r, gj)) != BEM_OK) return st;
     if ((st = check_dev_err(h)) != BEM_OK) return st;
     h->stage = 4;
     return BEM_OK;
@@ -574,15 +580,23 @@ bem_status bem_factor_rhs_planewave(bem_handle h, double rel_tol, const double* 
         return bem_fail(h, BEM_E_INVALID, "bem_factor_rhs_planewave: need angles, v, 1 <= nrhs <= 65535, ld >= N");
     BEM_CUDA(h, cudaSetDevice(h->device));
     if (!h->aux) BEM_CUDA(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    if (!h->hi) {
+        int least = 0, greatest = 0;
+        BEM_CUDA(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        BEM_CUDA(h, cudaStreamCreateWithPriority(&h->hi, cudaStreamNonBlocking, greatest));
+    }
     cudaStream_t mainst = h->stream;
     cudaEvent_t done = nullptr;
+    bool forked = false;
     bem_status rst = BEM_OK;
     std::string rerr;
     auto fork_rhs = [&]() -> bem_status {
         cudaEvent_t qr = bem_event_get(h);
         BEM_CUDA(h, cudaEventRecord(qr, mainst));
         BEM_CUDA(h, cudaStreamWaitEvent(h->aux, qr, 0));
-        h->evpool.push_back(qr);            // the wait took the record; the event may be reused
+        BEM_CUDA(h, cudaStreamWaitEvent(h->hi, qr, 0));
+        h->evpool.push_back(qr);            // the waits took the record; the event may be reused
+        forked = true;
         h->stream = h->aux;
         h->rhs_aux = true;
         rst = rhs_common(h, "bem_factor_rhs_planewave", nrhs, f_out, v_out, ld,
@@ -590,14 +604,20 @@ bem_status bem_factor_rhs_planewave(bem_handle h, double rel_tol, const double* 
         if (rst != BEM_OK) rerr = h->err;
         done = bem_event_get(h);
         cudaEventRecord(done, h->aux);
-        h->stream = mainst;
+        h->stream = h->hi;                  // the rest of the compression, and the factor
         h->rhs_aux = false;
         return BEM_OK;                      // the right-hand sides' status is reported after the join
     };
     bem_status st = compress_impl(h, rel_tol, rank_out, fork_rhs);
-    h->stream = mainst;
     h->rhs_aux = false;
     if (st == BEM_OK) st = factor(h);
+    h->stream = mainst;
+    if (forked) {
+        cudaEvent_t hd = bem_event_get(h);
+        cudaEventRecord(hd, h->hi);
+        cudaStreamWaitEvent(mainst, hd, 0);
+        h->evpool.push_back(hd);
+    }
     if (done) {
         cudaStreamWaitEvent(mainst, done, 0);
         h->evpool.push_back(done);

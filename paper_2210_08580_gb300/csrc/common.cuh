@@ -130,6 +130,10 @@ struct bem_ctx {
     // the factor; while they are enqueued (rhs_aux), their scratch comes from work2 and the
     // split products' B operand from its own buffer, so nothing is shared with the other chain
     cudaStream_t aux = nullptr;
+    cudaStream_t hi = nullptr;       // the compression and factor meanwhile, at the highest
+                                     // priority: the block scheduler serves its kernels before
+                                     // the GEMM's queued CTAs (at equal priority it would not
+                                     // start them until the GEMM's last CTAs were dispatched)
     void* work2 = nullptr;
     size_t work2_bytes = 0;
     bool rhs_aux = false;

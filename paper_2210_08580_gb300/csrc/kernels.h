@@ -61,8 +61,10 @@ bem_status launch_scale_real_cols(bem_ctx* h, const double* in, double* out, con
                                   int64_t rows, int64_t cols);
 // dfl_arith: double-float arithmetic on the FP32 pipe (X is overwritten in that format)
 bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* perm, bool dfl_arith);
-bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double* sigma, cplx* E);
-bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r);
+size_t jacobi_scratch_bytes(int n);
+bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double* sigma, cplx* E, void* scratch);
+size_t gauss_jordan_scratch_bytes(int r);
+bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r, void* scratch);
 bem_status launch_axpby(bem_ctx* h, cplx* y, int64_t ldy, const cplx* x, int64_t ldx, cplx a, cplx b,
                         int64_t rows, int64_t cols);   // y = a*x + b*y
 bem_status launch_add_identity(bem_ctx* h, cplx* A, int64_t ld, int r, cplx d);

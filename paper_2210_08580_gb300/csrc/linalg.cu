@@ -1264,18 +1264,29 @@ __global__ void k_conj_transpose(const cplx* R, float4* X, int n) {
     X[idx] = cdfl_pack({dfl_from(v.x), dfl_from(-v.y)});
 }
 
-bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double* sigma, cplx* E) {
+// scratch of launch_jacobi_svd: X (n x n double-float), the sweep flags, the column
+// versions and the norms, each 256-byte aligned
+#define JAC_MAX_SWEEPS 40
+static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+size_t jacobi_scratch_bytes(int n) {
+    return al256(sizeof(float4) * (size_t)n * n) + al256(sizeof(int) * JAC_MAX_SWEEPS) + al256(sizeof(int) * (size_t)n) +
+           al256(sizeof(double) * (size_t)n);
+}
+
+// scratch: jacobi_scratch_bytes(n) bytes the caller keeps until the stream has run the SVD
+// (the handle's workspace: no stream-ordered allocation, so the SVD can run on any stream)
+bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double* sigma, cplx* E, void* scratch) {
     if (n > 1024) return bem_fail(h, BEM_E_UNSUPPORTED, "Jacobi SVD: more than 1024 columns");
-    float4* X = nullptr;
-    int* flags = nullptr;
-    double* tmp = nullptr;
-    int* ver = nullptr;
-    const int max_sweeps = 40;
-    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&X, sizeof(float4) * (size_t)n * n));
-    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&flags, sizeof(int) * max_sweeps));
-    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&ver, sizeof(int) * n));
+    const int max_sweeps = JAC_MAX_SWEEPS;
+    char* sp = (char*)scratch;
+    float4* X = (float4*)sp;
+    sp += al256(sizeof(float4) * (size_t)n * n);
+    int* flags = (int*)sp;
+    sp += al256(sizeof(int) * max_sweeps);
+    int* ver = (int*)sp;
+    sp += al256(sizeof(int) * (size_t)n);
+    double* tmp = (double*)sp;
     BEM_CUDA(h, cudaMemsetAsync(ver, 0, sizeof(int) * n, h->stream));
-    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&tmp, sizeof(double) * n));
     BEM_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(int) * max_sweeps, h->stream));
     BEM_TIMED(h, "k_conj_transpose",
               (k_conj_transpose<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, h->stream>>>(R, X, n)));
@@ -1290,10 +1301,6 @@ bem_status launch_jacobi_svd(bem_ctx* h, cplx* R, int n, const int* perm, double
         BEM_TIMED(h, "k_sort_sv", (k_sort_sv<<<1, 256, 0, h->stream>>>(X, n, perm, sigma, E, tmp)));
         BEM_LAUNCH(h, "k_sort_sv");
     }
-    bem_dfree_async(h, X);
-    bem_dfree_async(h, flags);
-    bem_dfree_async(h, ver);
-    bem_dfree_async(h, tmp);
     return st;
 }
 
@@ -1402,12 +1409,20 @@ __global__ void k_augment(const cplx* K, cplx* M, cplx* colbuf, int* ready, int 
     if (c < r && i == 0) ready[c] = (c == 0) ? 1 : 0;   // step 0's pivot column is K's first
 }
 
-bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
-    cplx *M = nullptr, *colbuf = nullptr;
-    int* ready = nullptr;
-    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&M, sizeof(cplx) * (size_t)r * 2 * r));
-    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&colbuf, sizeof(cplx) * (size_t)r * r));
-    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&ready, sizeof(int) * (size_t)r));
+// scratch of launch_gauss_jordan: [K | I] (r x 2r), the published pivot columns (r x r) and
+// their flags, each 256-byte aligned
+size_t gauss_jordan_scratch_bytes(int r) {
+    return al256(sizeof(cplx) * (size_t)r * 2 * r) + al256(sizeof(cplx) * (size_t)r * r) + al256(sizeof(int) * (size_t)r);
+}
+
+// scratch: gauss_jordan_scratch_bytes(r) bytes, as for launch_jacobi_svd
+bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r, void* scratch) {
+    char* sp = (char*)scratch;
+    cplx* M = (cplx*)sp;
+    sp += al256(sizeof(cplx) * (size_t)r * 2 * r);
+    cplx* colbuf = (cplx*)sp;
+    sp += al256(sizeof(cplx) * (size_t)r * r);
+    int* ready = (int*)sp;
     BEM_TIMED(h, "k_augment", (k_augment<<<(unsigned)(((int64_t)r * 2 * r + 255) / 256), 256, 0, h->stream>>>(K, M, colbuf, ready, r)));
     BEM_LAUNCH(h, "k_augment");
     const size_t smem = sizeof(cplx) * (size_t)r;
@@ -1427,9 +1442,6 @@ bem_status launch_gauss_jordan(bem_ctx* h, const cplx* K, cplx* Kinv, int r) {
     BEM_LAUNCH(h, "k_gauss_jordan");
     BEM_CUDA(h, cudaMemcpy2DAsync(Kinv, sizeof(cplx) * r, M + (size_t)r * r, sizeof(cplx) * r,
                                   sizeof(cplx) * r, r, cudaMemcpyDeviceToDevice, h->stream));
-    bem_dfree_async(h, M);
-    bem_dfree_async(h, colbuf);
-    bem_dfree_async(h, ready);
     return BEM_OK;
 }
 
