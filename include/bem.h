@@ -230,10 +230,11 @@ bem_status bem_rhs_pointsource(bem_handle h, const double* src_xy_dev, int64_t n
                                void* v_out_dev, int64_t ld);
 
 /* bem_factor_rhs_planewave -- compress_compact(rel_tol), factor and bem_rhs_planewave in one
- * call (Sec. IV-C and Sec. II), with the same results: the right-hand sides (their product
- * with S is the largest of the path) run on a second stream of the handle, started once the
- * compression's QR is enqueued and joined to the handle's stream before the call returns,
- * so they overlap the Jacobi SVD, the compression products and the factor.  Arguments as
+ * call (Sec. IV-C and Sec. II), with the same results: once the compression's QR has run,
+ * the right-hand sides (their product with S is the largest of the path) run on a second
+ * stream of the handle while the rest of the compression and the factor run on a third, of
+ * the highest priority; both are joined to the handle's stream before the call returns.
+ * The handle keeps the two streams until bem_destroy.  Arguments as
  * for those calls; v_out_dev is required (f_out_dev may be NULL).  Needs filter_apply.
  * Writes the rank to *rank_out; synchronises the handle's stream as compress_compact does.
  * Errors: those of the three calls (the first one met is returned). */
