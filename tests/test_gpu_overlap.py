@@ -19,10 +19,10 @@ def B():
     return bem
 
 
-def _run(B, verts, k, ang, prec, memory, fused):
+def _run(B, verts, k, ang, prec, memory, fused, alpha=0.0):
     s = B.Solver(device=0, prec=prec, memory=memory, refine_rtol=1e-8)
-    s.assemble(torch.from_numpy(verts).cuda(), k, ops="SW")
-    s.filter_apply(2 * 40 + 1)
+    s.assemble(torch.from_numpy(verts).cuda(), k, ops="SWD" if alpha else "SW")
+    s.filter_apply(2 * 40 + 1, alpha=alpha)
     if fused:
         r, v = s.factor_rhs_planewave(1e-10, ang)
     else:
@@ -43,6 +43,17 @@ def test_fused_call_reproduces_the_sequential_calls(B, prec, memory):
     ang = torch.from_numpy(I.planewave_angles(256))
     a = _run(B, verts, 2.0, ang, prec, memory, fused=False)
     b = _run(B, verts, 2.0, ang, prec, memory, fused=True)
+    assert a["r"] == b["r"]
+    for key in ("sigma", "U", "Vh", "v", "x"):
+        assert torch.equal(a[key], b[key]), (key, float((a[key] - b[key]).abs().max()))
+
+
+def test_fused_call_reproduces_the_sequential_calls_cfie(B):
+    """the CFIE (alpha > 0): the right-hand sides add - alpha G^-1 h2 on the second stream"""
+    verts, _, _ = I.equal_chord_mesh(I.random_star(4), 1024)
+    ang = torch.from_numpy(I.planewave_angles(64))
+    a = _run(B, verts, 3.0, ang, "mixed", "torch", fused=False, alpha=0.5)
+    b = _run(B, verts, 3.0, ang, "mixed", "torch", fused=True, alpha=0.5)
     assert a["r"] == b["r"]
     for key in ("sigma", "U", "Vh", "v", "x"):
         assert torch.equal(a[key], b[key]), (key, float((a[key] - b[key]).abs().max()))
