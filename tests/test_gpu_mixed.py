@@ -1,7 +1,7 @@
 """Mixed-precision path (split-bf16 tcgen05 products + FP64 refinement) against the CPU
 oracle and against the FP64 GPU path.
 
-Bar (BASELINE metric): the refined mixed solution within 1e-8 of the FP64 reference.
+Bar (the mixed path's accuracy target): the refined mixed solution within 1e-8 of the FP64 reference.
 The operator blocks themselves are checked tighter, at the accuracy the split gives."""
 import numpy as np
 import pytest
@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 MIXED_SOLVE_TOL = 1e-8      # relative current error after refinement
 # preconditioned RHS v, relative to max: its product S Y keeps 5 of the 6 digit slices
 # (35 bits), so its error is a few times 2^-35 (2.9e-11) of max|v| -- measured 1.2e-10 on the
-# 301-point star; the solution bar below is what the method's accuracy is judged by
+# 301-point star; the solution bar below is the method's accuracy target
 MIXED_RHS_TOL = 5e-10
 MIXED_BLOCK_TOL = 1e-9      # filtered block B, relative to max: B = Y/g - Q^T/4 cancels ~3 digits
 
