@@ -18,7 +18,10 @@ in numpy/scipy double precision, following the paper's order:
             the preconditioner carries the factor i k, see ``calderon_system``),
             C2 = Z2 - I/4.
   Sec. III  Laplacian L, L~ = G^-1/2 L G^-1/2, the filter P^L_n from the n
-            smoothest eigenvectors of L~ (eq. LapFilter).
+            smoothest eigenvectors of L~ (eq. LapFilter).  The literal route
+            (``filter_literal``, ``filtered_solve_literal``) takes any mesh, including
+            the non-equal-chord ones for which the paper prescribes L~; the block route
+            is for equal-chord meshes, where G and L are circulant.
   Sec. IV   filtered equation (I/4 + P C2) j2 = v_e2, its CFIE generalisation,
             low-rank C = U V^H and the Woodbury inverse.
 

@@ -18,11 +18,13 @@ other shapes are the synthetic workloads of this project):
 * ``perturbed_circle()``             r(theta) = 2 + 0.2 sin(8 theta)   (Sec. V, Table I)
 * ``ellipse(a, b)``                  polar form of the ellipse with semi-axes a, b (Sec. V)
 
-Meshes are *equal-chord*: vertices r_i = r(theta_i) (cos theta_i, sin theta_i),
+Meshes are *equal-chord* by default: vertices r_i = r(theta_i) (cos theta_i, sin theta_i),
 theta_0 = 0, counter-clockwise, with |r_{i+1} - r_i| = h for every i including the
 closing chord.  The paper does not say how its meshes are built; equal chords make
 the P1 Gram and Laplacian matrices exactly circulant, which is the setting in which
-the Laplacian filter can be applied with Fourier modes (Sec. III-A).
+the Laplacian filter can be applied with Fourier modes (Sec. III-A).  ``parameter_mesh``
+builds the non-equal-chord meshes (uniform or smoothly graded in the polar angle), for
+which the paper's orthonormalised Laplacian has no closed-form eigenvectors.
 """
 from __future__ import annotations
 
@@ -35,6 +37,7 @@ __all__ = [
     "PolarCurve", "circle", "cos_star", "random_star", "fourier_star",
     "perturbed_circle", "ellipse", "equal_chord_mesh", "regular_polygon",
     "planewave_angles", "batch_problems", "BatchProblem", "equal_chord_tangent",
+    "parameter_mesh",
 ]
 
 
@@ -136,6 +139,20 @@ def regular_polygon(N: int, a: float = 1.0) -> np.ndarray:
     """Vertices a (cos 2 pi i/N, sin 2 pi i/N): the equal-chord mesh of a circle."""
     th = 2.0 * math.pi * np.arange(N) / N
     return np.ascontiguousarray(np.stack([a * np.cos(th), a * np.sin(th)], axis=-1))
+
+
+def parameter_mesh(curve: PolarCurve, N: int, grade: float = 0.0, phase: float = 0.0):
+    """Vertices at theta_i = t_i + grade sin(t_i - phase), t_i = 2 pi i / N: returns
+    (verts (N,2) f64, theta (N,)).  With grade = 0 the vertices are uniform in the polar
+    angle (the chords then follow the curve's speed); 0 < |grade| < 1 grades them smoothly,
+    adjacent chords of a circle differing by up to a factor (1 + |grade|)/(1 - |grade|)
+    across the curve.  These are the non-equal-chord meshes, for which G and L are general
+    cyclic tridiagonal matrices (Sec. III-A's orthonormalised Laplacian)."""
+    if not abs(grade) < 1.0:
+        raise ValueError("grade must lie in (-1, 1)")
+    t = 2.0 * math.pi * np.arange(N) / N
+    th = t + grade * np.sin(t - phase)
+    return np.ascontiguousarray(curve.point(th)), th
 
 
 def _arclength_thetas(curve: PolarCurve, N: int, fine: int | None = None) -> np.ndarray:

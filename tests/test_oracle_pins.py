@@ -542,3 +542,68 @@ def test_hypersingular_null_space_at_low_frequency():
         np.add.at(K1, (E + a) % N, -(k * k) * nud * Iq[:, a, :].sum(axis=1))
     err = np.max(np.abs(W.sum(axis=1) - K1)) / np.max(np.abs(K1))
     assert err <= 1e-7, err
+
+
+# ------------------------------------------------------------------ non-equal-chord meshes
+
+
+def test_general_mesh_gram_and_laplacian_forms():
+    """On a graded mesh G and L are the P1 mass and stiffness matrices: G 1 sums to the
+    hat integrals (h_{i-1} + h_i)/2, 1^T G 1 is the perimeter, L has the constant kernel,
+    and x^T L x of the nodal values of a linear function f(x, y) = c . r equals the
+    chord-wise sum of (c . t_e)^2 h_e (the exact energy of the interpolant)."""
+    v, _ = I.parameter_mesh(I.perturbed_circle(), 97, grade=0.4)
+    h = np.linalg.norm(np.roll(v, -1, 0) - v, axis=1)
+    G, L = O.gram(v), O.laplacian(v)
+    assert np.allclose(G @ np.ones(97), 0.5 * (h + np.roll(h, 1)), rtol=1e-14)
+    assert abs(np.ones(97) @ G @ np.ones(97) - h.sum()) < 1e-13 * h.sum()
+    assert np.max(np.abs(L @ np.ones(97))) < 1e-12 * np.max(np.abs(L))
+    c = np.array([0.7, -1.3])
+    x = v @ c
+    t = (np.roll(v, -1, 0) - v) / h[:, None]
+    assert abs(x @ L @ x - np.sum((t @ c) ** 2 * h)) < 1e-12 * np.sum((t @ c) ** 2 * h)
+
+
+def test_general_mesh_filter_is_the_generalized_eigenspace():
+    """The literal filter built from L~ = G^-1/2 L G^-1/2 (Sec. III-A) on a graded,
+    asymmetric mesh projects onto G^1/2 span(Phi), Phi the n lowest eigenvectors of the
+    pencil L phi = lambda G phi from a Cholesky-based generalized solver, with the same
+    eigenvalues; the lowest eigenvalues approach those of the curve's Laplace-Beltrami
+    operator, (2 pi m / perimeter)^2, at second order in h."""
+    sla = pytest.importorskip("scipy.linalg")
+    v, _ = I.parameter_mesh(I.perturbed_circle(), 160, grade=0.25, phase=0.7)
+    G, L = O.gram(v), O.laplacian(v)
+    n = 21
+    P, lam = O.filter_literal(v, n)
+    w, Phi = sla.eigh(L, G, subset_by_index=[0, n - 1])
+    Gh = sla.sqrtm(G).real
+    P2 = Gh @ Phi @ Phi.T @ Gh
+    assert np.max(np.abs(P - P2)) < 1e-10
+    assert np.allclose(lam[:n], w, rtol=1e-10, atol=1e-10)
+    errs = []
+    for N in (200, 400):
+        vv, _ = I.parameter_mesh(I.circle(1.0), N, grade=0.3)
+        ww = sla.eigh(O.laplacian(vv), O.gram(vv), eigvals_only=True, subset_by_index=[0, 10])
+        m = np.array([0, 1, 1, 2, 2, 3, 3, 4, 4, 5, 5], dtype=float)
+        perim = np.linalg.norm(np.roll(vv, -1, 0) - vv, axis=1).sum()
+        errs.append(np.max(np.abs(ww - (2 * math.pi * m / perim) ** 2)))
+    assert errs[1] < 0.02 and 3.5 < errs[0] / errs[1] < 4.6, errs     # lambda up to 25
+
+
+def test_general_mesh_mie_second_order():
+    """On graded meshes of the unit circle the literal route's filtered, compressed
+    solution approaches the exact Mie current at O(h^2), as on equal-chord meshes."""
+    k = 1.0
+    errs = []
+    for N in (64, 128):
+        v, th = I.parameter_mesh(I.circle(1.0), N, grade=0.3, phase=0.4)
+        m = O.assemble(v, k, "SW")
+        ang = np.array([0.3, 2.0])
+        f = O.rhs_planewave(v, k, ang)
+        res = O.filtered_solve_literal(m, v, f, 15, 1e-10)
+        G = O.gram(v)
+        e = max(O.g_norm(G, res["x"][:, w] - O.mie_current(k, 1.0, th, ang[w]))[0]
+                / O.g_norm(G, O.mie_current(k, 1.0, th, ang[w]))[0] for w in range(2))
+        errs.append(e)
+    assert errs[1] < 1e-3, errs
+    assert 3.3 < errs[0] / errs[1] < 4.8, errs
