@@ -27,10 +27,14 @@
  *    changes nothing.  Re-running an earlier stage invalidates the later ones.
  *  - No call aborts, prints or exits.  On failure the status says what kind of error
  *    happened and bem_last_error(h) returns a message (valid until the next call on h).
- *  - Meshes must be equal-chord (all segment lengths equal to within 1e-10 relative):
- *    that makes the P1 Gram and Laplacian matrices circulant, so the Laplacian filter is
- *    exactly a set of Fourier modes (Sec. III-A).  Other meshes return
- *    BEM_E_UNSUPPORTED.
+ *  - Meshes: on an equal-chord polygon (all segment lengths equal to within 1e-10
+ *    relative) the P1 Gram and Laplacian matrices are circulant and the Laplacian filter is
+ *    exactly a set of Fourier modes (Sec. III-A).  Any other polygon is a non-homogeneous
+ *    discretisation, for which Sec. III-A prescribes the orthonormalised Laplacian
+ *    L~ = G^-1/2 L G^-1/2: G and L are then general cyclic tridiagonal matrices, solved
+ *    through a bordered LDL^T factorisation, and the filter basis is computed (the lowest
+ *    eigenvectors of the pencil L phi = lambda G phi, see filter_apply).  bem_shape_vjp
+ *    takes equal-chord meshes only.
  */
 #ifndef BEM_GB300_H
 #define BEM_GB300_H
@@ -47,7 +51,7 @@ typedef enum {
     BEM_E_INVALID = 1,        /* bad argument or call out of order */
     BEM_E_NOMEM = 2,          /* device allocation failed */
     BEM_E_CUDA = 3,           /* a CUDA runtime call or kernel launch failed */
-    BEM_E_UNSUPPORTED = 4,    /* mesh not equal-chord, k h too large, size limits */
+    BEM_E_UNSUPPORTED = 4,    /* k h too large, size limits, an equal-chord-only call */
     BEM_E_SINGULAR = 5,       /* zero pivot in the Woodbury core */
     BEM_E_NOT_CONVERGED = 6,  /* mixed-precision refinement missed refine_rtol */
     BEM_E_TIMEOUT = 7         /* a bounded device-side wait gave up */
@@ -69,8 +73,11 @@ enum {
     BEM_MAT_B = 3,            /* n x N  B = Q^T (C_x - alpha G^-1 D): P C_x = Q B          */
     BEM_MAT_U = 4,            /* N x r  skeleton left factor                                */
     BEM_MAT_VH = 5,           /* r x N  skeleton right factor V^H                           */
-    BEM_MAT_SIGMA = 6         /* n real doubles: singular values of the filtered compact
+    BEM_MAT_SIGMA = 6,        /* n real doubles: singular values of the filtered compact
                                  part in the orthonormal basis, descending                 */
+    BEM_MAT_Q = 7             /* N x n REAL doubles: the filter basis Q (Fourier modes on an
+                                 equal-chord mesh; G-orthonormal lowest eigenvectors of the
+                                 pencil (L, G) on any other mesh)                          */
 };
 
 typedef struct {
@@ -118,6 +125,8 @@ typedef struct {
     int prec;                 /* bem_precision in use                                       */
     int64_t quad_points;      /* Gauss points (kernel evaluations) the last bem_assemble
                                  spent on separated segment pairs, counted on the device   */
+    int equal_chord;          /* 1: the assembled mesh is equal-chord (circulant G, L);
+                                 0: general cyclic tridiagonal G, L                        */
 } bem_info;
 
 typedef struct bem_ctx* bem_handle;
@@ -164,9 +173,11 @@ bem_status bem_set_stream(bem_handle h, void* cuda_stream);
  * N uses Maue's integration by parts:
  *     <phi_i, N phi_j> = int int g2 [phi_i' phi_j' - k^2 (nu_x . nu_y) phi_i phi_j].
  * `ops` is a mask of BEM_OP_S | BEM_OP_W | BEM_OP_D; S and W are needed by the EFIE
- * path, D by the CFIE (alpha != 0).  Requires N >= 16, k > 0, k*h <= 2.  Synchronises
- * the stream once (to validate the mesh).  Errors: BEM_E_INVALID (bad arguments),
- * BEM_E_UNSUPPORTED (chords not equal to 1e-10, k h > 2), BEM_E_NOMEM, BEM_E_CUDA. */
+ * path, D by the CFIE (alpha != 0).  Requires N >= 16, k > 0, k*h <= 2 for the longest
+ * chord h.  Chords that differ by more than 1e-10 of their mean make the mesh a general
+ * one (see the notes at the top): its Gram matrix is factored here.  Synchronises the
+ * stream once (to validate the mesh).  Errors: BEM_E_INVALID (bad arguments),
+ * BEM_E_UNSUPPORTED (k h > 2), BEM_E_NOMEM, BEM_E_CUDA. */
 bem_status bem_assemble(bem_handle h, const double* verts_xy_dev, int64_t N, double k,
                         unsigned ops);
 
@@ -191,12 +202,21 @@ bem_status bem_assemble_batch(bem_handle* hs, int64_t nprob, const double* const
  *       = diag(1/g_m) (Q^T S G^-1 N - alpha Q^T D) - Q^T/4,
  * so that the filtered operator in nodal coordinates is beta I + Q B with
  * beta = (1 + 2 alpha)/4 (alpha = 0: filtered TE-EFIE; alpha > 0: filtered Yukawa-Calderon
- * TE-CFIE).  n_modes must be odd, 3 <= n_modes <= min(N - 1, 1023).  Needs S, W (and D if alpha != 0). */
+ * TE-CFIE).  On any other mesh Q is the G-orthonormal basis of the n lowest eigenvectors of
+ * the pencil L phi = lambda G phi (Q = G^-1/2 V_n, V_n those of L~; the filter in nodal
+ * coordinates is Q Q^T G), g_m = 1, and
+ *     B = Q^T G (G^-1 S G^-1 N - I/4 - alpha G^-1 D) = (Q^T S) G^-1 N - alpha Q^T D - (G Q)^T/4;
+ * Q comes from shift-and-invert subspace iteration on (L + sigma G)^-1 G (block of about
+ * 2n + 9 columns, at most 1023, started from arclength Fourier modes, Cholesky-QR
+ * G-orthonormalised) and one Rayleigh-Ritz step through the Jacobi SVD; its span matches
+ * the eigenvectors to rounding (a non-positive Cholesky pivot returns BEM_E_SINGULAR).
+ * n_modes must be odd, 3 <= n_modes <= min(N - 1, 1023).  Needs S, W (and D if alpha != 0). */
 bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha);
 
 /* compress_compact -- skeleton of the filtered compact part (Sec. IV-C): computes the SVD
  * of diag(sqrt g) B G^-1/2 (the block in the orthonormal, G^1/2-weighted basis of the
- * paper) by Householder QR plus one-sided Jacobi, keeps the singular values
+ * paper; G^-1/2 is taken as F^-1 with F^T F = G, which leaves the singular values and left
+ * singular vectors unchanged) by Householder QR plus one-sided Jacobi, keeps the singular values
  * sigma_i >= rel_tol * sigma_1 and forms U (N x r), V^H (r x N) with Q B ~= U V^H.
  * Writes the rank to *rank_out (host pointer, may be NULL); synchronises the stream. */
 bem_status compress_compact(bem_handle h, double rel_tol, int64_t* rank_out);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libbem_gb300.so")
 BEM_FP64 = 0
 BEM_MIXED_BF16 = 1
 BEM_OP_S, BEM_OP_W, BEM_OP_D = 1, 2, 4
-MATS = {"S": 0, "W": 1, "N": 1, "D": 2, "B": 3, "U": 4, "Vh": 5, "sigma": 6}
+MATS = {"S": 0, "W": 1, "N": 1, "D": 2, "B": 3, "U": 4, "Vh": 5, "sigma": 6, "Q": 7}
 STATUS = {0: "BEM_OK", 1: "BEM_E_INVALID", 2: "BEM_E_NOMEM", 3: "BEM_E_CUDA", 4: "BEM_E_UNSUPPORTED",
           5: "BEM_E_SINGULAR", 6: "BEM_E_NOT_CONVERGED", 7: "BEM_E_TIMEOUT"}
 
@@ -43,7 +43,7 @@ class BemInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("n", ctypes.c_int64), ("r", ctypes.c_int64),
                 ("k", ctypes.c_double), ("h", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("beta", ctypes.c_double), ("sigma_max", ctypes.c_double), ("stage", ctypes.c_int),
-                ("prec", ctypes.c_int), ("quad_points", ctypes.c_int64)]
+                ("prec", ctypes.c_int), ("quad_points", ctypes.c_int64), ("equal_chord", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -363,7 +363,8 @@ class Solver:
         return {f: getattr(inf, f) for f, _ in BemInfo._fields_}
 
     def matrix(self, name: str) -> torch.Tensor:
-        """Copy of an internal matrix as a (rows, cols) complex128 tensor."""
+        """Copy of an internal matrix as a (rows, cols) complex128 tensor (``"Q"``, the real
+        filter basis, as float64; ``"sigma"`` as a float64 vector)."""
         inf = self.info()
         N, r = inf["N"], inf["r"]
         nc = inf["n"] if self._include_kernel() else inf["n"] - 1
@@ -373,6 +374,11 @@ class Solver:
             self._check(self.L.bem_get_matrix(self.h, which, _ptr(out), 0))
             torch.cuda.synchronize(self.device)
             return out
+        if name == "Q":
+            buf = torch.empty((nc, N), dtype=torch.float64, device=self.device)
+            self._check(self.L.bem_get_matrix(self.h, which, _ptr(buf), N))
+            torch.cuda.synchronize(self.device)
+            return buf.T
         rows, cols = {"S": (N, N), "W": (N, N), "N": (N, N), "D": (N, N), "B": (nc, N),
                       "U": (N, r), "Vh": (r, N)}[name]
         buf = torch.empty((cols, rows), dtype=torch.complex128, device=self.device)

@@ -204,8 +204,11 @@ static void free_stage_buffers(bem_ctx* h, int from_stage) {
     free_ptr(h, (void**)&h->rexp); h->rexp_valid = false;
     free_ptr(h, (void**)&h->k1); free_ptr(h, (void**)&h->kpart); h->kpart_slots = 0; h->k1_valid = false;
     free_ptr(h, (void**)&h->seg);
+    free_ptr(h, (void**)&h->gfac);
+    h->general = false;
     tc_release_operands(h);
     free_ptr(h, (void**)&h->B); free_ptr(h, (void**)&h->gm); free_ptr(h, (void**)&h->Q);
+    free_ptr(h, (void**)&h->GQ);
     free_ptr(h, (void**)&h->Bs);
     free_ptr(h, (void**)&h->sigma); free_ptr(h, (void**)&h->E);
     free_ptr(h, (void**)&h->U); free_ptr(h, (void**)&h->Vh);
@@ -274,12 +277,19 @@ static bem_status assemble_begin(bem_handle h, const double* verts, int64_t N, d
     const double hmean = hs[2] / (double)N;
     if (!(hs[0] > 0.0) || !std::isfinite(hs[2]))
         return bem_fail(h, BEM_E_INVALID, "bem_assemble: degenerate or non-finite vertices");
-    if ((hs[1] - hs[0]) > 1e-10 * hmean)
-        return bem_fail(h, BEM_E_UNSUPPORTED, "bem_assemble: mesh is not equal-chord (spread " +
-                                                  std::to_string((hs[1] - hs[0]) / hmean) + ")");
     if (k * hs[1] > 2.0)
         return bem_fail(h, BEM_E_UNSUPPORTED, "bem_assemble: k h > 2 (mesh too coarse for this frequency)");
     h->hbar = hmean;
+    h->hmax = hs[1];
+    // chords equal to rounding (1e-10 of the mean): circulant G and L, Fourier filter basis;
+    // otherwise the general cyclic tridiagonal G and L of mesh.cu
+    h->general = (hs[1] - hs[0]) > 1e-10 * hmean;
+    if (h->general) {
+        if ((st = ensure_alloc(h, (void**)&h->gfac, sizeof(double) * 4 * N)) != BEM_OK) return st;
+        if ((st = launch_cyc_factor(h, 0.0, 1.0, h->gfac)) != BEM_OK) return st;
+    } else {
+        free_ptr(h, (void**)&h->gfac);
+    }
     h->ops = BEM_OP_S | BEM_OP_W | (ops & BEM_OP_D);
     return BEM_OK;
 }
@@ -354,7 +364,13 @@ bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha) {
     h->M = (n_modes - 1) / 2;
     h->alpha = alpha;
     h->beta = (1.0 + 2.0 * alpha) / 4.0;
-    if ((st = launch_fourier_basis(h, h->Q, N, nc, inc, h->gm, h->hbar)) != BEM_OK) return st;
+    if (h->general) {
+        // the lowest eigenvectors of the pencil (L, G), G-orthonormal (gm = 1), and G Q
+        if ((st = ensure_alloc(h, (void**)&h->GQ, sizeof(double) * nc * N)) != BEM_OK) return st;
+        if ((st = general_filter_basis(h, nc, inc)) != BEM_OK) return st;
+    } else {
+        if ((st = launch_fourier_basis(h, h->Q, N, nc, inc, h->gm, h->hbar)) != BEM_OK) return st;
+    }
     cplx *Y1 = nullptr, *tmp = nullptr, *cfix = nullptr;
     Carve cv;
     cv.add((void**)&Y1, sizeof(cplx) * nc * N);
@@ -392,8 +408,8 @@ bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha) {
         if (alpha != 0.0)
             if ((st = dzgemm_realA(h, OP_T, nc, N, N, -alpha, h->Q, N, h->D, N, 1.0, h->B, nc)) != BEM_OK) return st;
     }
-    // B = diag(1/g) B - Q^T/4
-    if ((st = launch_finish_B(h, h->B, h->gm, h->Q, nc, N)) != BEM_OK) return st;
+    // B = diag(1/g) B - Q^T/4  (general mesh: B - (G Q)^T/4, g = 1)
+    if ((st = launch_finish_B(h, h->B, h->gm, h->general ? h->GQ : h->Q, nc, N)) != BEM_OK) return st;
     h->stage = 2;
     return BEM_OK;
 }
@@ -743,6 +759,10 @@ bem_status bem_get_matrix(bem_handle h, int which, void* dst, int64_t ld) {
             if (h->stage < 3) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: not compressed");
             BEM_CUDA(h, cudaMemcpyAsync(dst, h->sigma, sizeof(double) * h->ncols, cudaMemcpyDeviceToDevice, h->stream));
             return BEM_OK;
+        case BEM_MAT_Q:
+            if (h->stage < 2) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: not filtered");
+            if (ld < N) return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: ld < rows");
+            return launch_copy2d(h, dst, ld, h->Q, N, N, h->ncols, sizeof(double));
         default:
             return bem_fail(h, BEM_E_INVALID, "bem_get_matrix: unknown matrix");
     }
@@ -862,6 +882,7 @@ bem_status bem_shape_vjp(bem_handle h, const double* angles, const void* amplitu
     if (h->stage < 2 || !h->S || !h->W)
         return bem_fail(h, BEM_E_INVALID, "bem_shape_vjp: needs S and N assembled and filter_apply");
     if (h->alpha != 0.0) return bem_fail(h, BEM_E_UNSUPPORTED, "bem_shape_vjp: EFIE only (alpha = 0)");
+    if (h->general) return bem_fail(h, BEM_E_UNSUPPORTED, "bem_shape_vjp: equal-chord meshes only");
     if (!angles || !obs_angles || !x_dev || !gu_dev || !lambda_dev || !grad_dev || nrhs < 1 || nrhs > 65535 ||
         nobs < 1 || nobs > 65535)
         return bem_fail(h, BEM_E_INVALID, "bem_shape_vjp: bad arguments");
@@ -1001,6 +1022,7 @@ bem_status bem_get_info(bem_handle h, bem_info* info) {
     unsigned long long q = 0;
     BEM_CUDA(h, cudaMemcpy(&q, h->qpts, sizeof(q), cudaMemcpyDeviceToHost));
     info->quad_points = (int64_t)q;
+    info->equal_chord = h->general ? 0 : 1;
     return BEM_OK;
 }
 

@@ -1313,7 +1313,7 @@ static bem_status asm_prepare(bem_ctx* h, unsigned ops, AsmParams& p, cplx** nea
     p.ld = h->N;
     p.qpts = h->qpts;
     BEM_CUDA(h, cudaMemsetAsync(h->qpts, 0, sizeof(unsigned long long), h->stream));
-    series_coefficients(h->k, 2.0 * h->hbar, &p.sc);
+    series_coefficients(h->k, 2.0 * (h->general ? h->hmax : h->hbar), &p.sc);
     bem_status st = bessel_table(h, &p.btab, &p.btabf);
     if (st != BEM_OK) return st;
     cplx* near = nullptr;
@@ -1957,7 +1957,7 @@ bem_status launch_assemble_vjp(bem_ctx* h, const cplx* OmS, const cplx* OmW, dou
     const float4* tabf = nullptr;
     bem_status st = bessel_table(h, &p.btab, &tabf);
     if (st != BEM_OK) return st;
-    series_coefficients(h->k, 2.0 * h->hbar, &p.sc);
+    series_coefficients(h->k, 2.0 * (h->general ? h->hmax : h->hbar), &p.sc);
     p.OmS = OmS;
     p.OmW = OmW;
     p.grad = grad;

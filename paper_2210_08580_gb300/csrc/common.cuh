@@ -94,6 +94,10 @@ struct bem_ctx {
     // geometry and assembly
     int64_t N = 0;
     double k = 0.0, hbar = 0.0;
+    double hmax = 0.0;                // longest chord
+    bool general = false;             // chords not equal (spread above 1e-10 of the mean):
+                                      // general cyclic tridiagonal G and L (mesh.cu)
+    double* gfac = nullptr;           // 4N: bordered LDL^T of the general Gram matrix
     unsigned ops = 0;
     double* seg = nullptr;            // 5*N: x0, y0, tx, ty, h (SoA)
     cplx *S = nullptr, *W = nullptr, *D = nullptr;
@@ -111,8 +115,11 @@ struct bem_ctx {
     double alpha = 0.0, beta = 0.25;
     cplx* B = nullptr;                // ncols x N, ld = ncols
     cplx* Bs = nullptr;               // diag(sqrt g) B
-    double* gm = nullptr;             // ncols Gram eigenvalues of the Fourier columns
-    double* Q = nullptr;              // N x ncols Fourier basis
+    double* gm = nullptr;             // ncols Gram eigenvalues of the Fourier columns (1 on a
+                                      // general mesh, whose basis is G-orthonormal)
+    double* Q = nullptr;              // N x ncols filter basis: Fourier modes, or on a general
+                                      // mesh the lowest eigenvectors of the pencil (L, G)
+    double* GQ = nullptr;             // N x ncols: G Q (general mesh only)
 
     // compression / factor
     int64_t r = 0;

@@ -48,6 +48,7 @@ bem_status dzgemm_realA(bem_ctx* h, int opa, int64_t M, int64_t Nc, int64_t K, d
                         const double* A, int64_t lda, const cplx* B, int64_t ldb, double beta,
                         cplx* C, int64_t ldc);
 // G^-1 (mode 0) or F^-T = (I + r Z)^-1 * sqrt(6 r/h) (mode 1) along index i of a strided array
+// (equal-chord meshes; on a general mesh the bordered factor of mesh.cu, G = F^T F)
 bem_status apply_gram_inverse(bem_ctx* h, int mode, const cplx* in, cplx* out, cplx* tmp,
                               int64_t N, int64_t ncols, int64_t si, int64_t sc, double hbar,
                               bool conj_out);
@@ -83,5 +84,14 @@ bem_status launch_col_cdot(bem_ctx* h, const cplx* v, int64_t ldv, const cplx* l
                            int64_t cols, cplx* g);
 // out = T x for T: P x n row-major (FP64)
 bem_status launch_row_dot(bem_ctx* h, const double* T, int64_t P, int64_t n, const double* x, double* out);
+// mesh.cu (non-equal-chord meshes)
+// bordered LDL^T of cL L + cG G (4N doubles at fac) on h's stream
+bem_status launch_cyc_factor(bem_ctx* h, double cL, double cG, double* fac);
+// apply_gram_inverse for a general mesh: mode 0 G^-1, mode 1 D^-1/2 L^-1 (rows times F^-1)
+bem_status general_gram_apply(bem_ctx* h, int mode, const cplx* in, cplx* out, int64_t N, int64_t ncols,
+                              int64_t si, int64_t sc, bool conj_out);
+// h->Q, h->GQ, h->gm of a general mesh (nc columns, with the constant mode when inc)
+bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc);
+void general_basis_plan(int64_t N, int64_t n, double perimeter, int64_t* p_out, int* iters_out, double* sigma_out);
 bem_status launch_copy2d(bem_ctx* h, void* dst, int64_t ldd, const void* src, int64_t lds,
                          int64_t rows, int64_t cols, size_t elem);

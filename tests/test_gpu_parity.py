@@ -356,13 +356,17 @@ def test_errors_are_reported_not_raised_on_device(B):
     with pytest.raises(B.BemError) as e:
         s.filter_apply(15)
     assert e.value.status == 1
-    # unequal chords
+    # a mesh too coarse for the wavenumber (k h > 2)
+    with pytest.raises(B.BemError) as e:
+        s.assemble(_cuda(v), 100.0)
+    assert e.value.status == 4
+    # unequal chords are a general mesh, not an error
     vb = v.copy()
     vb[3] *= 1.01
-    with pytest.raises(B.BemError) as e:
-        s.assemble(_cuda(vb), 1.0)
-    assert e.value.status == 4
+    s.assemble(_cuda(vb), 1.0)
+    assert s.info()["equal_chord"] == 0
     s.assemble(_cuda(v), 1.0)
+    assert s.info()["equal_chord"] == 1
     for bad in (14, 2, 64):
         with pytest.raises(B.BemError):
             s.filter_apply(bad)
