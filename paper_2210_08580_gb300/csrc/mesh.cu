@@ -42,40 +42,65 @@ __device__ __forceinline__ double tri_off(const double* h, int i, double cL, dou
     return -cL / h[i] + cG * h[i] * (1.0 / 6.0);
 }
 
-__global__ void k_cyc_factor(const double* __restrict__ h, int N, double cL, double cG, double* fac, int* err) {
+// coefficients for the factorisation: a (diagonal) in the sd slot, b (T_{i,i+1}) in the m slot
+__global__ void k_tri_coef(const double* __restrict__ h, int N, double cL, double cG, double* fac) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    fac[3 * N + i] = tri_diag(h, N, i, cL, cG);
+    fac[2 * N + i] = tri_off(h, i, cL, cG);
+}
+
+// the pivot chain d_{i+1} = a_{i+1} - b_i^2 / d_i with the border (one division per step; the
+// coefficients are read eight steps ahead, each before the step that overwrites its slot)
+#define CYC_CH 8
+__global__ void k_cyc_factor(int N, double* fac, int* err) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     double* l = fac;
     double* dinv = fac + N;
-    double* m = fac + 2 * N;
-    double* sd = fac + 3 * N;
-    // border column: c_0 = T_{0,N-1}, c_{N-2} = T_{N-2,N-1} (both on the same entry when N = 2)
-    const double c0 = tri_off(h, N - 1, cL, cG), cl = tri_off(h, N - 2, cL, cG);
-    double d = tri_diag(h, N, 0, cL, cG);
+    double* m = fac + 2 * N;             // holds b on entry
+    const double* a = fac + 3 * N;       // holds a on entry
+    // border column: c_0 = T_{0,N-1}, c_{N-2} = T_{N-2,N-1}
+    const double c0 = m[N - 1], cl = m[N - 2];
+    double d = a[0];
     double z = c0;                       // z = L'^-1 c, running
     double schur = 0.0;                  // sum z_i^2 / d_i
     bool bad = !(d > 0.0);
     l[0] = 0.0;
-    for (int i = 0;; ++i) {
-        const double di = 1.0 / d;
-        dinv[i] = di;
-        sd[i] = sqrt(di);
-        m[i] = z * di;
-        schur += z * z * di;
-        if (i == N - 2) break;
-        const double b = tri_off(h, i, cL, cG);
-        const double li = b * di;
-        l[i + 1] = li;
-        d = tri_diag(h, N, i + 1, cL, cG) - li * b;
-        bad |= !(d > 0.0);
-        z = ((i + 1 == N - 2) ? cl : 0.0) - li * z;
+    for (int i0 = 0; i0 <= N - 2; i0 += CYC_CH) {
+        double bv[CYC_CH], av[CYC_CH];
+#pragma unroll
+        for (int j = 0; j < CYC_CH; ++j) {
+            const int i = i0 + j;
+            bv[j] = (i <= N - 2) ? m[i] : 0.0;
+            av[j] = (i + 1 <= N - 1) ? a[i + 1] : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < CYC_CH; ++j) {
+            const int i = i0 + j;
+            if (i > N - 2) break;
+            const double di = 1.0 / d;
+            dinv[i] = di;
+            m[i] = z * di;
+            schur = fma(z * z, di, schur);
+            if (i == N - 2) break;
+            const double li = bv[j] * di;
+            l[i + 1] = li;
+            d = fma(-li, bv[j], av[j]);
+            bad |= !(d > 0.0);
+            z = ((i + 1 == N - 2) ? cl : 0.0) - li * z;
+        }
     }
-    const double dl = tri_diag(h, N, N - 1, cL, cG) - schur;
+    const double dl = a[N - 1] - schur;
     bad |= !(dl > 0.0);
     l[N - 1] = 0.0;
     m[N - 1] = 0.0;
     dinv[N - 1] = 1.0 / dl;
-    sd[N - 1] = sqrt(1.0 / dl);
     if (bad) atomicOr(err, DEVERR_SINGULAR);
+}
+
+__global__ void k_fac_sqrt(int N, double* fac) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) fac[3 * N + i] = sqrt(fac[N + i]);
 }
 
 // -----------------------------------------------------------------------------------------
@@ -98,61 +123,131 @@ template <typename T> __device__ __forceinline__ T zero_of();
 template <> __device__ __forceinline__ double zero_of<double>() { return 0.0; }
 template <> __device__ __forceinline__ cplx zero_of<cplx>() { return cmk(0, 0); }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(64) k_cyc_solve(const T* in, T* out, int64_t N, int64_t ncols, int64_t si,
+// One warp per CTA, one lane per column.  The recursion is a chain of dependent steps, so
+// what bounds it is memory latency: chunks of CH elements are loaded one chunk ahead of the
+// one being computed (a chunk's loads only touch elements that no earlier step has written,
+// so in place is allowed), and the coefficients, common to all columns, are loaded once per
+// chunk by the first CH lanes and broadcast by shuffles.  Lanes past ncols follow column 0's
+// reads (in bounds) and store nothing.
+__device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+template <typename T, int MODE, int CH>
+__global__ void __launch_bounds__(32) k_cyc_solve(const T* in, T* out, int64_t N, int64_t ncols, int64_t si,
                                                   int64_t sc, const double* __restrict__ fac, double scale,
                                                   int conj_out) {
-    const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= ncols) return;
+    const int lane = threadIdx.x;
+    const int64_t col = (int64_t)blockIdx.x * 32 + lane;
+    const bool valid = col < ncols;
     const double* l = fac;
     const double* dinv = fac + N;
     const double* m = fac + 2 * N;
     const double* sd = fac + 3 * N;
-    const T* x = in + col * sc;
-    T* y = out + col * sc;
-    // forward: u_0 = x_0, u_i = x_i - l_i u_{i-1} (i <= N-2), u_{N-1} = x_{N-1} - sum m_i u_i
+    const T* x = in + (valid ? col : 0) * sc;
+    T* y = out + (valid ? col : 0) * sc;
+    // forward: u_0 = x_0, u_i = x_i - l_i u_{i-1} (1 <= i <= N-2), u_{N-1} = x_{N-1} - sum m_i u_i
     T prev = x[0];
     T s = zero_of<T>();
-    s = fma_acc(s, m[0], prev);
-    if (MODE == 0) y[0] = sc_mul(prev, dinv[0]);
-    else y[0] = maybe_conj(sc_mul(prev, scale * sd[0]), conj_out);
-    for (int64_t i = 1; i < N - 1; ++i) {
-        const T u = axmy(x[i * si], l[i], prev);
-        s = fma_acc(s, m[i], u);
-        if (MODE == 0) y[i * si] = sc_mul(u, dinv[i]);
-        else y[i * si] = maybe_conj(sc_mul(u, scale * sd[i]), conj_out);
-        prev = u;
+    s = fma_acc(s, __ldg(m), prev);
+    if (valid) y[0] = (MODE == 0) ? sc_mul(prev, __ldg(dinv)) : maybe_conj(sc_mul(prev, scale * __ldg(sd)), conj_out);
+    const int64_t ie = N - 1;                      // forward steps cover [1, ie)
+    T xc[CH], xn[CH];
+    double lc = 0.0, mc = 0.0, dc = 0.0, ln = 0.0, mn = 0.0, dn = 0.0;
+#define CYC_LOAD_F(I0, XV, LV, MV, DV)                                                              \
+    {                                                                                               \
+        _Pragma("unroll") for (int j = 0; j < CH; ++j) {                                            \
+            const int64_t i = (I0) + j;                                                             \
+            XV[j] = (i < ie) ? x[i * si] : zero_of<T>();                                            \
+        }                                                                                           \
+        const int64_t i = (I0) + lane;                                                              \
+        const bool ok = lane < CH && i < ie;                                                        \
+        LV = ok ? __ldg(l + i) : 0.0;                                                               \
+        MV = ok ? __ldg(m + i) : 0.0;                                                               \
+        DV = ok ? ((MODE == 0) ? __ldg(dinv + i) : scale * __ldg(sd + i)) : 0.0;                    \
     }
+    CYC_LOAD_F(1, xc, lc, mc, dc);
+    for (int64_t i0 = 1; i0 < ie; i0 += CH) {
+        if (i0 + CH < ie) CYC_LOAD_F(i0 + CH, xn, ln, mn, dn);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const int64_t i = i0 + j;
+            if (i < ie) {
+                const double lj = shfl_d(lc, j), mj = shfl_d(mc, j), dj = shfl_d(dc, j);
+                const T u = axmy(xc[j], lj, prev);
+                s = fma_acc(s, mj, u);
+                if (valid) y[i * si] = (MODE == 0) ? sc_mul(u, dj) : maybe_conj(sc_mul(u, dj), conj_out);
+                prev = u;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CH; ++j) xc[j] = xn[j];
+        lc = ln; mc = mn; dc = dn;
+    }
+#undef CYC_LOAD_F
     const T ul = tsub(x[(N - 1) * si], s);
     if (MODE == 1) {
-        y[(N - 1) * si] = maybe_conj(sc_mul(ul, scale * sd[N - 1]), conj_out);
+        if (valid) y[(N - 1) * si] = maybe_conj(sc_mul(ul, scale * __ldg(sd + N - 1)), conj_out);
         return;
     }
     // backward: y_{N-1} = w_{N-1}; y_{N-2} = w_{N-2} - m_{N-2} y_{N-1};
-    // y_i = w_i - l_{i+1} y_{i+1} - m_i y_{N-1}
-    const T yl = sc_mul(ul, dinv[N - 1]);
-    y[(N - 1) * si] = maybe_conj(sc_mul(yl, scale), conj_out);
-    T next = axmy(y[(N - 2) * si], m[N - 2], yl);
-    y[(N - 2) * si] = maybe_conj(sc_mul(next, scale), conj_out);
-    for (int64_t i = N - 3; i >= 0; --i) {
-        const T v = axmy(axmy(y[i * si], l[i + 1], next), m[i], yl);
-        y[i * si] = maybe_conj(sc_mul(v, scale), conj_out);
-        next = v;
+    // y_i = w_i - l_{i+1} y_{i+1} - m_i y_{N-1}   (i = N-3 .. 0, in descending chunks)
+    const T yl = sc_mul(ul, __ldg(dinv + N - 1));
+    if (valid) y[(N - 1) * si] = maybe_conj(sc_mul(yl, scale), conj_out);
+    T next = axmy(y[(N - 2) * si], __ldg(m + N - 2), yl);
+    if (valid) y[(N - 2) * si] = maybe_conj(sc_mul(next, scale), conj_out);
+#define CYC_LOAD_B(I0, WV, LV, MV)                                                                  \
+    {                                                                                               \
+        _Pragma("unroll") for (int j = 0; j < CH; ++j) {                                            \
+            const int64_t i = (I0) - j;                                                             \
+            WV[j] = (i >= 0) ? y[i * si] : zero_of<T>();                                            \
+        }                                                                                           \
+        const int64_t i = (I0) - lane;                                                              \
+        const bool ok = lane < CH && i >= 0;                                                        \
+        LV = ok ? __ldg(l + i + 1) : 0.0;                                                           \
+        MV = ok ? __ldg(m + i) : 0.0;                                                               \
     }
+    CYC_LOAD_B(N - 3, xc, lc, mc);
+    for (int64_t i0 = N - 3; i0 >= 0; i0 -= CH) {
+        if (i0 - CH >= 0) CYC_LOAD_B(i0 - CH, xn, ln, mn);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const int64_t i = i0 - j;
+            if (i >= 0) {
+                const double lj = shfl_d(lc, j), mj = shfl_d(mc, j);
+                const T v = axmy(axmy(xc[j], lj, next), mj, yl);
+                if (valid) y[i * si] = maybe_conj(sc_mul(v, scale), conj_out);
+                next = v;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CH; ++j) xc[j] = xn[j];
+        lc = ln; mc = mn;
+    }
+#undef CYC_LOAD_B
 }
 
-// y = T x for the cyclic tridiagonal T above, on the columns of real N x ncols (ld N)
+// tridiagonal coefficients of G (cL = 0, cG = 1) or L (cL = 1, cG = 0): ab[i] = T_ii,
+// ab[N + i] = T_{i,i+1}
+__global__ void k_tri_ab(const double* __restrict__ h, int N, double cL, double cG, double* ab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    ab[i] = tri_diag(h, N, i, cL, cG);
+    ab[N + i] = tri_off(h, i, cL, cG);
+}
+
+// y = T x, T from its coefficients ab, on the columns of a real N x ncols block, column-major
+// (element (i, c) at c N + i) or row-major (at i ncols + c)
+template <bool ROWMAJOR>
 __global__ void k_tri_mul(const double* __restrict__ x, double* __restrict__ y, int64_t N, int64_t ncols,
-                          const double* __restrict__ h, double cL, double cG) {
+                          const double* __restrict__ ab) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= N * ncols) return;
-    const int64_t i = idx % N, c = idx / N;
-    const int n = (int)N;
-    const int ip = (i == 0) ? n - 1 : (int)i - 1, in = (i == N - 1) ? 0 : (int)i + 1;
-    const double* xc = x + c * N;
-    double v = tri_diag(h, n, (int)i, cL, cG) * xc[i];
-    v = fma(tri_off(h, ip, cL, cG), xc[ip], v);
-    v = fma(tri_off(h, (int)i, cL, cG), xc[in], v);
+    const int64_t i = ROWMAJOR ? idx / ncols : idx % N;
+    const int64_t c = ROWMAJOR ? idx % ncols : idx / N;
+    const int64_t ip = (i == 0) ? N - 1 : i - 1, in = (i == N - 1) ? 0 : i + 1;
+    const int64_t si = ROWMAJOR ? ncols : 1, base = ROWMAJOR ? c : c * N;
+    double v = __ldg(ab + i) * x[base + i * si];
+    v = fma(__ldg(ab + N + ip), x[base + ip * si], v);
+    v = fma(__ldg(ab + N + i), x[base + in * si], v);
     y[idx] = v;
 }
 
@@ -164,13 +259,13 @@ __global__ void k_arclength(const double* __restrict__ h, int N, double* s) {
     s[N] = a;
 }
 
-// Starting basis of the subspace iteration: arclength Fourier modes, column c of X (N x p):
-// 1, cos(2 pi m s_i / P), sin(2 pi m s_i / P) for m = 1, 2, ... (cos and sin adjacent)
+// Starting basis of the subspace iteration: arclength Fourier modes, column c of X (N x p,
+// row-major): 1, cos(2 pi m s_i / P), sin(2 pi m s_i / P) for m = 1, 2, ... (cos and sin adjacent)
 __global__ void k_fourier_arc(double* X, int64_t N, int64_t p, const double* __restrict__ s) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= N * p) return;
-    const int64_t i = idx % N;
-    const int c = (int)(idx / N);
+    const int64_t i = idx / p;
+    const int c = (int)(idx % p);
     double v = 1.0;
     if (c > 0) {
         const int m = (c + 1) / 2;
@@ -187,24 +282,28 @@ __global__ void k_fourier_arc(double* X, int64_t N, int64_t p, const double* __r
 // Real FP64 GEMM, C = alpha op(A) op(B) + beta C (column-major), 64 x 64 tiles, 16-deep K
 // slices in shared memory, 4 x 4 outputs per thread.  The basis iteration's products.
 // -----------------------------------------------------------------------------------------
+// Split K: blockIdx.z takes K indices [z kchunk, (z + 1) kchunk) and writes its partial
+// product to C + z zstride (kchunk = K, one z: the plain product).
 template <int OPA, int OPB>
 __global__ void __launch_bounds__(256) k_dgemm(int M, int Nc, int K, double alpha, const double* __restrict__ A,
                                                int64_t lda, const double* __restrict__ B, int64_t ldb, double beta,
-                                               double* C, int64_t ldc) {
+                                               double* C, int64_t ldc, int kchunk, int64_t zstride) {
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
     const int t = threadIdx.x, tx = t % 16, ty = t / 16;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    C += blockIdx.z * zstride;
     double acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int k0 = kb; k0 < ke; k0 += BK) {
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             int mm, kk;
             if (OPA == OP_N) { mm = t % 64; kk = t / 64 + 4 * s; } else { kk = t % 16; mm = t / 16 + 16 * s; }
             const int gm = m0 + mm, gk = k0 + kk;
             double v = 0.0;
-            if (gm < M && gk < K) v = (OPA == OP_N) ? A[gm + (int64_t)gk * lda] : A[gk + (int64_t)gm * lda];
+            if (gm < M && gk < ke) v = (OPA == OP_N) ? A[gm + (int64_t)gk * lda] : A[gk + (int64_t)gm * lda];
             As[kk][mm] = v;
         }
 #pragma unroll
@@ -213,7 +312,7 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int Nc, int K, double alph
             if (OPB == OP_N) { kk = t % 16; nn = t / 16 + 16 * s; } else { nn = t % 64; kk = t / 64 + 4 * s; }
             const int gk = k0 + kk, gn = n0 + nn;
             double v = 0.0;
-            if (gk < K && gn < Nc) v = (OPB == OP_N) ? B[gk + (int64_t)gn * ldb] : B[gn + (int64_t)gk * ldb];
+            if (gk < ke && gn < Nc) v = (OPB == OP_N) ? B[gk + (int64_t)gn * ldb] : B[gn + (int64_t)gk * ldb];
             Bs[kk][nn] = v;
         }
         __syncthreads();
@@ -245,16 +344,27 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int Nc, int K, double alph
     }
 }
 
+// C = sum over z of P[z] (fixed order), count entries each
+__global__ void k_sum_splits(const double* __restrict__ P, int nz, int64_t count, double* C) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double v = P[i];
+    for (int z = 1; z < nz; ++z) v += P[z * count + i];
+    C[i] = v;
+}
+
 // -----------------------------------------------------------------------------------------
 // One CTA: upper Cholesky factor of a small SPD matrix, C + shift I = R^T R (R in C's upper
-// triangle, in place; C column-major, ld p), and, with want_inv, Rinv = R^-1 (upper, the
-// strict lower part zeroed).  A pivot that is not positive sets DEVERR_SINGULAR (and is
-// replaced by 1 so the kernel finishes).  Rc, when given, receives R as complex (strict
-// lower part zero), the input form of the Jacobi SVD.
+// triangle, in place; C column-major, ld p), row j staged in shared memory for the trailing
+// update.  Afterwards R is mirrored into the strict lower triangle (C[k + i p] = R_ik), where a
+// row of R is contiguous, and, when Rc is given, copied as complex (strict lower part zero: the
+// input of the Jacobi SVD).  A pivot that is not positive sets DEVERR_SINGULAR (and is
+// replaced by 1 so the kernel finishes).
 // -----------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_chol_inv(double* C, int p, double shift, double* Rinv, cplx* Rc, int* err) {
+__global__ void __launch_bounds__(1024) k_chol(double* C, int p, double shift, cplx* Rc, int* err) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     __shared__ double s_rjj;
+    __shared__ double srow[1024];          // row j of R (p <= 1023)
     if (shift != 0.0)
         for (int j = tid; j < p; j += nt) C[j + (int64_t)j * p] += shift;
     __syncthreads();
@@ -268,31 +378,45 @@ __global__ void __launch_bounds__(1024) k_chol_inv(double* C, int p, double shif
         }
         __syncthreads();
         const double ir = 1.0 / s_rjj;
-        for (int k = j + 1 + tid; k < p; k += nt) C[j + (int64_t)k * p] *= ir;
+        for (int k = j + 1 + tid; k < p; k += nt) {
+            const double v = C[j + (int64_t)k * p] * ir;
+            C[j + (int64_t)k * p] = v;
+            srow[k] = v;
+        }
         __syncthreads();
         // trailing update of the upper triangle: C_ik -= R_ji R_jk (j < i <= k)
         for (int k = j + 1 + warp; k < p; k += nw) {
-            const double rjk = C[j + (int64_t)k * p];
-            for (int i = j + 1 + lane; i <= k; i += 32) C[i + (int64_t)k * p] = fma(-C[j + (int64_t)i * p], rjk, C[i + (int64_t)k * p]);
+            const double rjk = srow[k];
+            for (int i = j + 1 + lane; i <= k; i += 32) C[i + (int64_t)k * p] = fma(-srow[i], rjk, C[i + (int64_t)k * p]);
         }
         __syncthreads();
     }
-    if (Rc)
-        for (int64_t idx = tid; idx < (int64_t)p * p; idx += nt) {
-            const int i = (int)(idx % p), k = (int)(idx / p);
-            Rc[idx] = cmk(i <= k ? C[idx] : 0.0, 0.0);
-        }
-    if (!Rinv) return;
-    // column j of R^-1 by back substitution (one thread per column)
-    for (int j = tid; j < p; j += nt) {
-        double* x = Rinv + (int64_t)j * p;
-        for (int i = j + 1; i < p; ++i) x[i] = 0.0;
-        x[j] = 1.0 / C[j + (int64_t)j * p];
-        for (int i = j - 1; i >= 0; --i) {
-            double acc = 0.0;
-            for (int k = i + 1; k <= j; ++k) acc = fma(C[i + (int64_t)k * p], x[k], acc);
-            x[i] = -acc / C[i + (int64_t)i * p];
-        }
+    for (int64_t idx = tid; idx < (int64_t)p * p; idx += nt) {
+        const int i = (int)(idx % p), k = (int)(idx / p);
+        if (i < k) C[k + (int64_t)i * p] = C[idx];            // R_ik into the lower triangle
+        if (Rc) Rc[idx] = cmk(i <= k ? C[idx] : 0.0, 0.0);
+    }
+}
+
+// Rinv = R^-1 (upper, ld p; strict lower part zero) from the mirrored factor of k_chol: one
+// warp per column, x_i = -(sum_{k=i+1..j} R_ik x_k) / R_ii, the sum over the lanes (R_ik at
+// C[k + i p], contiguous in k) reduced in a fixed order
+__global__ void __launch_bounds__(256) k_tri_inv(const double* __restrict__ C, int p, double* Rinv) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= p) return;
+    double* x = Rinv + (int64_t)j * p;
+    for (int i = j + 1 + lane; i < p; i += 32) x[i] = 0.0;
+    if (lane == 0) x[j] = 1.0 / C[j + (int64_t)j * p];
+    __syncwarp();
+    for (int i = j - 1; i >= 0; --i) {
+        const double* ri = C + (int64_t)i * p;
+        double acc = 0.0;
+        for (int k = i + 1 + lane; k <= j; k += 32) acc = fma(ri[k], x[k], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) x[i] = -acc / C[i + (int64_t)i * p];
+        __syncwarp();
     }
 }
 
@@ -331,7 +455,11 @@ struct WorkParts {
 }  // namespace
 
 bem_status launch_cyc_factor(bem_ctx* h, double cL, double cG, double* fac) {
-    BEM_TIMED(h, "k_cyc_factor", (k_cyc_factor<<<1, 1, 0, h->stream>>>(h->seg + 4 * h->N, (int)h->N, cL, cG, fac, h->dev_err)));
+    const int N = (int)h->N;
+    const unsigned g = (unsigned)((N + 255) / 256);
+    BEM_TIMED(h, "k_cyc_factor", (k_tri_coef<<<g, 256, 0, h->stream>>>(h->seg + 4 * h->N, N, cL, cG, fac),
+                                  k_cyc_factor<<<1, 1, 0, h->stream>>>(N, fac, h->dev_err),
+                                  k_fac_sqrt<<<g, 256, 0, h->stream>>>(N, fac)));
     BEM_LAUNCH(h, "k_cyc_factor");
     return BEM_OK;
 }
@@ -339,37 +467,66 @@ bem_status launch_cyc_factor(bem_ctx* h, double cL, double cG, double* fac) {
 bem_status general_gram_apply(bem_ctx* h, int mode, const cplx* in, cplx* out, int64_t N, int64_t ncols,
                               int64_t si, int64_t sc, bool conj_out) {
     if (!h->gfac) return bem_fail(h, BEM_E_INVALID, "Gram solve: no factor of the general Gram matrix");
-    const unsigned blocks = (unsigned)((ncols + 63) / 64);
+    const unsigned blocks = (unsigned)((ncols + 31) / 32);      // one warp per CTA: more SMs' FP64 pipes
     if (mode == 0) {
-        BEM_TIMED(h, "k_cyc_solve", (k_cyc_solve<cplx, 0><<<blocks, 64, 0, h->stream>>>(in, out, N, ncols, si, sc, h->gfac,
+        BEM_TIMED(h, "k_cyc_solve", (k_cyc_solve<cplx, 0, 8><<<blocks, 32, 0, h->stream>>>(in, out, N, ncols, si, sc, h->gfac,
                                                                                       1.0, conj_out ? 1 : 0)));
     } else {
-        BEM_TIMED(h, "k_cyc_solve", (k_cyc_solve<cplx, 1><<<blocks, 64, 0, h->stream>>>(in, out, N, ncols, si, sc, h->gfac,
+        BEM_TIMED(h, "k_cyc_solve", (k_cyc_solve<cplx, 1, 8><<<blocks, 32, 0, h->stream>>>(in, out, N, ncols, si, sc, h->gfac,
                                                                                       1.0, conj_out ? 1 : 0)));
     }
     BEM_LAUNCH(h, "k_cyc_solve");
     return BEM_OK;
 }
 
-static bem_status dgemm(bem_ctx* h, int opa, int opb, int64_t M, int64_t Nc, int64_t K, double alpha, const double* A,
-                        int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
-    dim3 grid((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
-    if (opa == OP_T && opb == OP_N) {
-        BEM_TIMED(h, "k_dgemm", (k_dgemm<OP_T, OP_N><<<grid, 256, 0, h->stream>>>((int)M, (int)Nc, (int)K, alpha, A, lda, B, ldb,
-                                                                                   beta, C, ldc)));
-    } else {
-        BEM_TIMED(h, "k_dgemm", (k_dgemm<OP_N, OP_N><<<grid, 256, 0, h->stream>>>((int)M, (int)Nc, (int)K, alpha, A, lda, B, ldb,
-                                                                                   beta, C, ldc)));
-    }
+template <int OPA, int OPB>
+static bem_status dgemm_t(bem_ctx* h, int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
+                          int64_t ldb, double* C, int64_t ldc, int nz = 1, int kchunk = 0, int64_t zstride = 0) {
+    dim3 grid((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64), (unsigned)nz);
+    BEM_TIMED(h, "k_dgemm", (k_dgemm<OPA, OPB><<<grid, 256, 0, h->stream>>>((int)M, (int)Nc, (int)K, 1.0, A, lda, B, ldb, 0.0,
+                                                                             C, ldc, nz == 1 ? (int)K : kchunk, zstride)));
     BEM_LAUNCH(h, "k_dgemm");
     return BEM_OK;
 }
 
-static bem_status tri_mul(bem_ctx* h, const double* x, double* y, int64_t ncols, double cL, double cG) {
+// splits of the long-K Gram products (p x p over K = N): enough CTAs for two waves
+static int gram_splits(int64_t p, int64_t K) {
+    const int64_t tiles = ((p + 63) / 64) * ((p + 63) / 64);
+    int64_t z = (2 * 152 + tiles - 1) / tiles;
+    z = std::min<int64_t>(z, std::max<int64_t>(1, K / 256));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(z, 64));
+}
+
+// C = X^T Z (p x p, ld p) for row-major N x p blocks X, Z (column-major p x N, ld p), split
+// over N into `part` (gram_splits(p, N) p^2 doubles) and summed in a fixed order
+static bem_status gram_product(bem_ctx* h, int64_t p, int64_t N, const double* X, const double* Z, double* C, double* part) {
+    const int nz = gram_splits(p, N);
+    int kchunk = (int)((N + nz - 1) / nz);
+    kchunk = (kchunk + 15) & ~15;
+    bem_status st = dgemm_t<OP_N, OP_T>(h, p, p, N, X, p, Z, p, part, p, nz, kchunk, p * p);
+    if (st != BEM_OK) return st;
+    BEM_TIMED(h, "k_sum_splits", (k_sum_splits<<<(unsigned)((p * p + 255) / 256), 256, 0, h->stream>>>(part, nz, p * p, C)));
+    BEM_LAUNCH(h, "k_sum_splits");
+    return BEM_OK;
+}
+
+static bem_status tri_mul(bem_ctx* h, const double* x, double* y, int64_t ncols, const double* ab, bool rowmajor) {
     const int64_t tot = h->N * ncols;
-    BEM_TIMED(h, "k_tri_mul", (k_tri_mul<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(x, y, h->N, ncols,
-                                                                                             h->seg + 4 * h->N, cL, cG)));
+    const unsigned g = (unsigned)((tot + 255) / 256);
+    if (rowmajor) {
+        BEM_TIMED(h, "k_tri_mul", (k_tri_mul<true><<<g, 256, 0, h->stream>>>(x, y, h->N, ncols, ab)));
+    } else {
+        BEM_TIMED(h, "k_tri_mul", (k_tri_mul<false><<<g, 256, 0, h->stream>>>(x, y, h->N, ncols, ab)));
+    }
     BEM_LAUNCH(h, "k_tri_mul");
+    return BEM_OK;
+}
+
+static bem_status chol_inv(bem_ctx* h, double* C, int64_t p, double* Rinv) {
+    BEM_TIMED(h, "k_chol", (k_chol<<<1, 1024, 0, h->stream>>>(C, (int)p, 0.0, nullptr, h->dev_err)));
+    BEM_LAUNCH(h, "k_chol");
+    BEM_TIMED(h, "k_tri_inv", (k_tri_inv<<<(unsigned)((p + 7) / 8), 256, 0, h->stream>>>(C, (int)p, Rinv)));
+    BEM_LAUNCH(h, "k_tri_inv");
     return BEM_OK;
 }
 
@@ -416,7 +573,7 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     double sigma;
     general_basis_plan(N, n, h->hbar * (double)N, &p, &iters, &sigma);
     double *X = nullptr, *Y = nullptr, *Z = nullptr, *C = nullptr, *Rinv = nullptr, *Cf = nullptr, *fac = nullptr,
-           *s = nullptr, *sig = nullptr;
+           *s = nullptr, *sig = nullptr, *part = nullptr, *abG = nullptr, *abL = nullptr;
     cplx *Rc = nullptr, *E = nullptr;
     int* perm = nullptr;
     void* jac = nullptr;
@@ -426,8 +583,11 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     cv.add((void**)&Z, sizeof(double) * N * p);
     cv.add((void**)&C, sizeof(double) * p * p);
     cv.add((void**)&Rinv, sizeof(double) * p * p);
+    cv.add((void**)&part, sizeof(double) * p * p * gram_splits(p, N));
     cv.add((void**)&Cf, sizeof(double) * p * nc);
     cv.add((void**)&fac, sizeof(double) * 4 * N);
+    cv.add((void**)&abG, sizeof(double) * 2 * N);
+    cv.add((void**)&abL, sizeof(double) * 2 * N);
     cv.add((void**)&s, sizeof(double) * (N + 1));
     cv.add((void**)&sig, sizeof(double) * p);
     cv.add((void**)&Rc, sizeof(cplx) * p * p);
@@ -436,40 +596,49 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     cv.add(&jac, jacobi_scratch_bytes((int)p));
     bem_status st;
     if ((st = cv.commit(h)) != BEM_OK) return st;
-    // (L + sigma G) = L D L^T for the shift-and-invert steps
+    // (L + sigma G) = L D L^T for the shift-and-invert steps; the coefficients of G and L
     if ((st = launch_cyc_factor(h, 1.0, sigma, fac)) != BEM_OK) return st;
+    const unsigned gN = (unsigned)((N + 255) / 256);
+    BEM_TIMED(h, "k_tri_ab", (k_tri_ab<<<gN, 256, 0, h->stream>>>(h->seg + 4 * N, (int)N, 0.0, 1.0, abG),
+                              k_tri_ab<<<gN, 256, 0, h->stream>>>(h->seg + 4 * N, (int)N, 1.0, 0.0, abL)));
+    BEM_LAUNCH(h, "k_tri_ab");
     BEM_TIMED(h, "k_arclength", (k_arclength<<<1, 1, 0, h->stream>>>(h->seg + 4 * N, (int)N, s)));
     BEM_LAUNCH(h, "k_arclength");
     BEM_TIMED(h, "k_fourier_arc", (k_fourier_arc<<<(unsigned)((N * p + 255) / 256), 256, 0, h->stream>>>(X, N, p, s)));
     BEM_LAUNCH(h, "k_fourier_arc");
-    // G-orthonormalise the columns of `in` into `out`: R^T R = in^T G in, out = in R^-1
+    // The basis blocks X, Y, Z are row-major N x p, so the solves' threads (one per column)
+    // read adjacent addresses.  G-orthonormalise the columns of `in` into `out`:
+    // R^T R = in^T G in, out = in R^-1 (as out^T = R^-T in^T)
     auto cholqr = [&](const double* in, double* out) -> bem_status {
         bem_status q;
-        if ((q = tri_mul(h, in, Z, p, 0.0, 1.0)) != BEM_OK) return q;
-        if ((q = dgemm(h, OP_T, OP_N, p, p, N, 1.0, in, N, Z, N, 0.0, C, p)) != BEM_OK) return q;
-        BEM_TIMED(h, "k_chol_inv", (k_chol_inv<<<1, 1024, 0, h->stream>>>(C, (int)p, 0.0, Rinv, nullptr, h->dev_err)));
-        BEM_LAUNCH(h, "k_chol_inv");
-        return dgemm(h, OP_N, OP_N, N, p, p, 1.0, in, N, Rinv, p, 0.0, out, N);
+        if ((q = tri_mul(h, in, Z, p, abG, true)) != BEM_OK) return q;
+        if ((q = gram_product(h, p, N, in, Z, C, part)) != BEM_OK) return q;
+        if ((q = chol_inv(h, C, p, Rinv)) != BEM_OK) return q;
+        return dgemm_t<OP_T, OP_N>(h, p, N, p, Rinv, p, in, p, out, p);
     };
     if ((st = cholqr(X, Y)) != BEM_OK) return st;
     std::swap(X, Y);
-    const unsigned sblocks = (unsigned)((p + 63) / 64);
+    const unsigned sblocks = (unsigned)((p + 31) / 32);
     for (int it = 0; it < iters; ++it) {
         // Y = (L + sigma G)^-1 G X
-        if ((st = tri_mul(h, X, Z, p, 0.0, 1.0)) != BEM_OK) return st;
-        BEM_TIMED(h, "k_cyc_solve", (k_cyc_solve<double, 0><<<sblocks, 64, 0, h->stream>>>(Z, Y, N, p, 1, N, fac, 1.0, 0)));
+        if ((st = tri_mul(h, X, Z, p, abG, true)) != BEM_OK) return st;
+        BEM_TIMED(h, "k_cyc_solve", (k_cyc_solve<double, 0, 16><<<sblocks, 32, 0, h->stream>>>(Z, Y, N, p, p, 1, fac, 1.0, 0)));
         BEM_LAUNCH(h, "k_cyc_solve");
-        if ((st = cholqr(Y, X)) != BEM_OK) return st;
+        // The span does not depend on the basis, so the basis is re-orthonormalised only every
+        // third step (its condition grows by at most (lambda_p + sigma)/sigma, about 17, per
+        // step) and at each of the last three, which set the final accuracy.
+        if (it % 3 == 2 || it >= iters - 3) {
+            if ((st = cholqr(Y, X)) != BEM_OK) return st;
+        } else {
+            std::swap(X, Y);
+        }
     }
-    // a second Cholesky QR restores G-orthonormality to rounding
-    if ((st = cholqr(X, Y)) != BEM_OK) return st;
-    std::swap(X, Y);
     // Rayleigh-Ritz: A = X^T L X; the eigenvectors of A + sigma I are the right singular
     // vectors of its Cholesky factor (Jacobi SVD, sorted by decreasing singular value)
-    if ((st = tri_mul(h, X, Z, p, 1.0, 0.0)) != BEM_OK) return st;
-    if ((st = dgemm(h, OP_T, OP_N, p, p, N, 1.0, X, N, Z, N, 0.0, C, p)) != BEM_OK) return st;
-    BEM_TIMED(h, "k_chol_inv", (k_chol_inv<<<1, 1024, 0, h->stream>>>(C, (int)p, sigma, nullptr, Rc, h->dev_err)));
-    BEM_LAUNCH(h, "k_chol_inv");
+    if ((st = tri_mul(h, X, Z, p, abL, true)) != BEM_OK) return st;
+    if ((st = gram_product(h, p, N, X, Z, C, part)) != BEM_OK) return st;
+    BEM_TIMED(h, "k_chol", (k_chol<<<1, 1024, 0, h->stream>>>(C, (int)p, sigma, Rc, h->dev_err)));
+    BEM_LAUNCH(h, "k_chol");
     BEM_TIMED(h, "k_iota", (k_iota<<<(unsigned)((p + 255) / 256), 256, 0, h->stream>>>(perm, (int)p)));
     BEM_LAUNCH(h, "k_iota");
     if ((st = launch_jacobi_svd(h, Rc, (int)p, perm, sig, E, jac)) != BEM_OK) return st;
@@ -478,7 +647,8 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     BEM_TIMED(h, "k_take_cols", (k_take_cols<<<(unsigned)((p * nc + 255) / 256), 256, 0, h->stream>>>(E, (int)p, (int)(p - n),
                                                                                                    (int)nc, Cf, h->gm)));
     BEM_LAUNCH(h, "k_take_cols");
-    if ((st = dgemm(h, OP_N, OP_N, N, nc, p, 1.0, X, N, Cf, p, 0.0, h->Q, N)) != BEM_OK) return st;
-    if ((st = tri_mul(h, h->Q, h->GQ, nc, 0.0, 1.0)) != BEM_OK) return st;
+    // Q = X Cf (column-major N x nc)
+    if ((st = dgemm_t<OP_T, OP_N>(h, N, nc, p, X, p, Cf, p, h->Q, N)) != BEM_OK) return st;
+    if ((st = tri_mul(h, h->Q, h->GQ, nc, abG, false)) != BEM_OK) return st;
     return read_basis_err(h);
 }
