@@ -285,7 +285,7 @@ static bem_status assemble_begin(bem_handle h, const double* verts, int64_t N, d
     // otherwise the general cyclic tridiagonal G and L of mesh.cu
     h->general = (hs[1] - hs[0]) > 1e-10 * hmean;
     if (h->general) {
-        if ((st = ensure_alloc(h, (void**)&h->gfac, sizeof(double) * 4 * N)) != BEM_OK) return st;
+        if ((st = ensure_alloc(h, (void**)&h->gfac, cyc_factor_bytes(N))) != BEM_OK) return st;
         if ((st = launch_cyc_factor(h, 0.0, 1.0, h->gfac)) != BEM_OK) return st;
     } else {
         free_ptr(h, (void**)&h->gfac);
@@ -441,10 +441,12 @@ static bem_status compress_impl(bem_ctx* h, double rel_tol, int64_t* rank_out, A
     cv.add((void**)&Qs, sizeof(double) * nc * N);
     cv.add((void**)&perm, sizeof(int) * nc);
     cv.add(&jac, jacobi_scratch_bytes((int)nc));
+    cplx* gtmp = nullptr;                      // scratch of the general mesh's chunked Gram solve
+    if (h->general) cv.add((void**)&gtmp, sizeof(cplx) * nc * N);
     if ((st = cv.commit(h)) != BEM_OK) return st;
     // Bs = diag(sqrt g) B ;  X = (Bs F^-1)^H  (N x nc, stored with row stride nc)
     if ((st = launch_row_scale(h, h->B, h->Bs, h->gm, 1, nc, N, nc)) != BEM_OK) return st;
-    if ((st = apply_gram_inverse(h, 1, h->Bs, X, nullptr, N, nc, nc, 1, h->hbar, true)) != BEM_OK) return st;
+    if ((st = apply_gram_inverse(h, 1, h->Bs, X, gtmp, N, nc, nc, 1, h->hbar, true)) != BEM_OK) return st;
     // B^ = X^H: pivoted QR X P = Q R, then the left singular vectors of R^H, rows permuted
     // back by P, are those of B^
     if ((st = launch_house_qr(h, X, N, (int)nc, R, perm, h->opt.prec == BEM_MIXED_BF16)) != BEM_OK) return st;

@@ -97,7 +97,8 @@ struct bem_ctx {
     double hmax = 0.0;                // longest chord
     bool general = false;             // chords not equal (spread above 1e-10 of the mean):
                                       // general cyclic tridiagonal G and L (mesh.cu)
-    double* gfac = nullptr;           // 4N: bordered LDL^T of the general Gram matrix
+    double* gfac = nullptr;           // bordered LDL^T of the general Gram matrix and the chunk
+                                      // propagators of its solves (mesh.cu)
     unsigned ops = 0;
     double* seg = nullptr;            // 5*N: x0, y0, tx, ty, h (SoA)
     cplx *S = nullptr, *W = nullptr, *D = nullptr;

@@ -263,7 +263,8 @@ __global__ void k_iir(const cplx* __restrict__ in, cplx* __restrict__ out, int64
 
 bem_status apply_gram_inverse(bem_ctx* h, int mode, const cplx* in, cplx* out, cplx* tmp, int64_t N,
                               int64_t ncols, int64_t si, int64_t sc, double hbar, bool conj_out) {
-    if (h->general) return general_gram_apply(h, mode, in, out, N, ncols, si, sc, conj_out);
+    // on a general mesh tmp (when given) holds at least N ncols elements: the chunked solves' scratch
+    if (h->general) return general_gram_apply(h, mode, in, out, tmp, tmp ? (size_t)(N * ncols) : 0, N, ncols, si, sc, conj_out);
     const double r = 2.0 - sqrt(3.0);
     const int64_t nchunk = (N + IIR_CHUNK - 1) / IIR_CHUNK;
     const int64_t threads = nchunk * ncols;

@@ -25,14 +25,18 @@
 #include <algorithm>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "kernels.h"
 
 // -----------------------------------------------------------------------------------------
 // Bordered LDL^T of a cyclic symmetric tridiagonal matrix T with
 //     T_ii = cL (1/h_{i-1} + 1/h_i) + cG (h_{i-1} + h_i)/3,
 //     T_{i,i+1} = T_{i+1,i} = -cL / h_i + cG h_i / 6       (indices mod N)
-// Factor layout (4 N doubles): l[i] (i = 1..N-2, subdiagonal of L), dinv[i] = 1/d_i,
-// m[i] (i = 0..N-2, L's last row), sdinv[i] = d_i^-1/2.  Sequential, one thread: O(N).
+// Factor layout (CYC_FAC N doubles): l[i] (i = 1..N-2, subdiagonal of L), dinv[i] = 1/d_i,
+// m[i] (i = 0..N-2, L's last row), sdinv[i] = d_i^-1/2, then the chunk propagators of the
+// chunked solves: psiF[i] = prod (-l_k) over k from i's forward chunk start to i,
+// psiB[i] = prod (-l_{k+1}) over k from i's backward chunk top down to i, and per forward
+// chunk c msum[c] = sum m_i psiF[i].  The pivot chain is sequential (one thread, O(N)).
 // -----------------------------------------------------------------------------------------
 __device__ __forceinline__ double tri_diag(const double* h, int N, int i, double cL, double cG) {
     const double hp = h[i == 0 ? N - 1 : i - 1], hi = h[i];
@@ -103,6 +107,36 @@ __global__ void k_fac_sqrt(int N, double* fac) {
     if (i < N) fac[3 * N + i] = sqrt(fac[N + i]);
 }
 
+// Chunks of the chunked solves: forward chunk c covers i in [1 + c CL, 1 + (c+1) CL) within
+// [1, N-1); backward chunk c covers i from N-3 - c CL down to N-2 - (c+1) CL within [0, N-2).
+#define CYC_CL 64
+#define CYC_FAC 7
+__host__ __device__ __forceinline__ int64_t cyc_nch(int64_t N) { return (N - 2 + CYC_CL - 1) / CYC_CL; }
+
+__global__ void k_cyc_prop(int64_t N, double* fac) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cyc_nch(N)) return;
+    const double* l = fac;
+    const double* m = fac + 2 * N;
+    double* psiF = fac + 4 * N;
+    double* psiB = fac + 5 * N;
+    double* msum = fac + 6 * N;
+    double psi = 1.0, ms = 0.0;
+    const int64_t s = 1 + c * CYC_CL, e = min(N - 1, s + CYC_CL);
+    for (int64_t i = s; i < e; ++i) {
+        psi *= -l[i];
+        psiF[i] = psi;
+        ms = fma(m[i], psi, ms);
+    }
+    msum[c] = ms;
+    const int64_t t = N - 3 - c * CYC_CL, b = max((int64_t)0, t - CYC_CL + 1);
+    double phi = 1.0;
+    for (int64_t i = t; i >= b; --i) {
+        phi *= -l[i + 1];
+        psiB[i] = phi;
+    }
+}
+
 // -----------------------------------------------------------------------------------------
 // Solves along index i of a strided array (element i of column c at c*sc + i*si), one thread
 // per column.  MODE 0: y = scale T^-1 x (forward L, diagonal, backward L^T).  MODE 1:
@@ -118,6 +152,8 @@ __device__ __forceinline__ cplx maybe_conj(cplx x, int c) { return c ? cmk(x.x, 
 __device__ __forceinline__ double fma_acc(double acc, double a, double x) { return fma(a, x, acc); }
 __device__ __forceinline__ cplx fma_acc(cplx acc, double a, cplx x) { return cmk(fma(a, x.x, acc.x), fma(a, x.y, acc.y)); }
 __device__ __forceinline__ double tsub(double a, double b) { return a - b; }
+__device__ __forceinline__ double tadd(double a, double b) { return a + b; }
+__device__ __forceinline__ cplx tadd(cplx a, cplx b) { return cmk(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ cplx tsub(cplx a, cplx b) { return cmk(a.x - b.x, a.y - b.y); }
 template <typename T> __device__ __forceinline__ T zero_of();
 template <> __device__ __forceinline__ double zero_of<double>() { return 0.0; }
@@ -225,6 +261,141 @@ __global__ void __launch_bounds__(32) k_cyc_solve(const T* in, T* out, int64_t N
 #undef CYC_LOAD_B
 }
 
+// -----------------------------------------------------------------------------------------
+// Chunked solves (MODE 0, T^-1 x; MODE 1, D^-1/2 L^-1 x): the recurrences split into chunks of
+// CYC_CL steps solved from a zero start in parallel (one thread per chunk and column), a
+// sequential pass per column over the chunks that carries the boundary values, and an
+// elementwise pass that adds each chunk's propagator times its incoming value.  Exact in exact
+// arithmetic (the superposition of a linear recurrence); the FP64 work spreads over the whole
+// GPU instead of one lane per column.  part: 2 nch ncols + 2 nch ncols + ncols elements.
+// -----------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_cyc_fwd_local(const T* in, T* out, int64_t N, int64_t ncols, int64_t si, int64_t sc,
+                                const double* __restrict__ fac, T* part) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t col = tid % ncols, c = tid / ncols;
+    if (c >= cyc_nch(N)) return;
+    const double* l = fac;
+    const double* m = fac + 2 * N;
+    const T* x = in + col * sc;
+    T* y = out + col * sc;
+    T u = zero_of<T>(), acc = zero_of<T>();
+    const int64_t s = 1 + c * CYC_CL, e = min(N - 1, s + CYC_CL);
+    for (int64_t i = s; i < e; ++i) {
+        u = axmy(x[i * si], __ldg(l + i), u);
+        acc = fma_acc(acc, __ldg(m + i), u);
+        y[i * si] = u;
+    }
+    part[2 * (c * ncols + col)] = u;
+    part[2 * (c * ncols + col) + 1] = acc;
+}
+
+// per column: carry[c] = u_{s_c - 1}; tail = sum_{i <= N-2} m_i u_i
+template <typename T>
+__global__ void k_cyc_fwd_carry(const T* in, int64_t N, int64_t ncols, int64_t sc, const double* __restrict__ fac,
+                                const T* part, T* carry, T* tail) {
+    const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    const double* m = fac + 2 * N;
+    const double* psiF = fac + 4 * N;
+    const double* msum = fac + 6 * N;
+    const int64_t nch = cyc_nch(N);
+    T cur = in[col * sc];                              // u_0 = x_0
+    T s = zero_of<T>();
+    s = fma_acc(s, m[0], cur);
+    for (int64_t c = 0; c < nch; ++c) {
+        carry[c * ncols + col] = cur;
+        const int64_t e = min(N - 1, 1 + (c + 1) * CYC_CL);
+        s = fma_acc(tadd(s, part[2 * (c * ncols + col) + 1]), msum[c], cur);
+        cur = fma_acc(part[2 * (c * ncols + col)], psiF[e - 1], cur);
+    }
+    tail[col] = s;
+}
+
+template <typename T, int MODE>
+__global__ void k_cyc_fwd_fix(const T* in, T* out, int64_t N, int64_t ncols, int64_t si, int64_t sc,
+                              const double* __restrict__ fac, const T* carry, const T* tail, int conj_out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * ncols) return;
+    const int64_t col = idx % ncols, i = idx / ncols;
+    const double* dinv = fac + N;
+    const double* sd = fac + 3 * N;
+    const double* psiF = fac + 4 * N;
+    T u;
+    if (i == 0) u = in[col * sc];
+    else if (i == N - 1) u = tsub(in[col * sc + (N - 1) * si], tail[col]);
+    else u = fma_acc(out[col * sc + i * si], psiF[i], carry[((i - 1) / CYC_CL) * ncols + col]);
+    out[col * sc + i * si] = (MODE == 0) ? sc_mul(u, dinv[i]) : maybe_conj(sc_mul(u, sd[i]), conj_out);
+}
+
+// backward on w (in place): v_{N-2} = w_{N-2} - m_{N-2} w_{N-1}, v_i = (w_i - m_i w_{N-1}) - l_{i+1} v_{i+1}
+template <typename T>
+__global__ void k_cyc_bwd_local(T* y, int64_t N, int64_t ncols, int64_t si, int64_t sc, const double* __restrict__ fac,
+                                T* part) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t col = tid % ncols, c = tid / ncols;
+    if (c >= cyc_nch(N)) return;
+    const double* l = fac;
+    const double* m = fac + 2 * N;
+    T* yc = y + col * sc;
+    const T yl = yc[(N - 1) * si];
+    T v = zero_of<T>();
+    const int64_t t = N - 3 - c * CYC_CL, b = max((int64_t)0, t - CYC_CL + 1);
+    for (int64_t i = t; i >= b; --i) {
+        v = axmy(axmy(yc[i * si], __ldg(m + i), yl), __ldg(l + i + 1), v);
+        yc[i * si] = v;
+    }
+    part[c * ncols + col] = v;
+}
+
+template <typename T>
+__global__ void k_cyc_bwd_carry(const T* y, int64_t N, int64_t ncols, int64_t si, int64_t sc,
+                                const double* __restrict__ fac, const T* part, T* carry) {
+    const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    const double* m = fac + 2 * N;
+    const double* psiB = fac + 5 * N;
+    const T* yc = y + col * sc;
+    T cur = axmy(yc[(N - 2) * si], m[N - 2], yc[(N - 1) * si]);     // v_{N-2}
+    const int64_t nch = cyc_nch(N);
+    for (int64_t c = 0; c < nch; ++c) {
+        carry[c * ncols + col] = cur;
+        const int64_t t = N - 3 - c * CYC_CL, b = max((int64_t)0, t - CYC_CL + 1);
+        cur = fma_acc(part[c * ncols + col], psiB[b], cur);
+    }
+}
+
+template <typename T>
+__global__ void k_cyc_bwd_fix(T* y, int64_t N, int64_t ncols, int64_t si, int64_t sc, const double* __restrict__ fac,
+                              const T* carry, int conj_out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * ncols) return;
+    const int64_t col = idx % ncols, i = idx / ncols;
+    const double* m = fac + 2 * N;
+    const double* psiB = fac + 5 * N;
+    T* yc = y + col * sc;
+    T v;
+    if (i == N - 1) v = yc[i * si];
+    else if (i == N - 2) v = axmy(yc[i * si], m[N - 2], yc[(N - 1) * si]);
+    else v = fma_acc(yc[i * si], psiB[i], carry[((N - 3 - i) / CYC_CL) * ncols + col]);
+    // every thread of column col reads y[N-1], y[N-2] above; they are rewritten only by
+    // their own threads with values derived from themselves in an earlier pass, so the
+    // final values are written in a separate launch (k_cyc_bwd_ends) to keep reads race-free
+    if (i < N - 2) yc[i * si] = maybe_conj(v, conj_out);
+}
+
+template <typename T>
+__global__ void k_cyc_bwd_ends(T* y, int64_t N, int64_t ncols, int64_t si, int64_t sc, const double* __restrict__ fac,
+                               int conj_out) {
+    const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    const double* m = fac + 2 * N;
+    T* yc = y + col * sc;
+    const T yl = yc[(N - 1) * si];
+    yc[(N - 2) * si] = maybe_conj(axmy(yc[(N - 2) * si], m[N - 2], yl), conj_out);
+    yc[(N - 1) * si] = maybe_conj(yl, conj_out);
+}
+
 // tridiagonal coefficients of G (cL = 0, cG = 1) or L (cL = 1, cG = 0): ab[i] = T_ii,
 // ab[N + i] = T_{i,i+1}
 __global__ void k_tri_ab(const double* __restrict__ h, int N, double cL, double cG, double* ab) {
@@ -279,23 +450,30 @@ __global__ void k_fourier_arc(double* X, int64_t N, int64_t p, const double* __r
 }
 
 // -----------------------------------------------------------------------------------------
-// Real FP64 GEMM, C = alpha op(A) op(B) + beta C (column-major), 64 x 64 tiles, 16-deep K
-// slices in shared memory, 4 x 4 outputs per thread.  The basis iteration's products.
+// Real GEMM C = op(A) op(B) (column-major, FP64 in and out) in double-float on the FP32 pipe:
+// GB300 issues FP32 at 64x its FP64 rate, and in FP64 these products ran at the FP64 roofline.
+// 64 x 64 tiles, 16-deep K slices staged in shared memory as hi + lo float pairs, 4 x 4
+// outputs per thread, Dekker products and two-sum accumulation, results rounded to double.
+// About 48 significant bits per operation, so a K-term sum carries errors of order
+// sqrt(K) 2^-48 of its terms' magnitudes.  Split K: blockIdx.z takes K indices
+// [z kchunk, (z + 1) kchunk) and writes its partial product to C + z zstride.
 // -----------------------------------------------------------------------------------------
-// Split K: blockIdx.z takes K indices [z kchunk, (z + 1) kchunk) and writes its partial
-// product to C + z zstride (kchunk = K, one z: the plain product).
 template <int OPA, int OPB>
-__global__ void __launch_bounds__(256) k_dgemm(int M, int Nc, int K, double alpha, const double* __restrict__ A,
-                                               int64_t lda, const double* __restrict__ B, int64_t ldb, double beta,
-                                               double* C, int64_t ldc, int kchunk, int64_t zstride) {
+__global__ void __launch_bounds__(256) k_dgemm_df(int M, int Nc, int K, const double* __restrict__ A, int64_t lda,
+                                                  const double* __restrict__ B, int64_t ldb, double* C, int64_t ldc,
+                                                  int kchunk, int64_t zstride) {
     constexpr int BM = 64, BN = 64, BK = 16;
-    __shared__ double As[BK][BM + 1];
-    __shared__ double Bs[BK][BN + 1];
+    __shared__ float2 As[BK][BM + 1];
+    __shared__ float2 Bs[BK][BN + 1];
     const int t = threadIdx.x, tx = t % 16, ty = t / 16;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
     C += blockIdx.z * zstride;
-    double acc[4][4] = {};
+    dfl acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = {0.f, 0.f};
     for (int k0 = kb; k0 < ke; k0 += BK) {
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -304,7 +482,8 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int Nc, int K, double alph
             const int gm = m0 + mm, gk = k0 + kk;
             double v = 0.0;
             if (gm < M && gk < ke) v = (OPA == OP_N) ? A[gm + (int64_t)gk * lda] : A[gk + (int64_t)gm * lda];
-            As[kk][mm] = v;
+            const dfl d = dfl_from(v);
+            As[kk][mm] = make_float2(d.hi, d.lo);
         }
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -313,20 +492,21 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int Nc, int K, double alph
             const int gk = k0 + kk, gn = n0 + nn;
             double v = 0.0;
             if (gk < ke && gn < Nc) v = (OPB == OP_N) ? B[gk + (int64_t)gn * ldb] : B[gn + (int64_t)gk * ldb];
-            Bs[kk][nn] = v;
+            const dfl d = dfl_from(v);
+            Bs[kk][nn] = make_float2(d.hi, d.lo);
         }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
         for (int kk = 0; kk < BK; ++kk) {
-            double a[4], b[4];
+            dfl a[4], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+            for (int i = 0; i < 4; ++i) a[i] = dfl_mk(As[kk][tx + 16 * i]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+            for (int j = 0; j < 4; ++j) b[j] = dfl_mk(Bs[kk][ty + 16 * j]);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) acc[i][j] = dfl_fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
@@ -338,8 +518,7 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int Nc, int K, double alph
         for (int j = 0; j < 4; ++j) {
             const int gn = n0 + ty + 16 * j;
             if (gn >= Nc) continue;
-            double* cp = C + gm + (int64_t)gn * ldc;
-            *cp = (beta == 0.0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *cp);
+            C[gm + (int64_t)gn * ldc] = dfl_to(acc[i][j]);
         }
     }
 }
@@ -354,47 +533,63 @@ __global__ void k_sum_splits(const double* __restrict__ P, int nz, int64_t count
 }
 
 // -----------------------------------------------------------------------------------------
-// One CTA: upper Cholesky factor of a small SPD matrix, C + shift I = R^T R (R in C's upper
-// triangle, in place; C column-major, ld p), row j staged in shared memory for the trailing
-// update.  Afterwards R is mirrored into the strict lower triangle (C[k + i p] = R_ik), where a
-// row of R is contiguous, and, when Rc is given, copied as complex (strict lower part zero: the
-// input of the Jacobi SVD).  A pivot that is not positive sets DEVERR_SINGULAR (and is
-// replaced by 1 so the kernel finishes).
+// One CTA: upper Cholesky factor of a small SPD matrix, C + shift I = R^T R (C column-major,
+// ld p), in double-float on the FP32 pipe (one SM's FP64 rate bounded the FP64 version): the
+// upper triangle is copied into W (p^2 float pairs), factored there with row j staged in
+// shared memory for the trailing update, and R written back to C's upper triangle and
+// mirrored into its strict lower triangle (C[k + i p] = R_ik, where a row of R is
+// contiguous); when Rc is given, R is also copied as complex (strict lower part zero: the
+// input of the Jacobi SVD).  The pivots' square roots and reciprocals are taken in FP64.  A
+// pivot that is not positive sets DEVERR_SINGULAR (and is replaced by 1 so the kernel ends).
 // -----------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_chol(double* C, int p, double shift, cplx* Rc, int* err) {
+__global__ void __launch_bounds__(1024) k_chol(double* C, float2* W, int p, double shift, cplx* Rc, int* err) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    __shared__ double s_rjj;
-    __shared__ double srow[1024];          // row j of R (p <= 1023)
-    if (shift != 0.0)
-        for (int j = tid; j < p; j += nt) C[j + (int64_t)j * p] += shift;
+    __shared__ float2 s_ir;
+    __shared__ float2 srow[1024];          // row j of R (p <= 1023)
+    for (int64_t idx = tid; idx < (int64_t)p * p; idx += nt) {
+        const int i = (int)(idx % p), k = (int)(idx / p);
+        if (i <= k) {
+            const dfl d = dfl_from(C[idx] + (i == k ? shift : 0.0));
+            W[idx] = make_float2(d.hi, d.lo);
+        }
+    }
     __syncthreads();
     for (int j = 0; j < p; ++j) {
         if (tid == 0) {
-            double v = C[j + (int64_t)j * p];
+            double v = dfl_to(dfl_mk(W[j + (int64_t)j * p]));
             if (!(v > 0.0)) { atomicOr(err, DEVERR_SINGULAR); v = 1.0; }
-            v = sqrt(v);
-            C[j + (int64_t)j * p] = v;
-            s_rjj = v;
+            const double r = sqrt(v);
+            const dfl dr = dfl_from(r), di = dfl_from(1.0 / r);
+            W[j + (int64_t)j * p] = make_float2(dr.hi, dr.lo);
+            s_ir = make_float2(di.hi, di.lo);
         }
         __syncthreads();
-        const double ir = 1.0 / s_rjj;
+        const dfl ir = dfl_mk(s_ir);
         for (int k = j + 1 + tid; k < p; k += nt) {
-            const double v = C[j + (int64_t)k * p] * ir;
-            C[j + (int64_t)k * p] = v;
-            srow[k] = v;
+            const dfl v = dfl_mul(dfl_mk(W[j + (int64_t)k * p]), ir);
+            W[j + (int64_t)k * p] = make_float2(v.hi, v.lo);
+            srow[k] = make_float2(-v.hi, -v.lo);
         }
         __syncthreads();
-        // trailing update of the upper triangle: C_ik -= R_ji R_jk (j < i <= k)
+        // trailing update of the upper triangle: W_ik -= R_ji R_jk (j < i <= k)
         for (int k = j + 1 + warp; k < p; k += nw) {
-            const double rjk = srow[k];
-            for (int i = j + 1 + lane; i <= k; i += 32) C[i + (int64_t)k * p] = fma(-srow[i], rjk, C[i + (int64_t)k * p]);
+            const dfl rjk = dfl_mk(srow[k]);
+            const dfl nrjk = {-rjk.hi, -rjk.lo};
+            for (int i = j + 1 + lane; i <= k; i += 32) {
+                const dfl w = dfl_fma(dfl_mk(srow[i]), nrjk, dfl_mk(W[i + (int64_t)k * p]));
+                W[i + (int64_t)k * p] = make_float2(w.hi, w.lo);
+            }
         }
         __syncthreads();
     }
     for (int64_t idx = tid; idx < (int64_t)p * p; idx += nt) {
         const int i = (int)(idx % p), k = (int)(idx / p);
-        if (i < k) C[k + (int64_t)i * p] = C[idx];            // R_ik into the lower triangle
-        if (Rc) Rc[idx] = cmk(i <= k ? C[idx] : 0.0, 0.0);
+        if (i <= k) {
+            const double v = dfl_to(dfl_mk(W[idx]));
+            C[idx] = v;
+            if (i < k) C[k + (int64_t)i * p] = v;        // R_ik into the lower triangle
+        }
+        if (Rc) Rc[idx] = cmk(i <= k ? dfl_to(dfl_mk(W[idx])) : 0.0, 0.0);
     }
 }
 
@@ -457,16 +652,57 @@ struct WorkParts {
 bem_status launch_cyc_factor(bem_ctx* h, double cL, double cG, double* fac) {
     const int N = (int)h->N;
     const unsigned g = (unsigned)((N + 255) / 256);
+    const unsigned gc = (unsigned)((cyc_nch(N) + 127) / 128);
     BEM_TIMED(h, "k_cyc_factor", (k_tri_coef<<<g, 256, 0, h->stream>>>(h->seg + 4 * h->N, N, cL, cG, fac),
                                   k_cyc_factor<<<1, 1, 0, h->stream>>>(N, fac, h->dev_err),
-                                  k_fac_sqrt<<<g, 256, 0, h->stream>>>(N, fac)));
+                                  k_fac_sqrt<<<g, 256, 0, h->stream>>>(N, fac),
+                                  k_cyc_prop<<<gc, 128, 0, h->stream>>>((int64_t)N, fac)));
     BEM_LAUNCH(h, "k_cyc_factor");
     return BEM_OK;
 }
 
-bem_status general_gram_apply(bem_ctx* h, int mode, const cplx* in, cplx* out, int64_t N, int64_t ncols,
-                              int64_t si, int64_t sc, bool conj_out) {
+size_t cyc_factor_bytes(int64_t N) { return sizeof(double) * CYC_FAC * (size_t)N; }
+template <typename T>
+static size_t cyc_scratch_elems(int64_t N, int64_t ncols) { return (size_t)(5 * cyc_nch(N) * ncols + ncols); }
+
+// the chunked solve of mode 0 (T^-1) or 1 (D^-1/2 L^-1) on h's stream; scratch: at least
+// cyc_scratch_elems elements of T
+template <typename T>
+static bem_status cyc_solve_chunked(bem_ctx* h, int mode, const T* in, T* out, int64_t N, int64_t ncols, int64_t si,
+                                    int64_t sc, const double* fac, T* scratch, bool conj_out) {
+    const int64_t nch = cyc_nch(N);
+    T* partF = scratch;                     // 2 nch ncols
+    T* carryF = partF + 2 * nch * ncols;    // nch ncols
+    T* partB = carryF + nch * ncols;        // nch ncols
+    T* carryB = partB + nch * ncols;        // nch ncols
+    T* tail = carryB + nch * ncols;         // ncols
+    const unsigned gl = (unsigned)((nch * ncols + 127) / 128), gcol = (unsigned)((ncols + 127) / 128),
+                   gall = (unsigned)((N * ncols + 255) / 256);
+    const int cj = conj_out ? 1 : 0;
+    BEM_TIMED(h, "k_cyc_solve",
+              (k_cyc_fwd_local<T><<<gl, 128, 0, h->stream>>>(in, out, N, ncols, si, sc, fac, partF),
+               k_cyc_fwd_carry<T><<<gcol, 128, 0, h->stream>>>(in, N, ncols, sc, fac, partF, carryF, tail)));
+    if (mode == 1) {
+        BEM_TIMED(h, "k_cyc_solve", (k_cyc_fwd_fix<T, 1><<<gall, 256, 0, h->stream>>>(in, out, N, ncols, si, sc, fac, carryF,
+                                                                                       tail, cj)));
+        BEM_LAUNCH(h, "k_cyc_solve");
+        return BEM_OK;
+    }
+    BEM_TIMED(h, "k_cyc_solve",
+              (k_cyc_fwd_fix<T, 0><<<gall, 256, 0, h->stream>>>(in, out, N, ncols, si, sc, fac, carryF, tail, 0),
+               k_cyc_bwd_local<T><<<gl, 128, 0, h->stream>>>(out, N, ncols, si, sc, fac, partB),
+               k_cyc_bwd_carry<T><<<gcol, 128, 0, h->stream>>>(out, N, ncols, si, sc, fac, partB, carryB),
+               k_cyc_bwd_fix<T><<<gall, 256, 0, h->stream>>>(out, N, ncols, si, sc, fac, carryB, cj),
+               k_cyc_bwd_ends<T><<<gcol, 128, 0, h->stream>>>(out, N, ncols, si, sc, fac, cj)));
+    BEM_LAUNCH(h, "k_cyc_solve");
+    return BEM_OK;
+}
+
+bem_status general_gram_apply(bem_ctx* h, int mode, const cplx* in, cplx* out, cplx* tmp, size_t tmp_elems, int64_t N,
+                              int64_t ncols, int64_t si, int64_t sc, bool conj_out) {
     if (!h->gfac) return bem_fail(h, BEM_E_INVALID, "Gram solve: no factor of the general Gram matrix");
+    if (tmp && tmp_elems >= cyc_scratch_elems<cplx>(N, ncols))
+        return cyc_solve_chunked<cplx>(h, mode, in, out, N, ncols, si, sc, h->gfac, tmp, conj_out);
     const unsigned blocks = (unsigned)((ncols + 31) / 32);      // one warp per CTA: more SMs' FP64 pipes
     if (mode == 0) {
         BEM_TIMED(h, "k_cyc_solve", (k_cyc_solve<cplx, 0, 8><<<blocks, 32, 0, h->stream>>>(in, out, N, ncols, si, sc, h->gfac,
@@ -483,9 +719,9 @@ template <int OPA, int OPB>
 static bem_status dgemm_t(bem_ctx* h, int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
                           int64_t ldb, double* C, int64_t ldc, int nz = 1, int kchunk = 0, int64_t zstride = 0) {
     dim3 grid((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64), (unsigned)nz);
-    BEM_TIMED(h, "k_dgemm", (k_dgemm<OPA, OPB><<<grid, 256, 0, h->stream>>>((int)M, (int)Nc, (int)K, 1.0, A, lda, B, ldb, 0.0,
-                                                                             C, ldc, nz == 1 ? (int)K : kchunk, zstride)));
-    BEM_LAUNCH(h, "k_dgemm");
+    BEM_TIMED(h, "k_dgemm_df", (k_dgemm_df<OPA, OPB><<<grid, 256, 0, h->stream>>>((int)M, (int)Nc, (int)K, A, lda, B, ldb,
+                                                                                    C, ldc, nz == 1 ? (int)K : kchunk, zstride)));
+    BEM_LAUNCH(h, "k_dgemm_df");
     return BEM_OK;
 }
 
@@ -522,8 +758,9 @@ static bem_status tri_mul(bem_ctx* h, const double* x, double* y, int64_t ncols,
     return BEM_OK;
 }
 
-static bem_status chol_inv(bem_ctx* h, double* C, int64_t p, double* Rinv) {
-    BEM_TIMED(h, "k_chol", (k_chol<<<1, 1024, 0, h->stream>>>(C, (int)p, 0.0, nullptr, h->dev_err)));
+// W: p^2 float2 scratch of the factorisation
+static bem_status chol_inv(bem_ctx* h, double* C, float2* W, int64_t p, double* Rinv) {
+    BEM_TIMED(h, "k_chol", (k_chol<<<1, 1024, 0, h->stream>>>(C, W, (int)p, 0.0, nullptr, h->dev_err)));
     BEM_LAUNCH(h, "k_chol");
     BEM_TIMED(h, "k_tri_inv", (k_tri_inv<<<(unsigned)((p + 7) / 8), 256, 0, h->stream>>>(C, (int)p, Rinv)));
     BEM_LAUNCH(h, "k_tri_inv");
@@ -573,8 +810,9 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     double sigma;
     general_basis_plan(N, n, h->hbar * (double)N, &p, &iters, &sigma);
     double *X = nullptr, *Y = nullptr, *Z = nullptr, *C = nullptr, *Rinv = nullptr, *Cf = nullptr, *fac = nullptr,
-           *s = nullptr, *sig = nullptr, *part = nullptr, *abG = nullptr, *abL = nullptr;
+           *s = nullptr, *sig = nullptr, *part = nullptr, *abG = nullptr, *abL = nullptr, *cscr = nullptr;
     cplx *Rc = nullptr, *E = nullptr;
+    float2* Wdf = nullptr;
     int* perm = nullptr;
     void* jac = nullptr;
     WorkParts cv;
@@ -583,9 +821,11 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     cv.add((void**)&Z, sizeof(double) * N * p);
     cv.add((void**)&C, sizeof(double) * p * p);
     cv.add((void**)&Rinv, sizeof(double) * p * p);
+    cv.add((void**)&Wdf, sizeof(float2) * p * p);
     cv.add((void**)&part, sizeof(double) * p * p * gram_splits(p, N));
     cv.add((void**)&Cf, sizeof(double) * p * nc);
-    cv.add((void**)&fac, sizeof(double) * 4 * N);
+    cv.add((void**)&fac, cyc_factor_bytes(N));
+    cv.add((void**)&cscr, sizeof(double) * cyc_scratch_elems<double>(N, p));
     cv.add((void**)&abG, sizeof(double) * 2 * N);
     cv.add((void**)&abL, sizeof(double) * 2 * N);
     cv.add((void**)&s, sizeof(double) * (N + 1));
@@ -613,17 +853,15 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
         bem_status q;
         if ((q = tri_mul(h, in, Z, p, abG, true)) != BEM_OK) return q;
         if ((q = gram_product(h, p, N, in, Z, C, part)) != BEM_OK) return q;
-        if ((q = chol_inv(h, C, p, Rinv)) != BEM_OK) return q;
+        if ((q = chol_inv(h, C, Wdf, p, Rinv)) != BEM_OK) return q;
         return dgemm_t<OP_T, OP_N>(h, p, N, p, Rinv, p, in, p, out, p);
     };
     if ((st = cholqr(X, Y)) != BEM_OK) return st;
     std::swap(X, Y);
-    const unsigned sblocks = (unsigned)((p + 31) / 32);
     for (int it = 0; it < iters; ++it) {
         // Y = (L + sigma G)^-1 G X
         if ((st = tri_mul(h, X, Z, p, abG, true)) != BEM_OK) return st;
-        BEM_TIMED(h, "k_cyc_solve", (k_cyc_solve<double, 0, 16><<<sblocks, 32, 0, h->stream>>>(Z, Y, N, p, p, 1, fac, 1.0, 0)));
-        BEM_LAUNCH(h, "k_cyc_solve");
+        if ((st = cyc_solve_chunked<double>(h, 0, Z, Y, N, p, p, 1, fac, cscr, false)) != BEM_OK) return st;
         // The span does not depend on the basis, so the basis is re-orthonormalised only every
         // third step (its condition grows by at most (lambda_p + sigma)/sigma, about 17, per
         // step) and at each of the last three, which set the final accuracy.
@@ -637,7 +875,7 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     // vectors of its Cholesky factor (Jacobi SVD, sorted by decreasing singular value)
     if ((st = tri_mul(h, X, Z, p, abL, true)) != BEM_OK) return st;
     if ((st = gram_product(h, p, N, X, Z, C, part)) != BEM_OK) return st;
-    BEM_TIMED(h, "k_chol", (k_chol<<<1, 1024, 0, h->stream>>>(C, (int)p, sigma, Rc, h->dev_err)));
+    BEM_TIMED(h, "k_chol", (k_chol<<<1, 1024, 0, h->stream>>>(C, Wdf, (int)p, sigma, Rc, h->dev_err)));
     BEM_LAUNCH(h, "k_chol");
     BEM_TIMED(h, "k_iota", (k_iota<<<(unsigned)((p + 255) / 256), 256, 0, h->stream>>>(perm, (int)p)));
     BEM_LAUNCH(h, "k_iota");
