@@ -95,10 +95,39 @@ def tc_gemm_flops(name, N, nrhs, n_modes, r, S):
     return S * (S + 1) / 2 * 2.0 * parts * M * Nc * K
 
 
-def kernel_roofline(name, cnt, ms, args, n_modes, r, quad_points):
+# double-float multiply-add on the FP32 pipe (Dekker product, two-sum, renormalisation): 15
+# FP32 operations for 2 FP64-equivalent flops
+DF_OPS_PER_FMA = 15
+
+
+def kernel_roofline(name, cnt, ms, args, n_modes, r, quad_points, basis=None):
     """Roofline entry of one kernel (average launch of the timed region)."""
     avg_s = ms / cnt / 1000.0
     pk = _peaks()
+    if name == "k_dgemm_df" and basis:
+        # the basis iteration's products: every launch but one forms 2 N p^2 flops (the Gram
+        # products X^T (G X) and X^T (L X), the re-orthonormalisation X R^-1); one forms Q = X Cf
+        p, N, nc = basis["block"], args.N, basis["ncols"]
+        fl = ((cnt - 1) * 2.0 * N * p * p + 2.0 * N * p * nc) / cnt
+        ach = fl / avg_s / 1e12
+        peak = FP32_PEAK_TOPS * 2.0 / DF_OPS_PER_FMA
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s (FP64-equivalent, double-float on the FP32 pipe)", "frac": ach / peak,
+                "traffic": None, "ms_per_launch": 1000 * avg_s, "flops_per_launch": fl,
+                "peak_source": f"derived: FP32 pipe (152 SMs x 128 lanes x 2.07 GHz) / {DF_OPS_PER_FMA} ops per "
+                               "double-float multiply-add x 2 flops",
+                "vs_fp64_pipe": {"peak": FP64_PEAK_TFLOPS, "frac": ach / FP64_PEAK_TFLOPS}}
+    if name == "k_chol" and basis:
+        # one CTA: p^3 / 6 double-float multiply-adds against one SM's FP32 pipe
+        p = basis["block"]
+        fl = p ** 3 / 3.0
+        ach = fl / avg_s / 1e12
+        peak = 128 * 2.070e9 / 1e12 * 2.0 / DF_OPS_PER_FMA
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s (FP64-equivalent, one SM's FP32 pipe)", "frac": ach / peak, "traffic": None,
+                "ms_per_launch": 1000 * avg_s, "flops_per_launch": fl,
+                "peak_source": "derived: one SM (one CTA) x 128 FP32 lanes x 2.07 GHz / 15 ops x 2 flops",
+                "note": "a sequence of p pivot steps, each a block barrier: latency, not the pipe, bounds it"}
     if name == "k_assemble":
         ach = quad_points * ASM_OPS_PER_POINT / avg_s / 1e12
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TOPS,
@@ -127,10 +156,10 @@ def kernel_roofline(name, cnt, ms, args, n_modes, r, quad_points):
                           "note": "tensor-pipe occupancy by the split-bf16 digit products (emulation work)"}}
 
 
-def roofline(rep, args, n_modes, r, quad_points, top=3):
+def roofline(rep, args, n_modes, r, quad_points, top=3, basis=None):
     """(dominant kernel's roofline, the top kernels' rooflines by time per step)."""
     order = sorted(rep.items(), key=lambda kv: -kv[1][1])
-    rows = [kernel_roofline(nm, c, ms, args, n_modes, r, quad_points) for nm, (c, ms) in order[:top]]
+    rows = [kernel_roofline(nm, c, ms, args, n_modes, r, quad_points, basis) for nm, (c, ms) in order[:top]]
     # the filter's two products are one step (a4): report Q^T S beside Y2 N when present
     names = [x["kernel"] for x in rows]
     if "tc_filter_YN" in names and "tc_filter_QtS" in rep and "tc_filter_QtS" not in names:
@@ -160,6 +189,9 @@ def parse():
                     help="skip timing the FP64 path beside the mixed path")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 path (median)")
     ap.add_argument("--fp64-warmup", type=int, default=2)
+    ap.add_argument("--mesh", default="equal-chord", choices=["equal-chord", "graded"],
+                    help="graded: the same star meshed at polar angles t + 0.2 sin t (chords differ by up to "
+                         "1.5x), a non-equal-chord mesh with general G and L (computed filter basis)")
     ap.add_argument("--workload", default="single", choices=["single", "batch"],
                     help="single: one N=16384 star (the headline metric); batch: many uneven stars at once")
     ap.add_argument("--batch-count", type=int, default=64)
@@ -408,8 +440,10 @@ def run_batch(args, rank, world):
 
 
 def workload_config(args):
+    mesh = ("" if args.mesh == "equal-chord" else
+            ", mesh at polar angles t + 0.2 sin t (non-equal chords: general G, L, computed filter basis)")
     return {"workload": f"random 8-harmonic star (seed=rank), N={args.N}, k={args.k}, n={2 * args.M + 1}, "
-                        f"tol={args.tol}, {args.nrhs} plane waves",
+                        f"tol={args.tol}, {args.nrhs} plane waves{mesh}", "mesh": args.mesh,
             "N": args.N, "k": args.k, "n_modes": 2 * args.M + 1, "tol": args.tol, "nrhs": args.nrhs,
             "prec": args.prec, "parallelism": f"replicas x{args.gpus}",
             "schedule": ("compress, factor, right-hand sides in turn" if args.no_overlap else
@@ -437,7 +471,10 @@ def main():
     torch.cuda.set_device(dev)
     from paper_2210_08580_gb300 import bem, inputs as I
 
-    verts_np, _, _ = I.equal_chord_mesh(I.random_star(replica_seed(rank)), args.N)
+    if args.mesh == "graded":
+        verts_np, _ = I.parameter_mesh(I.random_star(replica_seed(rank)), args.N, grade=0.2)
+    else:
+        verts_np, _, _ = I.equal_chord_mesh(I.random_star(replica_seed(rank)), args.N)
     ang_np = I.planewave_angles(args.nrhs)
     verts = torch.from_numpy(verts_np).to(dev)
     ang = torch.from_numpy(ang_np).to(dev)
@@ -510,11 +547,16 @@ def main():
 
     # ---- roofline of the dominant kernel
     launches = sum(c for c, _ in rep.values())
-    quad_points = s.info()["quad_points"]
-    roof, roofs = roofline(rep, args, n_modes, info["r"], quad_points)
+    sinfo = s.info()
+    quad_points = sinfo["quad_points"]
+    basis = None
+    if not sinfo["equal_chord"]:
+        basis = {"block": sinfo["basis_block"], "iters": sinfo["basis_iters"],
+                 "ncols": n_modes}                   # the bench keeps the kernel mode (default)
+    roof, roofs = roofline(rep, args, n_modes, info["r"], quad_points, basis=basis)
     # the same rooflines with every kernel running alone (the phase-split step): in the timed
     # steps the right-hand-side product shares its SMs with the compression and factor
-    _, roofs_alone = roofline(rep_alone, args, n_modes, info["r"], quad_points)
+    _, roofs_alone = roofline(rep_alone, args, n_modes, info["r"], quad_points, basis=basis)
 
     # ---- end to end through the Python API with host buffers.  Every step copies its inputs
     # from pinned host memory and its solution back to pinned host memory inside the timed
@@ -607,7 +649,8 @@ def main():
         del v64, x64, x_mixed
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    # the oracle's measured leg is its block route, which takes equal-chord meshes only
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.mesh == "equal-chord":
         m = oracle_measured(args.N, args.nrhs, args.k, args.M, args.tol)
         cpu = {"value": args.nrhs / m["step_s"], "unit": "RHS/s", "cores": m["workers"], "kind": "oracle",
                "sample": oracle_sample_text(m, golden_c3_run()), "phases_s": {
@@ -626,6 +669,8 @@ def main():
                 "roofline": roof, "rooflines": roofs, "rooflines_alone": roofs_alone, "clocks": clk, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu}
         if fp64_cmp:
             line["fp64_path"] = fp64_cmp
+        if basis:
+            line["config"]["filter_basis"] = {"block": basis["block"], "shift_invert_steps": basis["iters"]}
         print(json.dumps(line), flush=True)
     s.close()
     if dist is not None:

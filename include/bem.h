@@ -127,6 +127,8 @@ typedef struct {
                                  spent on separated segment pairs, counted on the device   */
     int equal_chord;          /* 1: the assembled mesh is equal-chord (circulant G, L);
                                  0: general cyclic tridiagonal G, L                        */
+    int basis_block;          /* general mesh: block size p of the filter basis iteration   */
+    int basis_iters;          /* general mesh: its shifted-inverse steps (0 otherwise)      */
 } bem_info;
 
 typedef struct bem_ctx* bem_handle;

@@ -43,7 +43,8 @@ class BemInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("n", ctypes.c_int64), ("r", ctypes.c_int64),
                 ("k", ctypes.c_double), ("h", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("beta", ctypes.c_double), ("sigma_max", ctypes.c_double), ("stage", ctypes.c_int),
-                ("prec", ctypes.c_int), ("quad_points", ctypes.c_int64), ("equal_chord", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("quad_points", ctypes.c_int64), ("equal_chord", ctypes.c_int),
+                ("basis_block", ctypes.c_int), ("basis_iters", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

@@ -1025,6 +1025,8 @@ bem_status bem_get_info(bem_handle h, bem_info* info) {
     BEM_CUDA(h, cudaMemcpy(&q, h->qpts, sizeof(q), cudaMemcpyDeviceToHost));
     info->quad_points = (int64_t)q;
     info->equal_chord = h->general ? 0 : 1;
+    info->basis_block = h->general ? h->basis_block : 0;
+    info->basis_iters = h->general ? h->basis_iters : 0;
     return BEM_OK;
 }
 

@@ -97,6 +97,7 @@ struct bem_ctx {
     double hmax = 0.0;                // longest chord
     bool general = false;             // chords not equal (spread above 1e-10 of the mean):
                                       // general cyclic tridiagonal G and L (mesh.cu)
+    int basis_block = 0, basis_iters = 0;   // subspace iteration of the last general filter basis
     double* gfac = nullptr;           // bordered LDL^T of the general Gram matrix and the chunk
                                       // propagators of its solves (mesh.cu)
     unsigned ops = 0;

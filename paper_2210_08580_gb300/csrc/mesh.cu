@@ -534,18 +534,25 @@ __global__ void k_sum_splits(const double* __restrict__ P, int nz, int64_t count
 
 // -----------------------------------------------------------------------------------------
 // One CTA: upper Cholesky factor of a small SPD matrix, C + shift I = R^T R (C column-major,
-// ld p), in double-float on the FP32 pipe (one SM's FP64 rate bounded the FP64 version): the
-// upper triangle is copied into W (p^2 float pairs), factored there with row j staged in
-// shared memory for the trailing update, and R written back to C's upper triangle and
-// mirrored into its strict lower triangle (C[k + i p] = R_ik, where a row of R is
-// contiguous); when Rc is given, R is also copied as complex (strict lower part zero: the
-// input of the Jacobi SVD).  The pivots' square roots and reciprocals are taken in FP64.  A
-// pivot that is not positive sets DEVERR_SINGULAR (and is replaced by 1 so the kernel ends).
+// ld p), in double-float on the FP32 pipe, blocked by panels of CHOL_NB rows: the upper
+// triangle is copied into W (p^2 float pairs); each panel (its rows of the upper triangle)
+// is staged in shared memory and factored there, written back, and the trailing triangle
+// receives one rank-CHOL_NB update per panel, reading the panel from shared memory (the
+// unblocked form streamed the trailing triangle through the SM at every pivot).  R is then
+// written back to C's upper triangle and mirrored into its strict lower triangle
+// (C[k + i p] = R_ik, where a row of R is contiguous); when Rc is given, R is also copied as
+// complex (strict lower part zero: the input of the Jacobi SVD).  Pivot square roots and
+// reciprocals: one Newton correction of the FP32 values, r = s + (v - s^2)/(2 s) and
+// q + q (1 - q r).  A pivot that is not positive sets DEVERR_SINGULAR (and is replaced by 1
+// so the kernel ends).  Dynamic shared memory: chol_smem_bytes(p).
 // -----------------------------------------------------------------------------------------
+#define CHOL_NB 16
+static size_t chol_smem_bytes(int p) { return sizeof(float2) * CHOL_NB * (size_t)p; }
+
 __global__ void __launch_bounds__(1024) k_chol(double* C, float2* W, int p, double shift, cplx* Rc, int* err) {
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    extern __shared__ float2 pan[];        // CHOL_NB rows x p columns (row r at pan + r p)
     __shared__ float2 s_ir;
-    __shared__ float2 srow[1024];          // row j of R (p <= 1023)
+    const int tid = threadIdx.x, nt = blockDim.x;
     for (int64_t idx = tid; idx < (int64_t)p * p; idx += nt) {
         const int i = (int)(idx % p), k = (int)(idx / p);
         if (i <= k) {
@@ -554,31 +561,59 @@ __global__ void __launch_bounds__(1024) k_chol(double* C, float2* W, int p, doub
         }
     }
     __syncthreads();
-    for (int j = 0; j < p; ++j) {
-        if (tid == 0) {
-            double v = dfl_to(dfl_mk(W[j + (int64_t)j * p]));
-            if (!(v > 0.0)) { atomicOr(err, DEVERR_SINGULAR); v = 1.0; }
-            const double r = sqrt(v);
-            const dfl dr = dfl_from(r), di = dfl_from(1.0 / r);
-            W[j + (int64_t)j * p] = make_float2(dr.hi, dr.lo);
-            s_ir = make_float2(di.hi, di.lo);
+    for (int jb = 0; jb < p; jb += CHOL_NB) {
+        const int nb = min(CHOL_NB, p - jb);
+        for (int idx = tid; idx < nb * p; idx += nt) {
+            const int r = idx / p, k = idx % p;
+            if (k >= jb + r) pan[r * p + k] = W[(jb + r) + (int64_t)k * p];
         }
         __syncthreads();
-        const dfl ir = dfl_mk(s_ir);
-        for (int k = j + 1 + tid; k < p; k += nt) {
-            const dfl v = dfl_mul(dfl_mk(W[j + (int64_t)k * p]), ir);
-            W[j + (int64_t)k * p] = make_float2(v.hi, v.lo);
-            srow[k] = make_float2(-v.hi, -v.lo);
-        }
-        __syncthreads();
-        // trailing update of the upper triangle: W_ik -= R_ji R_jk (j < i <= k)
-        for (int k = j + 1 + warp; k < p; k += nw) {
-            const dfl rjk = dfl_mk(srow[k]);
-            const dfl nrjk = {-rjk.hi, -rjk.lo};
-            for (int i = j + 1 + lane; i <= k; i += 32) {
-                const dfl w = dfl_fma(dfl_mk(srow[i]), nrjk, dfl_mk(W[i + (int64_t)k * p]));
-                W[i + (int64_t)k * p] = make_float2(w.hi, w.lo);
+        for (int jj = 0; jj < nb; ++jj) {
+            const int j = jb + jj;
+            if (tid == 0) {
+                dfl v = dfl_mk(pan[jj * p + j]);
+                if (!(v.hi > 0.0f)) { atomicOr(err, DEVERR_SINGULAR); v = {1.0f, 0.0f}; }
+                const float sr = sqrtf(v.hi);
+                const float res = fmaf(-sr, sr, v.hi) + v.lo;
+                const dfl r = dfl_qts(sr, res / (2.0f * sr));
+                const float q = 1.0f / r.hi;
+                const float e = fmaf(-q, r.hi, 1.0f) - q * r.lo;
+                const dfl ir = dfl_qts(q, q * e);
+                pan[jj * p + j] = make_float2(r.hi, r.lo);
+                s_ir = make_float2(ir.hi, ir.lo);
             }
+            __syncthreads();
+            const dfl ir = dfl_mk(s_ir);
+            for (int k = j + 1 + tid; k < p; k += nt) {
+                const dfl v = dfl_mul(dfl_mk(pan[jj * p + k]), ir);
+                pan[jj * p + k] = make_float2(v.hi, v.lo);
+            }
+            __syncthreads();
+            // the panel's later rows: pan[rr][k] -= R_{j, jb+rr} R_{j, k}  (k >= jb + rr)
+            const int nr = nb - jj - 1, nk = p - j - 1;
+            for (int idx = tid; idx < nr * nk; idx += nt) {
+                const int rr = jj + 1 + idx / nk, k = j + 1 + idx % nk;
+                if (k >= jb + rr) {
+                    const float2 a = pan[jj * p + jb + rr];
+                    const dfl w = dfl_fma(dfl_mk(make_float2(-a.x, -a.y)), dfl_mk(pan[jj * p + k]), dfl_mk(pan[rr * p + k]));
+                    pan[rr * p + k] = make_float2(w.hi, w.lo);
+                }
+            }
+            __syncthreads();
+        }
+        for (int idx = tid; idx < nb * p; idx += nt) {
+            const int r = idx / p, k = idx % p;
+            if (k >= jb + r) W[(jb + r) + (int64_t)k * p] = pan[r * p + k];
+        }
+        // trailing triangle: W_ik -= sum_r R_{jb+r, i} R_{jb+r, k}  (jb + nb <= i <= k)
+        const int t0 = jb + nb, m = p - t0;
+        for (int64_t idx = tid; idx < (int64_t)m * m; idx += nt) {
+            const int i = t0 + (int)(idx % m), k = t0 + (int)(idx / m);
+            if (i > k) continue;
+            dfl acc = {0.f, 0.f};
+            for (int r = 0; r < nb; ++r) acc = dfl_fma(dfl_mk(pan[r * p + i]), dfl_mk(pan[r * p + k]), acc);
+            const dfl w = dfl_sub(dfl_mk(W[i + (int64_t)k * p]), acc);
+            W[i + (int64_t)k * p] = make_float2(w.hi, w.lo);
         }
         __syncthreads();
     }
@@ -759,9 +794,17 @@ static bem_status tri_mul(bem_ctx* h, const double* x, double* y, int64_t ncols,
 }
 
 // W: p^2 float2 scratch of the factorisation
-static bem_status chol_inv(bem_ctx* h, double* C, float2* W, int64_t p, double* Rinv) {
-    BEM_TIMED(h, "k_chol", (k_chol<<<1, 1024, 0, h->stream>>>(C, W, (int)p, 0.0, nullptr, h->dev_err)));
+static bem_status chol_launch(bem_ctx* h, double* C, float2* W, int64_t p, double shift, cplx* Rc) {
+    const size_t sm = chol_smem_bytes((int)p);
+    BEM_CUDA(h, cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    BEM_TIMED(h, "k_chol", (k_chol<<<1, 1024, sm, h->stream>>>(C, W, (int)p, shift, Rc, h->dev_err)));
     BEM_LAUNCH(h, "k_chol");
+    return BEM_OK;
+}
+
+static bem_status chol_inv(bem_ctx* h, double* C, float2* W, int64_t p, double* Rinv) {
+    bem_status st = chol_launch(h, C, W, p, 0.0, nullptr);
+    if (st != BEM_OK) return st;
     BEM_TIMED(h, "k_tri_inv", (k_tri_inv<<<(unsigned)((p + 7) / 8), 256, 0, h->stream>>>(C, (int)p, Rinv)));
     BEM_LAUNCH(h, "k_tri_inv");
     return BEM_OK;
@@ -809,6 +852,8 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     int iters;
     double sigma;
     general_basis_plan(N, n, h->hbar * (double)N, &p, &iters, &sigma);
+    h->basis_block = (int)p;
+    h->basis_iters = iters;
     double *X = nullptr, *Y = nullptr, *Z = nullptr, *C = nullptr, *Rinv = nullptr, *Cf = nullptr, *fac = nullptr,
            *s = nullptr, *sig = nullptr, *part = nullptr, *abG = nullptr, *abL = nullptr, *cscr = nullptr;
     cplx *Rc = nullptr, *E = nullptr;
@@ -875,8 +920,7 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     // vectors of its Cholesky factor (Jacobi SVD, sorted by decreasing singular value)
     if ((st = tri_mul(h, X, Z, p, abL, true)) != BEM_OK) return st;
     if ((st = gram_product(h, p, N, X, Z, C, part)) != BEM_OK) return st;
-    BEM_TIMED(h, "k_chol", (k_chol<<<1, 1024, 0, h->stream>>>(C, Wdf, (int)p, sigma, Rc, h->dev_err)));
-    BEM_LAUNCH(h, "k_chol");
+    if ((st = chol_launch(h, C, Wdf, p, sigma, Rc)) != BEM_OK) return st;
     BEM_TIMED(h, "k_iota", (k_iota<<<(unsigned)((p + 255) / 256), 256, 0, h->stream>>>(perm, (int)p)));
     BEM_LAUNCH(h, "k_iota");
     if ((st = launch_jacobi_svd(h, Rc, (int)p, perm, sig, E, jac)) != BEM_OK) return st;
