@@ -452,8 +452,10 @@ __global__ void k_fourier_arc(double* X, int64_t N, int64_t p, const double* __r
 // -----------------------------------------------------------------------------------------
 // Real GEMM C = op(A) op(B) (column-major, FP64 in and out) in double-float on the FP32 pipe:
 // GB300 issues FP32 at 64x its FP64 rate, and in FP64 these products ran at the FP64 roofline.
-// 64 x 64 tiles, 16-deep K slices staged in shared memory as hi + lo float pairs, 4 x 4
-// outputs per thread, Dekker products and two-sum accumulation, results rounded to double.
+// 64 x 64 tiles, 16-deep K slices staged in shared memory as hi + lo float pairs (split from
+// the bit fields with integer operations: the FP64 pipe's conversions took a third of its
+// cycles; operands below 2^-74 in magnitude, far below the basis' entries, stage as zero),
+// 4 x 4 outputs per thread, Dekker products and two-sum accumulation, results rounded to double.
 // About 48 significant bits per operation, so a K-term sum carries errors of order
 // sqrt(K) 2^-48 of its terms' magnitudes.  Split K: blockIdx.z takes K indices
 // [z kchunk, (z + 1) kchunk) and writes its partial product to C + z zstride.
@@ -482,7 +484,7 @@ __global__ void __launch_bounds__(256) k_dgemm_df(int M, int Nc, int K, const do
             const int gm = m0 + mm, gk = k0 + kk;
             double v = 0.0;
             if (gm < M && gk < ke) v = (OPA == OP_N) ? A[gm + (int64_t)gk * lda] : A[gk + (int64_t)gm * lda];
-            const dfl d = dfl_from(v);
+            const dfl d = dfl_from_bits(v);
             As[kk][mm] = make_float2(d.hi, d.lo);
         }
 #pragma unroll
@@ -492,7 +494,7 @@ __global__ void __launch_bounds__(256) k_dgemm_df(int M, int Nc, int K, const do
             const int gk = k0 + kk, gn = n0 + nn;
             double v = 0.0;
             if (gk < ke && gn < Nc) v = (OPB == OP_N) ? B[gk + (int64_t)gn * ldb] : B[gn + (int64_t)gk * ldb];
-            const dfl d = dfl_from(v);
+            const dfl d = dfl_from_bits(v);
             Bs[kk][nn] = make_float2(d.hi, d.lo);
         }
         __syncthreads();
@@ -855,7 +857,8 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     h->basis_block = (int)p;
     h->basis_iters = iters;
     double *X = nullptr, *Y = nullptr, *Z = nullptr, *C = nullptr, *Rinv = nullptr, *Cf = nullptr, *fac = nullptr,
-           *s = nullptr, *sig = nullptr, *part = nullptr, *abG = nullptr, *abL = nullptr, *cscr = nullptr;
+           *s = nullptr, *sig = nullptr, *part = nullptr, *abG = nullptr, *abL = nullptr, *abGs = nullptr,
+           *cscr = nullptr;
     cplx *Rc = nullptr, *E = nullptr;
     float2* Wdf = nullptr;
     int* perm = nullptr;
@@ -873,6 +876,7 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     cv.add((void**)&cscr, sizeof(double) * cyc_scratch_elems<double>(N, p));
     cv.add((void**)&abG, sizeof(double) * 2 * N);
     cv.add((void**)&abL, sizeof(double) * 2 * N);
+    cv.add((void**)&abGs, sizeof(double) * 2 * N);
     cv.add((void**)&s, sizeof(double) * (N + 1));
     cv.add((void**)&sig, sizeof(double) * p);
     cv.add((void**)&Rc, sizeof(cplx) * p * p);
@@ -884,8 +888,12 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     // (L + sigma G) = L D L^T for the shift-and-invert steps; the coefficients of G and L
     if ((st = launch_cyc_factor(h, 1.0, sigma, fac)) != BEM_OK) return st;
     const unsigned gN = (unsigned)((N + 255) / 256);
+    // the steps apply sigma (L + sigma G)^-1 G, whose eigenvalues sigma / (lambda + sigma) lie in
+    // (0, 1]: the iterates never grow, whatever the curve's size (the double-float products
+    // stage floats)
     BEM_TIMED(h, "k_tri_ab", (k_tri_ab<<<gN, 256, 0, h->stream>>>(h->seg + 4 * N, (int)N, 0.0, 1.0, abG),
-                              k_tri_ab<<<gN, 256, 0, h->stream>>>(h->seg + 4 * N, (int)N, 1.0, 0.0, abL)));
+                              k_tri_ab<<<gN, 256, 0, h->stream>>>(h->seg + 4 * N, (int)N, 1.0, 0.0, abL),
+                              k_tri_ab<<<gN, 256, 0, h->stream>>>(h->seg + 4 * N, (int)N, 0.0, sigma, abGs)));
     BEM_LAUNCH(h, "k_tri_ab");
     BEM_TIMED(h, "k_arclength", (k_arclength<<<1, 1, 0, h->stream>>>(h->seg + 4 * N, (int)N, s)));
     BEM_LAUNCH(h, "k_arclength");
@@ -904,8 +912,8 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     if ((st = cholqr(X, Y)) != BEM_OK) return st;
     std::swap(X, Y);
     for (int it = 0; it < iters; ++it) {
-        // Y = (L + sigma G)^-1 G X
-        if ((st = tri_mul(h, X, Z, p, abG, true)) != BEM_OK) return st;
+        // Y = sigma (L + sigma G)^-1 G X
+        if ((st = tri_mul(h, X, Z, p, abGs, true)) != BEM_OK) return st;
         if ((st = cyc_solve_chunked<double>(h, 0, Z, Y, N, p, p, 1, fac, cscr, false)) != BEM_OK) return st;
         // The span does not depend on the basis, so the basis is re-orthonormalised only every
         // third step (its condition grows by at most (lambda_p + sigma)/sigma, about 17, per
