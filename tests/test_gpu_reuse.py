@@ -53,3 +53,26 @@ def test_reused_handle_matches_fresh_handles(B, prec):
         assert torch.equal(x, x0), (N, n, float((x - x0).abs().max()))
     # and the two visits of the first case agree with each other
     assert torch.equal(got[0][0], got[2][0]) and torch.equal(got[0][0], got[4][0])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_handle_between_equal_chord_and_general_meshes(B, prec):
+    """The same N meshed with equal chords and at graded polar angles, alternately, on one
+    handle: the general mesh's factor, basis and G Q must not leak into the equal-chord
+    problem (nor the other way round)."""
+    star = I.cos_star(1.0, 0.3, 5)
+    eq = torch.from_numpy(I.equal_chord_mesh(star, 256)[0])
+    gr = torch.from_numpy(I.parameter_mesh(star, 256, grade=0.3)[0])
+    seq = [(eq, 21), (gr, 21), (eq, 21), (gr, 31), (gr, 21)]
+    reused = B.Solver(device=0, prec=prec)
+    got = []
+    for v, n in seq:
+        got.append(_run(reused, v, n))
+        assert reused.info()["equal_chord"] == (1 if v is eq else 0)
+    reused.close()
+    for (v, n), (x, r) in zip(seq, got):
+        fresh = B.Solver(device=0, prec=prec)
+        x0, r0 = _run(fresh, v, n)
+        fresh.close()
+        assert r == r0
+        assert torch.equal(x, x0), float((x - x0).abs().max())
