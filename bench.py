@@ -100,15 +100,19 @@ def tc_gemm_flops(name, N, nrhs, n_modes, r, S):
 DF_OPS_PER_FMA = 15
 
 
-def kernel_roofline(name, cnt, ms, args, n_modes, r, quad_points, basis=None):
+def kernel_roofline(name, cnt, ms, args, n_modes, r, quad_points, basis=None, nsteps=1):
     """Roofline entry of one kernel (average launch of the timed region)."""
     avg_s = ms / cnt / 1000.0
     pk = _peaks()
-    if name == "k_dgemm_df" and basis:
-        # the basis iteration's products: every launch but one forms 2 N p^2 flops (the Gram
-        # products X^T (G X) and X^T (L X), the re-orthonormalisation X R^-1); one forms Q = X Cf
+    if name in ("k_dgemm_df", "k_dgemm_df_tri") and basis:
+        # the basis iteration's products: the Gram products X^T (G X) and X^T (L X) form
+        # 2 N p^2 flops each and Q = X Cf (one launch per step) 2 N p n; the re-orthonormalisation
+        # X R^-1 (k_dgemm_df_tri) N p (p + 1), R^-1 being triangular
         p, N, nc = basis["block"], args.N, basis["ncols"]
-        fl = ((cnt - 1) * 2.0 * N * p * p + 2.0 * N * p * nc) / cnt
+        if name == "k_dgemm_df_tri":
+            fl = float(N) * p * (p + 1)
+        else:                                  # one Q = X Cf launch per step among cnt
+            fl = ((cnt - nsteps) * 2.0 * N * p * p + nsteps * 2.0 * N * p * nc) / cnt
         ach = fl / avg_s / 1e12
         peak = FP32_PEAK_TOPS * 2.0 / DF_OPS_PER_FMA
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
@@ -156,10 +160,11 @@ def kernel_roofline(name, cnt, ms, args, n_modes, r, quad_points, basis=None):
                           "note": "tensor-pipe occupancy by the split-bf16 digit products (emulation work)"}}
 
 
-def roofline(rep, args, n_modes, r, quad_points, top=3, basis=None):
-    """(dominant kernel's roofline, the top kernels' rooflines by time per step)."""
+def roofline(rep, args, n_modes, r, quad_points, top=3, basis=None, nsteps=1):
+    """(dominant kernel's roofline, the top kernels' rooflines by time per step); nsteps: the
+    steps the timing report covers."""
     order = sorted(rep.items(), key=lambda kv: -kv[1][1])
-    rows = [kernel_roofline(nm, c, ms, args, n_modes, r, quad_points, basis) for nm, (c, ms) in order[:top]]
+    rows = [kernel_roofline(nm, c, ms, args, n_modes, r, quad_points, basis, nsteps) for nm, (c, ms) in order[:top]]
     # the filter's two products are one step (a4): report Q^T S beside Y2 N when present
     names = [x["kernel"] for x in rows]
     if "tc_filter_YN" in names and "tc_filter_QtS" in rep and "tc_filter_QtS" not in names:
@@ -553,10 +558,10 @@ def main():
     if not sinfo["equal_chord"]:
         basis = {"block": sinfo["basis_block"], "iters": sinfo["basis_iters"],
                  "ncols": n_modes}                   # the bench keeps the kernel mode (default)
-    roof, roofs = roofline(rep, args, n_modes, info["r"], quad_points, basis=basis)
+    roof, roofs = roofline(rep, args, n_modes, info["r"], quad_points, basis=basis, nsteps=args.steps)
     # the same rooflines with every kernel running alone (the phase-split step): in the timed
     # steps the right-hand-side product shares its SMs with the compression and factor
-    _, roofs_alone = roofline(rep_alone, args, n_modes, info["r"], quad_points, basis=basis)
+    _, roofs_alone = roofline(rep_alone, args, n_modes, info["r"], quad_points, basis=basis, nsteps=1)
 
     # ---- end to end through the Python API with host buffers.  Every step copies its inputs
     # from pinned host memory and its solution back to pinned host memory inside the timed

@@ -28,6 +28,12 @@
 #include "dfloat.cuh"
 #include "kernels.h"
 
+// Chunks of the chunked solves: forward chunk c covers i in [1 + c CL, 1 + (c+1) CL) within
+// [1, N-1); backward chunk c covers i from N-3 - c CL down to N-2 - (c+1) CL within [0, N-2).
+#define CYC_CL 64
+#define CYC_FAC 7
+__host__ __device__ __forceinline__ int64_t cyc_nch(int64_t N) { return (N - 2 + CYC_CL - 1) / CYC_CL; }
+
 // -----------------------------------------------------------------------------------------
 // Bordered LDL^T of a cyclic symmetric tridiagonal matrix T with
 //     T_ii = cL (1/h_{i-1} + 1/h_i) + cG (h_{i-1} + h_i)/3,
@@ -36,7 +42,7 @@
 // m[i] (i = 0..N-2, L's last row), sdinv[i] = d_i^-1/2, then the chunk propagators of the
 // chunked solves: psiF[i] = prod (-l_k) over k from i's forward chunk start to i,
 // psiB[i] = prod (-l_{k+1}) over k from i's backward chunk top down to i, and per forward
-// chunk c msum[c] = sum m_i psiF[i].  The pivot chain is sequential (one thread, O(N)).
+// chunk c msum[c] = sum m_i psiF[i].
 // -----------------------------------------------------------------------------------------
 __device__ __forceinline__ double tri_diag(const double* h, int N, int i, double cL, double cG) {
     const double hp = h[i == 0 ? N - 1 : i - 1], hi = h[i];
@@ -54,64 +60,158 @@ __global__ void k_tri_coef(const double* __restrict__ h, int N, double cL, doubl
     fac[2 * N + i] = tri_off(h, i, cL, cG);
 }
 
-// the pivot chain d_{i+1} = a_{i+1} - b_i^2 / d_i with the border (one division per step; the
-// coefficients are read eight steps ahead, each before the step that overwrites its slot)
-#define CYC_CH 8
-__global__ void k_cyc_factor(int N, double* fac, int* err) {
+// -----------------------------------------------------------------------------------------
+// The factorisation in parallel over chunks of CYC_CL pivots.  The pivots are ratios of
+// leading minors, P_i = a_i P_{i-1} - b_{i-1}^2 P_{i-2}, d_i = P_i / P_{i-1}: each chunk's
+// product of the 2 x 2 transfer matrices (rescaled by powers of two) is formed in parallel,
+// one thread carries the minors' vector over the chunks, and each chunk then runs the pivot
+// recursion from its carried start (a start off by rounding is pulled back by the recursion,
+// whose derivative b^2/d^2 = l^2 is below one).  The border column z_i = c_0 prod (-l_k) is a
+// prefix product, carried the same way, and the Schur complement is summed per chunk in a
+// fixed order.  Scratch: 9 nch + 3 doubles in the msum slot (k_cyc_prop fills it afterwards).
+// -----------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int64_t fac_nch(int64_t N) { return (N - 1 + CYC_CL - 1) / CYC_CL; }
+
+__device__ __forceinline__ double pow2_scale_of(double m) {      // 2^-e with m = f 2^e, f in [0.5, 1)
+    int e;
+    frexp(m, &e);
+    return ldexp(1.0, -e);
+}
+
+__global__ void k_fac_transfer(int64_t N, double* fac) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nch = fac_nch(N);
+    if (c >= nch) return;
+    const double* b = fac + 2 * N;            // T_{i,i+1} (m slot, on entry)
+    const double* a = fac + 3 * N;            // diagonal (sd slot, on entry)
+    double* T = fac + 6 * N + 4 * c;
+    double t00 = 1.0, t01 = 0.0, t10 = 0.0, t11 = 1.0;
+    const int64_t s = c * CYC_CL, e = min(N - 1, s + CYC_CL);
+    for (int64_t i = s; i < e; ++i) {
+        const double bb = (i >= 1) ? b[i - 1] * b[i - 1] : 0.0;
+        // [[a_i, -bb], [1, 0]] times T
+        const double n00 = a[i] * t00 - bb * t10, n01 = a[i] * t01 - bb * t11;
+        t10 = t00; t11 = t01; t00 = n00; t01 = n01;
+        const double sc = pow2_scale_of(fmax(fmax(fabs(t00), fabs(t01)), fmax(fabs(t10), fabs(t11))));
+        t00 *= sc; t01 *= sc; t10 *= sc; t11 *= sc;
+    }
+    T[0] = t00; T[1] = t01; T[2] = t10; T[3] = t11;
+}
+
+__global__ void k_fac_carry(int64_t N, double* fac) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int64_t nch = fac_nch(N);
+    const double* T = fac + 6 * N;
+    double* v = fac + 6 * N + 4 * nch;
+    double v0 = 1.0, v1 = 0.0;                // (P_{-1}, P_{-2})
+    for (int64_t c = 0; c < nch; ++c) {
+        v[2 * c] = v0; v[2 * c + 1] = v1;
+        const double w0 = T[4 * c] * v0 + T[4 * c + 1] * v1, w1 = T[4 * c + 2] * v0 + T[4 * c + 3] * v1;
+        const double sc = pow2_scale_of(fmax(fabs(w0), fabs(w1)));
+        v0 = w0 * sc; v1 = w1 * sc;
+    }
+}
+
+// pivots of chunk c from its carried minors, and the chunk's prefix products of (-l) (into the
+// psiF slot) with their total
+__global__ void k_fac_pivots(int64_t N, double* fac, int* err) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nch = fac_nch(N);
+    if (c >= nch) return;
     double* l = fac;
     double* dinv = fac + N;
-    double* m = fac + 2 * N;             // holds b on entry
-    const double* a = fac + 3 * N;       // holds a on entry
-    // border column: c_0 = T_{0,N-1}, c_{N-2} = T_{N-2,N-1}
-    const double c0 = m[N - 1], cl = m[N - 2];
-    double d = a[0];
-    double z = c0;                       // z = L'^-1 c, running
-    double schur = 0.0;                  // sum z_i^2 / d_i
-    bool bad = !(d > 0.0);
-    l[0] = 0.0;
-    for (int i0 = 0; i0 <= N - 2; i0 += CYC_CH) {
-        double bv[CYC_CH], av[CYC_CH];
-#pragma unroll
-        for (int j = 0; j < CYC_CH; ++j) {
-            const int i = i0 + j;
-            bv[j] = (i <= N - 2) ? m[i] : 0.0;
-            av[j] = (i + 1 <= N - 1) ? a[i + 1] : 0.0;
+    const double* b = fac + 2 * N;
+    double* a_sd = fac + 3 * N;
+    double* loc = fac + 4 * N;
+    const double* v = fac + 6 * N + 4 * nch;
+    double* tot = fac + 6 * N + 6 * nch;
+    const int64_t s = c * CYC_CL, e = min(N - 1, s + CYC_CL);
+    double d = (c == 0) ? 0.0 : v[2 * c] / v[2 * c + 1];      // d_{s-1}
+    double p = 1.0;
+    bool bad = false;
+    for (int64_t i = s; i < e; ++i) {
+        double dn;
+        if (i == 0) {
+            dn = a_sd[0];
+        } else {
+            const double li = b[i - 1] / d;
+            l[i] = li;
+            dn = fma(-li, b[i - 1], a_sd[i]);
+            p *= -li;
         }
-#pragma unroll
-        for (int j = 0; j < CYC_CH; ++j) {
-            const int i = i0 + j;
-            if (i > N - 2) break;
-            const double di = 1.0 / d;
-            dinv[i] = di;
-            m[i] = z * di;
-            schur = fma(z * z, di, schur);
-            if (i == N - 2) break;
-            const double li = bv[j] * di;
-            l[i + 1] = li;
-            d = fma(-li, bv[j], av[j]);
-            bad |= !(d > 0.0);
-            z = ((i + 1 == N - 2) ? cl : 0.0) - li * z;
-        }
+        bad |= !(dn > 0.0);
+        d = dn;
+        const double di = 1.0 / dn;
+        dinv[i] = di;
+        a_sd[i] = sqrt(di);
+        if (i <= N - 3) loc[i] = p;
     }
-    const double dl = a[N - 1] - schur;
-    bad |= !(dl > 0.0);
-    l[N - 1] = 0.0;
-    m[N - 1] = 0.0;
-    dinv[N - 1] = 1.0 / dl;
+    tot[c] = p;
     if (bad) atomicOr(err, DEVERR_SINGULAR);
 }
 
-__global__ void k_fac_sqrt(int N, double* fac) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) fac[3 * N + i] = sqrt(fac[N + i]);
+// z_in per chunk (one thread), then z, m and the Schur partials per chunk
+__global__ void k_fac_border_carry(int64_t N, double* fac) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int64_t nch = fac_nch(N);
+    const double* b = fac + 2 * N;
+    const double* tot = fac + 6 * N + 6 * nch;
+    double* zin = fac + 6 * N + 7 * nch;
+    double* ends = fac + 6 * N + 9 * nch;     // c_0, c_{N-2}, z_{N-3}
+    ends[0] = b[N - 1];
+    ends[1] = b[N - 2];
+    double z = b[N - 1];
+    for (int64_t c = 0; c < nch; ++c) {
+        zin[c] = z;
+        z *= tot[c];
+    }
 }
 
-// Chunks of the chunked solves: forward chunk c covers i in [1 + c CL, 1 + (c+1) CL) within
-// [1, N-1); backward chunk c covers i from N-3 - c CL down to N-2 - (c+1) CL within [0, N-2).
-#define CYC_CL 64
-#define CYC_FAC 7
-__host__ __device__ __forceinline__ int64_t cyc_nch(int64_t N) { return (N - 2 + CYC_CL - 1) / CYC_CL; }
+__global__ void k_fac_border(int64_t N, double* fac) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nch = fac_nch(N);
+    if (c >= nch) return;
+    const double* dinv = fac + N;
+    double* m = fac + 2 * N;
+    const double* loc = fac + 4 * N;
+    const double* zin = fac + 6 * N + 7 * nch;
+    double* part = fac + 6 * N + 8 * nch;
+    double* ends = fac + 6 * N + 9 * nch;
+    const int64_t s = c * CYC_CL, e = min(N - 2, s + CYC_CL);
+    double sp = 0.0;
+    for (int64_t i = s; i < e; ++i) {
+        const double z = zin[c] * loc[i];
+        m[i] = z * dinv[i];
+        sp = fma(z * z, dinv[i], sp);
+        if (i == N - 3) ends[2] = z;
+    }
+    part[c] = sp;
+}
+
+__global__ void k_fac_final(int64_t N, double* fac, int* err) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int64_t nch = fac_nch(N);
+    double* l = fac;
+    double* dinv = fac + N;
+    double* m = fac + 2 * N;
+    double* a_sd = fac + 3 * N;
+    const double* part = fac + 6 * N + 8 * nch;
+    const double* ends = fac + 6 * N + 9 * nch;
+    const double zl = ends[1] - l[N - 2] * ends[2];        // z_{N-2} = c_{N-2} - l_{N-2} z_{N-3}
+    m[N - 2] = zl * dinv[N - 2];
+    double schur = 0.0;
+    for (int64_t c = 0; c < nch; ++c) schur += part[c];
+    schur = fma(zl * zl, dinv[N - 2], schur);
+    const double dl = a_sd[N - 1] - schur;
+    if (!(dl > 0.0)) atomicOr(err, DEVERR_SINGULAR);
+    l[0] = 0.0;
+    l[N - 1] = 0.0;
+    m[N - 1] = 0.0;
+    dinv[N - 1] = 1.0 / dl;
+    a_sd[N - 1] = sqrt(1.0 / dl);
+}
+
+
 
 __global__ void k_cyc_prop(int64_t N, double* fac) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -460,7 +560,9 @@ __global__ void k_fourier_arc(double* X, int64_t N, int64_t p, const double* __r
 // sqrt(K) 2^-48 of its terms' magnitudes.  Split K: blockIdx.z takes K indices
 // [z kchunk, (z + 1) kchunk) and writes its partial product to C + z zstride.
 // -----------------------------------------------------------------------------------------
-template <int OPA, int OPB>
+// TRI: op(A) is lower triangular (A[k, m] = 0 for k > m, an upper-triangular A taken
+// transposed), so a tile of rows m0.. needs K only below m0 + 64.
+template <int OPA, int OPB, bool TRI>
 __global__ void __launch_bounds__(256) k_dgemm_df(int M, int Nc, int K, const double* __restrict__ A, int64_t lda,
                                                   const double* __restrict__ B, int64_t ldb, double* C, int64_t ldc,
                                                   int kchunk, int64_t zstride) {
@@ -469,7 +571,7 @@ __global__ void __launch_bounds__(256) k_dgemm_df(int M, int Nc, int K, const do
     __shared__ float2 Bs[BK][BN + 1];
     const int t = threadIdx.x, tx = t % 16, ty = t / 16;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    const int kb = blockIdx.z * kchunk, ke = min(min(K, kb + kchunk), TRI ? m0 + BM : K);
     C += blockIdx.z * zstride;
     dfl acc[4][4];
 #pragma unroll
@@ -551,7 +653,8 @@ __global__ void k_sum_splits(const double* __restrict__ P, int nz, int64_t count
 #define CHOL_NB 16
 static size_t chol_smem_bytes(int p) { return sizeof(float2) * CHOL_NB * (size_t)p; }
 
-__global__ void __launch_bounds__(1024) k_chol(double* C, float2* W, int p, double shift, cplx* Rc, int* err) {
+__global__ void __launch_bounds__(1024) k_chol(double* C, float2* W, int p, double shift, cplx* Rc, double* rdiag,
+                                               int* err) {
     extern __shared__ float2 pan[];        // CHOL_NB rows x p columns (row r at pan + r p)
     __shared__ float2 s_ir;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -583,6 +686,7 @@ __global__ void __launch_bounds__(1024) k_chol(double* C, float2* W, int p, doub
                 const dfl ir = dfl_qts(q, q * e);
                 pan[jj * p + j] = make_float2(r.hi, r.lo);
                 s_ir = make_float2(ir.hi, ir.lo);
+                if (rdiag) rdiag[j] = dfl_to(ir);
             }
             __syncthreads();
             const dfl ir = dfl_mk(s_ir);
@@ -630,16 +734,17 @@ __global__ void __launch_bounds__(1024) k_chol(double* C, float2* W, int p, doub
     }
 }
 
-// Rinv = R^-1 (upper, ld p; strict lower part zero) from the mirrored factor of k_chol: one
-// warp per column, x_i = -(sum_{k=i+1..j} R_ik x_k) / R_ii, the sum over the lanes (R_ik at
-// C[k + i p], contiguous in k) reduced in a fixed order
-__global__ void __launch_bounds__(256) k_tri_inv(const double* __restrict__ C, int p, double* Rinv) {
+// Rinv = R^-1 (upper, ld p; strict lower part zero) from the mirrored factor of k_chol and the
+// pivots' reciprocals rdiag: one warp per column, x_i = -(sum_{k=i+1..j} R_ik x_k) / R_ii, the
+// sum over the lanes (R_ik at C[k + i p], contiguous in k) reduced in a fixed order
+__global__ void __launch_bounds__(256) k_tri_inv(const double* __restrict__ C, const double* __restrict__ rdiag, int p,
+                                                 double* Rinv) {
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= p) return;
     double* x = Rinv + (int64_t)j * p;
     for (int i = j + 1 + lane; i < p; i += 32) x[i] = 0.0;
-    if (lane == 0) x[j] = 1.0 / C[j + (int64_t)j * p];
+    if (lane == 0) x[j] = rdiag[j];
     __syncwarp();
     for (int i = j - 1; i >= 0; --i) {
         const double* ri = C + (int64_t)i * p;
@@ -647,7 +752,7 @@ __global__ void __launch_bounds__(256) k_tri_inv(const double* __restrict__ C, i
         for (int k = i + 1 + lane; k <= j; k += 32) acc = fma(ri[k], x[k], acc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) x[i] = -acc / C[i + (int64_t)i * p];
+        if (lane == 0) x[i] = -acc * rdiag[i];
         __syncwarp();
     }
 }
@@ -689,11 +794,16 @@ struct WorkParts {
 bem_status launch_cyc_factor(bem_ctx* h, double cL, double cG, double* fac) {
     const int N = (int)h->N;
     const unsigned g = (unsigned)((N + 255) / 256);
-    const unsigned gc = (unsigned)((cyc_nch(N) + 127) / 128);
+    const unsigned gc = (unsigned)((cyc_nch(N) + 127) / 128), gf = (unsigned)((fac_nch(N) + 127) / 128);
+    const int64_t N64 = N;
     BEM_TIMED(h, "k_cyc_factor", (k_tri_coef<<<g, 256, 0, h->stream>>>(h->seg + 4 * h->N, N, cL, cG, fac),
-                                  k_cyc_factor<<<1, 1, 0, h->stream>>>(N, fac, h->dev_err),
-                                  k_fac_sqrt<<<g, 256, 0, h->stream>>>(N, fac),
-                                  k_cyc_prop<<<gc, 128, 0, h->stream>>>((int64_t)N, fac)));
+                                  k_fac_transfer<<<gf, 128, 0, h->stream>>>(N64, fac),
+                                  k_fac_carry<<<1, 1, 0, h->stream>>>(N64, fac),
+                                  k_fac_pivots<<<gf, 128, 0, h->stream>>>(N64, fac, h->dev_err),
+                                  k_fac_border_carry<<<1, 1, 0, h->stream>>>(N64, fac),
+                                  k_fac_border<<<gf, 128, 0, h->stream>>>(N64, fac),
+                                  k_fac_final<<<1, 1, 0, h->stream>>>(N64, fac, h->dev_err),
+                                  k_cyc_prop<<<gc, 128, 0, h->stream>>>(N64, fac)));
     BEM_LAUNCH(h, "k_cyc_factor");
     return BEM_OK;
 }
@@ -752,12 +862,14 @@ bem_status general_gram_apply(bem_ctx* h, int mode, const cplx* in, cplx* out, c
     return BEM_OK;
 }
 
-template <int OPA, int OPB>
+template <int OPA, int OPB, bool TRI = false>
 static bem_status dgemm_t(bem_ctx* h, int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
                           int64_t ldb, double* C, int64_t ldc, int nz = 1, int kchunk = 0, int64_t zstride = 0) {
     dim3 grid((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64), (unsigned)nz);
-    BEM_TIMED(h, "k_dgemm_df", (k_dgemm_df<OPA, OPB><<<grid, 256, 0, h->stream>>>((int)M, (int)Nc, (int)K, A, lda, B, ldb,
-                                                                                    C, ldc, nz == 1 ? (int)K : kchunk, zstride)));
+    BEM_TIMED(h, TRI ? "k_dgemm_df_tri" : "k_dgemm_df",
+              (k_dgemm_df<OPA, OPB, TRI><<<grid, 256, 0, h->stream>>>((int)M, (int)Nc, (int)K, A, lda, B,
+                                                                                         ldb, C, ldc,
+                                                                                         nz == 1 ? (int)K : kchunk, zstride)));
     BEM_LAUNCH(h, "k_dgemm_df");
     return BEM_OK;
 }
@@ -795,19 +907,19 @@ static bem_status tri_mul(bem_ctx* h, const double* x, double* y, int64_t ncols,
     return BEM_OK;
 }
 
-// W: p^2 float2 scratch of the factorisation
-static bem_status chol_launch(bem_ctx* h, double* C, float2* W, int64_t p, double shift, cplx* Rc) {
+// W: p^2 float2 scratch of the factorisation; rdiag (p doubles, or null) receives 1/R_jj
+static bem_status chol_launch(bem_ctx* h, double* C, float2* W, int64_t p, double shift, cplx* Rc, double* rdiag) {
     const size_t sm = chol_smem_bytes((int)p);
     BEM_CUDA(h, cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    BEM_TIMED(h, "k_chol", (k_chol<<<1, 1024, sm, h->stream>>>(C, W, (int)p, shift, Rc, h->dev_err)));
+    BEM_TIMED(h, "k_chol", (k_chol<<<1, 1024, sm, h->stream>>>(C, W, (int)p, shift, Rc, rdiag, h->dev_err)));
     BEM_LAUNCH(h, "k_chol");
     return BEM_OK;
 }
 
-static bem_status chol_inv(bem_ctx* h, double* C, float2* W, int64_t p, double* Rinv) {
-    bem_status st = chol_launch(h, C, W, p, 0.0, nullptr);
+static bem_status chol_inv(bem_ctx* h, double* C, float2* W, double* rdiag, int64_t p, double* Rinv) {
+    bem_status st = chol_launch(h, C, W, p, 0.0, nullptr, rdiag);
     if (st != BEM_OK) return st;
-    BEM_TIMED(h, "k_tri_inv", (k_tri_inv<<<(unsigned)((p + 7) / 8), 256, 0, h->stream>>>(C, (int)p, Rinv)));
+    BEM_TIMED(h, "k_tri_inv", (k_tri_inv<<<(unsigned)((p + 7) / 8), 256, 0, h->stream>>>(C, rdiag, (int)p, Rinv)));
     BEM_LAUNCH(h, "k_tri_inv");
     return BEM_OK;
 }
@@ -858,7 +970,7 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     h->basis_iters = iters;
     double *X = nullptr, *Y = nullptr, *Z = nullptr, *C = nullptr, *Rinv = nullptr, *Cf = nullptr, *fac = nullptr,
            *s = nullptr, *sig = nullptr, *part = nullptr, *abG = nullptr, *abL = nullptr, *abGs = nullptr,
-           *cscr = nullptr;
+           *cscr = nullptr, *rdg = nullptr;
     cplx *Rc = nullptr, *E = nullptr;
     float2* Wdf = nullptr;
     int* perm = nullptr;
@@ -870,6 +982,7 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     cv.add((void**)&C, sizeof(double) * p * p);
     cv.add((void**)&Rinv, sizeof(double) * p * p);
     cv.add((void**)&Wdf, sizeof(float2) * p * p);
+    cv.add((void**)&rdg, sizeof(double) * p);
     cv.add((void**)&part, sizeof(double) * p * p * gram_splits(p, N));
     cv.add((void**)&Cf, sizeof(double) * p * nc);
     cv.add((void**)&fac, cyc_factor_bytes(N));
@@ -906,8 +1019,8 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
         bem_status q;
         if ((q = tri_mul(h, in, Z, p, abG, true)) != BEM_OK) return q;
         if ((q = gram_product(h, p, N, in, Z, C, part)) != BEM_OK) return q;
-        if ((q = chol_inv(h, C, Wdf, p, Rinv)) != BEM_OK) return q;
-        return dgemm_t<OP_T, OP_N>(h, p, N, p, Rinv, p, in, p, out, p);
+        if ((q = chol_inv(h, C, Wdf, rdg, p, Rinv)) != BEM_OK) return q;
+        return dgemm_t<OP_T, OP_N, true>(h, p, N, p, Rinv, p, in, p, out, p);     // R^-1 upper triangular
     };
     if ((st = cholqr(X, Y)) != BEM_OK) return st;
     std::swap(X, Y);
@@ -928,7 +1041,7 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     // vectors of its Cholesky factor (Jacobi SVD, sorted by decreasing singular value)
     if ((st = tri_mul(h, X, Z, p, abL, true)) != BEM_OK) return st;
     if ((st = gram_product(h, p, N, X, Z, C, part)) != BEM_OK) return st;
-    if ((st = chol_launch(h, C, Wdf, p, sigma, Rc)) != BEM_OK) return st;
+    if ((st = chol_launch(h, C, Wdf, p, sigma, Rc, nullptr)) != BEM_OK) return st;
     BEM_TIMED(h, "k_iota", (k_iota<<<(unsigned)((p + 255) / 256), 256, 0, h->stream>>>(perm, (int)p)));
     BEM_LAUNCH(h, "k_iota");
     if ((st = launch_jacobi_svd(h, Rc, (int)p, perm, sig, E, jac)) != BEM_OK) return st;

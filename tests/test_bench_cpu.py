@@ -56,3 +56,26 @@ def test_filter_pair_reported_together():
     rep = {"tc_rhs_SY": (1, 18.0), "k_assemble": (1, 16.0), "tc_filter_YN": (1, 6.0), "tc_filter_QtS": (1, 3.0)}
     _, rows = bench.roofline(rep, _args(), 201, 201, 6.7e8)
     assert [r["kernel"] for r in rows] == ["tc_rhs_SY", "k_assemble", "tc_filter_YN", "tc_filter_QtS"]
+
+
+def test_basis_products_of_a_general_mesh():
+    """Non-equal-chord mesh: the double-float basis products count their algorithmic flops,
+    2 N p^2 per Gram product, 2 N p n for the one Q = X Cf launch per step, N p (p + 1) per
+    triangular re-orthonormalisation X R^-1, against the double-float peak derived from the
+    FP32 pipe; the one-CTA Cholesky counts p^3 / 3 against one SM."""
+    N, p, n, steps = 16384, 411, 201, 3
+    basis = {"block": p, "iters": 34, "ncols": n}
+    rep = {"k_dgemm_df": (16 * steps, steps * 30.0), "k_dgemm_df_tri": (15 * steps, steps * 20.0),
+           "k_chol": (16 * steps, steps * 35.0)}
+    _, rows = bench.roofline(rep, _args(N=N), n, 201, 0, basis=basis, nsteps=steps)
+    by = {r["kernel"]: r for r in rows}
+    g = by["k_dgemm_df"]
+    fl = (15 * 2.0 * N * p * p + 2.0 * N * p * n) / 16
+    assert g["flops_per_launch"] == pytest.approx(fl)
+    assert g["achieved"] == pytest.approx(fl / (30.0e-3 / 16) / 1e12)
+    assert g["peak"] == pytest.approx(152 * 128 * 2.07e9 / 1e12 * 2 / bench.DF_OPS_PER_FMA)
+    t = by["k_dgemm_df_tri"]
+    assert t["flops_per_launch"] == pytest.approx(float(N) * p * (p + 1))
+    c = by["k_chol"]
+    assert c["flops_per_launch"] == pytest.approx(p ** 3 / 3.0)
+    assert c["peak"] == pytest.approx(128 * 2.07e9 / 1e12 * 2 / bench.DF_OPS_PER_FMA)
