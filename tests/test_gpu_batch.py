@@ -166,3 +166,34 @@ def test_tile_tuner_picks_a_shape_per_bucket_and_stage(B, problems):
         assert out["rank"] == r
         assert float((out["x"] - x).abs().max() / x.abs().max()) <= 1e-10
     bs.close()
+
+
+def test_persistent_batch_assembly_with_general_meshes(B):
+    """Equal-chord and non-equal-chord problems in one persistent launch: every handle gets
+    the bits of its own bem_assemble (the general meshes' wider near-pair series radius and
+    their Gram factors included), and its filter and solve run on from there."""
+    bem, _ = B
+    star = I.cos_star(1.0, 0.3, 5)
+    meshes = [I.equal_chord_mesh(star, 400)[0], I.parameter_mesh(star, 333, grade=0.3)[0],
+              I.parameter_mesh(I.perturbed_circle(), 520)[0]]
+    ks = [2.0, 1.5, 0.4]
+    ss = [bem.Solver(device=0) for _ in meshes]
+    bem.assemble_batch(ss, [torch.from_numpy(v) for v in meshes], ks)
+    for v, k, s in zip(meshes, ks, ss):
+        one = bem.Solver(device=0)
+        one.assemble(torch.from_numpy(v).cuda(), k, ops="SW")
+        assert s.info()["equal_chord"] == one.info()["equal_chord"]
+        for op in "SW":
+            assert torch.equal(s.matrix(op), one.matrix(op)), (op, v.shape[0])
+        ang = torch.from_numpy(I.planewave_angles(3)).cuda()
+        xs = []
+        for h in (s, one):
+            h.filter_apply(21)
+            h.compress(1e-10)
+            h.factor()
+            xs.append(h.solve(h.rhs_planewave(ang)))
+        assert torch.equal(xs[0], xs[1])
+        one.close()
+    assert [s.info()["equal_chord"] for s in ss] == [1, 0, 0]
+    for s in ss:
+        s.close()
