@@ -88,8 +88,7 @@ bem_status launch_row_dot(bem_ctx* h, const double* T, int64_t P, int64_t n, con
 // bordered LDL^T of cL L + cG G (4N doubles at fac) on h's stream
 bem_status launch_cyc_factor(bem_ctx* h, double cL, double cG, double* fac);
 // apply_gram_inverse for a general mesh: mode 0 G^-1, mode 1 D^-1/2 L^-1 (rows times F^-1)
-// (chunked over N when tmp holds tmp_elems >= 5 ceil((N-2)/64) ncols + ncols elements, else
-// one lane per column)
+// (chunked over N; tmp holds tmp_elems >= 5 ceil((N-2)/64) ncols + ncols elements)
 bem_status general_gram_apply(bem_ctx* h, int mode, const cplx* in, cplx* out, cplx* tmp, size_t tmp_elems, int64_t N,
                               int64_t ncols, int64_t si, int64_t sc, bool conj_out);
 size_t cyc_factor_bytes(int64_t N);

@@ -238,10 +238,9 @@ __global__ void k_cyc_prop(int64_t N, double* fac) {
 }
 
 // -----------------------------------------------------------------------------------------
-// Solves along index i of a strided array (element i of column c at c*sc + i*si), one thread
-// per column.  MODE 0: y = scale T^-1 x (forward L, diagonal, backward L^T).  MODE 1:
-// y = scale D^-1/2 L^-1 x, i.e. the rows b F^-1 with F = D^1/2 L^T (F^T F = T).  In place
-// allowed (each element is read before it is written).
+// Solves along index i of a strided array (element i of column c at c*sc + i*si), real or
+// complex: MODE 0, y = T^-1 x (forward L, diagonal, backward L^T); MODE 1, y = D^-1/2 L^-1 x,
+// i.e. the rows b F^-1 with F = D^1/2 L^T (F^T F = T).  Helpers for both element types.
 // -----------------------------------------------------------------------------------------
 __device__ __forceinline__ double axmy(double x, double a, double y) { return fma(-a, y, x); }
 __device__ __forceinline__ cplx axmy(cplx x, double a, cplx y) { return cmk(fma(-a, y.x, x.x), fma(-a, y.y, x.y)); }
@@ -258,108 +257,6 @@ __device__ __forceinline__ cplx tsub(cplx a, cplx b) { return cmk(a.x - b.x, a.y
 template <typename T> __device__ __forceinline__ T zero_of();
 template <> __device__ __forceinline__ double zero_of<double>() { return 0.0; }
 template <> __device__ __forceinline__ cplx zero_of<cplx>() { return cmk(0, 0); }
-
-// One warp per CTA, one lane per column.  The recursion is a chain of dependent steps, so
-// what bounds it is memory latency: chunks of CH elements are loaded one chunk ahead of the
-// one being computed (a chunk's loads only touch elements that no earlier step has written,
-// so in place is allowed), and the coefficients, common to all columns, are loaded once per
-// chunk by the first CH lanes and broadcast by shuffles.  Lanes past ncols follow column 0's
-// reads (in bounds) and store nothing.
-__device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-
-template <typename T, int MODE, int CH>
-__global__ void __launch_bounds__(32) k_cyc_solve(const T* in, T* out, int64_t N, int64_t ncols, int64_t si,
-                                                  int64_t sc, const double* __restrict__ fac, double scale,
-                                                  int conj_out) {
-    const int lane = threadIdx.x;
-    const int64_t col = (int64_t)blockIdx.x * 32 + lane;
-    const bool valid = col < ncols;
-    const double* l = fac;
-    const double* dinv = fac + N;
-    const double* m = fac + 2 * N;
-    const double* sd = fac + 3 * N;
-    const T* x = in + (valid ? col : 0) * sc;
-    T* y = out + (valid ? col : 0) * sc;
-    // forward: u_0 = x_0, u_i = x_i - l_i u_{i-1} (1 <= i <= N-2), u_{N-1} = x_{N-1} - sum m_i u_i
-    T prev = x[0];
-    T s = zero_of<T>();
-    s = fma_acc(s, __ldg(m), prev);
-    if (valid) y[0] = (MODE == 0) ? sc_mul(prev, __ldg(dinv)) : maybe_conj(sc_mul(prev, scale * __ldg(sd)), conj_out);
-    const int64_t ie = N - 1;                      // forward steps cover [1, ie)
-    T xc[CH], xn[CH];
-    double lc = 0.0, mc = 0.0, dc = 0.0, ln = 0.0, mn = 0.0, dn = 0.0;
-#define CYC_LOAD_F(I0, XV, LV, MV, DV)                                                              \
-    {                                                                                               \
-        _Pragma("unroll") for (int j = 0; j < CH; ++j) {                                            \
-            const int64_t i = (I0) + j;                                                             \
-            XV[j] = (i < ie) ? x[i * si] : zero_of<T>();                                            \
-        }                                                                                           \
-        const int64_t i = (I0) + lane;                                                              \
-        const bool ok = lane < CH && i < ie;                                                        \
-        LV = ok ? __ldg(l + i) : 0.0;                                                               \
-        MV = ok ? __ldg(m + i) : 0.0;                                                               \
-        DV = ok ? ((MODE == 0) ? __ldg(dinv + i) : scale * __ldg(sd + i)) : 0.0;                    \
-    }
-    CYC_LOAD_F(1, xc, lc, mc, dc);
-    for (int64_t i0 = 1; i0 < ie; i0 += CH) {
-        if (i0 + CH < ie) CYC_LOAD_F(i0 + CH, xn, ln, mn, dn);
-#pragma unroll
-        for (int j = 0; j < CH; ++j) {
-            const int64_t i = i0 + j;
-            if (i < ie) {
-                const double lj = shfl_d(lc, j), mj = shfl_d(mc, j), dj = shfl_d(dc, j);
-                const T u = axmy(xc[j], lj, prev);
-                s = fma_acc(s, mj, u);
-                if (valid) y[i * si] = (MODE == 0) ? sc_mul(u, dj) : maybe_conj(sc_mul(u, dj), conj_out);
-                prev = u;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < CH; ++j) xc[j] = xn[j];
-        lc = ln; mc = mn; dc = dn;
-    }
-#undef CYC_LOAD_F
-    const T ul = tsub(x[(N - 1) * si], s);
-    if (MODE == 1) {
-        if (valid) y[(N - 1) * si] = maybe_conj(sc_mul(ul, scale * __ldg(sd + N - 1)), conj_out);
-        return;
-    }
-    // backward: y_{N-1} = w_{N-1}; y_{N-2} = w_{N-2} - m_{N-2} y_{N-1};
-    // y_i = w_i - l_{i+1} y_{i+1} - m_i y_{N-1}   (i = N-3 .. 0, in descending chunks)
-    const T yl = sc_mul(ul, __ldg(dinv + N - 1));
-    if (valid) y[(N - 1) * si] = maybe_conj(sc_mul(yl, scale), conj_out);
-    T next = axmy(y[(N - 2) * si], __ldg(m + N - 2), yl);
-    if (valid) y[(N - 2) * si] = maybe_conj(sc_mul(next, scale), conj_out);
-#define CYC_LOAD_B(I0, WV, LV, MV)                                                                  \
-    {                                                                                               \
-        _Pragma("unroll") for (int j = 0; j < CH; ++j) {                                            \
-            const int64_t i = (I0) - j;                                                             \
-            WV[j] = (i >= 0) ? y[i * si] : zero_of<T>();                                            \
-        }                                                                                           \
-        const int64_t i = (I0) - lane;                                                              \
-        const bool ok = lane < CH && i >= 0;                                                        \
-        LV = ok ? __ldg(l + i + 1) : 0.0;                                                           \
-        MV = ok ? __ldg(m + i) : 0.0;                                                               \
-    }
-    CYC_LOAD_B(N - 3, xc, lc, mc);
-    for (int64_t i0 = N - 3; i0 >= 0; i0 -= CH) {
-        if (i0 - CH >= 0) CYC_LOAD_B(i0 - CH, xn, ln, mn);
-#pragma unroll
-        for (int j = 0; j < CH; ++j) {
-            const int64_t i = i0 - j;
-            if (i >= 0) {
-                const double lj = shfl_d(lc, j), mj = shfl_d(mc, j);
-                const T v = axmy(axmy(xc[j], lj, next), mj, yl);
-                if (valid) y[i * si] = maybe_conj(sc_mul(v, scale), conj_out);
-                next = v;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < CH; ++j) xc[j] = xn[j];
-        lc = ln; mc = mn;
-    }
-#undef CYC_LOAD_B
-}
 
 // -----------------------------------------------------------------------------------------
 // Chunked solves (MODE 0, T^-1 x; MODE 1, D^-1/2 L^-1 x): the recurrences split into chunks of
@@ -848,18 +745,9 @@ static bem_status cyc_solve_chunked(bem_ctx* h, int mode, const T* in, T* out, i
 bem_status general_gram_apply(bem_ctx* h, int mode, const cplx* in, cplx* out, cplx* tmp, size_t tmp_elems, int64_t N,
                               int64_t ncols, int64_t si, int64_t sc, bool conj_out) {
     if (!h->gfac) return bem_fail(h, BEM_E_INVALID, "Gram solve: no factor of the general Gram matrix");
-    if (tmp && tmp_elems >= cyc_scratch_elems<cplx>(N, ncols))
-        return cyc_solve_chunked<cplx>(h, mode, in, out, N, ncols, si, sc, h->gfac, tmp, conj_out);
-    const unsigned blocks = (unsigned)((ncols + 31) / 32);      // one warp per CTA: more SMs' FP64 pipes
-    if (mode == 0) {
-        BEM_TIMED(h, "k_cyc_solve", (k_cyc_solve<cplx, 0, 8><<<blocks, 32, 0, h->stream>>>(in, out, N, ncols, si, sc, h->gfac,
-                                                                                      1.0, conj_out ? 1 : 0)));
-    } else {
-        BEM_TIMED(h, "k_cyc_solve", (k_cyc_solve<cplx, 1, 8><<<blocks, 32, 0, h->stream>>>(in, out, N, ncols, si, sc, h->gfac,
-                                                                                      1.0, conj_out ? 1 : 0)));
-    }
-    BEM_LAUNCH(h, "k_cyc_solve");
-    return BEM_OK;
+    if (!tmp || tmp_elems < cyc_scratch_elems<cplx>(N, ncols))
+        return bem_fail(h, BEM_E_INVALID, "Gram solve: the general mesh's chunked solve needs scratch");
+    return cyc_solve_chunked<cplx>(h, mode, in, out, N, ncols, si, sc, h->gfac, tmp, conj_out);
 }
 
 template <int OPA, int OPB, bool TRI = false>
