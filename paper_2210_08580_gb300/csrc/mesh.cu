@@ -920,9 +920,11 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
         if ((st = tri_mul(h, X, Z, p, abGs, true)) != BEM_OK) return st;
         if ((st = cyc_solve_chunked<double>(h, 0, Z, Y, N, p, p, 1, fac, cscr, false)) != BEM_OK) return st;
         // The span does not depend on the basis, so the basis is re-orthonormalised only every
-        // third step (its condition grows by at most (lambda_p + sigma)/sigma, about 17, per
-        // step) and at each of the last three, which set the final accuracy.
-        if (it % 3 == 2 || it >= iters - 3) {
+        // fourth step and at each of the last three, which set the final accuracy.  Its
+        // condition grows by at most (lambda_{p+1} + sigma)/sigma per step (about 11 for
+        // p = 1.5 n, 14 at n = 21), so the Gram matrix of the fourth step stays below 1e10,
+        // far inside what the double-float Cholesky factors.
+        if (it % 4 == 3 || it >= iters - 3) {
             if ((st = cholqr(Y, X)) != BEM_OK) return st;
         } else {
             std::swap(X, Y);
