@@ -32,6 +32,7 @@
 // [1, N-1); backward chunk c covers i from N-3 - c CL down to N-2 - (c+1) CL within [0, N-2).
 #define CYC_CL 64
 #define CYC_FAC 7
+#define CYC_PF 16                     // elements (chunks) a solve pass loads before computing
 __host__ __device__ __forceinline__ int64_t cyc_nch(int64_t N) { return (N - 2 + CYC_CL - 1) / CYC_CL; }
 
 // -----------------------------------------------------------------------------------------
@@ -278,10 +279,25 @@ __global__ void k_cyc_fwd_local(const T* in, T* out, int64_t N, int64_t ncols, i
     T* y = out + col * sc;
     T u = zero_of<T>(), acc = zero_of<T>();
     const int64_t s = 1 + c * CYC_CL, e = min(N - 1, s + CYC_CL);
-    for (int64_t i = s; i < e; ++i) {
-        u = axmy(x[i * si], __ldg(l + i), u);
-        acc = fma_acc(acc, __ldg(m + i), u);
-        y[i * si] = u;
+    // groups of CYC_PF elements loaded before any is computed (the chain's loads would
+    // otherwise wait one by one behind the stores, x and y possibly being the same array)
+    for (int64_t i0 = s; i0 < e; i0 += CYC_PF) {
+        T xv[CYC_PF];
+        double lv[CYC_PF], mv[CYC_PF];
+#pragma unroll
+        for (int j = 0; j < CYC_PF; ++j) {
+            const int64_t i = i0 + j;
+            if (i < e) { xv[j] = x[i * si]; lv[j] = __ldg(l + i); mv[j] = __ldg(m + i); }
+        }
+#pragma unroll
+        for (int j = 0; j < CYC_PF; ++j) {
+            const int64_t i = i0 + j;
+            if (i < e) {
+                u = axmy(xv[j], lv[j], u);
+                acc = fma_acc(acc, mv[j], u);
+                y[i * si] = u;
+            }
+        }
     }
     part[2 * (c * ncols + col)] = u;
     part[2 * (c * ncols + col) + 1] = acc;
@@ -300,11 +316,28 @@ __global__ void k_cyc_fwd_carry(const T* in, int64_t N, int64_t ncols, int64_t s
     T cur = in[col * sc];                              // u_0 = x_0
     T s = zero_of<T>();
     s = fma_acc(s, m[0], cur);
-    for (int64_t c = 0; c < nch; ++c) {
-        carry[c * ncols + col] = cur;
-        const int64_t e = min(N - 1, 1 + (c + 1) * CYC_CL);
-        s = fma_acc(tadd(s, part[2 * (c * ncols + col) + 1]), msum[c], cur);
-        cur = fma_acc(part[2 * (c * ncols + col)], psiF[e - 1], cur);
+    for (int64_t c0 = 0; c0 < nch; c0 += CYC_PF) {      // each group's loads issued together
+        T pu[CYC_PF], ps[CYC_PF];
+        double mv[CYC_PF], pe[CYC_PF];
+#pragma unroll
+        for (int j = 0; j < CYC_PF; ++j) {
+            const int64_t c = c0 + j;
+            if (c < nch) {
+                pu[j] = part[2 * (c * ncols + col)];
+                ps[j] = part[2 * (c * ncols + col) + 1];
+                mv[j] = msum[c];
+                pe[j] = psiF[min(N - 1, 1 + (c + 1) * CYC_CL) - 1];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CYC_PF; ++j) {
+            const int64_t c = c0 + j;
+            if (c < nch) {
+                carry[c * ncols + col] = cur;
+                s = fma_acc(tadd(s, ps[j]), mv[j], cur);
+                cur = fma_acc(pu[j], pe[j], cur);
+            }
+        }
     }
     tail[col] = s;
 }
@@ -338,9 +371,22 @@ __global__ void k_cyc_bwd_local(T* y, int64_t N, int64_t ncols, int64_t si, int6
     const T yl = yc[(N - 1) * si];
     T v = zero_of<T>();
     const int64_t t = N - 3 - c * CYC_CL, b = max((int64_t)0, t - CYC_CL + 1);
-    for (int64_t i = t; i >= b; --i) {
-        v = axmy(axmy(yc[i * si], __ldg(m + i), yl), __ldg(l + i + 1), v);
-        yc[i * si] = v;
+    for (int64_t i0 = t; i0 >= b; i0 -= CYC_PF) {
+        T wv[CYC_PF];
+        double lv[CYC_PF], mv[CYC_PF];
+#pragma unroll
+        for (int j = 0; j < CYC_PF; ++j) {
+            const int64_t i = i0 - j;
+            if (i >= b) { wv[j] = yc[i * si]; lv[j] = __ldg(l + i + 1); mv[j] = __ldg(m + i); }
+        }
+#pragma unroll
+        for (int j = 0; j < CYC_PF; ++j) {
+            const int64_t i = i0 - j;
+            if (i >= b) {
+                v = axmy(axmy(wv[j], mv[j], yl), lv[j], v);
+                yc[i * si] = v;
+            }
+        }
     }
     part[c * ncols + col] = v;
 }
@@ -355,10 +401,25 @@ __global__ void k_cyc_bwd_carry(const T* y, int64_t N, int64_t ncols, int64_t si
     const T* yc = y + col * sc;
     T cur = axmy(yc[(N - 2) * si], m[N - 2], yc[(N - 1) * si]);     // v_{N-2}
     const int64_t nch = cyc_nch(N);
-    for (int64_t c = 0; c < nch; ++c) {
-        carry[c * ncols + col] = cur;
-        const int64_t t = N - 3 - c * CYC_CL, b = max((int64_t)0, t - CYC_CL + 1);
-        cur = fma_acc(part[c * ncols + col], psiB[b], cur);
+    for (int64_t c0 = 0; c0 < nch; c0 += CYC_PF) {
+        T pv[CYC_PF];
+        double pb[CYC_PF];
+#pragma unroll
+        for (int j = 0; j < CYC_PF; ++j) {
+            const int64_t c = c0 + j;
+            if (c < nch) {
+                pv[j] = part[c * ncols + col];
+                pb[j] = psiB[max((int64_t)0, N - 3 - c * CYC_CL - CYC_CL + 1)];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CYC_PF; ++j) {
+            const int64_t c = c0 + j;
+            if (c < nch) {
+                carry[c * ncols + col] = cur;
+                cur = fma_acc(pv[j], pb[j], cur);
+            }
+        }
     }
 }
 
