@@ -1,6 +1,6 @@
-// Non-equal-chord meshes (Sec. III-A: "L should be replaced by L~ = G^-1/2 L G^-1/2 on
-// non-homogeneously discretised structures").  On such a polygon the P1 Gram matrix G and
-// Laplacian L are general cyclic tridiagonal matrices,
+// Non-equal-chord meshes.  Sec. III-A builds the filter of a non-homogeneous discretisation
+// from the orthonormalised Laplacian L~ = G^-1/2 L G^-1/2 instead of L.  On such a polygon the
+// P1 Gram matrix G and Laplacian L are general cyclic tridiagonal matrices,
 //     G_ii = (h_{i-1} + h_i)/3,  G_{i,i+1} = h_i/6;   L_ii = 1/h_{i-1} + 1/h_i,  L_{i,i+1} = -1/h_i
 // (segment i runs from vertex i to i+1), so neither is diagonalised by Fourier modes.  This
 // file supplies what the equal-chord path gets from circulant algebra:
@@ -17,9 +17,10 @@
 //        B = Phi^T G C_x = (Phi^T S) G^-1 N - (G Phi)^T / 4 - alpha Phi^T D.
 //    Only span(Phi) matters (any orthogonal mixing of its columns cancels in Phi B and in the
 //    compression), so Phi is found by shift-and-invert subspace iteration on
-//    (L + sigma G)^-1 G from the arclength Fourier modes, G-orthonormalised each step by a
-//    Cholesky QR, and one Rayleigh-Ritz step at the end whose small eigenproblem runs
-//    through the library's one-sided Jacobi SVD.
+//    sigma (L + sigma G)^-1 G from the arclength Fourier modes, G-orthonormalised every
+//    fourth step by a Cholesky QR, and one Rayleigh-Ritz step at the end whose small
+//    eigenproblem runs through the library's one-sided Jacobi SVD.  Its dense products and
+//    the small Cholesky run in double-float on the FP32 pipe.
 #include <math.h>
 
 #include <algorithm>
@@ -964,8 +965,8 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     BEM_LAUNCH(h, "k_arclength");
     BEM_TIMED(h, "k_fourier_arc", (k_fourier_arc<<<(unsigned)((N * p + 255) / 256), 256, 0, h->stream>>>(X, N, p, s)));
     BEM_LAUNCH(h, "k_fourier_arc");
-    // The basis blocks X, Y, Z are row-major N x p, so the solves' threads (one per column)
-    // read adjacent addresses.  G-orthonormalise the columns of `in` into `out`:
+    // The basis blocks X, Y, Z are row-major N x p, so the chunked solves' threads (adjacent
+    // columns of one chunk) read adjacent addresses.  G-orthonormalise the columns of `in` into `out`:
     // R^T R = in^T G in, out = in R^-1 (as out^T = R^-T in^T)
     auto cholqr = [&](const double* in, double* out) -> bem_status {
         bem_status q;
