@@ -22,10 +22,11 @@ and a summary with the oracle's wall time per phase and the host's core count in
 
 Configurations: star r = 1 + 0.3 cos 5t, N = 4096, k in {1e-3, 1e-2, 1e-1, 1, 5}, n = 201,
 tol 1e-10 (256 plane waves); random 8-harmonic star of seed 0, N = 16384, k = 2, n = 201,
-tol 1e-10 (1024 plane waves); a subsample of the uneven batch (run_c4); and, for the
-differentiation layer, the C5 misfit (run_c5).
+tol 1e-10 (1024 plane waves); a subsample of the uneven batch (run_c4); for the
+differentiation layer, the C5 misfit (run_c5); and a non-equal-chord mesh (run_general: the
+Table I curve meshed uniformly in the polar angle at the paper's N = 2008, by the literal route).
 
-    python tests/golden/make_goldens.py [--workers W] [--only c2|c3|c4|c5]
+    python tests/golden/make_goldens.py [--workers W] [--only c2|c3|c4|c5|general]
 """
 from __future__ import annotations
 
@@ -163,10 +164,38 @@ def run_c4(workers):
                 kappa=[float(out[f"p{i}_kappa"]) for i in range(C4_COUNT)])
 
 
+def run_general(workers):
+    """Non-equal-chord mesh: the perturbed circle r = 2 + 0.2 sin 8t (Table I) at N = 2008 vertices
+    uniform in the polar angle, k = 0.4, n = 201, tol 1e-3, right-hand sides the line source at
+    (3, 0) and four plane waves.  The literal route (dense G^-1/2, eigendecomposition of L~, SVD
+    of P C2; Sec. III-A, IV): solutions at 256 seeded rows, the uncompressed filtered solution
+    there, v = G^-1 S G^-1 f there, sigma (first n), rank."""
+    from oracle import bem_oracle as O
+    from paper_2210_08580_gb300 import inputs as I
+    t0 = time.perf_counter()
+    N, k, n, tol = 2008, 0.4, 201, 1e-3
+    verts, _ = I.parameter_mesh(I.perturbed_circle(), N)
+    src = np.array([[3.0, 0.0]])
+    angles = I.planewave_angles(4)
+    mats = O.assemble(verts, k, "SW", workers=workers)
+    t1 = time.perf_counter()
+    f = np.concatenate([O.rhs_pointsource(verts, k, src), O.rhs_planewave(verts, k, angles)], axis=1)
+    res = O.filtered_solve_literal(mats, verts, f, n, tol)
+    G = O.gram(verts)
+    vx = np.linalg.solve(G, mats["S"] @ np.linalg.solve(G, f))
+    rows = np.sort(np.random.default_rng(2008).choice(N, 256, replace=False))
+    name = "general_table1_n2008"
+    np.savez(os.path.join(HERE, name + ".npz"), rows=rows, angles=angles, source=src, x=res["x"][rows],
+             x_full=res["x_full"][rows], vx=vx[rows], sigma=res["sigma"][:n], rank=np.int64(res["rank"]),
+             N=np.int64(N), k=np.float64(k), n=np.int64(n), tol=np.float64(tol))
+    return dict(name=name, N=N, k=k, n=n, tol=tol, rank=int(res["rank"]), route="filtered_solve_literal",
+                seconds={"assemble": t1 - t0, "rest": time.perf_counter() - t1})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workers", type=int, default=os.cpu_count() or 1)
-    ap.add_argument("--only", default="", choices=["", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--only", default="", choices=["", "c2", "c3", "c4", "c5", "general"])
     args = ap.parse_args()
     summ_path = os.path.join(HERE, "oracle_runs.json")
     summary = {}
@@ -175,7 +204,7 @@ def main():
             summary = json.load(fh)
     runs = summary.get("runs", {})
     todo = [c for c in configs() if not args.only or c["name"].startswith(args.only)]
-    for extra in ("c4", "c5"):
+    for extra in ("c4", "c5", "general"):
         if not args.only or args.only == extra:
             todo.append(extra)
     for cfg in todo:
@@ -183,6 +212,8 @@ def main():
             r = run_c4(args.workers)
         elif cfg == "c5":
             r = run_c5(args.workers)
+        elif cfg == "general":
+            r = run_general(args.workers)
         else:
             r = run(cfg, args.workers)
         runs[r["name"]] = r

@@ -8,6 +8,8 @@ Table I geometry, chords following the curve's speed), N = 300 (ten assembly til
 ragged tail).  G and L are general cyclic tridiagonal there, G^-1 runs through the bordered
 LDL^T factor and the filter basis through the shifted subspace iteration.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -21,6 +23,7 @@ ENTRY_TOL = 1e-13
 SOLVE_TOL = 1e-10
 MIXED_TOL = 1e-8
 N_MODES = 21
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module")
@@ -178,3 +181,32 @@ def test_table1_geometry_uniform_in_angle(B):
     assert _rel(x, ref["x"]) <= SOLVE_TOL, _rel(x, ref["x"])
     s.close()
 
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_table1_n2008_against_stored_oracle(B, prec):
+    """The Table I curve meshed uniformly in the polar angle at the paper's N = 2008, n = 201,
+    tol 1e-3, k = 0.4: v, sigma, rank and the solutions for the line source at (3, 0) and four
+    plane waves at 256 rows against the oracle's literal route, stored by
+    tests/golden/make_goldens.py --only general."""
+    g = np.load(os.path.join(GOLDEN, "general_table1_n2008.npz"))
+    N, k, n, tol = int(g["N"]), float(g["k"]), int(g["n"]), float(g["tol"])
+    v, _ = I.parameter_mesh(I.perturbed_circle(), N)
+    s = B.Solver(device=0, prec=prec)
+    s.assemble(_cuda(v), k, ops="SW")
+    assert s.info()["equal_chord"] == 0
+    vv = torch.cat([s.rhs_pointsource(_cuda(g["source"])), s.rhs_planewave(_cuda(g["angles"]))], dim=0)
+    rows = g["rows"]
+    v_tol = 1e-12 if prec == "fp64" else 5e-10
+    assert _rel(_np(vv).T[rows], g["vx"]) <= v_tol, _rel(_np(vv).T[rows], g["vx"])
+    s.filter_apply(n)
+    r = s.compress(tol)
+    sig = _np(s.matrix("sigma"))
+    sig_tol = 1e-11 if prec == "fp64" else 1e-9
+    assert np.max(np.abs(sig - g["sigma"])) <= sig_tol * g["sigma"][0]
+    assert r == int(g["rank"])
+    s.factor()
+    x = _np(s.solve(vv)).T[rows]
+    x_tol = SOLVE_TOL if prec == "fp64" else MIXED_TOL
+    assert _rel(x, g["x"]) <= x_tol, (prec, _rel(x, g["x"]))
+    s.close()
