@@ -210,3 +210,51 @@ def test_table1_n2008_against_stored_oracle(B, prec):
     x_tol = SOLVE_TOL if prec == "fp64" else MIXED_TOL
     assert _rel(x, g["x"]) <= x_tol, (prec, _rel(x, g["x"]))
     s.close()
+
+
+def test_general_farfield_and_adjoint_gradient(B, graded):
+    """The far-field operator and the amplitude gradient of a far-field misfit on the graded
+    mesh (the differentiation layer's entry points that do not differentiate the mesh):
+    F x against the oracle's far-field matrix, and the gradient of J(a) = sum |F A^-1 (a_w v_w)
+    - t|^2 through torch.autograd against the oracle's dense-LU gradient on the literal route's
+    operator."""
+    c = graded
+    obs = np.linspace(0.0, 2 * np.pi, 24, endpoint=False)
+    F = O.farfield_matrix(c["v"], c["k"], obs)
+    s = _solver(B, c)
+    s.filter_apply(N_MODES)
+    s.compress(1e-10)
+    s.factor()
+    x = c["efie"]["x"]
+    u = _np(s.farfield(_cuda(obs), _cuda(x.T))).T
+    assert _rel(u, F @ x) <= 1e-12, _rel(u, F @ x)
+    # misfit gradient in the amplitudes: A x = v with the literal route's operator in x
+    # coordinates, A = beta I + G^-1/2 P C2 G^1/2
+    lit = c["efie"]
+    A = lit["Gmh"] @ (lit["beta"] * np.eye(len(c["v"])) + lit["U"] @ lit["Vh"]) @ lit["Gh"]
+    a = np.array([1.0 + 0.5j, -0.3 + 0.2j, 0.7, 0.1j, -0.4])
+    rng = np.random.default_rng(5)
+    t = rng.standard_normal((len(obs), 5)) + 1j * rng.standard_normal((len(obs), 5))
+    V = c["vx"]
+    Xa = np.linalg.solve(A, V * a[None, :])
+    R = F @ Xa - t
+    J_ref = float(np.sum(np.abs(R) ** 2))
+    # J through torch.autograd on the GPU path; its gradient (dJ/dRe a + i dJ/dIm a, the
+    # binding's convention) against central differences of the oracle's J
+    v0 = s.rhs_planewave(_cuda(c["ang"]))
+    ag = _cuda(a).requires_grad_(True)
+    uu = B.farfield_solve(ag[:, None] * v0, s, _cuda(obs))
+    J = ((uu - _cuda(t.T)).abs() ** 2).sum()
+    J.backward()
+    assert abs(J.item() - J_ref) <= 1e-10 * J_ref, (J.item(), J_ref)
+    def J_of(av):
+        return float(np.sum(np.abs(F @ np.linalg.solve(A, V * av[None, :]) - t) ** 2))
+    eps = 1e-6
+    g = np.zeros(5, dtype=complex)
+    for w in range(5):
+        e = np.zeros(5); e[w] = eps
+        dr = (J_of(a + e) - J_of(a - e)) / (2 * eps)
+        di = (J_of(a + 1j * e) - J_of(a - 1j * e)) / (2 * eps)
+        g[w] = dr + 1j * di
+    assert _rel(ag.grad.cpu().numpy(), g) <= 1e-6, (ag.grad.cpu().numpy(), g)
+    s.close()
