@@ -258,3 +258,32 @@ def test_general_farfield_and_adjoint_gradient(B, graded):
         g[w] = dr + 1j * di
     assert _rel(ag.grad.cpu().numpy(), g) <= 1e-6, (ag.grad.cpu().numpy(), g)
     s.close()
+
+
+@pytest.mark.parametrize("N,n", [(16, 7), (40, 31), (65, 9)])
+def test_general_mesh_edge_sizes(B, N, n):
+    """Edge cases of the general-mesh kernels against the literal route: the smallest mesh (one
+    chunk in the chunked factor and solves), a filter whose subspace block is capped at N - 1
+    (n = 31 of N = 40), and a chunk boundary one past a multiple of 64."""
+    v, _ = I.parameter_mesh(I.cos_star(1.0, 0.3, 5), N, grade=0.3)
+    k = 1.0
+    mats = O.assemble(v, k, "SW")
+    ang = I.planewave_angles(3)
+    f = O.rhs_planewave(v, k, ang)
+    ref = O.filtered_solve_literal(mats, v, f, n, 1e-12)
+    s = B.Solver(device=0)
+    s.assemble(_cuda(v), k, ops="SW")
+    assert s.info()["equal_chord"] == 0
+    vv = s.rhs_planewave(_cuda(ang))
+    G = O.gram(v)
+    vx = np.linalg.solve(G, mats["S"] @ np.linalg.solve(G, f))
+    assert _rel(_np(vv).T, vx) <= 1e-12
+    s.filter_apply(n)
+    assert s.info()["basis_block"] == min(n + n // 2 + 9, N - 1)
+    r = s.compress(1e-12)
+    assert abs(r - ref["rank"]) <= 1
+    s.factor()
+    x = _np(s.solve(vv)).T
+    if r == ref["rank"]:
+        assert _rel(x, ref["x"]) <= SOLVE_TOL, _rel(x, ref["x"])
+    s.close()
