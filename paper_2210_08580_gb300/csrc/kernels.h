@@ -94,6 +94,7 @@ bem_status general_gram_apply(bem_ctx* h, int mode, const cplx* in, cplx* out, c
 size_t cyc_factor_bytes(int64_t N);
 // h->Q, h->GQ, h->gm of a general mesh (nc columns, with the constant mode when inc)
 bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc);
-void general_basis_plan(int64_t N, int64_t n, double perimeter, int64_t* p_out, int* iters_out, double* sigma_out);
+void general_basis_plan(int64_t N, int64_t n, double perimeter, int64_t* p_out, int* iters_out, double* sigma_out,
+                        double* bound_out);
 bem_status launch_copy2d(bem_ctx* h, void* dst, int64_t ldd, const void* src, int64_t lds,
                          int64_t rows, int64_t cols, size_t elem);

@@ -16,9 +16,9 @@
 //    with Phi = G^-1/2 V_n, so the filtered compact part is P_x C_x = Phi B with
 //        B = Phi^T G C_x = (Phi^T S) G^-1 N - (G Phi)^T / 4 - alpha Phi^T D.
 //    Only span(Phi) matters (any orthogonal mixing of its columns cancels in Phi B and in the
-//    compression), so Phi is found by shift-and-invert subspace iteration on
-//    sigma (L + sigma G)^-1 G from the arclength Fourier modes, G-orthonormalised every
-//    fourth step by a Cholesky QR, and one Rayleigh-Ritz step at the end whose small
+//    compression), so Phi is found by Chebyshev-accelerated shift-and-invert subspace
+//    iteration on sigma (L + sigma G)^-1 G from the arclength Fourier modes, G-orthonormalised
+//    every second step by a Cholesky QR, and one Rayleigh-Ritz step at the end whose small
 //    eigenproblem runs through the library's one-sided Jacobi SVD.  Its dense products and
 //    the small Cholesky run in double-float on the FP32 pipe.
 #include <math.h>
@@ -481,6 +481,16 @@ __global__ void k_tri_mul(const double* __restrict__ x, double* __restrict__ y, 
     y[idx] = v;
 }
 
+// Chebyshev step on equal-layout blocks: out = a Z + c Yc - Yp (Yp may be null)
+__global__ void k_cheb_comb(double* __restrict__ out, const double* __restrict__ Z, const double* __restrict__ Yc,
+                            const double* __restrict__ Yp, int64_t cnt, double a, double c) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    double v = fma(a, Z[i], c * Yc[i]);
+    if (Yp) v -= Yp[i];
+    out[i] = v;
+}
+
 // s[i] = sum_{e < i} h_e (arclength at vertex i), s[N] = perimeter; one thread, fixed order
 __global__ void k_arclength(const double* __restrict__ h, int N, double* s) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -875,25 +885,32 @@ static bem_status chol_inv(bem_ctx* h, double* C, float2* W, double* rdiag, int6
 }
 
 // block size of the subspace iteration for n wanted pairs, and its iteration count
-void general_basis_plan(int64_t N, int64_t n, double perimeter, int64_t* p_out, int* iters_out, double* sigma_out) {
+void general_basis_plan(int64_t N, int64_t n, double perimeter, int64_t* p_out, int* iters_out, double* sigma_out,
+                        double* bound_out) {
     // block: measured at N = 16384, n = 201 against 2n + 9 and 1.75 n + 9 (the one-CTA
-    // Cholesky and the Jacobi grow as p^3, the products as N p^2, the step count as the rate
-    // below approaches one)
+    // Cholesky and the Jacobi grow as p^3, the products as N p^2, the step count as the
+    // separation below shrinks)
     int64_t p = n + n / 2 + 9;
     if (p > 1023) p = 1023;
     if (p > N - 1) p = N - 1;
     if (p < n) p = n;
-    // rates from the curve's Laplace-Beltrami spectrum lambda = (2 pi m / P)^2, which the
-    // pencil's low eigenvalues approach (and exceed) on any mesh that resolves them
+    // The operator sigma (L + sigma G)^-1 G has the eigenvalues mu = sigma / (lambda + sigma).
+    // The pencil's eigenvalues bound those of the curve's Laplace-Beltrami operator,
+    // lambda = (2 pi m / P)^2 on the polygon's perimeter P, from above (conforming P1
+    // Galerkin), so every unwanted mu lies in [0, b], b = sigma / (lambda_{p+1} + sigma): the
+    // interval the Chebyshev steps damp.  Degree: T_d(2 mu_n / b - 1) >= 1e17 on the wanted
+    // end, plus two.
     const double w = 2.0 * BEM_PI / perimeter;
     const double mn = (double)((n - 1) / 2 + 1), mp = (double)((p + 1) / 2);
     const double lam_n = (w * mn) * (w * mn), lam_p = (w * mp) * (w * mp);
     const double sigma = std::max(0.25 * lam_n, w * w);
-    const double rate = (lam_n + sigma) / (lam_p + sigma);
-    int it = (rate < 1.0) ? (int)ceil(log(1e-17) / log(rate)) + 2 : 400;
+    const double mu_n = sigma / (lam_n + sigma), b = sigma / (lam_p + sigma);
+    const double x0 = 2.0 * mu_n / b - 1.0;
+    int it = (x0 > 1.0) ? (int)ceil(acosh(1e17) / acosh(x0)) + 2 : 400;
     *p_out = p;
     *iters_out = std::min(std::max(it, 3), 400);
     *sigma_out = sigma;
+    *bound_out = b;
 }
 
 static bem_status read_basis_err(bem_ctx* h) {
@@ -917,11 +934,12 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     const int64_t n = inc ? nc : nc + 1;
     int64_t p;
     int iters;
-    double sigma;
-    general_basis_plan(N, n, h->hbar * (double)N, &p, &iters, &sigma);
+    double sigma, bnd;
+    general_basis_plan(N, n, h->hbar * (double)N, &p, &iters, &sigma, &bnd);
     h->basis_block = (int)p;
     h->basis_iters = iters;
-    double *X = nullptr, *Y = nullptr, *Z = nullptr, *C = nullptr, *Rinv = nullptr, *Cf = nullptr, *fac = nullptr,
+    double *X = nullptr, *Y = nullptr, *Z = nullptr, *Wb = nullptr, *Vb = nullptr, *C = nullptr, *Rinv = nullptr,
+           *Cf = nullptr, *fac = nullptr,
            *s = nullptr, *sig = nullptr, *part = nullptr, *abG = nullptr, *abL = nullptr, *abGs = nullptr,
            *cscr = nullptr, *rdg = nullptr;
     cplx *Rc = nullptr, *E = nullptr;
@@ -932,6 +950,8 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     cv.add((void**)&X, sizeof(double) * N * p);
     cv.add((void**)&Y, sizeof(double) * N * p);
     cv.add((void**)&Z, sizeof(double) * N * p);
+    cv.add((void**)&Wb, sizeof(double) * N * p);
+    cv.add((void**)&Vb, sizeof(double) * N * p);
     cv.add((void**)&C, sizeof(double) * p * p);
     cv.add((void**)&Rinv, sizeof(double) * p * p);
     cv.add((void**)&Wdf, sizeof(float2) * p * p);
@@ -977,21 +997,43 @@ bem_status general_filter_basis(bem_ctx* h, int64_t nc, int inc) {
     };
     if ((st = cholqr(X, Y)) != BEM_OK) return st;
     std::swap(X, Y);
-    for (int it = 0; it < iters; ++it) {
-        // Y = sigma (L + sigma G)^-1 G X
-        if ((st = tri_mul(h, X, Z, p, abGs, true)) != BEM_OK) return st;
-        if ((st = cyc_solve_chunked<double>(h, 0, Z, Y, N, p, p, 1, fac, cscr, false)) != BEM_OK) return st;
-        // The span does not depend on the basis, so the basis is re-orthonormalised only every
-        // fourth step and at each of the last three, which set the final accuracy.  Its
-        // condition grows by at most (lambda_{p+1} + sigma)/sigma per step (about 11 for
-        // p = 1.5 n, 14 at n = 21), so the Gram matrix of the fourth step stays below 1e10,
-        // far inside what the double-float Cholesky factors.
-        if (it % 4 == 3 || it >= iters - 3) {
-            if ((st = cholqr(Y, X)) != BEM_OK) return st;
+    // Chebyshev subspace iteration on the damped interval [0, b] of T = sigma (L + sigma G)^-1 G:
+    // with S = (2/b) T - I, Y_0 = X, Y_1 = S Y_0, Y_{d+1} = 2 S Y_d - Y_{d-1}; the wanted
+    // components grow as T_d(2 mu / b - 1) while every unwanted one stays within [-1, 1] (plain
+    // powers of T needed 56 steps for n = 201 where this needs 24).  The pair (Y_d, Y_{d+1}) is
+    // re-orthonormalised by one right factor (the recurrence is linear in the pair) every
+    // second step and at each of the last two: a step widens the spread of the components by
+    // at most T_1(2/b - 1) < 4/b (about 40 for p = 1.5 n), so the Gram matrix of the second
+    // step stays far inside what the double-float Cholesky factors.
+    const int64_t cnt = N * p;
+    const unsigned gcm = (unsigned)((cnt + 255) / 256);
+    auto apply_T = [&](const double* in, double* out) -> bem_status {    // out = T in
+        bem_status q;
+        if ((q = tri_mul(h, in, out, p, abGs, true)) != BEM_OK) return q;
+        return cyc_solve_chunked<double>(h, 0, out, out, N, p, p, 1, fac, cscr, false);
+    };
+    auto comb = [&](double* out, const double* Zs, const double* Yc_, const double* Yp_, double a_, double c_) -> bem_status {
+        BEM_TIMED(h, "k_cheb_comb", (k_cheb_comb<<<gcm, 256, 0, h->stream>>>(out, Zs, Yc_, Yp_, cnt, a_, c_)));
+        BEM_LAUNCH(h, "k_cheb_comb");
+        return BEM_OK;
+    };
+    double *Yp = X, *Yc = Y, *F1 = Wb, *F2 = Vb;
+    if ((st = apply_T(Yp, Z)) != BEM_OK) return st;
+    if ((st = comb(Yc, Z, Yp, nullptr, 2.0 / bnd, -1.0)) != BEM_OK) return st;
+    for (int d = 1; d < iters; ++d) {
+        if ((st = apply_T(Yc, Z)) != BEM_OK) return st;
+        if ((st = comb(F1, Z, Yc, Yp, 4.0 / bnd, -2.0)) != BEM_OK) return st;      // Y_{d+1}
+        if (d % 2 == 1 || d >= iters - 2) {
+            if ((st = cholqr(F1, F2)) != BEM_OK) return st;                        // Y_{d+1} R^-1
+            if ((st = dgemm_t<OP_T, OP_N, true>(h, p, N, p, Rinv, p, Yc, p, F1, p)) != BEM_OK) return st;   // Y_d R^-1
+            double *oYp = Yp, *oYc = Yc;
+            Yp = F1; Yc = F2; F1 = oYp; F2 = oYc;
         } else {
-            std::swap(X, Y);
+            double* oYp = Yp;
+            Yp = Yc; Yc = F1; F1 = oYp;
         }
     }
+    X = Yc;
     // Rayleigh-Ritz: A = X^T L X; the eigenvectors of A + sigma I are the right singular
     // vectors of its Cholesky factor (Jacobi SVD, sorted by decreasing singular value)
     if ((st = tri_mul(h, X, Z, p, abL, true)) != BEM_OK) return st;
