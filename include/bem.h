@@ -208,10 +208,11 @@ bem_status bem_assemble_batch(bem_handle* hs, int64_t nprob, const double* const
  * the pencil L phi = lambda G phi (Q = G^-1/2 V_n, V_n those of L~; the filter in nodal
  * coordinates is Q Q^T G), g_m = 1, and
  *     B = Q^T G (G^-1 S G^-1 N - I/4 - alpha G^-1 D) = (Q^T S) G^-1 N - alpha Q^T D - (G Q)^T/4;
- * Q comes from Chebyshev-accelerated shift-and-invert subspace iteration on sigma (L + sigma G)^-1 G (block of about
- * 1.5 n + 9 columns, at most 1023, started from arclength Fourier modes, Cholesky-QR
- * G-orthonormalised) and one Rayleigh-Ritz step through the Jacobi SVD; its span matches
- * the eigenvectors to rounding (a non-positive Cholesky pivot returns BEM_E_SINGULAR).
+ * Q comes from Chebyshev-accelerated shift-and-invert subspace iteration on
+ * sigma (L + sigma G)^-1 G (a block of about 1.5 n + 9 columns, at most 1023, started from
+ * arclength Fourier modes, Cholesky-QR G-orthonormalised) and one Rayleigh-Ritz step through
+ * the Jacobi SVD; its span matches the eigenvectors to rounding (a non-positive Cholesky
+ * pivot returns BEM_E_SINGULAR).
  * n_modes must be odd, 3 <= n_modes <= min(N - 1, 1023).  Needs S, W (and D if alpha != 0). */
 bem_status filter_apply(bem_handle h, int64_t n_modes, double alpha);
 
