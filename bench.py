@@ -419,10 +419,11 @@ def run_batch(args, rank, world):
     clocks.start()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        bs.run()
+        res = bs.run()
     torch.cuda.synchronize(dev)
     dt = reduce_max((time.perf_counter() - t0) / args.steps, dist, dev)
     clk = clocks.stop()
+    solve_stage = time_solve_stage(bs, res, dev)
     bs.close()
     if rank == 0:
         line = {"metric": "batched factor + RHS solves/s, uneven random stars", "value": job_value(nrhs_total, world, dt),
@@ -436,12 +437,71 @@ def run_batch(args, rank, world):
                            "tuned_tiles": {str(b): {k: v for k, v in c.items() if k != "times_ms"}
                                            for b, c in (tiles or {}).items()},
                            "assembly": "one persistent launch over a global tile queue (bem_assemble_batch)",
+                           "solve_stage": solve_stage,
                            "parallelism": f"replicas x{world}"},
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def time_solve_stage(bs, res, dev, reps=3):
+    """The FP64 Woodbury solves of every problem of a factored batch, two ways: the CUDA
+    graph of one solve_many_noalloc per problem (SolveGraph) and one persistent launch over
+    all problems' tiles (solve_grouped).  Wall time per solve of the whole batch, synchronised
+    on both sides (after one untimed run of each); the two results' largest relative
+    difference; FP64 flops of the method's products (8 per complex multiply-add:
+    V^H v, Kinv T, U T2)."""
+    import torch
+    from paper_2210_08580_gb300 import batch
+    vs = [out["v"] for out in res]
+    flops = sum(8.0 * out["v"].shape[0] * (2.0 * out["rank"] * out["v"].shape[1] + out["rank"] ** 2)
+                for out in res)
+    xs = [torch.empty_like(v) for v in vs]
+    runs = [("grouped", lambda: batch.solve_grouped(bs.solvers, vs, xs))]
+    try:
+        g = batch.SolveGraph(bs, device=dev.index)
+        for i, v in enumerate(vs):
+            g.v[i].copy_(v)
+        runs.insert(0, ("graph", g.replay))
+    except Exception as e:          # e.g. rank x nrhs above solve_many_noalloc's fixed scratch
+        g = None
+        graph_error = str(e)
+    timed = {"graph": None}
+    s0 = bs.solvers[0]
+    kernel_ms = None
+    for name, fn in runs:
+        fn()
+        torch.cuda.synchronize(dev)
+        if name == "grouped":
+            s0.timing(True)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize(dev)
+        timed[name] = (time.perf_counter() - t0) / reps
+        if name == "grouped":
+            cnt, tot = s0.timing_report().get("k_woodbury_batch", [0, 0.0])
+            s0.timing(False)
+            kernel_ms = tot / cnt if cnt else None
+    roof = None
+    if kernel_ms:
+        ach = flops / (kernel_ms / 1000.0) / 1e12
+        roof = {"kernel": "k_woodbury_batch", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s (FP64 pipe)", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "ms_per_launch": kernel_ms, "flops_per_launch": flops,
+                "peak_source": "derived: 152 SMs x 2 DFMA per clock x 2 flops x 2.07 GHz"}
+    if g is None:
+        return {"graph_ms": None, "graph_error": graph_error, "grouped_ms": round(1000 * timed["grouped"], 3),
+                "fp64_gflop": round(flops / 1e9, 2)}
+    diff = max(float((a - b).abs().max() / b.abs().max()) for a, b in zip(xs, g.x))
+    return {"graph_ms": round(1000 * timed["graph"], 3), "grouped_ms": round(1000 * timed["grouped"], 3),
+            "fp64_gflop": round(flops / 1e9, 2),
+            "grouped_fp64_tflops": round(flops / timed["grouped"] / 1e12, 3),
+            "max_rel_diff": diff, "reps": reps, "roofline": roof,
+            "how": "one solve of every problem's right-hand sides: CUDA graph of per-problem "
+                   "solve_many_noalloc vs one persistent launch (bem_solve_batch)"}
 
 
 def workload_config(args):

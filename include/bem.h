@@ -307,6 +307,28 @@ bem_status solve_backward(bem_handle h, const void* g_dev, int64_t ldg, void* la
 bem_status solve_many_noalloc(bem_handle h, const void* v_dev, int64_t ldv, void* x_dev, int64_t ldx,
                               int64_t nrhs);
 
+/* bem_solve_batch -- the FP64 Woodbury solve of solve_many (Sec. IV-A: x = v/beta -
+ * beta^-2 U (I_r + beta^-1 V^H U)^-1 V^H v) for nprob factored problems in ONE persistent
+ * launch: problem q solves with handle hs[q] the nrhs[q] right-hand sides v_dev[q] (column-major
+ * N_q x nrhs[q] complex128, leading dimension ldv[q]) into x_dev[q] (ldx[q]).  The arrays are
+ * host arrays of nprob entries; the buffers are device memory the caller owns.  CTAs take
+ * 64 x 64 tiles of all problems' products from one global queue (V^H v in 1024-long slices of
+ * N, then the core product, then x), so small problems fill the GPU beside large ones;
+ * a tile that needs another stage's results waits for them with a bounded device-side wait.
+ * Runs on hs[0]'s stream after every handle's earlier work; every handle's later work waits
+ * for it.  Synchronises hs[0]'s stream (to read the device status).  Scratch: the core
+ * products, sum over q of r_q nrhs[q] (ceil(N_q / 1024) + 1) complex doubles, taken from
+ * hs[0]'s device memory provider for the call.  The same handle may appear more than once;
+ * no x_dev[q] may overlap any v_dev or another x_dev.  On a BEM_MIXED_BF16 handle it solves
+ * with that handle's factors in FP64 without refinement, as solve_many_noalloc does.  The
+ * batching layer's solve stage; the paper solves one problem at a time.
+ * Errors: BEM_E_INVALID (null arrays, nprob outside [1, 65536], a handle not factored or on
+ * another device, bad v/x/ld/nrhs; the message names the problem and is left on hs[0]),
+ * BEM_E_UNSUPPORTED (N >= 2^30), BEM_E_NOMEM/BEM_E_CUDA (scratch, launch), BEM_E_TIMEOUT
+ * (a device-side wait gave up; x is then incomplete). */
+bem_status bem_solve_batch(bem_handle* hs, int64_t nprob, const void* const* v_dev, const int64_t* ldv,
+                           void* const* x_dev, const int64_t* ldx, const int64_t* nrhs);
+
 /* bem_farfield -- far field of the current x (P1 coefficients, x = -u_tot on the curve)
  * for the sound-hard problem of Sec. II: Green's representation u_s = int u_tot dg/dnu_y,
  * and g(x, y) ~ C0 e^{ik|x|}/sqrt|x| e^{-ik xhat.y}, C0 = e^{i pi/4}/sqrt(8 pi k), give

@@ -13,7 +13,9 @@ else overlaps freely.
 ``autotune_streams`` times a few stream counts on a sample of the batch and keeps the
 fastest per problem-size bucket.  ``SolveGraph`` records the FP64 Woodbury solves of every
 problem (``solve_many_noalloc``, which allocates nothing) into one CUDA graph, replayed
-for each new set of right-hand sides.
+for each new set of right-hand sides; ``solve_grouped`` instead solves every problem's
+right-hand sides in ONE persistent launch (``bem_solve_batch``: tiles of all problems'
+Woodbury products from a global queue, bounded device-side waits between the stages).
 
 By default the assembly stage of all problems is one persistent launch
 (``bem_assemble_batch``): CTAs take tiles from a global queue over every problem, largest
@@ -23,6 +25,7 @@ same tile code), so the results are those of the problems solved one after anoth
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
 import math
 import threading
@@ -289,3 +292,31 @@ class SolveGraph:
 
     def replay(self):
         self.graph.replay()
+
+
+def solve_grouped(solvers: list, vs: list, xs: list | None = None) -> list:
+    """x_i = A_i^-1 v_i for factored solvers (``bem.Solver``, one device) in one persistent
+    launch of FP64 Woodbury tiles (``bem_solve_batch``).  ``vs[i]`` is a complex128 tensor of
+    shape (nrhs_i, N_i) on the device; ``xs`` (same shapes) receives the solutions and is
+    allocated when None.  Runs on the first solver's stream, after every solver's earlier
+    work; returns once it is done."""
+    if len(solvers) != len(vs) or not solvers:
+        raise ValueError("one right-hand-side block per solver")
+    if xs is None:
+        xs = [torch.empty_like(v) for v in vs]
+    n = len(solvers)
+    L = bem.load_library()
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    hs = (vp * n)(*[s.h.value for s in solvers])
+    vv = (vp * n)(*[v.data_ptr() for v in vs])
+    xx = (vp * n)(*[x.data_ptr() for x in xs])
+    ld = (i64 * n)(*[s.N for s in solvers])
+    nr = (i64 * n)(*[v.shape[0] for v in vs])
+    for s, v, x in zip(solvers, vs, xs):
+        if v.dtype != torch.complex128 or v.shape != x.shape or v.shape[1] != s.N or not v.is_contiguous() \
+                or not x.is_contiguous():
+            raise ValueError("v, x: contiguous complex128 (nrhs, N) tensors")
+    st = L.bem_solve_batch(hs, n, vv, ld, xx, ld, nr)
+    if st != 0:
+        raise bem.BemError(st, L.bem_last_error(solvers[0].h).decode())
+    return xs

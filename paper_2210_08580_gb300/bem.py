@@ -28,7 +28,7 @@ EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error",
            "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info", "bem_timing_enable",
            "bem_timing_report", "solve_many_noalloc", "bem_farfield", "bem_farfield_adjoint",
            "bem_shape_vjp", "bem_rhs_pointsource", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain",
-           "bem_assemble_batch", "bem_factor_rhs_planewave")
+           "bem_assemble_batch", "bem_factor_rhs_planewave", "bem_solve_batch")
 
 
 class BemOptions(ctypes.Structure):
@@ -137,13 +137,15 @@ def load_library(path: str = LIB_PATH):
     L.bem_shape_chain.argtypes = [vp, vp, i64, vp, vp]
     L.bem_assemble_batch.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp), ctypes.POINTER(i64),
                                      ctypes.POINTER(dbl)]
+    L.bem_solve_batch.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                  ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.bem_timing_enable.argtypes = [vp, i32]
     L.bem_timing_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     for name in ("bem_create", "bem_destroy", "bem_set_stream", "bem_assemble", "filter_apply",
                  "compress_compact", "factor", "bem_rhs_planewave", "bem_rhs_pointsource", "solve_many", "solve_backward",
                  "bem_get_matrix", "bem_get_info", "bem_timing_enable", "bem_timing_report", "bem_farfield",
                  "bem_farfield_adjoint", "bem_shape_vjp", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain",
-                 "bem_assemble_batch", "bem_factor_rhs_planewave"):
+                 "bem_assemble_batch", "bem_factor_rhs_planewave", "bem_solve_batch"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

@@ -1,6 +1,7 @@
 """Batching layer: many uneven geometries solved concurrently on several streams give the
 results of solving them one by one; the recorded CUDA graph of the FP64 solves replays
-them; the stream-count tuner returns a choice per size bucket."""
+them, and so does the grouped persistent solve; the stream-count tuner returns a choice per
+size bucket."""
 import numpy as np
 import pytest
 import torch
@@ -73,6 +74,71 @@ def test_solve_graph_replays_all_solves(B, problems):
     bs.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_grouped_solve_matches_one_by_one(B, problems, prec):
+    """bem_solve_batch (every problem's Woodbury products in one persistent launch) gives
+    each problem's FP64 Woodbury solve: the batch's own solutions on FP64 handles,
+    solve_many_noalloc's on mixed ones (same factors, FP64 products; the slices of V^H v only
+    change the order of the sums)."""
+    bem, batch = B
+    L = bem.load_library()
+    bs = batch.BatchSolver(problems, prec=prec, n_streams=3)
+    res = bs.run()
+    vs = [out["v"] for out in res]
+    xg = batch.solve_grouped(bs.solvers, vs)
+    torch.cuda.synchronize()
+    for i, (s, out) in enumerate(zip(bs.solvers, res)):
+        x1 = torch.empty_like(vs[i])
+        assert L.solve_many_noalloc(s.h, vs[i].data_ptr(), s.N, x1.data_ptr(), s.N, vs[i].shape[0]) == 0
+        torch.cuda.synchronize()
+        err = float((xg[i] - x1).abs().max() / x1.abs().max())
+        assert err <= 1e-13, (i, err)
+        if prec == "fp64":
+            err = float((xg[i] - out["x"]).abs().max() / out["x"].abs().max())
+            assert err <= 1e-13, (i, err)
+    bs.close()
+
+
+def test_grouped_solve_edges(B):
+    """Ragged slices and tiles: N = 2500 (three 1024-long slices of V^H v, the last 452),
+    nrhs 1, 65 and 130 (one-wide and ragged column blocks), one handle twice with different
+    right-hand sides, a mixed handle beside FP64 ones; each against the handle's own FP64
+    Woodbury solve.  A handle that is not factored is refused by name, before any work."""
+    bem, batch = B
+    L = bem.load_library()
+    star = I.cos_star(1.0, 0.3, 5)
+    specs = [(I.equal_chord_mesh(star, 2500)[0], 2.0, "fp64"), (I.equal_chord_mesh(star, 300)[0], 0.7, "fp64"),
+             (I.equal_chord_mesh(I.perturbed_circle(), 700)[0], 1.3, "mixed")]
+    ss = []
+    for verts, k, prec in specs:
+        s = bem.Solver(device=0, prec=prec)
+        s.assemble(torch.from_numpy(verts).cuda(), k, ops="SW")
+        s.filter_apply(21)
+        s.compress(1e-10)
+        s.factor()
+        ss.append(s)
+    gen = torch.Generator().manual_seed(7)
+    shapes = [(130, 2500), (1, 300), (65, 2500), (65, 700)]
+    who = [ss[0], ss[1], ss[0], ss[2]]
+    vs = [torch.complex(torch.randn(sh, generator=gen, dtype=torch.float64),
+                        torch.randn(sh, generator=gen, dtype=torch.float64)).cuda() for sh in shapes]
+    xg = batch.solve_grouped(who, vs)
+    torch.cuda.synchronize()
+    for s, v, x in zip(who, vs, xg):
+        x1 = torch.empty_like(v)
+        assert L.solve_many_noalloc(s.h, v.data_ptr(), s.N, x1.data_ptr(), s.N, v.shape[0]) == 0
+        torch.cuda.synchronize()
+        err = float((x - x1).abs().max() / x1.abs().max())
+        assert err <= 1e-13, (s.N, v.shape[0], err)
+    fresh = bem.Solver(device=0)
+    fresh.assemble(torch.from_numpy(specs[1][0]).cuda(), 0.7, ops="SW")
+    with pytest.raises(bem.BemError) as ei:
+        batch.solve_grouped([ss[1], fresh], [vs[1], vs[1].clone()])
+    assert ei.value.status == 1 and "problem 1" in str(ei.value)
+    for s in ss + [fresh]:
+        s.close()
+
+
 def test_stream_tuner_picks_per_bucket(B, problems):
     _, batch = B
     best = batch.autotune_streams(problems[:3], prec="fp64", candidates=(1, 2), sample=2)
@@ -109,6 +175,7 @@ def test_batch_subsample_against_the_oracle(B, prec):
     problems = batch.problems_from_inputs(I.batch_problems(count=int(g["count"]), first_seed=100, n_hi=2048))
     bs = batch.BatchSolver(problems, prec=prec, n_streams=4, refine_rtol=1e-8)
     res = bs.run()
+    errs = []
     for i, out in enumerate(res):
         kappa = float(g[f"p{i}_kappa"])
         if prec == "fp64":
@@ -124,6 +191,16 @@ def test_batch_subsample_against_the_oracle(B, prec):
         print(f"batch {prec} problem {i}: N={problems[i].verts.shape[0]} k={problems[i].k:.3g} kappa={kappa:.3g} "
               f"rank {r}/{r0} x err {err:.2e} (tol {tol:.1e})")
         assert abs(r - r0) <= 1
+        assert err <= tol, (i, err, tol)
+        errs.append((x, ref, tol))
+    # the same right-hand sides through the grouped persistent solve (FP64 Woodbury tiles of
+    # all 8 problems in one launch; on mixed handles it is the exact inverse of the handle's
+    # compressed operator, which the refined solve converges to)
+    xg = batch.solve_grouped(bs.solvers, [out["v"] for out in res])
+    for i, (x_b, ref, tol) in enumerate(errs):
+        xgi = xg[i].cpu().numpy().T[g[f"p{i}_rows"]][:, g[f"p{i}_cols"]]
+        err = float(np.max(np.abs(xgi - ref)) / np.max(np.abs(ref)))
+        print(f"grouped {prec} problem {i}: x err {err:.2e} (tol {tol:.1e})")
         assert err <= tol, (i, err, tol)
     bs.close()
 
