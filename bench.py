@@ -201,6 +201,9 @@ def parse():
                     help="single: one N=16384 star (the headline metric); batch: many uneven stars at once")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--streams", type=int, default=0, help="batch streams (0 = tuned per size bucket)")
+    ap.add_argument("--batch-solve", default="each", choices=["each", "grouped"],
+                    help="batch solves: per problem on its stream, or one persistent launch after all "
+                         "right-hand sides")
     return ap.parse_args()
 
 
@@ -409,7 +412,8 @@ def run_batch(args, rank, world):
     else:
         tuned = batch.autotune_streams(problems, prec=args.prec, device=local, candidates=(1, 2, 4, 8), sample=4)
         n_streams = max(set(tuned.values()), key=list(tuned.values()).count)
-    bs = batch.BatchSolver(problems, prec=args.prec, device=local, n_streams=n_streams, tiles=tiles)
+    solve = args.batch_solve
+    bs = batch.BatchSolver(problems, prec=args.prec, device=local, n_streams=n_streams, tiles=tiles, solve=solve)
     for _ in range(args.warmup):
         bs.run()
     torch.cuda.synchronize(dev)
@@ -433,7 +437,7 @@ def run_batch(args, rank, world):
                 "config": {"workload": f"{args.batch_count} random stars (seeds 100.., N ~ U{{512..8192}}, "
                                        f"k = 10^U(-2, log10 5), 64..512 plane waves)",
                            "problems": args.batch_count, "rhs_total": nrhs_total, "prec": args.prec,
-                           "streams": n_streams, "tuned_streams": tuned,
+                           "streams": n_streams, "tuned_streams": tuned, "solve": solve,
                            "tuned_tiles": {str(b): {k: v for k, v in c.items() if k != "times_ms"}
                                            for b, c in (tiles or {}).items()},
                            "assembly": "one persistent launch over a global tile queue (bem_assemble_batch)",

@@ -65,11 +65,20 @@ class BatchSolver:
     """Solves a list of Problems concurrently on ``n_streams`` streams of one device."""
 
     def __init__(self, problems: list[Problem], prec: str = "mixed", device: int = 0, n_streams: int = 4,
-                 refine_rtol: float = 1e-10, persistent: bool = True, tiles: dict | None = None):
+                 refine_rtol: float = 1e-10, persistent: bool = True, tiles: dict | None = None,
+                 solve: str = "each"):
         """persistent: assemble every problem's S and N in one launch over a global tile queue
         (bem_assemble_batch) before the per-problem stages; False: each problem assembles on
         its own stream.  tiles: {size bucket: tile options} from ``autotune_tiles`` (mixed
-        path), applied to each problem by its bucket."""
+        path), applied to each problem by its bucket.  solve: "each" solves every problem on
+        its stream as soon as its right-hand sides are formed (the results of one-by-one
+        solves, bit for bit); "grouped" solves all problems after the last right-hand sides
+        in one persistent launch of FP64 Woodbury tiles (``solve_grouped``: the one-by-one
+        FP64 solves up to the order of the sums; on mixed handles the exact inverse of the
+        compressed operator, without refinement)."""
+        if solve not in ("each", "grouped"):
+            raise ValueError("solve: 'each' or 'grouped'")
+        self.solve = solve
         self.problems = problems
         self.prec = prec
         self.device = device
@@ -117,7 +126,7 @@ class BatchSolver:
                     self._budget += need
                     self._coop.notify_all()
             v = s.rhs_planewave(ang)
-            x = s.solve(v)
+            x = s.solve(v) if self.solve == "each" else None
             self.results[i] = dict(x=x, v=v, rank=r)
 
     def _coop_ctas(self, p: Problem) -> int:
@@ -160,6 +169,10 @@ class BatchSolver:
             t.join()
         if errors:
             raise errors[0]
+        if self.solve == "grouped":
+            xs = solve_grouped(self.solvers, [r["v"] for r in self.results])
+            for r, x in zip(self.results, xs):
+                r["x"] = x
         return self.results
 
     def close(self):

@@ -38,16 +38,18 @@ def _single(bem, p, prec):
     return x, r
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_batch_matches_one_by_one(B, problems, prec):
+@pytest.mark.parametrize("prec,solve", [("fp64", "each"), ("mixed", "each"), ("fp64", "grouped")])
+def test_batch_matches_one_by_one(B, problems, prec, solve):
+    """The batch gives the one-by-one solutions: to the last bits with per-problem solves, to
+    1e-13 with the grouped solve (the slices of V^H v reorder the FP64 sums)."""
     bem, batch = B
-    bs = batch.BatchSolver(problems, prec=prec, n_streams=3)
+    bs = batch.BatchSolver(problems, prec=prec, n_streams=3, solve=solve)
     res = bs.run()
     for p, out in zip(problems, res):
         x, r = _single(bem, p, prec)
         assert out["rank"] == r
         err = float((out["x"] - x).abs().max() / x.abs().max())
-        assert err <= 1e-14, err
+        assert err <= (1e-14 if solve == "each" else 1e-13), err
     bs.close()
 
 
