@@ -4,8 +4,9 @@
 //     x_p = v_p / beta_p - beta_p^-2 U_p Kinv_p (V_p^H v_p)      for every problem p.
 // Three stages of 64 x 64 complex tiles (column-major, FP64 FMAs) taken from one global
 // queue by persistent CTAs:
-//     A  partial products V^H v over 1024-long slices of N (split K: every SM gets work even
-//        when each problem has a handful of right-hand-side blocks),
+//     A  partial products V^H v over 256-long slices of N (split K: every SM gets work even
+//        when each problem has a handful of right-hand-side blocks, and a problem's chain of
+//        stages stays short: 16 K steps per slice instead of N/16),
 //     B  T2 = Kinv T, with T summed from the slices in slice order (a fixed order: the
 //        result does not depend on which CTA ran what),
 //     C  x = v / beta - beta^-2 U T2.
@@ -22,7 +23,7 @@
 
 #define WB_T 64      // tile edge (rows and right-hand sides)
 #define WB_BK 16     // K step staged in shared memory
-#define WB_KC 1024   // slice of N per stage-A tile
+#define WB_KC 256    // slice of N per stage-A tile
 
 struct WbProb {
     const cplx* U;       // N x r, ld N

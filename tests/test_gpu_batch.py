@@ -102,7 +102,7 @@ def test_grouped_solve_matches_one_by_one(B, problems, prec):
 
 
 def test_grouped_solve_edges(B):
-    """Ragged slices and tiles: N = 2500 (three 1024-long slices of V^H v, the last 452),
+    """Ragged slices and tiles: N = 2500 (ten 256-long slices of V^H v, the last 196),
     nrhs 1, 65 and 130 (one-wide and ragged column blocks), one handle twice with different
     right-hand sides, a mixed handle beside FP64 ones; each against the handle's own FP64
     Woodbury solve.  A handle that is not factored is refused by name, before any work."""
