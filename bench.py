@@ -176,7 +176,7 @@ def roofline(rep, args, n_modes, r, quad_points, top=3, basis=None, nsteps=1):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
@@ -226,6 +226,11 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # nvidia-smi takes a moment to start: let its first sample land before the timed
+            # region begins, so that the samples span the region (at most 3 s)
+            t0 = time.perf_counter()
+            while os.path.getsize(self.path) == 0 and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
