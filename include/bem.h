@@ -325,9 +325,19 @@ bem_status solve_many_noalloc(bem_handle h, const void* v_dev, int64_t ldv, void
  * Errors: BEM_E_INVALID (null arrays, nprob outside [1, 65536], a handle not factored or on
  * another device, bad v/x/ld/nrhs; the message names the problem and is left on hs[0]),
  * BEM_E_UNSUPPORTED (N >= 2^30), BEM_E_NOMEM/BEM_E_CUDA (scratch, launch), BEM_E_TIMEOUT
- * (a device-side wait gave up; x is then incomplete). */
+ * (a device-side wait gave up, after 10 s; x is then incomplete). */
 bem_status bem_solve_batch(bem_handle* hs, int64_t nprob, const void* const* v_dev, const int64_t* ldv,
                            void* const* x_dev, const int64_t* ldx, const int64_t* nrhs);
+
+/* bem_solve_batch_stall_check -- failure detection of bem_solve_batch's device-side waits,
+ * without a GPU fault: the same call and kernel, but the first completion counter of the
+ * first problem in the queue starts far below its target, so the tiles waiting on it give up
+ * after stall_ms (1 .. 10000) of wall time instead of the production limit of 10 s.  Expected
+ * result: BEM_E_TIMEOUT, with x incomplete, the device status word cleared and the handles
+ * usable for the next call.  Other errors as bem_solve_batch.  No paper counterpart. */
+bem_status bem_solve_batch_stall_check(bem_handle* hs, int64_t nprob, const void* const* v_dev,
+                                       const int64_t* ldv, void* const* x_dev, const int64_t* ldx,
+                                       const int64_t* nrhs, int stall_ms);
 
 /* bem_farfield -- far field of the current x (P1 coefficients, x = -u_tot on the curve)
  * for the sound-hard problem of Sec. II: Green's representation u_s = int u_tot dg/dnu_y,

@@ -307,29 +307,42 @@ class SolveGraph:
         self.graph.replay()
 
 
+def _grouped_args(solvers: list, vs: list, xs: list | None):
+    if len(solvers) != len(vs) or not solvers:
+        raise ValueError("one right-hand-side block per solver")
+    if xs is None:
+        xs = [torch.empty_like(v) for v in vs]
+    for s, v, x in zip(solvers, vs, xs):
+        if v.dtype != torch.complex128 or v.shape != x.shape or v.shape[1] != s.N or not v.is_contiguous() \
+                or not x.is_contiguous():
+            raise ValueError("v, x: contiguous complex128 (nrhs, N) tensors")
+    n = len(solvers)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    ld = (i64 * n)(*[s.N for s in solvers])
+    args = ((vp * n)(*[s.h.value for s in solvers]), n, (vp * n)(*[v.data_ptr() for v in vs]), ld,
+            (vp * n)(*[x.data_ptr() for x in xs]), ld, (i64 * n)(*[v.shape[0] for v in vs]))
+    return args, xs
+
+
 def solve_grouped(solvers: list, vs: list, xs: list | None = None) -> list:
     """x_i = A_i^-1 v_i for factored solvers (``bem.Solver``, one device) in one persistent
     launch of FP64 Woodbury tiles (``bem_solve_batch``).  ``vs[i]`` is a complex128 tensor of
     shape (nrhs_i, N_i) on the device; ``xs`` (same shapes) receives the solutions and is
     allocated when None.  Runs on the first solver's stream, after every solver's earlier
     work; returns once it is done."""
-    if len(solvers) != len(vs) or not solvers:
-        raise ValueError("one right-hand-side block per solver")
-    if xs is None:
-        xs = [torch.empty_like(v) for v in vs]
-    n = len(solvers)
     L = bem.load_library()
-    vp, i64 = ctypes.c_void_p, ctypes.c_int64
-    hs = (vp * n)(*[s.h.value for s in solvers])
-    vv = (vp * n)(*[v.data_ptr() for v in vs])
-    xx = (vp * n)(*[x.data_ptr() for x in xs])
-    ld = (i64 * n)(*[s.N for s in solvers])
-    nr = (i64 * n)(*[v.shape[0] for v in vs])
-    for s, v, x in zip(solvers, vs, xs):
-        if v.dtype != torch.complex128 or v.shape != x.shape or v.shape[1] != s.N or not v.is_contiguous() \
-                or not x.is_contiguous():
-            raise ValueError("v, x: contiguous complex128 (nrhs, N) tensors")
-    st = L.bem_solve_batch(hs, n, vv, ld, xx, ld, nr)
+    args, xs = _grouped_args(solvers, vs, xs)
+    st = L.bem_solve_batch(*args)
     if st != 0:
         raise bem.BemError(st, L.bem_last_error(solvers[0].h).decode())
     return xs
+
+
+def grouped_stall_check(solvers: list, vs: list, stall_ms: int = 200) -> tuple[int, str]:
+    """The failure-detection check of the grouped solve (``bem_solve_batch_stall_check``): the
+    same launch with one completion counter that never reaches its target, so its waiting
+    tiles give up after ``stall_ms``.  Returns (status, message); BEM_E_TIMEOUT (7) expected."""
+    L = bem.load_library()
+    args, _ = _grouped_args(solvers, vs, None)
+    st = L.bem_solve_batch_stall_check(*args, int(stall_ms))
+    return st, L.bem_last_error(solvers[0].h).decode()

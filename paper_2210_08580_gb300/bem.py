@@ -28,7 +28,8 @@ EXPORTS = ("bem_default_options", "bem_create", "bem_destroy", "bem_last_error",
            "solve_many", "solve_backward", "bem_get_matrix", "bem_get_info", "bem_timing_enable",
            "bem_timing_report", "solve_many_noalloc", "bem_farfield", "bem_farfield_adjoint",
            "bem_shape_vjp", "bem_rhs_pointsource", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain",
-           "bem_assemble_batch", "bem_factor_rhs_planewave", "bem_solve_batch")
+           "bem_assemble_batch", "bem_factor_rhs_planewave", "bem_solve_batch",
+           "bem_solve_batch_stall_check")
 
 
 class BemOptions(ctypes.Structure):
@@ -55,7 +56,9 @@ class TorchDeviceMemory:
     """Device memory provider of a handle backed by PyTorch's caching allocator: blocks are
     taken on the handle's current stream (``stream_of()``), so a block the library hands back
     is reused only by work ordered after that stream's (what bem_create asks of a provider).
-    ``allocated`` is the number of bytes currently held by the library."""
+    ``allocated`` is the number of bytes currently held by the library.  ``fail_after`` (None:
+    never) injects allocation failures for tests of the error paths: once that many more
+    requests have been served, every request is refused (counted in ``refused``)."""
 
     def __init__(self, device: int, stream_of):
         self.device = device
@@ -64,8 +67,15 @@ class TorchDeviceMemory:
         self.allocated = 0
         self.peak = 0
         self.calls = 0
+        self.fail_after = None
+        self.refused = 0
 
         def _alloc(nbytes, _ctx):
+            if self.fail_after is not None:
+                if self.fail_after <= 0:
+                    self.refused += 1
+                    return None
+                self.fail_after -= 1
             try:
                 ptr = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream_of())
             except Exception:
@@ -139,13 +149,16 @@ def load_library(path: str = LIB_PATH):
                                      ctypes.POINTER(dbl)]
     L.bem_solve_batch.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp), ctypes.POINTER(i64),
                                   ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.bem_solve_batch_stall_check.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                              ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i64), i32]
     L.bem_timing_enable.argtypes = [vp, i32]
     L.bem_timing_report.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     for name in ("bem_create", "bem_destroy", "bem_set_stream", "bem_assemble", "filter_apply",
                  "compress_compact", "factor", "bem_rhs_planewave", "bem_rhs_pointsource", "solve_many", "solve_backward",
                  "bem_get_matrix", "bem_get_info", "bem_timing_enable", "bem_timing_report", "bem_farfield",
                  "bem_farfield_adjoint", "bem_shape_vjp", "bem_rhs_scale", "bem_amplitude_grad", "bem_shape_chain",
-                 "bem_assemble_batch", "bem_factor_rhs_planewave", "bem_solve_batch"):
+                 "bem_assemble_batch", "bem_factor_rhs_planewave", "bem_solve_batch",
+                 "bem_solve_batch_stall_check"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

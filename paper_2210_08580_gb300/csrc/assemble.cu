@@ -291,16 +291,29 @@ static std::vector<double> g_btab_host;
 static std::vector<float> g_btabf_host;
 
 static bem_status bessel_table(bem_ctx* h, const double** out, const float4** outf) {
-    if (!h->btab) {
+    if (!h->btab || !h->btabf) {
         {
             std::lock_guard<std::mutex> lk(g_btab_mutex);
             if (g_btab_host.empty()) build_bessel_table(g_btab_host, g_btabf_host);
         }
+        // all or nothing: the handle keeps both tables, filled, or neither (a failed
+        // allocation or copy must not leave one set for the next call to use)
         const size_t nb = g_btab_host.size() * sizeof(double), nf = g_btabf_host.size() * sizeof(float);
-        BEM_CUDA(h, bem_dmalloc(h, (void**)&h->btab, nb));
-        BEM_CUDA(h, bem_dmalloc(h, (void**)&h->btabf, nf));
-        BEM_CUDA(h, cudaMemcpy(h->btab, g_btab_host.data(), nb, cudaMemcpyHostToDevice));
-        BEM_CUDA(h, cudaMemcpy(h->btabf, g_btabf_host.data(), nf, cudaMemcpyHostToDevice));
+        double* tb = nullptr;
+        float4* tf = nullptr;
+        cudaError_t e = bem_dmalloc(h, (void**)&tb, nb);
+        if (e == cudaSuccess) e = bem_dmalloc(h, (void**)&tf, nf);
+        if (e == cudaSuccess) e = cudaMemcpy(tb, g_btab_host.data(), nb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(tf, g_btabf_host.data(), nf, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            bem_dfree(h, tf);
+            bem_dfree(h, tb);
+            return bem_cuda_check(h, e, "Bessel tables");
+        }
+        bem_dfree(h, h->btabf);
+        bem_dfree(h, h->btab);
+        h->btab = tb;
+        h->btabf = tf;
     }
     *out = h->btab;
     *outf = h->btabf;

@@ -13,8 +13,9 @@
 // The queue hands out every A tile before any B tile and every B tile before any C tile, so
 // a tile only ever waits for tiles that running CTAs have already taken: no deadlock,
 // whatever the residency.  Per problem and column block a counter records the finished A
-// tiles (B waits on it) and the finished B tiles (C waits on it); the waits are bounded and
-// set DEVERR_TIMEOUT when they give up.
+// tiles (B waits on it) and the finished B tiles (C waits on it); the waits are bounded in
+// wall time (10 s, against about 1 ms in a normal run) and set DEVERR_TIMEOUT when they give
+// up, after which every CTA stops taking tiles and the call returns BEM_E_TIMEOUT.
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -83,15 +84,30 @@ __device__ __forceinline__ void wb_tile(cplx (&acc)[4][4], const cplx* __restric
     }
 }
 
-// Thread 0 waits (bounded) until *c >= target; false when the wait gave up or another CTA
-// reported an error.  Every thread returns the same value.
-__device__ __forceinline__ bool wb_wait(const int* c, int target, int* err, int* s_ok) {
+__device__ __forceinline__ unsigned long long wb_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Thread 0 waits until *c >= target, for at most limit_ns of wall time (the global timer;
+// a spin count caps it as well); false when the wait gave up (DEVERR_TIMEOUT) or another
+// CTA reported an error.  Every thread returns the same value.
+__device__ __forceinline__ bool wb_wait(const int* c, int target, int* err, int* s_ok,
+                                        unsigned long long limit_ns) {
     if (threadIdx.x == 0) {
         int ok = 1;
+        const unsigned long long t0 = wb_globaltimer();
         for (long long spins = 0; wb_ld_acquire(c) < target; ++spins) {
-            if (spins > (1ll << 24)) { atomicOr(err, DEVERR_TIMEOUT); ok = 0; break; }
-            if ((spins & 255) == 255 && *(volatile int*)err) { ok = 0; break; }
-            if (spins > 32) __nanosleep(64);
+            if ((spins & 63) == 63) {
+                if (*(volatile int*)err) { ok = 0; break; }
+                if (wb_globaltimer() - t0 > limit_ns || spins > (1ll << 26)) {
+                    atomicOr(err, DEVERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+            if (spins > 32) __nanosleep(128);
         }
         *s_ok = ok;
     }
@@ -111,7 +127,8 @@ __device__ __forceinline__ void wb_signal(int* c) {
 
 __global__ void __launch_bounds__(256) k_woodbury_batch(const WbProb* __restrict__ ps, int nprob,
                                                         long long nA, long long nB, long long nC,
-                                                        unsigned long long* queue, int* err) {
+                                                        unsigned long long* queue, int* err,
+                                                        unsigned long long limit_ns) {
     __shared__ cplx As[WB_BK][WB_T];
     __shared__ cplx Bs[WB_BK][WB_T];
     __shared__ long long s_t;
@@ -175,7 +192,7 @@ __global__ void __launch_bounds__(256) k_woodbury_batch(const WbProb* __restrict
             // B: tile (rb, cb) of T2 = Kinv T, T = sum of the slices in slice order
             const long long l = q - nA - P.first[1];
             const int rb = (int)(l % P.mr), cb = (int)(l / P.mr);
-            if (!wb_wait(P.cnt + cb, P.mr * P.nch, err, &s_ok)) continue;
+            if (!wb_wait(P.cnt + cb, P.mr * P.nch, err, &s_ok, limit_ns)) continue;
             const int m0 = rb * WB_T, n0 = cb * WB_T;
             const cplx* part = P.part;
             const long long slice = (long long)P.r * P.nrhs;
@@ -209,7 +226,7 @@ __global__ void __launch_bounds__(256) k_woodbury_batch(const WbProb* __restrict
             // C: tile (rb, cb) of x = v / beta - beta^-2 U T2
             const long long l = q - nA - nB - P.first[2];
             const int rb = (int)(l % P.mN), cb = (int)(l / P.mN);
-            if (!wb_wait(P.cnt + P.ncb + cb, P.mr, err, &s_ok)) continue;
+            if (!wb_wait(P.cnt + P.ncb + cb, P.mr, err, &s_ok, limit_ns)) continue;
             const int m0 = rb * WB_T, n0 = cb * WB_T;
             const cplx* T2 = P.T2;
             const int r = P.r, nrhs = P.nrhs;
@@ -236,8 +253,11 @@ __global__ void __launch_bounds__(256) k_woodbury_batch(const WbProb* __restrict
 
 static size_t wb_align(size_t b) { return (b + 255) & ~(size_t)255; }
 
-extern "C" bem_status bem_solve_batch(bem_handle* hs, int64_t nprob, const void* const* v_dev, const int64_t* ldv,
-                                      void* const* x_dev, const int64_t* ldx, const int64_t* nrhs) {
+// stall_ms > 0: the failure-detection check (bem_solve_batch_stall_check): the first stage-A
+// counter of the first problem in the queue starts far below its target, so the waits of that
+// block's stage-B tiles give up after stall_ms (every wait then runs with that limit).
+static bem_status solve_batch_impl(bem_handle* hs, int64_t nprob, const void* const* v_dev, const int64_t* ldv,
+                                   void* const* x_dev, const int64_t* ldx, const int64_t* nrhs, int stall_ms) {
     if (!hs || !v_dev || !ldv || !x_dev || !ldx || !nrhs || nprob < 1 || nprob > 65536) return BEM_E_INVALID;
     for (int64_t q = 0; q < nprob; ++q)
         if (!hs[q]) return BEM_E_INVALID;
@@ -316,6 +336,11 @@ extern "C" bem_status bem_solve_batch(bem_handle* hs, int64_t nprob, const void*
     }
     bem_status st = BEM_OK;
     e = cudaMemsetAsync(buf, 0, head, h0->stream);
+    static const int k_stalled = -(1 << 30);
+    if (e == cudaSuccess && stall_ms > 0)
+        e = cudaMemcpyAsync(ps[0].cnt, &k_stalled, sizeof(int), cudaMemcpyHostToDevice, h0->stream);
+    // a wait lasts about one stage-A tile (about 1 ms of one SM's FP64 pipe) in a normal run
+    const unsigned long long limit_ns = stall_ms > 0 ? 1000000ull * (unsigned long long)stall_ms : 10000000000ull;
     if (e == cudaSuccess) e = cudaMemcpyAsync(dps, ps.data(), sizeof(WbProb) * nprob, cudaMemcpyHostToDevice, h0->stream);
     int per = 0, nsm = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_woodbury_batch, 256, 0);
@@ -325,7 +350,8 @@ extern "C" bem_status bem_solve_batch(bem_handle* hs, int64_t nprob, const void*
         const long long all = tot[0] + tot[1] + tot[2];
         const long long ctas = std::min<long long>(all, (long long)std::max(per, 1) * nsm);
         BEM_TIMED(h0, "k_woodbury_batch", (k_woodbury_batch<<<(unsigned)ctas, 256, 0, h0->stream>>>(
-                                              dps, (int)nprob, tot[0], tot[1], tot[2], queue, h0->dev_err)));
+                                              dps, (int)nprob, tot[0], tot[1], tot[2], queue, h0->dev_err,
+                                              limit_ns)));
         e = cudaGetLastError();
         if (e != cudaSuccess) st = bem_cuda_check(h0, e, "k_woodbury_batch");
     }
@@ -349,4 +375,16 @@ extern "C" bem_status bem_solve_batch(bem_handle* hs, int64_t nprob, const void*
         return bem_fail(h0, BEM_E_CUDA, "bem_solve_batch: device error flag set");
     }
     return BEM_OK;
+}
+
+extern "C" bem_status bem_solve_batch(bem_handle* hs, int64_t nprob, const void* const* v_dev, const int64_t* ldv,
+                                      void* const* x_dev, const int64_t* ldx, const int64_t* nrhs) {
+    return solve_batch_impl(hs, nprob, v_dev, ldv, x_dev, ldx, nrhs, 0);
+}
+
+extern "C" bem_status bem_solve_batch_stall_check(bem_handle* hs, int64_t nprob, const void* const* v_dev,
+                                                  const int64_t* ldv, void* const* x_dev, const int64_t* ldx,
+                                                  const int64_t* nrhs, int stall_ms) {
+    if (stall_ms < 1 || stall_ms > 10000) return BEM_E_INVALID;
+    return solve_batch_impl(hs, nprob, v_dev, ldv, x_dev, ldx, nrhs, stall_ms);
 }

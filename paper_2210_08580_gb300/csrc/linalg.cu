@@ -1011,18 +1011,24 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* 
         // of 9 words per column and the window exponent, all starting at zero
         unsigned long long* lim = nullptr;
         const size_t lim_words = (size_t)3 * 9 * n + 1;
-        BEM_CUDA(h, bem_dmalloc_async(h, (void**)&lim, sizeof(unsigned long long) * lim_words));
-        BEM_CUDA(h, cudaMemsetAsync(lim, 0, sizeof(unsigned long long) * lim_words, h->stream));
-        int* emax = reinterpret_cast<int*>(lim + 27 * (size_t)n);
         float4* Pc = nullptr;                   // the next pivot column, two buffers
-        BEM_CUDA(h, bem_dmalloc_async(h, (void**)&Pc, sizeof(float4) * 2 * (size_t)N));
-        const int64_t cnt = N * (int64_t)n;
-        BEM_TIMED(h, "k_to_dfl", (k_to_dfl<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(reinterpret_cast<float4*>(X), cnt)));
-        BEM_LAUNCH(h, "k_to_dfl");
         // rows of R are written by column as the steps go (the pivots move columns between
         // positions after their earlier rows are known) and placed by position afterwards
         cplx* Rc = nullptr;
-        BEM_CUDA(h, bem_dmalloc_async(h, (void**)&Rc, sizeof(cplx) * (size_t)n * n));
+        cudaError_t ae = bem_dmalloc_async(h, (void**)&lim, sizeof(unsigned long long) * lim_words);
+        if (ae == cudaSuccess) ae = bem_dmalloc_async(h, (void**)&Pc, sizeof(float4) * 2 * (size_t)N);
+        if (ae == cudaSuccess) ae = bem_dmalloc_async(h, (void**)&Rc, sizeof(cplx) * (size_t)n * n);
+        if (ae != cudaSuccess) {                // nothing launched yet: hand back what was taken
+            bem_dfree_async(h, Rc);
+            bem_dfree_async(h, Pc);
+            bem_dfree_async(h, lim);
+            return bem_cuda_check(h, ae, "QR temporaries");
+        }
+        BEM_CUDA(h, cudaMemsetAsync(lim, 0, sizeof(unsigned long long) * lim_words, h->stream));
+        int* emax = reinterpret_cast<int*>(lim + 27 * (size_t)n);
+        const int64_t cnt = N * (int64_t)n;
+        BEM_TIMED(h, "k_to_dfl", (k_to_dfl<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(reinterpret_cast<float4*>(X), cnt)));
+        BEM_LAUNCH(h, "k_to_dfl");
         float4* Xf = reinterpret_cast<float4*>(X);
         void* args_df[] = {&Xf, &N, &n, &Rc, &perm, &lim, &emax, &Pc, &h->bar, &h->dev_err};
         const size_t smem = (size_t)QR_NP * (8 * sizeof(float4) + 8 * sizeof(float) + 3 * sizeof(float4) + sizeof(float2));
@@ -1039,10 +1045,16 @@ bem_status launch_house_qr(bem_ctx* h, cplx* X, int64_t N, int n, cplx* R, int* 
     double* partC = nullptr;
     cplx* partW = nullptr;
     unsigned long long* cnq = nullptr;
-    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&partC, sizeof(double) * (size_t)G * n));
-    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&cnq, sizeof(unsigned long long) * 2 * (size_t)n));
+    cudaError_t ae = bem_dmalloc_async(h, (void**)&partC, sizeof(double) * (size_t)G * n);
+    if (ae == cudaSuccess) ae = bem_dmalloc_async(h, (void**)&cnq, sizeof(unsigned long long) * 2 * (size_t)n);
+    if (ae == cudaSuccess) ae = bem_dmalloc_async(h, (void**)&partW, sizeof(cplx) * (size_t)G * n);
+    if (ae != cudaSuccess) {                    // nothing launched yet: hand back what was taken
+        bem_dfree_async(h, partW);
+        bem_dfree_async(h, cnq);
+        bem_dfree_async(h, partC);
+        return bem_cuda_check(h, ae, "QR temporaries");
+    }
     BEM_CUDA(h, cudaMemsetAsync(cnq, 0, sizeof(unsigned long long) * 2 * (size_t)n, h->stream));
-    BEM_CUDA(h, bem_dmalloc_async(h, (void**)&partW, sizeof(cplx) * (size_t)G * n));
     void* args[] = {&X, &N, &n, &R, &perm, &partC, &cnq, &partW, &h->bar, &h->dev_err};
     BEM_TIMED(h, "k_house_qr", st = coop_launch(h, (const void*)k_house_qr, G, 256, args, "k_house_qr"));
     bem_dfree_async(h, partC);

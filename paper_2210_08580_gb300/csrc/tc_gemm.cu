@@ -800,7 +800,7 @@ static bem_status reserve(bem_ctx* h, TcOperand& op, int64_t rows, int64_t Kp, i
         op.cap = need;
     }
     if ((size_t)rows * sizeof(int) > op.exp_cap) {
-        if (op.exps) { cudaStreamSynchronize(h->stream); bem_dfree(h, op.exps); op.exps = nullptr; }
+        if (op.exps) { cudaStreamSynchronize(h->stream); bem_dfree(h, op.exps); op.exps = nullptr; op.exp_cap = 0; }
         BEM_CUDA(h, bem_dmalloc(h, (void**)&op.exps, (size_t)rows * sizeof(int)));
         op.exp_cap = (size_t)rows * sizeof(int);
     }

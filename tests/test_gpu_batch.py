@@ -141,6 +141,29 @@ def test_grouped_solve_edges(B):
         s.close()
 
 
+def test_grouped_solve_wait_timeout_is_reported(B, problems):
+    """Failure detection without a GPU fault: the grouped kernel with one completion counter
+    that nothing brings to its target gives up the waits on it after 0.2 s of wall time, the
+    call returns BEM_E_TIMEOUT, and the same handles then solve normally."""
+    import time
+    bem, batch = B
+    L = bem.load_library()
+    bs = batch.BatchSolver(problems, prec="fp64", n_streams=2)
+    res = bs.run()
+    vs = [out["v"] for out in res]
+    t0 = time.perf_counter()
+    st, msg = batch.grouped_stall_check(bs.solvers, vs, stall_ms=200)
+    dt = time.perf_counter() - t0
+    assert st == 7 and "timed out" in msg, (st, msg)
+    assert 0.15 <= dt <= 5.0, dt
+    xg = batch.solve_grouped(bs.solvers, vs)
+    torch.cuda.synchronize()
+    for i, out in enumerate(res):
+        err = float((xg[i] - out["x"]).abs().max() / out["x"].abs().max())
+        assert err <= 1e-13, (i, err)
+    bs.close()
+
+
 def test_stream_tuner_picks_per_bucket(B, problems):
     _, batch = B
     best = batch.autotune_streams(problems[:3], prec="fp64", candidates=(1, 2), sample=2)

@@ -65,3 +65,50 @@ def test_one_hook_without_the_other_is_rejected():
     h = ctypes.c_void_p()
     st = L.bem_create(ctypes.byref(h), 0, None, None, mem.alloc_fn, bem.FREE_FN(), None)
     assert st == 1 and not h.value
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_every_refused_allocation_is_reported_and_recoverable(prec):
+    """Allocation failure injected on the host (the provider refuses every request after the
+    first n): for each n up to the path's last allocation, the failing call returns
+    BEM_E_NOMEM, the same handle then runs the whole path once the provider serves again and
+    gives the bits of a handle that never failed, and bem_destroy hands back every byte."""
+    from paper_2210_08580_gb300 import bem
+    v, _, _ = I.equal_chord_mesh(I.random_star(5), 1024)
+    vd = torch.from_numpy(v).cuda()
+    ang = torch.from_numpy(I.planewave_angles(16)).cuda()
+
+    def path(s):
+        s.assemble(vd, 1.5, ops="SW")
+        s.filter_apply(41)
+        s.compress(1e-10)
+        s.factor()
+        x = s.solve(s.rhs_planewave(ang))
+        torch.cuda.synchronize()
+        return x
+
+    ref = bem.Solver(device=0, prec=prec)
+    x_ref = path(ref)
+    ref.close()
+    failed = 0
+    for n in range(400):
+        s = bem.Solver(device=0, prec=prec)
+        mem = s.memory
+        mem.fail_after = n
+        try:
+            path(s)
+            clean = True
+        except bem.BemError as e:
+            assert e.status == 2, (n, str(e))
+            clean = False
+        torch.cuda.synchronize()
+        if not clean:
+            failed += 1
+            assert mem.refused >= 1
+            mem.fail_after = None
+            assert torch.equal(path(s), x_ref), n
+        s.close()
+        assert mem.allocated == 0 and not mem.sizes, (n, mem.allocated)
+        if clean:
+            break
+    assert clean and failed >= 5, (failed, n)
