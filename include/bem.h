@@ -312,12 +312,13 @@ bem_status solve_many_noalloc(bem_handle h, const void* v_dev, int64_t ldv, void
  * launch: problem q solves with handle hs[q] the nrhs[q] right-hand sides v_dev[q] (column-major
  * N_q x nrhs[q] complex128, leading dimension ldv[q]) into x_dev[q] (ldx[q]).  The arrays are
  * host arrays of nprob entries; the buffers are device memory the caller owns.  CTAs take
- * 64 x 64 tiles of all problems' products from one global queue (V^H v in 256-long slices of
- * N, then the core product, then x), so small problems fill the GPU beside large ones;
+ * 64 x 64 tiles of all problems' products from one global queue (V^H v in slices of N, 256
+ * long up to N = 16384 and at most 64 per problem beyond, then the core product, then x), so small problems fill the GPU beside large ones;
  * a tile that needs another stage's results waits for them with a bounded device-side wait.
  * Runs on hs[0]'s stream after every handle's earlier work; every handle's later work waits
  * for it.  Synchronises hs[0]'s stream (to read the device status).  Scratch: the core
- * products, sum over q of r_q nrhs[q] (ceil(N_q / 256) + 1) complex doubles, taken from
+ * products, sum over q of r_q nrhs[q] (s_q + 1) complex doubles, s_q = min(ceil(N_q / 256), 64)
+ * slices (up to 65 r_q nrhs[q]), taken from
  * hs[0]'s device memory provider for the call.  The same handle may appear more than once;
  * no x_dev[q] may overlap any v_dev or another x_dev.  On a BEM_MIXED_BF16 handle it solves
  * with that handle's factors in FP64 without refinement, as solve_many_noalloc does.  The

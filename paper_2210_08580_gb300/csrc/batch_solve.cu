@@ -6,7 +6,9 @@
 // queue by persistent CTAs:
 //     A  partial products V^H v over 256-long slices of N (split K: every SM gets work even
 //        when each problem has a handful of right-hand-side blocks, and a problem's chain of
-//        stages stays short: 16 K steps per slice instead of N/16),
+//        stages stays short: 16 K steps per slice instead of N/16); above N = 16384 the
+//        slices lengthen to ceil(N / 64), rounded up to 16, so that no problem keeps more
+//        than 64 partial products (the slicing depends on the problem's own N only),
 //     B  T2 = Kinv T, with T summed from the slices in slice order (a fixed order: the
 //        result does not depend on which CTA ran what),
 //     C  x = v / beta - beta^-2 U T2.
@@ -24,7 +26,8 @@
 
 #define WB_T 64      // tile edge (rows and right-hand sides)
 #define WB_BK 16     // K step staged in shared memory
-#define WB_KC 256    // slice of N per stage-A tile
+#define WB_KC 256    // slice of N per stage-A tile (at least)
+#define WB_NCH 64    // most slices per problem
 
 struct WbProb {
     const cplx* U;       // N x r, ld N
@@ -37,7 +40,7 @@ struct WbProb {
     int* cnt;            // [0, ncb): A tiles done per column block; [ncb, 2 ncb): B tiles done
     long long ldv, ldx;
     long long first[3];  // first tile of this problem in each stage's range
-    int N, r, nrhs, mr, ncb, nch, mN;
+    int N, r, nrhs, mr, ncb, nch, mN, kc;
     double ib, c2;       // 1 / beta and -1 / beta^2
 };
 
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(256) k_woodbury_batch(const WbProb* __restrict
             const int c = (int)(l % P.nch);
             const int cb = (int)(l / P.nch);
             const int m0 = rb * WB_T, n0 = cb * WB_T;
-            const int kbeg = c * WB_KC, kend = min(P.N, kbeg + WB_KC);
+            const int kbeg = c * P.kc, kend = min(P.N, kbeg + P.kc);
             const cplx* v = P.v;
             const long long ldv = P.ldv;
             const int nrhs = P.nrhs;
@@ -295,7 +298,8 @@ static bem_status solve_batch_impl(bem_handle* hs, int64_t nprob, const void* co
         P.N = (int)h->N; P.r = (int)h->r; P.nrhs = (int)nrhs[q];
         P.mr = (P.r + WB_T - 1) / WB_T;
         P.ncb = (P.nrhs + WB_T - 1) / WB_T;
-        P.nch = (P.N + WB_KC - 1) / WB_KC;
+        P.kc = std::max(WB_KC, ((P.N + WB_NCH - 1) / WB_NCH + 15) / 16 * 16);
+        P.nch = (P.N + P.kc - 1) / P.kc;
         P.mN = (P.N + WB_T - 1) / WB_T;
         P.ib = 1.0 / h->beta;
         P.c2 = -1.0 / (h->beta * h->beta);

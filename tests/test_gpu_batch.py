@@ -141,6 +141,37 @@ def test_grouped_solve_edges(B):
         s.close()
 
 
+def test_grouped_solve_long_slices(B):
+    """Above N = 16384 the slices of V^H v lengthen (at most 64 per problem): N = 20000 takes
+    63 slices of 320 (the last 160), beside a small problem with 256-long slices; each against
+    the handle's own FP64 Woodbury solve."""
+    bem, batch = B
+    L = bem.load_library()
+    star = I.cos_star(1.0, 0.3, 5)
+    ss = []
+    for N, k in ((20000, 0.5), (700, 1.0)):
+        s = bem.Solver(device=0)
+        s.assemble(torch.from_numpy(I.equal_chord_mesh(star, N)[0]).cuda(), k, ops="SW")
+        s.filter_apply(21)
+        s.compress(1e-10)
+        s.factor()
+        ss.append(s)
+    gen = torch.Generator().manual_seed(11)
+    vs = [torch.complex(torch.randn((nr, s.N), generator=gen, dtype=torch.float64),
+                        torch.randn((nr, s.N), generator=gen, dtype=torch.float64)).cuda()
+          for nr, s in zip((3, 70), ss)]
+    xg = batch.solve_grouped(ss, vs)
+    torch.cuda.synchronize()
+    for s, v, x in zip(ss, vs, xg):
+        x1 = torch.empty_like(v)
+        assert L.solve_many_noalloc(s.h, v.data_ptr(), s.N, x1.data_ptr(), s.N, v.shape[0]) == 0
+        torch.cuda.synchronize()
+        err = float((x - x1).abs().max() / x1.abs().max())
+        assert err <= 1e-13, (s.N, err)
+    for s in ss:
+        s.close()
+
+
 def test_grouped_solve_wait_timeout_is_reported(B, problems):
     """Failure detection without a GPU fault: the grouped kernel with one completion counter
     that nothing brings to its target gives up the waits on it after 0.2 s of wall time, the
