@@ -307,7 +307,7 @@ bem_status solve_backward(bem_handle h, const void* g_dev, int64_t ldg, void* la
 bem_status solve_many_noalloc(bem_handle h, const void* v_dev, int64_t ldv, void* x_dev, int64_t ldx,
                               int64_t nrhs);
 
-/* bem_solve_batch -- the FP64 Woodbury solve of solve_many (Sec. IV-A: x = v/beta -
+/* bem_solve_batch -- the FP64 Woodbury solve of solve_many (Sec. IV-C: x = v/beta -
  * beta^-2 U (I_r + beta^-1 V^H U)^-1 V^H v) for nprob factored problems in ONE persistent
  * launch: problem q solves with handle hs[q] the nrhs[q] right-hand sides v_dev[q] (column-major
  * N_q x nrhs[q] complex128, leading dimension ldv[q]) into x_dev[q] (ldx[q]).  The arrays are

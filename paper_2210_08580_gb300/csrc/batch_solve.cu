@@ -1,6 +1,6 @@
 // Grouped FP64 Woodbury solve of many factored problems in ONE persistent launch: the solve
 // stage of the batching layer (the paper solves one geometry at a time; the solve itself is
-// the Woodbury form of the compressed operator, Sec. IV-A):
+// the Woodbury form of the compressed operator, Sec. IV-C):
 //     x_p = v_p / beta_p - beta_p^-2 U_p Kinv_p (V_p^H v_p)      for every problem p.
 // Three stages of 64 x 64 complex tiles (column-major, FP64 FMAs) taken from one global
 // queue by persistent CTAs:
