@@ -43,3 +43,27 @@ def test_binding_fails_loudly_without_library(tmp_path):
         bem._lib = None
         bem.load_library(str(tmp_path / "missing.so"))
     bem._lib = None
+
+
+def test_batch_solve_refuses_bad_arguments_before_any_device_work(lib):
+    """bem_solve_batch and its stall check validate their host arrays first: null arrays, a
+    null handle, nprob outside [1, 65536] and a stall limit outside [1, 10000] ms return
+    BEM_E_INVALID (1) without touching a device."""
+    import ctypes
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    f = lib.bem_solve_batch
+    f.argtypes = [ctypes.POINTER(vp), i64, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                  ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    f.restype = ctypes.c_int
+    g = lib.bem_solve_batch_stall_check
+    g.argtypes = f.argtypes + [ctypes.c_int]
+    g.restype = ctypes.c_int
+    one = (i64 * 1)(16)
+    ptrs = (vp * 1)(None)
+    assert f(None, 1, ptrs, one, ptrs, one, one) == 1
+    assert f(ptrs, 1, ptrs, one, ptrs, one, one) == 1          # a null handle
+    assert f(ptrs, 0, ptrs, one, ptrs, one, one) == 1
+    assert f(ptrs, 65537, ptrs, one, ptrs, one, one) == 1
+    assert f(ptrs, 1, None, one, ptrs, one, one) == 1
+    assert g(ptrs, 1, ptrs, one, ptrs, one, one, 0) == 1
+    assert g(ptrs, 1, ptrs, one, ptrs, one, one, 10001) == 1
